@@ -1,0 +1,426 @@
+"""CPU oracle of the LightNE 2.0 hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline / reference
+legs of ``bench.py`` may import this package. The product path (the CUDA
+library and its binding) never imports, links or runs anything here, and this
+package never imports the product.
+
+Plain, slow, obviously checkable restatement of what the method computes, in
+FP64, each function citing the passage it follows:
+
+* sampling (C, ``lne_oracle.c``): Algorithm 1 (PathSampling), Algorithm 3
+  (per-edge sampling, Sec. 4.2) and the walk-step rule of Sec. 4.2;
+* ``netmf_values`` / ``sparsifier_csr``: Eq. 1 (the NetMF matrix with the
+  truncated logarithm) estimated from the sample counts;
+* ``gaussian_sketch``: the Gaussian test matrix of Algorithm 4, line 2;
+* ``eig_svd``: Algorithm 2 (eigSVD);
+* ``fast_randomized_svd``: Algorithm 4;
+* ``embedding_from_svd``: X = U Sigma^{1/2} (Sec. 3.2);
+* ``spectral_propagation``: Sec. 3.3 (Chebyshev filter in the normalised
+  Laplacian, then the economic SVD of the last stage, Sec. 5.4);
+* ``netmf_dense``: Eq. 1 evaluated densely, for tiny graphs.
+
+Library primitives used as single steps: numpy sort/unique, scipy sparse
+matrix products, ``numpy.linalg.eigh`` (the eig of Algorithm 2) and
+``scipy.special.iv`` (Bessel coefficients). Each is pinned by tests against
+closed forms, not against itself.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.special
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lne_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liblne_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C part of the oracle (gcc, no FMA contraction, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        f64p = ctypes.POINTER(ctypes.c_double)
+        L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.oracle_window_thresholds.argtypes = [ctypes.c_int, f64p, u64p]
+        L.oracle_arc_rate.argtypes = [ctypes.c_double, ctypes.c_int64, u64p, u64p]
+        L.oracle_arc_samples.argtypes = [ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+        L.oracle_arc_samples.restype = ctypes.c_uint64
+        L.oracle_count_samples.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                           ctypes.c_double, ctypes.c_uint64]
+        L.oracle_count_samples.restype = ctypes.c_int64
+        L.oracle_sample_trace.argtypes = [ctypes.c_int64, i64p, i32p, ctypes.c_int, f64p,
+                                          ctypes.c_double, ctypes.c_uint64, ctypes.c_int64,
+                                          ctypes.c_int64, i64p, i32p, i32p, i64p, i64p]
+        L.oracle_sample_trace.restype = ctypes.c_int64
+        L.oracle_sketch_words.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, u32p]
+        L.oracle_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray | None, ctype):
+    if a is None:
+        return ctypes.POINTER(ctype)()
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+# ----------------------------------------------------------------------------
+# random numbers
+# ----------------------------------------------------------------------------
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    """Philox4x32-10 block: 4 counter words, 2 key words -> 4 output words."""
+    c = np.asarray(ctr, dtype=np.uint32).copy()
+    k = np.asarray(key, dtype=np.uint32).copy()
+    out = np.zeros(4, dtype=np.uint32)
+    lib().oracle_philox4x32_10(_ptr(c, ctypes.c_uint32), _ptr(k, ctypes.c_uint32),
+                               _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def window_thresholds(s) -> np.ndarray:
+    """thr_1..thr_{T-1} for drawing r ~ Multinomial(s_1..s_T) (Algorithm 3, line 6)."""
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    thr = np.zeros(max(len(s) - 1, 1), dtype=np.uint64)
+    lib().oracle_window_thresholds(len(s), _ptr(s, ctypes.c_double), _ptr(thr, ctypes.c_uint64))
+    return thr[: len(s) - 1]
+
+
+def arc_rate(S: float, n_arcs: int) -> tuple[int, int]:
+    """(floor(S/2m), floor(frac(S/2m) * 2^32)) -- Algorithm 3, line 3."""
+    b = ctypes.c_uint64()
+    f = ctypes.c_uint64()
+    lib().oracle_arc_rate(float(S), int(n_arcs), ctypes.byref(b), ctypes.byref(f))
+    return int(b.value), int(f.value)
+
+
+def arc_samples(n_arcs: int, S: float, seed: int, a0: int = 0, a1: int | None = None) -> np.ndarray:
+    """n_a for arcs [a0, a1)."""
+    a1 = n_arcs if a1 is None else a1
+    base, thr = arc_rate(S, n_arcs)
+    L = lib()
+    return np.array([L.oracle_arc_samples(a, base, thr, seed) for a in range(a0, a1)], dtype=np.int64)
+
+
+def count_samples(n_arcs: int, S: float, seed: int, a0: int = 0, a1: int | None = None) -> int:
+    a1 = n_arcs if a1 is None else a1
+    return int(lib().oracle_count_samples(n_arcs, a0, a1, float(S), seed))
+
+
+def sample_trace(indptr, indices, T, s, S, seed, a0=0, a1=None, fields=("arc", "r", "sigma", "u1", "v1")):
+    """Every PathSampling draw of arcs [a0, a1) in (arc, sample) order.
+
+    Returns a dict with the requested fields: ``arc``, window ``r``, split
+    ``sigma`` and the ordered endpoints ``u1`` (walked from the arc's source)
+    and ``v1`` (walked from its target).
+    """
+    indptr = np.ascontiguousarray(indptr, dtype=np.int64)
+    indices = np.ascontiguousarray(indices, dtype=np.int32)
+    s = np.ascontiguousarray(s, dtype=np.float64)
+    n = indptr.shape[0] - 1
+    n_arcs = int(indptr[-1])
+    a1 = n_arcs if a1 is None else a1
+    total = count_samples(n_arcs, S, seed, a0, a1)
+    out = {
+        "arc": np.zeros(total, np.int64) if "arc" in fields else None,
+        "r": np.zeros(total, np.int32) if "r" in fields else None,
+        "sigma": np.zeros(total, np.int32) if "sigma" in fields else None,
+        "u1": np.zeros(total, np.int64) if "u1" in fields else None,
+        "v1": np.zeros(total, np.int64) if "v1" in fields else None,
+    }
+    got = lib().oracle_sample_trace(
+        n, _ptr(indptr, ctypes.c_int64), _ptr(indices, ctypes.c_int32), len(s),
+        _ptr(s, ctypes.c_double), float(S), int(seed), int(a0), int(a1),
+        _ptr(out["arc"], ctypes.c_int64), _ptr(out["r"], ctypes.c_int32),
+        _ptr(out["sigma"], ctypes.c_int32), _ptr(out["u1"], ctypes.c_int64),
+        _ptr(out["v1"], ctypes.c_int64))
+    assert got == total
+    return {k: v for k, v in out.items() if v is not None}
+
+
+def sample_pairs(indptr, indices, T, s, S, seed, a0=0, a1=None):
+    """Canonical endpoint pairs (x = min, y = max) of every draw of arcs [a0, a1)."""
+    tr = sample_trace(indptr, indices, T, s, S, seed, a0, a1, fields=("u1", "v1"))
+    return np.minimum(tr["u1"], tr["v1"]), np.maximum(tr["u1"], tr["v1"])
+
+
+def sparsifier_counts(indptr, indices, T, s, S, seed):
+    """Exact multiplicity K_xy of every sampled unordered pair (x <= y).
+
+    The aggregation of Sec. 4.2 (hash table with atomic counts) computes the
+    multiset of sampled pairs; here it is a sort and a run-length count.
+    Returns (x, y, count) sorted by (x, y).
+    """
+    n = len(indptr) - 1
+    x, y = sample_pairs(indptr, indices, T, s, S, seed)
+    keys, cnt = np.unique(x * n + y, return_counts=True)
+    return keys // n, keys % n, cnt.astype(np.int64)
+
+
+# ----------------------------------------------------------------------------
+# Eq. 1: from counts to the truncated-log NetMF estimate
+# ----------------------------------------------------------------------------
+
+def netmf_scale(vol: float, S: float, b: float = 1.0) -> tuple[float, float]:
+    """(alpha_off, alpha_diag) with entry = alpha * K_xy / (d_x d_y).
+
+    E[ordered count C_xy] = S/vol * [sum_r s_r D (D^-1 A)^r]_xy, so the Eq. 1
+    entry vol/b * [sum_r s_r (D^-1 A)^r D^-1]_xy equals vol^2/(S b) * E[C_xy] /
+    (d_x d_y). An unordered off-diagonal count K_xy = C_xy + C_yx estimates
+    2 E[C_xy]; a diagonal count estimates E[C_xx].
+    """
+    vv = vol * vol
+    return vv / ((2.0 * S) * b), vv / (S * b)
+
+
+def netmf_values(x, y, cnt, deg, S, b=1.0):
+    """Pre-log entries v, keep mask (v > 1) and float32 trunc_log values (Eq. 1).
+
+    v = fl(fl(K * alpha) / fl(d_x * d_y)); trunc_log(v) = max(0, log v) is zero
+    unless v > 1, and zero entries are dropped from the sparse matrix.
+    """
+    deg = np.asarray(deg, dtype=np.float64)
+    vol = float(deg.sum())
+    a_off, a_diag = netmf_scale(vol, float(S), float(b))
+    alpha = np.where(x == y, a_diag, a_off)
+    v = (np.asarray(cnt, dtype=np.float64) * alpha) / (deg[x] * deg[y])
+    keep = v > 1.0
+    val = np.zeros(v.shape, dtype=np.float32)
+    val[keep] = np.log(v[keep]).astype(np.float32)
+    return v, keep, val
+
+
+def sparsifier_csr(n, x, y, val):
+    """Symmetric CSR of the kept entries: both triangles, rows sorted by column."""
+    off = x != y
+    rows = np.concatenate([x, y[off]])
+    cols = np.concatenate([y, x[off]])
+    data = np.concatenate([val, val[off]]).astype(np.float32)
+    order = np.lexsort((cols, rows))
+    rows, cols, data = rows[order], cols[order], data[order]
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=indptr[1:])
+    return indptr, cols.astype(np.int32), data
+
+
+def sparsifier(indptr, indices, T, s, S, seed, b=1.0):
+    """Counts -> trunc_log -> CSR. Returns a dict with every intermediate."""
+    n = len(indptr) - 1
+    deg = np.diff(indptr)
+    x, y, cnt = sparsifier_counts(indptr, indices, T, s, S, seed)
+    v, keep, val = netmf_values(x, y, cnt, deg, S, b)
+    mp, mc, mv = sparsifier_csr(n, x[keep], y[keep], val[keep])
+    return dict(x=x, y=y, cnt=cnt, v=v, keep=keep, val=val, indptr=mp, indices=mc, data=mv)
+
+
+def netmf_dense(indptr, indices, T, s, b=1.0):
+    """Eq. 1 inside the truncated log, densely: vol/b * sum_r s_r (D^-1 A)^r D^-1.
+
+    For tiny graphs only (n <= a few hundred). ``s`` is normalised to sum 1.
+    """
+    n = len(indptr) - 1
+    A = sp.csr_matrix((np.ones(len(indices)), indices, indptr), shape=(n, n)).toarray()
+    d = A.sum(1)
+    vol = d.sum()
+    P = A / d[:, None]
+    s = np.asarray(s, dtype=np.float64)
+    s = s / s.sum()
+    acc = np.zeros((n, n))
+    Pr = np.eye(n)
+    for r in range(1, T + 1):
+        Pr = Pr @ P
+        acc += s[r - 1] * Pr
+    return vol / b * acc / d[None, :]
+
+
+# ----------------------------------------------------------------------------
+# randomized SVD (Algorithms 2 and 4)
+# ----------------------------------------------------------------------------
+
+def gaussian_sketch(n: int, c: int, seed: int) -> np.ndarray:
+    """Omega = randn(n, c) (Algorithm 4, line 2) by Box-Muller from Philox words.
+
+    Row i, column block cb = col // 4 uses the 4 words of counter (i, cb, 0, 0),
+    key (seed_lo ^ 0x4f4d4547, seed_hi); words (w0, w1) give columns 4cb, 4cb+1
+    and (w2, w3) give 4cb+2, 4cb+3 with u = (w + 0.5) / 2^32 and
+    z = sqrt(-2 ln u_a) * (cos, sin)(2 pi u_b).
+    """
+    nblk = (c + 3) // 4
+    words = np.zeros((n, nblk, 4), dtype=np.uint32)
+    lib().oracle_sketch_words(n, nblk, int(seed), _ptr(words, ctypes.c_uint32))
+    u = (words.astype(np.float64) + 0.5) / 4294967296.0
+    rad = np.sqrt(-2.0 * np.log(u[:, :, 0::2]))
+    ang = 2.0 * np.pi * u[:, :, 1::2]
+    z = np.empty((n, nblk, 4))
+    z[:, :, 0] = rad[:, :, 0] * np.cos(ang[:, :, 0])
+    z[:, :, 1] = rad[:, :, 0] * np.sin(ang[:, :, 0])
+    z[:, :, 2] = rad[:, :, 1] * np.cos(ang[:, :, 1])
+    z[:, :, 3] = rad[:, :, 1] * np.sin(ang[:, :, 1])
+    return z.reshape(n, nblk * 4)[:, :c].copy()
+
+
+def fix_signs(U: np.ndarray, *others: np.ndarray):
+    """Make the largest-magnitude entry of every column of U positive (first
+    index on ties) and flip the matching columns of ``others``."""
+    idx = np.argmax(np.abs(U), axis=0)
+    sg = np.sign(U[idx, np.arange(U.shape[1])])
+    sg[sg == 0] = 1.0
+    return (U * sg,) + tuple(o * sg for o in others)
+
+
+def eig_svd(X: np.ndarray):
+    """Algorithm 2 (eigSVD): C = X^T X; [V, D] = eig(C); S = sqrt(D); U = X V S^-1.
+
+    Columns are returned by decreasing singular value (the algorithm's callers
+    take the leading d), with the sign convention of ``fix_signs`` on U.
+    """
+    C = X.T @ X
+    D, V = np.linalg.eigh(C)
+    order = np.argsort(D)[::-1]
+    D = np.maximum(D[order], 0.0)
+    V = V[:, order]
+    S = np.sqrt(D)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        U = (X @ V) / S[None, :]
+    U[:, S == 0] = 0.0
+    U, V = fix_signs(U, V)
+    return U, S, V
+
+
+def spmm(indptr, indices, data, X):
+    n = len(indptr) - 1
+    M = sp.csr_matrix((np.asarray(data, np.float64), indices, indptr), shape=(n, X.shape[0]))
+    return M @ X
+
+
+def fast_randomized_svd(indptr, indices, data, d: int, q: int, oversample: int, seed: int,
+                        Omega: np.ndarray | None = None):
+    """Algorithm 4 (Fast Randomized SVD) on the symmetric sparse M.
+
+    Omega = randn(n, d+s); Y = M Omega; Q = eigSVD(Y).U; q times: Y = M Q,
+    T = Q, [Q, Sigma, V] = eigSVD(Y); return U = Q(:, 1:d), Sigma(1:d),
+    V = T V(:, 1:d). With q = 0 the eigSVD of M Omega supplies Sigma and V.
+    """
+    n = len(indptr) - 1
+    c = d + oversample
+    if Omega is None:
+        Omega = gaussian_sketch(n, c, seed)
+    Y = spmm(indptr, indices, data, Omega)
+    Q, Sig, V = eig_svd(Y)
+    T = Omega
+    for _ in range(q):
+        Y = spmm(indptr, indices, data, Q)
+        T = Q
+        Q, Sig, V = eig_svd(Y)
+    U = Q[:, :d]
+    Vout = T @ V[:, :d]
+    return dict(U=U, sigma=Sig[:d], V=Vout, sigma_all=Sig, Q=Q, Omega=Omega)
+
+
+def embedding_from_svd(U: np.ndarray, sigma: np.ndarray) -> np.ndarray:
+    """X = U Sigma^{1/2} (Sec. 3.2)."""
+    return U * np.sqrt(sigma)[None, :]
+
+
+# ----------------------------------------------------------------------------
+# spectral propagation (Sec. 3.3)
+# ----------------------------------------------------------------------------
+
+def chebyshev_coefficients(k: int, theta: float) -> np.ndarray:
+    """c_0 = I_0(theta), c_i = 2 (-1)^i I_i(theta): the first k Chebyshev
+    coefficients of exp(-theta y) on [-1, 1] (generating function of the
+    modified Bessel functions)."""
+    i = np.arange(k)
+    c = 2.0 * ((-1.0) ** i) * scipy.special.iv(i, theta)
+    if k > 0:
+        c[0] = scipy.special.iv(0, theta)
+    return c
+
+
+def spectral_propagation(indptr, indices, X0: np.ndarray, k: int, theta: float, mu: float):
+    """Chebyshev spectral propagation of X0 on the graph.
+
+    With Lap = I - D^-1 A (the paper's normalised Laplacian, Sec. 3.3) and
+    Yop = 1/2 (Lap - mu I)^2 - I (spectrum inside [-1, 1]):
+      F = sum_{i<k} c_i T_i(Yop) X0,  T_0 = X0, T_1 = Yop X0,
+      T_{i+1} = 2 Yop T_i - T_{i-1};
+      P = D^-1 A (X0 - F);  X = U_P Sigma_P^{1/2} from eigSVD(P) (Sec. 5.4).
+    k = 0 turns propagation off (X = X0). Degree-0 rows of D^-1 A are zero.
+    """
+    n = len(indptr) - 1
+    if k <= 0:
+        return dict(F=None, P=None, X=X0.copy())
+    A = sp.csr_matrix((np.ones(len(indices)), indices, indptr), shape=(n, n))
+    deg = np.asarray(A.sum(1)).ravel()
+    dinv = np.where(deg > 0, 1.0 / np.where(deg > 0, deg, 1.0), 0.0)
+    DA = sp.diags(dinv) @ A
+
+    def Lmu(X):
+        return X - DA @ X - mu * X
+
+    def Yop(X):
+        return 0.5 * Lmu(Lmu(X)) - X
+
+    c = chebyshev_coefficients(k, theta)
+    T0 = X0
+    F = c[0] * T0
+    if k >= 2:
+        T1 = Yop(X0)
+        F = F + c[1] * T1
+        for i in range(2, k):
+            T2 = 2.0 * Yop(T1) - T0
+            F = F + c[i] * T2
+            T0, T1 = T1, T2
+    P = DA @ (X0 - F)
+    U, S, _ = eig_svd(P)
+    return dict(F=F, P=P, U=U, sigma=S, X=embedding_from_svd(U, S))
+
+
+# ----------------------------------------------------------------------------
+# whole method
+# ----------------------------------------------------------------------------
+
+def embed(indptr, indices, T, s, S, d, q, k, theta, mu, seed, oversample=16, b=1.0):
+    """Sparsifier -> randomized SVD -> X0 -> spectral propagation -> X."""
+    sparse = sparsifier(indptr, indices, T, s, S, seed, b)
+    rs = fast_randomized_svd(sparse["indptr"], sparse["indices"], sparse["data"], d, q,
+                             oversample, seed)
+    X0 = embedding_from_svd(rs["U"], rs["sigma"])
+    prop = spectral_propagation(indptr, indices, X0, k, theta, mu)
+    return dict(sparse=sparse, rsvd=rs, X0=X0, prop=prop, X=prop["X"])
+
+
+def subspace_sin(U1: np.ndarray, U2: np.ndarray) -> float:
+    """sin of the largest principal angle between span(U1) and span(U2)."""
+    Q1, _ = np.linalg.qr(np.asarray(U1, dtype=np.float64))
+    Q2, _ = np.linalg.qr(np.asarray(U2, dtype=np.float64))
+    # ||(I - Q1 Q1^T) Q2||_2 is accurate for tiny angles (no 1 - cos^2 cancellation)
+    R = Q2 - Q1 @ (Q1.T @ Q2)
+    return float(min(1.0, np.linalg.norm(R, 2)))

@@ -1,0 +1,167 @@
+"""Pins of the oracle's linear-algebra stages against closed forms.
+
+* eigSVD (Algorithm 2) recovers planted singular triplets.
+* Fast randomized SVD (Algorithm 4) recovers a planted spectrum with a gap,
+  and its mean error respects the Eq. 2 bound.
+* Gaussian sketch moments and normality (Algorithm 4, line 2).
+* The Chebyshev coefficients expand exp(-theta y) (Bessel generating function).
+* Spectral propagation equals the filter evaluated on the eigenvalues of the
+  normalised Laplacian (Sec. 3.3), computed independently from a dense
+  eigendecomposition and cos(i arccos y).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.stats as st
+
+import oracle
+from paper_2302_07084_gb300 import synth
+
+
+def _orth(rng, n, k):
+    Q, _ = np.linalg.qr(rng.standard_normal((n, k)))
+    return Q
+
+
+def test_eig_svd_planted_triplets():
+    rng = np.random.default_rng(0)
+    n, k = 500, 24
+    Ua, Vb = _orth(rng, n, k), _orth(rng, k, k)
+    s = np.geomspace(100.0, 0.5, k)
+    X = (Ua * s) @ Vb.T
+    U, S, V = oracle.eig_svd(X)
+    np.testing.assert_allclose(S, s, rtol=1e-9)
+    np.testing.assert_allclose(np.abs(np.sum(U * Ua, axis=0)), 1.0, atol=1e-9)
+    np.testing.assert_allclose(U.T @ U, np.eye(k), atol=1e-9)
+    np.testing.assert_allclose((U * S) @ V.T, X, atol=1e-9 * s[0])
+    # sign convention: largest-magnitude entry of each column is positive
+    idx = np.argmax(np.abs(U), axis=0)
+    assert np.all(U[idx, np.arange(k)] > 0)
+
+
+def _planted_symmetric(rng, n, lam):
+    Q = _orth(rng, n, n)
+    M = (Q * lam) @ Q.T
+    M = 0.5 * (M + M.T)
+    Ms = sp.csr_matrix(M)
+    return Q, Ms
+
+
+def test_frsvd_recovers_planted_spectrum():
+    rng = np.random.default_rng(1)
+    n, d = 300, 12
+    lam = np.concatenate([np.linspace(50, 20, d) * np.where(np.arange(d) % 3 == 0, -1, 1),
+                          rng.uniform(-1, 1, n - d)])
+    Q, M = _planted_symmetric(rng, n, lam)
+    order = np.argsort(-np.abs(lam))
+    top = Q[:, order[:d]]
+    # the error of the range shrinks like (|lam_{d+1}| / |lam_d|)^(q+1) = 20^-(q+1)
+    out = oracle.fast_randomized_svd(M.indptr.astype(np.int64), M.indices, M.data, d, q=8,
+                                     oversample=8, seed=5)
+    np.testing.assert_allclose(out["sigma"], np.abs(lam[order[:d]]), rtol=1e-10)
+    assert oracle.subspace_sin(out["U"], top) < 1e-9
+    # more power iterations shrink the subspace error
+    e = [oracle.subspace_sin(oracle.fast_randomized_svd(M.indptr.astype(np.int64), M.indices, M.data,
+                                                         d, q=q, oversample=8, seed=5)["U"], top)
+         for q in (0, 1, 2)]
+    assert e[0] > e[1] > e[2]
+
+
+def test_frsvd_eq2_bound_mean():
+    rng = np.random.default_rng(2)
+    n, d, p = 200, 10, 6
+    lam = 1.0 / np.arange(1, n + 1) ** 0.7
+    Q, M = _planted_symmetric(rng, n, lam * np.where(rng.random(n) < 0.5, -1, 1))
+    Md = M.toarray()
+    sig_d1 = np.sort(lam)[::-1][d]
+    for q in (0, 1, 2):
+        errs = []
+        for seed in range(20):
+            out = oracle.fast_randomized_svd(M.indptr.astype(np.int64), M.indices, M.data, d, q=q,
+                                             oversample=p, seed=100 + seed)
+            Qb = out["Q"]
+            errs.append(np.linalg.norm(Md - Qb @ (Qb.T @ Md), 2))
+        factor = (1 + np.sqrt(d / (p - 1)) + np.e * np.sqrt(d + p) / p * np.sqrt(n - d)) ** (1.0 / (q + 1))
+        assert np.mean(errs) <= factor * sig_d1
+        # no basis of d+p columns does better than sigma_{d+p+1} (Eckart-Young)
+        assert min(errs) >= np.sort(lam)[::-1][d + p] * (1 - 1e-9)
+
+
+def test_gaussian_sketch_law():
+    n, c = 20000, 12
+    Om = oracle.gaussian_sketch(n, c, seed=9)
+    z = Om.ravel()
+    assert abs(z.mean()) < 5 / np.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 5 * np.sqrt(2.0 / z.size)
+    assert st.kstest(z, "norm").pvalue > 1e-4
+    C = np.corrcoef(Om.T)
+    assert np.max(np.abs(C - np.eye(c))) < 5 / np.sqrt(n)
+    # narrower sketches are column prefixes of wider ones; same seed, same matrix
+    np.testing.assert_array_equal(oracle.gaussian_sketch(50, 7, 9), Om[:50, :7])
+    assert not np.array_equal(oracle.gaussian_sketch(50, 7, 10), Om[:50, :7])
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.5, 1.0])
+def test_chebyshev_coefficients_expand_exponential(theta):
+    y = np.linspace(-1, 1, 201)
+    k = 25
+    c = oracle.chebyshev_coefficients(k, theta)
+    Tk = np.cos(np.outer(np.arange(k), np.arccos(y)))
+    np.testing.assert_allclose(c @ Tk, np.exp(-theta * y), atol=1e-14, rtol=1e-13)
+    # truncation at k = 10 stays within twice the Bessel tail
+    c10 = oracle.chebyshev_coefficients(10, theta)
+    err = np.max(np.abs(c10 @ Tk[:10] - np.exp(-theta * y)))
+    assert err <= 2.0 * np.sum(np.abs(c[10:])) + 1e-15
+
+
+def _spectral_filter(g, X0, k, theta, mu):
+    A = sp.csr_matrix((np.ones(g.n_arcs), g.indices, g.indptr), shape=(g.n, g.n)).toarray()
+    d = A.sum(1)
+    Dm = np.diag(d ** -0.5)
+    Nsym = np.eye(g.n) - Dm @ A @ Dm          # symmetric normalised Laplacian
+    lam, V = np.linalg.eigh(Nsym)
+    y = np.clip(0.5 * (lam - mu) ** 2 - 1.0, -1.0, 1.0)
+    c = oracle.chebyshev_coefficients(k, theta)
+    g_lam = np.cos(np.outer(np.arange(k), np.arccos(y))).T @ c
+    # I - D^-1 A = D^-1/2 Nsym D^1/2
+    G = np.diag(d ** -0.5) @ (V * g_lam) @ V.T @ np.diag(d ** 0.5)
+    F = G @ X0
+    P = (A / d[:, None]) @ (X0 - F)
+    return F, P
+
+
+@pytest.mark.parametrize("k,theta,mu", [(10, 0.5, 0.2), (3, 1.0, 0.0), (15, 0.3, 0.5), (1, 0.5, 0.2), (2, 0.7, 0.4)])
+def test_propagation_matches_spectral_filter(k, theta, mu):
+    g = synth.sbm(60, 3, 0.3, 0.05, seed=12)
+    X0 = np.random.default_rng(3).standard_normal((g.n, 8))
+    out = oracle.spectral_propagation(g.indptr, g.indices, X0, k, theta, mu)
+    F, P = _spectral_filter(g, X0, k, theta, mu)
+    np.testing.assert_allclose(out["F"], F, atol=1e-10 * np.abs(F).max())
+    np.testing.assert_allclose(out["P"], P, atol=1e-10 * np.abs(P).max())
+    # final stage: embedding from the SVD of P
+    U, S, Vt = np.linalg.svd(P, full_matrices=False)
+    np.testing.assert_allclose(out["sigma"], S, rtol=1e-8, atol=1e-12 * S[0])
+    assert oracle.subspace_sin(out["U"], U) < 1e-7
+
+
+def test_propagation_off_is_identity():
+    g = synth.ring(10)
+    X0 = np.arange(30, dtype=float).reshape(10, 3)
+    out = oracle.spectral_propagation(g.indptr, g.indices, X0, 0, 0.5, 0.2)
+    np.testing.assert_array_equal(out["X"], X0)
+
+
+def test_embedding_recovers_blocks():
+    g = synth.sbm(800, 4, 0.06, 0.004, seed=21)
+    out = oracle.embed(g.indptr, g.indices, T=10, s=np.ones(10), S=100.0 * g.m, d=16, q=1, k=10,
+                       theta=0.5, mu=0.2, seed=1)
+    X = out["X"]
+    y = np.argmax(g.labels, axis=1)
+    rng = np.random.default_rng(0)
+    idx = rng.permutation(g.n)
+    tr, te = idx[: g.n // 2], idx[g.n // 2:]
+    Y = np.eye(4)[y]
+    Xa = np.hstack([X, np.ones((g.n, 1))])
+    W, *_ = np.linalg.lstsq(Xa[tr], Y[tr], rcond=None)
+    acc = np.mean(np.argmax(Xa[te] @ W, 1) == y[te])
+    assert acc > 0.9
