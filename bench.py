@@ -1,0 +1,377 @@
+"""Benchmark of the LightNE 2.0 hot path on GB300.
+
+One step = the whole method on one graph: per-edge PathSampling -> exact pair
+counts -> trunc_log CSR (Eq. 1) -> fast randomized SVD (Algorithm 4) ->
+spectral propagation (Sec. 3.3). Workload: the BlogCatalog-shaped Chung-Lu
+graph (n=10,312, m=333,983, exponent 2.1, 39 labels), T=10 with Dirichlet
+window weights, S = 200 T m = 6.68e8 samples, d=128, q=1, k=10.
+
+Metric: sparsifier samples per second of the whole embedding step (S divided
+by the end-to-end embed time). Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank embeds its own copy of the graph
+(replicas; the method needs no exchange between independent problems) and
+value is the total samples of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "samples/s (end-to-end embed, S=200Tm)"
+WORKLOAD = "blogcatalog_like_chunglu_n10312_m333983_T10_S200Tm_d128_q1_k10"
+
+
+def workload():
+    from paper_2302_07084_gb300 import synth
+    g = synth.blogcatalog_like(seed=2)
+    s = synth.dirichlet_weights(10, seed=3)
+    params = dict(T=10, s=list(s), samples=200.0 * 10 * g.m, b=1.0, d=128, oversample=16, q=1, k=10,
+                  theta=0.5, mu=0.2, seed=2)
+    return g, params
+
+
+# ---------------------------------------------------------------------------
+# per-kernel algorithmic work (bytes or flops per launch), for the roofline
+# ---------------------------------------------------------------------------
+
+def kernel_model(name, g, params, counts):
+    """(bound, amount per launch, unit) of the algorithmic work of a kernel.
+
+    walk_emit:      HBM: 4 B key write per sample + 12 B per arc (indptr, target)
+    bucket_scatter: HBM: 4 B read + 4 B write per sample
+    bucket_reduce:  HBM: 4 B read per sample + 8 B per distinct pair written
+    spmm:           HBM: 12 B per nonzero (col, val) + dense operand once + out
+    jacobi_svd / chol_inv / gram_partial: FP64 flops
+    """
+    S = counts["total_samples"]
+    n, m2 = g.n, g.n_arcs
+    c = params["d"] + params["oversample"]
+    nnz_c = counts.get("nnz_c", 0)
+    nnz_M = counts.get("nnz_M", 0)
+    if name == "walk_emit":
+        return "hbm", 4.0 * S + 12.0 * m2, "GB/s"
+    if name == "bucket_scatter":
+        return "hbm", 8.0 * S, "GB/s"
+    if name == "bucket_reduce":
+        return "hbm", 4.0 * S + 8.0 * nnz_c, "GB/s"
+    if name == "spmm":
+        return "hbm", 12.0 * nnz_M + 8.0 * n * c + 8.0 * (n + 1), "GB/s"
+    if name == "graph_spmm":
+        d = params["d"]
+        return "hbm", 4.0 * m2 + 8.0 * (n + 1) + 4.0 * n * d * 4, "GB/s"
+    return None
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), float(pk["bf16_tflops"]), "measured"
+    except Exception:
+        return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        load = sorted(sm)[len(sm) // 2:]   # upper half: samples under load
+        return {"sm_mhz": float(statistics.median(load)), "sm_max_mhz": float(max(mx)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the CPU oracle, timed (cpu_baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_step(g, params, rep: int = 0):
+    """Oracle throughput on a bounded sample of the workload.
+
+    Sampling and aggregation are timed on a slice of arcs at the workload's own
+    per-arc rate (cost per sample); the rest (trunc_log, CSR, randomized SVD,
+    propagation) is timed once on a full-graph run at S/256. The estimate for
+    the whole workload is cost_per_sample * S + rest.
+    """
+    import oracle
+    S = params["samples"]
+    rate = S / g.n_arcs
+    arcs = max(1, int(4.0e6 / rate))
+    a0 = (rep * 7919 * arcs) % max(1, g.n_arcs - arcs)
+    t0 = time.perf_counter()
+    x, y = oracle.sample_pairs(g.indptr, g.indices, params["T"], params["s"], S, params["seed"], a0, a0 + arcs)
+    np.unique(x * g.n + y, return_counts=True)
+    t_samp = time.perf_counter() - t0
+    per_sample = t_samp / max(1, x.size)
+    S_red = S / 256.0
+    sp = oracle.sparsifier(g.indptr, g.indices, params["T"], params["s"], S_red, params["seed"])
+    t1 = time.perf_counter()
+    oracle.netmf_values(sp["x"], sp["y"], sp["cnt"], g.degrees(), S_red)
+    rs = oracle.fast_randomized_svd(sp["indptr"], sp["indices"], sp["data"], params["d"], params["q"],
+                                    params["oversample"], params["seed"])
+    X0 = oracle.embedding_from_svd(rs["U"], rs["sigma"])
+    oracle.spectral_propagation(g.indptr, g.indices, X0, params["k"], params["theta"], params["mu"])
+    t_rest = time.perf_counter() - t1
+    est = per_sample * S + t_rest
+    sample = (f"sampling+aggregation of {x.size} draws (arcs {a0}..{a0 + arcs} at the workload rate "
+              f"{rate:.0f}/arc) extrapolated to S={S:.3g}; trunc_log+CSR+RSVD+propagation timed on a "
+              f"full-graph run at S/256")
+    return dict(value=S / est, est_s=est, measured_s=t_samp + t_rest, sample=sample, cores=oracle.num_threads())
+
+
+# ---------------------------------------------------------------------------
+# main
+# ---------------------------------------------------------------------------
+
+def dist_setup(n_gpus):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args.gpus) if int(os.environ.get("WORLD_SIZE", "1")) > 1 else (1, 0, 0)
+    if rank != 0:
+        return
+    g, params = workload()
+    for w in range(args.warmup):
+        oracle_step(g, params, rep=w)
+    vals, t_meas = [], 0.0
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        r = oracle_step(g, params, rep=args.warmup + k)
+        vals.append(r["value"])
+        t_meas += r["measured_s"]
+    wall = time.perf_counter() - t0
+    est_ms = 1e3 * params["samples"] / statistics.mean(vals)
+    v = params["samples"] / (est_ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": est_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "samples": params["samples"]},
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": r["cores"], "kind": "oracle",
+                             "sample": r["sample"]},
+            "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup(args.gpus)
+    from paper_2302_07084_gb300 import lne
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    g, params = workload()
+    params = dict(params)
+    params["seed"] = params["seed"] + rank
+    P = lne.Params(**params)
+    ctx = lne.Context(local)
+    dg = lne.DeviceGraph(g.indptr, g.indices, device=dev)
+    X = torch.empty((g.n, P.d), dtype=torch.float32, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        ctx.embed(dg, P, out=X)
+    torch.cuda.synchronize()
+    counts = ctx.sparsifier_counts(dg, P)
+    csr = ctx.sparsifier_csr(dg, P)
+    info = dict(total_samples=counts["total_samples"], nnz_c=int(counts["x"].numel()), nnz_M=int(csr["nnz"]))
+    del counts, csr
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.trace(True)
+    launches0 = ctx.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.embed(dg, P, out=X)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier()
+    launches = ctx.kernel_launches() - launches0
+    trace = ctx.trace_read()
+    ctx.trace(False)
+    clk = clocks.stop()
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * params["samples"] / (ms / 1e3)
+
+    # ---- e2e: host buffers, copies inside the timed region ----
+    indptr_h = torch.from_numpy(g.indptr.astype(np.int64)).pin_memory()
+    indices_h = torch.from_numpy(g.indices.astype(np.int32)).pin_memory()
+    X_h = torch.empty((g.n, P.d), dtype=torch.float32).pin_memory()
+    e2e_ms = []
+    for _ in range(max(1, min(args.steps, 5))):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dg.indptr.copy_(indptr_h, non_blocking=True)
+        dg.indices.copy_(indices_h, non_blocking=True)
+        ctx.embed(dg, P, out=X)
+        X_h.copy_(X, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e = float(np.mean(e2e_ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = float(t.item())
+
+    # ---- roofline of the dominant kernel (CUDA events on the launching stream) ----
+    hbm, bf16, src = read_peaks()
+    per_launch = {}
+    for t in trace:
+        per_launch[t["name"]] = t
+    dom = max((t for t in trace if t["name"] in ("walk_emit", "bucket_scatter", "bucket_reduce", "spmm",
+                                                 "graph_spmm", "jacobi_svd", "chol_inv", "gram_partial",
+                                                 "csr_row_sort", "trunclog", "csr_fill", "right_multiply",
+                                                 "tile_counts", "sketch", "compact")),
+              key=lambda t: t["ms"])
+    model = kernel_model(dom["name"], g, params, info)
+    roof = None
+    if model is not None:
+        bound, amount, unit = model
+        avg_s = dom["ms"] / max(1, dom["regions"]) / 1e3
+        achieved = amount / avg_s / 1e9
+        roof = {"kernel": dom["name"], "bound": bound, "achieved": achieved, "peak": hbm, "unit": unit,
+                "frac": achieved / hbm, "traffic": None, "peak_source": src,
+                "avg_launch_ms": avg_s * 1e3}
+    else:
+        roof = {"kernel": dom["name"], "bound": "fp64", "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None, "avg_launch_ms": dom["ms"] / max(1, dom["regions"])}
+    step_total = sum(t["ms"] for t in trace if t["name"] not in ("scan_exclusive",)) / max(1, args.steps)
+    breakdown = {t["name"]: round(t["ms"] / max(1, args.steps), 4) for t in trace}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            r = oracle_step(g, params, rep=0)
+            cpu = {"value": r["value"], "unit": "samples/s", "cores": r["cores"], "kind": "oracle",
+                   "sample": r["sample"]}
+        line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+                "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "samples": params["samples"], "T": 10,
+                           "d": 128, "q": 1, "k": 10, "l2": "flushed (256 MB write) between steps",
+                           "parallelism": f"replicas{world}", "nnz_pairs": info["nnz_c"],
+                           "nnz_M": info["nnz_M"]},
+                "e2e": {"value": world * params["samples"] / (e2e / 1e3), "unit": "samples/s",
+                        "h2d_bytes_per_step": int(g.indptr.nbytes + g.indices.astype(np.int32).nbytes),
+                        "d2h_bytes_per_step": int(g.n * P.d * 4), "ms_per_step": e2e},
+                "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
+                "kernel_ms_per_step": breakdown}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

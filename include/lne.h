@@ -1,0 +1,206 @@
+/*
+ * lne.h -- C ABI of the GB300 (sm_103a) LightNE 2.0 hot path.
+ *
+ * The method (Qiu et al., "Towards Lightweight and Automated Representation
+ * Learning System for Networks", LightNE 2.0):
+ *   1. sparsifier construction: per-edge PathSampling (Algorithms 1 and 3,
+ *      Sec. 4.2) aggregated into exact pair counts, scaled and passed through
+ *      the truncated logarithm of Eq. 1;
+ *   2. fast randomized SVD of that sparse matrix (Algorithm 4) giving the
+ *      initial embedding X0 = U Sigma^{1/2} (Sec. 3.2);
+ *   3. spectral propagation of X0 by a Chebyshev filter in the normalised
+ *      Laplacian I - D^-1 A, followed by an economic SVD (Sec. 3.3, Sec. 5.4).
+ *
+ * Conventions shared by every entry point:
+ *   - Every pointer named *_dev is CUDA device memory on the context's device;
+ *     every other pointer is host memory. The caller owns what it passes in.
+ *     Buffers handed back through lne_counts / lne_csr are owned by the context
+ *     and stay valid until the next call on the same context or lne_destroy.
+ *   - Dense matrices are row-major float32 with the stated leading dimension.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) unless they return a host scalar, which implies a synchronise.
+ *     A context may be used by one host thread at a time.
+ *   - Every call returns LNE_OK (0) or a negative LNE_ERR_* code; the message of
+ *     the last failure is returned by lne_last_error. A failed call leaves the
+ *     context usable.
+ *   - Graphs are undirected and unweighted: symmetric CSR, no self-loops, no
+ *     duplicate edges, rows sorted. Only cheap checks are made (sizes, indptr
+ *     monotone end points); a graph that breaks the contract gives undefined
+ *     (but memory-safe within the stated sizes) results.
+ */
+#ifndef LNE_H
+#define LNE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LNE_OK               0
+#define LNE_ERR_INVALID     -1   /* bad argument or size */
+#define LNE_ERR_OOM         -2   /* device allocation failed */
+#define LNE_ERR_CUDA        -3   /* CUDA runtime error (message says which) */
+#define LNE_ERR_TIMEOUT     -4   /* a bounded device wait ran out */
+#define LNE_ERR_UNSUPPORTED -5   /* valid input outside what this build handles */
+#define LNE_ERR_NUMERIC     -6   /* Cholesky breakdown or non-finite values */
+
+/* Precision of the dense operand of the sparse products (Algorithm 4 lines 3
+ * and 5, the propagation products). Accumulation is FP32 in both; the Gram,
+ * Cholesky and small SVD are FP64 in both. */
+#define LNE_PREC_FP32        0
+#define LNE_PREC_BF16_MIXED  1
+
+typedef struct {
+    int64_t n;                 /* vertices */
+    int64_t nnz;               /* arcs = 2m = indptr[n] */
+    const int64_t *indptr;     /* device, [n+1] */
+    const int32_t *indices;    /* device, [nnz] */
+} lne_graph;
+
+/* Parameters in the paper's notation (notation table of Sec. 3). */
+typedef struct {
+    int32_t T;                 /* window size, 1..16 */
+    const double *s;           /* host, [T] window weights s_1..s_T (>= 0, sum > 0; normalised) */
+    double samples;            /* S: total expected edge samples; S/(2m) per arc (Algorithm 3) */
+    double b;                  /* negative samples b of Eq. 1 (1 if <= 0) */
+    int32_t d;                 /* embedding dimension */
+    int32_t oversample;        /* oversampling s of Algorithm 4 (16 if < 0) */
+    int32_t q;                 /* power iterations of Algorithm 4, >= 0 */
+    int32_t k;                 /* Chebyshev terms of the propagation; 0 = no propagation */
+    double theta;              /* filter width theta */
+    double mu;                 /* filter centre mu */
+    uint64_t seed;             /* Philox key for sampling and the sketch */
+    int32_t precision;         /* LNE_PREC_* */
+} lne_params;
+
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    int64_t *indptr;           /* device [n+1] */
+    int32_t *indices;          /* device [nnz], sorted within each row */
+    float *data;               /* device [nnz] */
+} lne_csr;
+
+typedef struct {
+    int64_t nnz;               /* distinct sampled unordered pairs */
+    int32_t *x;                /* device [nnz], x <= y, sorted by (x, y) */
+    int32_t *y;                /* device [nnz] */
+    uint32_t *count;           /* device [nnz], exact multiplicities */
+    int64_t total_samples;     /* sum of all per-arc sample counts */
+} lne_counts;
+
+typedef struct lne_ctx lne_ctx;
+
+/* Create a context on CUDA device `device`. The context owns its workspace. */
+int lne_create(lne_ctx **out, int device);
+void lne_destroy(lne_ctx *ctx);
+const char *lne_last_error(const lne_ctx *ctx);
+/* Bytes of device workspace the context currently holds. */
+int64_t lne_workspace_bytes(const lne_ctx *ctx);
+/* Release all workspace (the next call re-allocates). */
+int lne_trim(lne_ctx *ctx);
+
+/*
+ * Raw PathSampling draws of arcs [arc_begin, arc_end) (Algorithm 1 driven per
+ * arc as in Algorithm 3), in (arc, sample) order: u1_dev[i] is the end of the
+ * walk from the arc's source, v1_dev[i] the end of the walk from its target.
+ * `capacity` is the length of the two output arrays; *count_out receives the
+ * number of draws (synchronises). Fails with LNE_ERR_INVALID if capacity is too
+ * small (nothing is written then).
+ */
+int lne_sample_pairs(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
+                     int64_t arc_begin, int64_t arc_end, int32_t *u1_dev, int32_t *v1_dev,
+                     int64_t capacity, int64_t *count_out, void *stream);
+
+/*
+ * Exact multiplicity of every sampled unordered pair (x <= y) over all arcs --
+ * the aggregation step of Sec. 4.2 ("sparse parallel hashing"). Output buffers
+ * are context-owned. Synchronises.
+ */
+int lne_sparsifier_counts(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
+                          lne_counts *out, void *stream);
+
+/*
+ * The sparse NetMF estimate M (Eq. 1): entry v = K * alpha / (d_x d_y) with
+ * alpha = vol^2 / (2 S b) off the diagonal and vol^2 / (S b) on it (K the
+ * unordered count), kept iff v > 1 (decided exactly as fl(fl(K alpha) /
+ * fl(d_x d_y)) > 1 in FP64), value log(v) in float32. Symmetric CSR, both
+ * triangles, rows sorted; context-owned. Synchronises.
+ */
+int lne_sparsifier_csr(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
+                       lne_csr *out, void *stream);
+
+/*
+ * Gaussian sketch Omega = randn(n, c) (Algorithm 4, line 2), Box-Muller from
+ * Philox4x32-10 words: row i, column block j/4 uses counter (i, j/4, 0, 0) and
+ * key (seed_lo ^ 0x4f4d4547, seed_hi). out_dev is [n][ld], ld >= c.
+ */
+int lne_gaussian_sketch(lne_ctx *ctx, int64_t n, int32_t c, uint64_t seed, float *out_dev,
+                        int64_t ld, void *stream);
+
+/* Y = M X for CSR M (n x n) and X [n][ldx] (c columns), Y [n][ldy]. FP32. */
+int lne_spmm(lne_ctx *ctx, const lne_csr *M, const float *X_dev, int64_t ldx, int32_t c,
+             float *Y_dev, int64_t ldy, void *stream);
+
+/*
+ * CholeskyQR2 of Y [n][ld] (c columns, c <= 256) in place: Y := Q with Q^T Q = I,
+ * and R_dev (optional, [c][c] FP64 row-major, upper triangular) such that
+ * Y_in = Q R. Gram and Cholesky in FP64. Returns LNE_ERR_NUMERIC when the
+ * Gram is not numerically positive definite.
+ */
+int lne_cholqr2(lne_ctx *ctx, float *Y_dev, int64_t n, int32_t c, int64_t ld, double *R_dev,
+                void *stream);
+
+/*
+ * Fast randomized SVD (Algorithm 4) of the symmetric CSR M with the Gaussian
+ * sketch of lne_gaussian_sketch(seed = p->seed): U_dev [n][d] (left singular
+ * vectors, largest-magnitude entry of each column positive), sigma_dev [d]
+ * (FP64, descending), X0_dev [n][d] = U Sigma^{1/2}. Any output may be NULL.
+ */
+int lne_rsvd(lne_ctx *ctx, const lne_csr *M, const lne_params *p, float *U_dev,
+             double *sigma_dev, float *X0_dev, void *stream);
+
+/*
+ * Spectral propagation (Sec. 3.3): with Lap = I - D^-1 A and
+ * Yop = (Lap - mu I)^2 / 2 - I, F = sum_{i<k} c_i T_i(Yop) X0 where
+ * c_0 = I_0(theta), c_i = 2 (-1)^i I_i(theta); P = D^-1 A (X0 - F); X = U_P
+ * Sigma_P^{1/2} from the SVD of P (Sec. 5.4). X0_dev and X_dev are [n][d]. With
+ * k = 0, X = X0. F_dev / P_dev, when not NULL, receive F and P ([n][d]).
+ */
+int lne_propagate(lne_ctx *ctx, const lne_graph *g, const lne_params *p, const float *X0_dev,
+                  float *X_dev, float *F_dev, float *P_dev, void *stream);
+
+/* The whole method: sparsifier -> randomized SVD -> propagation. X_dev [n][d]. */
+int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_dev, void *stream);
+
+/*
+ * Instrumentation (no counterpart in the paper, which reports wall-clock time
+ * per stage only, Table "time distribution" of Sec. 5.4).
+ *
+ * lne_kernel_launches: kernels launched by this library in this process so far.
+ * lne_trace_enable: start (on != 0) or stop recording named regions; clears
+ *   earlier records. While on, each region (one kernel or one stage) records a
+ *   CUDA event pair on the stream its kernels are launched on.
+ * lne_trace_read: waits for the recorded events and returns one entry per
+ *   region name, in order of first appearance (regions = times the region ran,
+ *   launches = kernels launched inside it, total_ms = summed event time); at
+ *   most `capacity` entries are written and *count receives how many exist.
+ *   Clears the records.
+ */
+typedef struct {
+    char name[40];
+    int64_t regions;
+    int64_t launches;
+    double total_ms;
+} lne_trace_entry;
+
+int64_t lne_kernel_launches(void);
+int lne_trace_enable(lne_ctx *ctx, int on);
+int lne_trace_read(lne_ctx *ctx, lne_trace_entry *out, int capacity, int *count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LNE_H */

@@ -1,0 +1,477 @@
+// C ABI of the library (declared in include/lne.h): argument checks, device
+// selection, error reporting, and the composition of the stages.
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "lne.h"
+#include "runtime.h"
+
+namespace lne {
+
+namespace {
+thread_local std::string g_msg;
+}
+
+int fail(int code, const std::string &msg) {
+    g_msg = msg;
+    return code;
+}
+
+int cuda_fail(const char *what, cudaError_t e, const char *file, int line) {
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), "%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    g_msg = buf;
+    return (e == cudaErrorMemoryAllocation) ? LNE_ERR_OOM : LNE_ERR_CUDA;
+}
+
+const std::string &last_message() { return g_msg; }
+void clear_message() { g_msg.clear(); }
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Per-context record of timed regions (CUDA event pairs).
+struct Tracer {
+    bool on = false;
+    struct Rec {
+        std::string name;
+        cudaEvent_t a = nullptr, b = nullptr;
+        int64_t launches = 0;
+        bool closed = false;
+    };
+    std::vector<Rec> recs;
+    std::vector<size_t> open;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t take() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back();
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return e;
+    }
+    void recycle() {
+        for (auto &r : recs) {
+            if (r.a) pool.push_back(r.a);
+            if (r.b) pool.push_back(r.b);
+        }
+        recs.clear();
+        open.clear();
+    }
+    ~Tracer() {
+        recycle();
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+namespace {
+thread_local Tracer *g_tracer = nullptr;
+}
+
+void set_tracer(Tracer *t) { g_tracer = t; }
+
+void trace_begin(const char *name, cudaStream_t st) {
+    Tracer *t = g_tracer;
+    if (!t || !t->on) return;
+    Tracer::Rec r;
+    r.name = name;
+    r.a = t->take();
+    r.b = t->take();
+    r.launches = g_launches.load(std::memory_order_relaxed);
+    if (!r.a || !r.b) return;
+    cudaEventRecord(r.a, st);
+    t->open.push_back(t->recs.size());
+    t->recs.push_back(r);
+}
+
+void trace_end(cudaStream_t st) {
+    Tracer *t = g_tracer;
+    if (!t || !t->on || t->open.empty()) return;
+    Tracer::Rec &r = t->recs[t->open.back()];
+    t->open.pop_back();
+    cudaEventRecord(r.b, st);
+    r.launches = g_launches.load(std::memory_order_relaxed) - r.launches;
+    r.closed = true;
+}
+
+int Workspace::get(const std::string &name, size_t bytes, void **ptr) {
+    if (bytes == 0) bytes = 1;
+    Buf &b = bufs_[name];
+    if (b.bytes < bytes) {
+        if (b.p) {
+            cudaError_t e = cudaFree(b.p);
+            b.p = nullptr;
+            b.bytes = 0;
+            if (e != cudaSuccess) return cuda_fail("cudaFree", e, __FILE__, __LINE__);
+        }
+        // round up to limit regrowth
+        size_t want = bytes + bytes / 8;
+        want = (want + 255) & ~(size_t)255;
+        cudaError_t e = cudaMalloc(&b.p, want);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            b.p = nullptr;
+            char buf[256];
+            std::snprintf(buf, sizeof(buf), "device allocation of %zu bytes for '%s' failed: %s", want,
+                          name.c_str(), cudaGetErrorString(e));
+            g_msg = buf;
+            return LNE_ERR_OOM;
+        }
+        b.bytes = want;
+    }
+    *ptr = b.p;
+    return 0;
+}
+
+void Workspace::release() {
+    for (auto &kv : bufs_)
+        if (kv.second.p) cudaFree(kv.second.p);
+    bufs_.clear();
+}
+
+int64_t Workspace::bytes() const {
+    int64_t t = 0;
+    for (auto &kv : bufs_) t += (int64_t)kv.second.bytes;
+    return t;
+}
+
+}  // namespace lne
+
+struct lne_ctx {
+    int device = 0;
+    std::string err;
+    lne::Workspace ws;
+    lne::Tracer tracer;
+};
+
+namespace {
+
+cudaStream_t as_stream(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int finish(lne_ctx *ctx, int rc) {
+    if (rc != 0) {
+        ctx->err = lne::last_message();
+        if (ctx->err.empty()) ctx->err = "unknown error";
+    }
+    return rc;
+}
+
+int enter(lne_ctx *ctx) {
+    lne::clear_message();
+    lne::set_tracer(&ctx->tracer);
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) return lne::cuda_fail("cudaSetDevice", e, __FILE__, __LINE__);
+    return 0;
+}
+
+int check_graph(const lne_graph *g) {
+    if (!g) return lne::fail(LNE_ERR_INVALID, "graph is NULL");
+    if (g->n < 1) return lne::fail(LNE_ERR_INVALID, "graph needs n >= 1");
+    if (g->n > 2147483647LL) return lne::fail(LNE_ERR_UNSUPPORTED, "more than 2^31 - 1 vertices");
+    if (g->nnz < 0) return lne::fail(LNE_ERR_INVALID, "graph nnz < 0");
+    if (!g->indptr || (g->nnz > 0 && !g->indices)) return lne::fail(LNE_ERR_INVALID, "graph arrays are NULL");
+    return 0;
+}
+
+lne::GraphView view(const lne_graph *g) {
+    lne::GraphView v;
+    v.n = g->n;
+    v.nnz = g->nnz;
+    v.indptr = g->indptr;
+    v.indices = g->indices;
+    return v;
+}
+
+int check_params(const lne_params *p, bool sampling) {
+    if (!p) return lne::fail(LNE_ERR_INVALID, "params is NULL");
+    if (sampling) {
+        if (p->T < 1 || p->T > 16) return lne::fail(LNE_ERR_INVALID, "T must be in 1..16");
+        if (!p->s) return lne::fail(LNE_ERR_INVALID, "s is NULL");
+        if (!(p->samples > 0.0) || !std::isfinite(p->samples))
+            return lne::fail(LNE_ERR_INVALID, "samples must be a finite value > 0");
+    }
+    if (p->precision != LNE_PREC_FP32 && p->precision != LNE_PREC_BF16_MIXED)
+        return lne::fail(LNE_ERR_INVALID, "unknown precision");
+    if (p->precision == LNE_PREC_BF16_MIXED)
+        return lne::fail(LNE_ERR_UNSUPPORTED, "BF16 mixed precision is not built yet");
+    return 0;
+}
+
+int oversample_of(const lne_params *p) { return p->oversample < 0 ? 16 : p->oversample; }
+
+// Checks the graph's end points on the device (indptr[0] == 0, indptr[n] == nnz).
+int check_graph_device(const lne_graph *g, cudaStream_t st) {
+    int64_t ends[2] = {0, 0};
+    LNE_CUDA_TRY(cudaMemcpyAsync(&ends[0], g->indptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaMemcpyAsync(&ends[1], g->indptr + g->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (ends[0] != 0 || ends[1] != g->nnz)
+        return lne::fail(LNE_ERR_INVALID, "graph indptr must start at 0 and end at nnz");
+    return 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lne_create(lne_ctx **out, int device) {
+    if (!out) return LNE_ERR_INVALID;
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return LNE_ERR_CUDA;
+    }
+    lne_ctx *ctx = new lne_ctx();
+    ctx->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete ctx;
+        return LNE_ERR_CUDA;
+    }
+    *out = ctx;
+    return LNE_OK;
+}
+
+void lne_destroy(lne_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    lne::set_tracer(nullptr);
+    ctx->ws.release();
+    delete ctx;
+}
+
+int64_t lne_kernel_launches(void) { return lne::g_launches.load(); }
+
+int lne_trace_enable(lne_ctx *ctx, int on) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0) {
+        cudaDeviceSynchronize();
+        ctx->tracer.recycle();
+        ctx->tracer.on = on != 0;
+    }
+    return finish(ctx, rc);
+}
+
+int lne_trace_read(lne_ctx *ctx, lne_trace_entry *out, int capacity, int *count) {
+    if (!ctx || !count || (capacity > 0 && !out)) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc != 0) return finish(ctx, rc);
+    // aggregate closed regions by name, in order of first appearance
+    std::vector<lne_trace_entry> agg;
+    for (auto &r : ctx->tracer.recs) {
+        if (!r.closed) continue;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return finish(ctx, lne::cuda_fail("cudaEventSynchronize", e, __FILE__, __LINE__));
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) return finish(ctx, lne::cuda_fail("cudaEventElapsedTime", e, __FILE__, __LINE__));
+        lne_trace_entry *hit = nullptr;
+        for (auto &a : agg)
+            if (std::strncmp(a.name, r.name.c_str(), sizeof(a.name)) == 0) hit = &a;
+        if (!hit) {
+            lne_trace_entry z;
+            std::memset(&z, 0, sizeof(z));
+            std::strncpy(z.name, r.name.c_str(), sizeof(z.name) - 1);
+            agg.push_back(z);
+            hit = &agg.back();
+        }
+        hit->regions += 1;
+        hit->launches += r.launches;
+        hit->total_ms += ms;
+    }
+    ctx->tracer.recycle();
+    *count = (int)agg.size();
+    for (int i = 0; i < (int)agg.size() && i < capacity; ++i) out[i] = agg[i];
+    return finish(ctx, 0);
+}
+
+const char *lne_last_error(const lne_ctx *ctx) { return ctx ? ctx->err.c_str() : "context is NULL"; }
+
+int64_t lne_workspace_bytes(const lne_ctx *ctx) { return ctx ? ctx->ws.bytes() : 0; }
+
+int lne_trim(lne_ctx *ctx) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0) {
+        cudaDeviceSynchronize();
+        ctx->ws.release();
+    }
+    return finish(ctx, rc);
+}
+
+int lne_sample_pairs(lne_ctx *ctx, const lne_graph *g, const lne_params *p, int64_t arc_begin,
+                     int64_t arc_end, int32_t *u1_dev, int32_t *v1_dev, int64_t capacity,
+                     int64_t *count_out, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0) rc = check_graph(g);
+    if (rc == 0) rc = check_params(p, true);
+    if (rc == 0 && (!count_out || (capacity > 0 && (!u1_dev || !v1_dev))))
+        rc = lne::fail(LNE_ERR_INVALID, "NULL output");
+    cudaStream_t st = as_stream(stream);
+    if (rc == 0) rc = check_graph_device(g, st);
+    lne::SamplerSpec sp;
+    if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
+    if (rc == 0) rc = lne::sample_pairs(ctx->ws, view(g), sp, arc_begin, arc_end, u1_dev, v1_dev, capacity,
+                                        count_out, st);
+    return finish(ctx, rc);
+}
+
+int lne_sparsifier_counts(lne_ctx *ctx, const lne_graph *g, const lne_params *p, lne_counts *out,
+                          void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0) rc = check_graph(g);
+    if (rc == 0) rc = check_params(p, true);
+    if (rc == 0 && !out) rc = lne::fail(LNE_ERR_INVALID, "NULL output");
+    cudaStream_t st = as_stream(stream);
+    if (rc == 0) rc = check_graph_device(g, st);
+    lne::SamplerSpec sp;
+    if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
+    lne::CountsResult r;
+    if (rc == 0) rc = lne::sparsifier_counts(ctx->ws, view(g), sp, &r, st);
+    if (rc == 0) {
+        out->nnz = r.nnz;
+        out->x = r.x;
+        out->y = r.y;
+        out->count = r.cnt;
+        out->total_samples = r.total_samples;
+    }
+    return finish(ctx, rc);
+}
+
+int lne_sparsifier_csr(lne_ctx *ctx, const lne_graph *g, const lne_params *p, lne_csr *out, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0) rc = check_graph(g);
+    if (rc == 0) rc = check_params(p, true);
+    if (rc == 0 && !out) rc = lne::fail(LNE_ERR_INVALID, "NULL output");
+    cudaStream_t st = as_stream(stream);
+    if (rc == 0) rc = check_graph_device(g, st);
+    lne::SamplerSpec sp;
+    if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
+    lne::CsrResult r;
+    if (rc == 0) rc = lne::sparsifier_csr(ctx->ws, view(g), sp, &r, st);
+    if (rc == 0) {
+        out->n = r.n;
+        out->nnz = r.nnz;
+        out->indptr = r.indptr;
+        out->indices = r.indices;
+        out->data = r.data;
+    }
+    return finish(ctx, rc);
+}
+
+int lne_gaussian_sketch(lne_ctx *ctx, int64_t n, int32_t c, uint64_t seed, float *out_dev, int64_t ld,
+                        void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (n < 0 || c < 0 || ld < c || (n > 0 && c > 0 && !out_dev)))
+        rc = lne::fail(LNE_ERR_INVALID, "bad sketch arguments");
+    if (rc == 0) rc = lne::gaussian_sketch(n, c, seed, out_dev, ld, as_stream(stream));
+    return finish(ctx, rc);
+}
+
+int lne_spmm(lne_ctx *ctx, const lne_csr *M, const float *X_dev, int64_t ldx, int32_t c, float *Y_dev,
+             int64_t ldy, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (!M || M->n < 0 || c < 1 || ldx < c || ldy < c || !X_dev || !Y_dev || !M->indptr))
+        rc = lne::fail(LNE_ERR_INVALID, "bad SpMM arguments");
+    if (rc == 0) {
+        lne::CsrView v;
+        v.n = M->n;
+        v.nnz = M->nnz;
+        v.indptr = M->indptr;
+        v.indices = M->indices;
+        v.data = M->data;
+        rc = lne::spmm(v, X_dev, ldx, c, Y_dev, ldy, as_stream(stream));
+    }
+    return finish(ctx, rc);
+}
+
+int lne_cholqr2(lne_ctx *ctx, float *Y_dev, int64_t n, int32_t c, int64_t ld, double *R_dev, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (!Y_dev || ld < c)) rc = lne::fail(LNE_ERR_INVALID, "bad CholeskyQR2 arguments");
+    if (rc == 0) rc = lne::cholqr2(ctx->ws, Y_dev, n, c, ld, R_dev, as_stream(stream));
+    return finish(ctx, rc);
+}
+
+int lne_rsvd(lne_ctx *ctx, const lne_csr *M, const lne_params *p, float *U_dev, double *sigma_dev,
+             float *X0_dev, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (!M || !M->indptr || M->n < 1)) rc = lne::fail(LNE_ERR_INVALID, "bad matrix");
+    if (rc == 0) rc = check_params(p, false);
+    if (rc == 0) {
+        lne::CsrView v;
+        v.n = M->n;
+        v.nnz = M->nnz;
+        v.indptr = M->indptr;
+        v.indices = M->indices;
+        v.data = M->data;
+        rc = lne::rsvd(ctx->ws, v, p->d, oversample_of(p), p->q, p->seed, U_dev, sigma_dev, X0_dev,
+                       as_stream(stream));
+    }
+    return finish(ctx, rc);
+}
+
+int lne_propagate(lne_ctx *ctx, const lne_graph *g, const lne_params *p, const float *X0_dev, float *X_dev,
+                  float *F_dev, float *P_dev, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0) rc = check_graph(g);
+    if (rc == 0) rc = check_params(p, false);
+    if (rc == 0 && (!X0_dev || !X_dev)) rc = lne::fail(LNE_ERR_INVALID, "NULL embedding buffer");
+    if (rc == 0 && (p->k < 0 || !std::isfinite(p->theta) || !std::isfinite(p->mu)))
+        rc = lne::fail(LNE_ERR_INVALID, "need k >= 0 and finite theta, mu");
+    if (rc == 0 && p->d < 1) rc = lne::fail(LNE_ERR_INVALID, "need d >= 1");
+    if (rc == 0)
+        rc = lne::propagate(ctx->ws, view(g), p->d, p->k, p->theta, p->mu, X0_dev, X_dev, F_dev, P_dev,
+                            as_stream(stream));
+    return finish(ctx, rc);
+}
+
+int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_dev, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0) rc = check_graph(g);
+    if (rc == 0) rc = check_params(p, true);
+    if (rc == 0 && !X_dev) rc = lne::fail(LNE_ERR_INVALID, "NULL embedding buffer");
+    if (rc == 0 && (p->k < 0 || p->q < 0 || p->d < 1)) rc = lne::fail(LNE_ERR_INVALID, "need d >= 1, q >= 0, k >= 0");
+    cudaStream_t st = as_stream(stream);
+    if (rc == 0) rc = check_graph_device(g, st);
+    lne::SamplerSpec sp;
+    if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
+    lne::CsrResult M;
+    if (rc == 0) rc = lne::sparsifier_csr(ctx->ws, view(g), sp, &M, st);
+    float *X0 = nullptr;
+    if (rc == 0) rc = ctx->ws.get("embed.x0", (size_t)g->n * p->d, &X0);
+    if (rc == 0) {
+        lne::CsrView v;
+        v.n = M.n;
+        v.nnz = M.nnz;
+        v.indptr = M.indptr;
+        v.indices = M.indices;
+        v.data = M.data;
+        rc = lne::rsvd(ctx->ws, v, p->d, oversample_of(p), p->q, p->seed, nullptr, nullptr, X0, st);
+    }
+    if (rc == 0) rc = lne::propagate(ctx->ws, view(g), p->d, p->k, p->theta, p->mu, X0, X_dev, nullptr, nullptr, st);
+    return finish(ctx, rc);
+}
+
+}  // extern "C"

@@ -1,0 +1,216 @@
+// Composition of the stages: fast randomized SVD (Algorithm 4) and spectral
+// propagation (Sec. 3.3 / Sec. 5.4).
+#include <cmath>
+#include <utility>
+
+#include "runtime.h"
+
+namespace lne {
+namespace {
+
+__global__ void scale_copy_kernel(const float *__restrict__ X, float a, float *__restrict__ Y, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        Y[i] = a * X[i];
+}
+
+__global__ void sub_kernel(const float *__restrict__ A, const float *__restrict__ B, float *__restrict__ C,
+                           int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        C[i] = A[i] - B[i];
+}
+
+int elem_grid(int64_t count) {
+    return (int)std::min<int64_t>(ceil_div(std::max<int64_t>(count, 1), 256), 152 * 16);
+}
+
+// I_nu(x) from its power series sum_m (x/2)^(2m+nu) / (m! (m+nu)!).
+double bessel_i(int nu, double x) {
+    const double h = 0.5 * x;
+    double term = 1.0;
+    for (int j = 1; j <= nu; ++j) term *= h / (double)j;
+    double sum = term;
+    for (int m = 1; m < 1000 && term != 0.0; ++m) {
+        term *= h * h / ((double)m * (double)(m + nu));
+        sum += term;
+        if (term < 1e-18 * sum) break;
+    }
+    return sum;
+}
+
+// SVD of the tall matrix Yq [n][c] (overwritten by its Q factor): left
+// singular vectors of the leading dout columns into U [n][dout], sigma [dout].
+int tall_svd(Workspace &ws, float *Yq, int64_t n, int c, int dout, float *U, double *sigma,
+             cudaStream_t st) {
+    double *R = nullptr, *UR = nullptr, *sig = nullptr;
+    LNE_TRY(ws.get("tsvd.R", (size_t)c * c, &R));
+    LNE_TRY(ws.get("tsvd.UR", (size_t)c * c, &UR));
+    LNE_TRY(ws.get("tsvd.sig", (size_t)c, &sig));
+    LNE_TRY(cholqr2(ws, Yq, n, c, c, R, st));
+    LNE_TRY(small_svd(ws, R, c, UR, sig, st));
+    LNE_TRY(right_multiply(Yq, n, c, c, UR, c, dout, nullptr, U, dout, st));
+    LNE_CUDA_TRY(cudaMemcpyAsync(sigma, sig, sizeof(double) * dout, cudaMemcpyDeviceToDevice, st));
+    return 0;
+}
+
+}  // namespace
+
+std::vector<double> chebyshev_coefficients(int k, double theta) {
+    std::vector<double> c(std::max(k, 0));
+    for (int i = 0; i < k; ++i) {
+        double v = bessel_i(i, theta);
+        c[i] = i == 0 ? v : 2.0 * ((i & 1) ? -v : v);
+    }
+    return c;
+}
+
+int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t seed, float *U,
+         double *sigma, float *X0, cudaStream_t st) {
+    const int64_t n = M.n;
+    const int c = d + oversample;
+    if (d < 1 || oversample < 0) return fail(LNE_ERR_INVALID, "need d >= 1 and oversample >= 0");
+    if (c > n) return fail(LNE_ERR_INVALID, "d + oversample must not exceed the number of vertices");
+    if (c > 160) return fail(LNE_ERR_UNSUPPORTED, "d + oversample > 160 is not supported by the small SVD");
+    if (q < 0) return fail(LNE_ERR_INVALID, "q must be >= 0");
+    float *Om = nullptr, *Ya = nullptr, *Yb = nullptr, *Ub = nullptr;
+    double *sg = nullptr;
+    LNE_TRY(ws.get("rsvd.omega", (size_t)n * c, &Om));
+    LNE_TRY(ws.get("rsvd.ya", (size_t)n * c, &Ya));
+    LNE_TRY(ws.get("rsvd.yb", (size_t)n * c, &Yb));
+    if (!U) LNE_TRY(ws.get("rsvd.u", (size_t)n * d, &Ub));
+    if (!sigma) LNE_TRY(ws.get("rsvd.sigma", (size_t)d, &sg));
+    float *Uo = U ? U : Ub;
+    double *so = sigma ? sigma : sg;
+    // Algorithm 4: Omega = randn(n, d+s); Y = M Omega
+    LNE_TRY(gaussian_sketch(n, c, seed, Om, c, st));
+    LNE_TRY(spmm(M, Om, c, c, Ya, c, st));
+    // power iterations: Q = orth(Y); Y = M Q (q times)
+    for (int it = 0; it < q; ++it) {
+        LNE_TRY(cholqr2(ws, Ya, n, c, c, nullptr, st));
+        LNE_TRY(spmm(M, Ya, c, c, Yb, c, st));
+        std::swap(Ya, Yb);
+    }
+    // final eigSVD of Y: U = Q(:, 1:d), Sigma(1:d)
+    LNE_TRY(tall_svd(ws, Ya, n, c, d, Uo, so, st));
+    LNE_TRY(sign_fix_embed(ws, Uo, n, d, d, so, X0, d, st));
+    return 0;
+}
+
+int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, double mu, const float *X0,
+              float *X, float *F, float *P, cudaStream_t st) {
+    const int64_t n = g.n;
+    const int64_t cnt = n * d;
+    if (k <= 0) {
+        LNE_CUDA_TRY(cudaMemcpyAsync(X, X0, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, st));
+        return 0;
+    }
+    if (d > n) return fail(LNE_ERR_INVALID, "d must not exceed the number of vertices");
+    if (d > 160) return fail(LNE_ERR_UNSUPPORTED, "d > 160 is not supported by the small SVD");
+    const std::vector<double> cf = chebyshev_coefficients(k, theta);
+    float *Fb = F, *Pb = P, *Z = nullptr, *Gb = nullptr, *Ta = nullptr, *Tb = nullptr, *Tc = nullptr,
+          *Qb = nullptr, *Ub = nullptr;
+    double *sig = nullptr;
+    if (!Fb) LNE_TRY(ws.get("prop.F", (size_t)cnt, &Fb));
+    if (!Pb) LNE_TRY(ws.get("prop.P", (size_t)cnt, &Pb));
+    LNE_TRY(ws.get("prop.Z", (size_t)cnt, &Z));
+    LNE_TRY(ws.get("prop.G", (size_t)cnt, &Gb));
+    LNE_TRY(ws.get("prop.Ta", (size_t)cnt, &Ta));
+    LNE_TRY(ws.get("prop.Tb", (size_t)cnt, &Tb));
+    LNE_TRY(ws.get("prop.Tc", (size_t)cnt, &Tc));
+    LNE_TRY(ws.get("prop.Q", (size_t)cnt, &Qb));
+    LNE_TRY(ws.get("prop.U", (size_t)cnt, &Ub));
+    LNE_TRY(ws.get("prop.sig", (size_t)d, &sig));
+    const float om = (float)(1.0 - mu);
+    // F = c_0 X0
+    {
+        LNE_TRACE("scale_copy", st);
+        scale_copy_kernel<<<elem_grid(cnt), 256, 0, st>>>(X0, (float)cf[0], Fb, cnt);
+        LNE_LAUNCH_CHECK();
+    }
+    if (k == 1) {
+        {
+            LNE_TRACE("sub", st);
+            sub_kernel<<<elem_grid(cnt), 256, 0, st>>>(X0, Fb, Gb, cnt);
+            LNE_LAUNCH_CHECK();
+        }
+    } else {
+        // Z = (Lap - mu I) X0 = (1 - mu) X0 - D^-1 A X0
+        SpmmEpilogue e1;
+        e1.alpha = -1.f;
+        e1.dinv = true;
+        e1.E1 = X0;
+        e1.b1 = om;
+        e1.lde = d;
+        LNE_TRY(graph_spmm(g, X0, d, d, Z, d, e1, st));
+        // T_1 = Yop X0 = (Lap - mu I) Z / 2 - X0; F += c_1 T_1
+        SpmmEpilogue e2;
+        e2.alpha = -0.5f;
+        e2.dinv = true;
+        e2.E1 = Z;
+        e2.b1 = 0.5f * om;
+        e2.E2 = X0;
+        e2.b2 = -1.f;
+        e2.lde = d;
+        e2.F = Fb;
+        e2.gamma = (float)cf[1];
+        if (k == 2) {
+            e2.X0 = X0;
+            e2.G = Gb;
+        }
+        LNE_TRY(graph_spmm(g, Z, d, d, Ta, d, e2, st));
+        // T_{i-2}, T_{i-1} rotate through three buffers; X0 is never written
+        float *const bufs[3] = {Ta, Tb, Tc};
+        const float *prev = X0;
+        float *cur = Ta;
+        for (int i = 2; i < k; ++i) {
+            float *nxt = nullptr;
+            for (float *b : bufs)
+                if (b != prev && b != cur) {
+                    nxt = b;
+                    break;
+                }
+            // Z = (Lap - mu I) T_{i-1}
+            SpmmEpilogue ez;
+            ez.alpha = -1.f;
+            ez.dinv = true;
+            ez.E1 = cur;
+            ez.b1 = om;
+            ez.lde = d;
+            LNE_TRY(graph_spmm(g, cur, d, d, Z, d, ez, st));
+            // T_i = 2 Yop T_{i-1} - T_{i-2} = (Lap - mu I) Z - 2 T_{i-1} - T_{i-2}
+            SpmmEpilogue e;
+            e.alpha = -1.f;
+            e.dinv = true;
+            e.E1 = Z;
+            e.b1 = om;
+            e.E2 = cur;
+            e.b2 = -2.f;
+            e.E3 = prev;
+            e.b3 = -1.f;
+            e.lde = d;
+            e.F = Fb;
+            e.gamma = (float)cf[i];
+            if (i == k - 1) {
+                e.X0 = X0;
+                e.G = Gb;
+            }
+            LNE_TRY(graph_spmm(g, Z, d, d, nxt, d, e, st));
+            prev = cur;
+            cur = nxt;
+        }
+    }
+    // P = D^-1 A (X0 - F)
+    SpmmEpilogue ep;
+    ep.alpha = 1.f;
+    ep.dinv = true;
+    ep.lde = d;
+    LNE_TRY(graph_spmm(g, Gb, d, d, Pb, d, ep, st));
+    // X = U_P Sigma_P^{1/2} from the SVD of P (economic SVD of the last stage)
+    LNE_CUDA_TRY(cudaMemcpyAsync(Qb, Pb, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, st));
+    LNE_TRY(tall_svd(ws, Qb, n, d, d, Ub, sig, st));
+    LNE_TRY(sign_fix_embed(ws, Ub, n, d, d, sig, X, d, st));
+    return 0;
+}
+
+}  // namespace lne

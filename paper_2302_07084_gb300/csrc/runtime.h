@@ -1,0 +1,138 @@
+// Internal host-side API of the library: device workspace and the stage
+// functions that the C ABI (capi.cu) composes.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace lne {
+
+// Named, grow-only device buffers owned by a context. A buffer keeps its
+// contents until it is re-requested with a larger size.
+class Workspace {
+public:
+    ~Workspace() { release(); }
+    // Returns 0 and sets *ptr, or LNE_ERR_OOM / LNE_ERR_CUDA.
+    int get(const std::string &name, size_t bytes, void **ptr);
+    template <typename T>
+    int get(const std::string &name, size_t count, T **ptr) {
+        return get(name, count * sizeof(T), reinterpret_cast<void **>(ptr));
+    }
+    void release();
+    int64_t bytes() const;
+
+private:
+    struct Buf {
+        void *p = nullptr;
+        size_t bytes = 0;
+    };
+    std::map<std::string, Buf> bufs_;
+};
+
+struct GraphView {
+    int64_t n = 0;
+    int64_t nnz = 0;
+    const int64_t *indptr = nullptr;
+    const int32_t *indices = nullptr;
+};
+
+struct CsrView {
+    int64_t n = 0;
+    int64_t nnz = 0;
+    const int64_t *indptr = nullptr;
+    const int32_t *indices = nullptr;
+    const float *data = nullptr;
+};
+
+// Host-derived constants of the sampler (Algorithm 3 with the readings of the
+// window draw, the per-arc Bernoulli and the Philox stream layout).
+struct SamplerSpec {
+    uint32_t k0 = 0, k1 = 0;      // Philox key = (seed_lo, seed_hi)
+    uint32_t base = 0;            // floor(S / 2m)
+    uint32_t thr_frac = 0;        // floor(frac(S / 2m) * 2^32)
+    int T = 1;
+    uint64_t thr[16] = {0};       // thr_1..thr_{T-1}
+    int B = 1;                    // bits per endpoint in a pair key
+    double alpha_off = 0, alpha_diag = 0;
+};
+
+int make_sampler_spec(const GraphView &g, int T, const double *s, double S, double b, uint64_t seed,
+                      SamplerSpec *out);
+
+// ---- sparsifier (sampler.cu) ------------------------------------------------
+int sample_pairs(Workspace &ws, const GraphView &g, const SamplerSpec &sp, int64_t a0, int64_t a1,
+                 int32_t *u1, int32_t *v1, int64_t capacity, int64_t *count, cudaStream_t st);
+
+struct CountsResult {
+    int64_t nnz = 0;
+    int64_t total_samples = 0;
+    int32_t *x = nullptr;
+    int32_t *y = nullptr;
+    uint32_t *cnt = nullptr;
+};
+int sparsifier_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out,
+                      cudaStream_t st);
+
+struct CsrResult {
+    int64_t n = 0, nnz = 0;
+    int64_t *indptr = nullptr;
+    int32_t *indices = nullptr;
+    float *data = nullptr;
+};
+int sparsifier_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out,
+                   cudaStream_t st);
+
+// ---- dense and sparse linear algebra (dense.cu, spmm.cu) -------------------
+int gaussian_sketch(int64_t n, int c, uint64_t seed, float *out, int64_t ld, cudaStream_t st);
+int spmm(const CsrView &M, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
+         cudaStream_t st);
+// Y := Q in place; R (optional, device FP64 [c][c]) receives the upper factor.
+int cholqr2(Workspace &ws, float *Y, int64_t n, int c, int64_t ld, double *R, cudaStream_t st);
+// SVD of an upper-triangular c x c FP64 R: U_R [c][c] FP64, sigma [c] descending.
+int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma, cudaStream_t st);
+// out[n][dout] = Y[n][c] * W[c][dout] (W FP64 row-major with leading dim ldw),
+// optionally scaled per output column by colscale (FP64, length dout).
+int right_multiply(const float *Y, int64_t n, int c, int64_t ldy, const double *W, int64_t ldw,
+                   int dout, const double *colscale, float *out, int64_t ldo, cudaStream_t st);
+// Flip columns of U [n][d] so that each column's largest-magnitude entry is
+// positive; if X is not NULL also writes X = U diag(sqrt(sigma)).
+int sign_fix_embed(Workspace &ws, float *U, int64_t n, int d, int64_t ld, const double *sigma,
+                   float *X, int64_t ldx, cudaStream_t st);
+
+// Epilogue of the graph products (see spmm.cu).
+struct SpmmEpilogue {
+    float alpha = 1.f;
+    bool dinv = false;                  // multiply (A X)_i by 1 / deg(i)
+    const float *E1 = nullptr;
+    float b1 = 0.f;
+    const float *E2 = nullptr;
+    float b2 = 0.f;
+    const float *E3 = nullptr;
+    float b3 = 0.f;
+    int64_t lde = 0;                    // leading dimension of E*, F, X0, G
+    float *F = nullptr;                 // F += gamma * out
+    float gamma = 0.f;
+    const float *X0 = nullptr;          // with G: G = X0 - F (after the update)
+    float *G = nullptr;
+    bool store = true;                  // write out to Y
+};
+int graph_spmm(const GraphView &g, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
+               const SpmmEpilogue &ep, cudaStream_t st);
+
+// Randomized SVD (Algorithm 4) and propagation (Sec. 3.3).
+int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t seed,
+         float *U, double *sigma, float *X0, cudaStream_t st);
+int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, double mu,
+              const float *X0, float *X, float *F, float *P, cudaStream_t st);
+
+// Exclusive scan helpers (scan.cu).
+int scan_exclusive_u32_to_i64(const uint32_t *in, int64_t *out, int64_t n, cudaStream_t st);
+int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st);
+
+}  // namespace lne

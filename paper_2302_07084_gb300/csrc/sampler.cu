@@ -1,0 +1,763 @@
+// Sparsifier construction on the GPU (Sec. 4.2 of the paper, re-designed):
+//
+//   1. tile_counts     per-arc sample counts n_a = floor(S/2m) + Bernoulli
+//                      (Algorithm 3, line 3) summed per tile of arcs; scanned
+//                      into tile offsets.
+//   2. walk_emit       one thread per sample: window r ~ Multinomial(s)
+//                      (Algorithm 3, line 6), split sigma ~ U{0..r-1} and the
+//                      two walks of PathSampling (Algorithm 1), each step
+//                      x <- nbr(x)[word mod deg(x)] (Sec. 4.2). Emits the
+//                      canonical pair key (min << B | max) and a shared-memory
+//                      histogram of key buckets.
+//   3. bucket_scatter  moves keys into their bucket's region (CTA-aggregated
+//                      cursors; order inside a bucket does not matter).
+//   4. bucket_reduce   one CTA per bucket counts its keys in a dense 2^15-entry
+//                      shared-memory histogram and writes the distinct keys in
+//                      key order with their exact counts -- the integer
+//                      aggregation the paper does with a concurrent hash table.
+//   5. trunclog        Eq. 1 value v = K alpha / (d_x d_y), kept iff v > 1 (an
+//                      exact FP64 decision), log(v) as float32.
+//   6. csr_fill/sort   symmetric CSR of the kept entries, rows sorted.
+//
+// Every integer result (counts, keep decisions, CSR structure) is independent of
+// scheduling, so it equals the CPU oracle bit for bit.
+#include <cstring>
+
+#include "runtime.h"
+
+namespace lne {
+namespace {
+
+constexpr int kBucketBits = 15;                 // keys per reduce bucket = 2^15
+constexpr int kMaxSmemBuckets = 12288;          // walk/scatter histogram capacity
+constexpr int kWalkThreads = 256;
+
+struct WalkArgs {
+    const int64_t *indptr;
+    const int32_t *indices;
+    int64_t n;
+    int64_t n_arcs;
+    uint32_t k0, k1;
+    uint32_t base;
+    uint32_t thr_frac;
+    int T;
+    int B;
+    uint64_t thr[16];
+};
+
+__device__ __forceinline__ uint32_t arc_count(const WalkArgs &A, int64_t arc) {
+    if (A.thr_frac == 0) return A.base;
+    u32x4 c = {0xFFFFFFFFu, (uint32_t)((uint64_t)arc & 0xFFFFFFFFu), (uint32_t)((uint64_t)arc >> 32),
+               0xFFFFFFFFu};
+    u32x4 w = philox10(c, A.k0, A.k1);
+    return A.base + (w.x < A.thr_frac ? 1u : 0u);
+}
+
+__device__ __forceinline__ int32_t arc_source(const int64_t *__restrict__ indptr, int64_t n,
+                                              int64_t a) {
+    int64_t lo = 0, hi = n;   // indptr[lo] <= a < indptr[hi]
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(indptr + mid) <= a) lo = mid; else hi = mid;
+    }
+    return (int32_t)lo;
+}
+
+// The sample's stream of 32-bit Philox words: counter (j, a_lo, a_hi, blk).
+struct WordStream {
+    u32x4 cur;
+    uint32_t c0, c1, c2, blk;
+    uint32_t k0, k1;
+    int pos;
+    __device__ __forceinline__ uint32_t next() {
+        if (pos == 4) {
+            ++blk;
+            cur = philox10(u32x4{c0, c1, c2, blk}, k0, k1);
+            pos = 0;
+        }
+        uint32_t r = pos == 0 ? cur.x : pos == 1 ? cur.y : pos == 2 ? cur.z : cur.w;
+        ++pos;
+        return r;
+    }
+};
+
+__device__ __forceinline__ int32_t walk_steps(const WalkArgs &A, int32_t x, int steps,
+                                              WordStream &ws) {
+    for (int t = 0; t < steps; ++t) {
+        uint32_t w = ws.next();
+        int64_t b = __ldg(A.indptr + x);
+        uint32_t deg = (uint32_t)(__ldg(A.indptr + x + 1) - b);
+        if (deg == 0) continue;   // only on graphs that break the contract
+        x = __ldg(A.indices + b + (w % deg));
+    }
+    return x;
+}
+
+// One PathSampling draw of sample j on arc (u -> v).
+__device__ __forceinline__ void draw(const WalkArgs &A, int64_t arc, uint32_t j, int32_t u,
+                                     int32_t v, int32_t *pu, int32_t *pv) {
+    WordStream ws;
+    ws.c0 = j;
+    ws.c1 = (uint32_t)((uint64_t)arc & 0xFFFFFFFFu);
+    ws.c2 = (uint32_t)((uint64_t)arc >> 32);
+    ws.blk = 0;
+    ws.k0 = A.k0;
+    ws.k1 = A.k1;
+    ws.cur = philox10(u32x4{ws.c0, ws.c1, ws.c2, 0u}, A.k0, A.k1);
+    ws.pos = 3;   // words 0..2: window, split, reserved coin
+    int r = 1;
+#pragma unroll 16
+    for (int i = 0; i < 15; ++i)
+        if (i < A.T - 1) r += ((uint64_t)ws.cur.x >= A.thr[i]) ? 1 : 0;
+    int sigma = (int)(ws.cur.y % (uint32_t)r);
+    *pu = walk_steps(A, u, sigma, ws);
+    *pv = walk_steps(A, v, r - 1 - sigma, ws);
+}
+
+// In-place exclusive scan of s[0..n) in shared memory by one CTA; returns total.
+template <int BLOCK>
+__device__ uint32_t block_exclusive_scan(uint32_t *s, int n) {
+    __shared__ uint32_t warp_tot[BLOCK / 32];
+    __shared__ uint32_t total_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (n + BLOCK - 1) / BLOCK;
+    const int i0 = tid * per;
+    uint32_t local = 0;
+    for (int j = 0; j < per; ++j)
+        if (i0 + j < n) local += s[i0 + j];
+    uint32_t x = local;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < BLOCK / 32 ? warp_tot[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        if (lane < BLOCK / 32) warp_tot[lane] = w;
+        if (lane == BLOCK / 32 - 1) total_s = w;
+    }
+    __syncthreads();
+    uint32_t run = (warp > 0 ? warp_tot[warp - 1] : 0) + x - local;
+    for (int j = 0; j < per; ++j) {
+        if (i0 + j < n) {
+            uint32_t t = s[i0 + j];
+            s[i0 + j] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    uint32_t t = total_s;
+    __syncthreads();
+    return t;
+}
+
+__global__ void __launch_bounds__(kWalkThreads) tile_counts_kernel(WalkArgs A, int64_t a_begin,
+                                                                   int64_t a_end, int tile_arcs,
+                                                                   uint32_t *__restrict__ tile_cnt) {
+    __shared__ uint32_t red[kWalkThreads / 32];
+    const int64_t a0 = a_begin + (int64_t)blockIdx.x * tile_arcs;
+    const int64_t a1 = min(a0 + tile_arcs, a_end);
+    uint32_t c = 0;
+    for (int64_t a = a0 + threadIdx.x; a < a1; a += kWalkThreads) c += arc_count(A, a);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kWalkThreads / 32; ++w) t += red[w];
+        tile_cnt[blockIdx.x] = t;
+    }
+}
+
+// MODE 0: write ordered endpoint pairs (u1, v1). MODE 1: write canonical keys
+// and count key buckets.
+template <typename KeyT, int MODE>
+__global__ void __launch_bounds__(kWalkThreads) walk_emit_kernel(
+    WalkArgs A, int64_t a_begin, int64_t a_end, int tile_arcs, const int64_t *__restrict__ tile_off,
+    KeyT *__restrict__ keys, int32_t *__restrict__ u1, int32_t *__restrict__ v1,
+    uint32_t *__restrict__ bucket_cnt, int nb_smem) {
+    extern __shared__ uint32_t smem[];
+    uint32_t *s_off = smem;                                      // tile_arcs + 1
+    int32_t *s_src = reinterpret_cast<int32_t *>(s_off + tile_arcs + 1);
+    int32_t *s_dst = s_src + tile_arcs;
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_dst + tile_arcs);
+    const int tid = threadIdx.x;
+    const int64_t a0 = a_begin + (int64_t)blockIdx.x * tile_arcs;
+    const int na = (int)imin64(tile_arcs, a_end - a0);
+    if (MODE == 1)
+        for (int i = tid; i < nb_smem; i += kWalkThreads) s_hist[i] = 0;
+    for (int i = tid; i < na; i += kWalkThreads) {
+        s_off[i] = arc_count(A, a0 + i);
+        s_src[i] = arc_source(A.indptr, A.n, a0 + i);
+        s_dst[i] = __ldg(A.indices + a0 + i);
+    }
+    __syncthreads();
+    const uint32_t total = block_exclusive_scan<kWalkThreads>(s_off, na);
+    if (tid == 0) s_off[na] = total;
+    __syncthreads();
+    const int64_t out0 = tile_off[blockIdx.x];
+    for (uint32_t s = tid; s < total; s += kWalkThreads) {
+        int lo = 0, hi = na;   // s_off[lo] <= s < s_off[hi]
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (s_off[mid] <= s) lo = mid; else hi = mid;
+        }
+        const uint32_t j = s - s_off[lo];
+        int32_t pu, pv;
+        draw(A, a0 + lo, j, s_src[lo], s_dst[lo], &pu, &pv);
+        if (MODE == 0) {
+            u1[out0 + s] = pu;
+            v1[out0 + s] = pv;
+        } else {
+            const uint32_t x = (uint32_t)min(pu, pv), y = (uint32_t)max(pu, pv);
+            const KeyT key = ((KeyT)x << A.B) | (KeyT)y;
+            keys[out0 + s] = key;
+            const uint32_t b = (uint32_t)(key >> kBucketBits);
+            if (nb_smem > 0) atomicAdd(&s_hist[b], 1u);
+            else atomicAdd(&bucket_cnt[b], 1u);
+        }
+    }
+    if (MODE == 1 && nb_smem > 0) {
+        __syncthreads();
+        for (int i = tid; i < nb_smem; i += kWalkThreads) {
+            uint32_t c = s_hist[i];
+            if (c) atomicAdd(&bucket_cnt[i], c);
+        }
+    }
+}
+
+constexpr int kScatterThreads = 512;
+constexpr int kScatterItems = 16;
+
+template <typename KeyT>
+__global__ void __launch_bounds__(kScatterThreads) bucket_scatter_kernel(
+    const KeyT *__restrict__ in, int64_t nkeys, KeyT *__restrict__ out,
+    unsigned long long *__restrict__ cursor, int nb) {
+    extern __shared__ unsigned long long s_base[];                 // nb
+    uint32_t *s_cnt = reinterpret_cast<uint32_t *>(s_base + nb);  // nb
+    const int tid = threadIdx.x;
+    for (int i = tid; i < nb; i += kScatterThreads) s_cnt[i] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kScatterThreads * kScatterItems;
+    KeyT k[kScatterItems];
+    uint32_t rank[kScatterItems];
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i) {
+        int64_t idx = base + (int64_t)i * kScatterThreads + tid;
+        if (idx < nkeys) {
+            k[i] = in[idx];
+            rank[i] = atomicAdd(&s_cnt[(uint32_t)(k[i] >> kBucketBits)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < nb; i += kScatterThreads) {
+        uint32_t c = s_cnt[i];
+        if (c) s_base[i] = atomicAdd(&cursor[i], (unsigned long long)c);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kScatterItems; ++i) {
+        int64_t idx = base + (int64_t)i * kScatterThreads + tid;
+        if (idx < nkeys) out[s_base[(uint32_t)(k[i] >> kBucketBits)] + rank[i]] = k[i];
+    }
+}
+
+// Global-atomic fallback when the bucket count does not fit shared memory.
+template <typename KeyT>
+__global__ void bucket_scatter_global_kernel(const KeyT *__restrict__ in, int64_t nkeys,
+                                             KeyT *__restrict__ out,
+                                             unsigned long long *__restrict__ cursor) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nkeys;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        KeyT k = in[i];
+        out[atomicAdd(&cursor[(uint32_t)(k >> kBucketBits)], 1ull)] = k;
+    }
+}
+
+constexpr int kReduceThreads = 1024;
+
+// One CTA per bucket: dense shared-memory histogram over the bucket's 2^15
+// keys, then the distinct keys in key order with their counts.
+template <typename KeyT>
+__global__ void __launch_bounds__(kReduceThreads) bucket_reduce_kernel(
+    const KeyT *__restrict__ keys, const int64_t *__restrict__ bucket_off, KeyT *__restrict__ out_key,
+    uint32_t *__restrict__ out_cnt, uint32_t *__restrict__ distinct) {
+    extern __shared__ uint32_t hist[];   // 2^kBucketBits
+    constexpr int W = 1 << kBucketBits;
+    constexpr int PER = W / kReduceThreads;
+    __shared__ uint32_t warp_tot[kReduceThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int b = blockIdx.x;
+    const int64_t lo = bucket_off[b], hi = bucket_off[b + 1];
+    if (lo == hi) {
+        if (tid == 0) distinct[b] = 0;
+        return;
+    }
+    for (int i = tid; i < W; i += kReduceThreads) hist[i] = 0;
+    __syncthreads();
+    for (int64_t i = lo + tid; i < hi; i += kReduceThreads)
+        atomicAdd(&hist[(uint32_t)(keys[i] & (KeyT)(W - 1))], 1u);
+    __syncthreads();
+    // each thread owns PER consecutive histogram slots
+    uint32_t nz = 0;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) nz += hist[tid * PER + j] != 0;
+    uint32_t x = nz;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = warp_tot[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        warp_tot[lane] = w;
+    }
+    __syncthreads();
+    uint32_t pos = (warp > 0 ? warp_tot[warp - 1] : 0) + x - nz;
+    const KeyT kbase = (KeyT)b << kBucketBits;
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        uint32_t c = hist[tid * PER + j];
+        if (c) {
+            out_key[lo + pos] = kbase | (KeyT)(tid * PER + j);
+            out_cnt[lo + pos] = c;
+            ++pos;
+        }
+    }
+    if (tid == kReduceThreads - 1) distinct[b] = pos;
+}
+
+// Copies every bucket's distinct entries to contiguous (x, y, count) arrays.
+template <typename KeyT>
+__global__ void compact_kernel(const KeyT *__restrict__ rkey, const uint32_t *__restrict__ rcnt,
+                               const int64_t *__restrict__ bucket_off,
+                               const int64_t *__restrict__ dst_off, int B, int32_t *__restrict__ x,
+                               int32_t *__restrict__ y, uint32_t *__restrict__ cnt) {
+    const int b = blockIdx.x;
+    const int64_t src = bucket_off[b];
+    const int64_t dst = dst_off[b];
+    const int64_t m = dst_off[b + 1] - dst;
+    const KeyT mask = ((KeyT)1 << B) - 1;
+    for (int64_t i = threadIdx.x; i < m; i += blockDim.x) {
+        KeyT k = rkey[src + i];
+        x[dst + i] = (int32_t)(k >> B);
+        y[dst + i] = (int32_t)(k & mask);
+        cnt[dst + i] = rcnt[src + i];
+    }
+}
+
+// Eq. 1 with the truncated log. The keep decision fl(fl(K alpha) / q) > 1 is
+// evaluated without a division: with p = fl(K alpha) and q = d_x d_y, a
+// correctly rounded quotient exceeds 1 iff p / q > 1 + 2^-53, i.e. iff p >= 2q
+// or (q < p and (p - q) 2^53 > q); p - q is exact there (Sterbenz).
+__global__ void trunclog_kernel(const int32_t *__restrict__ x, const int32_t *__restrict__ y,
+                                const uint32_t *__restrict__ cnt, int64_t nnz,
+                                const int64_t *__restrict__ indptr, double alpha_off,
+                                double alpha_diag, float *__restrict__ val,
+                                uint8_t *__restrict__ keep, uint32_t *__restrict__ rowcnt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t xi = x[i], yi = y[i];
+        const int64_t dx = __ldg(indptr + xi + 1) - __ldg(indptr + xi);
+        const int64_t dy = __ldg(indptr + yi + 1) - __ldg(indptr + yi);
+        const double alpha = xi == yi ? alpha_diag : alpha_off;
+        const double p = __dmul_rn((double)cnt[i], alpha);
+        const double q = __ll2double_rn(dx * dy);
+        bool k = false;
+        if (p > q) {
+            if (p >= __dmul_rn(2.0, q)) k = true;
+            else k = __dmul_rn(__dsub_rn(p, q), 9007199254740992.0) > q;
+        }
+        float v = 0.f;
+        if (k) {
+            if (p < __dmul_rn(2.0, q)) {
+                v = log1pf(__fdiv_rn((float)__dsub_rn(p, q), (float)q));
+            } else if (p < 1e30) {
+                v = logf(__fdiv_rn((float)p, (float)q));
+            } else {
+                v = (float)(log(p) - log(q));
+            }
+            atomicAdd(&rowcnt[xi], 1u);
+            if (xi != yi) atomicAdd(&rowcnt[yi], 1u);
+        }
+        keep[i] = k;
+        val[i] = v;
+    }
+}
+
+__global__ void csr_fill_kernel(const int32_t *__restrict__ x, const int32_t *__restrict__ y,
+                                const float *__restrict__ val, const uint8_t *__restrict__ keep,
+                                int64_t nnz, const int64_t *__restrict__ rowptr,
+                                uint32_t *__restrict__ cursor, int32_t *__restrict__ col,
+                                float *__restrict__ data) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (!keep[i]) continue;
+        const int32_t xi = x[i], yi = y[i];
+        const float v = val[i];
+        int64_t p = rowptr[xi] + atomicAdd(&cursor[xi], 1u);
+        col[p] = yi;
+        data[p] = v;
+        if (xi != yi) {
+            p = rowptr[yi] + atomicAdd(&cursor[yi], 1u);
+            col[p] = xi;
+            data[p] = v;
+        }
+    }
+}
+
+constexpr int kSortThreads = 512;
+constexpr int kSortMax = 16384;   // entries of one row sorted in shared memory
+
+// Bitonic sort of every row by column (columns in a row are distinct). Rows are
+// packed as (col << 32 | float bits) so the sort key is the column.
+__global__ void __launch_bounds__(kSortThreads) csr_row_sort_kernel(const int64_t *__restrict__ rowptr,
+                                                                    int32_t *__restrict__ col,
+                                                                    float *__restrict__ data,
+                                                                    int *__restrict__ too_long) {
+    extern __shared__ unsigned long long e[];
+    const int64_t r0 = rowptr[blockIdx.x], r1 = rowptr[blockIdx.x + 1];
+    const int L = (int)(r1 - r0);
+    if (L <= 1) return;
+    if (L > kSortMax) {
+        if (threadIdx.x == 0) atomicMax(too_long, L);
+        return;
+    }
+    int P = 1;
+    while (P < L) P <<= 1;
+    for (int i = threadIdx.x; i < P; i += kSortThreads) {
+        if (i < L)
+            e[i] = ((unsigned long long)(uint32_t)col[r0 + i] << 32) |
+                   (unsigned long long)__float_as_uint(data[r0 + i]);
+        else
+            e[i] = ~0ull;
+    }
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < P; i += kSortThreads) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    unsigned long long a = e[i], b = e[ixj];
+                    bool up = (i & k) == 0;
+                    if ((a > b) == up) {
+                        e[i] = b;
+                        e[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < L; i += kSortThreads) {
+        col[r0 + i] = (int32_t)(e[i] >> 32);
+        data[r0 + i] = __uint_as_float((uint32_t)(e[i] & 0xFFFFFFFFull));
+    }
+}
+
+WalkArgs make_walk_args(const GraphView &g, const SamplerSpec &sp) {
+    WalkArgs A;
+    A.indptr = g.indptr;
+    A.indices = g.indices;
+    A.n = g.n;
+    A.n_arcs = g.nnz;
+    A.k0 = sp.k0;
+    A.k1 = sp.k1;
+    A.base = sp.base;
+    A.thr_frac = sp.thr_frac;
+    A.T = sp.T;
+    A.B = sp.B;
+    for (int i = 0; i < 16; ++i) A.thr[i] = sp.thr[i];
+    return A;
+}
+
+// Tile size: aim for ~32k samples per CTA but at least ~8 CTAs per SM overall.
+int choose_tile_arcs(int64_t n_arcs, double rate) {
+    double per_arc = rate < 1.0 ? 1.0 : rate;
+    double total = per_arc * (double)n_arcs;
+    double want = total / (152.0 * 8.0);
+    if (want > 32768.0) want = 32768.0;
+    if (want < 2048.0) want = 2048.0;
+    int64_t t = (int64_t)(want / per_arc);
+    if (t < 1) t = 1;
+    if (t > 4096) t = 4096;
+    return (int)t;
+}
+
+int walk_smem_bytes(int tile_arcs, int nb_smem) {
+    return (tile_arcs + 1) * 4 + 2 * tile_arcs * 4 + nb_smem * 4;
+}
+
+// Per-tile offsets of arcs [a0, a1): returns the total number of samples.
+int tile_offsets(Workspace &ws, const WalkArgs &A, int64_t a0, int64_t a1, int tile_arcs,
+                 int64_t **tile_off, int64_t *total, cudaStream_t st) {
+    const int64_t ntiles = ceil_div(a1 - a0, tile_arcs);
+    uint32_t *tile_cnt = nullptr;
+    LNE_TRY(ws.get("walk.tile_cnt", (size_t)ntiles, &tile_cnt));
+    LNE_TRY(ws.get("walk.tile_off", (size_t)ntiles + 1, tile_off));
+    {
+        LNE_TRACE("tile_counts", st);
+        tile_counts_kernel<<<(unsigned)ntiles, kWalkThreads, 0, st>>>(A, a0, a1, tile_arcs, tile_cnt);
+        LNE_LAUNCH_CHECK();
+    }
+    LNE_TRY(scan_exclusive_u32_to_i64(tile_cnt, *tile_off, ntiles, st));
+    LNE_CUDA_TRY(cudaMemcpyAsync(total, *tile_off + ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    return 0;
+}
+
+}  // namespace
+
+int make_sampler_spec(const GraphView &g, int T, const double *s, double S, double b, uint64_t seed,
+                      SamplerSpec *out) {
+    if (T < 1 || T > 16) return fail(LNE_ERR_INVALID, "T must be in 1..16");
+    if (!s) return fail(LNE_ERR_INVALID, "window weights s are NULL");
+    if (g.nnz <= 0) return fail(LNE_ERR_INVALID, "graph has no edges");
+    if (!(S > 0.0)) return fail(LNE_ERR_INVALID, "sample count S must be > 0");
+    SamplerSpec sp;
+    sp.k0 = (uint32_t)(seed & 0xFFFFFFFFu);
+    sp.k1 = (uint32_t)(seed >> 32);
+    sp.T = T;
+    double total = 0.0;
+    for (int t = 0; t < T; ++t) {
+        if (!(s[t] >= 0.0)) return fail(LNE_ERR_INVALID, "window weights must be >= 0");
+        total += s[t];
+    }
+    if (!(total > 0.0)) return fail(LNE_ERR_INVALID, "window weights must not all be zero");
+    // thr_i = min(2^32, floor(2^32 * (s_1 + .. + s_i) / (s_1 + .. + s_T)))
+    double cum = 0.0;
+    for (int i = 0; i + 1 < T; ++i) {
+        cum += s[i];
+        double p = cum / total;
+        double x = std::floor(p * 4294967296.0);
+        sp.thr[i] = x >= 4294967296.0 ? (1ull << 32) : x <= 0.0 ? 0ull : (uint64_t)x;
+    }
+    double rate = S / (double)g.nnz;
+    if (rate >= 4294967295.0) return fail(LNE_ERR_UNSUPPORTED, "more than 2^32 samples per arc");
+    double fl = std::floor(rate);
+    sp.base = (uint32_t)fl;
+    sp.thr_frac = (uint32_t)std::floor((rate - fl) * 4294967296.0);
+    int B = 1;
+    while (((int64_t)1 << B) < g.n) ++B;
+    sp.B = B;
+    if (b <= 0.0) b = 1.0;
+    const double vol = (double)g.nnz;
+    const double vv = vol * vol;
+    sp.alpha_off = vv / ((2.0 * S) * b);
+    sp.alpha_diag = vv / (S * b);
+    *out = sp;
+    return 0;
+}
+
+int sample_pairs(Workspace &ws, const GraphView &g, const SamplerSpec &sp, int64_t a0, int64_t a1,
+                 int32_t *u1, int32_t *v1, int64_t capacity, int64_t *count, cudaStream_t st) {
+    if (a0 < 0 || a1 > g.nnz || a0 > a1) return fail(LNE_ERR_INVALID, "arc range out of bounds");
+    *count = 0;
+    if (a0 == a1) return 0;
+    WalkArgs A = make_walk_args(g, sp);
+    const int tile_arcs = choose_tile_arcs(a1 - a0, (double)sp.base + 0.5);
+    int64_t *tile_off = nullptr;
+    int64_t total = 0;
+    LNE_TRY(tile_offsets(ws, A, a0, a1, tile_arcs, &tile_off, &total, st));
+    *count = total;
+    if (total > capacity) return fail(LNE_ERR_INVALID, "output capacity too small for the sampled pairs");
+    const int64_t ntiles = ceil_div(a1 - a0, tile_arcs);
+    const int smem = walk_smem_bytes(tile_arcs, 0);
+    {
+        LNE_TRACE("walk_emit", st);
+        walk_emit_kernel<uint32_t, 0><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
+            A, a0, a1, tile_arcs, tile_off, nullptr, u1, v1, nullptr, 0);
+        LNE_LAUNCH_CHECK();
+    }
+    return 0;
+}
+
+namespace {
+
+// Sample, bucket and reduce: distinct keys with counts in per-bucket regions.
+struct Reduced {
+    int64_t total = 0;
+    int nb = 0;
+    int64_t *bucket_off = nullptr;   // [nb+1], region of bucket b in rkey/rcnt
+    uint32_t *distinct = nullptr;    // [nb]
+    uint32_t *rkey = nullptr;
+    uint32_t *rcnt = nullptr;
+};
+
+int sample_and_reduce(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Reduced *R,
+                      cudaStream_t st) {
+    if (2 * sp.B > 32)
+        return fail(LNE_ERR_UNSUPPORTED, "graphs with more than 65536 vertices need 64-bit pair keys (not in this build)");
+    WalkArgs A = make_walk_args(g, sp);
+    const int tile_arcs = choose_tile_arcs(g.nnz, (double)sp.base + 0.5);
+    int64_t *tile_off = nullptr;
+    int64_t total = 0;
+    LNE_TRY(tile_offsets(ws, A, 0, g.nnz, tile_arcs, &tile_off, &total, st));
+    R->total = total;
+    const uint64_t max_key = ((uint64_t)(g.n - 1) << sp.B) | (uint64_t)(g.n - 1);
+    const int nb = (int)((max_key >> kBucketBits) + 1);
+    R->nb = nb;
+    uint32_t *keys0 = nullptr, *keys1 = nullptr, *bucket_cnt = nullptr;
+    unsigned long long *cursor = nullptr;
+    LNE_TRY(ws.get("spars.keys0", (size_t)std::max<int64_t>(total, 1), &keys0));
+    LNE_TRY(ws.get("spars.keys1", (size_t)std::max<int64_t>(total, 1), &keys1));
+    LNE_TRY(ws.get("spars.bucket_cnt", (size_t)nb, &bucket_cnt));
+    LNE_TRY(ws.get("spars.bucket_off", (size_t)nb + 1, &R->bucket_off));
+    LNE_TRY(ws.get("spars.cursor", (size_t)nb, &cursor));
+    LNE_TRY(ws.get("spars.distinct", (size_t)nb, &R->distinct));
+    LNE_CUDA_TRY(cudaMemsetAsync(bucket_cnt, 0, sizeof(uint32_t) * nb, st));
+    const int64_t ntiles = ceil_div(g.nnz, tile_arcs);
+    const int nb_smem = nb <= kMaxSmemBuckets ? nb : 0;
+    const int smem = walk_smem_bytes(tile_arcs, nb_smem);
+    if (smem > 48 * 1024)
+        LNE_CUDA_TRY(cudaFuncSetAttribute(walk_emit_kernel<uint32_t, 1>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    {
+        LNE_TRACE("walk_emit", st);
+        walk_emit_kernel<uint32_t, 1><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
+            A, 0, g.nnz, tile_arcs, tile_off, keys0, nullptr, nullptr, bucket_cnt, nb_smem);
+        LNE_LAUNCH_CHECK();
+    }
+    LNE_TRY(scan_exclusive_u32_to_i64(bucket_cnt, R->bucket_off, nb, st));
+    static_assert(sizeof(unsigned long long) == sizeof(int64_t), "cursor layout");
+    LNE_CUDA_TRY(cudaMemcpyAsync(cursor, R->bucket_off, sizeof(int64_t) * nb,
+                                 cudaMemcpyDeviceToDevice, st));
+    if (total > 0) {
+        if (nb <= kMaxSmemBuckets) {
+            const int sm = nb * (8 + 4);
+            if (sm > 48 * 1024)
+                LNE_CUDA_TRY(cudaFuncSetAttribute(bucket_scatter_kernel<uint32_t>,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+            const int64_t grid = ceil_div(total, (int64_t)kScatterThreads * kScatterItems);
+            LNE_TRACE("bucket_scatter", st);
+            bucket_scatter_kernel<uint32_t><<<(unsigned)grid, kScatterThreads, sm, st>>>(
+                keys0, total, keys1, cursor, nb);
+            LNE_LAUNCH_CHECK();
+        } else {
+            LNE_TRACE("bucket_scatter", st);
+            bucket_scatter_global_kernel<uint32_t><<<152 * 8, 256, 0, st>>>(keys0, total, keys1, cursor);
+            LNE_LAUNCH_CHECK();
+        }
+    }
+    // reduce into keys0 (reused) and a count array of the same size
+    uint32_t *rcnt = nullptr;
+    LNE_TRY(ws.get("spars.rcnt", (size_t)std::max<int64_t>(total, 1), &rcnt));
+    const int rsmem = (1 << kBucketBits) * 4;
+    LNE_CUDA_TRY(cudaFuncSetAttribute(bucket_reduce_kernel<uint32_t>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, rsmem));
+    {
+        LNE_TRACE("bucket_reduce", st);
+        bucket_reduce_kernel<uint32_t><<<nb, kReduceThreads, rsmem, st>>>(keys1, R->bucket_off, keys0,
+                                                                          rcnt, R->distinct);
+        LNE_LAUNCH_CHECK();
+    }
+    R->rkey = keys0;
+    R->rcnt = rcnt;
+    return 0;
+}
+
+int compact_counts(Workspace &ws, const SamplerSpec &sp, const Reduced &R, CountsResult *out,
+                   cudaStream_t st) {
+    int64_t *dst_off = nullptr;
+    LNE_TRY(ws.get("spars.dst_off", (size_t)R.nb + 1, &dst_off));
+    LNE_TRY(scan_exclusive_u32_to_i64(R.distinct, dst_off, R.nb, st));
+    int64_t nnz = 0;
+    LNE_CUDA_TRY(cudaMemcpyAsync(&nnz, dst_off + R.nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    LNE_TRY(ws.get("counts.x", (size_t)std::max<int64_t>(nnz, 1), &out->x));
+    LNE_TRY(ws.get("counts.y", (size_t)std::max<int64_t>(nnz, 1), &out->y));
+    LNE_TRY(ws.get("counts.cnt", (size_t)std::max<int64_t>(nnz, 1), &out->cnt));
+    {
+        LNE_TRACE("compact", st);
+        compact_kernel<uint32_t><<<R.nb, 256, 0, st>>>(R.rkey, R.rcnt, R.bucket_off, dst_off, sp.B,
+                                                       out->x, out->y, out->cnt);
+        LNE_LAUNCH_CHECK();
+    }
+    out->nnz = nnz;
+    out->total_samples = R.total;
+    return 0;
+}
+
+}  // namespace
+
+int sparsifier_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out,
+                      cudaStream_t st) {
+    Reduced R;
+    LNE_TRY(sample_and_reduce(ws, g, sp, &R, st));
+    LNE_TRY(compact_counts(ws, sp, R, out, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    return 0;
+}
+
+int sparsifier_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out,
+                   cudaStream_t st) {
+    Reduced R;
+    LNE_TRY(sample_and_reduce(ws, g, sp, &R, st));
+    CountsResult C;
+    LNE_TRY(compact_counts(ws, sp, R, &C, st));
+    const int64_t nnz_c = C.nnz;
+    float *val = nullptr;
+    uint8_t *keep = nullptr;
+    uint32_t *rowcnt = nullptr;
+    LNE_TRY(ws.get("csr.val_c", (size_t)std::max<int64_t>(nnz_c, 1), &val));
+    LNE_TRY(ws.get("csr.keep", (size_t)std::max<int64_t>(nnz_c, 1), &keep));
+    LNE_TRY(ws.get("csr.rowcnt", (size_t)g.n, &rowcnt));
+    LNE_TRY(ws.get("csr.indptr", (size_t)g.n + 1, &out->indptr));
+    LNE_CUDA_TRY(cudaMemsetAsync(rowcnt, 0, sizeof(uint32_t) * g.n, st));
+    const int grid = (int)std::min<int64_t>(ceil_div(std::max<int64_t>(nnz_c, 1), 256), 152 * 16);
+    {
+        LNE_TRACE("trunclog", st);
+        trunclog_kernel<<<grid, 256, 0, st>>>(C.x, C.y, C.cnt, nnz_c, g.indptr, sp.alpha_off,
+                                              sp.alpha_diag, val, keep, rowcnt);
+        LNE_LAUNCH_CHECK();
+    }
+    LNE_TRY(scan_exclusive_u32_to_i64(rowcnt, out->indptr, g.n, st));
+    int64_t nnz = 0;
+    LNE_CUDA_TRY(cudaMemcpyAsync(&nnz, out->indptr + g.n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    LNE_TRY(ws.get("csr.indices", (size_t)std::max<int64_t>(nnz, 1), &out->indices));
+    LNE_TRY(ws.get("csr.data", (size_t)std::max<int64_t>(nnz, 1), &out->data));
+    LNE_CUDA_TRY(cudaMemsetAsync(rowcnt, 0, sizeof(uint32_t) * g.n, st));
+    {
+        LNE_TRACE("csr_fill", st);
+        csr_fill_kernel<<<grid, 256, 0, st>>>(C.x, C.y, val, keep, nnz_c, out->indptr, rowcnt,
+                                              out->indices, out->data);
+        LNE_LAUNCH_CHECK();
+    }
+    int *too_long = nullptr;
+    LNE_TRY(ws.get("csr.too_long", 1, &too_long));
+    LNE_CUDA_TRY(cudaMemsetAsync(too_long, 0, sizeof(int), st));
+    const int ssmem = kSortMax * 8;
+    LNE_CUDA_TRY(cudaFuncSetAttribute(csr_row_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      ssmem));
+    {
+        LNE_TRACE("csr_row_sort", st);
+        csr_row_sort_kernel<<<(unsigned)g.n, kSortThreads, ssmem, st>>>(out->indptr, out->indices,
+                                                                       out->data, too_long);
+        LNE_LAUNCH_CHECK();
+    }
+    int tl = 0;
+    LNE_CUDA_TRY(cudaMemcpyAsync(&tl, too_long, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (tl > 0) return fail(LNE_ERR_UNSUPPORTED, "a sparsifier row is longer than the in-shared-memory row sort handles");
+    out->n = g.n;
+    out->nnz = nnz;
+    return 0;
+}
+
+}  // namespace lne

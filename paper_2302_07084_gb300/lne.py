@@ -1,0 +1,320 @@
+"""Python binding of the C ABI in ``include/lne.h`` (argument marshalling only).
+
+Every computation runs in the CUDA library ``_build/liblne.so``; PyTorch only
+provides device memory and streams. There is no CPU fallback: if the library
+is missing or fails to load, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "liblne.so")
+
+LNE_OK = 0
+ERRORS = {-1: "LNE_ERR_INVALID", -2: "LNE_ERR_OOM", -3: "LNE_ERR_CUDA", -4: "LNE_ERR_TIMEOUT",
+          -5: "LNE_ERR_UNSUPPORTED", -6: "LNE_ERR_NUMERIC"}
+PREC_FP32 = 0
+PREC_BF16_MIXED = 1
+
+EXPORTED = [
+    "lne_create", "lne_destroy", "lne_last_error", "lne_workspace_bytes", "lne_trim",
+    "lne_sample_pairs", "lne_sparsifier_counts", "lne_sparsifier_csr", "lne_gaussian_sketch",
+    "lne_spmm", "lne_cholqr2", "lne_rsvd", "lne_propagate", "lne_embed",
+    "lne_kernel_launches", "lne_trace_enable", "lne_trace_read",
+]
+
+
+class LneError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class _Graph(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("indptr", ctypes.c_void_p),
+                ("indices", ctypes.c_void_p)]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("s", ctypes.POINTER(ctypes.c_double)), ("samples", ctypes.c_double),
+                ("b", ctypes.c_double), ("d", ctypes.c_int32), ("oversample", ctypes.c_int32),
+                ("q", ctypes.c_int32), ("k", ctypes.c_int32), ("theta", ctypes.c_double),
+                ("mu", ctypes.c_double), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32)]
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("indptr", ctypes.c_void_p),
+                ("indices", ctypes.c_void_p), ("data", ctypes.c_void_p)]
+
+
+class _TraceEntry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 40), ("regions", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("total_ms", ctypes.c_double)]
+
+
+class _Counts(ctypes.Structure):
+    _fields_ = [("nnz", ctypes.c_int64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
+                ("count", ctypes.c_void_p), ("total_samples", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not found at {path}; build it with __graft_entry__.build() "
+                           "or python paper_2302_07084_gb300/build.py")
+    L = ctypes.CDLL(path)
+    vp, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+    L.lne_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    L.lne_destroy.argtypes = [vp]
+    L.lne_destroy.restype = None
+    L.lne_last_error.argtypes = [vp]
+    L.lne_last_error.restype = ctypes.c_char_p
+    L.lne_workspace_bytes.argtypes = [vp]
+    L.lne_workspace_bytes.restype = i64
+    L.lne_trim.argtypes = [vp]
+    gp, pp = ctypes.POINTER(_Graph), ctypes.POINTER(_Params)
+    L.lne_sample_pairs.argtypes = [vp, gp, pp, i64, i64, vp, vp, i64, ctypes.POINTER(i64), vp]
+    L.lne_sparsifier_counts.argtypes = [vp, gp, pp, ctypes.POINTER(_Counts), vp]
+    L.lne_sparsifier_csr.argtypes = [vp, gp, pp, ctypes.POINTER(_Csr), vp]
+    L.lne_gaussian_sketch.argtypes = [vp, i64, i32, u64, vp, i64, vp]
+    L.lne_spmm.argtypes = [vp, ctypes.POINTER(_Csr), vp, i64, i32, vp, i64, vp]
+    L.lne_cholqr2.argtypes = [vp, vp, i64, i32, i64, vp, vp]
+    L.lne_rsvd.argtypes = [vp, ctypes.POINTER(_Csr), pp, vp, vp, vp, vp]
+    L.lne_propagate.argtypes = [vp, gp, pp, vp, vp, vp, vp, vp]
+    L.lne_embed.argtypes = [vp, gp, pp, vp, vp]
+    L.lne_kernel_launches.argtypes = []
+    L.lne_kernel_launches.restype = i64
+    L.lne_trace_enable.argtypes = [vp, ctypes.c_int]
+    L.lne_trace_read.argtypes = [vp, ctypes.POINTER(_TraceEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    _lib = L
+    return L
+
+
+@dataclasses.dataclass
+class Params:
+    """Method parameters in the paper's notation."""
+    T: int = 10
+    s: Sequence[float] = dataclasses.field(default_factory=lambda: [0.1] * 10)
+    samples: float = 1.0          # S, total edge samples
+    b: float = 1.0
+    d: int = 128
+    oversample: int = 16
+    q: int = 1
+    k: int = 10
+    theta: float = 0.5
+    mu: float = 0.2
+    seed: int = 0
+    precision: int = PREC_FP32
+
+    def _c(self):
+        s = np.ascontiguousarray(np.asarray(self.s, dtype=np.float64))
+        arr = (ctypes.c_double * max(1, len(s)))(*s.tolist())
+        p = _Params(int(self.T), ctypes.cast(arr, ctypes.POINTER(ctypes.c_double)), float(self.samples),
+                    float(self.b), int(self.d), int(self.oversample), int(self.q), int(self.k),
+                    float(self.theta), float(self.mu), int(self.seed) & 0xFFFFFFFFFFFFFFFF,
+                    int(self.precision))
+        return p, arr
+
+
+class DeviceGraph:
+    """A CSR graph resident on the GPU (int64 indptr, int32 indices)."""
+
+    def __init__(self, indptr, indices, device="cuda"):
+        self.indptr = torch.as_tensor(np.asarray(indptr, dtype=np.int64)).to(device)
+        self.indices = torch.as_tensor(np.asarray(indices, dtype=np.int32)).to(device)
+        self.n = int(self.indptr.numel() - 1)
+        self.nnz = int(self.indices.numel())
+
+    @classmethod
+    def from_graph(cls, g, device="cuda"):
+        return cls(g.indptr, g.indices, device)
+
+    def _c(self):
+        return _Graph(self.n, self.nnz, self.indptr.data_ptr(), self.indices.data_ptr() if self.nnz else None)
+
+
+class _DevView:
+    """Zero-copy view of context-owned device memory for torch.as_tensor."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr or 0), False),
+                                         "version": 3, "strides": None}
+
+
+def _own(ptr, n, typestr, dtype, device):
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device=device)
+    return torch.as_tensor(_DevView(ptr, n, typestr), device=device).clone()
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """One library context (workspace owner) on a CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load_library()
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = self.lib.lne_create(ctypes.byref(h), device)
+        if rc != 0:
+            raise LneError(rc, f"lne_create failed on device {device}")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lne_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise LneError(rc, self.lib.lne_last_error(self.h).decode())
+
+    def workspace_bytes(self) -> int:
+        return int(self.lib.lne_workspace_bytes(self.h))
+
+    def trim(self):
+        self._check(self.lib.lne_trim(self.h))
+
+    def kernel_launches(self) -> int:
+        return int(self.lib.lne_kernel_launches())
+
+    def trace(self, on: bool = True):
+        self._check(self.lib.lne_trace_enable(self.h, 1 if on else 0))
+
+    def trace_read(self) -> list[dict]:
+        """Per region name: regions run, kernels launched, summed CUDA-event ms."""
+        cap = 128
+        buf = (_TraceEntry * cap)()
+        cnt = ctypes.c_int()
+        self._check(self.lib.lne_trace_read(self.h, buf, cap, ctypes.byref(cnt)))
+        return [dict(name=buf[i].name.decode(), regions=int(buf[i].regions), launches=int(buf[i].launches),
+                     ms=float(buf[i].total_ms)) for i in range(min(cnt.value, cap))]
+
+    @property
+    def dev(self):
+        return torch.device("cuda", self.device)
+
+    # ---- sparsifier ---------------------------------------------------------
+    def sample_pairs(self, g: DeviceGraph, p: Params, arc_begin: int = 0, arc_end: Optional[int] = None,
+                     capacity: Optional[int] = None):
+        arc_end = g.nnz if arc_end is None else arc_end
+        if capacity is None:
+            rate = float(p.samples) / max(g.nnz, 1)
+            capacity = int((arc_end - arc_begin) * (np.floor(rate) + 1)) + 1
+        u1 = torch.empty(capacity, dtype=torch.int32, device=self.dev)
+        v1 = torch.empty(capacity, dtype=torch.int32, device=self.dev)
+        cnt = ctypes.c_int64()
+        gc = g._c()
+        pc, keep = p._c()
+        self._check(self.lib.lne_sample_pairs(self.h, ctypes.byref(gc), ctypes.byref(pc), arc_begin, arc_end,
+                                              _ptr(u1), _ptr(v1), capacity, ctypes.byref(cnt), _stream()))
+        return u1[: cnt.value], v1[: cnt.value]
+
+    def sparsifier_counts(self, g: DeviceGraph, p: Params):
+        out = _Counts()
+        gc = g._c()
+        pc, keep = p._c()
+        self._check(self.lib.lne_sparsifier_counts(self.h, ctypes.byref(gc), ctypes.byref(pc), ctypes.byref(out),
+                                                   _stream()))
+        return dict(x=_own(out.x, out.nnz, "<i4", torch.int32, self.dev),
+                    y=_own(out.y, out.nnz, "<i4", torch.int32, self.dev),
+                    count=_own(out.count, out.nnz, "<u4", torch.uint32, self.dev),
+                    total_samples=int(out.total_samples))
+
+    def sparsifier_csr(self, g: DeviceGraph, p: Params):
+        out = _Csr()
+        gc = g._c()
+        pc, keep = p._c()
+        self._check(self.lib.lne_sparsifier_csr(self.h, ctypes.byref(gc), ctypes.byref(pc), ctypes.byref(out),
+                                                _stream()))
+        return dict(n=int(out.n), nnz=int(out.nnz),
+                    indptr=_own(out.indptr, out.n + 1, "<i8", torch.int64, self.dev),
+                    indices=_own(out.indices, out.nnz, "<i4", torch.int32, self.dev),
+                    data=_own(out.data, out.nnz, "<f4", torch.float32, self.dev))
+
+    # ---- linear algebra -----------------------------------------------------
+    def gaussian_sketch(self, n: int, c: int, seed: int) -> torch.Tensor:
+        out = torch.empty((n, c), dtype=torch.float32, device=self.dev)
+        self._check(self.lib.lne_gaussian_sketch(self.h, n, c, int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out), c,
+                                                 _stream()))
+        return out
+
+    @staticmethod
+    def _csr(csr: dict) -> _Csr:
+        return _Csr(int(csr["n"]), int(csr["nnz"]), csr["indptr"].data_ptr(),
+                    csr["indices"].data_ptr() if csr["nnz"] else None,
+                    csr["data"].data_ptr() if csr["nnz"] else None)
+
+    def spmm(self, csr: dict, X: torch.Tensor) -> torch.Tensor:
+        X = X.contiguous()
+        n, c = X.shape
+        Y = torch.empty((int(csr["n"]), c), dtype=torch.float32, device=self.dev)
+        m = self._csr(csr)
+        self._check(self.lib.lne_spmm(self.h, ctypes.byref(m), _ptr(X), c, c, _ptr(Y), c, _stream()))
+        return Y
+
+    def cholqr2(self, Y: torch.Tensor):
+        """Returns (Q, R): Q overwrites a copy of Y; R is FP64 upper triangular."""
+        Q = Y.contiguous().clone()
+        n, c = Q.shape
+        R = torch.zeros((c, c), dtype=torch.float64, device=self.dev)
+        self._check(self.lib.lne_cholqr2(self.h, _ptr(Q), n, c, c, _ptr(R), _stream()))
+        return Q, R
+
+    def rsvd(self, csr: dict, p: Params):
+        n = int(csr["n"])
+        U = torch.empty((n, p.d), dtype=torch.float32, device=self.dev)
+        X0 = torch.empty((n, p.d), dtype=torch.float32, device=self.dev)
+        sig = torch.empty(p.d, dtype=torch.float64, device=self.dev)
+        m = self._csr(csr)
+        pc, keep = p._c()
+        self._check(self.lib.lne_rsvd(self.h, ctypes.byref(m), ctypes.byref(pc), _ptr(U), _ptr(sig), _ptr(X0),
+                                      _stream()))
+        return dict(U=U, sigma=sig, X0=X0)
+
+    def propagate(self, g: DeviceGraph, p: Params, X0: torch.Tensor, want_intermediates: bool = False):
+        X0 = X0.contiguous()
+        X = torch.empty_like(X0)
+        F = torch.empty_like(X0) if want_intermediates else None
+        P = torch.empty_like(X0) if want_intermediates else None
+        gc = g._c()
+        pc, keep = p._c()
+        self._check(self.lib.lne_propagate(self.h, ctypes.byref(gc), ctypes.byref(pc), _ptr(X0), _ptr(X), _ptr(F),
+                                           _ptr(P), _stream()))
+        return dict(X=X, F=F, P=P)
+
+    def embed(self, g: DeviceGraph, p: Params, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        X = out if out is not None else torch.empty((g.n, p.d), dtype=torch.float32, device=self.dev)
+        gc = g._c()
+        pc, keep = p._c()
+        self._check(self.lib.lne_embed(self.h, ctypes.byref(gc), ctypes.byref(pc), _ptr(X), _stream()))
+        return X

@@ -1,0 +1,178 @@
+"""GPU sparsifier construction against the CPU oracle (bit-exact integer work).
+
+* raw PathSampling draws (lne_sample_pairs) equal the oracle's draws;
+* exact pair counts (lne_sparsifier_counts) equal the oracle's;
+* the trunc_log CSR (lne_sparsifier_csr): structure and keep decisions exact,
+  values within 1e-6 relative (FP32 log vs FP64 log rounded to FP32);
+* the bench workload (BlogCatalog-shaped graph, S = 200 T m) on sampled arc
+  ranges plus whole-run invariants.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2302_07084_gb300 import lne, synth
+from gpu_common import make_params, oracle_counts, to_np
+
+pytestmark = pytest.mark.gpu
+
+VAL_RTOL = 1e-6
+VAL_ATOL = 1e-7
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2302_07084_gb300 import build
+    build.build()
+    c = lne.Context(0)
+    yield c
+    c.close()
+
+
+def _graphs():
+    return {
+        "sbm600": synth.sbm(600, 3, 0.05, 0.005, seed=3),
+        "chunglu2k": synth.chung_lu(2000, 12000, 2.1, seed=4, n_labels=5),
+        "lollipop": synth.lollipop_tiny(),
+        "ring97": synth.ring(97),
+    }
+
+
+GRAPHS = _graphs()
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("T,rate", [(10, 3.0), (1, 2.0), (5, 2.5), (16, 0.7)])
+def test_sample_pairs_bit_exact(ctx, name, T, rate):
+    g = GRAPHS[name]
+    s = synth.dirichlet_weights(T, seed=T)
+    p = make_params(T, s, rate * g.n_arcs, seed=77)
+    dg = lne.DeviceGraph.from_graph(g)
+    for a0, a1 in [(0, g.n_arcs), (1, min(g.n_arcs, 40)), (g.n_arcs // 3, g.n_arcs - 1)]:
+        if a1 <= a0:
+            continue
+        u1, v1 = ctx.sample_pairs(dg, p, a0, a1)
+        tr = oracle.sample_trace(g.indptr, g.indices, T, s, p.samples, p.seed, a0, a1, fields=("u1", "v1"))
+        assert np.array_equal(to_np(u1).astype(np.int64), tr["u1"])
+        assert np.array_equal(to_np(v1).astype(np.int64), tr["v1"])
+
+
+def test_sample_pairs_capacity_error(ctx):
+    g = GRAPHS["sbm600"]
+    p = make_params(10, np.ones(10), 4.0 * g.n_arcs)
+    with pytest.raises(lne.LneError) as e:
+        ctx.sample_pairs(lne.DeviceGraph.from_graph(g), p, 0, g.n_arcs, capacity=10)
+    assert e.value.code == -1
+    # the context stays usable after an error
+    u1, _ = ctx.sample_pairs(lne.DeviceGraph.from_graph(g), p, 0, 5)
+    assert u1.numel() == 20
+
+
+def _check_counts(ctx, g, p):
+    res = ctx.sparsifier_counts(lne.DeviceGraph.from_graph(g), p)
+    x, y, c = oracle_counts(g, p)
+    assert res["total_samples"] == oracle.count_samples(g.n_arcs, p.samples, p.seed)
+    assert np.array_equal(to_np(res["x"]).astype(np.int64), x)
+    assert np.array_equal(to_np(res["y"]).astype(np.int64), y)
+    assert np.array_equal(to_np(res["count"]).astype(np.int64), c)
+    return res
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_counts_bit_exact(ctx, name):
+    g = GRAPHS[name]
+    _check_counts(ctx, g, make_params(10, synth.dirichlet_weights(10, 5), 20.0 * g.n_arcs, seed=9))
+
+
+def test_counts_T1_edges_only(ctx):
+    g = GRAPHS["sbm600"]
+    res = _check_counts(ctx, g, make_params(1, [1.0], 3.0 * g.n_arcs, seed=2))
+    assert np.all(to_np(res["count"]) == 6)
+
+
+def test_counts_sbm_small_workload(ctx):
+    """The 10k-node SBM workload (T=10, s_r=1/T, S=10 T m) in full."""
+    g = synth.sbm_small()
+    _check_counts(ctx, g, make_params(10, np.full(10, 0.1), 100.0 * g.m, seed=1))
+
+
+def _check_csr(ctx, g, p):
+    out = ctx.sparsifier_csr(lne.DeviceGraph.from_graph(g), p)
+    sp = oracle.sparsifier(g.indptr, g.indices, p.T, p.s, p.samples, p.seed, p.b)
+    assert np.array_equal(to_np(out["indptr"]), sp["indptr"])
+    assert np.array_equal(to_np(out["indices"]).astype(np.int64), sp["indices"])
+    np.testing.assert_allclose(to_np(out["data"]), sp["data"], rtol=VAL_RTOL, atol=VAL_ATOL)
+    return out, sp
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("rate", [1.0, 20.0])
+def test_csr_matches_oracle(ctx, name, rate):
+    g = GRAPHS[name]
+    _check_csr(ctx, g, make_params(10, np.full(10, 0.1), rate * g.n_arcs, seed=4))
+
+
+def test_csr_b_and_isolated_vertices(ctx):
+    # vertices 600..609 have no edges: zero rows everywhere
+    g0 = synth.sbm(600, 3, 0.05, 0.005, seed=3)
+    indptr = np.concatenate([g0.indptr, np.full(10, g0.indptr[-1])])
+    g = synth.Graph(610, indptr, g0.indices, None, "isolated")
+    out, sp = _check_csr(ctx, g, make_params(5, [0.3, 0.3, 0.2, 0.1, 0.1], 8.0 * g.n_arcs, seed=12, b=2.0))
+    assert np.all(np.diff(to_np(out["indptr"]))[600:] == 0)
+
+
+def test_bad_arguments_are_rejected(ctx):
+    g = GRAPHS["sbm600"]
+    dg = lne.DeviceGraph.from_graph(g)
+    for bad in [dict(T=0, s=[1.0]), dict(T=17, s=[1.0] * 17), dict(s=[0.0] * 10), dict(S=0.0)]:
+        T = bad.get("T", 10)
+        p = make_params(T, bad.get("s", np.ones(T)), bad.get("S", 10.0 * g.n_arcs))
+        with pytest.raises(lne.LneError) as e:
+            ctx.sparsifier_counts(dg, p)
+        assert e.value.code == -1
+    # indptr not ending at nnz
+    broken = lne.DeviceGraph(g.indptr, g.indices)
+    broken.nnz = g.n_arcs - 1
+    with pytest.raises(lne.LneError):
+        ctx.sparsifier_counts(broken, make_params(10, np.ones(10), 10.0 * g.n_arcs))
+
+
+def test_bench_workload_sampled(ctx):
+    """BlogCatalog-shaped workload at full size: S = 200 T m = 6.68e8 samples.
+
+    The oracle cannot aggregate 6.68e8 samples in seconds, so it checks random
+    arc ranges draw by draw; the full run is checked through invariants that
+    hold at any size."""
+    g = synth.blogcatalog_like()
+    s = synth.dirichlet_weights(10, seed=3)
+    p = make_params(10, s, 200.0 * 10 * g.m, seed=2, d=128)
+    dg = lne.DeviceGraph.from_graph(g)
+    rng = np.random.default_rng(0)
+    for _ in range(6):
+        a0 = int(rng.integers(0, g.n_arcs - 300))
+        a1 = a0 + int(rng.integers(1, 300))
+        u1, v1 = ctx.sample_pairs(dg, p, a0, a1)
+        tr = oracle.sample_trace(g.indptr, g.indices, 10, s, p.samples, p.seed, a0, a1, fields=("u1", "v1"))
+        assert np.array_equal(to_np(u1).astype(np.int64), tr["u1"])
+        assert np.array_equal(to_np(v1).astype(np.int64), tr["v1"])
+    res = ctx.sparsifier_counts(dg, p)
+    assert res["total_samples"] == int(p.samples)          # S/2m = 1000 exactly
+    cnt = res["count"].to(torch.int64)
+    assert int(cnt.sum()) == res["total_samples"]
+    x, y = res["x"].to(torch.int64), res["y"].to(torch.int64)
+    key = x * g.n + y
+    assert bool((key[1:] > key[:-1]).all())
+    assert bool((x <= y).all()) and int(y.max()) < g.n
+    # each sampled pair's count against an independent oracle draw of one arc's samples:
+    # the pairs drawn from arcs [a0, a1) are a sub-multiset of the full counts
+    a0, a1 = 1000, 1100
+    tr = oracle.sample_trace(g.indptr, g.indices, 10, s, p.samples, p.seed, a0, a1, fields=("u1", "v1"))
+    sub = np.minimum(tr["u1"], tr["v1"]) * g.n + np.maximum(tr["u1"], tr["v1"])
+    uk, uc = np.unique(sub, return_counts=True)
+    full = dict(zip(to_np(key).tolist(), to_np(cnt).tolist()))
+    assert all(full.get(int(k_), 0) >= int(c_) for k_, c_ in zip(uk, uc))
+    out = ctx.sparsifier_csr(dg, p)
+    ip = to_np(out["indptr"])
+    assert ip[0] == 0 and ip[-1] == out["nnz"] and np.all(np.diff(ip) >= 0)
+    assert bool((out["data"] > 0).all())
