@@ -314,11 +314,7 @@ def run_ours(args):
     per_launch = {}
     for t in trace:
         per_launch[t["name"]] = t
-    dom = max((t for t in trace if t["name"] in ("walk_emit", "bucket_scatter", "bucket_reduce", "spmm",
-                                                 "graph_spmm", "jacobi_svd", "chol_inv", "gram_partial",
-                                                 "csr_row_sort", "trunclog", "csr_fill", "right_multiply",
-                                                 "tile_counts", "sketch", "compact")),
-              key=lambda t: t["ms"])
+    dom = max(trace, key=lambda t: t["ms"])
     model = kernel_model(dom["name"], g, params, info)
     roof = None
     if model is not None:

@@ -92,6 +92,12 @@ typedef struct {
 
 typedef struct lne_ctx lne_ctx;
 
+/* Options of a context (lne_set_option). */
+#define LNE_OPT_AGGREGATION  1   /* how sampled pairs are counted: */
+#define LNE_AGG_AUTO         0   /*   dense table when it fits, else bucket sort */
+#define LNE_AGG_TABLE        1   /*   dense n x n count table, atomic increments */
+#define LNE_AGG_BUCKET       2   /*   keys bucketed by row block, shared-memory counting */
+
 /* Create a context on CUDA device `device`. The context owns its workspace. */
 int lne_create(lne_ctx **out, int device);
 void lne_destroy(lne_ctx *ctx);
@@ -100,6 +106,9 @@ const char *lne_last_error(const lne_ctx *ctx);
 int64_t lne_workspace_bytes(const lne_ctx *ctx);
 /* Release all workspace (the next call re-allocates). */
 int lne_trim(lne_ctx *ctx);
+/* Set a context option (LNE_OPT_*); both aggregation methods give identical
+ * (exact) counts, they differ in memory use and speed. */
+int lne_set_option(lne_ctx *ctx, int option, int64_t value);
 
 /*
  * Raw PathSampling draws of arcs [arc_begin, arc_end) (Algorithm 1 driven per
@@ -151,6 +160,16 @@ int lne_spmm(lne_ctx *ctx, const lne_csr *M, const float *X_dev, int64_t ldx, in
  */
 int lne_cholqr2(lne_ctx *ctx, float *Y_dev, int64_t n, int32_t c, int64_t ld, double *R_dev,
                 void *stream);
+
+/*
+ * SVD of a c x c FP64 matrix R (c <= 160; in the method R is the triangular
+ * factor of the last sketch, so that Y = Q R gives Y's SVD as Q U_R) -- the
+ * eig step of eigSVD (Algorithm 2). U_dev [c][c] row-major FP64 (column j = j-th
+ * left singular vector), sigma_dev [c] FP64 descending. FP64-accurate: FP32
+ * Jacobi start, Ogita-Aishima refinement of the eigenvectors of R^T R in FP64.
+ */
+int lne_svd_small(lne_ctx *ctx, const double *R_dev, int32_t c, double *U_dev, double *sigma_dev,
+                  void *stream);
 
 /*
  * Fast randomized SVD (Algorithm 4) of the symmetric CSR M with the Gaussian

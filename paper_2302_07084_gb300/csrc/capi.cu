@@ -149,6 +149,7 @@ int64_t Workspace::bytes() const {
 
 struct lne_ctx {
     int device = 0;
+    int aggregation = LNE_AGG_AUTO;
     std::string err;
     lne::Workspace ws;
     lne::Tracer tracer;
@@ -254,6 +255,18 @@ void lne_destroy(lne_ctx *ctx) {
 
 int64_t lne_kernel_launches(void) { return lne::g_launches.load(); }
 
+int lne_set_option(lne_ctx *ctx, int option, int64_t value) {
+    if (!ctx) return LNE_ERR_INVALID;
+    lne::clear_message();
+    if (option == LNE_OPT_AGGREGATION) {
+        if (value != LNE_AGG_AUTO && value != LNE_AGG_TABLE && value != LNE_AGG_BUCKET)
+            return finish(ctx, lne::fail(LNE_ERR_INVALID, "unknown aggregation method"));
+        ctx->aggregation = (int)value;
+        return LNE_OK;
+    }
+    return finish(ctx, lne::fail(LNE_ERR_INVALID, "unknown option"));
+}
+
 int lne_trace_enable(lne_ctx *ctx, int on) {
     if (!ctx) return LNE_ERR_INVALID;
     int rc = enter(ctx);
@@ -325,6 +338,7 @@ int lne_sample_pairs(lne_ctx *ctx, const lne_graph *g, const lne_params *p, int6
     if (rc == 0) rc = check_graph_device(g, st);
     lne::SamplerSpec sp;
     if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
+    sp.aggregation = ctx->aggregation;
     if (rc == 0) rc = lne::sample_pairs(ctx->ws, view(g), sp, arc_begin, arc_end, u1_dev, v1_dev, capacity,
                                         count_out, st);
     return finish(ctx, rc);
@@ -341,6 +355,7 @@ int lne_sparsifier_counts(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
     if (rc == 0) rc = check_graph_device(g, st);
     lne::SamplerSpec sp;
     if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
+    sp.aggregation = ctx->aggregation;
     lne::CountsResult r;
     if (rc == 0) rc = lne::sparsifier_counts(ctx->ws, view(g), sp, &r, st);
     if (rc == 0) {
@@ -363,6 +378,7 @@ int lne_sparsifier_csr(lne_ctx *ctx, const lne_graph *g, const lne_params *p, ln
     if (rc == 0) rc = check_graph_device(g, st);
     lne::SamplerSpec sp;
     if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
+    sp.aggregation = ctx->aggregation;
     lne::CsrResult r;
     if (rc == 0) rc = lne::sparsifier_csr(ctx->ws, view(g), sp, &r, st);
     if (rc == 0) {
@@ -408,6 +424,14 @@ int lne_cholqr2(lne_ctx *ctx, float *Y_dev, int64_t n, int32_t c, int64_t ld, do
     int rc = enter(ctx);
     if (rc == 0 && (!Y_dev || ld < c)) rc = lne::fail(LNE_ERR_INVALID, "bad CholeskyQR2 arguments");
     if (rc == 0) rc = lne::cholqr2(ctx->ws, Y_dev, n, c, ld, R_dev, as_stream(stream));
+    return finish(ctx, rc);
+}
+
+int lne_svd_small(lne_ctx *ctx, const double *R_dev, int32_t c, double *U_dev, double *sigma_dev, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (!R_dev || !U_dev || !sigma_dev || c < 1)) rc = lne::fail(LNE_ERR_INVALID, "bad small SVD arguments");
+    if (rc == 0) rc = lne::small_svd(ctx->ws, R_dev, c, U_dev, sigma_dev, as_stream(stream));
     return finish(ctx, rc);
 }
 
@@ -457,6 +481,7 @@ int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_de
     if (rc == 0) rc = check_graph_device(g, st);
     lne::SamplerSpec sp;
     if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
+    sp.aggregation = ctx->aggregation;
     lne::CsrResult M;
     if (rc == 0) rc = lne::sparsifier_csr(ctx->ws, view(g), sp, &M, st);
     float *X0 = nullptr;

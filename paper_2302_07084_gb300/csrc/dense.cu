@@ -4,13 +4,14 @@
 //   gram           G = Y^T Y in FP64: per-CTA partial Grams over row blocks
 //                  (products of FP32 inputs are exact in FP64), summed in a
 //                  fixed order so the result is reproducible.
-//   chol_inv       G = R^T R (upper Cholesky) and R^-1 in FP64, one CTA.
+//   chol           G = R^T R (upper Cholesky) in FP64, one CTA.
+//   trsm_rows      Q = Y R^-1 by forward substitution per row (FP32).
 //   right_multiply out = Y W for a small FP64 W (rounded to FP32), FP32 FMA.
 //   cholqr2        Q = Y R1^-1, then again: the orthonormalisation used in
 //                  place of eigSVD inside the power iteration (same range).
-//   small_svd      one-sided (Hestenes) Jacobi on the c x c factor R in FP64:
-//                  R V = U_R Sigma, so Y = Q R gives left singular vectors
-//                  Q U_R -- the final eigSVD step of Algorithm 4.
+//   small_svd      SVD of the c x c factor R: FP32 one-sided Jacobi, then
+//                  Ogita-Aishima refinement in FP64, so Y = Q R gives left
+//                  singular vectors Q U_R -- the final eigSVD of Algorithm 4.
 //   sign_fix_embed largest-magnitude entry of each column made positive, and
 //                  X = U Sigma^{1/2} (Sec. 3.2).
 #include <algorithm>
@@ -140,70 +141,99 @@ __global__ void gram_reduce_kernel(const double *__restrict__ partial, int nblk,
 }
 
 // ---------------------------------------------------------------------------
-// Cholesky (upper, G = R^T R) and R^-1, one CTA, FP64.
+// Cholesky (upper, G = R^T R), one CTA, FP64. Right-looking: for each k the
+// pivot row is scaled by 1/sqrt(pivot) and the trailing upper triangle takes
+// the rank-1 update.
 // ---------------------------------------------------------------------------
-constexpr int kCholThreads = 512;
+constexpr int kCholThreads = 1024;
 constexpr int kMaxSmemC = 160;
 
-__global__ void __launch_bounds__(kCholThreads) chol_inv_kernel(const double *__restrict__ G, int c,
-                                                                double *__restrict__ R,
-                                                                double *__restrict__ Rinv,
-                                                                int *__restrict__ status) {
+__global__ void __launch_bounds__(kCholThreads) chol_kernel(const double *__restrict__ G, int c,
+                                                            double *__restrict__ R, int *__restrict__ status) {
     extern __shared__ double sm[];
     const bool in_smem = c <= kMaxSmemC;
     double *A = in_smem ? sm : R;
+    __shared__ double s_inv;
+    __shared__ int bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kCholThreads / 32;
     for (int e = tid; e < c * c; e += kCholThreads) A[e] = G[e];
-    __syncthreads();
-    __shared__ int bad;
     if (tid == 0) bad = 0;
     __syncthreads();
     for (int k = 0; k < c; ++k) {
         if (tid == 0) {
-            double akk = A[k * c + k];
+            const double akk = A[k * c + k];
             if (!(akk > 0.0) || !isfinite(akk)) {
-                bad = k + 1;
+                if (!bad) bad = k + 1;
                 A[k * c + k] = 1.0;
+                s_inv = 1.0;
             } else {
-                A[k * c + k] = sqrt(akk);
+                const double dk = sqrt(akk);
+                A[k * c + k] = dk;
+                s_inv = 1.0 / dk;
             }
         }
         __syncthreads();
-        const double piv = A[k * c + k];
-        for (int j = k + 1 + tid; j < c; j += kCholThreads) A[k * c + j] /= piv;
+        const double inv = s_inv;
+        for (int j = k + 1 + tid; j < c; j += kCholThreads) A[k * c + j] *= inv;
         __syncthreads();
         for (int i = k + 1 + warp; i < c; i += nw) {
             const double aki = A[k * c + i];
-            for (int j = i + lane; j < c; j += 32) A[i * c + j] -= aki * A[k * c + j];
+            for (int j = i + lane; j < c; j += 32) A[i * c + j] = fma(-aki, A[k * c + j], A[i * c + j]);
         }
         __syncthreads();
     }
-    // R = upper triangle of A
-    if (in_smem) {
-        for (int e = tid; e < c * c; e += kCholThreads) {
-            int i = e / c, j = e - i * c;
-            R[e] = j >= i ? A[e] : 0.0;
-        }
-    } else {
-        for (int e = tid; e < c * c; e += kCholThreads) {
-            int i = e / c, j = e - i * c;
-            if (j < i) R[e] = 0.0;
-        }
-    }
-    __syncthreads();
-    // R^-1 row by row from the bottom: Rinv[i][j] = -(sum_{l=i+1..j} R[i][l] Rinv[l][j]) / R[i][i]
-    for (int e = tid; e < c * c; e += kCholThreads) Rinv[e] = 0.0;
-    __syncthreads();
-    for (int i = c - 1; i >= 0; --i) {
-        const double rii = R[i * c + i];
-        for (int j = i + tid; j < c; j += kCholThreads) {
-            double s = (j == i) ? 1.0 : 0.0;
-            for (int l = i + 1; l <= j; ++l) s -= R[i * c + l] * Rinv[l * c + j];
-            Rinv[i * c + j] = s / rii;
-        }
-        __syncthreads();
+    for (int e = tid; e < c * c; e += kCholThreads) {
+        const int i = e / c, j = e - i * c;
+        if (in_smem) R[e] = j >= i ? A[e] : 0.0;
+        else if (j < i) R[e] = 0.0;
     }
     if (tid == 0) *status = bad;
+}
+
+// Q = Y R^-1 for upper-triangular R (FP64, rounded to FP32): one warp per row
+// solves q R = y by forward substitution; lane l keeps the running sums of
+// columns l, l + 32, ...
+template <int NT>
+__global__ void __launch_bounds__(256) trsm_rows_kernel(const float *__restrict__ Y, int64_t n, int c, int64_t ldy,
+                                                        const double *__restrict__ R, float *__restrict__ Q,
+                                                        int64_t ldq) {
+    extern __shared__ float Rs[];   // c x c, row-major, plus the reciprocal diagonal
+    float *rdiag = Rs + c * c;
+    for (int e = threadIdx.x; e < c * c; e += blockDim.x) Rs[e] = (float)R[e];
+    for (int j = threadIdx.x; j < c; j += blockDim.x) rdiag[j] = (float)(1.0 / R[j * c + j]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        float y[NT], q[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int cc = lane + 32 * t;
+            y[t] = cc < c ? Y[i * ldy + cc] : 0.f;
+            q[t] = 0.f;
+        }
+        // column j: q_j = y_j * rdiag_j; then y_l -= q_j R[j][l] for l > j
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            for (int jj = 0; jj < 32; ++jj) {
+                const int j = 32 * t + jj;
+                if (j >= c) break;
+                const float qj = __shfl_sync(0xffffffffu, y[t], jj) * rdiag[j];
+                if (lane == jj) q[t] = qj;
+                const float *rj = Rs + j * c;
+#pragma unroll
+                for (int u = 0; u < NT; ++u) {
+                    const int l = lane + 32 * u;
+                    if (u >= t && l > j && l < c) y[u] = fmaf(-qj, rj[l], y[u]);
+                }
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+            const int cc = lane + 32 * t;
+            if (cc < c) Q[i * ldq + cc] = q[t];
+        }
+    }
 }
 
 // C = A B for upper-triangular c x c FP64 matrices (row i per CTA).
@@ -277,9 +307,16 @@ __global__ void __launch_bounds__(256) right_multiply_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// One-sided Jacobi SVD of a c x c FP64 matrix (c <= 160), one CTA. Columns are
-// paired by the circle method (m = c rounded up to even players, player 0
-// fixed); every round rotates m/2 disjoint column pairs, 8 threads per pair.
+// Small SVD of the c x c factor R (c <= 160), FP64-accurate:
+//   1. one-sided (Hestenes) Jacobi on R in FP32, one CTA, accumulating the
+//      right rotations V (columns paired by the circle method: m = c rounded up
+//      to even players, player 0 fixed, m/2 disjoint pairs per round, 8 threads
+//      per pair);
+//   2. Ogita-Aishima refinement of V as eigenvectors of G = R^T R in FP64
+//      (matrix products only, spread over many CTAs);
+//   3. sigma = sqrt(lambda), U_R = R V Sigma^-1, sorted by sigma descending.
+// FP64 rates on this GPU are a small fraction of FP32, so FP64 is used only
+// where the refinement needs it: its products.
 // ---------------------------------------------------------------------------
 constexpr int kJacTPP = 8;
 
@@ -287,29 +324,29 @@ __device__ __forceinline__ int circle_player(int pos, int round, int m) {
     return pos == 0 ? 0 : ((pos - 1 + round) % (m - 1)) + 1;
 }
 
-__global__ void jacobi_svd_kernel(const double *__restrict__ R, int c, double *__restrict__ UR,
-                                  double *__restrict__ sigma, int max_sweeps,
-                                  int *__restrict__ sweeps_out) {
-    extern __shared__ double A[];   // column-major: A[j * c + i]
-    __shared__ double red[32];
-    __shared__ double s_sig[kMaxSmemC + 1];
+__global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__restrict__ Vout, int max_sweeps,
+                                int *__restrict__ sweeps_out) {
+    extern __shared__ float js[];
+    float *A = js;            // column-major: A[j * c + i]
+    float *V = js + c * c;    // column-major
+    __shared__ float red[32];
     __shared__ int s_done;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthreads = blockDim.x;
     for (int e = tid; e < c * c; e += nthreads) {
         int i = e / c, j = e - i * c;
-        A[j * c + i] = R[e];
+        A[j * c + i] = (float)R[e];
+        V[j * c + i] = (i == j) ? 1.f : 0.f;
     }
     __syncthreads();
     const int m = c + (c & 1);
     const int pairs = m / 2;
     const int pi = tid / kJacTPP, sub = tid % kJacTPP;
-    const double tol = 1e-15;
+    const float tol = 2e-7f;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
-        double local_max = 0.0;
+        float local_max = 0.f;
         for (int round = 0; round < m - 1; ++round) {
-            // every lane takes part in the shuffles; lanes without a pair add zeros
             int p = 0, q = c;
             if (pi < pairs) {
                 p = circle_player(pi, round, m);
@@ -321,48 +358,51 @@ __global__ void jacobi_svd_kernel(const double *__restrict__ R, int c, double *_
                 }
             }
             const bool active = pi < pairs && q < c;
-            double al = 0.0, be = 0.0, ga = 0.0;
+            float al = 0.f, be = 0.f, ga = 0.f;
             if (active) {
-                const double *ap = A + p * c, *aq = A + q * c;
+                const float *ap = A + p * c, *aq = A + q * c;
                 for (int i = sub; i < c; i += kJacTPP) {
-                    double x = ap[i], y = aq[i];
-                    al = fma(x, x, al);
-                    be = fma(y, y, be);
-                    ga = fma(x, y, ga);
+                    float x = ap[i], y = aq[i];
+                    al = fmaf(x, x, al);
+                    be = fmaf(y, y, be);
+                    ga = fmaf(x, y, ga);
                 }
             }
+            // every lane takes part in the shuffles; lanes without a pair add zeros
 #pragma unroll
             for (int off = 1; off < kJacTPP; off <<= 1) {
                 al += __shfl_xor_sync(0xffffffffu, al, off);
                 be += __shfl_xor_sync(0xffffffffu, be, off);
                 ga += __shfl_xor_sync(0xffffffffu, ga, off);
             }
-            if (active && ga != 0.0 && al > 0.0 && be > 0.0) {
-                double rel = fabs(ga) / sqrt(al * be);
-                local_max = fmax(local_max, rel);
+            if (active && ga != 0.f && al > 0.f && be > 0.f) {
+                float rel = fabsf(ga) / sqrtf(al * be);
+                local_max = fmaxf(local_max, rel);
                 if (rel > tol) {
-                    double zeta = (be - al) / (2.0 * ga);
-                    double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    double cs = 1.0 / sqrt(1.0 + t * t);
-                    double sn = cs * t;
-                    double *ap = A + p * c, *aq = A + q * c;
+                    float zeta = (be - al) / (2.f * ga);
+                    float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                    float cs = rsqrtf(1.f + t * t);
+                    float sn = cs * t;
+                    float *ap = A + p * c, *aq = A + q * c, *vp = V + p * c, *vq = V + q * c;
                     for (int i = sub; i < c; i += kJacTPP) {
-                        double x = ap[i], y = aq[i];
+                        float x = ap[i], y = aq[i];
                         ap[i] = cs * x - sn * y;
                         aq[i] = sn * x + cs * y;
+                        float u = vp[i], w = vq[i];
+                        vp[i] = cs * u - sn * w;
+                        vq[i] = sn * u + cs * w;
                     }
                 }
             }
             __syncthreads();
         }
-        // block max of local_max
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) local_max = fmax(local_max, __shfl_xor_sync(0xffffffffu, local_max, off));
+        for (int off = 16; off > 0; off >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, off));
         if (lane == 0) red[warp] = local_max;
         __syncthreads();
         if (tid == 0) {
-            double mx = 0.0;
-            for (int w = 0; w < (nthreads + 31) / 32; ++w) mx = fmax(mx, red[w]);
+            float mx = 0.f;
+            for (int w = 0; w < (nthreads + 31) / 32; ++w) mx = fmaxf(mx, red[w]);
             s_done = mx <= tol;
         }
         __syncthreads();
@@ -371,22 +411,104 @@ __global__ void jacobi_svd_kernel(const double *__restrict__ R, int c, double *_
             break;
         }
     }
-    // singular values = column norms
-    for (int j = tid; j < c; j += nthreads) {
-        double s = 0.0;
-        for (int i = 0; i < c; ++i) s = fma(A[j * c + i], A[j * c + i], s);
-        s_sig[j] = sqrt(s);
+    for (int e = tid; e < c * c; e += nthreads) {
+        int i = e / c, j = e - i * c;
+        Vout[e] = (double)V[j * c + i];   // row-major, column j = j-th right vector
     }
+    if (tid == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+// C = op(A) op(B) (+ C0 if given), all c x c row-major FP64; 16 x 16 tile per CTA.
+__global__ void __launch_bounds__(256) dgemm_small_kernel(const double *__restrict__ A, int ta,
+                                                          const double *__restrict__ B, int tb,
+                                                          const double *__restrict__ C0,
+                                                          double *__restrict__ C, int c) {
+    __shared__ double As[16][17], Bs[16][17];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < c; k0 += 16) {
+        const int ka = k0 + tx;
+        As[ty][tx] = (row < c && ka < c) ? (ta ? A[ka * c + row] : A[row * c + ka]) : 0.0;
+        const int kb = k0 + ty;
+        Bs[ty][tx] = (kb < c && col < c) ? (tb ? B[col * c + kb] : B[kb * c + col]) : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc = fma(As[ty][k], Bs[k][tx], acc);
+        __syncthreads();
+    }
+    if (row < c && col < c) C[row * c + col] = C0 ? C0[row * c + col] + acc : acc;
+}
+
+__device__ double block_sum(double v, double *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
     __syncthreads();
-    for (int j = tid; j < c; j += nthreads) {
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) t += red[w];
+    return t;
+}
+
+// One Ogita-Aishima step (symmetric eigenvalue refinement, 2018): with
+// P = X^T X, Rr = I - P and S = X^T G X,  lambda_i = s_ii / (1 - r_ii),
+// delta = 2 (||S - diag(lambda)|| + ||G|| ||Rr||) (Frobenius norms bound the
+// 2-norms), E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) when
+// |lambda_i - lambda_j| > delta, else r_ij / 2; the update is X (I + E).
+__global__ void oa_update_kernel(const double *__restrict__ G, const double *__restrict__ S,
+                                 const double *__restrict__ P, int c, double *__restrict__ E,
+                                 double *__restrict__ lam) {
+    __shared__ double red[32];
+    __shared__ double s_lam[256];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < c; i += blockDim.x) s_lam[i] = S[i * c + i] / P[i * c + i];
+    __syncthreads();
+    double g2 = 0.0, r2 = 0.0, sd2 = 0.0;
+    for (int e = tid; e < c * c; e += blockDim.x) {
+        int i = e / c, j = e - i * c;
+        double gv = G[e];
+        double rv = (i == j ? 1.0 : 0.0) - P[e];
+        double sv = S[e] - (i == j ? s_lam[i] : 0.0);
+        g2 = fma(gv, gv, g2);
+        r2 = fma(rv, rv, r2);
+        sd2 = fma(sv, sv, sd2);
+    }
+    g2 = block_sum(g2, red);
+    r2 = block_sum(r2, red);
+    sd2 = block_sum(sd2, red);
+    const double delta = 2.0 * (sqrt(sd2) + sqrt(g2) * sqrt(r2));
+    for (int e = tid; e < c * c; e += blockDim.x) {
+        int i = e / c, j = e - i * c;
+        double rij = (i == j ? 1.0 : 0.0) - P[e];
+        double v;
+        if (i == j) {
+            v = 0.5 * rij;
+        } else {
+            double li = s_lam[i], lj = s_lam[j];
+            v = fabs(li - lj) > delta ? (S[e] + lj * rij) / (lj - li) : 0.5 * rij;
+        }
+        E[e] = v;
+    }
+    for (int i = tid; i < c; i += blockDim.x) lam[i] = s_lam[i];
+}
+
+// sigma sorted descending; U_R[:, rank_j] = T[:, j] / sigma_j with T = R X.
+__global__ void svd_finish_kernel(const double *__restrict__ T, const double *__restrict__ lam, int c,
+                                  double *__restrict__ UR, double *__restrict__ sigma) {
+    __shared__ double s_sig[256];
+    const int tid = threadIdx.x;
+    for (int j = tid; j < c; j += blockDim.x) s_sig[j] = sqrt(fmax(lam[j], 0.0));
+    __syncthreads();
+    for (int j = tid; j < c; j += blockDim.x) {
         const double sj = s_sig[j];
         int rank = 0;
         for (int i = 0; i < c; ++i) rank += (s_sig[i] > sj) || (s_sig[i] == sj && i < j);
         sigma[rank] = sj;
         const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
-        for (int i = 0; i < c; ++i) UR[i * c + rank] = A[j * c + i] * inv;
+        for (int i = 0; i < c; ++i) UR[i * c + rank] = T[i * c + j] * inv;
     }
-    if (tid == 0 && sweeps_out) *sweeps_out = sweep;
 }
 
 // ---------------------------------------------------------------------------
@@ -493,15 +615,15 @@ static int gram(Workspace &ws, const float *Y, int64_t n, int c, int64_t ld, dou
     return 0;
 }
 
-static int chol_inv(Workspace &ws, const double *G, int c, double *R, double *Rinv, cudaStream_t st) {
+static int chol(Workspace &ws, const double *G, int c, double *R, cudaStream_t st) {
     int *status = nullptr;
     LNE_TRY(ws.get("chol.status", 1, &status));
     const int smem = c <= kMaxSmemC ? c * c * 8 : 0;
     if (smem > 48 * 1024)
-        LNE_CUDA_TRY(cudaFuncSetAttribute(chol_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        LNE_CUDA_TRY(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     {
-        LNE_TRACE("chol_inv", st);
-        chol_inv_kernel<<<1, kCholThreads, smem, st>>>(G, c, R, Rinv, status);
+        LNE_TRACE("chol", st);
+        chol_kernel<<<1, kCholThreads, smem, st>>>(G, c, R, status);
         LNE_LAUNCH_CHECK();
     }
     int h = 0;
@@ -511,47 +633,126 @@ static int chol_inv(Workspace &ws, const double *G, int c, double *R, double *Ri
     return 0;
 }
 
+static int trsm_rows(const float *Y, int64_t n, int c, int64_t ldy, const double *R, float *Q, int64_t ldq,
+                     cudaStream_t st) {
+    const int nt = (c + 31) / 32;
+    const int smem = (c * c + c) * 4;
+    const int blocks = (int)std::min<int64_t>(ceil_div(n, 8), 152 * 8);
+    LNE_TRACE("trsm_rows", st);
+#define LNE_TRSM_CASE(K)                                                                               \
+    case K:                                                                                            \
+        if (smem > 48 * 1024)                                                                          \
+            LNE_CUDA_TRY(cudaFuncSetAttribute(trsm_rows_kernel<K>,                                     \
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem));     \
+        trsm_rows_kernel<K><<<blocks, 256, smem, st>>>(Y, n, c, ldy, R, Q, ldq);                      \
+        break;
+    switch (nt) {
+        LNE_TRSM_CASE(1)
+        LNE_TRSM_CASE(2)
+        LNE_TRSM_CASE(3)
+        LNE_TRSM_CASE(4)
+        LNE_TRSM_CASE(5)
+        LNE_TRSM_CASE(6)
+        LNE_TRSM_CASE(7)
+        LNE_TRSM_CASE(8)
+        default:
+            return fail(LNE_ERR_UNSUPPORTED, "CholeskyQR supports at most 256 columns");
+    }
+#undef LNE_TRSM_CASE
+    LNE_LAUNCH_CHECK();
+    return 0;
+}
+
 int cholqr2(Workspace &ws, float *Y, int64_t n, int c, int64_t ld, double *Rout, cudaStream_t st) {
     if (c <= 0 || c > 256) return fail(LNE_ERR_INVALID, "CholeskyQR2 needs 1 <= c <= 256");
     if (n < c) return fail(LNE_ERR_INVALID, "CholeskyQR2 needs at least as many rows as columns");
-    double *G = nullptr, *R1 = nullptr, *R1i = nullptr, *R2 = nullptr, *R2i = nullptr;
+    if ((size_t)(c * c + c) * 4 > 227 * 1024) return fail(LNE_ERR_UNSUPPORTED, "CholeskyQR2 column count too large");
+    double *G = nullptr, *R1 = nullptr, *R2 = nullptr;
     float *tmp = nullptr;
     LNE_TRY(ws.get("qr.G", (size_t)c * c, &G));
     LNE_TRY(ws.get("qr.R1", (size_t)c * c, &R1));
-    LNE_TRY(ws.get("qr.R1i", (size_t)c * c, &R1i));
     LNE_TRY(ws.get("qr.R2", (size_t)c * c, &R2));
-    LNE_TRY(ws.get("qr.R2i", (size_t)c * c, &R2i));
     LNE_TRY(ws.get("qr.tmp", (size_t)n * c, &tmp));
-    // pass 1
+    // pass 1: G = Y^T Y, R1 = chol(G), Q1 = Y R1^-1
     LNE_TRY(gram(ws, Y, n, c, ld, G, st));
-    LNE_TRY(chol_inv(ws, G, c, R1, R1i, st));
-    LNE_TRY(right_multiply(Y, n, c, ld, R1i, c, c, nullptr, tmp, c, st));
-    // pass 2
+    LNE_TRY(chol(ws, G, c, R1, st));
+    LNE_TRY(trsm_rows(Y, n, c, ld, R1, tmp, c, st));
+    // pass 2 on Q1
     LNE_TRY(gram(ws, tmp, n, c, c, G, st));
-    LNE_TRY(chol_inv(ws, G, c, R2, R2i, st));
-    LNE_TRY(right_multiply(tmp, n, c, c, R2i, c, c, nullptr, Y, ld, st));
+    LNE_TRY(chol(ws, G, c, R2, st));
+    LNE_TRY(trsm_rows(tmp, n, c, c, R2, Y, ld, st));
     if (Rout) {
-        {
-            LNE_TRACE("upper_matmul", st);
-            upper_matmul_kernel<<<c, 128, 0, st>>>(R2, R1, c, Rout);
-            LNE_LAUNCH_CHECK();
-        }
+        LNE_TRACE("upper_matmul", st);
+        upper_matmul_kernel<<<c, 128, 0, st>>>(R2, R1, c, Rout);
+        LNE_LAUNCH_CHECK();
     }
+    return 0;
+}
+
+static int dgemm_small(const double *A, bool ta, const double *B, bool tb, const double *C0, double *C, int c,
+                       cudaStream_t st) {
+    dim3 grid((unsigned)ceil_div(c, 16), (unsigned)ceil_div(c, 16));
+    LNE_TRACE("dgemm_small", st);
+    dgemm_small_kernel<<<grid, 256, 0, st>>>(A, ta ? 1 : 0, B, tb ? 1 : 0, C0, C, c);
+    LNE_LAUNCH_CHECK();
     return 0;
 }
 
 int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma, cudaStream_t st) {
     if (c > kMaxSmemC) return fail(LNE_ERR_UNSUPPORTED, "small SVD supports c <= 160");
+    double *G = nullptr, *X = nullptr, *X2 = nullptr, *W = nullptr, *S = nullptr, *P = nullptr, *E = nullptr,
+           *lam = nullptr;
     int *sweeps = nullptr;
+    const size_t cc = (size_t)c * c;
+    LNE_TRY(ws.get("svd.G", cc, &G));
+    LNE_TRY(ws.get("svd.X", cc, &X));
+    LNE_TRY(ws.get("svd.X2", cc, &X2));
+    LNE_TRY(ws.get("svd.W", cc, &W));
+    LNE_TRY(ws.get("svd.S", cc, &S));
+    LNE_TRY(ws.get("svd.P", cc, &P));
+    LNE_TRY(ws.get("svd.E", cc, &E));
+    LNE_TRY(ws.get("svd.lam", (size_t)c, &lam));
     LNE_TRY(ws.get("svd.sweeps", 1, &sweeps));
+    // G = R^T R in FP64
+    LNE_TRY(dgemm_small(R, true, R, false, nullptr, G, c, st));
+    // starting vectors: FP32 one-sided Jacobi on R
     const int m = c + (c & 1);
     const int threads = std::max(32, std::min(1024, (m / 2 * kJacTPP + 31) / 32 * 32));
-    const int smem = c * c * 8;
+    const int smem = 2 * c * c * 4;
     if (smem > 48 * 1024)
-        LNE_CUDA_TRY(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        LNE_CUDA_TRY(cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     {
-        LNE_TRACE("jacobi_svd", st);
-        jacobi_svd_kernel<<<1, threads, smem, st>>>(R, c, U_R, sigma, 60, sweeps);
+        LNE_TRACE("jacobi32", st);
+        jacobi32_kernel<<<1, threads, smem, st>>>(R, c, X, 40, sweeps);
+        LNE_LAUNCH_CHECK();
+    }
+    // FP64 refinement
+    for (int it = 0; it < 3; ++it) {
+        LNE_TRY(dgemm_small(G, false, X, false, nullptr, W, c, st));   // W = G X
+        LNE_TRY(dgemm_small(X, true, W, false, nullptr, S, c, st));    // S = X^T G X
+        LNE_TRY(dgemm_small(X, true, X, false, nullptr, P, c, st));    // P = X^T X
+        {
+            LNE_TRACE("oa_update", st);
+            oa_update_kernel<<<1, 256, 0, st>>>(G, S, P, c, E, lam);
+            LNE_LAUNCH_CHECK();
+        }
+        LNE_TRY(dgemm_small(X, false, E, false, X, X2, c, st));        // X2 = X + X E
+        std::swap(X, X2);
+    }
+    // Rayleigh quotients of the refined vectors
+    LNE_TRY(dgemm_small(G, false, X, false, nullptr, W, c, st));
+    LNE_TRY(dgemm_small(X, true, W, false, nullptr, S, c, st));
+    LNE_TRY(dgemm_small(X, true, X, false, nullptr, P, c, st));
+    {
+        LNE_TRACE("oa_update", st);
+        oa_update_kernel<<<1, 256, 0, st>>>(G, S, P, c, E, lam);
+        LNE_LAUNCH_CHECK();
+    }
+    // U_R = R X Sigma^-1, sorted
+    LNE_TRY(dgemm_small(R, false, X, false, nullptr, W, c, st));
+    {
+        LNE_TRACE("svd_finish", st);
+        svd_finish_kernel<<<1, 256, 0, st>>>(W, lam, c, U_R, sigma);
         LNE_LAUNCH_CHECK();
     }
     return 0;

@@ -60,6 +60,8 @@ struct SamplerSpec {
     uint64_t thr[16] = {0};       // thr_1..thr_{T-1}
     int B = 1;                    // bits per endpoint in a pair key
     double alpha_off = 0, alpha_diag = 0;
+    float off_hi = 0, off_lo = 0, diag_hi = 0, diag_lo = 0;   // alpha as float pairs
+    int aggregation = 0;          // LNE_AGG_* (0 = automatic)
 };
 
 int make_sampler_spec(const GraphView &g, int T, const double *s, double S, double b, uint64_t seed,

@@ -16,8 +16,15 @@
 //                      key order with their exact counts -- the integer
 //                      aggregation the paper does with a concurrent hash table.
 //   5. trunclog        Eq. 1 value v = K alpha / (d_x d_y), kept iff v > 1 (an
-//                      exact FP64 decision), log(v) as float32.
+//                      exact decision), log(v) as float32.
 //   6. csr_fill/sort   symmetric CSR of the kept entries, rows sorted.
+//
+// For graphs whose pair space fits a dense table (n <= 65536) the counting is
+// direct instead: the walk adds each sample into an n x n table of counters
+// (upper triangle, fire-and-forget atomics), one pass turns counts into Eq. 1
+// values in place, and 64 x 64 tiles of the symmetric matrix (the lower half
+// read through a shared-memory transpose) give row counts and then the CSR in
+// column order -- no key buffers, no sort.
 //
 // Every integer result (counts, keep decisions, CSR structure) is independent of
 // scheduling, so it equals the CPU oracle bit for bit.
@@ -178,7 +185,8 @@ __global__ void __launch_bounds__(kWalkThreads) tile_counts_kernel(WalkArgs A, i
 }
 
 // MODE 0: write ordered endpoint pairs (u1, v1). MODE 1: write canonical keys
-// and count key buckets.
+// and count key buckets. MODE 2: add the pair into the dense count table
+// table[x * ld + y] (x <= y); `keys` is the table, ld = nb_smem.
 template <typename KeyT, int MODE>
 __global__ void __launch_bounds__(kWalkThreads) walk_emit_kernel(
     WalkArgs A, int64_t a_begin, int64_t a_end, int tile_arcs, const int64_t *__restrict__ tile_off,
@@ -192,7 +200,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_emit_kernel(
     const int tid = threadIdx.x;
     const int64_t a0 = a_begin + (int64_t)blockIdx.x * tile_arcs;
     const int na = (int)imin64(tile_arcs, a_end - a0);
-    if (MODE == 1)
+    if (MODE == 1 && nb_smem > 0)
         for (int i = tid; i < nb_smem; i += kWalkThreads) s_hist[i] = 0;
     for (int i = tid; i < na; i += kWalkThreads) {
         s_off[i] = arc_count(A, a0 + i);
@@ -203,7 +211,7 @@ __global__ void __launch_bounds__(kWalkThreads) walk_emit_kernel(
     const uint32_t total = block_exclusive_scan<kWalkThreads>(s_off, na);
     if (tid == 0) s_off[na] = total;
     __syncthreads();
-    const int64_t out0 = tile_off[blockIdx.x];
+    const int64_t out0 = tile_off ? tile_off[blockIdx.x] : 0;
     for (uint32_t s = tid; s < total; s += kWalkThreads) {
         int lo = 0, hi = na;   // s_off[lo] <= s < s_off[hi]
         while (hi - lo > 1) {
@@ -216,6 +224,9 @@ __global__ void __launch_bounds__(kWalkThreads) walk_emit_kernel(
         if (MODE == 0) {
             u1[out0 + s] = pu;
             v1[out0 + s] = pv;
+        } else if (MODE == 2) {
+            const uint32_t x = (uint32_t)min(pu, pv), y = (uint32_t)max(pu, pv);
+            atomicAdd(reinterpret_cast<uint32_t *>(keys) + (size_t)x * (uint32_t)nb_smem + y, 1u);
         } else {
             const uint32_t x = (uint32_t)min(pu, pv), y = (uint32_t)max(pu, pv);
             const KeyT key = ((KeyT)x << A.B) | (KeyT)y;
@@ -361,37 +372,56 @@ __global__ void compact_kernel(const KeyT *__restrict__ rkey, const uint32_t *__
     }
 }
 
-// Eq. 1 with the truncated log. The keep decision fl(fl(K alpha) / q) > 1 is
-// evaluated without a division: with p = fl(K alpha) and q = d_x d_y, a
-// correctly rounded quotient exceeds 1 iff p / q > 1 + 2^-53, i.e. iff p >= 2q
-// or (q < p and (p - q) 2^53 > q); p - q is exact there (Sterbenz).
+struct NetmfConst {
+    double a_off, a_diag;              // alpha = vol^2 / (2 S b), vol^2 / (S b)
+    float off_hi, off_lo, diag_hi, diag_lo;
+};
+
+// Eq. 1 entry with the truncated log for count K of pair (x, y):
+// v = fl(fl(K alpha) / fl(d_x d_y)), kept iff v > 1, value log(v) as float32
+// (0 means dropped; log v > 0 for every kept entry).
+// Fast path: D = K alpha - q (q = d_x d_y) in FP32 with alpha split into a
+// float pair; fmaf makes the product exact, so D carries a relative error of
+// ~1e-7. Whenever |D| > 1e-5 q its sign is the FP64 decision and
+// log1p(D / q) is accurate to a few ulp. Otherwise (v within 1e-5 of 1, or
+// operands beyond 2^24) the exact FP64 rule decides: a correctly rounded
+// quotient exceeds 1 iff p >= 2q or (p > q and (p - q) 2^53 > q), with p - q
+// exact there (Sterbenz), so no division is needed.
+__device__ __forceinline__ float netmf_value(uint32_t cnt, int64_t dx, int64_t dy, bool diag,
+                                             const NetmfConst &k) {
+    const int64_t q64 = dx * dy;
+    if (cnt < (1u << 24) && q64 < (1ll << 24)) {
+        const float cf = (float)cnt, qf = (float)q64;
+        const float hi = diag ? k.diag_hi : k.off_hi, lo = diag ? k.diag_lo : k.off_lo;
+        const float dq = fmaf(cf, hi, -qf) + cf * lo;
+        if (fabsf(dq) > 1e-5f * qf) return dq > 0.f ? log1pf(__fdiv_rn(dq, qf)) : 0.f;
+    }
+    const double p = __dmul_rn((double)cnt, diag ? k.a_diag : k.a_off);
+    const double q = __ll2double_rn(q64);
+    if (!(p > q)) return 0.f;
+    const double q2 = __dmul_rn(2.0, q);
+    if (p < q2) {
+        const double dd = __dsub_rn(p, q);
+        if (!(__dmul_rn(dd, 9007199254740992.0) > q)) return 0.f;
+        return log1pf(__fdiv_rn((float)dd, (float)q));
+    }
+    if (p < 1e30) return logf(__fdiv_rn((float)p, (float)q));
+    return (float)(log(p) - log(q));
+}
+
 __global__ void trunclog_kernel(const int32_t *__restrict__ x, const int32_t *__restrict__ y,
                                 const uint32_t *__restrict__ cnt, int64_t nnz,
-                                const int64_t *__restrict__ indptr, double alpha_off,
-                                double alpha_diag, float *__restrict__ val,
-                                uint8_t *__restrict__ keep, uint32_t *__restrict__ rowcnt) {
+                                const int64_t *__restrict__ indptr, NetmfConst kc,
+                                float *__restrict__ val, uint8_t *__restrict__ keep,
+                                uint32_t *__restrict__ rowcnt) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t xi = x[i], yi = y[i];
         const int64_t dx = __ldg(indptr + xi + 1) - __ldg(indptr + xi);
         const int64_t dy = __ldg(indptr + yi + 1) - __ldg(indptr + yi);
-        const double alpha = xi == yi ? alpha_diag : alpha_off;
-        const double p = __dmul_rn((double)cnt[i], alpha);
-        const double q = __ll2double_rn(dx * dy);
-        bool k = false;
-        if (p > q) {
-            if (p >= __dmul_rn(2.0, q)) k = true;
-            else k = __dmul_rn(__dsub_rn(p, q), 9007199254740992.0) > q;
-        }
-        float v = 0.f;
+        const float v = netmf_value(cnt[i], dx, dy, xi == yi, kc);
+        const bool k = v > 0.f;
         if (k) {
-            if (p < __dmul_rn(2.0, q)) {
-                v = log1pf(__fdiv_rn((float)__dsub_rn(p, q), (float)q));
-            } else if (p < 1e30) {
-                v = logf(__fdiv_rn((float)p, (float)q));
-            } else {
-                v = (float)(log(p) - log(q));
-            }
             atomicAdd(&rowcnt[xi], 1u);
             if (xi != yi) atomicAdd(&rowcnt[yi], 1u);
         }
@@ -470,6 +500,178 @@ __global__ void __launch_bounds__(kSortThreads) csr_row_sort_kernel(const int64_
     }
 }
 
+// ---------------------------------------------------------------------------
+// dense-table aggregation (n <= 65536)
+// ---------------------------------------------------------------------------
+constexpr int kTile = 64;
+
+// Counts -> Eq. 1 values in place (float bits; 0 = not kept). One CTA per row
+// x of the upper triangle (y >= x).
+__global__ void table_values_kernel(uint32_t *__restrict__ T, int64_t ld, int n,
+                                    const int64_t *__restrict__ indptr, NetmfConst kc) {
+    const int x = blockIdx.x;
+    const int64_t dx = __ldg(indptr + x + 1) - __ldg(indptr + x);
+    uint32_t *row = T + (size_t)x * ld;
+    for (int y = x + threadIdx.x; y < n; y += blockDim.x) {
+        const uint32_t c = row[y];
+        if (c == 0) continue;
+        const int64_t dy = __ldg(indptr + y + 1) - __ldg(indptr + y);
+        row[y] = __float_as_uint(netmf_value(c, dx, dy, x == y, kc));
+    }
+}
+
+// Distinct pairs per upper-triangle row (for the counts output).
+__global__ void table_row_nnz_kernel(const uint32_t *__restrict__ T, int64_t ld, int n,
+                                     uint32_t *__restrict__ cnt) {
+    __shared__ uint32_t red[32];
+    const int x = blockIdx.x;
+    const uint32_t *row = T + (size_t)x * ld;
+    uint32_t c = 0;
+    for (int y = x + threadIdx.x; y < n; y += blockDim.x) c += row[y] != 0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < (int)blockDim.x / 32; ++w) t += red[w];
+        cnt[x] = t;
+    }
+}
+
+// (x, y, count) of the upper triangle in (x, y) order: one CTA per row, the
+// row is walked in chunks of blockDim with a block-wide ballot scan.
+__global__ void table_compact_kernel(const uint32_t *__restrict__ T, int64_t ld, int n,
+                                     const int64_t *__restrict__ off, int32_t *__restrict__ ox,
+                                     int32_t *__restrict__ oy, uint32_t *__restrict__ oc) {
+    __shared__ uint32_t warp_cnt[32];
+    __shared__ uint32_t base_s;
+    const int x = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const uint32_t *row = T + (size_t)x * ld;
+    if (threadIdx.x == 0) base_s = 0;
+    __syncthreads();
+    const int64_t o = off[x];
+    for (int y0 = x; y0 < n; y0 += blockDim.x) {
+        const int y = y0 + threadIdx.x;
+        const uint32_t c = y < n ? row[y] : 0u;
+        const unsigned bal = __ballot_sync(0xffffffffu, c != 0);
+        if (lane == 0) warp_cnt[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t before = base_s;
+        for (int w = 0; w < warp; ++w) before += warp_cnt[w];
+        if (c != 0) {
+            const int64_t pos = o + before + __popc(bal & ((1u << lane) - 1u));
+            ox[pos] = x;
+            oy[pos] = y;
+            oc[pos] = c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < nw; ++w) t += warp_cnt[w];
+            base_s += t;
+        }
+        __syncthreads();
+    }
+}
+
+// Loads the 64 x 64 tile (bx, by) of the symmetric value matrix into S
+// (S[i][j] = M[bx*64 + i][by*64 + j]); the table holds the upper triangle.
+__device__ __forceinline__ void load_sym_tile(const uint32_t *__restrict__ T, int64_t ld, int bx, int by,
+                                              uint32_t (*S)[kTile + 1]) {
+    if (bx < by) {
+        const uint32_t *base = T + (size_t)bx * kTile * ld + (size_t)by * kTile;
+        for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+            const int i = e / kTile, j = e % kTile;
+            S[i][j] = base[(size_t)i * ld + j];
+        }
+    } else if (bx > by) {
+        const uint32_t *base = T + (size_t)by * kTile * ld + (size_t)bx * kTile;
+        for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+            const int i = e / kTile, j = e % kTile;
+            S[j][i] = base[(size_t)i * ld + j];
+        }
+    } else {
+        const uint32_t *base = T + (size_t)bx * kTile * ld + (size_t)by * kTile;
+        for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
+            const int i = e / kTile, j = e % kTile;
+            S[i][j] = base[(size_t)min(i, j) * ld + max(i, j)];
+        }
+    }
+}
+
+// Kept entries per (row, column tile) of the symmetric matrix.
+__global__ void __launch_bounds__(256) tile_count_kernel(const uint32_t *__restrict__ T, int64_t ld, int n, int nt,
+                                                         uint32_t *__restrict__ rowtile) {
+    __shared__ uint32_t S[kTile][kTile + 1];
+    const int bx = blockIdx.y, by = blockIdx.x;
+    load_sym_tile(T, ld, bx, by, S);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < kTile; i += 8) {
+        const int r = bx * kTile + i;
+        if (r >= n) break;
+        const unsigned b0 = __ballot_sync(0xffffffffu, S[i][lane] != 0u);
+        const unsigned b1 = __ballot_sync(0xffffffffu, S[i][lane + 32] != 0u);
+        if (lane == 0) rowtile[(size_t)r * nt + by] = __popc(b0) + __popc(b1);
+    }
+}
+
+// Per row: exclusive scan of its tile counts (in place) and the row total.
+__global__ void row_tile_scan_kernel(uint32_t *__restrict__ rowtile, int n, int nt,
+                                     uint32_t *__restrict__ rowcnt) {
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= n) return;
+    uint32_t *rt = rowtile + (size_t)r * nt;
+    uint32_t carry = 0;
+    for (int t0 = 0; t0 < nt; t0 += 32) {
+        const int t = t0 + lane;
+        const uint32_t v = t < nt ? rt[t] : 0u;
+        uint32_t x = v;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (t < nt) rt[t] = carry + x - v;
+        carry += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) rowcnt[r] = carry;
+}
+
+// Writes every kept entry of the tile at its sorted position in the CSR.
+__global__ void __launch_bounds__(256) tile_fill_kernel(const uint32_t *__restrict__ T, int64_t ld, int n, int nt,
+                                                        const uint32_t *__restrict__ rowtile,
+                                                        const int64_t *__restrict__ indptr,
+                                                        int32_t *__restrict__ col, float *__restrict__ data) {
+    __shared__ uint32_t S[kTile][kTile + 1];
+    const int bx = blockIdx.y, by = blockIdx.x;
+    load_sym_tile(T, ld, bx, by, S);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < kTile; i += 8) {
+        const int r = bx * kTile + i;
+        if (r >= n) break;
+        const int64_t base = indptr[r] + rowtile[(size_t)r * nt + by];
+        const uint32_t v0 = S[i][lane], v1 = S[i][lane + 32];
+        const unsigned b0 = __ballot_sync(0xffffffffu, v0 != 0u);
+        const unsigned b1 = __ballot_sync(0xffffffffu, v1 != 0u);
+        const unsigned below = (1u << lane) - 1u;
+        if (v0) {
+            const int64_t pos = base + __popc(b0 & below);
+            col[pos] = by * kTile + lane;
+            data[pos] = __uint_as_float(v0);
+        }
+        if (v1) {
+            const int64_t pos = base + __popc(b0) + __popc(b1 & below);
+            col[pos] = by * kTile + 32 + lane;
+            data[pos] = __uint_as_float(v1);
+        }
+    }
+}
+
 WalkArgs make_walk_args(const GraphView &g, const SamplerSpec &sp) {
     WalkArgs A;
     A.indptr = g.indptr;
@@ -497,6 +699,17 @@ int choose_tile_arcs(int64_t n_arcs, double rate) {
     if (t < 1) t = 1;
     if (t > 4096) t = 4096;
     return (int)t;
+}
+
+NetmfConst netmf_const(const SamplerSpec &sp) {
+    NetmfConst k;
+    k.a_off = sp.alpha_off;
+    k.a_diag = sp.alpha_diag;
+    k.off_hi = sp.off_hi;
+    k.off_lo = sp.off_lo;
+    k.diag_hi = sp.diag_hi;
+    k.diag_lo = sp.diag_lo;
+    return k;
 }
 
 int walk_smem_bytes(int tile_arcs, int nb_smem) {
@@ -560,6 +773,10 @@ int make_sampler_spec(const GraphView &g, int T, const double *s, double S, doub
     const double vv = vol * vol;
     sp.alpha_off = vv / ((2.0 * S) * b);
     sp.alpha_diag = vv / (S * b);
+    sp.off_hi = (float)sp.alpha_off;
+    sp.off_lo = (float)(sp.alpha_off - (double)sp.off_hi);
+    sp.diag_hi = (float)sp.alpha_diag;
+    sp.diag_lo = (float)(sp.alpha_diag - (double)sp.diag_hi);
     *out = sp;
     return 0;
 }
@@ -695,8 +912,8 @@ int compact_counts(Workspace &ws, const SamplerSpec &sp, const Reduced &R, Count
 
 }  // namespace
 
-int sparsifier_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out,
-                      cudaStream_t st) {
+int bucket_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out,
+                  cudaStream_t st) {
     Reduced R;
     LNE_TRY(sample_and_reduce(ws, g, sp, &R, st));
     LNE_TRY(compact_counts(ws, sp, R, out, st));
@@ -704,8 +921,8 @@ int sparsifier_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
     return 0;
 }
 
-int sparsifier_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out,
-                   cudaStream_t st) {
+int bucket_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out,
+               cudaStream_t st) {
     Reduced R;
     LNE_TRY(sample_and_reduce(ws, g, sp, &R, st));
     CountsResult C;
@@ -722,8 +939,8 @@ int sparsifier_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Csr
     const int grid = (int)std::min<int64_t>(ceil_div(std::max<int64_t>(nnz_c, 1), 256), 152 * 16);
     {
         LNE_TRACE("trunclog", st);
-        trunclog_kernel<<<grid, 256, 0, st>>>(C.x, C.y, C.cnt, nnz_c, g.indptr, sp.alpha_off,
-                                              sp.alpha_diag, val, keep, rowcnt);
+        trunclog_kernel<<<grid, 256, 0, st>>>(C.x, C.y, C.cnt, nnz_c, g.indptr, netmf_const(sp), val, keep,
+                                              rowcnt);
         LNE_LAUNCH_CHECK();
     }
     LNE_TRY(scan_exclusive_u32_to_i64(rowcnt, out->indptr, g.n, st));
@@ -758,6 +975,134 @@ int sparsifier_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Csr
     out->n = g.n;
     out->nnz = nnz;
     return 0;
+}
+
+
+namespace {
+
+struct Table {
+    uint32_t *T = nullptr;
+    int64_t ld = 0;
+    int nt = 0;
+};
+
+bool use_table(const GraphView &g, const SamplerSpec &sp) {
+    if (sp.aggregation == LNE_AGG_TABLE) return true;
+    if (sp.aggregation == LNE_AGG_BUCKET) return false;
+    return g.n <= 65536;
+}
+
+// Walk every arc's samples and count them into the dense upper-triangle table.
+int sample_table(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Table *tb, cudaStream_t st) {
+    if (g.n > 65536) return fail(LNE_ERR_UNSUPPORTED, "the dense count table needs n <= 65536");
+    const int nt = (int)ceil_div(g.n, kTile);
+    const int64_t ld = (int64_t)nt * kTile;
+    LNE_TRY(ws.get("table.T", (size_t)(ld * ld), &tb->T));
+    tb->ld = ld;
+    tb->nt = nt;
+    LNE_CUDA_TRY(cudaMemsetAsync(tb->T, 0, sizeof(uint32_t) * (size_t)(ld * ld), st));
+    WalkArgs A = make_walk_args(g, sp);
+    const int tile_arcs = choose_tile_arcs(g.nnz, (double)sp.base + 0.5);
+    const int64_t ntiles = ceil_div(g.nnz, tile_arcs);
+    const int smem = walk_smem_bytes(tile_arcs, 0);
+    LNE_CUDA_TRY(cudaFuncSetAttribute(walk_emit_kernel<uint32_t, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      std::max(smem, 48 * 1024)));
+    LNE_TRACE("walk_count", st);
+    walk_emit_kernel<uint32_t, 2><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
+        A, 0, g.nnz, tile_arcs, nullptr, tb->T, nullptr, nullptr, nullptr, (int)ld);
+    LNE_LAUNCH_CHECK();
+    return 0;
+}
+
+int total_samples(Workspace &ws, const GraphView &g, const SamplerSpec &sp, int64_t *total, cudaStream_t st) {
+    WalkArgs A = make_walk_args(g, sp);
+    const int tile_arcs = choose_tile_arcs(g.nnz, (double)sp.base + 0.5);
+    int64_t *tile_off = nullptr;
+    return tile_offsets(ws, A, 0, g.nnz, tile_arcs, &tile_off, total, st);
+}
+
+int table_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out, cudaStream_t st) {
+    Table tb;
+    LNE_TRY(sample_table(ws, g, sp, &tb, st));
+    uint32_t *rc = nullptr;
+    int64_t *off = nullptr;
+    LNE_TRY(ws.get("table.rownnz", (size_t)g.n, &rc));
+    LNE_TRY(ws.get("table.rowoff", (size_t)g.n + 1, &off));
+    {
+        LNE_TRACE("table_row_nnz", st);
+        table_row_nnz_kernel<<<(unsigned)g.n, 256, 0, st>>>(tb.T, tb.ld, (int)g.n, rc);
+        LNE_LAUNCH_CHECK();
+    }
+    LNE_TRY(scan_exclusive_u32_to_i64(rc, off, g.n, st));
+    int64_t nnz = 0;
+    LNE_CUDA_TRY(cudaMemcpyAsync(&nnz, off + g.n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    LNE_TRY(ws.get("counts.x", (size_t)std::max<int64_t>(nnz, 1), &out->x));
+    LNE_TRY(ws.get("counts.y", (size_t)std::max<int64_t>(nnz, 1), &out->y));
+    LNE_TRY(ws.get("counts.cnt", (size_t)std::max<int64_t>(nnz, 1), &out->cnt));
+    {
+        LNE_TRACE("table_compact", st);
+        table_compact_kernel<<<(unsigned)g.n, 256, 0, st>>>(tb.T, tb.ld, (int)g.n, off, out->x, out->y, out->cnt);
+        LNE_LAUNCH_CHECK();
+    }
+    out->nnz = nnz;
+    LNE_TRY(total_samples(ws, g, sp, &out->total_samples, st));
+    return 0;
+}
+
+int table_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out, cudaStream_t st) {
+    Table tb;
+    LNE_TRY(sample_table(ws, g, sp, &tb, st));
+    const int n = (int)g.n;
+    {
+        LNE_TRACE("table_values", st);
+        table_values_kernel<<<(unsigned)n, 256, 0, st>>>(tb.T, tb.ld, n, g.indptr, netmf_const(sp));
+        LNE_LAUNCH_CHECK();
+    }
+    uint32_t *rowtile = nullptr, *rowcnt = nullptr;
+    LNE_TRY(ws.get("table.rowtile", (size_t)n * tb.nt, &rowtile));
+    LNE_TRY(ws.get("table.rowcnt", (size_t)n, &rowcnt));
+    LNE_TRY(ws.get("csr.indptr", (size_t)n + 1, &out->indptr));
+    dim3 grid((unsigned)tb.nt, (unsigned)tb.nt);
+    {
+        LNE_TRACE("tile_count", st);
+        tile_count_kernel<<<grid, 256, 0, st>>>(tb.T, tb.ld, n, tb.nt, rowtile);
+        LNE_LAUNCH_CHECK();
+    }
+    {
+        LNE_TRACE("row_tile_scan", st);
+        row_tile_scan_kernel<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(rowtile, n, tb.nt, rowcnt);
+        LNE_LAUNCH_CHECK();
+    }
+    LNE_TRY(scan_exclusive_u32_to_i64(rowcnt, out->indptr, n, st));
+    int64_t nnz = 0;
+    LNE_CUDA_TRY(cudaMemcpyAsync(&nnz, out->indptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    LNE_TRY(ws.get("csr.indices", (size_t)std::max<int64_t>(nnz, 1), &out->indices));
+    LNE_TRY(ws.get("csr.data", (size_t)std::max<int64_t>(nnz, 1), &out->data));
+    {
+        LNE_TRACE("tile_fill", st);
+        tile_fill_kernel<<<grid, 256, 0, st>>>(tb.T, tb.ld, n, tb.nt, rowtile, out->indptr, out->indices, out->data);
+        LNE_LAUNCH_CHECK();
+    }
+    out->n = g.n;
+    out->nnz = nnz;
+    return 0;
+}
+
+}  // namespace
+
+int sparsifier_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out,
+                      cudaStream_t st) {
+    if (use_table(g, sp)) LNE_TRY(table_counts(ws, g, sp, out, st));
+    else LNE_TRY(bucket_counts(ws, g, sp, out, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    return 0;
+}
+
+int sparsifier_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out, cudaStream_t st) {
+    if (use_table(g, sp)) return table_csr(ws, g, sp, out, st);
+    return bucket_csr(ws, g, sp, out, st);
 }
 
 }  // namespace lne

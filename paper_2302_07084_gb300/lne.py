@@ -27,8 +27,11 @@ EXPORTED = [
     "lne_create", "lne_destroy", "lne_last_error", "lne_workspace_bytes", "lne_trim",
     "lne_sample_pairs", "lne_sparsifier_counts", "lne_sparsifier_csr", "lne_gaussian_sketch",
     "lne_spmm", "lne_cholqr2", "lne_rsvd", "lne_propagate", "lne_embed",
-    "lne_kernel_launches", "lne_trace_enable", "lne_trace_read",
+    "lne_kernel_launches", "lne_trace_enable", "lne_trace_read", "lne_set_option",
+    "lne_svd_small",
 ]
+OPT_AGGREGATION = 1
+AGG_AUTO, AGG_TABLE, AGG_BUCKET = 0, 1, 2
 
 
 class LneError(RuntimeError):
@@ -98,6 +101,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lne_kernel_launches.argtypes = []
     L.lne_kernel_launches.restype = i64
     L.lne_trace_enable.argtypes = [vp, ctypes.c_int]
+    L.lne_set_option.argtypes = [vp, ctypes.c_int, i64]
+    L.lne_svd_small.argtypes = [vp, vp, i32, vp, vp, vp]
     L.lne_trace_read.argtypes = [vp, ctypes.POINTER(_TraceEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     _lib = L
     return L
@@ -204,6 +209,9 @@ class Context:
     def trim(self):
         self._check(self.lib.lne_trim(self.h))
 
+    def set_option(self, option: int, value: int):
+        self._check(self.lib.lne_set_option(self.h, option, value))
+
     def kernel_launches(self) -> int:
         return int(self.lib.lne_kernel_launches())
 
@@ -289,6 +297,15 @@ class Context:
         R = torch.zeros((c, c), dtype=torch.float64, device=self.dev)
         self._check(self.lib.lne_cholqr2(self.h, _ptr(Q), n, c, c, _ptr(R), _stream()))
         return Q, R
+
+    def svd_small(self, R: torch.Tensor):
+        """(U, sigma) of a small FP64 matrix R."""
+        R = R.to(torch.float64).contiguous()
+        c = R.shape[0]
+        U = torch.empty((c, c), dtype=torch.float64, device=self.dev)
+        sig = torch.empty(c, dtype=torch.float64, device=self.dev)
+        self._check(self.lib.lne_svd_small(self.h, _ptr(R), c, _ptr(U), _ptr(sig), _stream()))
+        return U, sig
 
     def rsvd(self, csr: dict, p: Params):
         n = int(csr["n"])

@@ -86,6 +86,26 @@ def test_cholqr2_rank_deficient_reports_numeric_error(ctx):
     assert e.value.code == -6
 
 
+@pytest.mark.parametrize("c,cond", [(144, 1e4), (128, 1e2), (48, 1e6), (16, 10.0), (7, 3.0), (160, 1e3)])
+def test_svd_small_fp64_accuracy(ctx, c, cond):
+    """The small SVD is FP64-accurate: singular values to ~1e-10 relative
+    (cond^2 * 1e-16 for the smallest), U orthonormal and diagonalising R R^T."""
+    rng = np.random.default_rng(c)
+    Ua, _ = np.linalg.qr(rng.standard_normal((c, c)))
+    Vb, _ = np.linalg.qr(rng.standard_normal((c, c)))
+    s = np.geomspace(1.0, 1.0 / cond, c)
+    R = np.triu(np.linalg.qr((Ua * s) @ Vb.T)[1])
+    U, sig = ctx.svd_small(torch.as_tensor(R).cuda())
+    U, sig = to_np(U), to_np(sig)
+    ref = np.linalg.svd(R, compute_uv=False)
+    assert np.all(np.diff(sig) <= 0)
+    np.testing.assert_allclose(sig, ref, rtol=max(1e-11, 1e-15 * cond * cond))
+    assert np.max(np.abs(U.T @ U - np.eye(c))) <= 1e-10
+    B = U.T @ R @ R.T @ U
+    off = B - np.diag(np.diag(B))
+    assert np.max(np.abs(off)) <= 1e-12 * ref[0] ** 2
+
+
 def _rsvd_compare(ctx, indptr, indices, data, d, p_os, q, seed):
     ref = oracle.fast_randomized_svd(indptr, indices, data, d, q, p_os, seed)
     p = make_params(1, [1.0], 1.0, d=d, oversample=p_os, q=q, seed=seed)
