@@ -50,32 +50,45 @@ def workload():
 # per-kernel algorithmic work (bytes or flops per launch), for the roofline
 # ---------------------------------------------------------------------------
 
-def kernel_model(name, g, params, counts):
-    """(bound, amount per launch, unit) of the algorithmic work of a kernel.
+def walk_ops_per_sample(params):
+    """Integer lane-operations one PathSampling draw needs (algorithmic count).
 
-    walk_emit:      HBM: 4 B key write per sample + 12 B per arc (indptr, target)
-    bucket_scatter: HBM: 4 B read + 4 B write per sample
-    bucket_reduce:  HBM: 4 B read per sample + 8 B per distinct pair written
-    spmm:           HBM: 12 B per nonzero (col, val) + dense operand once + out
-    jacobi_svd / chol_inv / gram_partial: FP64 flops
+    A Philox4x32-10 block is 10 rounds of 2 wide multiplies and 2 three-input
+    XORs (40 ops); a draw with window r needs ceil((r + 2) / 4) blocks (words:
+    r, split, coin, r - 1 steps). A walk step is a degree reduction by
+    multiply-shift (4 multiplies + 1 add = 5 ops); the window lookup, split,
+    pair ordering and the counter address take 12 ops per draw.
+    """
+    s = np.asarray(params["s"], dtype=np.float64)
+    s = s / s.sum()
+    r = np.arange(1, len(s) + 1)
+    blocks = np.ceil((r + 2) / 4.0)
+    return float(np.sum(s * (40.0 * blocks + 5.0 * (r - 1) + 12.0)))
+
+
+def kernel_model(name, g, params, counts):
+    """(bound, algorithmic amount per launch, unit) of a kernel, or None.
+
+    walk_count / walk_emit: ALU -- walk_ops_per_sample * samples (lane-ops).
+    spmm:       FMA -- 2 * nnz(M) * c flops (FP32).
+    graph_spmm: FMA -- 2 * nnz(A) * d flops (FP32).
+    gram_partial: FP64 -- n * c * (c + 1) flops (upper half of Y^T Y).
     """
     S = counts["total_samples"]
     n, m2 = g.n, g.n_arcs
     c = params["d"] + params["oversample"]
-    nnz_c = counts.get("nnz_c", 0)
-    nnz_M = counts.get("nnz_M", 0)
-    if name == "walk_emit":
-        return "hbm", 4.0 * S + 12.0 * m2, "GB/s"
-    if name == "bucket_scatter":
-        return "hbm", 8.0 * S, "GB/s"
-    if name == "bucket_reduce":
-        return "hbm", 4.0 * S + 8.0 * nnz_c, "GB/s"
+    if name in ("walk_count", "walk_emit"):
+        return "alu", walk_ops_per_sample(params) * S, "Gop/s"
     if name == "spmm":
-        return "hbm", 12.0 * nnz_M + 8.0 * n * c + 8.0 * (n + 1), "GB/s"
+        return "fma", 2.0 * counts.get("nnz_M", 0) * c, "GFLOP/s"
     if name == "graph_spmm":
-        d = params["d"]
-        return "hbm", 4.0 * m2 + 8.0 * (n + 1) + 4.0 * n * d * 4, "GB/s"
+        return "fma", 2.0 * m2 * params["d"], "GFLOP/s"
     return None
+
+
+def alu_peak_gops(sm_mhz):
+    """152 SMs x 4 sub-partitions x 32 lanes, one instruction per clock."""
+    return 152 * 128 * sm_mhz * 1e6 / 1e9
 
 
 def read_peaks():
@@ -316,17 +329,19 @@ def run_ours(args):
         per_launch[t["name"]] = t
     dom = max(trace, key=lambda t: t["ms"])
     model = kernel_model(dom["name"], g, params, info)
-    roof = None
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    peaks = {"alu": (alu_peak_gops(sm_mhz), "derived: 152 SMs x 128 lanes x median SM clock"),
+             "fma": (2 * alu_peak_gops(sm_mhz), "derived: 152 SMs x 128 FP32 lanes x 2 flops x median SM clock"),
+             "hbm": (hbm, src)}
+    roof = {"kernel": dom["name"], "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None, "avg_launch_ms": dom["ms"] / max(1, dom["regions"])}
     if model is not None:
         bound, amount, unit = model
         avg_s = dom["ms"] / max(1, dom["regions"]) / 1e3
         achieved = amount / avg_s / 1e9
-        roof = {"kernel": dom["name"], "bound": bound, "achieved": achieved, "peak": hbm, "unit": unit,
-                "frac": achieved / hbm, "traffic": None, "peak_source": src,
-                "avg_launch_ms": avg_s * 1e3}
-    else:
-        roof = {"kernel": dom["name"], "bound": "fp64", "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None, "avg_launch_ms": dom["ms"] / max(1, dom["regions"])}
+        peak, psrc = peaks[bound]
+        roof.update({"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                     "peak_source": psrc, "work_per_launch": amount})
     step_total = sum(t["ms"] for t in trace if t["name"] not in ("scan_exclusive",)) / max(1, args.steps)
     breakdown = {t["name"]: round(t["ms"] / max(1, args.steps), 4) for t in trace}
 
@@ -355,6 +370,33 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_case(args):
+    """A small, repeatable run of one stage for profilers (ncu): the bench graph
+    with S/10 samples; each stage runs `--steps` times."""
+    import torch
+    from paper_2302_07084_gb300 import lne
+    g, params = workload()
+    params = dict(params)
+    params["samples"] = params["samples"] / 10.0
+    P = lne.Params(**params)
+    ctx = lne.Context(0)
+    dg = lne.DeviceGraph(g.indptr, g.indices)
+    csr = ctx.sparsifier_csr(dg, P)
+    X0 = torch.randn((g.n, P.d), device="cuda")
+    for _ in range(args.steps):
+        if args.case == "sparsifier":
+            ctx.sparsifier_csr(dg, P)
+        elif args.case == "rsvd":
+            ctx.rsvd(csr, P)
+        elif args.case == "propagate":
+            ctx.propagate(dg, P, X0)
+        elif args.case == "embed":
+            ctx.embed(dg, P)
+    torch.cuda.synchronize()
+    ctx.close()
+    print(json.dumps({"case": args.case, "steps": args.steps, "samples": params["samples"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -362,8 +404,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=["sparsifier", "rsvd", "propagate", "embed"], default=None,
+                    help="run one stage on a reduced workload (for profilers) instead of the benchmark")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.case:
+        run_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

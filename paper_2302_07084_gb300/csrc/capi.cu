@@ -414,7 +414,7 @@ int lne_spmm(lne_ctx *ctx, const lne_csr *M, const float *X_dev, int64_t ldx, in
         v.indptr = M->indptr;
         v.indices = M->indices;
         v.data = M->data;
-        rc = lne::spmm(v, X_dev, ldx, c, Y_dev, ldy, as_stream(stream));
+        rc = lne::spmm(ctx->ws, v, X_dev, ldx, c, Y_dev, ldy, as_stream(stream));
     }
     return finish(ctx, rc);
 }

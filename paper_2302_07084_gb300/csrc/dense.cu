@@ -66,7 +66,7 @@ constexpr int kGramThreads = 256;
 __global__ void __launch_bounds__(kGramThreads) gram_partial_kernel(const float *__restrict__ Y, int64_t n, int c,
                                                                     int64_t ld, int64_t rows_per_cta,
                                                                     double *__restrict__ partial) {
-    extern __shared__ float ys[];   // kGramRows x cp
+    extern __shared__ double ys[];   // kGramRows x cp, rows converted to FP64 once
     const int cp = (c + 7) & ~7;
     const int nt = cp / 8;
     const int ntiles = nt * (nt + 1) / 2;
@@ -95,17 +95,17 @@ __global__ void __launch_bounds__(kGramThreads) gram_partial_kernel(const float 
             const int rows = (int)imin64(kGramRows, r1 - base);
             for (int e = tid; e < kGramRows * cp; e += kGramThreads) {
                 int rr = e / cp, cc = e - rr * cp;
-                ys[e] = (rr < rows && cc < c) ? Y[(base + rr) * ld + cc] : 0.0f;
+                ys[e] = (rr < rows && cc < c) ? (double)Y[(base + rr) * ld + cc] : 0.0;
             }
             __syncthreads();
             if (active) {
                 for (int rr = 0; rr < rows; ++rr) {
-                    const float *yr = ys + rr * cp;
+                    const double *yr = ys + rr * cp;
                     double av[8], bv[8];
 #pragma unroll
                     for (int t = 0; t < 8; ++t) {
-                        av[t] = (double)yr[ti * 8 + t];
-                        bv[t] = (double)yr[tj * 8 + t];
+                        av[t] = yr[ti * 8 + t];
+                        bv[t] = yr[tj * 8 + t];
                     }
 #pragma unroll
                     for (int x = 0; x < 8; ++x)
@@ -311,10 +311,10 @@ __global__ void __launch_bounds__(256) right_multiply_kernel(
 //   1. one-sided (Hestenes) Jacobi on R in FP32, one CTA, accumulating the
 //      right rotations V (columns paired by the circle method: m = c rounded up
 //      to even players, player 0 fixed, m/2 disjoint pairs per round, 8 threads
-//      per pair);
-//   2. Ogita-Aishima refinement of V as eigenvectors of G = R^T R in FP64
-//      (matrix products only, spread over many CTAs);
-//   3. sigma = sqrt(lambda), U_R = R V Sigma^-1, sorted by sigma descending.
+//      per pair); U = normalised columns of R V;
+//   2. Ogita-Aishima refinement of (U, Sigma, V) of R itself in FP64 (matrix
+//      products only, spread over many CTAs; R is never squared);
+//   3. sorted by sigma descending.
 // FP64 rates on this GPU are a small fraction of FP32, so FP64 is used only
 // where the refinement needs it: its products.
 // ---------------------------------------------------------------------------
@@ -324,8 +324,8 @@ __device__ __forceinline__ int circle_player(int pos, int round, int m) {
     return pos == 0 ? 0 : ((pos - 1 + round) % (m - 1)) + 1;
 }
 
-__global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__restrict__ Vout, int max_sweeps,
-                                int *__restrict__ sweeps_out) {
+__global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__restrict__ Uout,
+                                double *__restrict__ Vout, int max_sweeps, int *__restrict__ sweeps_out) {
     extern __shared__ float js[];
     float *A = js;            // column-major: A[j * c + i]
     float *V = js + c * c;    // column-major
@@ -342,7 +342,9 @@ __global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__r
     const int m = c + (c & 1);
     const int pairs = m / 2;
     const int pi = tid / kJacTPP, sub = tid % kJacTPP;
-    const float tol = 2e-7f;
+    // FP32 round-off floor of |a_p . a_q| / (|a_p| |a_q|) is about c * 2^-24; the
+    // FP64 refinement that follows takes the vectors the rest of the way.
+    const float tol = fmaxf(4.f * (float)c * 5.9604645e-8f, 1e-6f);
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         float local_max = 0.f;
@@ -411,9 +413,18 @@ __global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__r
             break;
         }
     }
+    // column norms of R V are the singular values; U = (R V) Sigma^-1
+    __shared__ float s_nrm[kMaxSmemC + 1];
+    for (int j = tid; j < c; j += nthreads) {
+        float t = 0.f;
+        for (int i = 0; i < c; ++i) t = fmaf(A[j * c + i], A[j * c + i], t);
+        s_nrm[j] = t > 0.f ? rsqrtf(t) : 0.f;
+    }
+    __syncthreads();
     for (int e = tid; e < c * c; e += nthreads) {
         int i = e / c, j = e - i * c;
-        Vout[e] = (double)V[j * c + i];   // row-major, column j = j-th right vector
+        Vout[e] = (double)V[j * c + i];                 // row-major, column j = j-th right vector
+        Uout[e] = (double)(A[j * c + i] * s_nrm[j]);    // column j = j-th left vector
     }
     if (tid == 0 && sweeps_out) *sweeps_out = sweep;
 }
@@ -452,62 +463,102 @@ __device__ double block_sum(double v, double *red) {
     return t;
 }
 
-// One Ogita-Aishima step (symmetric eigenvalue refinement, 2018): with
-// P = X^T X, Rr = I - P and S = X^T G X,  lambda_i = s_ii / (1 - r_ii),
-// delta = 2 (||S - diag(lambda)|| + ||G|| ||Rr||) (Frobenius norms bound the
-// 2-norms), E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) when
-// |lambda_i - lambda_j| > delta, else r_ij / 2; the update is X (I + E).
-__global__ void oa_update_kernel(const double *__restrict__ G, const double *__restrict__ S,
-                                 const double *__restrict__ P, int c, double *__restrict__ E,
-                                 double *__restrict__ lam) {
+// One step of Ogita-Aishima refinement of an SVD A = U Sigma V^T (Ogita and
+// Aishima, "Iterative refinement for singular value decomposition based on
+// matrix multiplication", 2020), written from first-order perturbation:
+// with U = U^(I + F), V = V^(I + G) exact, P = I - U^T U^ = F + F^T,
+// Q = I - V^T V^ = G + G^T and T = U^T A V^ = Sigma - F^T Sigma - Sigma G. So
+// sigma_i = t_ii / (1 - (p_ii + q_ii) / 2), f_ii = p_ii / 2, g_ii = q_ii / 2,
+// and for i != j the pair (f_ij, g_ij) solves
+//   [ s_j  -s_i ] [f_ij]   [t_ij + p_ij s_j]
+//   [-s_i   s_j ] [g_ij] = [t_ji + q_ij s_j],
+// taken as (p_ij / 2, q_ij / 2) when |s_i - s_j| <= delta (near-equal values),
+// delta = 2 (||offdiag T|| + max|s| (||P|| + ||Q||)). A itself is never squared,
+// so the accuracy does not depend on the condition number of A.
+__global__ void svd_oa_update_kernel(const double *__restrict__ P, const double *__restrict__ Q,
+                                     const double *__restrict__ T, int c, double *__restrict__ F,
+                                     double *__restrict__ Gm, double *__restrict__ sig) {
     __shared__ double red[32];
-    __shared__ double s_lam[256];
+    __shared__ double s_sig[256];
     const int tid = threadIdx.x;
-    for (int i = tid; i < c; i += blockDim.x) s_lam[i] = S[i * c + i] / P[i * c + i];
+    for (int i = tid; i < c; i += blockDim.x)
+        s_sig[i] = T[i * c + i] / (1.0 - 0.5 * (P[i * c + i] + Q[i * c + i]));
     __syncthreads();
-    double g2 = 0.0, r2 = 0.0, sd2 = 0.0;
+    double o2 = 0.0, p2 = 0.0, q2 = 0.0, smax = 0.0;
     for (int e = tid; e < c * c; e += blockDim.x) {
-        int i = e / c, j = e - i * c;
-        double gv = G[e];
-        double rv = (i == j ? 1.0 : 0.0) - P[e];
-        double sv = S[e] - (i == j ? s_lam[i] : 0.0);
-        g2 = fma(gv, gv, g2);
-        r2 = fma(rv, rv, r2);
-        sd2 = fma(sv, sv, sd2);
+        const int i = e / c, j = e - i * c;
+        const double t = i == j ? 0.0 : T[e];
+        o2 = fma(t, t, o2);
+        p2 = fma(P[e], P[e], p2);
+        q2 = fma(Q[e], Q[e], q2);
     }
-    g2 = block_sum(g2, red);
-    r2 = block_sum(r2, red);
-    sd2 = block_sum(sd2, red);
-    const double delta = 2.0 * (sqrt(sd2) + sqrt(g2) * sqrt(r2));
+    for (int i = tid; i < c; i += blockDim.x) smax = fmax(smax, fabs(s_sig[i]));
+    o2 = block_sum(o2, red);
+    p2 = block_sum(p2, red);
+    q2 = block_sum(q2, red);
+    // block max of smax
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, off));
+        __syncthreads();
+        if (lane == 0) red[warp] = smax;
+        __syncthreads();
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m = fmax(m, red[w]);
+        smax = m;
+    }
+    const double delta = 2.0 * (sqrt(o2) + smax * (sqrt(p2) + sqrt(q2)));
     for (int e = tid; e < c * c; e += blockDim.x) {
-        int i = e / c, j = e - i * c;
-        double rij = (i == j ? 1.0 : 0.0) - P[e];
-        double v;
+        const int i = e / c, j = e - i * c;
+        const double pij = P[e], qij = Q[e];
+        double f, g;
         if (i == j) {
-            v = 0.5 * rij;
+            f = 0.5 * pij;
+            g = 0.5 * qij;
         } else {
-            double li = s_lam[i], lj = s_lam[j];
-            v = fabs(li - lj) > delta ? (S[e] + lj * rij) / (lj - li) : 0.5 * rij;
+            const double si = s_sig[i], sj = s_sig[j];
+            if (fabs(sj - si) > delta) {
+                const double r1 = T[e] + pij * sj;
+                const double r2 = T[j * c + i] + qij * sj;
+                const double det = (sj - si) * (sj + si);
+                f = (sj * r1 + si * r2) / det;
+                g = (si * r1 + sj * r2) / det;
+            } else {
+                f = 0.5 * pij;
+                g = 0.5 * qij;
+            }
         }
-        E[e] = v;
+        F[e] = f;
+        Gm[e] = g;
     }
-    for (int i = tid; i < c; i += blockDim.x) lam[i] = s_lam[i];
+    for (int i = tid; i < c; i += blockDim.x) sig[i] = s_sig[i];
 }
 
-// sigma sorted descending; U_R[:, rank_j] = T[:, j] / sigma_j with T = R X.
-__global__ void svd_finish_kernel(const double *__restrict__ T, const double *__restrict__ lam, int c,
+// P := I - P and Q := I - Q in place (from the Gram products U^T U, V^T V).
+__global__ void svd_ia_kernel_prep(double *__restrict__ P, double *__restrict__ Q, int c) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= c * c) return;
+    const int i = e / c, j = e - i * c;
+    const double d = i == j ? 1.0 : 0.0;
+    P[e] = d - P[e];
+    Q[e] = d - Q[e];
+}
+
+// sigma sorted descending; U_R[:, rank_j] = sign(s_j) U[:, j].
+__global__ void svd_finish_kernel(const double *__restrict__ U, const double *__restrict__ sg, int c,
                                   double *__restrict__ UR, double *__restrict__ sigma) {
     __shared__ double s_sig[256];
     const int tid = threadIdx.x;
-    for (int j = tid; j < c; j += blockDim.x) s_sig[j] = sqrt(fmax(lam[j], 0.0));
+    for (int j = tid; j < c; j += blockDim.x) s_sig[j] = fabs(sg[j]);
     __syncthreads();
     for (int j = tid; j < c; j += blockDim.x) {
         const double sj = s_sig[j];
         int rank = 0;
         for (int i = 0; i < c; ++i) rank += (s_sig[i] > sj) || (s_sig[i] == sj && i < j);
         sigma[rank] = sj;
-        const double inv = sj > 0.0 ? 1.0 / sj : 0.0;
-        for (int i = 0; i < c; ++i) UR[i * c + rank] = T[i * c + j] * inv;
+        const double sgn = sg[j] < 0.0 ? -1.0 : 1.0;
+        for (int i = 0; i < c; ++i) UR[i * c + rank] = U[i * c + j] * sgn;
     }
 }
 
@@ -601,7 +652,7 @@ static int gram(Workspace &ws, const float *Y, int64_t n, int c, int64_t ld, dou
     nblk = ceil_div(std::max<int64_t>(n, 1), rows_per);
     double *partial = nullptr;
     LNE_TRY(ws.get("gram.partial", (size_t)nblk * cp * cp, &partial));
-    const int smem = kGramRows * cp * 4;
+    const int smem = kGramRows * cp * 8;
     {
         LNE_TRACE("gram_partial", st);
         gram_partial_kernel<<<(unsigned)nblk, threads, smem, st>>>(Y, n, c, ld, rows_per, partial);
@@ -700,22 +751,23 @@ static int dgemm_small(const double *A, bool ta, const double *B, bool tb, const
 
 int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma, cudaStream_t st) {
     if (c > kMaxSmemC) return fail(LNE_ERR_UNSUPPORTED, "small SVD supports c <= 160");
-    double *G = nullptr, *X = nullptr, *X2 = nullptr, *W = nullptr, *S = nullptr, *P = nullptr, *E = nullptr,
-           *lam = nullptr;
+    double *U = nullptr, *U2 = nullptr, *V = nullptr, *V2 = nullptr, *W = nullptr, *T = nullptr, *P = nullptr,
+           *Q = nullptr, *F = nullptr, *Gm = nullptr, *sg = nullptr;
     int *sweeps = nullptr;
     const size_t cc = (size_t)c * c;
-    LNE_TRY(ws.get("svd.G", cc, &G));
-    LNE_TRY(ws.get("svd.X", cc, &X));
-    LNE_TRY(ws.get("svd.X2", cc, &X2));
+    LNE_TRY(ws.get("svd.U", cc, &U));
+    LNE_TRY(ws.get("svd.U2", cc, &U2));
+    LNE_TRY(ws.get("svd.V", cc, &V));
+    LNE_TRY(ws.get("svd.V2", cc, &V2));
     LNE_TRY(ws.get("svd.W", cc, &W));
-    LNE_TRY(ws.get("svd.S", cc, &S));
+    LNE_TRY(ws.get("svd.T", cc, &T));
     LNE_TRY(ws.get("svd.P", cc, &P));
-    LNE_TRY(ws.get("svd.E", cc, &E));
-    LNE_TRY(ws.get("svd.lam", (size_t)c, &lam));
+    LNE_TRY(ws.get("svd.Q", cc, &Q));
+    LNE_TRY(ws.get("svd.F", cc, &F));
+    LNE_TRY(ws.get("svd.G", cc, &Gm));
+    LNE_TRY(ws.get("svd.sg", (size_t)c, &sg));
     LNE_TRY(ws.get("svd.sweeps", 1, &sweeps));
-    // G = R^T R in FP64
-    LNE_TRY(dgemm_small(R, true, R, false, nullptr, G, c, st));
-    // starting vectors: FP32 one-sided Jacobi on R
+    // starting point: FP32 one-sided Jacobi on R (U, V in FP64 storage)
     const int m = c + (c & 1);
     const int threads = std::max(32, std::min(1024, (m / 2 * kJacTPP + 31) / 32 * 32));
     const int smem = 2 * c * c * 4;
@@ -723,36 +775,31 @@ int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma,
         LNE_CUDA_TRY(cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     {
         LNE_TRACE("jacobi32", st);
-        jacobi32_kernel<<<1, threads, smem, st>>>(R, c, X, 40, sweeps);
+        jacobi32_kernel<<<1, threads, smem, st>>>(R, c, U, V, 10, sweeps);
         LNE_LAUNCH_CHECK();
     }
-    // FP64 refinement
-    for (int it = 0; it < 3; ++it) {
-        LNE_TRY(dgemm_small(G, false, X, false, nullptr, W, c, st));   // W = G X
-        LNE_TRY(dgemm_small(X, true, W, false, nullptr, S, c, st));    // S = X^T G X
-        LNE_TRY(dgemm_small(X, true, X, false, nullptr, P, c, st));    // P = X^T X
+    // FP64 refinement of the SVD of R itself (quadratic convergence; the FP32
+    // start may be loose in directions FP32 cannot resolve, hence four steps)
+    for (int it = 0; it < 4; ++it) {
+        LNE_TRY(dgemm_small(U, true, U, false, nullptr, P, c, st));   // P = U^T U (I - P below)
+        LNE_TRY(dgemm_small(V, true, V, false, nullptr, Q, c, st));   // Q = V^T V
+        LNE_TRY(dgemm_small(R, false, V, false, nullptr, W, c, st));  // W = R V
+        LNE_TRY(dgemm_small(U, true, W, false, nullptr, T, c, st));   // T = U^T R V
         {
-            LNE_TRACE("oa_update", st);
-            oa_update_kernel<<<1, 256, 0, st>>>(G, S, P, c, E, lam);
+            LNE_TRACE("svd_oa_update", st);
+            svd_ia_kernel_prep<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(P, Q, c);
+            LNE_LAUNCH_CHECK();
+            svd_oa_update_kernel<<<1, 256, 0, st>>>(P, Q, T, c, F, Gm, sg);
             LNE_LAUNCH_CHECK();
         }
-        LNE_TRY(dgemm_small(X, false, E, false, X, X2, c, st));        // X2 = X + X E
-        std::swap(X, X2);
+        LNE_TRY(dgemm_small(U, false, F, false, U, U2, c, st));       // U2 = U + U F
+        LNE_TRY(dgemm_small(V, false, Gm, false, V, V2, c, st));      // V2 = V + V G
+        std::swap(U, U2);
+        std::swap(V, V2);
     }
-    // Rayleigh quotients of the refined vectors
-    LNE_TRY(dgemm_small(G, false, X, false, nullptr, W, c, st));
-    LNE_TRY(dgemm_small(X, true, W, false, nullptr, S, c, st));
-    LNE_TRY(dgemm_small(X, true, X, false, nullptr, P, c, st));
-    {
-        LNE_TRACE("oa_update", st);
-        oa_update_kernel<<<1, 256, 0, st>>>(G, S, P, c, E, lam);
-        LNE_LAUNCH_CHECK();
-    }
-    // U_R = R X Sigma^-1, sorted
-    LNE_TRY(dgemm_small(R, false, X, false, nullptr, W, c, st));
     {
         LNE_TRACE("svd_finish", st);
-        svd_finish_kernel<<<1, 256, 0, st>>>(W, lam, c, U_R, sigma);
+        svd_finish_kernel<<<1, 256, 0, st>>>(U, sg, c, U_R, sigma);
         LNE_LAUNCH_CHECK();
     }
     return 0;

@@ -84,11 +84,11 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
     double *so = sigma ? sigma : sg;
     // Algorithm 4: Omega = randn(n, d+s); Y = M Omega
     LNE_TRY(gaussian_sketch(n, c, seed, Om, c, st));
-    LNE_TRY(spmm(M, Om, c, c, Ya, c, st));
+    LNE_TRY(spmm(ws, M, Om, c, c, Ya, c, st));
     // power iterations: Q = orth(Y); Y = M Q (q times)
     for (int it = 0; it < q; ++it) {
         LNE_TRY(cholqr2(ws, Ya, n, c, c, nullptr, st));
-        LNE_TRY(spmm(M, Ya, c, c, Yb, c, st));
+        LNE_TRY(spmm(ws, M, Ya, c, c, Yb, c, st));
         std::swap(Ya, Yb);
     }
     // final eigSVD of Y: U = Q(:, 1:d), Sigma(1:d)
@@ -142,7 +142,7 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
         e1.E1 = X0;
         e1.b1 = om;
         e1.lde = d;
-        LNE_TRY(graph_spmm(g, X0, d, d, Z, d, e1, st));
+        LNE_TRY(graph_spmm(ws, g, X0, d, d, Z, d, e1, st));
         // T_1 = Yop X0 = (Lap - mu I) Z / 2 - X0; F += c_1 T_1
         SpmmEpilogue e2;
         e2.alpha = -0.5f;
@@ -158,7 +158,7 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
             e2.X0 = X0;
             e2.G = Gb;
         }
-        LNE_TRY(graph_spmm(g, Z, d, d, Ta, d, e2, st));
+        LNE_TRY(graph_spmm(ws, g, Z, d, d, Ta, d, e2, st));
         // T_{i-2}, T_{i-1} rotate through three buffers; X0 is never written
         float *const bufs[3] = {Ta, Tb, Tc};
         const float *prev = X0;
@@ -177,7 +177,7 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
             ez.E1 = cur;
             ez.b1 = om;
             ez.lde = d;
-            LNE_TRY(graph_spmm(g, cur, d, d, Z, d, ez, st));
+            LNE_TRY(graph_spmm(ws, g, cur, d, d, Z, d, ez, st));
             // T_i = 2 Yop T_{i-1} - T_{i-2} = (Lap - mu I) Z - 2 T_{i-1} - T_{i-2}
             SpmmEpilogue e;
             e.alpha = -1.f;
@@ -195,7 +195,7 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
                 e.X0 = X0;
                 e.G = Gb;
             }
-            LNE_TRY(graph_spmm(g, Z, d, d, nxt, d, e, st));
+            LNE_TRY(graph_spmm(ws, g, Z, d, d, nxt, d, e, st));
             prev = cur;
             cur = nxt;
         }
@@ -205,7 +205,7 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
     ep.alpha = 1.f;
     ep.dinv = true;
     ep.lde = d;
-    LNE_TRY(graph_spmm(g, Gb, d, d, Pb, d, ep, st));
+    LNE_TRY(graph_spmm(ws, g, Gb, d, d, Pb, d, ep, st));
     // X = U_P Sigma_P^{1/2} from the SVD of P (economic SVD of the last stage)
     LNE_CUDA_TRY(cudaMemcpyAsync(Qb, Pb, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, st));
     LNE_TRY(tall_svd(ws, Qb, n, d, d, Ub, sig, st));

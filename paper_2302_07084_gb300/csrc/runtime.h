@@ -92,7 +92,7 @@ int sparsifier_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Csr
 
 // ---- dense and sparse linear algebra (dense.cu, spmm.cu) -------------------
 int gaussian_sketch(int64_t n, int c, uint64_t seed, float *out, int64_t ld, cudaStream_t st);
-int spmm(const CsrView &M, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
+int spmm(Workspace &ws, const CsrView &M, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
          cudaStream_t st);
 // Y := Q in place; R (optional, device FP64 [c][c]) receives the upper factor.
 int cholqr2(Workspace &ws, float *Y, int64_t n, int c, int64_t ld, double *R, cudaStream_t st);
@@ -124,7 +124,7 @@ struct SpmmEpilogue {
     float *G = nullptr;
     bool store = true;                  // write out to Y
 };
-int graph_spmm(const GraphView &g, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
+int graph_spmm(Workspace &ws, const GraphView &g, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
                const SpmmEpilogue &ep, cudaStream_t st);
 
 // Randomized SVD (Algorithm 4) and propagation (Sec. 3.3).

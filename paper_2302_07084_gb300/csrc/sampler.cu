@@ -42,6 +42,7 @@ constexpr int kWalkThreads = 256;
 struct WalkArgs {
     const int64_t *indptr;
     const int32_t *indices;
+    const uint4 *vinfo;           // per-vertex walk record (see build_vinfo_kernel)
     int64_t n;
     int64_t n_arcs;
     uint32_t k0, k1;
@@ -50,6 +51,12 @@ struct WalkArgs {
     int T;
     int B;
     uint64_t thr[16];
+    // derived on the host
+    uint32_t rk[20];              // Philox round keys (k0 + i W0, k1 + i W1), i = 0..9
+    uint32_t thr32[16];           // thresholds below 2^32, ascending
+    int T_eff;                    // how many thresholds are below 2^32
+    uint64_t base_magic;          // ceil(2^64 / base): s / base by a high multiply
+    uint64_t rmagic[17];          // ceil(2^64 / r) for r = 1..16 (index r)
 };
 
 __device__ __forceinline__ uint32_t arc_count(const WalkArgs &A, int64_t arc) {
@@ -58,6 +65,52 @@ __device__ __forceinline__ uint32_t arc_count(const WalkArgs &A, int64_t arc) {
                0xFFFFFFFFu};
     u32x4 w = philox10(c, A.k0, A.k1);
     return A.base + (w.x < A.thr_frac ? 1u : 0u);
+}
+
+// Philox4x32-10 with precomputed round keys; each 32 x 32 -> 64 product is one
+// wide multiply.
+__device__ __forceinline__ u32x4 philox_rk(u32x4 c, const uint32_t *rk) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c.z;
+        u32x4 n;
+        n.x = (uint32_t)(p1 >> 32) ^ c.y ^ rk[2 * round];
+        n.y = (uint32_t)p1;
+        n.z = (uint32_t)(p0 >> 32) ^ c.w ^ rk[2 * round + 1];
+        n.w = (uint32_t)p0;
+        c = n;
+    }
+    return c;
+}
+
+// a mod d and a / d for 32-bit a, d >= 1 with M = ceil(2^64 / d) (Lemire, Kaser
+// and Kurz, "Faster remainder by direct computation", 2019): the low 64 bits
+// of M a, times d, keep the remainder in their top 32 bits; M a >> 64 is the
+// quotient.
+__device__ __forceinline__ uint32_t fastmod32(uint32_t a, uint64_t M, uint32_t d) {
+    const uint64_t low = M * (uint64_t)a;
+    const uint64_t t = (uint64_t)(uint32_t)low * d;
+    const uint64_t u = (low >> 32) * (uint64_t)d + (t >> 32);
+    return (uint32_t)(u >> 32);
+}
+__device__ __forceinline__ uint32_t fastdiv32(uint32_t a, uint64_t M) {
+    return (uint32_t)__umul64hi(M, (uint64_t)a);
+}
+
+// Per-vertex walk record: x = (offset bits 0..31, offset bits 32..39 | degree
+// << 8, M lo, M hi) with M = ceil(2^64 / degree). Degrees of 2^24 and more are
+// marked 0xFFFFFF and read from indptr.
+__global__ void build_vinfo_kernel(const int64_t *__restrict__ indptr, int64_t n, uint4 *__restrict__ vinfo) {
+    for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t off = indptr[x];
+        const int64_t deg = indptr[x + 1] - off;
+        const uint32_t dfield = deg >= 0xFFFFFF ? 0xFFFFFFu : (uint32_t)deg;
+        const uint64_t M = deg > 0 && deg < (1ll << 32) ? (~0ull) / (uint64_t)deg + 1ull : 0ull;
+        vinfo[x] = make_uint4((uint32_t)off, (uint32_t)((off >> 32) & 0xFF) | (dfield << 8), (uint32_t)M,
+                              (uint32_t)(M >> 32));
+    }
 }
 
 __device__ __forceinline__ int32_t arc_source(const int64_t *__restrict__ indptr, int64_t n,
@@ -70,55 +123,61 @@ __device__ __forceinline__ int32_t arc_source(const int64_t *__restrict__ indptr
     return (int32_t)lo;
 }
 
-// The sample's stream of 32-bit Philox words: counter (j, a_lo, a_hi, blk).
-struct WordStream {
-    u32x4 cur;
-    uint32_t c0, c1, c2, blk;
-    uint32_t k0, k1;
-    int pos;
-    __device__ __forceinline__ uint32_t next() {
-        if (pos == 4) {
-            ++blk;
-            cur = philox10(u32x4{c0, c1, c2, blk}, k0, k1);
-            pos = 0;
-        }
-        uint32_t r = pos == 0 ? cur.x : pos == 1 ? cur.y : pos == 2 ? cur.z : cur.w;
-        ++pos;
-        return r;
+// One walk step: x <- nbr(x)[w mod deg(x)] (Sec. 4.2).
+__device__ __forceinline__ int32_t walk_step(const WalkArgs &A, int32_t x, uint32_t w) {
+    const uint4 rec = __ldg(A.vinfo + x);
+    uint32_t deg = rec.y >> 8;
+    int64_t off = (int64_t)rec.x | ((int64_t)(rec.y & 0xFF) << 32);
+    uint32_t j;
+    if (deg == 0xFFFFFFu) {
+        deg = (uint32_t)(__ldg(A.indptr + x + 1) - __ldg(A.indptr + x));
+        j = w % deg;
+    } else {
+        if (deg == 0) return x;   // only on graphs that break the contract
+        j = fastmod32(w, ((uint64_t)rec.w << 32) | rec.z, deg);
     }
-};
-
-__device__ __forceinline__ int32_t walk_steps(const WalkArgs &A, int32_t x, int steps,
-                                              WordStream &ws) {
-    for (int t = 0; t < steps; ++t) {
-        uint32_t w = ws.next();
-        int64_t b = __ldg(A.indptr + x);
-        uint32_t deg = (uint32_t)(__ldg(A.indptr + x + 1) - b);
-        if (deg == 0) continue;   // only on graphs that break the contract
-        x = __ldg(A.indices + b + (w % deg));
-    }
-    return x;
+    return __ldg(A.indices + off + j);
 }
 
-// One PathSampling draw of sample j on arc (u -> v).
-__device__ __forceinline__ void draw(const WalkArgs &A, int64_t arc, uint32_t j, int32_t u,
+// One PathSampling draw (Algorithm 1) of sample j on arc (u -> v): word 0 of
+// counter (j, a_lo, a_hi, 0) picks r, word 1 the split sigma, word 2 is the
+// reserved coin, words 3.. drive the walk steps, u side first.
+__device__ __forceinline__ void draw(const WalkArgs &A, const uint8_t *__restrict__ rlut,
+                                     const uint64_t *__restrict__ rmagic, int64_t arc, uint32_t j, int32_t u,
                                      int32_t v, int32_t *pu, int32_t *pv) {
-    WordStream ws;
-    ws.c0 = j;
-    ws.c1 = (uint32_t)((uint64_t)arc & 0xFFFFFFFFu);
-    ws.c2 = (uint32_t)((uint64_t)arc >> 32);
-    ws.blk = 0;
-    ws.k0 = A.k0;
-    ws.k1 = A.k1;
-    ws.cur = philox10(u32x4{ws.c0, ws.c1, ws.c2, 0u}, A.k0, A.k1);
-    ws.pos = 3;   // words 0..2: window, split, reserved coin
-    int r = 1;
-#pragma unroll 16
-    for (int i = 0; i < 15; ++i)
-        if (i < A.T - 1) r += ((uint64_t)ws.cur.x >= A.thr[i]) ? 1 : 0;
-    int sigma = (int)(ws.cur.y % (uint32_t)r);
-    *pu = walk_steps(A, u, sigma, ws);
-    *pv = walk_steps(A, v, r - 1 - sigma, ws);
+    const uint32_t c1 = (uint32_t)((uint64_t)arc & 0xFFFFFFFFu), c2 = (uint32_t)((uint64_t)arc >> 32);
+    const u32x4 b0 = philox_rk(u32x4{j, c1, c2, 0u}, A.rk);
+    // r = 1 + #{i : thr_i <= w0}; the table gives it unless a threshold falls
+    // inside the word's 2^20-wide bucket
+    const uint8_t e = rlut[b0.x >> 20];
+    int r = e & 31;
+    if (e & 0x80) {
+        r = 1;
+        for (int i = 0; i < A.T_eff; ++i) r += b0.x >= A.thr32[i] ? 1 : 0;
+    }
+    const int sigma = (int)fastmod32(b0.y, rmagic[r], (uint32_t)r);
+    const int steps = r - 1;
+    int32_t x = u, uend = u;
+    u32x4 nb = b0;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+        if (k >= steps) break;
+        if (k == sigma) {
+            uend = x;
+            x = v;
+        }
+        const int widx = 3 + k;
+        if ((widx & 3) == 0) nb = philox_rk(u32x4{j, c1, c2, (uint32_t)(widx >> 2)}, A.rk);
+        const uint32_t w = (widx & 3) == 0 ? nb.x : (widx & 3) == 1 ? nb.y : (widx & 3) == 2 ? nb.z : nb.w;
+        x = walk_step(A, x, w);
+    }
+    if (sigma >= steps) {
+        *pu = x;
+        *pv = v;
+    } else {
+        *pu = uend;
+        *pv = x;
+    }
 }
 
 // In-place exclusive scan of s[0..n) in shared memory by one CTA; returns total.
@@ -188,16 +247,30 @@ __global__ void __launch_bounds__(kWalkThreads) tile_counts_kernel(WalkArgs A, i
 // and count key buckets. MODE 2: add the pair into the dense count table
 // table[x * ld + y] (x <= y); `keys` is the table, ld = nb_smem.
 template <typename KeyT, int MODE>
-__global__ void __launch_bounds__(kWalkThreads) walk_emit_kernel(
+__global__ void __launch_bounds__(kWalkThreads, 5) walk_emit_kernel(
     WalkArgs A, int64_t a_begin, int64_t a_end, int tile_arcs, const int64_t *__restrict__ tile_off,
     KeyT *__restrict__ keys, int32_t *__restrict__ u1, int32_t *__restrict__ v1,
     uint32_t *__restrict__ bucket_cnt, int nb_smem) {
     extern __shared__ uint32_t smem[];
+    __shared__ uint8_t s_rlut[4096];
+    __shared__ uint64_t s_rmagic[17];
     uint32_t *s_off = smem;                                      // tile_arcs + 1
     int32_t *s_src = reinterpret_cast<int32_t *>(s_off + tile_arcs + 1);
     int32_t *s_dst = s_src + tile_arcs;
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_dst + tile_arcs);
     const int tid = threadIdx.x;
+    // window-length table over the top 12 bits of the word
+    for (int b = tid; b < 4096; b += kWalkThreads) {
+        const uint32_t lo = (uint32_t)b << 20, hi = lo | 0xFFFFFu;
+        int r = 1;
+        bool amb = false;
+        for (int i = 0; i < A.T_eff; ++i) {
+            r += lo >= A.thr32[i] ? 1 : 0;
+            amb |= (A.thr32[i] > lo) && (A.thr32[i] <= hi);
+        }
+        s_rlut[b] = (uint8_t)(r | (amb ? 0x80 : 0));
+    }
+    if (tid < 17) s_rmagic[tid] = A.rmagic[tid];
     const int64_t a0 = a_begin + (int64_t)blockIdx.x * tile_arcs;
     const int na = (int)imin64(tile_arcs, a_end - a0);
     if (MODE == 1 && nb_smem > 0)
@@ -212,15 +285,23 @@ __global__ void __launch_bounds__(kWalkThreads) walk_emit_kernel(
     if (tid == 0) s_off[na] = total;
     __syncthreads();
     const int64_t out0 = tile_off ? tile_off[blockIdx.x] : 0;
+    const bool uniform = A.thr_frac == 0;
     for (uint32_t s = tid; s < total; s += kWalkThreads) {
-        int lo = 0, hi = na;   // s_off[lo] <= s < s_off[hi]
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (s_off[mid] <= s) lo = mid; else hi = mid;
+        int lo;
+        if (uniform) {
+            // every arc draws `base` samples (ceil(2^64 / 1) wraps to 0, hence the case)
+            lo = A.base == 1 ? (int)s : (int)fastdiv32(s, A.base_magic);
+        } else {
+            lo = 0;
+            int hi = na;   // s_off[lo] <= s < s_off[hi]
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (s_off[mid] <= s) lo = mid; else hi = mid;
+            }
         }
         const uint32_t j = s - s_off[lo];
         int32_t pu, pv;
-        draw(A, a0 + lo, j, s_src[lo], s_dst[lo], &pu, &pv);
+        draw(A, s_rlut, s_rmagic, a0 + lo, j, s_src[lo], s_dst[lo], &pu, &pv);
         if (MODE == 0) {
             u1[out0 + s] = pu;
             v1[out0 + s] = pv;
@@ -684,8 +765,35 @@ WalkArgs make_walk_args(const GraphView &g, const SamplerSpec &sp) {
     A.thr_frac = sp.thr_frac;
     A.T = sp.T;
     A.B = sp.B;
+    A.vinfo = nullptr;
     for (int i = 0; i < 16; ++i) A.thr[i] = sp.thr[i];
+    uint32_t k0 = sp.k0, k1 = sp.k1;
+    for (int r = 0; r < 10; ++r) {
+        A.rk[2 * r] = k0;
+        A.rk[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    A.T_eff = 0;
+    for (int i = 0; i + 1 < sp.T; ++i)
+        if (sp.thr[i] < (1ull << 32)) A.thr32[A.T_eff++] = (uint32_t)sp.thr[i];
+    for (int i = A.T_eff; i < 16; ++i) A.thr32[i] = 0xFFFFFFFFu;
+    A.base_magic = sp.base > 0 ? (~0ull) / sp.base + 1ull : 0ull;
+    A.rmagic[0] = 0;
+    for (int r = 1; r <= 16; ++r) A.rmagic[r] = (~0ull) / (uint64_t)r + 1ull;
     return A;
+}
+
+// Builds the per-vertex walk records into the workspace.
+int attach_vinfo(Workspace &ws, const GraphView &g, WalkArgs *A, cudaStream_t st) {
+    uint4 *vi = nullptr;
+    LNE_TRY(ws.get("walk.vinfo", (size_t)std::max<int64_t>(g.n, 1), &vi));
+    LNE_TRACE("build_vinfo", st);
+    build_vinfo_kernel<<<(unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(g.n, 1), 256), 152 * 8), 256, 0, st>>>(
+        g.indptr, g.n, vi);
+    LNE_LAUNCH_CHECK();
+    A->vinfo = vi;
+    return 0;
 }
 
 // Tile size: aim for ~32k samples per CTA but at least ~8 CTAs per SM overall.
@@ -787,6 +895,7 @@ int sample_pairs(Workspace &ws, const GraphView &g, const SamplerSpec &sp, int64
     *count = 0;
     if (a0 == a1) return 0;
     WalkArgs A = make_walk_args(g, sp);
+    LNE_TRY(attach_vinfo(ws, g, &A, st));
     const int tile_arcs = choose_tile_arcs(a1 - a0, (double)sp.base + 0.5);
     int64_t *tile_off = nullptr;
     int64_t total = 0;
@@ -821,6 +930,7 @@ int sample_and_reduce(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
     if (2 * sp.B > 32)
         return fail(LNE_ERR_UNSUPPORTED, "graphs with more than 65536 vertices need 64-bit pair keys (not in this build)");
     WalkArgs A = make_walk_args(g, sp);
+    LNE_TRY(attach_vinfo(ws, g, &A, st));
     const int tile_arcs = choose_tile_arcs(g.nnz, (double)sp.base + 0.5);
     int64_t *tile_off = nullptr;
     int64_t total = 0;
@@ -1002,6 +1112,7 @@ int sample_table(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Table
     tb->nt = nt;
     LNE_CUDA_TRY(cudaMemsetAsync(tb->T, 0, sizeof(uint32_t) * (size_t)(ld * ld), st));
     WalkArgs A = make_walk_args(g, sp);
+    LNE_TRY(attach_vinfo(ws, g, &A, st));
     const int tile_arcs = choose_tile_arcs(g.nnz, (double)sp.base + 0.5);
     const int64_t ntiles = ceil_div(g.nnz, tile_arcs);
     const int smem = walk_smem_bytes(tile_arcs, 0);

@@ -5,9 +5,15 @@
 //     fused into the epilogue:  out = alpha * rs_i (A X)_i + b1 E1 + b2 E2 + b3 E3,
 //     optionally F += gamma * out and G = X0 - F.
 //
-// One warp per row; lane l owns columns l, l+32, ...; the row's column indices
-// and values are read 32 at a time and broadcast by shuffles. Rows are
-// summed in CSR order, so results are deterministic.
+// Main path (column count a multiple of 4): nonzero-balanced ("merge") SpMM.
+// Warp w owns nonzeros [w W, (w + 1) W); lane l gathers columns 4l..4l+3
+// (+128 t) of each referenced X row with 16-byte loads. A row wholly inside one
+// warp's slice is finished there; a row crossing slice boundaries leaves its
+// partial sums in a carry buffer, and a fix-up kernel adds them in slice order.
+// Every sum has a fixed order, so results are deterministic and independent of
+// the degree distribution's skew.
+// Fallback (other column counts): one warp per row, lane l owns columns l,
+// l+32, ...; rows longer than 512 nonzeros get a whole CTA.
 #include "runtime.h"
 
 namespace lne {
@@ -129,6 +135,166 @@ __global__ void __launch_bounds__(kCtaWarps * 32) spmm_cta_kernel(int64_t n, con
     }
 }
 
+// ---------------------------------------------------------------------------
+// merge path
+// ---------------------------------------------------------------------------
+template <int NV>
+struct Acc4 {
+    float4 v[NV];
+};
+
+template <int NV, bool WEIGHTED>
+__device__ __forceinline__ void gather4(const int32_t *__restrict__ indices, const float *__restrict__ vals,
+                                        int64_t p, int cnt, const float4 *__restrict__ X4, int64_t ldx4, int c4,
+                                        int lane, Acc4<NV> &acc) {
+    const int col = lane < cnt ? __ldg(indices + p + lane) : 0;
+    float v = 0.f;
+    if (WEIGHTED) v = lane < cnt ? __ldg(vals + p + lane) : 0.f;
+#pragma unroll 4
+    for (int k = 0; k < cnt; ++k) {
+        const int ck = __shfl_sync(0xffffffffu, col, k);
+        const float vk = WEIGHTED ? __shfl_sync(0xffffffffu, v, k) : 1.f;
+        const float4 *xr = X4 + (int64_t)ck * ldx4;
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            const int q = lane + 32 * t;
+            if (q < c4) {
+                const float4 x = __ldg(xr + q);
+                if (WEIGHTED) {
+                    acc.v[t].x = fmaf(vk, x.x, acc.v[t].x);
+                    acc.v[t].y = fmaf(vk, x.y, acc.v[t].y);
+                    acc.v[t].z = fmaf(vk, x.z, acc.v[t].z);
+                    acc.v[t].w = fmaf(vk, x.w, acc.v[t].w);
+                } else {
+                    acc.v[t].x += x.x;
+                    acc.v[t].y += x.y;
+                    acc.v[t].z += x.z;
+                    acc.v[t].w += x.w;
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ float epi1(float a, float rs, int64_t e, const SpmmEpilogue &ep, float *__restrict__ y) {
+    float o = rs * a;
+    if (ep.E1) o = fmaf(ep.b1, ep.E1[e], o);
+    if (ep.E2) o = fmaf(ep.b2, ep.E2[e], o);
+    if (ep.E3) o = fmaf(ep.b3, ep.E3[e], o);
+    if (ep.store) *y = o;
+    if (ep.F) {
+        const float f = fmaf(ep.gamma, o, ep.F[e]);
+        ep.F[e] = f;
+        if (ep.G) ep.G[e] = ep.X0[e] - f;
+    }
+    return o;
+}
+
+template <int NV>
+__device__ __forceinline__ void epilogue4(int64_t i, int64_t deg, const Acc4<NV> &acc, int lane, int c4,
+                                          float *__restrict__ Y, int64_t ldy, const SpmmEpilogue &ep) {
+    float rs = ep.alpha;
+    if (ep.dinv) rs = deg > 0 ? ep.alpha / (float)deg : 0.f;
+#pragma unroll
+    for (int t = 0; t < NV; ++t) {
+        const int q = lane + 32 * t;
+        if (q >= c4) continue;
+        const int64_t e = i * ep.lde + 4 * q;
+        float *y = Y + i * ldy + 4 * q;
+        epi1(acc.v[t].x, rs, e + 0, ep, y + 0);
+        epi1(acc.v[t].y, rs, e + 1, ep, y + 1);
+        epi1(acc.v[t].z, rs, e + 2, ep, y + 2);
+        epi1(acc.v[t].w, rs, e + 3, ep, y + 3);
+    }
+}
+
+__device__ __forceinline__ int64_t row_of(const int64_t *__restrict__ indptr, int64_t n, int64_t p) {
+    int64_t lo = 0, hi = n;   // last row with indptr[row] <= p
+    while (hi - lo > 1) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (__ldg(indptr + mid) <= p) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <int NV, bool WEIGHTED>
+__global__ void __launch_bounds__(256) spmm_merge_kernel(int64_t n, int64_t nnz, const int64_t *__restrict__ indptr,
+                                                         const int32_t *__restrict__ indices,
+                                                         const float *__restrict__ vals, const float4 *__restrict__ X4,
+                                                         int64_t ldx4, int c4, float *__restrict__ Y, int64_t ldy,
+                                                         SpmmEpilogue ep, int64_t W, int64_t nwarps,
+                                                         float4 *__restrict__ carry, int64_t *__restrict__ carry_row) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (w >= nwarps) return;
+    const int64_t p0 = w * W, p1 = imin64(p0 + W, nnz);
+    if (lane == 0) {   // slots left from an earlier product must not be read
+        carry_row[w * 2] = -1;
+        carry_row[w * 2 + 1] = -1;
+    }
+    int64_t r = row_of(indptr, n, p0);
+    // skip empty rows sharing the start offset
+    while (r + 1 < n && __ldg(indptr + r + 1) <= p0) ++r;
+    int64_t p = p0;
+    while (p < p1) {
+        const int64_t rs = __ldg(indptr + r), re = __ldg(indptr + r + 1);
+        const int64_t e = imin64(re, p1);
+        Acc4<NV> acc;
+#pragma unroll
+        for (int t = 0; t < NV; ++t) acc.v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t q = p; q < e; q += 32)
+            gather4<NV, WEIGHTED>(indices, vals, q, (int)imin64(32, e - q), X4, ldx4, c4, lane, acc);
+        if (rs >= p0 && re <= p1) {
+            epilogue4<NV>(r, re - rs, acc, lane, c4, Y, ldy, ep);
+        } else {
+            const int slot = rs < p0 ? 0 : 1;
+            float4 *dst = carry + (w * 2 + slot) * (int64_t)(NV * 32);
+#pragma unroll
+            for (int t = 0; t < NV; ++t)
+                if (lane + 32 * t < c4) dst[lane + 32 * t] = acc.v[t];
+            if (lane == 0) carry_row[w * 2 + slot] = r;
+        }
+        p = e;
+        ++r;
+        while (p < p1 && r + 1 < n && __ldg(indptr + r + 1) <= p) ++r;   // empty rows
+    }
+}
+
+// Rows that are empty or cross slice boundaries: sum the partials in slice order.
+template <int NV>
+__global__ void __launch_bounds__(256) spmm_fixup_kernel(int64_t n, const int64_t *__restrict__ indptr, int c4,
+                                                         float *__restrict__ Y, int64_t ldy, SpmmEpilogue ep, int64_t W,
+                                                         const float4 *__restrict__ carry,
+                                                         const int64_t *__restrict__ carry_row) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
+        const int64_t rs = indptr[r], re = indptr[r + 1];
+        Acc4<NV> acc;
+#pragma unroll
+        for (int t = 0; t < NV; ++t) acc.v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (re > rs) {
+            const int64_t w0 = rs / W, w1 = (re - 1) / W;
+            if (w0 == w1) continue;   // finished by its warp
+            for (int64_t w = w0; w <= w1; ++w) {
+                const int slot = carry_row[w * 2] == r ? 0 : 1;
+                const float4 *src = carry + (w * 2 + slot) * (int64_t)(NV * 32);
+#pragma unroll
+                for (int t = 0; t < NV; ++t) {
+                    if (lane + 32 * t < c4) {
+                        const float4 x = src[lane + 32 * t];
+                        acc.v[t].x += x.x;
+                        acc.v[t].y += x.y;
+                        acc.v[t].z += x.z;
+                        acc.v[t].w += x.w;
+                    }
+                }
+            }
+        }
+        epilogue4<NV>(r, re - rs, acc, lane, c4, Y, ldy, ep);
+    }
+}
+
 template <bool WEIGHTED>
 int launch_spmm(int64_t n, const int64_t *indptr, const int32_t *indices, const float *vals,
                 const float *X, int64_t ldx, int c, float *Y, int64_t ldy, const SpmmEpilogue &ep,
@@ -163,16 +329,65 @@ int launch_spmm(int64_t n, const int64_t *indptr, const int32_t *indices, const 
     return 0;
 }
 
+bool merge_ok(const float *X, int64_t ldx, int c, int64_t ldy, const SpmmEpilogue &ep) {
+    return c % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 && ep.lde % 4 == 0 && c <= 256 &&
+           (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+}
+
+template <bool WEIGHTED>
+int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, const int32_t *indices,
+                 const float *vals, const float *X, int64_t ldx, int c, float *Y, int64_t ldy, const SpmmEpilogue &ep,
+                 cudaStream_t st) {
+    if (n <= 0) return 0;
+    const int c4 = c / 4;
+    const int nv = (c4 + 31) / 32;
+    // ~8 waves of warps, 32..1024 nonzeros each
+    int64_t W = nnz / (152 * 48 * 8);
+    W = std::max<int64_t>(32, std::min<int64_t>(1024, (W + 31) / 32 * 32));
+    const int64_t nwarps = std::max<int64_t>(1, ceil_div(nnz, W));
+    float4 *carry = nullptr;
+    int64_t *carry_row = nullptr;
+    LNE_TRY(ws.get("spmm.carry", (size_t)nwarps * 2 * nv * 32, &carry));
+    LNE_TRY(ws.get("spmm.carry_row", (size_t)nwarps * 2, &carry_row));
+    const unsigned mblocks = (unsigned)ceil_div(nwarps, 8);
+    const unsigned fblocks = (unsigned)std::min<int64_t>(ceil_div(n, 8), 152 * 32);
+    const float4 *X4 = reinterpret_cast<const float4 *>(X);
+    LNE_TRACE(WEIGHTED ? "spmm" : "graph_spmm", st);
+#define LNE_MERGE_CASE(K)                                                                                  \
+    case K:                                                                                                \
+        if (nnz > 0)                                                                                       \
+            spmm_merge_kernel<K, WEIGHTED><<<mblocks, 256, 0, st>>>(n, nnz, indptr, indices, vals, X4, ldx / 4, \
+                                                                     c4, Y, ldy, ep, W, nwarps, carry,     \
+                                                                     carry_row);                           \
+        spmm_fixup_kernel<K><<<fblocks, 256, 0, st>>>(n, indptr, c4, Y, ldy, ep, W, carry, carry_row);      \
+        break;
+    switch (nv) {
+        LNE_MERGE_CASE(1)
+        LNE_MERGE_CASE(2)
+        default:
+            return fail(LNE_ERR_UNSUPPORTED, "SpMM supports at most 256 dense columns");
+    }
+#undef LNE_MERGE_CASE
+    LNE_LAUNCH_CHECK();
+    ::lne::count_launch();
+    return 0;
+}
+
 }  // namespace
 
-int spmm(const CsrView &M, const float *X, int64_t ldx, int c, float *Y, int64_t ldy, cudaStream_t st) {
+int spmm(Workspace &ws, const CsrView &M, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
+         cudaStream_t st) {
     SpmmEpilogue ep;
     ep.lde = ldy;
+    if (merge_ok(X, ldx, c, ldy, ep))
+        return launch_merge<true>(ws, M.n, M.nnz, M.indptr, M.indices, M.data, X, ldx, c, Y, ldy, ep, st);
     return launch_spmm<true>(M.n, M.indptr, M.indices, M.data, X, ldx, c, Y, ldy, ep, st);
 }
 
-int graph_spmm(const GraphView &g, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
+int graph_spmm(Workspace &ws, const GraphView &g, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
                const SpmmEpilogue &ep, cudaStream_t st) {
+    if (merge_ok(X, ldx, c, ldy, ep))
+        return launch_merge<false>(ws, g.n, g.nnz, g.indptr, g.indices, nullptr, X, ldx, c, Y, ldy, ep, st);
     return launch_spmm<false>(g.n, g.indptr, g.indices, nullptr, X, ldx, c, Y, ldy, ep, st);
 }
 
