@@ -372,12 +372,13 @@ def run_ours(args):
 
 def run_case(args):
     """A small, repeatable run of one stage for profilers (ncu): the bench graph
-    with S/10 samples; each stage runs `--steps` times."""
+    with S / --scale samples (the dense count table keeps the footprint under
+    1 GB at any S); each stage runs `--steps` times."""
     import torch
     from paper_2302_07084_gb300 import lne
     g, params = workload()
     params = dict(params)
-    params["samples"] = params["samples"] / 10.0
+    params["samples"] = params["samples"] / args.scale
     P = lne.Params(**params)
     ctx = lne.Context(0)
     dg = lne.DeviceGraph(g.indptr, g.indices)
@@ -404,6 +405,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=10.0, help="sample-count divisor of --case runs")
     ap.add_argument("--case", choices=["sparsifier", "rsvd", "propagate", "embed"], default=None,
                     help="run one stage on a reduced workload (for profilers) instead of the benchmark")
     args = ap.parse_args()

@@ -324,27 +324,35 @@ __device__ __forceinline__ int circle_player(int pos, int round, int m) {
     return pos == 0 ? 0 : ((pos - 1 + round) % (m - 1)) + 1;
 }
 
+// Column stride of the shared-memory matrices: = 8 (mod 32), so the four
+// 8-thread pair groups of a warp hit distinct banks.
+__host__ __device__ __forceinline__ int jac_ld(int c) { return ((c + 23) / 32) * 32 + 8; }
+
+// Jacobi acts on the columns of A = R^T (for a triangular factor this
+// converges in fewer sweeps than on R): R^T W = Z Sigma with W the accumulated
+// rotations, so R = W Sigma Z^T -- left singular vectors U = W, right ones
+// V = normalised columns of R^T W.
 __global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__restrict__ Uout,
                                 double *__restrict__ Vout, int max_sweeps, int *__restrict__ sweeps_out) {
     extern __shared__ float js[];
-    float *A = js;            // column-major: A[j * c + i]
-    float *V = js + c * c;    // column-major
+    const int ldc = jac_ld(c);
+    float *A = js;              // column j at A + j * ldc
+    float *V = js + c * ldc;    // accumulated rotations
     __shared__ float red[32];
     __shared__ int s_done;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nthreads = blockDim.x;
     for (int e = tid; e < c * c; e += nthreads) {
         int i = e / c, j = e - i * c;
-        A[j * c + i] = (float)R[e];
-        V[j * c + i] = (i == j) ? 1.f : 0.f;
+        A[i * ldc + j] = (float)R[e];   // column i of R^T = row i of R
+        V[j * ldc + i] = (i == j) ? 1.f : 0.f;
     }
     __syncthreads();
     const int m = c + (c & 1);
     const int pairs = m / 2;
     const int pi = tid / kJacTPP, sub = tid % kJacTPP;
-    // FP32 round-off floor of |a_p . a_q| / (|a_p| |a_q|) is about c * 2^-24; the
-    // FP64 refinement that follows takes the vectors the rest of the way.
-    const float tol = fmaxf(4.f * (float)c * 5.9604645e-8f, 1e-6f);
+    // FP32 round-off floor of |a_p . a_q| / (|a_p| |a_q|) is about c * 2^-24
+    const float tol = 4.f * (float)c * 5.9604645e-8f;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         float local_max = 0.f;
@@ -362,7 +370,7 @@ __global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__r
             const bool active = pi < pairs && q < c;
             float al = 0.f, be = 0.f, ga = 0.f;
             if (active) {
-                const float *ap = A + p * c, *aq = A + q * c;
+                const float *ap = A + p * ldc, *aq = A + q * ldc;
                 for (int i = sub; i < c; i += kJacTPP) {
                     float x = ap[i], y = aq[i];
                     al = fmaf(x, x, al);
@@ -378,14 +386,14 @@ __global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__r
                 ga += __shfl_xor_sync(0xffffffffu, ga, off);
             }
             if (active && ga != 0.f && al > 0.f && be > 0.f) {
-                float rel = fabsf(ga) / sqrtf(al * be);
+                float rel = fabsf(ga) * rsqrtf(al * be);
                 local_max = fmaxf(local_max, rel);
                 if (rel > tol) {
                     float zeta = (be - al) / (2.f * ga);
                     float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
                     float cs = rsqrtf(1.f + t * t);
                     float sn = cs * t;
-                    float *ap = A + p * c, *aq = A + q * c, *vp = V + p * c, *vq = V + q * c;
+                    float *ap = A + p * ldc, *aq = A + q * ldc, *vp = V + p * ldc, *vq = V + q * ldc;
                     for (int i = sub; i < c; i += kJacTPP) {
                         float x = ap[i], y = aq[i];
                         ap[i] = cs * x - sn * y;
@@ -413,18 +421,17 @@ __global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__r
             break;
         }
     }
-    // column norms of R V are the singular values; U = (R V) Sigma^-1
     __shared__ float s_nrm[kMaxSmemC + 1];
     for (int j = tid; j < c; j += nthreads) {
         float t = 0.f;
-        for (int i = 0; i < c; ++i) t = fmaf(A[j * c + i], A[j * c + i], t);
+        for (int i = 0; i < c; ++i) t = fmaf(A[j * ldc + i], A[j * ldc + i], t);
         s_nrm[j] = t > 0.f ? rsqrtf(t) : 0.f;
     }
     __syncthreads();
     for (int e = tid; e < c * c; e += nthreads) {
         int i = e / c, j = e - i * c;
-        Vout[e] = (double)V[j * c + i];                 // row-major, column j = j-th right vector
-        Uout[e] = (double)(A[j * c + i] * s_nrm[j]);    // column j = j-th left vector
+        Uout[e] = (double)V[j * ldc + i];                 // left vectors of R: the rotations
+        Vout[e] = (double)(A[j * ldc + i] * s_nrm[j]);    // right vectors: normalised R^T W
     }
     if (tid == 0 && sweeps_out) *sweeps_out = sweep;
 }
@@ -475,9 +482,9 @@ __device__ double block_sum(double v, double *red) {
 // taken as (p_ij / 2, q_ij / 2) when |s_i - s_j| <= delta (near-equal values),
 // delta = 2 (||offdiag T|| + max|s| (||P|| + ||Q||)). A itself is never squared,
 // so the accuracy does not depend on the condition number of A.
-__global__ void svd_oa_update_kernel(const double *__restrict__ P, const double *__restrict__ Q,
-                                     const double *__restrict__ T, int c, double *__restrict__ F,
-                                     double *__restrict__ Gm, double *__restrict__ sig) {
+__global__ void svd_oa_norms_kernel(const double *__restrict__ P, const double *__restrict__ Q,
+                                    const double *__restrict__ T, int c, double *__restrict__ sig,
+                                    double *__restrict__ delta_out) {
     __shared__ double red[32];
     __shared__ double s_sig[256];
     const int tid = threadIdx.x;
@@ -496,7 +503,6 @@ __global__ void svd_oa_update_kernel(const double *__restrict__ P, const double 
     o2 = block_sum(o2, red);
     p2 = block_sum(p2, red);
     q2 = block_sum(q2, red);
-    // block max of smax
     {
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -508,31 +514,36 @@ __global__ void svd_oa_update_kernel(const double *__restrict__ P, const double 
         for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m = fmax(m, red[w]);
         smax = m;
     }
-    const double delta = 2.0 * (sqrt(o2) + smax * (sqrt(p2) + sqrt(q2)));
-    for (int e = tid; e < c * c; e += blockDim.x) {
-        const int i = e / c, j = e - i * c;
-        const double pij = P[e], qij = Q[e];
-        double f, g;
-        if (i == j) {
-            f = 0.5 * pij;
-            g = 0.5 * qij;
-        } else {
-            const double si = s_sig[i], sj = s_sig[j];
-            if (fabs(sj - si) > delta) {
-                const double r1 = T[e] + pij * sj;
-                const double r2 = T[j * c + i] + qij * sj;
-                const double det = (sj - si) * (sj + si);
-                f = (sj * r1 + si * r2) / det;
-                g = (si * r1 + sj * r2) / det;
-            } else {
-                f = 0.5 * pij;
-                g = 0.5 * qij;
+    for (int i = tid; i < c; i += blockDim.x) sig[i] = s_sig[i];
+    if (tid == 0) *delta_out = 2.0 * (sqrt(o2) + smax * (sqrt(p2) + sqrt(q2)));
+}
+
+// F, G of the update, one element per thread (the divisions spread over the GPU).
+__global__ void svd_oa_fg_kernel(const double *__restrict__ P, const double *__restrict__ Q,
+                                 const double *__restrict__ T, int c, const double *__restrict__ sig,
+                                 const double *__restrict__ delta_in, double *__restrict__ F, double *__restrict__ Gm) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= c * c) return;
+    const int i = e / c, j = e - i * c;
+    const double pij = P[e], qij = Q[e];
+    double f = 0.5 * pij, g = 0.5 * qij;
+    if (i != j) {
+        const double si = sig[i], sj = sig[j];
+        if (fabs(sj - si) > *delta_in) {
+            const double r1 = T[e] + pij * sj;
+            const double r2 = T[j * c + i] + qij * sj;
+            const double inv = 1.0 / ((sj - si) * (sj + si));
+            const double ff = (sj * r1 + si * r2) * inv;
+            const double gg = (si * r1 + sj * r2) * inv;
+            // outside the first-order regime this step only restores orthogonality
+            if (fabs(ff) <= 0.25 && fabs(gg) <= 0.25) {
+                f = ff;
+                g = gg;
             }
         }
-        F[e] = f;
-        Gm[e] = g;
     }
-    for (int i = tid; i < c; i += blockDim.x) sig[i] = s_sig[i];
+    F[e] = f;
+    Gm[e] = g;
 }
 
 // P := I - P and Q := I - Q in place (from the Gram products U^T U, V^T V).
@@ -653,6 +664,8 @@ static int gram(Workspace &ws, const float *Y, int64_t n, int c, int64_t ld, dou
     double *partial = nullptr;
     LNE_TRY(ws.get("gram.partial", (size_t)nblk * cp * cp, &partial));
     const int smem = kGramRows * cp * 8;
+    if (smem > 48 * 1024)
+        LNE_CUDA_TRY(cudaFuncSetAttribute(gram_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     {
         LNE_TRACE("gram_partial", st);
         gram_partial_kernel<<<(unsigned)nblk, threads, smem, st>>>(Y, n, c, ld, rows_per, partial);
@@ -766,16 +779,18 @@ int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma,
     LNE_TRY(ws.get("svd.F", cc, &F));
     LNE_TRY(ws.get("svd.G", cc, &Gm));
     LNE_TRY(ws.get("svd.sg", (size_t)c, &sg));
+    double *dl = nullptr;
+    LNE_TRY(ws.get("svd.delta", 1, &dl));
     LNE_TRY(ws.get("svd.sweeps", 1, &sweeps));
     // starting point: FP32 one-sided Jacobi on R (U, V in FP64 storage)
     const int m = c + (c & 1);
     const int threads = std::max(32, std::min(1024, (m / 2 * kJacTPP + 31) / 32 * 32));
-    const int smem = 2 * c * c * 4;
+    const int smem = 2 * c * jac_ld(c) * 4;
     if (smem > 48 * 1024)
         LNE_CUDA_TRY(cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     {
         LNE_TRACE("jacobi32", st);
-        jacobi32_kernel<<<1, threads, smem, st>>>(R, c, U, V, 10, sweeps);
+        jacobi32_kernel<<<1, threads, smem, st>>>(R, c, U, V, 20, sweeps);
         LNE_LAUNCH_CHECK();
     }
     // FP64 refinement of the SVD of R itself (quadratic convergence; the FP32
@@ -789,7 +804,9 @@ int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma,
             LNE_TRACE("svd_oa_update", st);
             svd_ia_kernel_prep<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(P, Q, c);
             LNE_LAUNCH_CHECK();
-            svd_oa_update_kernel<<<1, 256, 0, st>>>(P, Q, T, c, F, Gm, sg);
+            svd_oa_norms_kernel<<<1, 256, 0, st>>>(P, Q, T, c, sg, dl);
+            LNE_LAUNCH_CHECK();
+            svd_oa_fg_kernel<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(P, Q, T, c, sg, dl, F, Gm);
             LNE_LAUNCH_CHECK();
         }
         LNE_TRY(dgemm_small(U, false, F, false, U, U2, c, st));       // U2 = U + U F

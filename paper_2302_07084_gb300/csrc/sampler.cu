@@ -38,11 +38,14 @@ namespace {
 constexpr int kBucketBits = 15;                 // keys per reduce bucket = 2^15
 constexpr int kMaxSmemBuckets = 12288;          // walk/scatter histogram capacity
 constexpr int kWalkThreads = 256;
+constexpr int kWalkWarps = kWalkThreads / 32;
+constexpr int kChunk = 2048;                     // samples ranked by window length at a time
 
 struct WalkArgs {
     const int64_t *indptr;
     const int32_t *indices;
     const uint4 *vinfo;           // per-vertex walk record (see build_vinfo_kernel)
+    const uint4 *arcrec;          // per-arc record of the arc's head vertex
     int64_t n;
     int64_t n_arcs;
     uint32_t k0, k1;
@@ -98,8 +101,8 @@ __device__ __forceinline__ uint32_t fastdiv32(uint32_t a, uint64_t M) {
     return (uint32_t)__umul64hi(M, (uint64_t)a);
 }
 
-// Per-vertex walk record: x = (offset bits 0..31, offset bits 32..39 | degree
-// << 8, M lo, M hi) with M = ceil(2^64 / degree). Degrees of 2^24 and more are
+// Per-vertex walk record {offset bits 0..31, offset bits 32..39 | degree << 8,
+// m = floor(2^32 / degree) (0 for degree < 2), 0}. Degrees of 2^24 and more are
 // marked 0xFFFFFF and read from indptr.
 __global__ void build_vinfo_kernel(const int64_t *__restrict__ indptr, int64_t n, uint4 *__restrict__ vinfo) {
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
@@ -107,9 +110,21 @@ __global__ void build_vinfo_kernel(const int64_t *__restrict__ indptr, int64_t n
         const int64_t off = indptr[x];
         const int64_t deg = indptr[x + 1] - off;
         const uint32_t dfield = deg >= 0xFFFFFF ? 0xFFFFFFu : (uint32_t)deg;
-        const uint64_t M = deg > 0 && deg < (1ll << 32) ? (~0ull) / (uint64_t)deg + 1ull : 0ull;
-        vinfo[x] = make_uint4((uint32_t)off, (uint32_t)((off >> 32) & 0xFF) | (dfield << 8), (uint32_t)M,
-                              (uint32_t)(M >> 32));
+        const uint32_t m = (deg >= 2 && deg < 0xFFFFFF) ? (uint32_t)((1ull << 32) / (uint64_t)deg) : 0u;
+        vinfo[x] = make_uint4((uint32_t)off, (uint32_t)((off >> 32) & 0xFF) | (dfield << 8), m, 0u);
+    }
+}
+
+// Per-arc record (16 bytes): for arc p -> v, {v, v's offset bits 0..31,
+// v's offset bits 32..39 | degree << 8, v's m}. A walk step reads the record of
+// the arc it takes and so learns the next vertex's offset, degree and
+// reciprocal in one 16-byte load: one dependent load per step.
+__global__ void build_arcrec_kernel(const int32_t *__restrict__ indices, int64_t nnz, const uint4 *__restrict__ vinfo,
+                                    uint4 *__restrict__ arcrec) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = indices[p];
+        const uint4 r = vinfo[v];
+        arcrec[p] = make_uint4((uint32_t)v, r.x, r.y, r.z);
     }
 }
 
@@ -123,30 +138,62 @@ __device__ __forceinline__ int32_t arc_source(const int64_t *__restrict__ indptr
     return (int32_t)lo;
 }
 
-// One walk step: x <- nbr(x)[w mod deg(x)] (Sec. 4.2).
-__device__ __forceinline__ int32_t walk_step(const WalkArgs &A, int32_t x, uint32_t w) {
-    const uint4 rec = __ldg(A.vinfo + x);
-    uint32_t deg = rec.y >> 8;
-    int64_t off = (int64_t)rec.x | ((int64_t)(rec.y & 0xFF) << 32);
-    uint32_t j;
-    if (deg == 0xFFFFFFu) {
-        deg = (uint32_t)(__ldg(A.indptr + x + 1) - __ldg(A.indptr + x));
-        j = w % deg;
-    } else {
-        if (deg == 0) return x;   // only on graphs that break the contract
-        j = fastmod32(w, ((uint64_t)rec.w << 32) | rec.z, deg);
-    }
-    return __ldg(A.indices + off + j);
+// Walk state: the current vertex and its walk record.
+struct WalkCur {
+    int32_t x;
+    uint32_t off_lo, hidg, m;   // offset bits 0..31, offset bits 32..39 | degree << 8, floor(2^32 / degree)
+};
+
+__device__ __forceinline__ WalkCur walk_start(const WalkArgs &A, int32_t x) {
+    const uint4 r = __ldg(A.vinfo + x);
+    return WalkCur{x, r.x, r.y, r.z};
 }
 
-// One PathSampling draw (Algorithm 1) of sample j on arc (u -> v): word 0 of
-// counter (j, a_lo, a_hi, 0) picks r, word 1 the split sigma, word 2 is the
-// reserved coin, words 3.. drive the walk steps, u side first.
-__device__ __forceinline__ void draw(const WalkArgs &A, const uint8_t *__restrict__ rlut,
-                                     const uint64_t *__restrict__ rmagic, int64_t arc, uint32_t j, int32_t u,
-                                     int32_t v, int32_t *pu, int32_t *pv) {
-    const uint32_t c1 = (uint32_t)((uint64_t)arc & 0xFFFFFFFFu), c2 = (uint32_t)((uint64_t)arc >> 32);
-    const u32x4 b0 = philox_rk(u32x4{j, c1, c2, 0u}, A.rk);
+// w mod d for 2 <= d < 2^24 with m = floor(2^32 / d) (Barrett reduction):
+// q = floor(w m / 2^32) is the true quotient or one less, so one conditional
+// subtraction finishes the remainder.
+__device__ __forceinline__ uint32_t barrett_mod(uint32_t w, uint32_t m, uint32_t d) {
+    const uint32_t q = __umulhi(w, m);
+    uint32_t r = w - q * d;
+    return r >= d ? r - d : r;
+}
+
+// One walk step: x <- nbr(x)[w mod deg(x)] (Sec. 4.2), reading the taken
+// arc's record.
+__device__ __forceinline__ void walk_step(const WalkArgs &A, WalkCur &c, uint32_t w) {
+    uint32_t deg = c.hidg >> 8;
+    const int64_t off = (int64_t)c.off_lo | ((int64_t)(c.hidg & 0xFF) << 32);
+    if (deg == 0) return;   // only on graphs that break the contract
+    uint32_t j;
+    if (deg == 0xFFFFFFu) {
+        deg = (uint32_t)(__ldg(A.indptr + c.x + 1) - __ldg(A.indptr + c.x));
+        j = w % deg;
+    } else {
+        j = deg == 1 ? 0u : barrett_mod(w, c.m, deg);
+    }
+    const uint4 ra = __ldg(A.arcrec + off + j);
+    c = WalkCur{(int32_t)ra.x, ra.y, ra.z, ra.w};
+}
+
+// One PathSampling draw (Algorithm 1) of sample j on arc a = (u -> v), as a
+// small state machine. Words of counter
+// (j, a_lo, a_hi, blk): word 0 picks the window r (Algorithm 3), word 1 the
+// split sigma, word 2 is the reserved coin, words 3.. drive the walk steps,
+// sigma from u first, then r - 1 - sigma from v.
+struct Draw {
+    uint32_t j, c1, c2;
+    int steps, sigma;
+    u32x4 nb;            // current Philox block
+    WalkCur cur;
+    int32_t v, uend;
+};
+
+// Block 0 of the sample's stream: the window r, the split sigma and word 3.
+__device__ __forceinline__ void draw_head(const WalkArgs &A, const uint8_t *__restrict__ rlut,
+                                          const uint64_t *__restrict__ rmagic, int64_t arc, uint32_t j, int *r_out,
+                                          int *sigma_out, uint32_t *w3_out) {
+    const u32x4 b0 = philox_rk(u32x4{j, (uint32_t)((uint64_t)arc & 0xFFFFFFFFu), (uint32_t)((uint64_t)arc >> 32), 0u},
+                               A.rk);
     // r = 1 + #{i : thr_i <= w0}; the table gives it unless a threshold falls
     // inside the word's 2^20-wide bucket
     const uint8_t e = rlut[b0.x >> 20];
@@ -155,30 +202,62 @@ __device__ __forceinline__ void draw(const WalkArgs &A, const uint8_t *__restric
         r = 1;
         for (int i = 0; i < A.T_eff; ++i) r += b0.x >= A.thr32[i] ? 1 : 0;
     }
-    const int sigma = (int)fastmod32(b0.y, rmagic[r], (uint32_t)r);
-    const int steps = r - 1;
-    int32_t x = u, uend = u;
-    u32x4 nb = b0;
-#pragma unroll
-    for (int k = 0; k < 15; ++k) {
-        if (k >= steps) break;
-        if (k == sigma) {
-            uend = x;
-            x = v;
-        }
-        const int widx = 3 + k;
-        if ((widx & 3) == 0) nb = philox_rk(u32x4{j, c1, c2, (uint32_t)(widx >> 2)}, A.rk);
-        const uint32_t w = (widx & 3) == 0 ? nb.x : (widx & 3) == 1 ? nb.y : (widx & 3) == 2 ? nb.z : nb.w;
-        x = walk_step(A, x, w);
-    }
-    if (sigma >= steps) {
-        *pu = x;
-        *pv = v;
-    } else {
-        *pu = uend;
-        *pv = x;
+    *r_out = r;
+    *sigma_out = (int)fastmod32(b0.y, rmagic[r], (uint32_t)r);
+    *w3_out = b0.w;
+}
+
+// The draw's walk state from its head.
+__device__ __forceinline__ void draw_begin(const WalkArgs &A, int64_t arc, uint32_t j, int r, int sigma, uint32_t w3,
+                                           int32_t u, int32_t v, Draw &d) {
+    d.j = j;
+    d.c1 = (uint32_t)((uint64_t)arc & 0xFFFFFFFFu);
+    d.c2 = (uint32_t)((uint64_t)arc >> 32);
+    d.nb = u32x4{0u, 0u, 0u, w3};
+    d.steps = r - 1;
+    d.sigma = sigma;
+    d.v = v;
+    d.uend = u;
+    d.cur = walk_start(A, sigma == 0 && d.steps > 0 ? v : u);
+}
+
+// Step k (word 3 + k) of the draw, if it has one.
+template <int K>
+__device__ __forceinline__ void draw_step(const WalkArgs &A, Draw &d) {
+    if (K >= d.steps) return;
+    constexpr int widx = 3 + K;
+    if ((widx & 3) == 0) d.nb = philox_rk(u32x4{d.j, d.c1, d.c2, (uint32_t)(widx >> 2)}, A.rk);
+    const uint32_t w = (widx & 3) == 0 ? d.nb.x : (widx & 3) == 1 ? d.nb.y : (widx & 3) == 2 ? d.nb.z : d.nb.w;
+    walk_step(A, d.cur, w);
+    if (K + 1 == d.sigma && K + 1 < d.steps) {   // u side done: continue from v
+        d.uend = d.cur.x;
+        d.cur = walk_start(A, d.v);
     }
 }
+
+__device__ __forceinline__ void draw_end(const Draw &d, int32_t *pu, int32_t *pv) {
+    if (d.sigma >= d.steps) {   // every step on the u side (or none at all)
+        *pu = d.steps > 0 ? d.cur.x : d.uend;
+        *pv = d.v;
+    } else {
+        *pu = d.uend;
+        *pv = d.cur.x;
+    }
+}
+
+template <int K>
+struct StepAll {
+    __device__ __forceinline__ static void run(const WalkArgs &A, Draw &a, Draw &b, int kmax) {
+        if (K >= kmax) return;
+        draw_step<K>(A, a);
+        draw_step<K>(A, b);
+        StepAll<K + 1>::run(A, a, b, kmax);
+    }
+};
+template <>
+struct StepAll<15> {
+    __device__ __forceinline__ static void run(const WalkArgs &, Draw &, Draw &, int) {}
+};
 
 // In-place exclusive scan of s[0..n) in shared memory by one CTA; returns total.
 template <int BLOCK>
@@ -247,13 +326,16 @@ __global__ void __launch_bounds__(kWalkThreads) tile_counts_kernel(WalkArgs A, i
 // and count key buckets. MODE 2: add the pair into the dense count table
 // table[x * ld + y] (x <= y); `keys` is the table, ld = nb_smem.
 template <typename KeyT, int MODE>
-__global__ void __launch_bounds__(kWalkThreads, 5) walk_emit_kernel(
+__global__ void __launch_bounds__(kWalkThreads, 4) walk_emit_kernel(
     WalkArgs A, int64_t a_begin, int64_t a_end, int tile_arcs, const int64_t *__restrict__ tile_off,
     KeyT *__restrict__ keys, int32_t *__restrict__ u1, int32_t *__restrict__ v1,
     uint32_t *__restrict__ bucket_cnt, int nb_smem) {
     extern __shared__ uint32_t smem[];
     __shared__ uint8_t s_rlut[4096];
     __shared__ uint64_t s_rmagic[17];
+    __shared__ uint32_t s_upack[kChunk], s_uw3[kChunk], s_pack[kChunk], s_w3[kChunk];
+    __shared__ uint32_t s_wcnt[17 * kWalkWarps];
+
     uint32_t *s_off = smem;                                      // tile_arcs + 1
     int32_t *s_src = reinterpret_cast<int32_t *>(s_off + tile_arcs + 1);
     int32_t *s_dst = s_src + tile_arcs;
@@ -286,8 +368,8 @@ __global__ void __launch_bounds__(kWalkThreads, 5) walk_emit_kernel(
     __syncthreads();
     const int64_t out0 = tile_off ? tile_off[blockIdx.x] : 0;
     const bool uniform = A.thr_frac == 0;
-    for (uint32_t s = tid; s < total; s += kWalkThreads) {
-        int lo;
+    // sample s of the tile -> (arc within the tile, sample index j on that arc)
+    auto locate = [&](uint32_t s, int &lo, uint32_t &j) {
         if (uniform) {
             // every arc draws `base` samples (ceil(2^64 / 1) wraps to 0, hence the case)
             lo = A.base == 1 ? (int)s : (int)fastdiv32(s, A.base_magic);
@@ -295,13 +377,13 @@ __global__ void __launch_bounds__(kWalkThreads, 5) walk_emit_kernel(
             lo = 0;
             int hi = na;   // s_off[lo] <= s < s_off[hi]
             while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
+                const int mid = (lo + hi) >> 1;
                 if (s_off[mid] <= s) lo = mid; else hi = mid;
             }
         }
-        const uint32_t j = s - s_off[lo];
-        int32_t pu, pv;
-        draw(A, s_rlut, s_rmagic, a0 + lo, j, s_src[lo], s_dst[lo], &pu, &pv);
+        j = s - s_off[lo];
+    };
+    auto emit = [&](uint32_t s, int32_t pu, int32_t pv) {
         if (MODE == 0) {
             u1[out0 + s] = pu;
             v1[out0 + s] = pv;
@@ -316,6 +398,96 @@ __global__ void __launch_bounds__(kWalkThreads, 5) walk_emit_kernel(
             if (nb_smem > 0) atomicAdd(&s_hist[b], 1u);
             else atomicAdd(&bucket_cnt[b], 1u);
         }
+    };
+    // Chunks of kChunk samples. Phase 1 draws each sample's head and ranks the
+    // chunk by window length r: __match_any groups equal r within a warp, the
+    // group leader adds to the warp's row of a (warp x r) histogram, and one
+    // scan turns the histogram into positions. Phase 2 walks the samples in
+    // r order, so the lanes of a warp take the same number of steps.
+    const int lane = tid & 31, warp = tid >> 5;
+    for (uint32_t cb = 0; cb < total; cb += kChunk) {
+        const uint32_t cn = min((uint32_t)kChunk, total - cb);
+        for (int e = tid; e < 17 * kWalkWarps; e += kWalkThreads) s_wcnt[e] = 0;
+        __syncthreads();
+#pragma unroll 1
+        for (int t = 0; t < kChunk / kWalkThreads; ++t) {
+            const uint32_t idx = (uint32_t)t * kWalkThreads + tid;
+            int r = 0, sg = 0;
+            uint32_t w3 = 0;
+            if (idx < cn) {
+                int lo;
+                uint32_t j;
+                locate(cb + idx, lo, j);
+                draw_head(A, s_rlut, s_rmagic, a0 + lo, j, &r, &sg, &w3);
+            }
+            const unsigned grp = __match_any_sync(0xffffffffu, r);
+            const int leader = __ffs(grp) - 1;
+            uint32_t base = 0;
+            if (lane == leader) {
+                base = s_wcnt[r * kWalkWarps + warp];
+                s_wcnt[r * kWalkWarps + warp] = base + (uint32_t)__popc(grp);
+            }
+            base = __shfl_sync(0xffffffffu, base, leader);
+            const uint32_t lpos = base + (uint32_t)__popc(grp & ((1u << lane) - 1u));
+            s_upack[idx] = idx | ((uint32_t)r << 11) | ((uint32_t)sg << 16) | (lpos << 20);
+            s_uw3[idx] = w3;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // exclusive scan over (r, warp) in r-major order; r = 0 marks empty slots
+            uint32_t carry = 0;
+            for (int e0 = 0; e0 < 17 * kWalkWarps; e0 += 32) {
+                const int e = e0 + lane;
+                const uint32_t v = e < 17 * kWalkWarps ? s_wcnt[e] : 0u;
+                uint32_t x = v;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, x, off);
+                    if (lane >= off) x += y;
+                }
+                if (e < 17 * kWalkWarps) s_wcnt[e] = carry + x - v;
+                carry += __shfl_sync(0xffffffffu, x, 31);
+            }
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int t = 0; t < kChunk / kWalkThreads; ++t) {
+            const uint32_t idx = (uint32_t)t * kWalkThreads + tid;
+            const uint32_t pk = s_upack[idx];
+            const uint32_t r = (pk >> 11) & 31;
+            const uint32_t pos = s_wcnt[r * kWalkWarps + warp] + (pk >> 20);
+            s_pack[pos] = pk;
+            s_w3[pos] = s_uw3[idx];
+        }
+        __syncthreads();
+        // empty slots (r = 0) sort first: skip them. Two draws per thread,
+        // interleaved step by step (same r in a warp, two chains in flight).
+        const uint32_t first = s_wcnt[1 * kWalkWarps];
+        for (uint32_t q0 = first + tid; q0 < kChunk; q0 += 2 * kWalkThreads) {
+            const uint32_t q1 = q0 + kWalkThreads;
+            const bool has1 = q1 < kChunk;
+            const uint32_t pk0 = s_pack[q0], pk1 = s_pack[has1 ? q1 : q0];
+            const uint32_t s0 = cb + (pk0 & 0x7FFu), s1 = cb + (pk1 & 0x7FFu);
+            int lo0, lo1;
+            uint32_t j0, j1;
+            locate(s0, lo0, j0);
+            locate(s1, lo1, j1);
+            Draw d0, d1;
+            draw_begin(A, a0 + lo0, j0, (int)((pk0 >> 11) & 31), (int)((pk0 >> 16) & 15), s_w3[q0], s_src[lo0],
+                       s_dst[lo0], d0);
+            draw_begin(A, a0 + lo1, j1, (int)((pk1 >> 11) & 31), (int)((pk1 >> 16) & 15), s_w3[has1 ? q1 : q0],
+                       s_src[lo1], s_dst[lo1], d1);
+            if (!has1) d1.steps = 0;
+            StepAll<0>::run(A, d0, d1, max(d0.steps, d1.steps));
+            int32_t pu, pv;
+            draw_end(d0, &pu, &pv);
+            emit(s0, pu, pv);
+            if (has1) {
+                draw_end(d1, &pu, &pv);
+                emit(s1, pu, pv);
+            }
+        }
+        __syncthreads();
     }
     if (MODE == 1 && nb_smem > 0) {
         __syncthreads();
@@ -793,6 +965,15 @@ int attach_vinfo(Workspace &ws, const GraphView &g, WalkArgs *A, cudaStream_t st
         g.indptr, g.n, vi);
     LNE_LAUNCH_CHECK();
     A->vinfo = vi;
+    uint4 *ar = nullptr;
+    LNE_TRY(ws.get("walk.arcrec", (size_t)std::max<int64_t>(g.nnz, 1), &ar));
+    {
+        LNE_TRACE("build_arcrec", st);
+        build_arcrec_kernel<<<(unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(g.nnz, 1), 256), 152 * 16), 256, 0,
+                              st>>>(g.indices, g.nnz, vi, ar);
+        LNE_LAUNCH_CHECK();
+    }
+    A->arcrec = ar;
     return 0;
 }
 
@@ -904,6 +1085,8 @@ int sample_pairs(Workspace &ws, const GraphView &g, const SamplerSpec &sp, int64
     if (total > capacity) return fail(LNE_ERR_INVALID, "output capacity too small for the sampled pairs");
     const int64_t ntiles = ceil_div(a1 - a0, tile_arcs);
     const int smem = walk_smem_bytes(tile_arcs, 0);
+    // dynamic shared memory comes on top of the kernel's static tables
+    LNE_CUDA_TRY(cudaFuncSetAttribute(walk_emit_kernel<uint32_t, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     {
         LNE_TRACE("walk_emit", st);
         walk_emit_kernel<uint32_t, 0><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
@@ -951,9 +1134,8 @@ int sample_and_reduce(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
     const int64_t ntiles = ceil_div(g.nnz, tile_arcs);
     const int nb_smem = nb <= kMaxSmemBuckets ? nb : 0;
     const int smem = walk_smem_bytes(tile_arcs, nb_smem);
-    if (smem > 48 * 1024)
-        LNE_CUDA_TRY(cudaFuncSetAttribute(walk_emit_kernel<uint32_t, 1>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    // dynamic shared memory comes on top of the kernel's static tables
+    LNE_CUDA_TRY(cudaFuncSetAttribute(walk_emit_kernel<uint32_t, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     {
         LNE_TRACE("walk_emit", st);
         walk_emit_kernel<uint32_t, 1><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
@@ -1116,8 +1298,7 @@ int sample_table(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Table
     const int tile_arcs = choose_tile_arcs(g.nnz, (double)sp.base + 0.5);
     const int64_t ntiles = ceil_div(g.nnz, tile_arcs);
     const int smem = walk_smem_bytes(tile_arcs, 0);
-    LNE_CUDA_TRY(cudaFuncSetAttribute(walk_emit_kernel<uint32_t, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      std::max(smem, 48 * 1024)));
+    LNE_CUDA_TRY(cudaFuncSetAttribute(walk_emit_kernel<uint32_t, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     LNE_TRACE("walk_count", st);
     walk_emit_kernel<uint32_t, 2><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
         A, 0, g.nnz, tile_arcs, nullptr, tb->T, nullptr, nullptr, nullptr, (int)ld);
