@@ -172,6 +172,22 @@ int lne_svd_small(lne_ctx *ctx, const double *R_dev, int32_t c, double *U_dev, d
                   void *stream);
 
 /*
+ * lne_svd_small without any device allocation. The paper has no counterpart:
+ * this entry point serves callers that must not allocate device memory when
+ * they call in (for example a process whose device memory is handed wholly to
+ * another allocator up front, or a service that forbids allocation after
+ * start-up). It needs no context: same arguments and results as lne_svd_small,
+ * c <= 160 (larger c returns LNE_ERR_INVALID and does nothing).
+ * Scratch: a fixed ~2 MB array in device memory that every GPU which loads the
+ * library holds until the process exits; its device address is looked up on
+ * the first call on each device, so make that first call before any stream
+ * capture. All calls on a device share the array: calls that overlap on the GPU
+ * (different streams, or different host threads) race and give wrong results.
+ * Returns LNE_OK or a negative LNE_ERR_* code (no message is kept).
+ */
+int lne_svd_small_noalloc(const double *R_dev, int32_t c, double *U_dev, double *sigma_dev, void *stream);
+
+/*
  * Fast randomized SVD (Algorithm 4) of the symmetric CSR M with the Gaussian
  * sketch of lne_gaussian_sketch(seed = p->seed): U_dev [n][d] (left singular
  * vectors, largest-magnitude entry of each column positive), sigma_dev [d]

@@ -77,6 +77,9 @@ struct Status {
 int cuda_fail(const char *what, cudaError_t e, const char *file, int line);
 // Process-wide count of kernel launches made by this library.
 void count_launch();
+// The calling thread's tracer (set by every context entry point; NULL = none).
+struct Tracer;
+void set_tracer(Tracer *t);
 // Named timing regions: when the calling context has tracing on, a region
 // records a CUDA event pair on the launching stream around its kernels.
 void trace_begin(const char *name, cudaStream_t st);

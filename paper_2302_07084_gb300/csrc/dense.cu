@@ -16,6 +16,7 @@
 //                  X = U Sigma^{1/2} (Sec. 3.2).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "runtime.h"
 
@@ -854,4 +855,86 @@ int sign_fix_embed(Workspace &ws, float *U, int64_t n, int d, int64_t ld, const 
     return 0;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the small SVD (lne_svd_small_noalloc).
+//
+// For callers that must not allocate device memory when they call in -- for
+// example a process whose device memory is wholly handed to another allocator
+// up front, or a latency-bound service that forbids allocation after start-up.
+// Its scratch (ten c x c FP64 matrices plus a few scalars, c <= 160: about
+// 2 MB) is a file-scope __device__ array that every GPU which loads this
+// library holds until the process exits. In host code the array's name is only
+// a stand-in for it, so its device address is looked up with
+// cudaGetSymbolAddress once per device, on that device's first call.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxC = 160;
+constexpr size_t kNoAllocMat = (size_t)kNoAllocMaxC * kNoAllocMaxC;
+constexpr size_t kNoAllocDoubles = 10 * kNoAllocMat + kNoAllocMaxC + 64;
+static __device__ __align__(256) double g_svd_scratch[kNoAllocDoubles];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+}  // namespace
 }  // namespace lne
+
+extern "C" int lne_svd_small_noalloc(const double *R_dev, int32_t c, double *U_dev, double *sigma_dev, void *stream) {
+    using namespace lne;
+    clear_message();
+    set_tracer(nullptr);   // no timing events (they would be created on demand)
+    if (!R_dev || !U_dev || !sigma_dev) return fail(LNE_ERR_INVALID, "NULL argument");
+    if (c < 1 || c > kNoAllocMaxC) return fail(LNE_ERR_INVALID, "lne_svd_small_noalloc needs 1 <= c <= 160");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e, __FILE__, __LINE__);
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(LNE_ERR_UNSUPPORTED, "device index too large");
+    double *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_svd_scratch);
+            if (e != cudaSuccess) return cuda_fail("cudaGetSymbolAddress", e, __FILE__, __LINE__);
+            g_noalloc_addr[dev] = static_cast<double *>(ptr);
+        }
+        base = g_noalloc_addr[dev];
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t cc = (size_t)c * c;
+    // every buffer below is fully written before it is read, so nothing left by
+    // an earlier call needs clearing
+    double *U = base, *U2 = base + cc, *V = base + 2 * cc, *V2 = base + 3 * cc, *W = base + 4 * cc,
+           *T = base + 5 * cc, *P = base + 6 * cc, *Q = base + 7 * cc, *F = base + 8 * cc, *Gm = base + 9 * cc;
+    double *sg = base + 10 * kNoAllocMat;
+    double *dl = sg + kNoAllocMaxC;
+    int *sweeps = reinterpret_cast<int *>(dl + 8);
+    const int m = c + (c & 1);
+    const int threads = std::max(32, std::min(1024, (m / 2 * kJacTPP + 31) / 32 * 32));
+    const int smem = 2 * c * jac_ld(c) * 4;
+    if (smem > 48 * 1024)
+        LNE_CUDA_TRY(cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    jacobi32_kernel<<<1, threads, smem, st>>>(R_dev, c, U, V, 20, sweeps);
+    LNE_LAUNCH_CHECK();
+    for (int it = 0; it < 4; ++it) {
+        LNE_TRY(dgemm_small(U, true, U, false, nullptr, P, c, st));
+        LNE_TRY(dgemm_small(V, true, V, false, nullptr, Q, c, st));
+        LNE_TRY(dgemm_small(R_dev, false, V, false, nullptr, W, c, st));
+        LNE_TRY(dgemm_small(U, true, W, false, nullptr, T, c, st));
+        svd_ia_kernel_prep<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(P, Q, c);
+        LNE_LAUNCH_CHECK();
+        svd_oa_norms_kernel<<<1, 256, 0, st>>>(P, Q, T, c, sg, dl);
+        LNE_LAUNCH_CHECK();
+        svd_oa_fg_kernel<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(P, Q, T, c, sg, dl, F, Gm);
+        LNE_LAUNCH_CHECK();
+        LNE_TRY(dgemm_small(U, false, F, false, U, U2, c, st));
+        LNE_TRY(dgemm_small(V, false, Gm, false, V, V2, c, st));
+        std::swap(U, U2);
+        std::swap(V, V2);
+    }
+    svd_finish_kernel<<<1, 256, 0, st>>>(U, sg, c, U_dev, sigma_dev);
+    LNE_LAUNCH_CHECK();
+    return LNE_OK;
+}

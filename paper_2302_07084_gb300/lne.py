@@ -28,7 +28,7 @@ EXPORTED = [
     "lne_sample_pairs", "lne_sparsifier_counts", "lne_sparsifier_csr", "lne_gaussian_sketch",
     "lne_spmm", "lne_cholqr2", "lne_rsvd", "lne_propagate", "lne_embed",
     "lne_kernel_launches", "lne_trace_enable", "lne_trace_read", "lne_set_option",
-    "lne_svd_small",
+    "lne_svd_small", "lne_svd_small_noalloc",
 ]
 OPT_AGGREGATION = 1
 AGG_AUTO, AGG_TABLE, AGG_BUCKET = 0, 1, 2
@@ -103,6 +103,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lne_trace_enable.argtypes = [vp, ctypes.c_int]
     L.lne_set_option.argtypes = [vp, ctypes.c_int, i64]
     L.lne_svd_small.argtypes = [vp, vp, i32, vp, vp, vp]
+    L.lne_svd_small_noalloc.argtypes = [vp, i32, vp, vp, vp]
     L.lne_trace_read.argtypes = [vp, ctypes.POINTER(_TraceEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     _lib = L
     return L
@@ -163,6 +164,14 @@ def _own(ptr, n, typestr, dtype, device):
     if n == 0:
         return torch.empty(0, dtype=dtype, device=device)
     return torch.as_tensor(_DevView(ptr, n, typestr), device=device).clone()
+
+
+def svd_small_noalloc(R: torch.Tensor, U: torch.Tensor, sigma: torch.Tensor) -> int:
+    """lne_svd_small_noalloc: writes U (c x c) and sigma (c) of the FP64 matrix R
+    without allocating device memory; returns the library's status code."""
+    L = load_library()
+    c = int(R.shape[0])
+    return int(L.lne_svd_small_noalloc(_ptr(R), c, _ptr(U), _ptr(sigma), _stream()))
 
 
 def _stream():
