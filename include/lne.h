@@ -47,7 +47,10 @@ extern "C" {
 
 /* Precision of the dense operand of the sparse products (Algorithm 4 lines 3
  * and 5, the propagation products). Accumulation is FP32 in both; the Gram,
- * Cholesky and small SVD are FP64 in both. */
+ * Cholesky and small SVD are FP64 in both. With LNE_PREC_BF16_MIXED the sketch,
+ * the power-iteration bases and the propagation operands are gathered as
+ * bfloat16 copies (the recurrences themselves stay FP32); d and d + oversample
+ * must be multiples of 4. */
 #define LNE_PREC_FP32        0
 #define LNE_PREC_BF16_MIXED  1
 
@@ -148,9 +151,12 @@ int lne_sparsifier_csr(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
 int lne_gaussian_sketch(lne_ctx *ctx, int64_t n, int32_t c, uint64_t seed, float *out_dev,
                         int64_t ld, void *stream);
 
-/* Y = M X for CSR M (n x n) and X [n][ldx] (c columns), Y [n][ldy]. FP32. */
-int lne_spmm(lne_ctx *ctx, const lne_csr *M, const float *X_dev, int64_t ldx, int32_t c,
-             float *Y_dev, int64_t ldy, void *stream);
+/* Y = M X for CSR M (n x n) and X [n][ldx] (c columns), Y [n][ldy] FP32,
+ * accumulated in FP32 (Algorithm 4, lines 3 and 5). X_dev is float
+ * (precision LNE_PREC_FP32) or bfloat16 (LNE_PREC_BF16_MIXED; c and ldx must then
+ * be multiples of 4). */
+int lne_spmm(lne_ctx *ctx, const lne_csr *M, const void *X_dev, int64_t ldx, int32_t c,
+             float *Y_dev, int64_t ldy, int32_t precision, void *stream);
 
 /*
  * CholeskyQR2 of Y [n][ld] (c columns, c <= 256) in place: Y := Q with Q^T Q = I,
@@ -205,6 +211,22 @@ int lne_rsvd(lne_ctx *ctx, const lne_csr *M, const lne_params *p, float *U_dev,
  */
 int lne_propagate(lne_ctx *ctx, const lne_graph *g, const lne_params *p, const float *X0_dev,
                   float *X_dev, float *F_dev, float *P_dev, void *stream);
+
+/*
+ * Downstream objective of the embedding (Sec. 5.1): one-vs-rest L2-regularised
+ * logistic regression (the LIBLINEAR model: for each label minimise
+ * 1/2 |w|^2 + C sum log(1 + exp(-y w.x)), x with a constant-1 bias feature),
+ * trained by `iters` Newton steps from w = 0 on the rows train_dev[0..n_train),
+ * then each row of test_dev predicts its k highest-scoring labels (k = its
+ * number of true labels). X_dev [n][ldx] float (d columns used, d <= 159);
+ * labels_dev [n][L] uint8 0/1; train/test row indices int32 on the device.
+ * *macro_f1 = mean over labels of 2TP / (2TP + FP + FN) (0 for a label with no
+ * positives or predictions), *micro_f1 = the same on pooled counts. Host
+ * outputs: synchronises.
+ */
+int lne_macro_f1(lne_ctx *ctx, const float *X_dev, int64_t n, int32_t d, int64_t ldx, const uint8_t *labels_dev,
+                 int32_t L, const int32_t *train_dev, int64_t n_train, const int32_t *test_dev, int64_t n_test,
+                 double C, int32_t iters, double *macro_f1, double *micro_f1, void *stream);
 
 /* The whole method: sparsifier -> randomized SVD -> propagation. X_dev [n][d]. */
 int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_dev, void *stream);

@@ -424,3 +424,66 @@ def subspace_sin(U1: np.ndarray, U2: np.ndarray) -> float:
     # ||(I - Q1 Q1^T) Q2||_2 is accurate for tiny angles (no 1 - cos^2 cancellation)
     R = Q2 - Q1 @ (Q1.T @ Q2)
     return float(min(1.0, np.linalg.norm(R, 2)))
+
+
+# ----------------------------------------------------------------------------
+# downstream objective: one-vs-rest logistic regression, Macro-F1 (Sec. 5.1)
+# ----------------------------------------------------------------------------
+
+def logreg_ovr(X: np.ndarray, Y: np.ndarray, C: float = 1.0, iters: int = 10) -> np.ndarray:
+    """One-vs-rest L2-regularised logistic regression (the LIBLINEAR model of
+    Sec. 5.1): for each label l, minimise 1/2 |w|^2 + C sum_i log(1 + exp(-y_il w.x_i))
+    with y in {-1, +1} and a constant-1 bias feature appended to x. Solved by
+    `iters` Newton steps from w = 0 (a library solve per step). Returns W of
+    shape (d + 1, L)."""
+    n, d = X.shape
+    Xa = np.hstack([X, np.ones((n, 1))])
+    L = Y.shape[1]
+    W = np.zeros((d + 1, L))
+    S = np.where(Y, 1.0, -1.0)
+    for _ in range(iters):
+        Z = Xa @ W                                   # margins
+        sg = 1.0 / (1.0 + np.exp(-S * Z))            # sigma(y z)
+        R = C * (sg - 1.0) * S                       # d loss / d z
+        Dw = C * sg * (1.0 - sg)                     # d^2 loss / d z^2
+        G = W + Xa.T @ R
+        for l in range(L):
+            H = np.eye(d + 1) + Xa.T @ (Xa * Dw[:, l:l + 1])
+            W[:, l] -= np.linalg.solve(H, G[:, l])
+    return W
+
+
+def predict_topk(scores: np.ndarray, k_per_row: np.ndarray) -> np.ndarray:
+    """Each row predicts its k highest-scoring labels (k = its number of true
+    labels; ties broken by the lower label index)."""
+    n, L = scores.shape
+    order = np.lexsort((np.tile(np.arange(L), (n, 1)), -scores), axis=1)
+    pred = np.zeros((n, L), dtype=bool)
+    for i in range(n):
+        pred[i, order[i, :k_per_row[i]]] = True
+    return pred
+
+
+def f1_scores(Y_true: np.ndarray, Y_pred: np.ndarray):
+    """(Macro-F1, Micro-F1): F1 = 2 TP / (2 TP + FP + FN) per label (0 when the
+    denominator is 0), averaged over labels; Micro-F1 pools the counts."""
+    tp = np.sum(Y_true & Y_pred, axis=0).astype(np.float64)
+    fp = np.sum(~Y_true & Y_pred, axis=0).astype(np.float64)
+    fn = np.sum(Y_true & ~Y_pred, axis=0).astype(np.float64)
+    den = 2 * tp + fp + fn
+    f1 = np.where(den > 0, 2 * tp / np.where(den > 0, den, 1.0), 0.0)
+    micro_den = 2 * tp.sum() + fp.sum() + fn.sum()
+    micro = 2 * tp.sum() / micro_den if micro_den > 0 else 0.0
+    return float(f1.mean()), float(micro)
+
+
+def macro_f1(X, labels, train_idx, test_idx, C=1.0, iters=10):
+    """Train on train_idx, predict test_idx with the top-k rule, return
+    (Macro-F1, Micro-F1, W)."""
+    labels = np.asarray(labels, dtype=bool)
+    W = logreg_ovr(np.asarray(X, np.float64)[train_idx], labels[train_idx], C, iters)
+    Xt = np.asarray(X, np.float64)[test_idx]
+    scores = np.hstack([Xt, np.ones((len(test_idx), 1))]) @ W
+    pred = predict_topk(scores, labels[test_idx].sum(1))
+    ma, mi = f1_scores(labels[test_idx], pred)
+    return ma, mi, W

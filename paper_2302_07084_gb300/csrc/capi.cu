@@ -203,8 +203,6 @@ int check_params(const lne_params *p, bool sampling) {
     }
     if (p->precision != LNE_PREC_FP32 && p->precision != LNE_PREC_BF16_MIXED)
         return lne::fail(LNE_ERR_INVALID, "unknown precision");
-    if (p->precision == LNE_PREC_BF16_MIXED)
-        return lne::fail(LNE_ERR_UNSUPPORTED, "BF16 mixed precision is not built yet");
     return 0;
 }
 
@@ -401,12 +399,14 @@ int lne_gaussian_sketch(lne_ctx *ctx, int64_t n, int32_t c, uint64_t seed, float
     return finish(ctx, rc);
 }
 
-int lne_spmm(lne_ctx *ctx, const lne_csr *M, const float *X_dev, int64_t ldx, int32_t c, float *Y_dev,
-             int64_t ldy, void *stream) {
+int lne_spmm(lne_ctx *ctx, const lne_csr *M, const void *X_dev, int64_t ldx, int32_t c, float *Y_dev,
+             int64_t ldy, int32_t precision, void *stream) {
     if (!ctx) return LNE_ERR_INVALID;
     int rc = enter(ctx);
     if (rc == 0 && (!M || M->n < 0 || c < 1 || ldx < c || ldy < c || !X_dev || !Y_dev || !M->indptr))
         rc = lne::fail(LNE_ERR_INVALID, "bad SpMM arguments");
+    if (rc == 0 && precision != LNE_PREC_FP32 && precision != LNE_PREC_BF16_MIXED)
+        rc = lne::fail(LNE_ERR_INVALID, "unknown precision");
     if (rc == 0) {
         lne::CsrView v;
         v.n = M->n;
@@ -414,7 +414,11 @@ int lne_spmm(lne_ctx *ctx, const lne_csr *M, const float *X_dev, int64_t ldx, in
         v.indptr = M->indptr;
         v.indices = M->indices;
         v.data = M->data;
-        rc = lne::spmm(ctx->ws, v, X_dev, ldx, c, Y_dev, ldy, as_stream(stream));
+        if (precision == LNE_PREC_BF16_MIXED)
+            rc = lne::spmm_bf16(ctx->ws, v, static_cast<const __nv_bfloat16 *>(X_dev), ldx, c, Y_dev, ldy, nullptr,
+                                as_stream(stream));
+        else
+            rc = lne::spmm(ctx->ws, v, static_cast<const float *>(X_dev), ldx, c, Y_dev, ldy, as_stream(stream));
     }
     return finish(ctx, rc);
 }
@@ -448,7 +452,7 @@ int lne_rsvd(lne_ctx *ctx, const lne_csr *M, const lne_params *p, float *U_dev, 
         v.indptr = M->indptr;
         v.indices = M->indices;
         v.data = M->data;
-        rc = lne::rsvd(ctx->ws, v, p->d, oversample_of(p), p->q, p->seed, U_dev, sigma_dev, X0_dev,
+        rc = lne::rsvd(ctx->ws, v, p->d, oversample_of(p), p->q, p->seed, p->precision, U_dev, sigma_dev, X0_dev,
                        as_stream(stream));
     }
     return finish(ctx, rc);
@@ -465,8 +469,21 @@ int lne_propagate(lne_ctx *ctx, const lne_graph *g, const lne_params *p, const f
         rc = lne::fail(LNE_ERR_INVALID, "need k >= 0 and finite theta, mu");
     if (rc == 0 && p->d < 1) rc = lne::fail(LNE_ERR_INVALID, "need d >= 1");
     if (rc == 0)
-        rc = lne::propagate(ctx->ws, view(g), p->d, p->k, p->theta, p->mu, X0_dev, X_dev, F_dev, P_dev,
-                            as_stream(stream));
+        rc = lne::propagate(ctx->ws, view(g), p->d, p->k, p->theta, p->mu, p->precision, X0_dev, X_dev, F_dev,
+                            P_dev, as_stream(stream));
+    return finish(ctx, rc);
+}
+
+int lne_macro_f1(lne_ctx *ctx, const float *X_dev, int64_t n, int32_t d, int64_t ldx, const uint8_t *labels_dev,
+                 int32_t L, const int32_t *train_dev, int64_t n_train, const int32_t *test_dev, int64_t n_test,
+                 double C, int32_t iters, double *macro_f1, double *micro_f1, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (!X_dev || !labels_dev || !train_dev || !test_dev || !macro_f1 || !micro_f1 || ldx < d || n < 1))
+        rc = lne::fail(LNE_ERR_INVALID, "bad Macro-F1 arguments");
+    if (rc == 0)
+        rc = lne::macro_f1(ctx->ws, X_dev, n, d, ldx, labels_dev, L, train_dev, n_train, test_dev, n_test, C, iters,
+                           macro_f1, micro_f1, as_stream(stream));
     return finish(ctx, rc);
 }
 
@@ -493,9 +510,11 @@ int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_de
         v.indptr = M.indptr;
         v.indices = M.indices;
         v.data = M.data;
-        rc = lne::rsvd(ctx->ws, v, p->d, oversample_of(p), p->q, p->seed, nullptr, nullptr, X0, st);
+        rc = lne::rsvd(ctx->ws, v, p->d, oversample_of(p), p->q, p->seed, p->precision, nullptr, nullptr, X0, st);
     }
-    if (rc == 0) rc = lne::propagate(ctx->ws, view(g), p->d, p->k, p->theta, p->mu, X0, X_dev, nullptr, nullptr, st);
+    if (rc == 0)
+        rc = lne::propagate(ctx->ws, view(g), p->d, p->k, p->theta, p->mu, p->precision, X0, X_dev, nullptr, nullptr,
+                            st);
     return finish(ctx, rc);
 }
 

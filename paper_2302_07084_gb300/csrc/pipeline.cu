@@ -65,7 +65,7 @@ std::vector<double> chebyshev_coefficients(int k, double theta) {
     return c;
 }
 
-int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t seed, float *U,
+int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t seed, int precision, float *U,
          double *sigma, float *X0, cudaStream_t st) {
     const int64_t n = M.n;
     const int c = d + oversample;
@@ -82,13 +82,26 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
     if (!sigma) LNE_TRY(ws.get("rsvd.sigma", (size_t)d, &sg));
     float *Uo = U ? U : Ub;
     double *so = sigma ? sigma : sg;
+    const bool bf16 = precision == LNE_PREC_BF16_MIXED;
+    __nv_bfloat16 *Xh = nullptr;   // BF16 dense operand of the products
+    if (bf16) LNE_TRY(ws.get("rsvd.xh", (size_t)n * c, &Xh));
     // Algorithm 4: Omega = randn(n, d+s); Y = M Omega
     LNE_TRY(gaussian_sketch(n, c, seed, Om, c, st));
-    LNE_TRY(spmm(ws, M, Om, c, c, Ya, c, st));
+    if (bf16) {
+        LNE_TRY(to_bf16(Om, Xh, n * c, st));
+        LNE_TRY(spmm_bf16(ws, M, Xh, c, c, Ya, c, nullptr, st));
+    } else {
+        LNE_TRY(spmm(ws, M, Om, c, c, Ya, c, st));
+    }
     // power iterations: Q = orth(Y); Y = M Q (q times)
     for (int it = 0; it < q; ++it) {
         LNE_TRY(cholqr2(ws, Ya, n, c, c, nullptr, st));
-        LNE_TRY(spmm(ws, M, Ya, c, c, Yb, c, st));
+        if (bf16) {
+            LNE_TRY(to_bf16(Ya, Xh, n * c, st));
+            LNE_TRY(spmm_bf16(ws, M, Xh, c, c, Yb, c, nullptr, st));
+        } else {
+            LNE_TRY(spmm(ws, M, Ya, c, c, Yb, c, st));
+        }
         std::swap(Ya, Yb);
     }
     // final eigSVD of Y: U = Q(:, 1:d), Sigma(1:d)
@@ -97,8 +110,8 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
     return 0;
 }
 
-int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, double mu, const float *X0,
-              float *X, float *F, float *P, cudaStream_t st) {
+int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, double mu, int precision,
+              const float *X0, float *X, float *F, float *P, cudaStream_t st) {
     const int64_t n = g.n;
     const int64_t cnt = n * d;
     if (k <= 0) {
@@ -122,6 +135,36 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
     LNE_TRY(ws.get("prop.U", (size_t)cnt, &Ub));
     LNE_TRY(ws.get("prop.sig", (size_t)d, &sig));
     const float om = (float)(1.0 - mu);
+    // BF16 mode: every gathered operand also lives as a BF16 copy (written by the
+    // producing epilogue); the recurrence itself stays FP32.
+    const bool bf16 = precision == LNE_PREC_BF16_MIXED;
+    __nv_bfloat16 *X0h = nullptr, *Zh = nullptr, *Gh = nullptr, *Th[3] = {nullptr, nullptr, nullptr};
+    if (bf16) {
+        LNE_TRY(ws.get("prop.X0h", (size_t)cnt, &X0h));
+        LNE_TRY(ws.get("prop.Zh", (size_t)cnt, &Zh));
+        LNE_TRY(ws.get("prop.Gh", (size_t)cnt, &Gh));
+        LNE_TRY(ws.get("prop.Tah", (size_t)cnt, &Th[0]));
+        LNE_TRY(ws.get("prop.Tbh", (size_t)cnt, &Th[1]));
+        LNE_TRY(ws.get("prop.Tch", (size_t)cnt, &Th[2]));
+        LNE_TRY(to_bf16(X0, X0h, cnt, st));
+    }
+    auto half_of = [&](const float *t) -> __nv_bfloat16 * {
+        if (t == X0) return X0h;
+        if (t == Z) return Zh;
+        if (t == Gb) return Gh;
+        if (t == Ta) return Th[0];
+        if (t == Tb) return Th[1];
+        if (t == Tc) return Th[2];
+        return nullptr;
+    };
+    // Y = op(A) X with X given in FP32; BF16 mode gathers X's BF16 copy and
+    // keeps a BF16 copy of the output too
+    auto gspmm = [&](const float *Xin, float *Yout, SpmmEpilogue ep) -> int {
+        if (!bf16) return graph_spmm(ws, g, Xin, d, d, Yout, d, ep, st);
+        ep.Yb = half_of(Yout);
+        if (ep.G) ep.Gb = Gh;
+        return graph_spmm_bf16(ws, g, half_of(Xin), d, d, Yout, d, ep, st);
+    };
     // F = c_0 X0
     {
         LNE_TRACE("scale_copy", st);
@@ -134,6 +177,7 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
             sub_kernel<<<elem_grid(cnt), 256, 0, st>>>(X0, Fb, Gb, cnt);
             LNE_LAUNCH_CHECK();
         }
+        if (bf16) LNE_TRY(to_bf16(Gb, Gh, cnt, st));
     } else {
         // Z = (Lap - mu I) X0 = (1 - mu) X0 - D^-1 A X0
         SpmmEpilogue e1;
@@ -142,7 +186,7 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
         e1.E1 = X0;
         e1.b1 = om;
         e1.lde = d;
-        LNE_TRY(graph_spmm(ws, g, X0, d, d, Z, d, e1, st));
+        LNE_TRY(gspmm(X0, Z, e1));
         // T_1 = Yop X0 = (Lap - mu I) Z / 2 - X0; F += c_1 T_1
         SpmmEpilogue e2;
         e2.alpha = -0.5f;
@@ -158,7 +202,7 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
             e2.X0 = X0;
             e2.G = Gb;
         }
-        LNE_TRY(graph_spmm(ws, g, Z, d, d, Ta, d, e2, st));
+        LNE_TRY(gspmm(Z, Ta, e2));
         // T_{i-2}, T_{i-1} rotate through three buffers; X0 is never written
         float *const bufs[3] = {Ta, Tb, Tc};
         const float *prev = X0;
@@ -177,7 +221,7 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
             ez.E1 = cur;
             ez.b1 = om;
             ez.lde = d;
-            LNE_TRY(graph_spmm(ws, g, cur, d, d, Z, d, ez, st));
+            LNE_TRY(gspmm(cur, Z, ez));
             // T_i = 2 Yop T_{i-1} - T_{i-2} = (Lap - mu I) Z - 2 T_{i-1} - T_{i-2}
             SpmmEpilogue e;
             e.alpha = -1.f;
@@ -195,7 +239,7 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
                 e.X0 = X0;
                 e.G = Gb;
             }
-            LNE_TRY(graph_spmm(ws, g, Z, d, d, nxt, d, e, st));
+            LNE_TRY(gspmm(Z, nxt, e));
             prev = cur;
             cur = nxt;
         }
@@ -205,7 +249,7 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
     ep.alpha = 1.f;
     ep.dinv = true;
     ep.lde = d;
-    LNE_TRY(graph_spmm(ws, g, Gb, d, d, Pb, d, ep, st));
+    LNE_TRY(gspmm(Gb, Pb, ep));
     // X = U_P Sigma_P^{1/2} from the SVD of P (economic SVD of the last stage)
     LNE_CUDA_TRY(cudaMemcpyAsync(Qb, Pb, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, st));
     LNE_TRY(tall_svd(ws, Qb, n, d, d, Ub, sig, st));

@@ -2,6 +2,7 @@
 // functions that the C ABI (capi.cu) composes.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -123,15 +124,29 @@ struct SpmmEpilogue {
     const float *X0 = nullptr;          // with G: G = X0 - F (after the update)
     float *G = nullptr;
     bool store = true;                  // write out to Y
+    __nv_bfloat16 *Yb = nullptr;        // BF16 copy of out (leading dimension ldy)
+    __nv_bfloat16 *Gb = nullptr;        // BF16 copy of G (leading dimension lde)
 };
 int graph_spmm(Workspace &ws, const GraphView &g, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
                const SpmmEpilogue &ep, cudaStream_t st);
+// The same products with a BF16 dense operand (FP32 accumulation); c % 4 == 0.
+int spmm_bf16(Workspace &ws, const CsrView &M, const __nv_bfloat16 *X, int64_t ldx, int c, float *Y, int64_t ldy,
+              __nv_bfloat16 *Yb, cudaStream_t st);
+int graph_spmm_bf16(Workspace &ws, const GraphView &g, const __nv_bfloat16 *X, int64_t ldx, int c, float *Y,
+                    int64_t ldy, const SpmmEpilogue &ep, cudaStream_t st);
+// out[i] = bf16(in[i]) for count elements.
+int to_bf16(const float *in, __nv_bfloat16 *out, int64_t count, cudaStream_t st);
 
 // Randomized SVD (Algorithm 4) and propagation (Sec. 3.3).
-int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t seed,
+int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t seed, int precision,
          float *U, double *sigma, float *X0, cudaStream_t st);
-int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, double mu,
+int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, double mu, int precision,
               const float *X0, float *X, float *F, float *P, cudaStream_t st);
+
+// One-vs-rest logistic regression + Micro/Macro-F1 (eval.cu).
+int macro_f1(Workspace &ws, const float *X, int64_t n, int d, int64_t ldx, const uint8_t *labels, int L,
+             const int32_t *train_idx, int64_t n_train, const int32_t *test_idx, int64_t n_test, double C, int iters,
+             double *macro, double *micro, cudaStream_t st);
 
 // Exclusive scan helpers (scan.cu).
 int scan_exclusive_u32_to_i64(const uint32_t *in, int64_t *out, int64_t n, cudaStream_t st);

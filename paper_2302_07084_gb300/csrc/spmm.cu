@@ -143,9 +143,21 @@ struct Acc4 {
     float4 v[NV];
 };
 
-template <int NV, bool WEIGHTED>
+// Four consecutive operand values as FP32: one 16-byte load (FP32) or one
+// 8-byte load (BF16, widened).
+__device__ __forceinline__ float4 load4(const float *__restrict__ row, int q) {
+    return __ldg(reinterpret_cast<const float4 *>(row) + q);
+}
+__device__ __forceinline__ float4 load4(const __nv_bfloat16 *__restrict__ row, int q) {
+    const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(row) + q);
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+template <int NV, bool WEIGHTED, typename TX>
 __device__ __forceinline__ void gather4(const int32_t *__restrict__ indices, const float *__restrict__ vals,
-                                        int64_t p, int cnt, const float4 *__restrict__ X4, int64_t ldx4, int c4,
+                                        int64_t p, int cnt, const TX *__restrict__ X, int64_t ldx, int c4,
                                         int lane, Acc4<NV> &acc) {
     const int col = lane < cnt ? __ldg(indices + p + lane) : 0;
     float v = 0.f;
@@ -154,12 +166,12 @@ __device__ __forceinline__ void gather4(const int32_t *__restrict__ indices, con
     for (int k = 0; k < cnt; ++k) {
         const int ck = __shfl_sync(0xffffffffu, col, k);
         const float vk = WEIGHTED ? __shfl_sync(0xffffffffu, v, k) : 1.f;
-        const float4 *xr = X4 + (int64_t)ck * ldx4;
+        const TX *xr = X + (int64_t)ck * ldx;
 #pragma unroll
         for (int t = 0; t < NV; ++t) {
             const int q = lane + 32 * t;
             if (q < c4) {
-                const float4 x = __ldg(xr + q);
+                const float4 x = load4(xr, q);
                 if (WEIGHTED) {
                     acc.v[t].x = fmaf(vk, x.x, acc.v[t].x);
                     acc.v[t].y = fmaf(vk, x.y, acc.v[t].y);
@@ -176,16 +188,22 @@ __device__ __forceinline__ void gather4(const int32_t *__restrict__ indices, con
     }
 }
 
-__device__ __forceinline__ float epi1(float a, float rs, int64_t e, const SpmmEpilogue &ep, float *__restrict__ y) {
+__device__ __forceinline__ float epi1(float a, float rs, int64_t e, int64_t yoff, const SpmmEpilogue &ep,
+                                      float *__restrict__ Y) {
     float o = rs * a;
     if (ep.E1) o = fmaf(ep.b1, ep.E1[e], o);
     if (ep.E2) o = fmaf(ep.b2, ep.E2[e], o);
     if (ep.E3) o = fmaf(ep.b3, ep.E3[e], o);
-    if (ep.store) *y = o;
+    if (ep.store) Y[yoff] = o;
+    if (ep.Yb) ep.Yb[yoff] = __float2bfloat16_rn(o);
     if (ep.F) {
         const float f = fmaf(ep.gamma, o, ep.F[e]);
         ep.F[e] = f;
-        if (ep.G) ep.G[e] = ep.X0[e] - f;
+        if (ep.G) {
+            const float gv = ep.X0[e] - f;
+            ep.G[e] = gv;
+            if (ep.Gb) ep.Gb[e] = __float2bfloat16_rn(gv);
+        }
     }
     return o;
 }
@@ -200,11 +218,11 @@ __device__ __forceinline__ void epilogue4(int64_t i, int64_t deg, const Acc4<NV>
         const int q = lane + 32 * t;
         if (q >= c4) continue;
         const int64_t e = i * ep.lde + 4 * q;
-        float *y = Y + i * ldy + 4 * q;
-        epi1(acc.v[t].x, rs, e + 0, ep, y + 0);
-        epi1(acc.v[t].y, rs, e + 1, ep, y + 1);
-        epi1(acc.v[t].z, rs, e + 2, ep, y + 2);
-        epi1(acc.v[t].w, rs, e + 3, ep, y + 3);
+        const int64_t yo = i * ldy + 4 * q;
+        epi1(acc.v[t].x, rs, e + 0, yo + 0, ep, Y);
+        epi1(acc.v[t].y, rs, e + 1, yo + 1, ep, Y);
+        epi1(acc.v[t].z, rs, e + 2, yo + 2, ep, Y);
+        epi1(acc.v[t].w, rs, e + 3, yo + 3, ep, Y);
     }
 }
 
@@ -217,11 +235,11 @@ __device__ __forceinline__ int64_t row_of(const int64_t *__restrict__ indptr, in
     return lo;
 }
 
-template <int NV, bool WEIGHTED>
+template <int NV, bool WEIGHTED, typename TX>
 __global__ void __launch_bounds__(256) spmm_merge_kernel(int64_t n, int64_t nnz, const int64_t *__restrict__ indptr,
                                                          const int32_t *__restrict__ indices,
-                                                         const float *__restrict__ vals, const float4 *__restrict__ X4,
-                                                         int64_t ldx4, int c4, float *__restrict__ Y, int64_t ldy,
+                                                         const float *__restrict__ vals, const TX *__restrict__ X,
+                                                         int64_t ldx, int c4, float *__restrict__ Y, int64_t ldy,
                                                          SpmmEpilogue ep, int64_t W, int64_t nwarps,
                                                          float4 *__restrict__ carry, int64_t *__restrict__ carry_row) {
     const int lane = threadIdx.x & 31;
@@ -243,7 +261,7 @@ __global__ void __launch_bounds__(256) spmm_merge_kernel(int64_t n, int64_t nnz,
 #pragma unroll
         for (int t = 0; t < NV; ++t) acc.v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int64_t q = p; q < e; q += 32)
-            gather4<NV, WEIGHTED>(indices, vals, q, (int)imin64(32, e - q), X4, ldx4, c4, lane, acc);
+            gather4<NV, WEIGHTED, TX>(indices, vals, q, (int)imin64(32, e - q), X, ldx, c4, lane, acc);
         if (rs >= p0 && re <= p1) {
             epilogue4<NV>(r, re - rs, acc, lane, c4, Y, ldy, ep);
         } else {
@@ -329,14 +347,15 @@ int launch_spmm(int64_t n, const int64_t *indptr, const int32_t *indices, const 
     return 0;
 }
 
-bool merge_ok(const float *X, int64_t ldx, int c, int64_t ldy, const SpmmEpilogue &ep) {
+template <typename TX>
+bool merge_ok(const TX *X, int64_t ldx, int c, int64_t ldy, const SpmmEpilogue &ep) {
     return c % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 && ep.lde % 4 == 0 && c <= 256 &&
-           (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+           (reinterpret_cast<uintptr_t>(X) & (4 * sizeof(TX) - 1)) == 0;
 }
 
-template <bool WEIGHTED>
+template <bool WEIGHTED, typename TX>
 int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, const int32_t *indices,
-                 const float *vals, const float *X, int64_t ldx, int c, float *Y, int64_t ldy, const SpmmEpilogue &ep,
+                 const float *vals, const TX *X, int64_t ldx, int c, float *Y, int64_t ldy, const SpmmEpilogue &ep,
                  cudaStream_t st) {
     if (n <= 0) return 0;
     const int c4 = c / 4;
@@ -351,12 +370,11 @@ int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, c
     LNE_TRY(ws.get("spmm.carry_row", (size_t)nwarps * 2, &carry_row));
     const unsigned mblocks = (unsigned)ceil_div(nwarps, 8);
     const unsigned fblocks = (unsigned)std::min<int64_t>(ceil_div(n, 8), 152 * 32);
-    const float4 *X4 = reinterpret_cast<const float4 *>(X);
     LNE_TRACE(WEIGHTED ? "spmm" : "graph_spmm", st);
 #define LNE_MERGE_CASE(K)                                                                                  \
     case K:                                                                                                \
         if (nnz > 0)                                                                                       \
-            spmm_merge_kernel<K, WEIGHTED><<<mblocks, 256, 0, st>>>(n, nnz, indptr, indices, vals, X4, ldx / 4, \
+            spmm_merge_kernel<K, WEIGHTED, TX><<<mblocks, 256, 0, st>>>(n, nnz, indptr, indices, vals, X, ldx, \
                                                                      c4, Y, ldy, ep, W, nwarps, carry,     \
                                                                      carry_row);                           \
         spmm_fixup_kernel<K><<<fblocks, 256, 0, st>>>(n, indptr, c4, Y, ldy, ep, W, carry, carry_row);      \
@@ -380,14 +398,44 @@ int spmm(Workspace &ws, const CsrView &M, const float *X, int64_t ldx, int c, fl
     SpmmEpilogue ep;
     ep.lde = ldy;
     if (merge_ok(X, ldx, c, ldy, ep))
-        return launch_merge<true>(ws, M.n, M.nnz, M.indptr, M.indices, M.data, X, ldx, c, Y, ldy, ep, st);
+        return launch_merge<true, float>(ws, M.n, M.nnz, M.indptr, M.indices, M.data, X, ldx, c, Y, ldy, ep, st);
     return launch_spmm<true>(M.n, M.indptr, M.indices, M.data, X, ldx, c, Y, ldy, ep, st);
+}
+
+int spmm_bf16(Workspace &ws, const CsrView &M, const __nv_bfloat16 *X, int64_t ldx, int c, float *Y, int64_t ldy,
+              __nv_bfloat16 *Yb, cudaStream_t st) {
+    SpmmEpilogue ep;
+    ep.lde = ldy;
+    ep.Yb = Yb;
+    if (!merge_ok(X, ldx, c, ldy, ep)) return fail(LNE_ERR_UNSUPPORTED, "BF16 operands need c and ld multiples of 4");
+    return launch_merge<true, __nv_bfloat16>(ws, M.n, M.nnz, M.indptr, M.indices, M.data, X, ldx, c, Y, ldy, ep, st);
+}
+
+int graph_spmm_bf16(Workspace &ws, const GraphView &g, const __nv_bfloat16 *X, int64_t ldx, int c, float *Y,
+                    int64_t ldy, const SpmmEpilogue &ep, cudaStream_t st) {
+    if (!merge_ok(X, ldx, c, ldy, ep)) return fail(LNE_ERR_UNSUPPORTED, "BF16 operands need c and ld multiples of 4");
+    return launch_merge<false, __nv_bfloat16>(ws, g.n, g.nnz, g.indptr, g.indices, nullptr, X, ldx, c, Y, ldy, ep, st);
+}
+
+namespace {
+__global__ void to_bf16_kernel(const float *__restrict__ in, __nv_bfloat16 *__restrict__ out, int64_t count) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(in[i]);
+}
+}  // namespace
+
+int to_bf16(const float *in, __nv_bfloat16 *out, int64_t count, cudaStream_t st) {
+    if (count <= 0) return 0;
+    LNE_TRACE("to_bf16", st);
+    to_bf16_kernel<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), 152 * 16), 256, 0, st>>>(in, out, count);
+    LNE_LAUNCH_CHECK();
+    return 0;
 }
 
 int graph_spmm(Workspace &ws, const GraphView &g, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
                const SpmmEpilogue &ep, cudaStream_t st) {
     if (merge_ok(X, ldx, c, ldy, ep))
-        return launch_merge<false>(ws, g.n, g.nnz, g.indptr, g.indices, nullptr, X, ldx, c, Y, ldy, ep, st);
+        return launch_merge<false, float>(ws, g.n, g.nnz, g.indptr, g.indices, nullptr, X, ldx, c, Y, ldy, ep, st);
     return launch_spmm<false>(g.n, g.indptr, g.indices, nullptr, X, ldx, c, Y, ldy, ep, st);
 }
 

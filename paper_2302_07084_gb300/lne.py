@@ -28,7 +28,7 @@ EXPORTED = [
     "lne_sample_pairs", "lne_sparsifier_counts", "lne_sparsifier_csr", "lne_gaussian_sketch",
     "lne_spmm", "lne_cholqr2", "lne_rsvd", "lne_propagate", "lne_embed",
     "lne_kernel_launches", "lne_trace_enable", "lne_trace_read", "lne_set_option",
-    "lne_svd_small", "lne_svd_small_noalloc",
+    "lne_svd_small", "lne_svd_small_noalloc", "lne_macro_f1",
 ]
 OPT_AGGREGATION = 1
 AGG_AUTO, AGG_TABLE, AGG_BUCKET = 0, 1, 2
@@ -93,7 +93,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lne_sparsifier_counts.argtypes = [vp, gp, pp, ctypes.POINTER(_Counts), vp]
     L.lne_sparsifier_csr.argtypes = [vp, gp, pp, ctypes.POINTER(_Csr), vp]
     L.lne_gaussian_sketch.argtypes = [vp, i64, i32, u64, vp, i64, vp]
-    L.lne_spmm.argtypes = [vp, ctypes.POINTER(_Csr), vp, i64, i32, vp, i64, vp]
+    L.lne_spmm.argtypes = [vp, ctypes.POINTER(_Csr), vp, i64, i32, vp, i64, i32, vp]
     L.lne_cholqr2.argtypes = [vp, vp, i64, i32, i64, vp, vp]
     L.lne_rsvd.argtypes = [vp, ctypes.POINTER(_Csr), pp, vp, vp, vp, vp]
     L.lne_propagate.argtypes = [vp, gp, pp, vp, vp, vp, vp, vp]
@@ -104,6 +104,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lne_set_option.argtypes = [vp, ctypes.c_int, i64]
     L.lne_svd_small.argtypes = [vp, vp, i32, vp, vp, vp]
     L.lne_svd_small_noalloc.argtypes = [vp, i32, vp, vp, vp]
+    L.lne_macro_f1.argtypes = [vp, vp, i64, i32, i64, vp, i32, vp, i64, vp, i64, ctypes.c_double, i32,
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     L.lne_trace_read.argtypes = [vp, ctypes.POINTER(_TraceEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     _lib = L
     return L
@@ -292,11 +294,15 @@ class Context:
                     csr["data"].data_ptr() if csr["nnz"] else None)
 
     def spmm(self, csr: dict, X: torch.Tensor) -> torch.Tensor:
+        """Y = M X; X float32 or bfloat16 (FP32 accumulation either way)."""
         X = X.contiguous()
         n, c = X.shape
+        prec = PREC_BF16_MIXED if X.dtype == torch.bfloat16 else PREC_FP32
+        if prec == PREC_FP32:
+            X = X.float()
         Y = torch.empty((int(csr["n"]), c), dtype=torch.float32, device=self.dev)
         m = self._csr(csr)
-        self._check(self.lib.lne_spmm(self.h, ctypes.byref(m), _ptr(X), c, c, _ptr(Y), c, _stream()))
+        self._check(self.lib.lne_spmm(self.h, ctypes.byref(m), _ptr(X), c, c, _ptr(Y), c, prec, _stream()))
         return Y
 
     def cholqr2(self, Y: torch.Tensor):
@@ -337,6 +343,20 @@ class Context:
         self._check(self.lib.lne_propagate(self.h, ctypes.byref(gc), ctypes.byref(pc), _ptr(X0), _ptr(X), _ptr(F),
                                            _ptr(P), _stream()))
         return dict(X=X, F=F, P=P)
+
+    def macro_f1(self, X: torch.Tensor, labels: torch.Tensor, train_idx: torch.Tensor, test_idx: torch.Tensor,
+                 C: float = 1.0, iters: int = 10):
+        """(Macro-F1, Micro-F1) of one-vs-rest logistic regression on X."""
+        X = X.contiguous().float()
+        lab = labels.contiguous().to(torch.uint8)
+        tr = train_idx.contiguous().to(torch.int32)
+        te = test_idx.contiguous().to(torch.int32)
+        n, d = X.shape
+        ma, mi = ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.lne_macro_f1(self.h, _ptr(X), n, d, d, _ptr(lab), lab.shape[1], _ptr(tr), tr.numel(),
+                                          _ptr(te), te.numel(), float(C), int(iters), ctypes.byref(ma),
+                                          ctypes.byref(mi), _stream()))
+        return float(ma.value), float(mi.value)
 
     def embed(self, g: DeviceGraph, p: Params, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         X = out if out is not None else torch.empty((g.n, p.d), dtype=torch.float32, device=self.dev)
