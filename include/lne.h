@@ -100,6 +100,8 @@ typedef struct lne_ctx lne_ctx;
 #define LNE_AGG_AUTO         0   /*   dense table when it fits, else bucket sort */
 #define LNE_AGG_TABLE        1   /*   dense n x n count table, atomic increments */
 #define LNE_AGG_BUCKET       2   /*   keys bucketed by row block, shared-memory counting */
+#define LNE_OPT_SPMM_THREADS 2   /* CTA size of the batched-tuning SpMM: 0 = picked by timing
+                                    (default), or 64 / 128 / 256; results do not depend on it */
 
 /* Create a context on CUDA device `device`. The context owns its workspace. */
 int lne_create(lne_ctx **out, int device);
@@ -230,6 +232,27 @@ int lne_macro_f1(lne_ctx *ctx, const float *X_dev, int64_t n, int32_t d, int64_t
 
 /* The whole method: sparsifier -> randomized SVD -> propagation. X_dev [n][d]. */
 int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_dev, void *stream);
+
+/*
+ * Batched hyper-parameter tuning (Sec. 4.3: the method's parameters are tuned
+ * per data set by scoring many configurations on the downstream task). Each of
+ * the ncand host candidates cands[j] is a full parameter set; the result for
+ * candidate j equals lne_embed(cands[j]) followed by lne_macro_f1 on the given
+ * split (macro_f1[j] / micro_f1[j], host arrays of ncand). Candidates that
+ * agree on T, s, S, b, d, oversample, q and seed share one sparsifier and one
+ * randomized SVD; the propagation of all candidates with k >= 1 runs as column
+ * blocks of one product (up to 1024 / d candidates per block), captured in a
+ * CUDA graph on the second call of a given shape and replayed afterwards.
+ * Requirements: every candidate has the same d (a multiple of 4, <= 160) and
+ * precision LNE_PREC_FP32 (else LNE_ERR_UNSUPPORTED / LNE_ERR_INVALID). X_dev,
+ * when not NULL, receives the embeddings, [ncand][n][d]. The evaluation
+ * arguments are those of lne_macro_f1 (with ldx = d). Host outputs:
+ * synchronises. Not to be called while `stream` is being captured.
+ */
+int lne_tune_batch(lne_ctx *ctx, const lne_graph *g, const lne_params *cands, int32_t ncand,
+                   const uint8_t *labels_dev, int32_t L, const int32_t *train_dev, int64_t n_train,
+                   const int32_t *test_dev, int64_t n_test, double C, int32_t iters, double *macro_f1,
+                   double *micro_f1, float *X_dev, void *stream);
 
 /*
  * Instrumentation (no counterpart in the paper, which reports wall-clock time

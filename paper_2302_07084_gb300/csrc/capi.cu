@@ -79,6 +79,9 @@ thread_local Tracer *g_tracer = nullptr;
 }
 
 void set_tracer(Tracer *t) { g_tracer = t; }
+Tracer *get_tracer() { return g_tracer; }
+int64_t launches_now() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void trace_begin(const char *name, cudaStream_t st) {
     Tracer *t = g_tracer;
@@ -153,6 +156,8 @@ struct lne_ctx {
     std::string err;
     lne::Workspace ws;
     lne::Tracer tracer;
+    lne::SpmmTune spmm_tune;
+    lne::PropBatchGraph *prop_graph = nullptr;
 };
 
 namespace {
@@ -247,6 +252,7 @@ void lne_destroy(lne_ctx *ctx) {
     cudaSetDevice(ctx->device);
     cudaDeviceSynchronize();
     lne::set_tracer(nullptr);
+    if (ctx->prop_graph) lne::destroy_prop_cache(ctx->prop_graph);
     ctx->ws.release();
     delete ctx;
 }
@@ -260,6 +266,12 @@ int lne_set_option(lne_ctx *ctx, int option, int64_t value) {
         if (value != LNE_AGG_AUTO && value != LNE_AGG_TABLE && value != LNE_AGG_BUCKET)
             return finish(ctx, lne::fail(LNE_ERR_INVALID, "unknown aggregation method"));
         ctx->aggregation = (int)value;
+        return LNE_OK;
+    }
+    if (option == LNE_OPT_SPMM_THREADS) {
+        if (value != 0 && value != 64 && value != 128 && value != 256)
+            return finish(ctx, lne::fail(LNE_ERR_INVALID, "SpMM CTA size must be 0 (timed), 64, 128 or 256"));
+        ctx->spmm_tune.forced = (int)value;
         return LNE_OK;
     }
     return finish(ctx, lne::fail(LNE_ERR_INVALID, "unknown option"));
@@ -318,6 +330,8 @@ int lne_trim(lne_ctx *ctx) {
     int rc = enter(ctx);
     if (rc == 0) {
         cudaDeviceSynchronize();
+        if (ctx->prop_graph) lne::destroy_prop_cache(ctx->prop_graph);
+        ctx->prop_graph = nullptr;
         ctx->ws.release();
     }
     return finish(ctx, rc);
@@ -515,6 +529,28 @@ int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_de
     if (rc == 0)
         rc = lne::propagate(ctx->ws, view(g), p->d, p->k, p->theta, p->mu, p->precision, X0, X_dev, nullptr, nullptr,
                             st);
+    return finish(ctx, rc);
+}
+
+int lne_tune_batch(lne_ctx *ctx, const lne_graph *g, const lne_params *cands, int32_t ncand,
+                   const uint8_t *labels_dev, int32_t L, const int32_t *train_dev, int64_t n_train,
+                   const int32_t *test_dev, int64_t n_test, double C, int32_t iters, double *macro_f1,
+                   double *micro_f1, float *X_dev, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0) rc = check_graph(g);
+    if (rc == 0 && (!cands || ncand < 1)) rc = lne::fail(LNE_ERR_INVALID, "need at least one candidate");
+    for (int j = 0; rc == 0 && j < ncand; ++j) rc = check_params(&cands[j], true);
+    if (rc == 0 && (!macro_f1 || !micro_f1)) rc = lne::fail(LNE_ERR_INVALID, "NULL score outputs");
+    if (rc == 0 && (!labels_dev || L < 1 || !train_dev || n_train < 1 || !test_dev || n_test < 1 || iters < 0))
+        rc = lne::fail(LNE_ERR_INVALID, "bad evaluation split or labels");
+    cudaStream_t st = as_stream(stream);
+    if (rc == 0) rc = check_graph_device(g, st);
+    if (rc == 0 && !ctx->prop_graph) ctx->prop_graph = lne::new_prop_cache();
+    if (rc == 0)
+        rc = lne::tune_batch(ctx->ws, ctx->prop_graph, ctx->spmm_tune, ctx->aggregation, view(g), cands, ncand,
+                             labels_dev, L, train_dev, n_train, test_dev, n_test, C, iters, macro_f1, micro_f1,
+                             X_dev, st);
     return finish(ctx, rc);
 }
 

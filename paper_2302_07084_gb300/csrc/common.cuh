@@ -80,6 +80,11 @@ void count_launch();
 // The calling thread's tracer (set by every context entry point; NULL = none).
 struct Tracer;
 void set_tracer(Tracer *t);
+Tracer *get_tracer();
+// Kernels counted so far (count_launch); add_launches counts n kernels that a
+// CUDA graph replay runs.
+int64_t launches_now();
+void add_launches(int64_t n);
 // Named timing regions: when the calling context has tracing on, a region
 // records a CUDA event pair on the launching stream around its kernels.
 void trace_begin(const char *name, cudaStream_t st);

@@ -258,3 +258,209 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
 }
 
 }  // namespace lne
+
+// ---------------------------------------------------------------------------
+// Batched propagation: ncand candidates (k_j, theta_j, mu_j) on the same graph
+// run as column blocks of one wide product -- Lap is shared, so each column
+// evolves independently and every column gets exactly the arithmetic of a
+// single-candidate run. Per-column coefficients live in device memory, so the
+// chain can be captured once in a CUDA graph and replayed for new candidates.
+// ---------------------------------------------------------------------------
+namespace lne {
+namespace {
+
+__global__ void scale_cols_kernel(const float *__restrict__ X, const float *__restrict__ s, int64_t n, int C,
+                                  float *__restrict__ Y) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * C; e += (int64_t)gridDim.x * blockDim.x)
+        Y[e] = s[e % C] * X[e];
+}
+
+}  // namespace
+
+struct PropBatchGraph {
+    bool valid = false;
+    int seen = 0;
+    int64_t kernels = 0;
+    std::vector<uintptr_t> key;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t capture = nullptr;   // the chain is captured here (the caller's stream may be the legacy one)
+    ~PropBatchGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (capture) cudaStreamDestroy(capture);
+    }
+};
+
+static int prop_batch_chain(Workspace &ws, const GraphView &g, int C, int kmax, const float *X0, float *F, float *Z,
+                            float *Tbuf[3], float *G, float *P, const float *om, const float *hom, const float *gam,
+                            int threads, cudaStream_t st) {
+    const int64_t cnt = g.n * C;
+    {
+        LNE_TRACE("scale_cols", st);
+        scale_cols_kernel<<<elem_grid(cnt), 256, 0, st>>>(X0, gam, g.n, C, F);
+        LNE_LAUNCH_CHECK();
+    }
+    if (kmax >= 2) {
+        SpmmEpilogue e1;
+        e1.alpha = -1.f;
+        e1.dinv = true;
+        e1.E1 = X0;
+        e1.b1_col = om;
+        e1.lde = C;
+        e1.threads = threads;
+        e1.carry_tag = "pb.carry";
+        LNE_TRY(graph_spmm(ws, g, X0, C, C, Z, C, e1, st));
+        SpmmEpilogue e2;
+        e2.alpha = -0.5f;
+        e2.dinv = true;
+        e2.E1 = Z;
+        e2.b1_col = hom;
+        e2.E2 = X0;
+        e2.b2 = -1.f;
+        e2.lde = C;
+        e2.F = F;
+        e2.gamma_col = gam + C;
+        e2.threads = threads;
+        e2.carry_tag = "pb.carry";
+        LNE_TRY(graph_spmm(ws, g, Z, C, C, Tbuf[0], C, e2, st));
+        const float *prev = X0;
+        float *cur = Tbuf[0];
+        for (int i = 2; i < kmax; ++i) {
+            float *nxt = nullptr;
+            for (int b = 0; b < 3; ++b)
+                if (Tbuf[b] != prev && Tbuf[b] != cur) {
+                    nxt = Tbuf[b];
+                    break;
+                }
+            SpmmEpilogue ez;
+            ez.alpha = -1.f;
+            ez.dinv = true;
+            ez.E1 = cur;
+            ez.b1_col = om;
+            ez.lde = C;
+            ez.threads = threads;
+            ez.carry_tag = "pb.carry";
+            LNE_TRY(graph_spmm(ws, g, cur, C, C, Z, C, ez, st));
+            SpmmEpilogue e;
+            e.alpha = -1.f;
+            e.dinv = true;
+            e.E1 = Z;
+            e.b1_col = om;
+            e.E2 = cur;
+            e.b2 = -2.f;
+            e.E3 = prev;
+            e.b3 = -1.f;
+            e.lde = C;
+            e.F = F;
+            e.gamma_col = gam + (int64_t)i * C;
+            e.threads = threads;
+            e.carry_tag = "pb.carry";
+            LNE_TRY(graph_spmm(ws, g, Z, C, C, nxt, C, e, st));
+            prev = cur;
+            cur = nxt;
+        }
+    }
+    {
+        LNE_TRACE("sub", st);
+        sub_kernel<<<elem_grid(cnt), 256, 0, st>>>(X0, F, G, cnt);
+        LNE_LAUNCH_CHECK();
+    }
+    SpmmEpilogue ep;
+    ep.alpha = 1.f;
+    ep.dinv = true;
+    ep.lde = C;
+    ep.threads = threads;
+    ep.carry_tag = "pb.carry";
+    return graph_spmm(ws, g, G, C, C, P, C, ep, st);
+}
+
+int propagate_batch(Workspace &ws, PropBatchGraph *cache, const GraphView &g, int d, int ncand, const int *k,
+                    const double *theta, const double *mu, const float *X0, float *P, int threads, cudaStream_t st) {
+    const int C = d * ncand;
+    if (C % 4 != 0 || C > 1024) return fail(LNE_ERR_UNSUPPORTED, "batched propagation needs d * ncand <= 1024, % 4");
+    int kmax = 1;
+    for (int j = 0; j < ncand; ++j) {
+        if (k[j] < 1) return fail(LNE_ERR_INVALID, "batched propagation needs k >= 1 for every candidate");
+        kmax = std::max(kmax, k[j]);
+    }
+    // per-column coefficient tables: om = 1 - mu, hom = (1 - mu) / 2, gam[i] = c_i(theta) for i < k
+    std::vector<float> h((size_t)(2 + kmax) * C, 0.f);
+    for (int j = 0; j < ncand; ++j) {
+        const std::vector<double> cf = chebyshev_coefficients(k[j], theta[j]);
+        for (int t = 0; t < d; ++t) {
+            const int col = j * d + t;
+            h[col] = (float)(1.0 - mu[j]);
+            h[C + col] = (float)(0.5 * (1.0 - mu[j]));
+            for (int i = 0; i < k[j]; ++i) h[(size_t)(2 + i) * C + col] = (float)cf[i];
+        }
+    }
+    float *coef = nullptr, *F = nullptr, *Z = nullptr, *G = nullptr, *Tb[3] = {nullptr, nullptr, nullptr};
+    const int64_t cnt = g.n * C;
+    LNE_TRY(ws.get("pb.coef", h.size(), &coef));
+    LNE_TRY(ws.get("pb.F", (size_t)cnt, &F));
+    LNE_TRY(ws.get("pb.Z", (size_t)cnt, &Z));
+    LNE_TRY(ws.get("pb.G", (size_t)cnt, &G));
+    LNE_TRY(ws.get("pb.Ta", (size_t)cnt, &Tb[0]));
+    LNE_TRY(ws.get("pb.Tb", (size_t)cnt, &Tb[1]));
+    LNE_TRY(ws.get("pb.Tc", (size_t)cnt, &Tb[2]));
+    LNE_CUDA_TRY(cudaMemcpyAsync(coef, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st));
+    float4 *carry = nullptr;
+    int64_t *carry_row = nullptr;
+    LNE_TRY(merge_carry(ws, "pb.carry", g.nnz, C, &carry, &carry_row));
+    const float *om = coef, *hom = coef + C, *gam = coef + 2 * C;
+    if (!cache) return prop_batch_chain(ws, g, C, kmax, X0, F, Z, Tb, G, P, om, hom, gam, threads, st);
+    // graph key: everything the captured launches depend on
+    std::vector<uintptr_t> key = {(uintptr_t)g.indptr, (uintptr_t)g.indices, (uintptr_t)g.n,  (uintptr_t)g.nnz,
+                                  (uintptr_t)C,        (uintptr_t)kmax,      (uintptr_t)X0,   (uintptr_t)P,
+                                  (uintptr_t)coef,     (uintptr_t)F,         (uintptr_t)Z,    (uintptr_t)G,
+                                  (uintptr_t)Tb[0],    (uintptr_t)Tb[1],     (uintptr_t)Tb[2], (uintptr_t)threads,
+                                  (uintptr_t)carry,    (uintptr_t)carry_row};
+    if (cache->valid && cache->key == key) {
+        LNE_TRACE("propagate_batch_graph", st);
+        LNE_CUDA_TRY(cudaGraphLaunch(cache->exec, st));
+        add_launches(cache->kernels);
+        return 0;
+    }
+    if (cache->key != key) {
+        cache->key = key;
+        cache->seen = 0;
+        cache->valid = false;
+    }
+    if (cache->seen == 0) {   // first run: eager (allocates every buffer the chain needs)
+        cache->seen = 1;
+        return prop_batch_chain(ws, g, C, kmax, X0, F, Z, Tb, G, P, om, hom, gam, threads, st);
+    }
+    // second run with the same key: capture, instantiate, launch
+    if (cache->exec) {
+        cudaGraphExecDestroy(cache->exec);
+        cache->exec = nullptr;
+    }
+    // launches counted while capturing are the kernels the graph runs (once
+    // now, then once per replay)
+    Tracer *const tracer = get_tracer();
+    set_tracer(nullptr);
+    cudaGraph_t graph = nullptr;
+    if (!cache->capture) LNE_CUDA_TRY(cudaStreamCreateWithFlags(&cache->capture, cudaStreamNonBlocking));
+    const int64_t before = launches_now();
+    LNE_CUDA_TRY(cudaStreamBeginCapture(cache->capture, cudaStreamCaptureModeThreadLocal));
+    int rc = prop_batch_chain(ws, g, C, kmax, X0, F, Z, Tb, G, P, om, hom, gam, threads, cache->capture);
+    cudaError_t e = cudaStreamEndCapture(cache->capture, &graph);
+    set_tracer(tracer);
+    cache->kernels = launches_now() - before;
+    if (rc != 0) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail("cudaStreamEndCapture", e, __FILE__, __LINE__);
+    e = cudaGraphInstantiate(&cache->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail("cudaGraphInstantiate", e, __FILE__, __LINE__);
+    cache->valid = true;
+    LNE_TRACE("propagate_batch_graph", st);
+    LNE_CUDA_TRY(cudaGraphLaunch(cache->exec, st));
+    return 0;
+}
+
+void destroy_prop_cache(PropBatchGraph *c) { delete c; }
+PropBatchGraph *new_prop_cache() { return new PropBatchGraph(); }
+
+}  // namespace lne

@@ -126,7 +126,15 @@ struct SpmmEpilogue {
     bool store = true;                  // write out to Y
     __nv_bfloat16 *Yb = nullptr;        // BF16 copy of out (leading dimension ldy)
     __nv_bfloat16 *Gb = nullptr;        // BF16 copy of G (leading dimension lde)
+    // per-column coefficients (device, length c); when set they replace b1 / gamma
+    const float *b1_col = nullptr;
+    const float *gamma_col = nullptr;
+    int threads = 0;                    // CTA size of the merge kernel (0 = default)
+    const char *carry_tag = nullptr;    // workspace name of the merge carry buffers (NULL = shared)
 };
+// Carry buffers of the merge SpMM for nnz nonzeros and c columns, under the
+// workspace names tag + ".c" / tag + ".r" (tag NULL = "spmm.carry").
+int merge_carry(Workspace &ws, const char *tag, int64_t nnz, int c, float4 **carry, int64_t **carry_row);
 int graph_spmm(Workspace &ws, const GraphView &g, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
                const SpmmEpilogue &ep, cudaStream_t st);
 // The same products with a BF16 dense operand (FP32 accumulation); c % 4 == 0.
@@ -142,6 +150,29 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
          float *U, double *sigma, float *X0, cudaStream_t st);
 int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, double mu, int precision,
               const float *X0, float *X, float *F, float *P, cudaStream_t st);
+
+// Batched propagation of ncand candidates as column blocks (pipeline.cu);
+// with a cache the chain is captured in a CUDA graph and replayed.
+struct PropBatchGraph;
+PropBatchGraph *new_prop_cache();
+void destroy_prop_cache(PropBatchGraph *c);
+int propagate_batch(Workspace &ws, PropBatchGraph *cache, const GraphView &g, int d, int ncand, const int *k,
+                    const double *theta, const double *mu, const float *X0, float *P, int threads, cudaStream_t st);
+std::vector<double> chebyshev_coefficients(int k, double theta);
+
+// CTA size of the merge SpMM, picked by timing per (row-length bucket, nnz
+// bucket, width bucket) unless forced; results do not depend on it.
+struct SpmmTune {
+    int forced = 0;
+    std::map<uint64_t, int> best;
+};
+int spmm_threads_for(SpmmTune &tc, Workspace &ws, const GraphView &g, const float *X, int C, float *Y,
+                     cudaStream_t st);
+// Batched tuning over ncand candidate parameter sets (tune.cu).
+int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregation, const GraphView &g,
+               const lne_params *cands, int ncand, const uint8_t *labels, int L, const int32_t *train,
+               int64_t n_train, const int32_t *test, int64_t n_test, double Creg, int iters, double *macro,
+               double *micro, float *X_out, cudaStream_t st);
 
 // One-vs-rest logistic regression + Micro/Macro-F1 (eval.cu).
 int macro_f1(Workspace &ws, const float *X, int64_t n, int d, int64_t ldx, const uint8_t *labels, int L,

@@ -66,12 +66,12 @@ __device__ __forceinline__ void epilogue(int64_t i, int64_t deg, const float (&a
         if (cc >= c) continue;
         const int64_t e = i * ep.lde + cc;
         float o = rs * acc[t];
-        if (ep.E1) o = fmaf(ep.b1, ep.E1[e], o);
+        if (ep.E1) o = fmaf(ep.b1_col ? ep.b1_col[cc] : ep.b1, ep.E1[e], o);
         if (ep.E2) o = fmaf(ep.b2, ep.E2[e], o);
         if (ep.E3) o = fmaf(ep.b3, ep.E3[e], o);
         if (ep.store) Y[i * ldy + cc] = o;
         if (ep.F) {
-            const float f = fmaf(ep.gamma, o, ep.F[e]);
+            const float f = fmaf(ep.gamma_col ? ep.gamma_col[cc] : ep.gamma, o, ep.F[e]);
             ep.F[e] = f;
             if (ep.G) ep.G[e] = ep.X0[e] - f;
         }
@@ -149,10 +149,10 @@ __device__ __forceinline__ float4 load4(const float *__restrict__ row, int q) {
     return __ldg(reinterpret_cast<const float4 *>(row) + q);
 }
 __device__ __forceinline__ float4 load4(const __nv_bfloat16 *__restrict__ row, int q) {
+    // a bfloat16 is the upper half of the FP32 with the same value
     const uint2 raw = __ldg(reinterpret_cast<const uint2 *>(row) + q);
-    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.x));
-    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&raw.y));
-    return make_float4(a.x, a.y, b.x, b.y);
+    return make_float4(__uint_as_float(raw.x << 16), __uint_as_float(raw.x & 0xffff0000u),
+                       __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xffff0000u));
 }
 
 template <int NV, bool WEIGHTED, typename TX>
@@ -188,26 +188,23 @@ __device__ __forceinline__ void gather4(const int32_t *__restrict__ indices, con
     }
 }
 
-__device__ __forceinline__ float epi1(float a, float rs, int64_t e, int64_t yoff, const SpmmEpilogue &ep,
-                                      float *__restrict__ Y) {
-    float o = rs * a;
-    if (ep.E1) o = fmaf(ep.b1, ep.E1[e], o);
-    if (ep.E2) o = fmaf(ep.b2, ep.E2[e], o);
-    if (ep.E3) o = fmaf(ep.b3, ep.E3[e], o);
-    if (ep.store) Y[yoff] = o;
-    if (ep.Yb) ep.Yb[yoff] = __float2bfloat16_rn(o);
-    if (ep.F) {
-        const float f = fmaf(ep.gamma, o, ep.F[e]);
-        ep.F[e] = f;
-        if (ep.G) {
-            const float gv = ep.X0[e] - f;
-            ep.G[e] = gv;
-            if (ep.Gb) ep.Gb[e] = __float2bfloat16_rn(gv);
-        }
-    }
-    return o;
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
+__device__ __forceinline__ float4 fma4(float4 a, float4 x, float4 y) {
+    return make_float4(fmaf(a.x, x.x, y.x), fmaf(a.y, x.y, y.y), fmaf(a.z, x.z, y.z), fmaf(a.w, x.w, y.w));
+}
+__device__ __forceinline__ float4 splat4(float a) { return make_float4(a, a, a, a); }
+__device__ __forceinline__ uint32_t bf16_bits(float x) { return __bfloat16_as_ushort(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ void st4_bf16(__nv_bfloat16 *p, float4 v) {
+    uint2 raw;
+    raw.x = bf16_bits(v.x) | (bf16_bits(v.y) << 16);
+    raw.y = bf16_bits(v.z) | (bf16_bits(v.w) << 16);
+    *reinterpret_cast<uint2 *>(p) = raw;
 }
 
+// The epilogue on four consecutive columns 4q..4q+3 of row i, with 16-byte
+// loads and stores (every operand is 16-byte aligned, leading dimensions are
+// multiples of 4); per element the same FMA chain as a scalar epilogue.
 template <int NV>
 __device__ __forceinline__ void epilogue4(int64_t i, int64_t deg, const Acc4<NV> &acc, int lane, int c4,
                                           float *__restrict__ Y, int64_t ldy, const SpmmEpilogue &ep) {
@@ -219,10 +216,23 @@ __device__ __forceinline__ void epilogue4(int64_t i, int64_t deg, const Acc4<NV>
         if (q >= c4) continue;
         const int64_t e = i * ep.lde + 4 * q;
         const int64_t yo = i * ldy + 4 * q;
-        epi1(acc.v[t].x, rs, e + 0, yo + 0, ep, Y);
-        epi1(acc.v[t].y, rs, e + 1, yo + 1, ep, Y);
-        epi1(acc.v[t].z, rs, e + 2, yo + 2, ep, Y);
-        epi1(acc.v[t].w, rs, e + 3, yo + 3, ep, Y);
+        const float4 a = acc.v[t];
+        float4 o = make_float4(rs * a.x, rs * a.y, rs * a.z, rs * a.w);
+        if (ep.E1) o = fma4(ep.b1_col ? ld4(ep.b1_col + 4 * q) : splat4(ep.b1), ld4(ep.E1 + e), o);
+        if (ep.E2) o = fma4(splat4(ep.b2), ld4(ep.E2 + e), o);
+        if (ep.E3) o = fma4(splat4(ep.b3), ld4(ep.E3 + e), o);
+        if (ep.store) st4(Y + yo, o);
+        if (ep.Yb) st4_bf16(ep.Yb + yo, o);
+        if (ep.F) {
+            const float4 f = fma4(ep.gamma_col ? ld4(ep.gamma_col + 4 * q) : splat4(ep.gamma), o, ld4(ep.F + e));
+            st4(ep.F + e, f);
+            if (ep.G) {
+                const float4 x0 = ld4(ep.X0 + e);
+                const float4 gv = make_float4(x0.x - f.x, x0.y - f.y, x0.z - f.z, x0.w - f.w);
+                st4(ep.G + e, gv);
+                if (ep.Gb) st4_bf16(ep.Gb + e, gv);
+            }
+        }
     }
 }
 
@@ -347,10 +357,27 @@ int launch_spmm(int64_t n, const int64_t *indptr, const int32_t *indices, const 
     return 0;
 }
 
+inline bool aligned(const void *p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
 template <typename TX>
-bool merge_ok(const TX *X, int64_t ldx, int c, int64_t ldy, const SpmmEpilogue &ep) {
-    return c % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 && ep.lde % 4 == 0 && c <= 256 &&
-           (reinterpret_cast<uintptr_t>(X) & (4 * sizeof(TX) - 1)) == 0;
+bool merge_ok(const TX *X, int64_t ldx, int c, const float *Y, int64_t ldy, const SpmmEpilogue &ep) {
+    return c % 4 == 0 && ldx % 4 == 0 && ldy % 4 == 0 && ep.lde % 4 == 0 && c <= 1024 &&
+           aligned(X, 4 * sizeof(TX)) && aligned(Y, 16) && aligned(ep.E1, 16) && aligned(ep.E2, 16) &&
+           aligned(ep.E3, 16) && aligned(ep.F, 16) && aligned(ep.X0, 16) && aligned(ep.G, 16) &&
+           aligned(ep.Yb, 8) && aligned(ep.Gb, 8) && aligned(ep.b1_col, 16) && aligned(ep.gamma_col, 16);
+}
+
+// nonzeros per warp slice: ~8 waves of warps, 32..1024 nonzeros each
+int64_t merge_slice(int64_t nnz) {
+    const int64_t W = nnz / (152 * 48 * 8);
+    return std::max<int64_t>(32, std::min<int64_t>(1024, (W + 31) / 32 * 32));
+}
+
+int merge_vectors(int c) {
+    int nv = (c / 4 + 31) / 32;
+    if (nv == 3) nv = 4;
+    if (nv > 4 && nv < 8) nv = 8;
+    return nv;
 }
 
 template <bool WEIGHTED, typename TX>
@@ -359,22 +386,20 @@ int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, c
                  cudaStream_t st) {
     if (n <= 0) return 0;
     const int c4 = c / 4;
-    const int nv = (c4 + 31) / 32;
-    // ~8 waves of warps, 32..1024 nonzeros each
-    int64_t W = nnz / (152 * 48 * 8);
-    W = std::max<int64_t>(32, std::min<int64_t>(1024, (W + 31) / 32 * 32));
+    const int nv = merge_vectors(c);
+    const int64_t W = merge_slice(nnz);
     const int64_t nwarps = std::max<int64_t>(1, ceil_div(nnz, W));
     float4 *carry = nullptr;
     int64_t *carry_row = nullptr;
-    LNE_TRY(ws.get("spmm.carry", (size_t)nwarps * 2 * nv * 32, &carry));
-    LNE_TRY(ws.get("spmm.carry_row", (size_t)nwarps * 2, &carry_row));
-    const unsigned mblocks = (unsigned)ceil_div(nwarps, 8);
+    LNE_TRY(merge_carry(ws, ep.carry_tag, nnz, c, &carry, &carry_row));
+    const int threads = ep.threads > 0 ? ep.threads : 256;
+    const unsigned mblocks = (unsigned)ceil_div(nwarps, threads / 32);
     const unsigned fblocks = (unsigned)std::min<int64_t>(ceil_div(n, 8), 152 * 32);
     LNE_TRACE(WEIGHTED ? "spmm" : "graph_spmm", st);
 #define LNE_MERGE_CASE(K)                                                                                  \
     case K:                                                                                                \
         if (nnz > 0)                                                                                       \
-            spmm_merge_kernel<K, WEIGHTED, TX><<<mblocks, 256, 0, st>>>(n, nnz, indptr, indices, vals, X, ldx, \
+            spmm_merge_kernel<K, WEIGHTED, TX><<<mblocks, threads, 0, st>>>(n, nnz, indptr, indices, vals, X, ldx, \
                                                                      c4, Y, ldy, ep, W, nwarps, carry,     \
                                                                      carry_row);                           \
         spmm_fixup_kernel<K><<<fblocks, 256, 0, st>>>(n, indptr, c4, Y, ldy, ep, W, carry, carry_row);      \
@@ -382,8 +407,10 @@ int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, c
     switch (nv) {
         LNE_MERGE_CASE(1)
         LNE_MERGE_CASE(2)
+        LNE_MERGE_CASE(4)
+        LNE_MERGE_CASE(8)
         default:
-            return fail(LNE_ERR_UNSUPPORTED, "SpMM supports at most 256 dense columns");
+            return fail(LNE_ERR_UNSUPPORTED, "SpMM supports at most 1024 dense columns");
     }
 #undef LNE_MERGE_CASE
     LNE_LAUNCH_CHECK();
@@ -393,11 +420,19 @@ int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, c
 
 }  // namespace
 
+int merge_carry(Workspace &ws, const char *tag, int64_t nnz, int c, float4 **carry, int64_t **carry_row) {
+    const int64_t nwarps = std::max<int64_t>(1, ceil_div(nnz, merge_slice(nnz)));
+    const std::string t = tag ? tag : "spmm.carry";
+    LNE_TRY(ws.get(t + ".c", (size_t)nwarps * 2 * merge_vectors(c) * 32, carry));
+    LNE_TRY(ws.get(t + ".r", (size_t)nwarps * 2, carry_row));
+    return 0;
+}
+
 int spmm(Workspace &ws, const CsrView &M, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
          cudaStream_t st) {
     SpmmEpilogue ep;
     ep.lde = ldy;
-    if (merge_ok(X, ldx, c, ldy, ep))
+    if (merge_ok(X, ldx, c, Y, ldy, ep))
         return launch_merge<true, float>(ws, M.n, M.nnz, M.indptr, M.indices, M.data, X, ldx, c, Y, ldy, ep, st);
     return launch_spmm<true>(M.n, M.indptr, M.indices, M.data, X, ldx, c, Y, ldy, ep, st);
 }
@@ -407,13 +442,13 @@ int spmm_bf16(Workspace &ws, const CsrView &M, const __nv_bfloat16 *X, int64_t l
     SpmmEpilogue ep;
     ep.lde = ldy;
     ep.Yb = Yb;
-    if (!merge_ok(X, ldx, c, ldy, ep)) return fail(LNE_ERR_UNSUPPORTED, "BF16 operands need c and ld multiples of 4");
+    if (!merge_ok(X, ldx, c, Y, ldy, ep)) return fail(LNE_ERR_UNSUPPORTED, "BF16 operands need c and ld multiples of 4");
     return launch_merge<true, __nv_bfloat16>(ws, M.n, M.nnz, M.indptr, M.indices, M.data, X, ldx, c, Y, ldy, ep, st);
 }
 
 int graph_spmm_bf16(Workspace &ws, const GraphView &g, const __nv_bfloat16 *X, int64_t ldx, int c, float *Y,
                     int64_t ldy, const SpmmEpilogue &ep, cudaStream_t st) {
-    if (!merge_ok(X, ldx, c, ldy, ep)) return fail(LNE_ERR_UNSUPPORTED, "BF16 operands need c and ld multiples of 4");
+    if (!merge_ok(X, ldx, c, Y, ldy, ep)) return fail(LNE_ERR_UNSUPPORTED, "BF16 operands need c and ld multiples of 4");
     return launch_merge<false, __nv_bfloat16>(ws, g.n, g.nnz, g.indptr, g.indices, nullptr, X, ldx, c, Y, ldy, ep, st);
 }
 
@@ -434,7 +469,7 @@ int to_bf16(const float *in, __nv_bfloat16 *out, int64_t count, cudaStream_t st)
 
 int graph_spmm(Workspace &ws, const GraphView &g, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
                const SpmmEpilogue &ep, cudaStream_t st) {
-    if (merge_ok(X, ldx, c, ldy, ep))
+    if (merge_ok(X, ldx, c, Y, ldy, ep))
         return launch_merge<false, float>(ws, g.n, g.nnz, g.indptr, g.indices, nullptr, X, ldx, c, Y, ldy, ep, st);
     return launch_spmm<false>(g.n, g.indptr, g.indices, nullptr, X, ldx, c, Y, ldy, ep, st);
 }

@@ -1,0 +1,194 @@
+// Batched parameter tuning (Sec. 4.3: the hyper-parameters of the method --
+// window weights, sample count, filter k / theta / mu -- are tuned by running
+// many candidate configurations on one graph and keeping the best downstream
+// Macro-F1).
+//
+// The GPU-side batching:
+//   * candidates that agree on everything the sparsifier and the randomized SVD
+//     read (T, s, S, b, d, oversample, q, seed) share one sparsifier and one
+//     randomized SVD;
+//   * the spectral propagation of every candidate with k >= 1 runs as one
+//     column block of a single wide product [n][m d] -- the normalized
+//     Laplacian is the same matrix for all of them, so each column evolves on
+//     its own with exactly the arithmetic of a one-candidate run; the per-column
+//     (1 - mu) and c_i(theta) live in a device table, and the chain of
+//     products is captured once in a CUDA graph and replayed for the next
+//     candidate set of the same shape;
+//   * the merge SpMM's CTA size is picked by timing (results do not depend on
+//     it: every warp owns the same nonzero slice whatever the CTA size).
+// Each candidate then gets its own final SVD (Sec. 5.4 economic SVD of P) and
+// its own Macro-F1.
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <vector>
+
+#include "common.cuh"
+#include "runtime.h"
+
+namespace lne {
+
+namespace {
+
+bool same_rsvd_inputs(const lne_params &a, const lne_params &b, int osa, int osb) {
+    if (a.T != b.T || a.samples != b.samples || a.b != b.b || a.d != b.d || osa != osb || a.q != b.q ||
+        a.seed != b.seed)
+        return false;
+    for (int i = 0; i < a.T; ++i)
+        if (a.s[i] != b.s[i]) return false;
+    return true;
+}
+
+}  // namespace
+
+int spmm_threads_for(SpmmTune &tc, Workspace &ws, const GraphView &g, const float *X, int C, float *Y,
+                     cudaStream_t st) {
+    if (tc.forced > 0) return tc.forced;
+    const int64_t avg = g.n > 0 ? std::max<int64_t>(1, g.nnz / g.n) : 1;
+    int dbucket = 0;
+    while ((int64_t(1) << (dbucket + 1)) <= avg) ++dbucket;
+    int nbucket = 0;
+    while ((int64_t(1) << (nbucket + 1)) <= std::max<int64_t>(1, g.nnz)) ++nbucket;
+    const uint64_t key = (uint64_t)dbucket | ((uint64_t)nbucket << 8) | ((uint64_t)((C / 4 + 31) / 32) << 16);
+    auto it = tc.best.find(key);
+    if (it != tc.best.end()) return it->second;
+    cudaEvent_t e0, e1;
+    LNE_CUDA_TRY(cudaEventCreate(&e0));
+    LNE_CUDA_TRY(cudaEventCreate(&e1));
+    const int cand[3] = {64, 128, 256};
+    int best = 256;
+    float best_ms = 1e30f;
+    int rc = 0;
+    for (int t : cand) {
+        SpmmEpilogue ep;
+        ep.alpha = 1.f;
+        ep.dinv = true;
+        ep.lde = C;
+        ep.threads = t;
+        if ((rc = graph_spmm(ws, g, X, C, C, Y, C, ep, st)) != 0) break;   // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3 && rc == 0; ++r) rc = graph_spmm(ws, g, X, C, C, Y, C, ep, st);
+        cudaEventRecord(e1, st);
+        if (rc != 0) break;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            rc = cuda_fail("cudaEventSynchronize", e, __FILE__, __LINE__);
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = t;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != 0) return -1;
+    tc.best[key] = best;
+    return best;
+}
+
+int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregation, const GraphView &g,
+               const lne_params *cands, int ncand, const uint8_t *labels, int L, const int32_t *train,
+               int64_t n_train, const int32_t *test, int64_t n_test, double Creg, int iters, double *macro,
+               double *micro, float *X_out, cudaStream_t st) {
+    if (ncand < 1) return fail(LNE_ERR_INVALID, "need at least one candidate");
+    const int d = cands[0].d;
+    const int64_t n = g.n;
+    for (int j = 0; j < ncand; ++j) {
+        const lne_params &p = cands[j];
+        if (p.d != d) return fail(LNE_ERR_INVALID, "all candidates must share the embedding dimension d");
+        if (p.precision != LNE_PREC_FP32) return fail(LNE_ERR_UNSUPPORTED, "batched tuning runs in FP32 only");
+        if (p.k < 0 || p.q < 0) return fail(LNE_ERR_INVALID, "need q >= 0 and k >= 0");
+    }
+    if (d < 4 || d % 4 != 0) return fail(LNE_ERR_UNSUPPORTED, "batched tuning needs d to be a multiple of 4");
+    if (d > 160) return fail(LNE_ERR_UNSUPPORTED, "d > 160 is not supported by the small SVD");
+    if (d > n) return fail(LNE_ERR_INVALID, "d must not exceed the number of vertices");
+    auto os_of = [](const lne_params &p) { return p.oversample < 0 ? 16 : p.oversample; };
+    // groups of candidates sharing the sparsifier and the randomized SVD
+    std::vector<int> group(ncand), leader;
+    for (int j = 0; j < ncand; ++j) {
+        int gid = -1;
+        for (int q = 0; q < (int)leader.size() && gid < 0; ++q)
+            if (same_rsvd_inputs(cands[leader[q]], cands[j], os_of(cands[leader[q]]), os_of(cands[j]))) gid = q;
+        if (gid < 0) {
+            gid = (int)leader.size();
+            leader.push_back(j);
+        }
+        group[j] = gid;
+    }
+    float *X0s = nullptr;
+    LNE_TRY(ws.get("tune.x0", (size_t)leader.size() * n * d, &X0s));
+    for (int q = 0; q < (int)leader.size(); ++q) {
+        const lne_params &p = cands[leader[q]];
+        SamplerSpec sp;
+        LNE_TRY(make_sampler_spec(g, p.T, p.s, p.samples, p.b, p.seed, &sp));
+        sp.aggregation = aggregation;
+        CsrResult M;
+        LNE_TRY(sparsifier_csr(ws, g, sp, &M, st));
+        CsrView v;
+        v.n = M.n;
+        v.nnz = M.nnz;
+        v.indptr = M.indptr;
+        v.indices = M.indices;
+        v.data = M.data;
+        LNE_TRY(rsvd(ws, v, d, os_of(p), p.q, p.seed, p.precision, nullptr, nullptr, X0s + (size_t)q * n * d, st));
+    }
+    float *X = nullptr, *U = nullptr;
+    double *R = nullptr, *UR = nullptr, *sig = nullptr;
+    LNE_TRY(ws.get("tune.x", (size_t)n * d, &X));
+    LNE_TRY(ws.get("tune.u", (size_t)n * d, &U));
+    LNE_TRY(ws.get("tune.r", (size_t)d * d, &R));
+    LNE_TRY(ws.get("tune.ur", (size_t)d * d, &UR));
+    LNE_TRY(ws.get("tune.sig", (size_t)d, &sig));
+    auto score = [&](int j, const float *Xj) -> int {
+        if (X_out)
+            LNE_CUDA_TRY(cudaMemcpyAsync(X_out + (size_t)j * n * d, Xj, sizeof(float) * n * d,
+                                         cudaMemcpyDeviceToDevice, st));
+        return macro_f1(ws, Xj, n, d, d, labels, L, train, n_train, test, n_test, Creg, iters, &macro[j], &micro[j],
+                        st);
+    };
+    // k = 0: the embedding is X0 itself
+    std::vector<int> prop;
+    for (int j = 0; j < ncand; ++j) {
+        if (cands[j].k == 0)
+            LNE_TRY(score(j, X0s + (size_t)group[j] * n * d));
+        else
+            prop.push_back(j);
+    }
+    const int per_chunk = std::max(1, 1024 / d);
+    for (size_t b0 = 0; b0 < prop.size(); b0 += per_chunk) {
+        const int m = (int)std::min<size_t>(per_chunk, prop.size() - b0);
+        const int C = m * d;
+        float *X0r = nullptr, *P = nullptr;
+        LNE_TRY(ws.get("tune.x0rep", (size_t)n * C, &X0r));
+        LNE_TRY(ws.get("tune.p", (size_t)n * C, &P));
+        std::vector<int> ks(m);
+        std::vector<double> th(m), mu(m);
+        for (int t = 0; t < m; ++t) {
+            const lne_params &p = cands[prop[b0 + t]];
+            ks[t] = p.k;
+            th[t] = p.theta;
+            mu[t] = p.mu;
+            LNE_CUDA_TRY(cudaMemcpy2DAsync(X0r + (size_t)t * d, sizeof(float) * C,
+                                           X0s + (size_t)group[prop[b0 + t]] * n * d, sizeof(float) * d,
+                                           sizeof(float) * d, n, cudaMemcpyDeviceToDevice, st));
+        }
+        const int threads = spmm_threads_for(tc, ws, g, X0r, C, P, st);
+        if (threads < 0) return -1;
+        LNE_TRY(propagate_batch(ws, cache, g, d, m, ks.data(), th.data(), mu.data(), X0r, P, threads, st));
+        // per candidate: X = U_P Sigma_P^{1/2} from the economic SVD of its block of P
+        for (int t = 0; t < m; ++t) {
+            float *Pj = P + (size_t)t * d;
+            LNE_TRY(cholqr2(ws, Pj, n, d, C, R, st));
+            LNE_TRY(small_svd(ws, R, d, UR, sig, st));
+            LNE_TRY(right_multiply(Pj, n, d, C, UR, d, d, nullptr, U, d, st));
+            LNE_TRY(sign_fix_embed(ws, U, n, d, d, sig, X, d, st));
+            LNE_TRY(score(prop[b0 + t], X));
+        }
+    }
+    return 0;
+}
+
+}  // namespace lne

@@ -28,9 +28,10 @@ EXPORTED = [
     "lne_sample_pairs", "lne_sparsifier_counts", "lne_sparsifier_csr", "lne_gaussian_sketch",
     "lne_spmm", "lne_cholqr2", "lne_rsvd", "lne_propagate", "lne_embed",
     "lne_kernel_launches", "lne_trace_enable", "lne_trace_read", "lne_set_option",
-    "lne_svd_small", "lne_svd_small_noalloc", "lne_macro_f1",
+    "lne_svd_small", "lne_svd_small_noalloc", "lne_macro_f1", "lne_tune_batch",
 ]
 OPT_AGGREGATION = 1
+OPT_SPMM_THREADS = 2
 AGG_AUTO, AGG_TABLE, AGG_BUCKET = 0, 1, 2
 
 
@@ -106,6 +107,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lne_svd_small_noalloc.argtypes = [vp, i32, vp, vp, vp]
     L.lne_macro_f1.argtypes = [vp, vp, i64, i32, i64, vp, i32, vp, i64, vp, i64, ctypes.c_double, i32,
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
+    L.lne_tune_batch.argtypes = [vp, gp, vp, i32, vp, i32, vp, i64, vp, i64, ctypes.c_double, i32,
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp, vp]
     L.lne_trace_read.argtypes = [vp, ctypes.POINTER(_TraceEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     _lib = L
     return L
@@ -357,6 +360,28 @@ class Context:
                                           _ptr(te), te.numel(), float(C), int(iters), ctypes.byref(ma),
                                           ctypes.byref(mi), _stream()))
         return float(ma.value), float(mi.value)
+
+    def tune_batch(self, g: DeviceGraph, cands: Sequence[Params], labels: torch.Tensor, train_idx: torch.Tensor,
+                   test_idx: torch.Tensor, C: float = 1.0, iters: int = 10, want_embeddings: bool = False):
+        """Macro-F1 / Micro-F1 of every candidate parameter set (lne_tune_batch):
+        numpy arrays of len(cands), plus the embeddings [ncand][n][d] if asked."""
+        nc = len(cands)
+        built = [p._c() for p in cands]
+        arr = (_Params * nc)(*[b[0] for b in built])
+        lab = labels.contiguous().to(torch.uint8)
+        tr = train_idx.contiguous().to(torch.int32)
+        te = test_idx.contiguous().to(torch.int32)
+        ma = (ctypes.c_double * nc)()
+        mi = (ctypes.c_double * nc)()
+        X = torch.empty((nc, g.n, cands[0].d), dtype=torch.float32, device=self.dev) if want_embeddings else None
+        gc = g._c()
+        self._check(self.lib.lne_tune_batch(self.h, ctypes.byref(gc), ctypes.cast(arr, ctypes.c_void_p), nc,
+                                            _ptr(lab), lab.shape[1], _ptr(tr), tr.numel(), _ptr(te), te.numel(),
+                                            float(C), int(iters), ma, mi, _ptr(X) if X is not None else None,
+                                            _stream()))
+        del built
+        out = (np.array(ma[:]), np.array(mi[:]))
+        return out + (X,) if want_embeddings else out
 
     def embed(self, g: DeviceGraph, p: Params, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         X = out if out is not None else torch.empty((g.n, p.d), dtype=torch.float32, device=self.dev)

@@ -1,0 +1,133 @@
+"""Batched tuning (lne_tune_batch) against one-candidate runs.
+
+Every candidate's embedding and scores must equal what lne_embed followed by
+lne_macro_f1 gives for that candidate alone: the batch shares the sparsifier
+and the randomized SVD between candidates with the same sampling inputs and
+runs all propagations as column blocks of one product, which changes no
+arithmetic of any column. The captured CUDA graph (second call of a shape) and
+its replays (later calls, new coefficients) must give the same results, and so
+must every CTA size of the merge SpMM.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2302_07084_gb300 import lne, synth
+from gpu_common import make_params, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2302_07084_gb300 import build
+    build.build()
+    c = lne.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def case():
+    g = synth.chung_lu(3000, 30000, 2.1, seed=9, n_labels=12)
+    idx = np.random.default_rng(5).permutation(g.n)
+    tr, te = idx[: g.n // 2], idx[g.n // 2:]
+    dev = dict(g=lne.DeviceGraph.from_graph(g), labels=torch.as_tensor(g.labels).cuda(),
+               tr=torch.as_tensor(tr).cuda(), te=torch.as_tensor(te).cuda())
+    return g, dev
+
+
+def _cands(g, d, spec):
+    return [make_params(10, np.full(10, 0.1), 50.0 * g.m, d=d, q=1, k=k, theta=th, mu=mu, seed=seed)
+            for (k, th, mu, seed) in spec]
+
+
+def _single(ctx, dev, p):
+    X = ctx.embed(dev["g"], p)
+    ma, mi = ctx.macro_f1(X, dev["labels"], dev["tr"], dev["te"])
+    return to_np(X), ma, mi
+
+
+def _check_against_single(ctx, dev, cands, ma, mi, X):
+    for j, p in enumerate(cands):
+        Xs, mas, mis = _single(ctx, dev, p)
+        Xb = to_np(X[j])
+        err = np.max(np.abs(Xb - Xs)) / np.max(np.abs(Xs))
+        assert err <= 1e-5, (j, err)
+        # the same embedding gives the same scores; a last-bit difference may move a near tie
+        tol = 0.0 if np.array_equal(Xb, Xs) else 0.005
+        assert abs(ma[j] - mas) <= tol and abs(mi[j] - mis) <= tol, (j, ma[j], mas)
+
+
+SPEC = [(10, 0.5, 0.2, 3), (5, 1.0, 0.5, 3), (1, 0.5, 0.2, 3), (0, 0.5, 0.2, 3), (2, 0.3, 0.1, 3),
+        (10, 0.5, 0.2, 4), (7, 2.0, -0.3, 4)]
+
+
+def test_batch_equals_single_runs(ctx, case):
+    g, dev = case
+    cands = _cands(g, 32, SPEC)
+    ma, mi, X = ctx.tune_batch(dev["g"], cands, dev["labels"], dev["tr"], dev["te"], want_embeddings=True)
+    _check_against_single(ctx, dev, cands, ma, mi, X)
+    exact = [bool(np.array_equal(to_np(X[j]), to_np(ctx.embed(dev["g"], p)))) for j, p in enumerate(cands)]
+    print("bit-identical to one-candidate runs:", exact)
+
+
+def test_graph_capture_and_replay(ctx, case):
+    g, dev = case
+    # same shape (k values) three times: eager, captured, replayed with new theta / mu
+    specs = [[(10, 0.5, 0.2, 3), (6, 1.0, 0.5, 3)],
+             [(10, 0.7, 0.3, 3), (6, 0.4, 0.0, 3)],
+             [(10, 1.5, -0.2, 3), (6, 0.2, 0.9, 3)]]
+    for spec in specs:
+        cands = _cands(g, 32, spec)
+        ma, mi, X = ctx.tune_batch(dev["g"], cands, dev["labels"], dev["tr"], dev["te"], want_embeddings=True)
+        _check_against_single(ctx, dev, cands, ma, mi, X)
+    ctx.trace(True)
+    cands = _cands(g, 32, specs[0])
+    ctx.tune_batch(dev["g"], cands, dev["labels"], dev["tr"], dev["te"])
+    names = [r["name"] for r in ctx.trace_read()]
+    ctx.trace(False)
+    assert "propagate_batch_graph" in names and "graph_spmm" not in names
+
+
+def test_cta_size_does_not_change_results(ctx, case):
+    g, dev = case
+    cands = _cands(g, 32, SPEC[:3])
+    outs = []
+    for t in (64, 128, 256, 0):
+        ctx.set_option(lne.OPT_SPMM_THREADS, t)
+        outs.append(ctx.tune_batch(dev["g"], cands, dev["labels"], dev["tr"], dev["te"], want_embeddings=True))
+    ctx.set_option(lne.OPT_SPMM_THREADS, 0)
+    for o in outs[1:]:
+        assert torch.equal(o[2], outs[0][2])
+        assert np.array_equal(o[0], outs[0][0])
+
+
+def test_several_column_blocks(ctx, case):
+    g, dev = case
+    # d = 128: 8 candidates per block, so 9 propagating candidates need two blocks
+    spec = [(3 + (j % 4), 0.5 + 0.1 * j, 0.1 * (j % 3), 3) for j in range(9)]
+    cands = _cands(g, 128, spec)
+    ma, mi, X = ctx.tune_batch(dev["g"], cands, dev["labels"], dev["tr"], dev["te"], want_embeddings=True)
+    picks = [0, 7, 8]
+    _check_against_single(ctx, dev, [cands[j] for j in picks], ma[picks], mi[picks], X[picks])
+
+
+def test_rejects_bad_candidates(ctx, case):
+    g, dev = case
+    cands = _cands(g, 32, SPEC[:2])
+    cands[1].d = 16
+    with pytest.raises(lne.LneError) as e:
+        ctx.tune_batch(dev["g"], cands, dev["labels"], dev["tr"], dev["te"])
+    assert e.value.code == -1
+    cands = _cands(g, 32, SPEC[:2])
+    cands[0].precision = lne.PREC_BF16_MIXED
+    with pytest.raises(lne.LneError) as e:
+        ctx.tune_batch(dev["g"], cands, dev["labels"], dev["tr"], dev["te"])
+    assert e.value.code == -5
+    cands = _cands(g, 30, SPEC[:2])
+    with pytest.raises(lne.LneError) as e:
+        ctx.tune_batch(dev["g"], cands, dev["labels"], dev["tr"], dev["te"])
+    assert e.value.code == -5
+    with pytest.raises(lne.LneError):
+        ctx.set_option(lne.OPT_SPMM_THREADS, 96)
