@@ -398,6 +398,54 @@ def run_case(args):
     print(json.dumps({"case": args.case, "steps": args.steps, "samples": params["samples"]}))
 
 
+def run_tune(args):
+    """Tuning throughput on the many-graph SBM suite (graph seeds 100.., 32
+    candidates per graph: s ~ Dirichlet(1), k ~ U{3..20}, theta ~ U[0.3, 1],
+    mu ~ U[0, 0.5], q = 1, d = 32, S = 100 m): candidates scored per second by
+    lne_tune_tasks against the plain loop (lne_embed + lne_macro_f1 per
+    candidate, on the first graphs only, to bound its time)."""
+    import torch
+    from paper_2302_07084_gb300 import lne, synth
+    G, per = args.tune, 32
+    graphs = [synth.tuning_graph(100 + i) for i in range(G)]
+    ctx = lne.Context(0)
+    tasks, cands = [], []
+    for i, g in enumerate(graphs):
+        idx = np.random.default_rng(100 + i).permutation(g.n)
+        tasks.append((lne.DeviceGraph(g.indptr, g.indices), torch.as_tensor(g.labels).cuda(),
+                      torch.as_tensor(idx[: g.n // 2]).cuda(), torch.as_tensor(idx[g.n // 2:]).cuda()))
+        cands.append([lne.Params(T=10, s=list(c["s"]), samples=100.0 * g.m, b=1.0, d=32, oversample=16, q=1,
+                                 k=c["k"], theta=c["theta"], mu=c["mu"], seed=100 + i)
+                      for c in synth.tuning_candidates(1000 + i, per)])
+    out = {"metric": "candidates/s (tuning, SBM suite, 32 candidates per graph)", "unit": "candidates/s",
+           "graphs": G, "sum_n": int(sum(g.n for g in graphs)), "sum_m": int(sum(g.m for g in graphs))}
+    ctx.tune_tasks(tasks[:2], cands[:2])          # warm-up: workspaces, SpMM CTA sizes
+    for w in (1, 4, 8):
+        ctx.set_option(lne.OPT_TUNE_WORKERS, w)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ma, _ = ctx.tune_tasks(tasks, cands)
+        dt = time.perf_counter() - t0
+        out[f"batched_workers{w}"] = G * per / dt
+    out["value"] = max(out[f"batched_workers{w}"] for w in (1, 4, 8))
+    out["best_macro_f1_mean"] = float(ma.max(axis=1).mean())
+    Gp = min(G, 2)
+    for j in range(2):                             # warm-up of the plain path
+        X = ctx.embed(tasks[0][0], cands[0][j])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(Gp):
+        dg, lab, tr, te = tasks[i]
+        for j in range(per):
+            X = ctx.embed(dg, cands[i][j])
+            ctx.macro_f1(X, lab, tr, te)
+    dt = time.perf_counter() - t0
+    out["plain"] = Gp * per / dt
+    out["speedup_vs_plain"] = out["value"] / out["plain"]
+    ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,8 +456,12 @@ def main():
     ap.add_argument("--scale", type=float, default=10.0, help="sample-count divisor of --case runs")
     ap.add_argument("--case", choices=["sparsifier", "rsvd", "propagate", "embed"], default=None,
                     help="run one stage on a reduced workload (for profilers) instead of the benchmark")
+    ap.add_argument("--tune", type=int, default=0, metavar="G",
+                    help="measure tuning throughput on G graphs of the SBM suite instead of the benchmark")
     args = ap.parse_args()
-    if args.case:
+    if args.tune:
+        run_tune(args)
+    elif args.case:
         run_case(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -102,6 +102,8 @@ typedef struct lne_ctx lne_ctx;
 #define LNE_AGG_BUCKET       2   /*   keys bucketed by row block, shared-memory counting */
 #define LNE_OPT_SPMM_THREADS 2   /* CTA size of the batched-tuning SpMM: 0 = picked by timing
                                     (default), or 64 / 128 / 256; results do not depend on it */
+#define LNE_OPT_TUNE_WORKERS 3   /* host worker threads (each with its own stream and workspace)
+                                    of lne_tune_tasks, 1..16 (default 4) */
 
 /* Create a context on CUDA device `device`. The context owns its workspace. */
 int lne_create(lne_ctx **out, int device);
@@ -253,6 +255,30 @@ int lne_tune_batch(lne_ctx *ctx, const lne_graph *g, const lne_params *cands, in
                    const uint8_t *labels_dev, int32_t L, const int32_t *train_dev, int64_t n_train,
                    const int32_t *test_dev, int64_t n_test, double C, int32_t iters, double *macro_f1,
                    double *micro_f1, float *X_dev, void *stream);
+
+/*
+ * Many independent tuning tasks (Sec. 4.3 tuning, repeated over data sets):
+ * task t is a graph with its labels and split (the evaluation arguments of
+ * lne_macro_f1); its ncand candidates are cands[t * ncand .. t * ncand + ncand)
+ * and its scores land in macro_f1 / micro_f1[t * ncand + j] (host). Each task is
+ * lne_tune_batch on that graph, with results identical to it. Host worker
+ * threads (LNE_OPT_TUNE_WORKERS), each with its own stream and workspace, take
+ * tasks in turn so the kernels of different graphs overlap. The call first
+ * synchronises `stream` (inputs written there are complete), and returns when
+ * every score is on the host. The first failing task's error is returned.
+ */
+typedef struct {
+    lne_graph graph;
+    const uint8_t *labels_dev;   /* [n][L] 0/1 */
+    int32_t L;
+    const int32_t *train_dev;    /* [n_train] row indices */
+    int64_t n_train;
+    const int32_t *test_dev;     /* [n_test] row indices */
+    int64_t n_test;
+} lne_task;
+
+int lne_tune_tasks(lne_ctx *ctx, const lne_task *tasks, int32_t ntasks, const lne_params *cands, int32_t ncand,
+                   double C, int32_t iters, double *macro_f1, double *micro_f1, void *stream);
 
 /*
  * Instrumentation (no counterpart in the paper, which reports wall-clock time

@@ -158,6 +158,8 @@ struct lne_ctx {
     lne::Tracer tracer;
     lne::SpmmTune spmm_tune;
     lne::PropBatchGraph *prop_graph = nullptr;
+    int tune_workers = 4;
+    std::vector<std::unique_ptr<lne::TuneWorker>> workers;
 };
 
 namespace {
@@ -253,6 +255,7 @@ void lne_destroy(lne_ctx *ctx) {
     cudaDeviceSynchronize();
     lne::set_tracer(nullptr);
     if (ctx->prop_graph) lne::destroy_prop_cache(ctx->prop_graph);
+    ctx->workers.clear();
     ctx->ws.release();
     delete ctx;
 }
@@ -272,6 +275,11 @@ int lne_set_option(lne_ctx *ctx, int option, int64_t value) {
         if (value != 0 && value != 64 && value != 128 && value != 256)
             return finish(ctx, lne::fail(LNE_ERR_INVALID, "SpMM CTA size must be 0 (timed), 64, 128 or 256"));
         ctx->spmm_tune.forced = (int)value;
+        return LNE_OK;
+    }
+    if (option == LNE_OPT_TUNE_WORKERS) {
+        if (value < 1 || value > 16) return finish(ctx, lne::fail(LNE_ERR_INVALID, "tuning workers must be 1..16"));
+        ctx->tune_workers = (int)value;
         return LNE_OK;
     }
     return finish(ctx, lne::fail(LNE_ERR_INVALID, "unknown option"));
@@ -332,6 +340,7 @@ int lne_trim(lne_ctx *ctx) {
         cudaDeviceSynchronize();
         if (ctx->prop_graph) lne::destroy_prop_cache(ctx->prop_graph);
         ctx->prop_graph = nullptr;
+        ctx->workers.clear();
         ctx->ws.release();
     }
     return finish(ctx, rc);
@@ -551,6 +560,43 @@ int lne_tune_batch(lne_ctx *ctx, const lne_graph *g, const lne_params *cands, in
         rc = lne::tune_batch(ctx->ws, ctx->prop_graph, ctx->spmm_tune, ctx->aggregation, view(g), cands, ncand,
                              labels_dev, L, train_dev, n_train, test_dev, n_test, C, iters, macro_f1, micro_f1,
                              X_dev, st);
+    return finish(ctx, rc);
+}
+
+int lne_tune_tasks(lne_ctx *ctx, const lne_task *tasks, int32_t ntasks, const lne_params *cands, int32_t ncand,
+                   double C, int32_t iters, double *macro_f1, double *micro_f1, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (!tasks || ntasks < 1 || !cands || ncand < 1))
+        rc = lne::fail(LNE_ERR_INVALID, "need at least one task and one candidate per task");
+    if (rc == 0 && (!macro_f1 || !micro_f1)) rc = lne::fail(LNE_ERR_INVALID, "NULL score outputs");
+    if (rc == 0 && iters < 0) rc = lne::fail(LNE_ERR_INVALID, "iters must be >= 0");
+    cudaStream_t st = as_stream(stream);
+    std::vector<lne::TuneTask> tt(rc == 0 ? ntasks : 0);
+    for (int t = 0; rc == 0 && t < ntasks; ++t) {
+        const lne_task &k = tasks[t];
+        rc = check_graph(&k.graph);
+        if (rc == 0 && (!k.labels_dev || k.L < 1 || !k.train_dev || k.n_train < 1 || !k.test_dev || k.n_test < 1))
+            rc = lne::fail(LNE_ERR_INVALID, "bad evaluation split or labels");
+        for (int j = 0; rc == 0 && j < ncand; ++j) rc = check_params(&cands[(size_t)t * ncand + j], true);
+        if (rc == 0) rc = check_graph_device(&k.graph, st);
+        if (rc == 0) {
+            tt[t].g = view(&k.graph);
+            tt[t].labels = k.labels_dev;
+            tt[t].L = k.L;
+            tt[t].train = k.train_dev;
+            tt[t].n_train = k.n_train;
+            tt[t].test = k.test_dev;
+            tt[t].n_test = k.n_test;
+        }
+    }
+    if (rc == 0) {   // inputs written on `stream` are complete before the workers start
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = lne::cuda_fail("cudaStreamSynchronize", e, __FILE__, __LINE__);
+    }
+    if (rc == 0)
+        rc = lne::tune_tasks(ctx->workers, ctx->tune_workers, ctx->device, ctx->spmm_tune.forced, ctx->aggregation,
+                             tt.data(), ntasks, cands, ncand, C, iters, macro_f1, micro_f1);
     return finish(ctx, rc);
 }
 

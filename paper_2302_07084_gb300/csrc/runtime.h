@@ -7,6 +7,7 @@
 #include <stdint.h>
 
 #include <map>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -173,6 +174,27 @@ int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregati
                const lne_params *cands, int ncand, const uint8_t *labels, int L, const int32_t *train,
                int64_t n_train, const int32_t *test, int64_t n_test, double Creg, int iters, double *macro,
                double *micro, float *X_out, cudaStream_t st);
+
+// Independent tuning tasks run by host worker threads, each with its own
+// workspace and stream (tune.cu).
+struct TuneWorker {
+    Workspace ws;
+    SpmmTune tune;
+    cudaStream_t st = nullptr;
+    ~TuneWorker();
+};
+struct TuneTask {
+    GraphView g;
+    const uint8_t *labels = nullptr;
+    int L = 0;
+    const int32_t *train = nullptr;
+    int64_t n_train = 0;
+    const int32_t *test = nullptr;
+    int64_t n_test = 0;
+};
+int tune_tasks(std::vector<std::unique_ptr<TuneWorker>> &workers, int nworkers, int device, int forced_threads,
+               int aggregation, const TuneTask *tasks, int ntasks, const lne_params *cands, int ncand, double Creg,
+               int iters, double *macro, double *micro);
 
 // One-vs-rest logistic regression + Micro/Macro-F1 (eval.cu).
 int macro_f1(Workspace &ws, const float *X, int64_t n, int d, int64_t ldx, const uint8_t *labels, int L,

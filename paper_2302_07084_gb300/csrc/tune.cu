@@ -19,8 +19,13 @@
 // Each candidate then gets its own final SVD (Sec. 5.4 economic SVD of P) and
 // its own Macro-F1.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
@@ -188,6 +193,66 @@ int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregati
             LNE_TRY(score(prop[b0 + t], X));
         }
     }
+    return 0;
+}
+
+}  // namespace lne
+
+// ---------------------------------------------------------------------------
+// Many independent tuning tasks (one graph + its labelled split each): host
+// worker threads, each with its own workspace and non-blocking stream, take
+// tasks in turn, so the small kernels of different graphs overlap on the GPU.
+// ---------------------------------------------------------------------------
+namespace lne {
+
+TuneWorker::~TuneWorker() {
+    if (st) cudaStreamDestroy(st);
+}
+
+int tune_tasks(std::vector<std::unique_ptr<TuneWorker>> &workers, int nworkers, int device, int forced_threads,
+               int aggregation, const TuneTask *tasks, int ntasks, const lne_params *cands, int ncand, double Creg,
+               int iters, double *macro, double *micro) {
+    nworkers = std::max(1, std::min(nworkers, ntasks));
+    while ((int)workers.size() < nworkers) {
+        auto w = std::make_unique<TuneWorker>();
+        LNE_CUDA_TRY(cudaStreamCreateWithFlags(&w->st, cudaStreamNonBlocking));
+        workers.push_back(std::move(w));
+    }
+    std::atomic<int> next{0};
+    std::atomic<bool> stop{false};
+    std::mutex mu;
+    int err = 0;
+    std::string msg;
+    auto run = [&](TuneWorker *w) {
+        clear_message();
+        set_tracer(nullptr);
+        cudaError_t e = cudaSetDevice(device);
+        int rc = e == cudaSuccess ? 0 : cuda_fail("cudaSetDevice", e, __FILE__, __LINE__);
+        w->tune.forced = forced_threads;
+        for (int t; rc == 0 && !stop.load() && (t = next.fetch_add(1)) < ntasks;) {
+            const TuneTask &k = tasks[t];
+            rc = tune_batch(w->ws, nullptr, w->tune, aggregation, k.g, cands + (size_t)t * ncand, ncand, k.labels,
+                            k.L, k.train, k.n_train, k.test, k.n_test, Creg, iters, macro + (size_t)t * ncand,
+                            micro + (size_t)t * ncand, nullptr, w->st);
+        }
+        if (rc == 0) {
+            e = cudaStreamSynchronize(w->st);
+            if (e != cudaSuccess) rc = cuda_fail("cudaStreamSynchronize", e, __FILE__, __LINE__);
+        }
+        if (rc != 0) {
+            stop.store(true);
+            std::lock_guard<std::mutex> lock(mu);
+            if (err == 0) {
+                err = rc;
+                msg = last_message();
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int i = 1; i < nworkers; ++i) pool.emplace_back(run, workers[i].get());
+    run(workers[0].get());
+    for (auto &th : pool) th.join();
+    if (err != 0) return fail(err, "tuning task failed: " + msg);
     return 0;
 }
 

@@ -28,10 +28,11 @@ EXPORTED = [
     "lne_sample_pairs", "lne_sparsifier_counts", "lne_sparsifier_csr", "lne_gaussian_sketch",
     "lne_spmm", "lne_cholqr2", "lne_rsvd", "lne_propagate", "lne_embed",
     "lne_kernel_launches", "lne_trace_enable", "lne_trace_read", "lne_set_option",
-    "lne_svd_small", "lne_svd_small_noalloc", "lne_macro_f1", "lne_tune_batch",
+    "lne_svd_small", "lne_svd_small_noalloc", "lne_macro_f1", "lne_tune_batch", "lne_tune_tasks",
 ]
 OPT_AGGREGATION = 1
 OPT_SPMM_THREADS = 2
+OPT_TUNE_WORKERS = 3
 AGG_AUTO, AGG_TABLE, AGG_BUCKET = 0, 1, 2
 
 
@@ -44,6 +45,11 @@ class LneError(RuntimeError):
 class _Graph(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("indptr", ctypes.c_void_p),
                 ("indices", ctypes.c_void_p)]
+
+
+class _Task(ctypes.Structure):
+    _fields_ = [("graph", _Graph), ("labels", ctypes.c_void_p), ("L", ctypes.c_int32), ("train", ctypes.c_void_p),
+                ("n_train", ctypes.c_int64), ("test", ctypes.c_void_p), ("n_test", ctypes.c_int64)]
 
 
 class _Params(ctypes.Structure):
@@ -109,6 +115,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp]
     L.lne_tune_batch.argtypes = [vp, gp, vp, i32, vp, i32, vp, i64, vp, i64, ctypes.c_double, i32,
                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp, vp]
+    L.lne_tune_tasks.argtypes = [vp, vp, i32, vp, i32, ctypes.c_double, i32, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_double), vp]
     L.lne_trace_read.argtypes = [vp, ctypes.POINTER(_TraceEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     _lib = L
     return L
@@ -382,6 +390,32 @@ class Context:
         del built
         out = (np.array(ma[:]), np.array(mi[:]))
         return out + (X,) if want_embeddings else out
+
+    def tune_tasks(self, tasks, cands, C: float = 1.0, iters: int = 10):
+        """Scores of many tuning tasks (lne_tune_tasks). tasks: list of
+        (DeviceGraph, labels, train_idx, test_idx) with device tensors;
+        cands: one list of Params per task, all of the same length.
+        Returns (macro, micro) numpy arrays [ntasks][ncand]."""
+        nt, nc = len(tasks), len(cands[0])
+        assert len(cands) == nt and all(len(c) == nc for c in cands)
+        keep = []
+        tarr = (_Task * nt)()
+        for t, (g, lab, tr, te) in enumerate(tasks):
+            lab = lab.contiguous().to(torch.uint8)
+            tr = tr.contiguous().to(torch.int32)
+            te = te.contiguous().to(torch.int32)
+            keep += [lab, tr, te]
+            tarr[t] = _Task(g._c(), lab.data_ptr(), lab.shape[1], tr.data_ptr(), tr.numel(), te.data_ptr(),
+                            te.numel())
+        built = [p._c() for row in cands for p in row]
+        parr = (_Params * (nt * nc))(*[b[0] for b in built])
+        ma = (ctypes.c_double * (nt * nc))()
+        mi = (ctypes.c_double * (nt * nc))()
+        self._check(self.lib.lne_tune_tasks(self.h, ctypes.cast(tarr, ctypes.c_void_p), nt,
+                                            ctypes.cast(parr, ctypes.c_void_p), nc, float(C), int(iters), ma, mi,
+                                            _stream()))
+        del built, keep
+        return np.array(ma[:]).reshape(nt, nc), np.array(mi[:]).reshape(nt, nc)
 
     def embed(self, g: DeviceGraph, p: Params, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         X = out if out is not None else torch.empty((g.n, p.d), dtype=torch.float32, device=self.dev)

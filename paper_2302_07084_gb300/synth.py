@@ -252,3 +252,30 @@ def lollipop_tiny() -> Graph:
     u = np.array([a for a, _ in e]); v = np.array([b for _, b in e])
     indptr, indices = csr_from_edges(7, u, v)
     return Graph(7, indptr, indices, None, "lollipop7")
+
+
+def tuning_graph(seed: int) -> Graph:
+    """One graph of the many-graph tuning workload: an SBM with
+    n ~ U{1000..50000}, blocks ~ U{2..20}, average degree ~ U[10, 40] and
+    intra-block edge fraction ~ U[0.6, 0.9], all drawn from ``seed``; the block
+    is each vertex's label."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(1000, 50001))
+    nb = int(rng.integers(2, 21))
+    deg = float(rng.uniform(10.0, 40.0))
+    frac = float(rng.uniform(0.6, 0.9))
+    size = n / nb
+    p_in = min(1.0, frac * deg / max(size - 1.0, 1.0))
+    p_out = min(1.0, (1.0 - frac) * deg / max(n - size, 1.0))
+    return sbm(n, nb, p_in, p_out, seed, name=f"tune_sbm{seed}")
+
+
+def tuning_candidates(seed: int, count: int, T: int = 10) -> list[dict]:
+    """Candidate parameter sets of the tuning workload: s ~ Dirichlet(1) over T
+    windows, k ~ U{3..20}, theta ~ U[0.3, 1], mu ~ U[0, 0.5]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        out.append(dict(s=rng.dirichlet(np.ones(T)), k=int(rng.integers(3, 21)),
+                        theta=float(rng.uniform(0.3, 1.0)), mu=float(rng.uniform(0.0, 0.5))))
+    return out

@@ -131,3 +131,47 @@ def test_rejects_bad_candidates(ctx, case):
     assert e.value.code == -5
     with pytest.raises(lne.LneError):
         ctx.set_option(lne.OPT_SPMM_THREADS, 96)
+
+
+def _task(seed, n, blocks):
+    g = synth.sbm(n, blocks, 12.0 / (n / blocks), 3.0 / n, seed)
+    idx = np.random.default_rng(seed).permutation(g.n)
+    tr, te = idx[: g.n // 2], idx[g.n // 2:]
+    dev = (lne.DeviceGraph.from_graph(g), torch.as_tensor(g.labels).cuda(), torch.as_tensor(tr).cuda(),
+           torch.as_tensor(te).cuda())
+    return g, dev
+
+
+def _suite_cands(g, seed, count):
+    out = []
+    for c in synth.tuning_candidates(seed, count):
+        out.append(make_params(10, c["s"], 20.0 * g.m, d=32, q=1, k=c["k"], theta=c["theta"], mu=c["mu"],
+                               seed=seed))
+    return out
+
+
+def test_tasks_equal_per_task_batches(ctx):
+    tasks = [_task(200 + t, n, b) for t, (n, b) in enumerate([(1500, 3), (2600, 5), (900, 2), (2000, 4)])]
+    cands = [_suite_cands(g, 300 + t, 5) for t, (g, _) in enumerate(tasks)]
+    ctx.set_option(lne.OPT_TUNE_WORKERS, 3)
+    ma, mi = ctx.tune_tasks([dev for _, dev in tasks], cands)
+    for t, (g, (dg, lab, tr, te)) in enumerate(tasks):
+        ma1, mi1 = ctx.tune_batch(dg, cands[t], lab, tr, te)
+        assert np.array_equal(ma[t], ma1) and np.array_equal(mi[t], mi1), t
+    # the planted blocks are recovered far above chance by the best candidate
+    assert ma.max(axis=1).min() > 0.5
+    ctx.set_option(lne.OPT_TUNE_WORKERS, 1)
+    ma2, mi2 = ctx.tune_tasks([dev for _, dev in tasks], cands)
+    assert np.array_equal(ma, ma2) and np.array_equal(mi, mi2)
+    ctx.set_option(lne.OPT_TUNE_WORKERS, 4)
+
+
+def test_tasks_report_the_failing_task(ctx):
+    tasks = [_task(210 + t, 1200, 3) for t in range(3)]
+    cands = [_suite_cands(g, 310 + t, 2) for t, (g, _) in enumerate(tasks)]
+    cands[2][1].d = 16
+    with pytest.raises(lne.LneError) as e:
+        ctx.tune_tasks([dev for _, dev in tasks], cands)
+    assert e.value.code == -1 and "dimension" in str(e.value)
+    with pytest.raises(lne.LneError):
+        ctx.set_option(lne.OPT_TUNE_WORKERS, 0)
