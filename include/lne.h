@@ -281,6 +281,43 @@ int lne_tune_tasks(lne_ctx *ctx, const lne_task *tasks, int32_t ntasks, const ln
                    double C, int32_t iters, double *macro_f1, double *micro_f1, void *stream);
 
 /*
+ * Surrogate of the tuning search. The paper tunes its hyper-parameters per data
+ * set with an AutoML search over full runs (Sec. 4.3); this regression network
+ * predicts a candidate's downstream score from 30 features (s_1..s_10, k,
+ * theta, mu, q and 16 graph statistics) so that the search runs only the
+ * candidates it ranks highest. One network per context:
+ * 30 standardised inputs -> 256 ReLU -> 256 ReLU -> 1; loss = mean squared
+ * error; Adam (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected). FP32 master
+ * weights; products use their bfloat16 roundings with FP32 accumulation.
+ * Parameters, flat FP32 (73,985): W1 [30][256], b1 [256], W2 [256][256],
+ * b2 [256], w3 [256], b3 [1] (W[i][j] = weight from input i to unit j).
+ * Features are row-major [rows][30] FP32 on the device; targets [rows].
+ *
+ * lne_surrogate_init: He-uniform weights from Philox(seed), zero biases,
+ *   mean 0 / std 1 scaling, Adam state cleared.
+ * lne_surrogate_fit_scaling: per-feature mean and population std of the rows
+ *   (std < 1e-6 -> 1), used by every later call.
+ * lne_surrogate_set_params / get_params: copy the weights and the scaling in
+ *   or out (host or device pointers; synchronises); set clears Adam state.
+ * lne_surrogate_train: `epochs` passes over the rows in a fresh seeded order
+ *   per pass, mini-batches of `batch` rows (the last one shorter), one Adam
+ *   step per batch; *final_loss (host, may be NULL) = MSE over all rows after
+ *   training (synchronises).
+ * lne_surrogate_predict: yhat_dev [rows] = network output.
+ * lne_surrogate_grad: gradient of the MSE over all `rows` at the current
+ *   weights into grad_dev [73,985] (may be NULL), *loss (host, may be NULL).
+ */
+int lne_surrogate_init(lne_ctx *ctx, uint64_t seed, void *stream);
+int lne_surrogate_fit_scaling(lne_ctx *ctx, const float *X_dev, int64_t rows, void *stream);
+int lne_surrogate_set_params(lne_ctx *ctx, const float *theta, const float *mean, const float *std, void *stream);
+int lne_surrogate_get_params(lne_ctx *ctx, float *theta, float *mean, float *std, void *stream);
+int lne_surrogate_train(lne_ctx *ctx, const float *X_dev, const float *y_dev, int64_t rows, int32_t epochs,
+                        int32_t batch, float lr, uint64_t seed, double *final_loss, void *stream);
+int lne_surrogate_predict(lne_ctx *ctx, const float *X_dev, int64_t rows, float *yhat_dev, void *stream);
+int lne_surrogate_grad(lne_ctx *ctx, const float *X_dev, const float *y_dev, int64_t rows, float *grad_dev,
+                       double *loss, void *stream);
+
+/*
  * Instrumentation (no counterpart in the paper, which reports wall-clock time
  * per stage only, Table "time distribution" of Sec. 5.4).
  *

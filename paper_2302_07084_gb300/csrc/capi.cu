@@ -160,6 +160,7 @@ struct lne_ctx {
     lne::PropBatchGraph *prop_graph = nullptr;
     int tune_workers = 4;
     std::vector<std::unique_ptr<lne::TuneWorker>> workers;
+    lne::Surrogate surrogate;
 };
 
 namespace {
@@ -597,6 +598,79 @@ int lne_tune_tasks(lne_ctx *ctx, const lne_task *tasks, int32_t ntasks, const ln
     if (rc == 0)
         rc = lne::tune_tasks(ctx->workers, ctx->tune_workers, ctx->device, ctx->spmm_tune.forced, ctx->aggregation,
                              tt.data(), ntasks, cands, ncand, C, iters, macro_f1, micro_f1);
+    return finish(ctx, rc);
+}
+
+int lne_surrogate_init(lne_ctx *ctx, uint64_t seed, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0) rc = lne::surrogate_init(ctx->surrogate, seed, as_stream(stream));
+    return finish(ctx, rc);
+}
+
+int lne_surrogate_fit_scaling(lne_ctx *ctx, const float *X_dev, int64_t rows, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (!X_dev || rows < 1)) rc = lne::fail(LNE_ERR_INVALID, "need rows >= 1 features");
+    if (rc == 0) rc = lne::surrogate_fit_scaling(ctx->surrogate, X_dev, rows, as_stream(stream));
+    return finish(ctx, rc);
+}
+
+int lne_surrogate_set_params(lne_ctx *ctx, const float *theta, const float *mean, const float *std, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (!theta || !mean || !std)) rc = lne::fail(LNE_ERR_INVALID, "NULL parameter array");
+    cudaStream_t st = as_stream(stream);
+    if (rc == 0) rc = lne::surrogate_set(ctx->surrogate, theta, mean, std, st);
+    if (rc == 0) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = lne::cuda_fail("cudaStreamSynchronize", e, __FILE__, __LINE__);
+    }
+    return finish(ctx, rc);
+}
+
+int lne_surrogate_get_params(lne_ctx *ctx, float *theta, float *mean, float *std, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    cudaStream_t st = as_stream(stream);
+    if (rc == 0) rc = lne::surrogate_get(ctx->surrogate, theta, mean, std, st);
+    if (rc == 0) {
+        cudaError_t e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = lne::cuda_fail("cudaStreamSynchronize", e, __FILE__, __LINE__);
+    }
+    return finish(ctx, rc);
+}
+
+int lne_surrogate_train(lne_ctx *ctx, const float *X_dev, const float *y_dev, int64_t rows, int32_t epochs,
+                        int32_t batch, float lr, uint64_t seed, double *final_loss, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (!X_dev || !y_dev || rows < 1 || rows > 2147483647LL))
+        rc = lne::fail(LNE_ERR_INVALID, "need 1 <= rows < 2^31 and non-NULL data");
+    if (rc == 0 && (epochs < 0 || batch < 1 || !(lr > 0.f)))
+        rc = lne::fail(LNE_ERR_INVALID, "need epochs >= 0, batch >= 1, lr > 0");
+    if (rc == 0)
+        rc = lne::surrogate_train(ctx->surrogate, ctx->ws, X_dev, y_dev, rows, epochs, batch, lr, seed, final_loss,
+                                  as_stream(stream));
+    return finish(ctx, rc);
+}
+
+int lne_surrogate_predict(lne_ctx *ctx, const float *X_dev, int64_t rows, float *yhat_dev, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (rows < 0 || (rows > 0 && (!X_dev || !yhat_dev))))
+        rc = lne::fail(LNE_ERR_INVALID, "need rows >= 0 and non-NULL buffers");
+    if (rc == 0) rc = lne::surrogate_predict(ctx->surrogate, X_dev, rows, yhat_dev, as_stream(stream));
+    return finish(ctx, rc);
+}
+
+int lne_surrogate_grad(lne_ctx *ctx, const float *X_dev, const float *y_dev, int64_t rows, float *grad_dev,
+                       double *loss, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (!X_dev || !y_dev || rows < 1)) rc = lne::fail(LNE_ERR_INVALID, "need rows >= 1 and data");
+    if (rc == 0)
+        rc = lne::surrogate_grad(ctx->surrogate, ctx->ws, X_dev, y_dev, rows, grad_dev, loss, as_stream(stream));
     return finish(ctx, rc);
 }
 

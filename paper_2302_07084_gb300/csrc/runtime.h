@@ -196,6 +196,30 @@ int tune_tasks(std::vector<std::unique_ptr<TuneWorker>> &workers, int nworkers, 
                int aggregation, const TuneTask *tasks, int ntasks, const lne_params *cands, int ncand, double Creg,
                int iters, double *macro, double *micro);
 
+// Surrogate regression network of the tuning search (surrogate.cu):
+// 30 -> 256 ReLU -> 256 ReLU -> 1, FP32 master weights, bfloat16 copies.
+constexpr int kSurrogateInputs = 30;
+constexpr int kSurrogateHidden = 256;
+constexpr int64_t kSurrogateParams = 30 * 256 + 256 + 256 * 256 + 256 + 256 + 1;
+struct Surrogate {
+    void *buf = nullptr;   // one allocation holding everything below
+    float *w = nullptr, *m = nullptr, *v = nullptr, *g = nullptr, *mean = nullptr, *std = nullptr;
+    __nv_bfloat16 *wb = nullptr, *w2t = nullptr;
+    int64_t step = 0;
+    bool ready = false;
+    ~Surrogate();
+    int ensure();
+};
+int surrogate_init(Surrogate &S, uint64_t seed, cudaStream_t st);
+int surrogate_fit_scaling(Surrogate &S, const float *X, int64_t rows, cudaStream_t st);
+int surrogate_set(Surrogate &S, const float *w, const float *mean, const float *std, cudaStream_t st);
+int surrogate_get(Surrogate &S, float *w, float *mean, float *std, cudaStream_t st);
+int surrogate_predict(Surrogate &S, const float *X, int64_t rows, float *yhat, cudaStream_t st);
+int surrogate_grad(Surrogate &S, Workspace &ws, const float *X, const float *t, int64_t rows, float *grad,
+                   double *loss, cudaStream_t st);
+int surrogate_train(Surrogate &S, Workspace &ws, const float *X, const float *t, int64_t rows, int epochs, int batch,
+                    float lr, uint64_t seed, double *final_loss, cudaStream_t st);
+
 // One-vs-rest logistic regression + Micro/Macro-F1 (eval.cu).
 int macro_f1(Workspace &ws, const float *X, int64_t n, int d, int64_t ldx, const uint8_t *labels, int L,
              const int32_t *train_idx, int64_t n_train, const int32_t *test_idx, int64_t n_test, double C, int iters,

@@ -29,7 +29,11 @@ EXPORTED = [
     "lne_spmm", "lne_cholqr2", "lne_rsvd", "lne_propagate", "lne_embed",
     "lne_kernel_launches", "lne_trace_enable", "lne_trace_read", "lne_set_option",
     "lne_svd_small", "lne_svd_small_noalloc", "lne_macro_f1", "lne_tune_batch", "lne_tune_tasks",
+    "lne_surrogate_init", "lne_surrogate_fit_scaling", "lne_surrogate_set_params", "lne_surrogate_get_params",
+    "lne_surrogate_train", "lne_surrogate_predict", "lne_surrogate_grad",
 ]
+SURROGATE_INPUTS = 30
+SURROGATE_PARAMS = 73_985
 OPT_AGGREGATION = 1
 OPT_SPMM_THREADS = 2
 OPT_TUNE_WORKERS = 3
@@ -117,6 +121,14 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                  ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp, vp]
     L.lne_tune_tasks.argtypes = [vp, vp, i32, vp, i32, ctypes.c_double, i32, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_double), vp]
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.lne_surrogate_init.argtypes = [vp, u64, vp]
+    L.lne_surrogate_fit_scaling.argtypes = [vp, vp, i64, vp]
+    L.lne_surrogate_set_params.argtypes = [vp, vp, vp, vp, vp]
+    L.lne_surrogate_get_params.argtypes = [vp, vp, vp, vp, vp]
+    L.lne_surrogate_train.argtypes = [vp, vp, vp, i64, i32, i32, ctypes.c_float, u64, dp, vp]
+    L.lne_surrogate_predict.argtypes = [vp, vp, i64, vp, vp]
+    L.lne_surrogate_grad.argtypes = [vp, vp, vp, i64, vp, dp, vp]
     L.lne_trace_read.argtypes = [vp, ctypes.POINTER(_TraceEntry), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     _lib = L
     return L
@@ -416,6 +428,53 @@ class Context:
                                             _stream()))
         del built, keep
         return np.array(ma[:]).reshape(nt, nc), np.array(mi[:]).reshape(nt, nc)
+
+    # ---- surrogate network ----------------------------------------------------
+    def surrogate_init(self, seed: int = 0):
+        self._check(self.lib.lne_surrogate_init(self.h, int(seed) & 0xFFFFFFFFFFFFFFFF, _stream()))
+
+    def surrogate_fit_scaling(self, X: torch.Tensor):
+        X = X.contiguous().float()
+        self._check(self.lib.lne_surrogate_fit_scaling(self.h, _ptr(X), X.shape[0], _stream()))
+
+    def surrogate_set_params(self, theta, mean, std):
+        th = torch.as_tensor(np.asarray(theta, np.float32)).to(self.dev)
+        mu = torch.as_tensor(np.asarray(mean, np.float32)).to(self.dev)
+        sd = torch.as_tensor(np.asarray(std, np.float32)).to(self.dev)
+        assert th.numel() == SURROGATE_PARAMS and mu.numel() == SURROGATE_INPUTS == sd.numel()
+        self._check(self.lib.lne_surrogate_set_params(self.h, _ptr(th), _ptr(mu), _ptr(sd), _stream()))
+
+    def surrogate_get_params(self):
+        th = torch.empty(SURROGATE_PARAMS, dtype=torch.float32, device=self.dev)
+        mu = torch.empty(SURROGATE_INPUTS, dtype=torch.float32, device=self.dev)
+        sd = torch.empty(SURROGATE_INPUTS, dtype=torch.float32, device=self.dev)
+        self._check(self.lib.lne_surrogate_get_params(self.h, _ptr(th), _ptr(mu), _ptr(sd), _stream()))
+        return th.cpu().numpy(), mu.cpu().numpy(), sd.cpu().numpy()
+
+    def surrogate_train(self, X: torch.Tensor, y: torch.Tensor, epochs: int, batch: int = 256, lr: float = 1e-3,
+                        seed: int = 0) -> float:
+        X = X.contiguous().float()
+        y = y.contiguous().float()
+        loss = ctypes.c_double()
+        self._check(self.lib.lne_surrogate_train(self.h, _ptr(X), _ptr(y), X.shape[0], int(epochs), int(batch),
+                                                 float(lr), int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(loss),
+                                                 _stream()))
+        return float(loss.value)
+
+    def surrogate_predict(self, X: torch.Tensor) -> torch.Tensor:
+        X = X.contiguous().float()
+        out = torch.empty(X.shape[0], dtype=torch.float32, device=self.dev)
+        self._check(self.lib.lne_surrogate_predict(self.h, _ptr(X), X.shape[0], _ptr(out), _stream()))
+        return out
+
+    def surrogate_grad(self, X: torch.Tensor, y: torch.Tensor):
+        X = X.contiguous().float()
+        y = y.contiguous().float()
+        g = torch.empty(SURROGATE_PARAMS, dtype=torch.float32, device=self.dev)
+        loss = ctypes.c_double()
+        self._check(self.lib.lne_surrogate_grad(self.h, _ptr(X), _ptr(y), X.shape[0], _ptr(g), ctypes.byref(loss),
+                                                _stream()))
+        return g, float(loss.value)
 
     def embed(self, g: DeviceGraph, p: Params, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         X = out if out is not None else torch.empty((g.n, p.d), dtype=torch.float32, device=self.dev)
