@@ -446,6 +446,61 @@ def run_tune(args):
     print(json.dumps(out))
 
 
+def run_surrogate(args):
+    """Surrogate-guided search on the SBM tuning suite (n <= 8000): the
+    network is trained on the full runs of `--surrogate` graphs (32 candidates
+    each), then on 16 held-out graphs the plain search (32 full runs) is timed
+    against the surrogate search (rank a pool of 256 by the network, run the
+    top 8); both report candidates considered per second and Macro-F1."""
+    import torch
+    from paper_2302_07084_gb300 import lne, search, synth
+    from scipy.stats import spearmanr
+    G, n_max, pool_n, top = args.surrogate, 8000, 256, 8
+
+    def task(seed):
+        g = synth.tuning_graph(seed, n_max=n_max)
+        idx = np.random.default_rng(seed).permutation(g.n)
+        return g, (lne.DeviceGraph(g.indptr, g.indices), torch.as_tensor(g.labels).cuda(),
+                   torch.as_tensor(idx[: g.n // 2]).cuda(), torch.as_tensor(idx[g.n // 2:]).cuda())
+
+    def cands(g, seed, count, off):
+        return [lne.Params(T=10, s=list(c["s"]), samples=100.0 * g.m, d=32, oversample=16, q=1, k=c["k"],
+                           theta=c["theta"], mu=c["mu"], seed=seed) for c in synth.tuning_candidates(seed + off, count)]
+
+    ctx = lne.Context(0)
+    graphs = [task(2000 + i) for i in range(G)]
+    stats = [search.graph_statistics(ctx, g.indptr, g.indices, seed=1) for g, _ in graphs]
+    cs = [cands(g, 2000 + i, 32, 1000) for i, (g, _) in enumerate(graphs)]
+    t0 = time.perf_counter()
+    scores, _ = ctx.tune_tasks([t for _, t in graphs], cs)
+    t_data = time.perf_counter() - t0
+    X, y = search.training_rows(cs, stats, scores)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = search.fit_surrogate(ctx, X, y, epochs=100, seed=1)
+    t_train = time.perf_counter() - t0
+    rows = []
+    for i in range(16):
+        g, t = task(9000 + i)
+        st = search.graph_statistics(ctx, g.indptr, g.indices, seed=1)
+        plain = cands(g, 9000 + i, 32, 1000)
+        _, sc, tp = search.plain_search(ctx, t, plain)
+        pool = plain + cands(g, 9000 + i, pool_n - 32, 3000)
+        _, best, pred, ts = search.surrogate_search(ctx, t, st, pool, top)
+        rows.append((sc.max(), best, sc[:top].max(), spearmanr(pred[:32], sc).correlation, tp, ts))
+    r = np.array(rows)
+    out = {"metric": "candidates/s (surrogate-guided search, SBM suite n<=8000)", "unit": "candidates/s",
+           "value": 16 * pool_n / r[:, 5].sum(), "plain": 16 * 32 / r[:, 4].sum(),
+           "macro_f1_plain32": float(r[:, 0].mean()), "macro_f1_surrogate": float(r[:, 1].mean()),
+           f"macro_f1_first{top}": float(r[:, 2].mean()), "gap_vs_plain": float(np.mean(r[:, 0] - r[:, 1])),
+           "wins_losses_vs_unguided": [int((r[:, 1] > r[:, 2]).sum()), int((r[:, 1] < r[:, 2]).sum())],
+           "rank_corr": float(np.nanmean(r[:, 3])), "train_rows": int(len(y)), "train_mse": loss,
+           "train_s": t_train, "data_s": t_data, "pool": pool_n, "top": top}
+    out["speedup_vs_plain"] = out["value"] / out["plain"]
+    ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -458,8 +513,12 @@ def main():
                     help="run one stage on a reduced workload (for profilers) instead of the benchmark")
     ap.add_argument("--tune", type=int, default=0, metavar="G",
                     help="measure tuning throughput on G graphs of the SBM suite instead of the benchmark")
+    ap.add_argument("--surrogate", type=int, default=0, metavar="G",
+                    help="measure surrogate-guided search after training on G graphs of the SBM suite")
     args = ap.parse_args()
-    if args.tune:
+    if args.surrogate:
+        run_surrogate(args)
+    elif args.tune:
         run_tune(args)
     elif args.case:
         run_case(args)

@@ -101,6 +101,24 @@ int fail(int code, const std::string &msg);
 const std::string &last_message();
 void clear_message();
 
+// Let `kernel` use as much dynamic shared memory as the device allows beside
+// its static shared memory. The value is the same on every call, so host
+// threads that launch the kernel concurrently cannot lower the limit under one
+// another's launch.
+template <typename Kernel>
+inline int allow_dynamic_smem(Kernel kernel) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    int dev = 0, optin = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - (int)fa.sharedSizeBytes);
+    if (e != cudaSuccess) return cuda_fail("cudaFuncSetAttribute", e, __FILE__, __LINE__);
+    return 0;
+}
+
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }

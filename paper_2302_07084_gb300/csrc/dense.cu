@@ -666,7 +666,7 @@ static int gram(Workspace &ws, const float *Y, int64_t n, int c, int64_t ld, dou
     LNE_TRY(ws.get("gram.partial", (size_t)nblk * cp * cp, &partial));
     const int smem = kGramRows * cp * 8;
     if (smem > 48 * 1024)
-        LNE_CUDA_TRY(cudaFuncSetAttribute(gram_partial_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        LNE_TRY(allow_dynamic_smem(gram_partial_kernel));
     {
         LNE_TRACE("gram_partial", st);
         gram_partial_kernel<<<(unsigned)nblk, threads, smem, st>>>(Y, n, c, ld, rows_per, partial);
@@ -685,7 +685,7 @@ static int chol(Workspace &ws, const double *G, int c, double *R, cudaStream_t s
     LNE_TRY(ws.get("chol.status", 1, &status));
     const int smem = c <= kMaxSmemC ? c * c * 8 : 0;
     if (smem > 48 * 1024)
-        LNE_CUDA_TRY(cudaFuncSetAttribute(chol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        LNE_TRY(allow_dynamic_smem(chol_kernel));
     {
         LNE_TRACE("chol", st);
         chol_kernel<<<1, kCholThreads, smem, st>>>(G, c, R, status);
@@ -706,9 +706,7 @@ static int trsm_rows(const float *Y, int64_t n, int c, int64_t ldy, const double
     LNE_TRACE("trsm_rows", st);
 #define LNE_TRSM_CASE(K)                                                                               \
     case K:                                                                                            \
-        if (smem > 48 * 1024)                                                                          \
-            LNE_CUDA_TRY(cudaFuncSetAttribute(trsm_rows_kernel<K>,                                     \
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem));     \
+        if (smem > 48 * 1024) LNE_TRY(allow_dynamic_smem(trsm_rows_kernel<K>));                        \
         trsm_rows_kernel<K><<<blocks, 256, smem, st>>>(Y, n, c, ldy, R, Q, ldq);                      \
         break;
     switch (nt) {
@@ -788,7 +786,7 @@ int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma,
     const int threads = std::max(32, std::min(1024, (m / 2 * kJacTPP + 31) / 32 * 32));
     const int smem = 2 * c * jac_ld(c) * 4;
     if (smem > 48 * 1024)
-        LNE_CUDA_TRY(cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        LNE_TRY(allow_dynamic_smem(jacobi32_kernel));
     {
         LNE_TRACE("jacobi32", st);
         jacobi32_kernel<<<1, threads, smem, st>>>(R, c, U, V, 20, sweeps);
@@ -915,7 +913,7 @@ extern "C" int lne_svd_small_noalloc(const double *R_dev, int32_t c, double *U_d
     const int threads = std::max(32, std::min(1024, (m / 2 * kJacTPP + 31) / 32 * 32));
     const int smem = 2 * c * jac_ld(c) * 4;
     if (smem > 48 * 1024)
-        LNE_CUDA_TRY(cudaFuncSetAttribute(jacobi32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        LNE_TRY(allow_dynamic_smem(jacobi32_kernel));
     jacobi32_kernel<<<1, threads, smem, st>>>(R_dev, c, U, V, 20, sweeps);
     LNE_LAUNCH_CHECK();
     for (int it = 0; it < 4; ++it) {

@@ -270,7 +270,7 @@ int macro_f1(Workspace &ws, const float *X, int64_t n, int d, int64_t ldx, const
     }
     const int hsmem = 2 * 32 * dp * 4;
     const int ssmem = (da * da + da) * 8;
-    LNE_CUDA_TRY(cudaFuncSetAttribute(newton_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ssmem));
+    LNE_TRY(allow_dynamic_smem(newton_solve_kernel));
     for (int it = 0; it < iters; ++it) {
         LNE_TRY(right_multiply(Xa, n_train, da, da, W, L, L, nullptr, Z, L, st));
         {

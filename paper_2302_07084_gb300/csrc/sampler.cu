@@ -1086,7 +1086,7 @@ int sample_pairs(Workspace &ws, const GraphView &g, const SamplerSpec &sp, int64
     const int64_t ntiles = ceil_div(a1 - a0, tile_arcs);
     const int smem = walk_smem_bytes(tile_arcs, 0);
     // dynamic shared memory comes on top of the kernel's static tables
-    LNE_CUDA_TRY(cudaFuncSetAttribute(walk_emit_kernel<uint32_t, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint32_t, 0>));
     {
         LNE_TRACE("walk_emit", st);
         walk_emit_kernel<uint32_t, 0><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
@@ -1135,7 +1135,7 @@ int sample_and_reduce(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
     const int nb_smem = nb <= kMaxSmemBuckets ? nb : 0;
     const int smem = walk_smem_bytes(tile_arcs, nb_smem);
     // dynamic shared memory comes on top of the kernel's static tables
-    LNE_CUDA_TRY(cudaFuncSetAttribute(walk_emit_kernel<uint32_t, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint32_t, 1>));
     {
         LNE_TRACE("walk_emit", st);
         walk_emit_kernel<uint32_t, 1><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
@@ -1150,8 +1150,7 @@ int sample_and_reduce(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
         if (nb <= kMaxSmemBuckets) {
             const int sm = nb * (8 + 4);
             if (sm > 48 * 1024)
-                LNE_CUDA_TRY(cudaFuncSetAttribute(bucket_scatter_kernel<uint32_t>,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sm));
+                LNE_TRY(allow_dynamic_smem(bucket_scatter_kernel<uint32_t>));
             const int64_t grid = ceil_div(total, (int64_t)kScatterThreads * kScatterItems);
             LNE_TRACE("bucket_scatter", st);
             bucket_scatter_kernel<uint32_t><<<(unsigned)grid, kScatterThreads, sm, st>>>(
@@ -1167,8 +1166,7 @@ int sample_and_reduce(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
     uint32_t *rcnt = nullptr;
     LNE_TRY(ws.get("spars.rcnt", (size_t)std::max<int64_t>(total, 1), &rcnt));
     const int rsmem = (1 << kBucketBits) * 4;
-    LNE_CUDA_TRY(cudaFuncSetAttribute(bucket_reduce_kernel<uint32_t>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, rsmem));
+    LNE_TRY(allow_dynamic_smem(bucket_reduce_kernel<uint32_t>));
     {
         LNE_TRACE("bucket_reduce", st);
         bucket_reduce_kernel<uint32_t><<<nb, kReduceThreads, rsmem, st>>>(keys1, R->bucket_off, keys0,
@@ -1252,8 +1250,7 @@ int bucket_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResu
     LNE_TRY(ws.get("csr.too_long", 1, &too_long));
     LNE_CUDA_TRY(cudaMemsetAsync(too_long, 0, sizeof(int), st));
     const int ssmem = kSortMax * 8;
-    LNE_CUDA_TRY(cudaFuncSetAttribute(csr_row_sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      ssmem));
+    LNE_TRY(allow_dynamic_smem(csr_row_sort_kernel));
     {
         LNE_TRACE("csr_row_sort", st);
         csr_row_sort_kernel<<<(unsigned)g.n, kSortThreads, ssmem, st>>>(out->indptr, out->indices,
@@ -1298,7 +1295,7 @@ int sample_table(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Table
     const int tile_arcs = choose_tile_arcs(g.nnz, (double)sp.base + 0.5);
     const int64_t ntiles = ceil_div(g.nnz, tile_arcs);
     const int smem = walk_smem_bytes(tile_arcs, 0);
-    LNE_CUDA_TRY(cudaFuncSetAttribute(walk_emit_kernel<uint32_t, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint32_t, 2>));
     LNE_TRACE("walk_count", st);
     walk_emit_kernel<uint32_t, 2><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
         A, 0, g.nnz, tile_arcs, nullptr, tb->T, nullptr, nullptr, nullptr, (int)ld);

@@ -367,9 +367,8 @@ int batch_bufs(Workspace &ws, int64_t B, BatchBufs *b) {
 }
 
 int set_smem_attributes() {
-    LNE_CUDA_TRY(cudaFuncSetAttribute(sur_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kFwdSmem));
-    LNE_CUDA_TRY(
-        cudaFuncSetAttribute(sur_backward_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBwdSmem));
+    LNE_TRY(allow_dynamic_smem(sur_forward_kernel));
+    LNE_TRY(allow_dynamic_smem(sur_backward_rows_kernel));
     return 0;
 }
 

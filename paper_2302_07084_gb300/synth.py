@@ -254,16 +254,16 @@ def lollipop_tiny() -> Graph:
     return Graph(7, indptr, indices, None, "lollipop7")
 
 
-def tuning_graph(seed: int) -> Graph:
+def tuning_graph(seed: int, n_max: int = 50000, blocks_max: int = 20, frac=(0.35, 0.6)) -> Graph:
     """One graph of the many-graph tuning workload: an SBM with
-    n ~ U{1000..50000}, blocks ~ U{2..20}, average degree ~ U[10, 40] and
-    intra-block edge fraction ~ U[0.6, 0.9], all drawn from ``seed``; the block
-    is each vertex's label."""
+    n ~ U{1000..n_max}, blocks ~ U{2..blocks_max}, average degree ~ U[10, 40]
+    and intra-block edge fraction ~ U[frac], all drawn from ``seed``; the
+    block is each vertex's label."""
     rng = np.random.default_rng(seed)
-    n = int(rng.integers(1000, 50001))
-    nb = int(rng.integers(2, 21))
+    n = int(rng.integers(1000, n_max + 1))
+    nb = int(rng.integers(2, blocks_max + 1))
     deg = float(rng.uniform(10.0, 40.0))
-    frac = float(rng.uniform(0.6, 0.9))
+    frac = float(rng.uniform(frac[0], frac[1]))
     size = n / nb
     p_in = min(1.0, frac * deg / max(size - 1.0, 1.0))
     p_out = min(1.0, (1.0 - frac) * deg / max(n - size, 1.0))
