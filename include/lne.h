@@ -97,9 +97,10 @@ typedef struct lne_ctx lne_ctx;
 
 /* Options of a context (lne_set_option). */
 #define LNE_OPT_AGGREGATION  1   /* how sampled pairs are counted: */
-#define LNE_AGG_AUTO         0   /*   dense table when it fits, else bucket sort */
-#define LNE_AGG_TABLE        1   /*   dense n x n count table, atomic increments */
-#define LNE_AGG_BUCKET       2   /*   keys bucketed by row block, shared-memory counting */
+#define LNE_AGG_AUTO         0   /*   dense table when n <= 65536 and it is the cheaper, else sort */
+#define LNE_AGG_TABLE        1   /*   dense n x n count table, atomic increments (n <= 65536) */
+#define LNE_AGG_BUCKET       2   /*   keys bucketed by row block, shared-memory counting (n <= 65536) */
+#define LNE_AGG_SORT         3   /*   64-bit keys, radix sort and run lengths (any n < 2^31) */
 #define LNE_OPT_SPMM_THREADS 2   /* CTA size of the batched-tuning SpMM: 0 = picked by timing
                                     (default), or 64 / 128 / 256; results do not depend on it */
 #define LNE_OPT_TUNE_WORKERS 3   /* host worker threads (each with its own stream and workspace)

@@ -1,5 +1,6 @@
 // C ABI of the library (declared in include/lne.h): argument checks, device
 // selection, error reporting, and the composition of the stages.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -118,7 +119,7 @@ int Workspace::get(const std::string &name, size_t bytes, void **ptr) {
             if (e != cudaSuccess) return cuda_fail("cudaFree", e, __FILE__, __LINE__);
         }
         // round up to limit regrowth
-        size_t want = bytes + bytes / 8;
+        size_t want = bytes + std::min(bytes / 8, (size_t)1 << 28);
         want = (want + 255) & ~(size_t)255;
         cudaError_t e = cudaMalloc(&b.p, want);
         if (e != cudaSuccess) {
@@ -140,6 +141,13 @@ void Workspace::release() {
     for (auto &kv : bufs_)
         if (kv.second.p) cudaFree(kv.second.p);
     bufs_.clear();
+}
+
+void Workspace::release(const std::string &name) {
+    auto it = bufs_.find(name);
+    if (it == bufs_.end()) return;
+    if (it->second.p) cudaFree(it->second.p);
+    bufs_.erase(it);
 }
 
 int64_t Workspace::bytes() const {
@@ -267,7 +275,7 @@ int lne_set_option(lne_ctx *ctx, int option, int64_t value) {
     if (!ctx) return LNE_ERR_INVALID;
     lne::clear_message();
     if (option == LNE_OPT_AGGREGATION) {
-        if (value != LNE_AGG_AUTO && value != LNE_AGG_TABLE && value != LNE_AGG_BUCKET)
+        if (value != LNE_AGG_AUTO && value != LNE_AGG_TABLE && value != LNE_AGG_BUCKET && value != LNE_AGG_SORT)
             return finish(ctx, lne::fail(LNE_ERR_INVALID, "unknown aggregation method"));
         ctx->aggregation = (int)value;
         return LNE_OK;

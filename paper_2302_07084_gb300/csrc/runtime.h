@@ -27,6 +27,8 @@ public:
         return get(name, count * sizeof(T), reinterpret_cast<void **>(ptr));
     }
     void release();
+    // Frees one named buffer (no-op if absent).
+    void release(const std::string &name);
     int64_t bytes() const;
 
 private:
@@ -228,5 +230,18 @@ int macro_f1(Workspace &ws, const float *X, int64_t n, int d, int64_t ldx, const
 // Exclusive scan helpers (scan.cu).
 int scan_exclusive_u32_to_i64(const uint32_t *in, int64_t *out, int64_t n, cudaStream_t st);
 int scan_exclusive_i64(const int64_t *in, int64_t *out, int64_t n, cudaStream_t st);
+// In place, per row: data[r][0..n) -> exclusive prefix, data[r][n] = row total
+// (rows of n + 1 entries).
+int scan_exclusive_rows_i64(int64_t *data, int64_t rows, int64_t n, cudaStream_t st);
+
+// Sorting of 64-bit keys (sort.cu). Stable LSD radix sort over the low `bits`
+// bits with an optional 32-bit payload (vals may be NULL); the result lands in
+// keys_alt / vals_alt when *in_alt is true, else in keys / vals.
+int radix_sort_u64(Workspace &ws, uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
+                   int64_t n, int bits, bool *in_alt, cudaStream_t st);
+// Unique keys of a sorted array and their multiplicities; start_scratch holds
+// n int64 values.
+int run_length(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t *ukeys, uint32_t *counts,
+               int64_t *start_scratch, int64_t *nunique, cudaStream_t st);
 
 }  // namespace lne

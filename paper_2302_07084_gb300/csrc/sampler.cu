@@ -324,7 +324,8 @@ __global__ void __launch_bounds__(kWalkThreads) tile_counts_kernel(WalkArgs A, i
 
 // MODE 0: write ordered endpoint pairs (u1, v1). MODE 1: write canonical keys
 // and count key buckets. MODE 2: add the pair into the dense count table
-// table[x * ld + y] (x <= y); `keys` is the table, ld = nb_smem.
+// table[x * ld + y] (x <= y); `keys` is the table, ld = nb_smem. MODE 3: write
+// the canonical key at the sample's position (no counting).
 template <typename KeyT, int MODE>
 __global__ void __launch_bounds__(kWalkThreads, 4) walk_emit_kernel(
     WalkArgs A, int64_t a_begin, int64_t a_end, int tile_arcs, const int64_t *__restrict__ tile_off,
@@ -390,6 +391,9 @@ __global__ void __launch_bounds__(kWalkThreads, 4) walk_emit_kernel(
         } else if (MODE == 2) {
             const uint32_t x = (uint32_t)min(pu, pv), y = (uint32_t)max(pu, pv);
             atomicAdd(reinterpret_cast<uint32_t *>(keys) + (size_t)x * (uint32_t)nb_smem + y, 1u);
+        } else if (MODE == 3) {
+            const uint32_t x = (uint32_t)min(pu, pv), y = (uint32_t)max(pu, pv);
+            keys[out0 + s] = ((KeyT)x << A.B) | (KeyT)y;
         } else {
             const uint32_t x = (uint32_t)min(pu, pv), y = (uint32_t)max(pu, pv);
             const KeyT key = ((KeyT)x << A.B) | (KeyT)y;
@@ -925,6 +929,183 @@ __global__ void __launch_bounds__(256) tile_fill_kernel(const uint32_t *__restri
     }
 }
 
+// ---------------------------------------------------------------------------
+// Sort path (any n < 2^31): 64-bit keys, radix sort, run lengths, then the
+// symmetric CSR assembled from the sorted unique pairs. Every entry u of the
+// unique list is handled by a thread owning kSortRun consecutive entries, so
+// the kept / mirrored indices of an entry come from one block scan per tile.
+// ---------------------------------------------------------------------------
+constexpr int kPathThreads = 256;
+constexpr int kPathRun = 32;
+constexpr int kPathTile = kPathThreads * kPathRun;
+
+struct PathEntry {
+    int32_t x, y;
+    float v;
+};
+
+__device__ __forceinline__ PathEntry path_entry(const uint64_t *__restrict__ uk, const uint32_t *__restrict__ cnt,
+                                                int64_t u, int B, const int64_t *__restrict__ indptr,
+                                                const NetmfConst &kc) {
+    PathEntry e;
+    const uint64_t k = uk[u];
+    e.x = (int32_t)(k >> B);
+    e.y = (int32_t)(k & ((1ull << B) - 1ull));
+    const int64_t dx = __ldg(indptr + e.x + 1) - __ldg(indptr + e.x);
+    const int64_t dy = __ldg(indptr + e.y + 1) - __ldg(indptr + e.y);
+    e.v = netmf_value(cnt[u], dx, dy, e.x == e.y, kc);
+    return e;
+}
+
+__device__ __forceinline__ int64_t path_block_scan(int64_t v, int64_t *s_warp) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    int64_t before = 0;
+    for (int w = 0; w < warp; ++w) before += s_warp[w];
+    __syncthreads();
+    return before + x - v;
+}
+
+__global__ void decode_keys_kernel(const uint64_t *__restrict__ uk, int64_t u, int B, int32_t *__restrict__ x,
+                                   int32_t *__restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < u; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = uk[i];
+        x[i] = (int32_t)(k >> B);
+        y[i] = (int32_t)(k & ((1ull << B) - 1ull));
+    }
+}
+
+// Per tile: entries kept (v > 1, i.e. log v > 0) and kept off-diagonal ones.
+__global__ void __launch_bounds__(kPathThreads) path_count_kernel(const uint64_t *__restrict__ uk,
+                                                                  const uint32_t *__restrict__ cnt, int64_t U, int B,
+                                                                  const int64_t *__restrict__ indptr, NetmfConst kc,
+                                                                  uint32_t *__restrict__ tile_kept,
+                                                                  uint32_t *__restrict__ tile_mir) {
+    __shared__ uint32_t s_k, s_m;
+    if (threadIdx.x == 0) s_k = s_m = 0;
+    __syncthreads();
+    const int64_t i0 = (int64_t)blockIdx.x * kPathTile + (int64_t)threadIdx.x * kPathRun;
+    uint32_t ck = 0, cm = 0;
+    for (int j = 0; j < kPathRun; ++j) {
+        const int64_t u = i0 + j;
+        if (u >= U) break;
+        const PathEntry e = path_entry(uk, cnt, u, B, indptr, kc);
+        if (e.v > 0.f) {
+            ++ck;
+            cm += e.x != e.y;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ck += __shfl_xor_sync(0xffffffffu, ck, o);
+        cm += __shfl_xor_sync(0xffffffffu, cm, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s_k, ck);
+        atomicAdd(&s_m, cm);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tile_kept[blockIdx.x] = s_k;
+        tile_mir[blockIdx.x] = s_m;
+    }
+}
+
+// Row lengths, the first kept index of every row, and the mirrored entries
+// (key (y << B) | x, value bits) in unique-list order.
+__global__ void __launch_bounds__(kPathThreads) path_rows_kernel(
+    const uint64_t *__restrict__ uk, const uint32_t *__restrict__ cnt, int64_t U, int B,
+    const int64_t *__restrict__ indptr, NetmfConst kc, const int64_t *__restrict__ kept_off,
+    const int64_t *__restrict__ mir_off, uint32_t *__restrict__ rowlen, uint32_t *__restrict__ mirlen,
+    unsigned long long *__restrict__ dstart, uint64_t *__restrict__ mkey, uint32_t *__restrict__ mval) {
+    __shared__ int64_t s_warp[kPathThreads / 32];
+    const int64_t i0 = (int64_t)blockIdx.x * kPathTile + (int64_t)threadIdx.x * kPathRun;
+    uint32_t ck = 0, cm = 0;
+    for (int j = 0; j < kPathRun; ++j) {
+        const int64_t u = i0 + j;
+        if (u >= U) break;
+        const PathEntry e = path_entry(uk, cnt, u, B, indptr, kc);
+        if (e.v > 0.f) {
+            ++ck;
+            cm += e.x != e.y;
+        }
+    }
+    int64_t k = kept_off[blockIdx.x] + path_block_scan(ck, s_warp);
+    int64_t m = mir_off[blockIdx.x] + path_block_scan(cm, s_warp);
+    for (int j = 0; j < kPathRun; ++j) {
+        const int64_t u = i0 + j;
+        if (u >= U) break;
+        const PathEntry e = path_entry(uk, cnt, u, B, indptr, kc);
+        if (!(e.v > 0.f)) continue;
+        atomicAdd(&rowlen[e.x], 1u);
+        atomicMin(&dstart[e.x], (unsigned long long)k);
+        if (e.x != e.y) {
+            atomicAdd(&rowlen[e.y], 1u);
+            atomicAdd(&mirlen[e.y], 1u);
+            mkey[m] = ((uint64_t)(uint32_t)e.y << B) | (uint64_t)(uint32_t)e.x;
+            mval[m] = __float_as_uint(e.v);
+            ++m;
+        }
+        ++k;
+    }
+}
+
+// Row x of the CSR: its mirrored entries (columns < x) first, then the direct
+// ones (columns >= x) in unique-list order.
+__global__ void __launch_bounds__(kPathThreads) path_direct_fill_kernel(
+    const uint64_t *__restrict__ uk, const uint32_t *__restrict__ cnt, int64_t U, int B,
+    const int64_t *__restrict__ indptr, NetmfConst kc, const int64_t *__restrict__ kept_off,
+    const int64_t *__restrict__ rowptr, const uint32_t *__restrict__ mirlen,
+    const unsigned long long *__restrict__ dstart, int32_t *__restrict__ col, float *__restrict__ data) {
+    __shared__ int64_t s_warp[kPathThreads / 32];
+    const int64_t i0 = (int64_t)blockIdx.x * kPathTile + (int64_t)threadIdx.x * kPathRun;
+    uint32_t ck = 0;
+    for (int j = 0; j < kPathRun; ++j) {
+        const int64_t u = i0 + j;
+        if (u >= U) break;
+        ck += path_entry(uk, cnt, u, B, indptr, kc).v > 0.f;
+    }
+    int64_t k = kept_off[blockIdx.x] + path_block_scan(ck, s_warp);
+    for (int j = 0; j < kPathRun; ++j) {
+        const int64_t u = i0 + j;
+        if (u >= U) break;
+        const PathEntry e = path_entry(uk, cnt, u, B, indptr, kc);
+        if (!(e.v > 0.f)) continue;
+        const int64_t pos = rowptr[e.x] + mirlen[e.x] + (k - (int64_t)dstart[e.x]);
+        col[pos] = e.y;
+        data[pos] = e.v;
+        ++k;
+    }
+}
+
+__global__ void path_mirror_first_kernel(const uint64_t *__restrict__ mk, int64_t M, int B,
+                                         int64_t *__restrict__ first) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < M; f += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t r = mk[f] >> B;
+        if (f == 0 || (mk[f - 1] >> B) != r) first[r] = f;
+    }
+}
+
+__global__ void path_mirror_fill_kernel(const uint64_t *__restrict__ mk, const uint32_t *__restrict__ mv,
+                                        int64_t M, int B, const int64_t *__restrict__ rowptr,
+                                        const int64_t *__restrict__ first, int32_t *__restrict__ col,
+                                        float *__restrict__ data) {
+    for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < M; f += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = mk[f];
+        const int64_t r = (int64_t)(k >> B);
+        const int64_t pos = rowptr[r] + (f - first[r]);
+        col[pos] = (int32_t)(k & ((1ull << B) - 1ull));
+        data[pos] = __uint_as_float(mv[f]);
+    }
+}
+
 WalkArgs make_walk_args(const GraphView &g, const SamplerSpec &sp) {
     WalkArgs A;
     A.indptr = g.indptr;
@@ -1275,10 +1456,170 @@ struct Table {
     int nt = 0;
 };
 
+// ---- sort path: host side ----------------------------------------------------
+
+// Samples of every arc as 64-bit keys, sorted, as unique keys with counts.
+// On return the unique keys are in *uk ("sort.k0" or "sort.k1"), counts in
+// "sort.cnt"; the other key buffer and the run starts are released.
+struct SortRaw {
+    int64_t total = 0, U = 0;
+    uint64_t *uk = nullptr;
+    uint32_t *cnt = nullptr;
+    const char *uk_name = nullptr, *spare_name = nullptr;
+};
+
+int sort_raw(Workspace &ws, const GraphView &g, const SamplerSpec &sp, SortRaw *R, cudaStream_t st) {
+    if (2 * sp.B > 64) return fail(LNE_ERR_UNSUPPORTED, "pair keys need 2 ceil(log2 n) <= 64 bits");
+    WalkArgs A = make_walk_args(g, sp);
+    LNE_TRY(attach_vinfo(ws, g, &A, st));
+    const int tile_arcs = choose_tile_arcs(g.nnz, (double)sp.base + 0.5);
+    int64_t *tile_off = nullptr;
+    int64_t total = 0;
+    LNE_TRY(tile_offsets(ws, A, 0, g.nnz, tile_arcs, &tile_off, &total, st));
+    R->total = total;
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    LNE_TRY(ws.get("sort.k0", (size_t)std::max<int64_t>(total, 1), &k0));
+    LNE_TRY(ws.get("sort.k1", (size_t)std::max<int64_t>(total, 1), &k1));
+    const int64_t ntiles = ceil_div(g.nnz, tile_arcs);
+    const int smem = walk_smem_bytes(tile_arcs, 0);
+    LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint64_t, 3>));
+    {
+        LNE_TRACE("walk_keys", st);
+        walk_emit_kernel<uint64_t, 3><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
+            A, 0, g.nnz, tile_arcs, tile_off, k0, nullptr, nullptr, nullptr, 0);
+        LNE_LAUNCH_CHECK();
+    }
+    bool in_alt = false;
+    LNE_TRY(radix_sort_u64(ws, k0, k1, nullptr, nullptr, total, 2 * sp.B, &in_alt, st));
+    uint64_t *sorted = in_alt ? k1 : k0, *spare = in_alt ? k0 : k1;
+    int64_t *start = nullptr;
+    LNE_TRY(ws.get("sort.start", (size_t)std::max<int64_t>(total, 1), &start));
+    LNE_TRY(ws.get("sort.cnt", (size_t)std::max<int64_t>(total, 1), &R->cnt));
+    LNE_TRY(run_length(ws, sorted, total, spare, R->cnt, start, &R->U, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    ws.release("sort.start");
+    ws.release("sort.offs");
+    R->uk = spare;
+    R->uk_name = in_alt ? "sort.k0" : "sort.k1";
+    R->spare_name = in_alt ? "sort.k1" : "sort.k0";
+    ws.release(R->spare_name);
+    return 0;
+}
+
+void sort_release(Workspace &ws) {
+    for (const char *n : {"sort.k0", "sort.k1", "sort.cnt", "sort.start", "sort.offs", "sort.mk", "sort.mv",
+                          "path.tk", "path.tm", "path.ko", "path.mo", "path.rowlen", "path.mirlen", "path.dstart",
+                          "path.first"})
+        ws.release(n);
+}
+
+int sort_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out, cudaStream_t st) {
+    SortRaw R;
+    LNE_TRY(sort_raw(ws, g, sp, &R, st));
+    const int64_t u = R.U;
+    LNE_TRY(ws.get("counts.x", (size_t)std::max<int64_t>(u, 1), &out->x));
+    LNE_TRY(ws.get("counts.y", (size_t)std::max<int64_t>(u, 1), &out->y));
+    LNE_TRY(ws.get("counts.cnt", (size_t)std::max<int64_t>(u, 1), &out->cnt));
+    if (u > 0) {
+        LNE_TRACE("decode_keys", st);
+        decode_keys_kernel<<<(unsigned)std::min<int64_t>(ceil_div(u, 256), 152 * 16), 256, 0, st>>>(
+            R.uk, u, sp.B, out->x, out->y);
+        LNE_LAUNCH_CHECK();
+        LNE_CUDA_TRY(cudaMemcpyAsync(out->cnt, R.cnt, sizeof(uint32_t) * u, cudaMemcpyDeviceToDevice, st));
+    }
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    sort_release(ws);
+    out->nnz = u;
+    out->total_samples = R.total;
+    return 0;
+}
+
+int sort_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out, cudaStream_t st) {
+    SortRaw R;
+    LNE_TRY(sort_raw(ws, g, sp, &R, st));
+    const int64_t U = R.U, n = g.n;
+    const int64_t ntiles = std::max<int64_t>(1, ceil_div(U, (int64_t)kPathTile));
+    const NetmfConst kc = netmf_const(sp);
+    uint32_t *tk = nullptr, *tm = nullptr, *rowlen = nullptr, *mirlen = nullptr;
+    int64_t *ko = nullptr, *mo = nullptr;
+    unsigned long long *dstart = nullptr;
+    LNE_TRY(ws.get("path.tk", (size_t)ntiles, &tk));
+    LNE_TRY(ws.get("path.tm", (size_t)ntiles, &tm));
+    LNE_TRY(ws.get("path.ko", (size_t)ntiles + 1, &ko));
+    LNE_TRY(ws.get("path.mo", (size_t)ntiles + 1, &mo));
+    LNE_TRY(ws.get("path.rowlen", (size_t)n, &rowlen));
+    LNE_TRY(ws.get("path.mirlen", (size_t)n, &mirlen));
+    LNE_TRY(ws.get("path.dstart", (size_t)n, &dstart));
+    LNE_TRY(ws.get("csr.indptr", (size_t)n + 1, &out->indptr));
+    LNE_CUDA_TRY(cudaMemsetAsync(rowlen, 0, sizeof(uint32_t) * n, st));
+    LNE_CUDA_TRY(cudaMemsetAsync(mirlen, 0, sizeof(uint32_t) * n, st));
+    LNE_CUDA_TRY(cudaMemsetAsync(dstart, 0xFF, sizeof(unsigned long long) * n, st));
+    {
+        LNE_TRACE("path_count", st);
+        path_count_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, U, sp.B, g.indptr, kc, tk, tm);
+        LNE_LAUNCH_CHECK();
+    }
+    LNE_TRY(scan_exclusive_u32_to_i64(tk, ko, ntiles, st));
+    LNE_TRY(scan_exclusive_u32_to_i64(tm, mo, ntiles, st));
+    int64_t nm = 0;
+    LNE_CUDA_TRY(cudaMemcpyAsync(&nm, mo + ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    uint64_t *mk = nullptr;
+    uint32_t *mv = nullptr;
+    LNE_TRY(ws.get("sort.mk", (size_t)std::max<int64_t>(nm, 1), &mk));
+    LNE_TRY(ws.get("sort.mv", (size_t)std::max<int64_t>(nm, 1), &mv));
+    {
+        LNE_TRACE("path_rows", st);
+        path_rows_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, U, sp.B, g.indptr, kc, ko, mo,
+                                                                   rowlen, mirlen, dstart, mk, mv);
+        LNE_LAUNCH_CHECK();
+    }
+    LNE_TRY(scan_exclusive_u32_to_i64(rowlen, out->indptr, n, st));
+    int64_t nnz = 0;
+    LNE_CUDA_TRY(cudaMemcpyAsync(&nnz, out->indptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    LNE_TRY(ws.get("csr.indices", (size_t)std::max<int64_t>(nnz, 1), &out->indices));
+    LNE_TRY(ws.get("csr.data", (size_t)std::max<int64_t>(nnz, 1), &out->data));
+    {
+        LNE_TRACE("path_direct_fill", st);
+        path_direct_fill_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, U, sp.B, g.indptr, kc, ko,
+                                                                          out->indptr, mirlen, dstart, out->indices,
+                                                                          out->data);
+        LNE_LAUNCH_CHECK();
+    }
+    // mirrored entries sorted by (row y, column x); the unique keys and the
+    // counts are no longer needed and serve as the sort's spare buffers
+    bool in_alt = false;
+    LNE_TRY(radix_sort_u64(ws, mk, R.uk, mv, R.cnt, nm, 2 * sp.B, &in_alt, st));
+    const uint64_t *smk = in_alt ? R.uk : mk;
+    const uint32_t *smv = in_alt ? R.cnt : mv;
+    int64_t *first = nullptr;
+    LNE_TRY(ws.get("path.first", (size_t)n, &first));
+    if (nm > 0) {
+        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(nm, 256), 152 * 16);
+        LNE_TRACE("path_mirror_fill", st);
+        path_mirror_first_kernel<<<grid, 256, 0, st>>>(smk, nm, sp.B, first);
+        LNE_LAUNCH_CHECK();
+        path_mirror_fill_kernel<<<grid, 256, 0, st>>>(smk, smv, nm, sp.B, out->indptr, first, out->indices,
+                                                      out->data);
+        LNE_LAUNCH_CHECK();
+    }
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    sort_release(ws);
+    out->n = n;
+    out->nnz = nnz;
+    return 0;
+}
+
 bool use_table(const GraphView &g, const SamplerSpec &sp) {
     if (sp.aggregation == LNE_AGG_TABLE) return true;
-    if (sp.aggregation == LNE_AGG_BUCKET) return false;
-    return g.n <= 65536;
+    if (sp.aggregation != LNE_AGG_AUTO) return false;
+    if (g.n > 65536) return false;
+    // the table costs ~10 passes over its n_pad^2 / 2 counters, the sort ~100
+    // bytes of traffic per sample: the table when it is the cheaper of the two
+    const double ld = (double)ceil_div(g.n, (int64_t)kTile) * kTile;
+    const double samples = (double)g.nnz * ((double)sp.base + (double)sp.thr_frac / 4294967296.0);
+    return ld * ld <= 10.0 * samples;
 }
 
 // Walk every arc's samples and count them into the dense upper-triangle table.
@@ -1384,14 +1725,16 @@ int table_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResul
 int sparsifier_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out,
                       cudaStream_t st) {
     if (use_table(g, sp)) LNE_TRY(table_counts(ws, g, sp, out, st));
-    else LNE_TRY(bucket_counts(ws, g, sp, out, st));
+    else if (sp.aggregation == LNE_AGG_BUCKET) LNE_TRY(bucket_counts(ws, g, sp, out, st));
+    else LNE_TRY(sort_counts(ws, g, sp, out, st));
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
     return 0;
 }
 
 int sparsifier_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out, cudaStream_t st) {
     if (use_table(g, sp)) return table_csr(ws, g, sp, out, st);
-    return bucket_csr(ws, g, sp, out, st);
+    if (sp.aggregation == LNE_AGG_BUCKET) return bucket_csr(ws, g, sp, out, st);
+    return sort_csr(ws, g, sp, out, st);
 }
 
 }  // namespace lne

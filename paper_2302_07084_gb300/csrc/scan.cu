@@ -10,10 +10,13 @@ namespace {
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 8;
 
+// One CTA per row: row b scans in[b * stride .. + n) into out[b * stride ..],
+// out[b * stride + n] = the row total (in and out may be the same array).
 template <typename In>
-__global__ void __launch_bounds__(kScanThreads) scan_exclusive_kernel(const In *__restrict__ in,
-                                                                      int64_t *__restrict__ out,
-                                                                      int64_t n) {
+__global__ void __launch_bounds__(kScanThreads) scan_exclusive_kernel(const In *in, int64_t *out,
+                                                                      int64_t n, int64_t stride = 0) {
+    in += (int64_t)blockIdx.x * stride;
+    out += (int64_t)blockIdx.x * stride;
     __shared__ int64_t warp_sums[kScanThreads / 32];
     __shared__ int64_t carry_s;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -72,6 +75,14 @@ int scan_exclusive_u32_to_i64(const uint32_t *in, int64_t *out, int64_t n, cudaS
         scan_exclusive_kernel<uint32_t><<<1, kScanThreads, 0, st>>>(in, out, n);
         LNE_LAUNCH_CHECK();
     }
+    return 0;
+}
+
+int scan_exclusive_rows_i64(int64_t *data, int64_t rows, int64_t n, cudaStream_t st) {
+    if (rows <= 0) return 0;
+    LNE_TRACE("scan_rows", st);
+    scan_exclusive_kernel<int64_t><<<(unsigned)rows, kScanThreads, 0, st>>>(data, data, n, n + 1);
+    LNE_LAUNCH_CHECK();
     return 0;
 }
 

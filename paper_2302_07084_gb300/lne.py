@@ -37,7 +37,7 @@ SURROGATE_PARAMS = 73_985
 OPT_AGGREGATION = 1
 OPT_SPMM_THREADS = 2
 OPT_TUNE_WORKERS = 3
-AGG_AUTO, AGG_TABLE, AGG_BUCKET = 0, 1, 2
+AGG_AUTO, AGG_TABLE, AGG_BUCKET, AGG_SORT = 0, 1, 2, 3
 
 
 class LneError(RuntimeError):

@@ -1,7 +1,8 @@
 """GPU sparsifier construction against the CPU oracle (bit-exact integer work).
 
 * raw PathSampling draws (lne_sample_pairs) equal the oracle's draws;
-* exact pair counts (lne_sparsifier_counts) equal the oracle's;
+* exact pair counts (lne_sparsifier_counts) equal the oracle's, with every
+  aggregation method (dense table, row buckets, 64-bit key sort);
 * the trunc_log CSR (lne_sparsifier_csr): structure and keep decisions exact,
   values within 1e-6 relative (FP32 log vs FP64 log rounded to FP32);
 * the bench workload (BlogCatalog-shaped graph, S = 200 T m) on sampled arc
@@ -21,13 +22,14 @@ VAL_RTOL = 1e-6
 VAL_ATOL = 1e-7
 
 
-@pytest.fixture(scope="module", params=["table", "bucket"])
+@pytest.fixture(scope="module", params=["table", "bucket", "sort"])
 def ctx(request):
-    """A context per aggregation method: both must give the oracle's counts."""
+    """A context per aggregation method: all must give the oracle's counts."""
     from paper_2302_07084_gb300 import build
     build.build()
     c = lne.Context(0)
-    c.set_option(lne.OPT_AGGREGATION, lne.AGG_TABLE if request.param == "table" else lne.AGG_BUCKET)
+    c.set_option(lne.OPT_AGGREGATION, {"table": lne.AGG_TABLE, "bucket": lne.AGG_BUCKET,
+                                       "sort": lne.AGG_SORT}[request.param])
     yield c
     c.close()
 
