@@ -367,10 +367,13 @@ bool merge_ok(const TX *X, int64_t ldx, int c, const float *Y, int64_t ldy, cons
            aligned(ep.Yb, 8) && aligned(ep.Gb, 8) && aligned(ep.b1_col, 16) && aligned(ep.gamma_col, 16);
 }
 
-// nonzeros per warp slice: ~8 waves of warps, 32..1024 nonzeros each
+// nonzeros per warp slice: ~8 waves of warps, at least 32 nonzeros each;
+// beyond 1024 per slice only for very large products (>6e7 nonzeros), which
+// keeps the carry buffers (two rows of c per warp) small
 int64_t merge_slice(int64_t nnz) {
     const int64_t W = nnz / (152 * 48 * 8);
-    return std::max<int64_t>(32, std::min<int64_t>(1024, (W + 31) / 32 * 32));
+    const int64_t cap = nnz > (int64_t)152 * 48 * 8 * 1024 ? 65536 : 1024;
+    return std::max<int64_t>(32, std::min<int64_t>(cap, (W + 31) / 32 * 32));
 }
 
 int merge_vectors(int c) {
