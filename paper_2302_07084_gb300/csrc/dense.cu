@@ -1,11 +1,13 @@
 // Dense stages of the randomized SVD (Algorithm 4) on the GPU:
 //
 //   sketch         Omega = randn(n, c) from Philox4x32-10 words (Box-Muller).
-//   gram           G = Y^T Y in FP64: per-CTA partial Grams over row blocks
-//                  (products of FP32 inputs are exact in FP64), summed in a
-//                  fixed order so the result is reproducible.
+//   gram           G = Y^T Y to FP64 accuracy: per-CTA partial Grams over row
+//                  blocks in error-free float-pair arithmetic, summed in FP64
+//                  in a fixed order so the result is reproducible.
 //   chol           G = R^T R (upper Cholesky) in FP64, one CTA.
-//   trsm_rows      Q = Y R^-1 by forward substitution per row (FP32).
+//   trsm_rows      Q = Y R^-1 by forward substitution per row (FP32): each
+//                  row's solve is backward stable, so Y = Q R holds to FP32
+//                  rounding whatever the conditioning of R.
 //   right_multiply out = Y W for a small FP64 W (rounded to FP32), FP32 FMA.
 //   cholqr2        Q = Y R1^-1, then again: the orthonormalisation used in
 //                  place of eigSVD inside the power iteration (same range).
@@ -58,60 +60,77 @@ __global__ void sketch_kernel(int64_t n, int c, uint32_t k0, uint32_t k1, float 
 }
 
 // ---------------------------------------------------------------------------
-// FP64 Gram: thread (ti, tj), ti <= tj, owns an 8x8 tile of the upper half.
+// Gram with FP64 accuracy from FP32 arithmetic: thread (ti, tj, half), ti <= tj,
+// owns 4 rows of an 8x8 tile of the upper half. Every product a*b is split exactly into
+// p + e (p = fl(a b), e = fma(a, b, -p)); p enters a float pair (hi, lo) by
+// an error-free two-sum, e and the two-sum's error go to lo. The pair carries
+// ~46 significant bits over a CTA's rows; CTAs are summed in FP64. FP64
+// arithmetic runs at a small fraction of the FP32 rate on this GPU, so this
+// is several times faster than FP64 FMAs. The _rn intrinsics keep the
+// compiler from contracting the error-free transformations.
 // ---------------------------------------------------------------------------
 constexpr int kGramRows = 32;   // rows staged per step
 
-constexpr int kGramThreads = 256;
+constexpr int kGramThreads = 384;
 
 __global__ void __launch_bounds__(kGramThreads) gram_partial_kernel(const float *__restrict__ Y, int64_t n, int c,
                                                                     int64_t ld, int64_t rows_per_cta,
                                                                     double *__restrict__ partial) {
-    extern __shared__ double ys[];   // kGramRows x cp, rows converted to FP64 once
+    extern __shared__ float ys[];   // kGramRows x cp
     const int cp = (c + 7) & ~7;
     const int nt = cp / 8;
-    const int ntiles = nt * (nt + 1) / 2;
+    const int nitems = nt * (nt + 1);   // (tile, half): rows 0-3 or 4-7 of an 8x8 tile
     const int tid = threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
     const int64_t r1 = imin64(n, r0 + rows_per_cta);
-    // tiles are processed in groups of kGramThreads (uniform trip count for the barriers)
-    for (int g0 = 0; g0 < ntiles; g0 += kGramThreads) {
-        const int tile = g0 + tid;
-        const bool active = tile < ntiles;
+    // items are processed in groups of kGramThreads (uniform trip count for the barriers)
+    for (int g0 = 0; g0 < nitems; g0 += kGramThreads) {
+        const int item = g0 + tid;
+        const bool active = item < nitems;
         int ti = 0, tj = 0;
+        const int half = item & 1;
         if (active) {
-            int rem = tile;
+            int rem = item >> 1;
             while (rem >= nt - ti) {
                 rem -= nt - ti;
                 ++ti;
             }
             tj = ti + rem;
         }
-        double acc[8][8];
+        const int xa = ti * 8 + half * 4;
+        float hi[4][8], lo[4][8];
 #pragma unroll
-        for (int a = 0; a < 8; ++a)
+        for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 8; ++b) acc[a][b] = 0.0;
+            for (int b = 0; b < 8; ++b) hi[a][b] = lo[a][b] = 0.f;
         for (int64_t base = r0; base < r1; base += kGramRows) {
             const int rows = (int)imin64(kGramRows, r1 - base);
             for (int e = tid; e < kGramRows * cp; e += kGramThreads) {
                 int rr = e / cp, cc = e - rr * cp;
-                ys[e] = (rr < rows && cc < c) ? (double)Y[(base + rr) * ld + cc] : 0.0;
+                ys[e] = (rr < rows && cc < c) ? Y[(base + rr) * ld + cc] : 0.f;
             }
             __syncthreads();
             if (active) {
                 for (int rr = 0; rr < rows; ++rr) {
-                    const double *yr = ys + rr * cp;
-                    double av[8], bv[8];
+                    const float *yr = ys + rr * cp;
+                    float av[4], bv[8];
 #pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        av[t] = yr[ti * 8 + t];
-                        bv[t] = yr[tj * 8 + t];
-                    }
+                    for (int t = 0; t < 4; ++t) av[t] = yr[xa + t];
 #pragma unroll
-                    for (int x = 0; x < 8; ++x)
+                    for (int t = 0; t < 8; ++t) bv[t] = yr[tj * 8 + t];
 #pragma unroll
-                        for (int y = 0; y < 8; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
+                    for (int x = 0; x < 4; ++x)
+#pragma unroll
+                        for (int y = 0; y < 8; ++y) {
+                            const float p = __fmul_rn(av[x], bv[y]);
+                            const float e = fmaf(av[x], bv[y], -p);
+                            const float h = hi[x][y];
+                            const float s = __fadd_rn(h, p);
+                            const float bb = __fsub_rn(s, h);
+                            const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+                            hi[x][y] = s;
+                            lo[x][y] = __fadd_rn(lo[x][y], __fadd_rn(err, e));
+                        }
                 }
             }
             __syncthreads();
@@ -119,9 +138,10 @@ __global__ void __launch_bounds__(kGramThreads) gram_partial_kernel(const float 
         if (active) {
             double *P = partial + (int64_t)blockIdx.x * cp * cp;
 #pragma unroll
-            for (int x = 0; x < 8; ++x)
+            for (int x = 0; x < 4; ++x)
 #pragma unroll
-                for (int y = 0; y < 8; ++y) P[(ti * 8 + x) * cp + tj * 8 + y] = acc[x][y];
+                for (int y = 0; y < 8; ++y)
+                    P[(xa + x) * cp + tj * 8 + y] = (double)hi[x][y] + (double)lo[x][y];
         }
     }
 }
@@ -577,47 +597,48 @@ __global__ void svd_finish_kernel(const double *__restrict__ U, const double *__
 // ---------------------------------------------------------------------------
 // sign convention and X = U Sigma^{1/2}
 // ---------------------------------------------------------------------------
-__global__ void col_absmax_kernel(const float *__restrict__ U, int64_t n, int d, int64_t ld,
-                                  unsigned long long *__restrict__ best) {
-    // thread handles one column for a strided set of rows; packs (|u| bits, ~row)
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * d;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = e / d;
-        int j = (int)(e - i * d);
-        float a = fabsf(U[i * ld + j]);
-        unsigned long long key = ((unsigned long long)__float_as_uint(a) << 32) |
-                                 (unsigned long long)(0xFFFFFFFFu - (uint32_t)i);
-        atomicMax(&best[j], key);
-    }
-}
-
-__global__ void apply_sign_kernel(float *__restrict__ U, int64_t n, int d, int64_t ld,
-                                  const float *__restrict__ sgn) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * d;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = e / d;
-        int j = (int)(e - i * d);
-        U[i * ld + j] *= sgn[j];
+// Per column: the largest |u| and, among equal magnitudes, the smallest row,
+// packed as (|u| bits << 32) | ~row so that one max orders both. Each thread
+// keeps a running maximum over a strided set of rows of one column; one
+// atomic per CTA and column.
+__global__ void __launch_bounds__(256) col_absmax_kernel(const float *__restrict__ U, int64_t n, int d, int64_t ld,
+                                                         unsigned long long *__restrict__ best) {
+    const int sub = blockDim.x / d;               // row subsets per CTA (d <= 256)
+    const int j = threadIdx.x % d, r0 = threadIdx.x / d;
+    unsigned long long m = 0;
+    if (r0 < sub) {
+        for (int64_t i = (int64_t)blockIdx.x * sub + r0; i < n; i += (int64_t)gridDim.x * sub) {
+            const float a = fabsf(U[i * ld + j]);
+            const unsigned long long key = ((unsigned long long)__float_as_uint(a) << 32) |
+                                           (unsigned long long)(0xFFFFFFFFu - (uint32_t)i);
+            m = key > m ? key : m;
+        }
+        atomicMax(&best[j], m);
     }
 }
 
 __global__ void column_signs_kernel(const float *__restrict__ U, int d, int64_t ld,
-                                    const unsigned long long *__restrict__ best,
-                                    float *__restrict__ sgn) {
+                                    const unsigned long long *__restrict__ best, const double *__restrict__ sigma,
+                                    float *__restrict__ sgn, float *__restrict__ scale) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= d) return;
-    int64_t arg = (int64_t)(0xFFFFFFFFu - (uint32_t)(best[j] & 0xFFFFFFFFull));
-    sgn[j] = U[arg * ld + j] < 0.f ? -1.f : 1.f;
+    const int64_t i = (int64_t)(0xFFFFFFFFu - (uint32_t)(best[j] & 0xFFFFFFFFull));
+    sgn[j] = U[i * ld + j] < 0.f ? -1.f : 1.f;
+    if (sigma) scale[j] = (float)sqrt(fmax(sigma[j], 0.0));
 }
 
-__global__ void embed_scale_kernel(const float *__restrict__ U, int64_t n, int d, int64_t ld,
-                                   const double *__restrict__ sigma, float *__restrict__ X,
-                                   int64_t ldx) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * d;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = e / d;
-        int j = (int)(e - i * d);
-        X[i * ldx + j] = (float)((double)U[i * ld + j] * sqrt(fmax(sigma[j], 0.0)));
+// U <- U diag(sgn); X = U diag(scale) when X is given.
+__global__ void sign_scale_kernel(float *__restrict__ U, int64_t n, int d, int64_t ld,
+                                  const float *__restrict__ sgn, const float *__restrict__ scale,
+                                  float *__restrict__ X, int64_t ldx) {
+    const int sub = blockDim.x / d;
+    const int j = threadIdx.x % d, r0 = threadIdx.x / d;
+    if (r0 >= sub) return;
+    const float sg = sgn[j], sc = X ? scale[j] : 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * sub + r0; i < n; i += (int64_t)gridDim.x * sub) {
+        const float u = U[i * ld + j] * sg;
+        U[i * ld + j] = u;
+        if (X) X[i * ldx + j] = u * sc;
     }
 }
 
@@ -664,7 +685,7 @@ static int gram(Workspace &ws, const float *Y, int64_t n, int c, int64_t ld, dou
     nblk = ceil_div(std::max<int64_t>(n, 1), rows_per);
     double *partial = nullptr;
     LNE_TRY(ws.get("gram.partial", (size_t)nblk * cp * cp, &partial));
-    const int smem = kGramRows * cp * 8;
+    const int smem = kGramRows * cp * 4;
     if (smem > 48 * 1024)
         LNE_TRY(allow_dynamic_smem(gram_partial_kernel));
     {
@@ -823,32 +844,29 @@ int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma,
 
 int sign_fix_embed(Workspace &ws, float *U, int64_t n, int d, int64_t ld, const double *sigma, float *X,
                    int64_t ldx, cudaStream_t st) {
+    if (d < 1 || d > 256) return fail(LNE_ERR_UNSUPPORTED, "sign fix supports 1..256 columns");
     unsigned long long *best = nullptr;
-    float *sgn = nullptr;
+    float *sgn = nullptr, *scale = nullptr;
     LNE_TRY(ws.get("sign.best", (size_t)d, &best));
     LNE_TRY(ws.get("sign.sgn", (size_t)d, &sgn));
+    LNE_TRY(ws.get("sign.scale", (size_t)d, &scale));
     LNE_CUDA_TRY(cudaMemsetAsync(best, 0, sizeof(unsigned long long) * d, st));
+    const int sub = 256 / d;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, sub), 152 * 8));
     {
         LNE_TRACE("col_absmax", st);
-        col_absmax_kernel<<<grid_for(n * d, 256), 256, 0, st>>>(U, n, d, ld, best);
+        col_absmax_kernel<<<blocks, 256, 0, st>>>(U, n, d, ld, best);
         LNE_LAUNCH_CHECK();
     }
     {
         LNE_TRACE("column_signs", st);
-        column_signs_kernel<<<(d + 127) / 128, 128, 0, st>>>(U, d, ld, best, sgn);
+        column_signs_kernel<<<(d + 127) / 128, 128, 0, st>>>(U, d, ld, best, X ? sigma : nullptr, sgn, scale);
         LNE_LAUNCH_CHECK();
     }
     {
-        LNE_TRACE("apply_sign", st);
-        apply_sign_kernel<<<grid_for(n * d, 256), 256, 0, st>>>(U, n, d, ld, sgn);
+        LNE_TRACE("sign_scale", st);
+        sign_scale_kernel<<<blocks, 256, 0, st>>>(U, n, d, ld, sgn, scale, X, ldx);
         LNE_LAUNCH_CHECK();
-    }
-    if (X) {
-        {
-            LNE_TRACE("embed_scale", st);
-            embed_scale_kernel<<<grid_for(n * d, 256), 256, 0, st>>>(U, n, d, ld, sigma, X, ldx);
-            LNE_LAUNCH_CHECK();
-        }
     }
     return 0;
 }
