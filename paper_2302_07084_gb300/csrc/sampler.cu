@@ -939,24 +939,6 @@ constexpr int kPathThreads = 256;
 constexpr int kPathRun = 32;
 constexpr int kPathTile = kPathThreads * kPathRun;
 
-struct PathEntry {
-    int32_t x, y;
-    float v;
-};
-
-__device__ __forceinline__ PathEntry path_entry(const uint64_t *__restrict__ uk, const uint32_t *__restrict__ cnt,
-                                                int64_t u, int B, const int64_t *__restrict__ indptr,
-                                                const NetmfConst &kc) {
-    PathEntry e;
-    const uint64_t k = uk[u];
-    e.x = (int32_t)(k >> B);
-    e.y = (int32_t)(k & ((1ull << B) - 1ull));
-    const int64_t dx = __ldg(indptr + e.x + 1) - __ldg(indptr + e.x);
-    const int64_t dy = __ldg(indptr + e.y + 1) - __ldg(indptr + e.y);
-    e.v = netmf_value(cnt[u], dx, dy, e.x == e.y, kc);
-    return e;
-}
-
 __device__ __forceinline__ int64_t path_block_scan(int64_t v, int64_t *s_warp) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     int64_t x = v;
@@ -982,24 +964,33 @@ __global__ void decode_keys_kernel(const uint64_t *__restrict__ uk, int64_t u, i
     }
 }
 
-// Per tile: entries kept (v > 1, i.e. log v > 0) and kept off-diagonal ones.
-__global__ void __launch_bounds__(kPathThreads) path_count_kernel(const uint64_t *__restrict__ uk,
-                                                                  const uint32_t *__restrict__ cnt, int64_t U, int B,
-                                                                  const int64_t *__restrict__ indptr, NetmfConst kc,
+__global__ void degree_kernel(const int64_t *__restrict__ indptr, int64_t n, uint32_t *__restrict__ deg) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        deg[i] = (uint32_t)(indptr[i + 1] - indptr[i]);
+}
+
+// Eq. 1 value of every unique pair, written over its count (float bits; 0 =
+// dropped), and per tile the number of kept and of kept off-diagonal pairs.
+__global__ void __launch_bounds__(kPathThreads) path_value_kernel(const uint64_t *__restrict__ uk,
+                                                                  uint32_t *__restrict__ cnt_val, int64_t U, int B,
+                                                                  const uint32_t *__restrict__ deg, NetmfConst kc,
                                                                   uint32_t *__restrict__ tile_kept,
                                                                   uint32_t *__restrict__ tile_mir) {
     __shared__ uint32_t s_k, s_m;
     if (threadIdx.x == 0) s_k = s_m = 0;
     __syncthreads();
-    const int64_t i0 = (int64_t)blockIdx.x * kPathTile + (int64_t)threadIdx.x * kPathRun;
     uint32_t ck = 0, cm = 0;
-    for (int j = 0; j < kPathRun; ++j) {
-        const int64_t u = i0 + j;
+    const int64_t t0 = (int64_t)blockIdx.x * kPathTile;
+    for (int j = threadIdx.x; j < kPathTile; j += kPathThreads) {   // coalesced here: counts only
+        const int64_t u = t0 + j;
         if (u >= U) break;
-        const PathEntry e = path_entry(uk, cnt, u, B, indptr, kc);
-        if (e.v > 0.f) {
+        const uint64_t k = uk[u];
+        const uint32_t x = (uint32_t)(k >> B), y = (uint32_t)(k & ((1ull << B) - 1ull));
+        const float v = netmf_value(cnt_val[u], __ldg(deg + x), __ldg(deg + y), x == y, kc);
+        cnt_val[u] = __float_as_uint(v);
+        if (v > 0.f) {
             ++ck;
-            cm += e.x != e.y;
+            cm += x != y;
         }
     }
 #pragma unroll
@@ -1018,78 +1009,97 @@ __global__ void __launch_bounds__(kPathThreads) path_count_kernel(const uint64_t
     }
 }
 
-// Row lengths, the first kept index of every row, and the mirrored entries
-// (key (y << B) | x, value bits) in unique-list order.
+// Kept entries compacted in unique-list order (= grouped by row, columns
+// ascending): their columns and values, and per row how many and where they
+// start (runs of equal rows within a thread's entries share one atomic); the
+// mirrored entries (key (y << B) | x, value bits) in the same order.
 __global__ void __launch_bounds__(kPathThreads) path_rows_kernel(
-    const uint64_t *__restrict__ uk, const uint32_t *__restrict__ cnt, int64_t U, int B,
-    const int64_t *__restrict__ indptr, NetmfConst kc, const int64_t *__restrict__ kept_off,
-    const int64_t *__restrict__ mir_off, uint32_t *__restrict__ rowlen, uint32_t *__restrict__ mirlen,
-    unsigned long long *__restrict__ dstart, uint64_t *__restrict__ mkey, uint32_t *__restrict__ mval) {
+    const uint64_t *__restrict__ uk, const uint32_t *__restrict__ val, int64_t U, int B,
+    const int64_t *__restrict__ kept_off, const int64_t *__restrict__ mir_off, uint32_t *__restrict__ dlen,
+    unsigned long long *__restrict__ dstart, int32_t *__restrict__ dcol, uint32_t *__restrict__ dval,
+    uint64_t *__restrict__ mkey, uint32_t *__restrict__ mval) {
     __shared__ int64_t s_warp[kPathThreads / 32];
     const int64_t i0 = (int64_t)blockIdx.x * kPathTile + (int64_t)threadIdx.x * kPathRun;
     uint32_t ck = 0, cm = 0;
     for (int j = 0; j < kPathRun; ++j) {
         const int64_t u = i0 + j;
         if (u >= U) break;
-        const PathEntry e = path_entry(uk, cnt, u, B, indptr, kc);
-        if (e.v > 0.f) {
+        if (__uint_as_float(val[u]) > 0.f) {
             ++ck;
-            cm += e.x != e.y;
+            const uint64_t k = uk[u];
+            cm += (k >> B) != (k & ((1ull << B) - 1ull));
         }
     }
     int64_t k = kept_off[blockIdx.x] + path_block_scan(ck, s_warp);
     int64_t m = mir_off[blockIdx.x] + path_block_scan(cm, s_warp);
+    int64_t run_x = -1, run_k = 0;
+    uint32_t run_n = 0;
     for (int j = 0; j < kPathRun; ++j) {
         const int64_t u = i0 + j;
         if (u >= U) break;
-        const PathEntry e = path_entry(uk, cnt, u, B, indptr, kc);
-        if (!(e.v > 0.f)) continue;
-        atomicAdd(&rowlen[e.x], 1u);
-        atomicMin(&dstart[e.x], (unsigned long long)k);
-        if (e.x != e.y) {
-            atomicAdd(&rowlen[e.y], 1u);
-            atomicAdd(&mirlen[e.y], 1u);
-            mkey[m] = ((uint64_t)(uint32_t)e.y << B) | (uint64_t)(uint32_t)e.x;
-            mval[m] = __float_as_uint(e.v);
+        const uint32_t vb = val[u];
+        if (!(__uint_as_float(vb) > 0.f)) continue;
+        const uint64_t key = uk[u];
+        const int64_t x = (int64_t)(key >> B), y = (int64_t)(key & ((1ull << B) - 1ull));
+        if (x != run_x) {
+            if (run_n) {
+                atomicAdd(&dlen[run_x], run_n);
+                atomicMin(&dstart[run_x], (unsigned long long)run_k);
+            }
+            run_x = x;
+            run_k = k;
+            run_n = 0;
+        }
+        ++run_n;
+        dcol[k] = (int32_t)y;
+        dval[k] = vb;
+        if (x != y) {
+            mkey[m] = ((uint64_t)y << B) | (uint64_t)x;
+            mval[m] = vb;
             ++m;
         }
         ++k;
     }
-}
-
-// Row x of the CSR: its mirrored entries (columns < x) first, then the direct
-// ones (columns >= x) in unique-list order.
-__global__ void __launch_bounds__(kPathThreads) path_direct_fill_kernel(
-    const uint64_t *__restrict__ uk, const uint32_t *__restrict__ cnt, int64_t U, int B,
-    const int64_t *__restrict__ indptr, NetmfConst kc, const int64_t *__restrict__ kept_off,
-    const int64_t *__restrict__ rowptr, const uint32_t *__restrict__ mirlen,
-    const unsigned long long *__restrict__ dstart, int32_t *__restrict__ col, float *__restrict__ data) {
-    __shared__ int64_t s_warp[kPathThreads / 32];
-    const int64_t i0 = (int64_t)blockIdx.x * kPathTile + (int64_t)threadIdx.x * kPathRun;
-    uint32_t ck = 0;
-    for (int j = 0; j < kPathRun; ++j) {
-        const int64_t u = i0 + j;
-        if (u >= U) break;
-        ck += path_entry(uk, cnt, u, B, indptr, kc).v > 0.f;
-    }
-    int64_t k = kept_off[blockIdx.x] + path_block_scan(ck, s_warp);
-    for (int j = 0; j < kPathRun; ++j) {
-        const int64_t u = i0 + j;
-        if (u >= U) break;
-        const PathEntry e = path_entry(uk, cnt, u, B, indptr, kc);
-        if (!(e.v > 0.f)) continue;
-        const int64_t pos = rowptr[e.x] + mirlen[e.x] + (k - (int64_t)dstart[e.x]);
-        col[pos] = e.y;
-        data[pos] = e.v;
-        ++k;
+    if (run_n) {
+        atomicAdd(&dlen[run_x], run_n);
+        atomicMin(&dstart[run_x], (unsigned long long)run_k);
     }
 }
 
-__global__ void path_mirror_first_kernel(const uint64_t *__restrict__ mk, int64_t M, int B,
-                                         int64_t *__restrict__ first) {
+// Over the mirrored entries sorted by (row, column): where each row's run
+// starts (first) and ends (end, exclusive; 0 = no mirrored entries).
+__global__ void path_mirror_rows_kernel(const uint64_t *__restrict__ mk, int64_t M, int B,
+                                        int64_t *__restrict__ first, int64_t *__restrict__ end) {
     for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < M; f += (int64_t)gridDim.x * blockDim.x) {
         const uint64_t r = mk[f] >> B;
         if (f == 0 || (mk[f - 1] >> B) != r) first[r] = f;
+        if (f + 1 == M || (mk[f + 1] >> B) != r) end[r] = f + 1;
+    }
+}
+
+__global__ void path_row_total_kernel(const uint32_t *__restrict__ dlen, const int64_t *__restrict__ end,
+                                      const int64_t *__restrict__ first, int64_t n, uint32_t *__restrict__ total) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        total[r] = dlen[r] + (end[r] ? (uint32_t)(end[r] - first[r]) : 0u);
+}
+
+// Row x of the CSR: its mirrored entries (columns < x) first, then its direct
+// ones (columns >= x), copied from the compacted kept list (a warp per row).
+__global__ void path_direct_fill_kernel(const int32_t *__restrict__ dcol, const uint32_t *__restrict__ dval,
+                                        const uint32_t *__restrict__ dlen,
+                                        const unsigned long long *__restrict__ dstart,
+                                        const int64_t *__restrict__ rowptr, int64_t n, int32_t *__restrict__ col,
+                                        float *__restrict__ data) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t x = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < n; x += warps) {
+        const uint32_t len = dlen[x];
+        if (len == 0) continue;
+        const int64_t src = (int64_t)dstart[x], dst = rowptr[x + 1] - len;
+        for (uint32_t i = lane; i < len; i += 32) {
+            col[dst + i] = dcol[src + i];
+            data[dst + i] = __uint_as_float(dval[src + i]);
+        }
     }
 }
 
@@ -1508,8 +1518,8 @@ int sort_raw(Workspace &ws, const GraphView &g, const SamplerSpec &sp, SortRaw *
 
 void sort_release(Workspace &ws) {
     for (const char *n : {"sort.k0", "sort.k1", "sort.cnt", "sort.start", "sort.offs", "sort.mk", "sort.mv",
-                          "path.tk", "path.tm", "path.ko", "path.mo", "path.rowlen", "path.mirlen", "path.dstart",
-                          "path.first"})
+                          "path.dcol", "path.dval", "path.tk", "path.tm", "path.ko", "path.mo", "path.deg",
+                          "path.dlen", "path.rowlen", "path.dstart", "path.first", "path.end"})
         ws.release(n);
 }
 
@@ -1539,70 +1549,92 @@ int sort_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult
     LNE_TRY(sort_raw(ws, g, sp, &R, st));
     const int64_t U = R.U, n = g.n;
     const int64_t ntiles = std::max<int64_t>(1, ceil_div(U, (int64_t)kPathTile));
-    const NetmfConst kc = netmf_const(sp);
-    uint32_t *tk = nullptr, *tm = nullptr, *rowlen = nullptr, *mirlen = nullptr;
-    int64_t *ko = nullptr, *mo = nullptr;
+    const unsigned egrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 152 * 16));
+    uint32_t *tk = nullptr, *tm = nullptr, *deg = nullptr, *dlen = nullptr, *rowlen = nullptr;
+    int64_t *ko = nullptr, *mo = nullptr, *first = nullptr, *end = nullptr;
     unsigned long long *dstart = nullptr;
     LNE_TRY(ws.get("path.tk", (size_t)ntiles, &tk));
     LNE_TRY(ws.get("path.tm", (size_t)ntiles, &tm));
     LNE_TRY(ws.get("path.ko", (size_t)ntiles + 1, &ko));
     LNE_TRY(ws.get("path.mo", (size_t)ntiles + 1, &mo));
+    LNE_TRY(ws.get("path.deg", (size_t)n, &deg));
+    LNE_TRY(ws.get("path.dlen", (size_t)n, &dlen));
     LNE_TRY(ws.get("path.rowlen", (size_t)n, &rowlen));
-    LNE_TRY(ws.get("path.mirlen", (size_t)n, &mirlen));
     LNE_TRY(ws.get("path.dstart", (size_t)n, &dstart));
+    LNE_TRY(ws.get("path.first", (size_t)n, &first));
+    LNE_TRY(ws.get("path.end", (size_t)n, &end));
     LNE_TRY(ws.get("csr.indptr", (size_t)n + 1, &out->indptr));
-    LNE_CUDA_TRY(cudaMemsetAsync(rowlen, 0, sizeof(uint32_t) * n, st));
-    LNE_CUDA_TRY(cudaMemsetAsync(mirlen, 0, sizeof(uint32_t) * n, st));
+    LNE_CUDA_TRY(cudaMemsetAsync(dlen, 0, sizeof(uint32_t) * n, st));
+    LNE_CUDA_TRY(cudaMemsetAsync(end, 0, sizeof(int64_t) * n, st));
     LNE_CUDA_TRY(cudaMemsetAsync(dstart, 0xFF, sizeof(unsigned long long) * n, st));
     {
-        LNE_TRACE("path_count", st);
-        path_count_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, U, sp.B, g.indptr, kc, tk, tm);
+        LNE_TRACE("path_value", st);
+        degree_kernel<<<egrid, 256, 0, st>>>(g.indptr, n, deg);
+        LNE_LAUNCH_CHECK();
+        // values overwrite the counts (the counts are not needed afterwards)
+        path_value_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, U, sp.B, deg, netmf_const(sp),
+                                                                    tk, tm);
         LNE_LAUNCH_CHECK();
     }
     LNE_TRY(scan_exclusive_u32_to_i64(tk, ko, ntiles, st));
     LNE_TRY(scan_exclusive_u32_to_i64(tm, mo, ntiles, st));
-    int64_t nm = 0;
+    int64_t nk = 0, nm = 0;
+    LNE_CUDA_TRY(cudaMemcpyAsync(&nk, ko + ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     LNE_CUDA_TRY(cudaMemcpyAsync(&nm, mo + ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    int32_t *dcol = nullptr;
+    uint32_t *dval = nullptr, *mv = nullptr;
     uint64_t *mk = nullptr;
-    uint32_t *mv = nullptr;
+    LNE_TRY(ws.get("path.dcol", (size_t)std::max<int64_t>(nk, 1), &dcol));
+    LNE_TRY(ws.get("path.dval", (size_t)std::max<int64_t>(nk, 1), &dval));
     LNE_TRY(ws.get("sort.mk", (size_t)std::max<int64_t>(nm, 1), &mk));
     LNE_TRY(ws.get("sort.mv", (size_t)std::max<int64_t>(nm, 1), &mv));
     {
         LNE_TRACE("path_rows", st);
-        path_rows_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, U, sp.B, g.indptr, kc, ko, mo,
-                                                                   rowlen, mirlen, dstart, mk, mv);
+        path_rows_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, U, sp.B, ko, mo, dlen, dstart,
+                                                                   dcol, dval, mk, mv);
+        LNE_LAUNCH_CHECK();
+    }
+    // mirrored entries sorted by (row y, column x); the unique keys and the
+    // values are no longer needed and serve as the sort's spare buffers
+    bool in_alt = false;
+    LNE_TRY(radix_sort_u64(ws, mk, R.uk, mv, R.cnt, nm, 2 * sp.B, &in_alt, st));
+    const uint64_t *smk = in_alt ? R.uk : mk;
+    const uint32_t *smv = in_alt ? R.cnt : mv;
+    const unsigned mgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nm, 256), 152 * 16));
+    {
+        LNE_TRACE("path_rows", st);
+        if (nm > 0) {
+            path_mirror_rows_kernel<<<mgrid, 256, 0, st>>>(smk, nm, sp.B, first, end);
+            LNE_LAUNCH_CHECK();
+        }
+        path_row_total_kernel<<<egrid, 256, 0, st>>>(dlen, end, first, n, rowlen);
         LNE_LAUNCH_CHECK();
     }
     LNE_TRY(scan_exclusive_u32_to_i64(rowlen, out->indptr, n, st));
     int64_t nnz = 0;
     LNE_CUDA_TRY(cudaMemcpyAsync(&nnz, out->indptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    // the buffers not holding the sorted mirrored entries are free now
+    if (in_alt) {
+        ws.release("sort.mk");
+        ws.release("sort.mv");
+    } else {
+        ws.release(R.uk_name);
+        ws.release("sort.cnt");
+    }
     LNE_TRY(ws.get("csr.indices", (size_t)std::max<int64_t>(nnz, 1), &out->indices));
     LNE_TRY(ws.get("csr.data", (size_t)std::max<int64_t>(nnz, 1), &out->data));
     {
-        LNE_TRACE("path_direct_fill", st);
-        path_direct_fill_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, U, sp.B, g.indptr, kc, ko,
-                                                                          out->indptr, mirlen, dstart, out->indices,
-                                                                          out->data);
+        LNE_TRACE("path_fill", st);
+        path_direct_fill_kernel<<<egrid, 256, 0, st>>>(dcol, dval, dlen, dstart, out->indptr, n, out->indices,
+                                                       out->data);
         LNE_LAUNCH_CHECK();
-    }
-    // mirrored entries sorted by (row y, column x); the unique keys and the
-    // counts are no longer needed and serve as the sort's spare buffers
-    bool in_alt = false;
-    LNE_TRY(radix_sort_u64(ws, mk, R.uk, mv, R.cnt, nm, 2 * sp.B, &in_alt, st));
-    const uint64_t *smk = in_alt ? R.uk : mk;
-    const uint32_t *smv = in_alt ? R.cnt : mv;
-    int64_t *first = nullptr;
-    LNE_TRY(ws.get("path.first", (size_t)n, &first));
-    if (nm > 0) {
-        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(nm, 256), 152 * 16);
-        LNE_TRACE("path_mirror_fill", st);
-        path_mirror_first_kernel<<<grid, 256, 0, st>>>(smk, nm, sp.B, first);
-        LNE_LAUNCH_CHECK();
-        path_mirror_fill_kernel<<<grid, 256, 0, st>>>(smk, smv, nm, sp.B, out->indptr, first, out->indices,
-                                                      out->data);
-        LNE_LAUNCH_CHECK();
+        if (nm > 0) {
+            path_mirror_fill_kernel<<<mgrid, 256, 0, st>>>(smk, smv, nm, sp.B, out->indptr, first, out->indices,
+                                                          out->data);
+            LNE_LAUNCH_CHECK();
+        }
     }
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
     sort_release(ws);
