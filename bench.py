@@ -501,6 +501,89 @@ def run_surrogate(args):
     print(json.dumps(out))
 
 
+def _sin_angle(torch, U1, U2, lead=None):
+    """sin of the largest principal angle between span(U1) and span(U2) (GPU, FP64)."""
+    if lead:
+        U1, U2 = U1[:, :lead], U2[:, :lead]
+    Q1 = torch.linalg.qr(U1.double()).Q
+    Q2 = torch.linalg.qr(U2.double()).Q
+    R = Q2 - Q1 @ (Q1.T @ Q2)
+    lam = torch.linalg.eigvalsh(R.T @ R)
+    return float(torch.sqrt(torch.clamp(lam[-1], min=0.0)).item())
+
+
+def run_large(args):
+    """Large-graph precision run: Chung-Lu with 10M vertices and 200M edges
+    (exponent 2.2, generated on the GPU), T = 5, s_r = 0.2, S = 5 T m = 5e9,
+    d = 128, q = 2, k = 10, BF16 dense operand (FP32 accumulation, FP64-accurate
+    Gram / Cholesky / small SVD). Times whole embeddings, checks sampled draws
+    bit for bit against the oracle, and reports per stage how far the BF16
+    operand path lands from the FP32 path at full size (the FP32 path's own
+    distance to the FP64 oracle is pinned on the 10k-vertex SBM by the tests).
+    `--scale` divides n and m."""
+    import torch
+    import oracle
+    from paper_2302_07084_gb300 import lne, synth
+    n, m = int(10_000_000 / args.scale), int(200_000_000 / args.scale)
+    indptr, indices = synth.chung_lu_device(n, m, 2.2, seed=4)
+    torch.cuda.empty_cache()      # the generator's temporaries go back to the device
+    g = lne.DeviceGraph.from_tensors(indptr, indices)
+    base = dict(T=5, s=[0.2] * 5, samples=5.0 * 5 * m, b=1.0, d=128, oversample=16, q=2, k=10, theta=0.5, mu=0.2,
+                seed=4)
+    p16 = lne.Params(**base, precision=lne.PREC_BF16_MIXED)
+    p32 = lne.Params(**base, precision=lne.PREC_FP32)
+    ctx = lne.Context(0)
+    out = {"metric": "samples/s (large-graph embed, BF16 operand)", "unit": "samples/s",
+           "config": {"workload": f"chunglu_n{n}_m{m}_gamma2.2_T5_S5Tm_d128_q2_k10_bf16", "n": n, "m": m,
+                      "samples": base["samples"]}}
+    for _ in range(max(1, args.warmup)):
+        X = ctx.embed(g, p16)
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(args.steps):
+        X = ctx.embed(g, p16)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    out.update(value=base["samples"] / (ms / 1e3), ms_per_step=ms, steps=args.steps,
+               workspace_gb=ctx.workspace_bytes() / 1e9)
+    ctx.trace(True)
+    ctx.embed(g, p16)
+    out["stage_ms"] = {r["name"]: round(r["ms"], 2) for r in ctx.trace_read()}
+    ctx.trace(False)
+    # sampled draws against the oracle
+    hp, hi = indptr.cpu().numpy(), indices.cpu().numpy().astype(np.int32)
+    exact, drawn = True, 0
+    for a0 in (0, g.nnz // 2, g.nnz - 2000):
+        u1, v1 = ctx.sample_pairs(g, p16, a0, a0 + 2000)
+        tr = oracle.sample_trace(hp, hi, 5, base["s"], base["samples"], base["seed"], a0, a0 + 2000,
+                                 fields=("u1", "v1"))
+        exact &= np.array_equal(u1.cpu().numpy().astype(np.int64), tr["u1"])
+        exact &= np.array_equal(v1.cpu().numpy().astype(np.int64), tr["v1"])
+        drawn += int(u1.numel())
+    out["draws_bit_exact"] = {"ok": bool(exact), "draws": drawn, "arc_ranges": 3}
+    # per-stage distance of the BF16 path from the FP32 path
+    csr = ctx.sparsifier_csr(g, p32, copy=False)
+    out["config"]["nnz_M"] = csr["nnz"]
+    r32 = ctx.rsvd(csr, p32)
+    r16 = ctx.rsvd(csr, p16)
+    dev = {"sigma_max_rel": float(((r16["sigma"] - r32["sigma"]).abs() / r32["sigma"]).max()),
+           "U_lead16_sin": _sin_angle(torch, r16["U"], r32["U"], 16),
+           "U_all_sin": _sin_angle(torch, r16["U"], r32["U"])}
+    X0 = r32["X0"]
+    del r16, csr
+    a = ctx.propagate(g, p32, X0, want_intermediates=True)
+    b = ctx.propagate(g, p16, X0, want_intermediates=True)
+    for k in ("F", "P"):
+        dev[k + "_rel_fro"] = float(torch.linalg.norm(b[k] - a[k]) / torch.linalg.norm(a[k]))
+    dev["X_lead16_sin"] = _sin_angle(torch, b["X"], a["X"], 16)
+    out["bf16_vs_fp32"] = dev
+    ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -515,8 +598,14 @@ def main():
                     help="measure tuning throughput on G graphs of the SBM suite instead of the benchmark")
     ap.add_argument("--surrogate", type=int, default=0, metavar="G",
                     help="measure surrogate-guided search after training on G graphs of the SBM suite")
+    ap.add_argument("--large", action="store_true",
+                    help="the 10M-vertex BF16 precision run instead of the benchmark (--scale divides its size)")
     args = ap.parse_args()
-    if args.surrogate:
+    if args.large:
+        if args.scale == 10.0 and "--scale" not in sys.argv:
+            args.scale = 1.0
+        run_large(args)
+    elif args.surrogate:
         run_surrogate(args)
     elif args.tune:
         run_tune(args)

@@ -239,9 +239,8 @@ int scan_exclusive_rows_i64(int64_t *data, int64_t rows, int64_t n, cudaStream_t
 // keys_alt / vals_alt when *in_alt is true, else in keys / vals.
 int radix_sort_u64(Workspace &ws, uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                    int64_t n, int bits, bool *in_alt, cudaStream_t st);
-// Unique keys of a sorted array and their multiplicities; start_scratch holds
-// n int64 values.
+// Unique keys of a sorted array and their multiplicities.
 int run_length(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t *ukeys, uint32_t *counts,
-               int64_t *start_scratch, int64_t *nunique, cudaStream_t st);
+               int64_t *nunique, cudaStream_t st);
 
 }  // namespace lne

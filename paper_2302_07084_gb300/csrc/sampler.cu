@@ -1502,13 +1502,10 @@ int sort_raw(Workspace &ws, const GraphView &g, const SamplerSpec &sp, SortRaw *
     bool in_alt = false;
     LNE_TRY(radix_sort_u64(ws, k0, k1, nullptr, nullptr, total, 2 * sp.B, &in_alt, st));
     uint64_t *sorted = in_alt ? k1 : k0, *spare = in_alt ? k0 : k1;
-    int64_t *start = nullptr;
-    LNE_TRY(ws.get("sort.start", (size_t)std::max<int64_t>(total, 1), &start));
-    LNE_TRY(ws.get("sort.cnt", (size_t)std::max<int64_t>(total, 1), &R->cnt));
-    LNE_TRY(run_length(ws, sorted, total, spare, R->cnt, start, &R->U, st));
-    LNE_CUDA_TRY(cudaStreamSynchronize(st));
-    ws.release("sort.start");
     ws.release("sort.offs");
+    LNE_TRY(ws.get("sort.cnt", (size_t)std::max<int64_t>(total, 1), &R->cnt));
+    LNE_TRY(run_length(ws, sorted, total, spare, R->cnt, &R->U, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
     R->uk = spare;
     R->uk_name = in_alt ? "sort.k0" : "sort.k1";
     R->spare_name = in_alt ? "sort.k1" : "sort.k0";
@@ -1545,6 +1542,10 @@ int sort_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Counts
 }
 
 int sort_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out, cudaStream_t st) {
+    // a previous sparsifier's arrays are rebuilt below: free them before the
+    // sort's peak (tens of GB for billions of samples)
+    ws.release("csr.indices");
+    ws.release("csr.data");
     SortRaw R;
     LNE_TRY(sort_raw(ws, g, sp, &R, st));
     const int64_t U = R.U, n = g.n;

@@ -12,7 +12,8 @@
 //            warps), stages them grouped by digit in shared memory and writes
 //            each digit's run contiguously to its global offset.
 // run_length: unique keys of a sorted array and their multiplicities (tile
-// flag counts, one scan over tiles, block scans inside tiles).
+// flag counts, one scan over tiles, block scans inside tiles, each run's
+// length counted by the thread owning its first key).
 #include "common.cuh"
 #include "runtime.h"
 
@@ -141,11 +142,13 @@ __global__ void __launch_bounds__(kSortThreads) rle_count_kernel(const uint64_t 
     if (threadIdx.x == 0) tile_cnt[blockIdx.x] = s;
 }
 
-// Unique keys and the index where each run starts (thread-blocked items, block scan).
+// Unique keys and their run lengths (thread-blocked items, block scan); the
+// thread that owns a run's first key walks forward to the run's end, so every
+// key is read about twice in all and no start index array is needed.
 __global__ void __launch_bounds__(kSortThreads) rle_write_kernel(const uint64_t *__restrict__ keys, int64_t n,
                                                                  const int64_t *__restrict__ tile_off,
                                                                  uint64_t *__restrict__ ukeys,
-                                                                 int64_t *__restrict__ start) {
+                                                                 uint32_t *__restrict__ counts) {
     __shared__ int64_t s_warp[kSortWarps];
     const int tid = threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * kSortTile + (int64_t)tid * kSortItems;
@@ -161,16 +164,14 @@ __global__ void __launch_bounds__(kSortThreads) rle_write_kernel(const uint64_t 
     int64_t pos = tile_off[blockIdx.x] + block_scan256(c, s_warp);
     for (int j = 0; j < kSortItems; ++j)
         if (flags & (1u << j)) {
-            ukeys[pos] = keys[i0 + j];
-            start[pos] = i0 + j;
+            const int64_t g = i0 + j;
+            const uint64_t k = keys[g];
+            int64_t e = g + 1;
+            while (e < n && keys[e] == k) ++e;
+            ukeys[pos] = k;
+            counts[pos] = (uint32_t)(e - g);
             ++pos;
         }
-}
-
-__global__ void rle_len_kernel(const int64_t *__restrict__ start, int64_t u, int64_t n,
-                               uint32_t *__restrict__ cnt) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < u; i += (int64_t)gridDim.x * blockDim.x)
-        cnt[i] = (uint32_t)((i + 1 < u ? start[i + 1] : n) - start[i]);
 }
 
 }  // namespace
@@ -207,7 +208,7 @@ int radix_sort_u64(Workspace &ws, uint64_t *keys, uint64_t *keys_alt, uint32_t *
 }
 
 int run_length(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t *ukeys, uint32_t *counts,
-               int64_t *start_scratch, int64_t *nunique, cudaStream_t st) {
+               int64_t *nunique, cudaStream_t st) {
     *nunique = 0;
     if (n <= 0) return 0;
     const int64_t ntiles = ceil_div(n, (int64_t)kSortTile);
@@ -219,14 +220,11 @@ int run_length(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t *ukeys, 
     rle_count_kernel<<<(unsigned)ntiles, kSortThreads, 0, st>>>(keys, n, tc);
     LNE_LAUNCH_CHECK();
     LNE_TRY(scan_exclusive_u32_to_i64(tc, toff, ntiles, st));
-    rle_write_kernel<<<(unsigned)ntiles, kSortThreads, 0, st>>>(keys, n, toff, ukeys, start_scratch);
+    rle_write_kernel<<<(unsigned)ntiles, kSortThreads, 0, st>>>(keys, n, toff, ukeys, counts);
     LNE_LAUNCH_CHECK();
     int64_t u = 0;
     LNE_CUDA_TRY(cudaMemcpyAsync(&u, toff + ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
-    rle_len_kernel<<<(unsigned)std::min<int64_t>(ceil_div(u, 256), 152 * 16), 256, 0, st>>>(start_scratch, u, n,
-                                                                                           counts);
-    LNE_LAUNCH_CHECK();
     *nunique = u;
     return 0;
 }

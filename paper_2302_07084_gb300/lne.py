@@ -173,6 +173,16 @@ class DeviceGraph:
     def from_graph(cls, g, device="cuda"):
         return cls(g.indptr, g.indices, device)
 
+    @classmethod
+    def from_tensors(cls, indptr: torch.Tensor, indices: torch.Tensor):
+        """Wrap CSR arrays already on the device (int64 indptr, int32 indices)."""
+        g = cls.__new__(cls)
+        g.indptr = indptr.contiguous()
+        g.indices = indices.contiguous()
+        g.n = int(indptr.numel() - 1)
+        g.nnz = int(indices.numel())
+        return g
+
     def _c(self):
         return _Graph(self.n, self.nnz, self.indptr.data_ptr(), self.indices.data_ptr() if self.nnz else None)
 
@@ -183,6 +193,12 @@ class _DevView:
     def __init__(self, ptr, n, typestr):
         self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr or 0), False),
                                          "version": 3, "strides": None}
+
+
+def _view(ptr, n, typestr, dtype, device):
+    if n == 0:
+        return torch.empty(0, dtype=dtype, device=device)
+    return torch.as_tensor(_DevView(ptr, n, typestr), device=device)
 
 
 def _own(ptr, n, typestr, dtype, device):
@@ -292,16 +308,19 @@ class Context:
                     count=_own(out.count, out.nnz, "<u4", torch.uint32, self.dev),
                     total_samples=int(out.total_samples))
 
-    def sparsifier_csr(self, g: DeviceGraph, p: Params):
+    def sparsifier_csr(self, g: DeviceGraph, p: Params, copy: bool = True):
+        """The trunc_log sparsifier as a CSR dict. copy=False returns views of
+        the context's buffers, valid until the next call on this context."""
         out = _Csr()
         gc = g._c()
         pc, keep = p._c()
         self._check(self.lib.lne_sparsifier_csr(self.h, ctypes.byref(gc), ctypes.byref(pc), ctypes.byref(out),
                                                 _stream()))
+        wrap = _own if copy else _view
         return dict(n=int(out.n), nnz=int(out.nnz),
-                    indptr=_own(out.indptr, out.n + 1, "<i8", torch.int64, self.dev),
-                    indices=_own(out.indices, out.nnz, "<i4", torch.int32, self.dev),
-                    data=_own(out.data, out.nnz, "<f4", torch.float32, self.dev))
+                    indptr=wrap(out.indptr, out.n + 1, "<i8", torch.int64, self.dev),
+                    indices=wrap(out.indices, out.nnz, "<i4", torch.int32, self.dev),
+                    data=wrap(out.data, out.nnz, "<f4", torch.float32, self.dev))
 
     # ---- linear algebra -----------------------------------------------------
     def gaussian_sketch(self, n: int, c: int, seed: int) -> torch.Tensor:
