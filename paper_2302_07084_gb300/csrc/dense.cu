@@ -340,6 +340,7 @@ __global__ void __launch_bounds__(256) right_multiply_kernel(
 // where the refinement needs it: its products.
 // ---------------------------------------------------------------------------
 constexpr int kJacTPP = 8;
+constexpr int kJacMaxE = (160 + kJacTPP - 1) / kJacTPP;   // elements per thread and column, c <= 160
 
 __device__ __forceinline__ int circle_player(int pos, int round, int m) {
     return pos == 0 ? 0 : ((pos - 1 + round) % (m - 1)) + 1;
@@ -390,14 +391,20 @@ __global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__r
             }
             const bool active = pi < pairs && q < c;
             float al = 0.f, be = 0.f, ga = 0.f;
-            if (active) {
-                const float *ap = A + p * ldc, *aq = A + q * ldc;
-                for (int i = sub; i < c; i += kJacTPP) {
-                    float x = ap[i], y = aq[i];
-                    al = fmaf(x, x, al);
-                    be = fmaf(y, y, be);
-                    ga = fmaf(x, y, ga);
-                }
+            // the pair's elements stay in registers between the dot products
+            // and the rotation (one shared-memory read and write per element)
+            float xr[kJacMaxE], yr[kJacMaxE];
+            float *ap = A + p * ldc, *aq = A + q * ldc;
+#pragma unroll
+            for (int e = 0; e < kJacMaxE; ++e) {
+                const int i = sub + e * kJacTPP;
+                const bool in = active && i < c;
+                const float x = in ? ap[i] : 0.f, y = in ? aq[i] : 0.f;
+                xr[e] = x;
+                yr[e] = y;
+                al = fmaf(x, x, al);
+                be = fmaf(y, y, be);
+                ga = fmaf(x, y, ga);
             }
             // every lane takes part in the shuffles; lanes without a pair add zeros
 #pragma unroll
@@ -414,14 +421,17 @@ __global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__r
                     float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
                     float cs = rsqrtf(1.f + t * t);
                     float sn = cs * t;
-                    float *ap = A + p * ldc, *aq = A + q * ldc, *vp = V + p * ldc, *vq = V + q * ldc;
-                    for (int i = sub; i < c; i += kJacTPP) {
-                        float x = ap[i], y = aq[i];
-                        ap[i] = cs * x - sn * y;
-                        aq[i] = sn * x + cs * y;
-                        float u = vp[i], w = vq[i];
-                        vp[i] = cs * u - sn * w;
-                        vq[i] = sn * u + cs * w;
+                    float *vp = V + p * ldc, *vq = V + q * ldc;
+#pragma unroll
+                    for (int e = 0; e < kJacMaxE; ++e) {
+                        const int i = sub + e * kJacTPP;
+                        if (i < c) {
+                            ap[i] = cs * xr[e] - sn * yr[e];
+                            aq[i] = sn * xr[e] + cs * yr[e];
+                            const float u = vp[i], w = vq[i];
+                            vp[i] = cs * u - sn * w;
+                            vq[i] = sn * u + cs * w;
+                        }
                     }
                 }
             }
