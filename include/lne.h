@@ -103,6 +103,10 @@ typedef struct lne_ctx lne_ctx;
 #define LNE_AGG_SORT         3   /*   64-bit keys, radix sort and run lengths (any n < 2^31) */
 #define LNE_OPT_SPMM_THREADS 2   /* CTA size of the batched-tuning SpMM: 0 = picked by timing
                                     (default), or 64 / 128 / 256; results do not depend on it */
+#define LNE_OPT_DENSE_PRODUCT 4  /* products of the randomized SVD (FP32) on the dense count table
+                                    instead of the CSR, when the table aggregation ran: 0 = when at
+                                    least 10% of all pairs are present (default), 1 = never,
+                                    2 = always; same values, different summation order */
 #define LNE_OPT_TUNE_WORKERS 3   /* host worker threads (each with its own stream and workspace)
                                     of lne_tune_tasks, 1..16 (default 4) */
 

@@ -167,6 +167,7 @@ struct lne_ctx {
     lne::SpmmTune spmm_tune;
     lne::PropBatchGraph *prop_graph = nullptr;
     int tune_workers = 4;
+    int dense_mode = 0;
     std::vector<std::unique_ptr<lne::TuneWorker>> workers;
     lne::Surrogate surrogate;
 };
@@ -284,6 +285,11 @@ int lne_set_option(lne_ctx *ctx, int option, int64_t value) {
         if (value != 0 && value != 64 && value != 128 && value != 256)
             return finish(ctx, lne::fail(LNE_ERR_INVALID, "SpMM CTA size must be 0 (timed), 64, 128 or 256"));
         ctx->spmm_tune.forced = (int)value;
+        return LNE_OK;
+    }
+    if (option == LNE_OPT_DENSE_PRODUCT) {
+        if (value < 0 || value > 2) return finish(ctx, lne::fail(LNE_ERR_INVALID, "dense product mode must be 0..2"));
+        ctx->dense_mode = (int)value;
         return LNE_OK;
     }
     if (option == LNE_OPT_TUNE_WORKERS) {
@@ -536,13 +542,8 @@ int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_de
     float *X0 = nullptr;
     if (rc == 0) rc = ctx->ws.get("embed.x0", (size_t)g->n * p->d, &X0);
     if (rc == 0) {
-        lne::CsrView v;
-        v.n = M.n;
-        v.nnz = M.nnz;
-        v.indptr = M.indptr;
-        v.indices = M.indices;
-        v.data = M.data;
-        rc = lne::rsvd(ctx->ws, v, p->d, oversample_of(p), p->q, p->seed, p->precision, nullptr, nullptr, X0, st);
+        rc = lne::rsvd(ctx->ws, lne::product_view(M, ctx->dense_mode), p->d, oversample_of(p), p->q, p->seed,
+                       p->precision, nullptr, nullptr, X0, st);
     }
     if (rc == 0)
         rc = lne::propagate(ctx->ws, view(g), p->d, p->k, p->theta, p->mu, p->precision, X0, X_dev, nullptr, nullptr,
@@ -566,7 +567,8 @@ int lne_tune_batch(lne_ctx *ctx, const lne_graph *g, const lne_params *cands, in
     if (rc == 0) rc = check_graph_device(g, st);
     if (rc == 0 && !ctx->prop_graph) ctx->prop_graph = lne::new_prop_cache();
     if (rc == 0)
-        rc = lne::tune_batch(ctx->ws, ctx->prop_graph, ctx->spmm_tune, ctx->aggregation, view(g), cands, ncand,
+        rc = lne::tune_batch(ctx->ws, ctx->prop_graph, ctx->spmm_tune, ctx->aggregation, ctx->dense_mode, view(g),
+                             cands, ncand,
                              labels_dev, L, train_dev, n_train, test_dev, n_test, C, iters, macro_f1, micro_f1,
                              X_dev, st);
     return finish(ctx, rc);
@@ -605,7 +607,7 @@ int lne_tune_tasks(lne_ctx *ctx, const lne_task *tasks, int32_t ntasks, const ln
     }
     if (rc == 0)
         rc = lne::tune_tasks(ctx->workers, ctx->tune_workers, ctx->device, ctx->spmm_tune.forced, ctx->aggregation,
-                             tt.data(), ntasks, cands, ncand, C, iters, macro_f1, micro_f1);
+                             ctx->dense_mode, tt.data(), ntasks, cands, ncand, C, iters, macro_f1, micro_f1);
     return finish(ctx, rc);
 }
 

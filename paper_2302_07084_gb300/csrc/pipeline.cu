@@ -85,13 +85,18 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
     const bool bf16 = precision == LNE_PREC_BF16_MIXED;
     __nv_bfloat16 *Xh = nullptr;   // BF16 dense operand of the products
     if (bf16) LNE_TRY(ws.get("rsvd.xh", (size_t)n * c, &Xh));
+    // FP32 products: the dense upper triangle when the caller supplied it
+    auto mprod = [&](const float *X, float *Y) -> int {
+        if (M.dense) return dense_sym_spmm(ws, M.dense, M.dense_ld, n, X, c, c, Y, c, st);
+        return spmm(ws, M, X, c, c, Y, c, st);
+    };
     // Algorithm 4: Omega = randn(n, d+s); Y = M Omega
     LNE_TRY(gaussian_sketch(n, c, seed, Om, c, st));
     if (bf16) {
         LNE_TRY(to_bf16(Om, Xh, n * c, st));
         LNE_TRY(spmm_bf16(ws, M, Xh, c, c, Ya, c, nullptr, st));
     } else {
-        LNE_TRY(spmm(ws, M, Om, c, c, Ya, c, st));
+        LNE_TRY(mprod(Om, Ya));
     }
     // power iterations: Q = orth(Y); Y = M Q (q times)
     for (int it = 0; it < q; ++it) {
@@ -100,7 +105,7 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
             LNE_TRY(to_bf16(Ya, Xh, n * c, st));
             LNE_TRY(spmm_bf16(ws, M, Xh, c, c, Yb, c, nullptr, st));
         } else {
-            LNE_TRY(spmm(ws, M, Ya, c, c, Yb, c, st));
+            LNE_TRY(mprod(Ya, Yb));
         }
         std::swap(Ya, Yb);
     }

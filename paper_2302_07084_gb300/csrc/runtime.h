@@ -52,6 +52,10 @@ struct CsrView {
     const int64_t *indptr = nullptr;
     const int32_t *indices = nullptr;
     const float *data = nullptr;
+    // the same matrix as a dense upper triangle (row-major, leading dimension
+    // dense_ld), when the products should use it instead of the CSR
+    const float *dense = nullptr;
+    int64_t dense_ld = 0;
 };
 
 // Host-derived constants of the sampler (Algorithm 3 with the readings of the
@@ -90,7 +94,13 @@ struct CsrResult {
     int64_t *indptr = nullptr;
     int32_t *indices = nullptr;
     float *data = nullptr;
+    const float *dense = nullptr;   // the count table after Eq. 1 (table aggregation only)
+    int64_t dense_ld = 0;
 };
+// The view the randomized SVD's products use: the dense table when there is
+// one and mode allows (0 = when at least 10% of the pairs are present,
+// 1 = never, 2 = always), else the CSR.
+CsrView product_view(const CsrResult &M, int dense_mode);
 int sparsifier_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out,
                    cudaStream_t st);
 
@@ -135,6 +145,10 @@ struct SpmmEpilogue {
     int threads = 0;                    // CTA size of the merge kernel (0 = default)
     const char *carry_tag = nullptr;    // workspace name of the merge carry buffers (NULL = shared)
 };
+// Y = M X for M held as the dense upper triangle T (float bits, leading
+// dimension ld) of the symmetric sparsifier (spmm.cu).
+int dense_sym_spmm(Workspace &ws, const float *T, int64_t ld, int64_t n, const float *X, int64_t ldx, int c,
+                   float *Y, int64_t ldy, cudaStream_t st);
 // Carry buffers of the merge SpMM for nnz nonzeros and c columns, under the
 // workspace names tag + ".c" / tag + ".r" (tag NULL = "spmm.carry").
 int merge_carry(Workspace &ws, const char *tag, int64_t nnz, int c, float4 **carry, int64_t **carry_row);
@@ -172,7 +186,7 @@ struct SpmmTune {
 int spmm_threads_for(SpmmTune &tc, Workspace &ws, const GraphView &g, const float *X, int C, float *Y,
                      cudaStream_t st);
 // Batched tuning over ncand candidate parameter sets (tune.cu).
-int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregation, const GraphView &g,
+int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregation, int dense_mode, const GraphView &g,
                const lne_params *cands, int ncand, const uint8_t *labels, int L, const int32_t *train,
                int64_t n_train, const int32_t *test, int64_t n_test, double Creg, int iters, double *macro,
                double *micro, float *X_out, cudaStream_t st);
@@ -195,7 +209,7 @@ struct TuneTask {
     int64_t n_test = 0;
 };
 int tune_tasks(std::vector<std::unique_ptr<TuneWorker>> &workers, int nworkers, int device, int forced_threads,
-               int aggregation, const TuneTask *tasks, int ntasks, const lne_params *cands, int ncand, double Creg,
+               int aggregation, int dense_mode, const TuneTask *tasks, int ntasks, const lne_params *cands, int ncand, double Creg,
                int iters, double *macro, double *micro);
 
 // Surrogate regression network of the tuning search (surrogate.cu):

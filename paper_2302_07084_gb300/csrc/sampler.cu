@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kWalkThreads) tile_counts_kernel(WalkArgs A, i
 // table[x * ld + y] (x <= y); `keys` is the table, ld = nb_smem. MODE 3: write
 // the canonical key at the sample's position (no counting).
 template <typename KeyT, int MODE>
-__global__ void __launch_bounds__(kWalkThreads, 4) walk_emit_kernel(
+__global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_kernel(
     WalkArgs A, int64_t a_begin, int64_t a_end, int tile_arcs, const int64_t *__restrict__ tile_off,
     KeyT *__restrict__ keys, int32_t *__restrict__ u1, int32_t *__restrict__ v1,
     uint32_t *__restrict__ bucket_cnt, int nb_smem) {
@@ -1750,10 +1750,27 @@ int table_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResul
     }
     out->n = g.n;
     out->nnz = nnz;
+    out->dense = reinterpret_cast<const float *>(tb.T);
+    out->dense_ld = tb.ld;
     return 0;
 }
 
 }  // namespace
+
+CsrView product_view(const CsrResult &M, int dense_mode) {
+    CsrView v;
+    v.n = M.n;
+    v.nnz = M.nnz;
+    v.indptr = M.indptr;
+    v.indices = M.indices;
+    v.data = M.data;
+    const double dens = M.n > 0 ? (double)M.nnz / ((double)M.n * (double)M.n) : 0.0;
+    if (M.dense && (dense_mode == 2 || (dense_mode == 0 && dens >= 0.1))) {
+        v.dense = M.dense;
+        v.dense_ld = M.dense_ld;
+    }
+    return v;
+}
 
 int sparsifier_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out,
                       cudaStream_t st) {

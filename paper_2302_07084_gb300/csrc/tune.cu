@@ -94,7 +94,7 @@ int spmm_threads_for(SpmmTune &tc, Workspace &ws, const GraphView &g, const floa
     return best;
 }
 
-int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregation, const GraphView &g,
+int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregation, int dense_mode, const GraphView &g,
                const lne_params *cands, int ncand, const uint8_t *labels, int L, const int32_t *train,
                int64_t n_train, const int32_t *test, int64_t n_test, double Creg, int iters, double *macro,
                double *micro, float *X_out, cudaStream_t st) {
@@ -132,13 +132,8 @@ int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregati
         sp.aggregation = aggregation;
         CsrResult M;
         LNE_TRY(sparsifier_csr(ws, g, sp, &M, st));
-        CsrView v;
-        v.n = M.n;
-        v.nnz = M.nnz;
-        v.indptr = M.indptr;
-        v.indices = M.indices;
-        v.data = M.data;
-        LNE_TRY(rsvd(ws, v, d, os_of(p), p.q, p.seed, p.precision, nullptr, nullptr, X0s + (size_t)q * n * d, st));
+        LNE_TRY(rsvd(ws, product_view(M, dense_mode), d, os_of(p), p.q, p.seed, p.precision, nullptr, nullptr,
+                     X0s + (size_t)q * n * d, st));
     }
     float *X = nullptr, *U = nullptr;
     double *R = nullptr, *UR = nullptr, *sig = nullptr;
@@ -210,7 +205,7 @@ TuneWorker::~TuneWorker() {
 }
 
 int tune_tasks(std::vector<std::unique_ptr<TuneWorker>> &workers, int nworkers, int device, int forced_threads,
-               int aggregation, const TuneTask *tasks, int ntasks, const lne_params *cands, int ncand, double Creg,
+               int aggregation, int dense_mode, const TuneTask *tasks, int ntasks, const lne_params *cands, int ncand, double Creg,
                int iters, double *macro, double *micro) {
     nworkers = std::max(1, std::min(nworkers, ntasks));
     while ((int)workers.size() < nworkers) {
@@ -231,7 +226,7 @@ int tune_tasks(std::vector<std::unique_ptr<TuneWorker>> &workers, int nworkers, 
         w->tune.forced = forced_threads;
         for (int t; rc == 0 && !stop.load() && (t = next.fetch_add(1)) < ntasks;) {
             const TuneTask &k = tasks[t];
-            rc = tune_batch(w->ws, nullptr, w->tune, aggregation, k.g, cands + (size_t)t * ncand, ncand, k.labels,
+            rc = tune_batch(w->ws, nullptr, w->tune, aggregation, dense_mode, k.g, cands + (size_t)t * ncand, ncand, k.labels,
                             k.L, k.train, k.n_train, k.test, k.n_test, Creg, iters, macro + (size_t)t * ncand,
                             micro + (size_t)t * ncand, nullptr, w->st);
         }

@@ -37,6 +37,7 @@ SURROGATE_PARAMS = 73_985
 OPT_AGGREGATION = 1
 OPT_SPMM_THREADS = 2
 OPT_TUNE_WORKERS = 3
+OPT_DENSE_PRODUCT = 4
 AGG_AUTO, AGG_TABLE, AGG_BUCKET, AGG_SORT = 0, 1, 2, 3
 
 
