@@ -39,7 +39,7 @@ constexpr int kBucketBits = 15;                 // keys per reduce bucket = 2^15
 constexpr int kMaxSmemBuckets = 12288;          // walk/scatter histogram capacity
 constexpr int kWalkThreads = 256;
 constexpr int kWalkWarps = kWalkThreads / 32;
-constexpr int kChunk = 2048;                     // samples ranked by window length at a time
+constexpr int kChunk = 1024;                     // samples ranked by window length at a time
 
 struct WalkArgs {
     const int64_t *indptr;
@@ -335,6 +335,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
     __shared__ uint8_t s_rlut[4096];
     __shared__ uint64_t s_rmagic[17];
     __shared__ uint32_t s_upack[kChunk], s_uw3[kChunk], s_pack[kChunk], s_w3[kChunk];
+    __shared__ uint16_t s_lo[kChunk];   // arc within the tile of each chunk sample (phase 1 -> phase 2)
     __shared__ uint32_t s_wcnt[17 * kWalkWarps];
 
     uint32_t *s_off = smem;                                      // tile_arcs + 1
@@ -422,6 +423,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
                 int lo;
                 uint32_t j;
                 locate(cb + idx, lo, j);
+                s_lo[idx] = (uint16_t)lo;
                 draw_head(A, s_rlut, s_rmagic, a0 + lo, j, &r, &sg, &w3);
             }
             const unsigned grp = __match_any_sync(0xffffffffu, r);
@@ -474,8 +476,10 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
             const uint32_t s0 = cb + (pk0 & 0x7FFu), s1 = cb + (pk1 & 0x7FFu);
             int lo0, lo1;
             uint32_t j0, j1;
-            locate(s0, lo0, j0);
-            locate(s1, lo1, j1);
+            lo0 = s_lo[pk0 & 0x7FFu];
+            lo1 = s_lo[pk1 & 0x7FFu];
+            j0 = s0 - s_off[lo0];
+            j1 = s1 - s_off[lo1];
             Draw d0, d1;
             draw_begin(A, a0 + lo0, j0, (int)((pk0 >> 11) & 31), (int)((pk0 >> 16) & 15), s_w3[q0], s_src[lo0],
                        s_dst[lo0], d0);
