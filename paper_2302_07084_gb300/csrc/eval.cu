@@ -19,7 +19,7 @@
 namespace lne {
 namespace {
 
-constexpr int kEvalRows = 1024;  // rows per FP32 partial sum
+constexpr int kEvalRows = 128;   // rows per FP32 partial sum (and per CTA)
 
 // Xa[i] = (X[idx[i]], 1), Ys[i][l] = +1 / -1.
 __global__ void gather_rows_kernel(const float *__restrict__ X, int64_t ldx, int d, const uint8_t *__restrict__ lab,
@@ -64,67 +64,30 @@ __global__ void grad_partial_kernel(const float *__restrict__ Xa, const float *_
 }
 
 // hpart[b][l][a][c] (a <= c) = sum over rows of block b of D[i][l] Xa[i][a] Xa[i][c];
-// thread (ti, tj), ti <= tj, owns an 8 x 8 tile; grid (row blocks, labels).
+// CTA (row block, label): the block's rows and their D-weighted copies staged in
+// shared memory, one thread per entry (a, c) of the upper triangle.
 __global__ void __launch_bounds__(256) hess_partial_kernel(const float *__restrict__ Xa, const float *__restrict__ D,
                                                            int64_t m, int da, int L, double *__restrict__ hpart) {
-    extern __shared__ float xs[];   // kGram rows x dp (weighted by D)
-    constexpr int kRows = 32;
+    extern __shared__ float xs[];   // kEvalRows x dp rows, then the weighted rows
     const int dp = (da + 7) & ~7;
-    const int nt = dp / 8;
-    const int ntiles = nt * (nt + 1) / 2;
     const int l = blockIdx.y;
     const int64_t r0 = (int64_t)blockIdx.x * kEvalRows;
-    const int64_t r1 = imin64(m, r0 + kEvalRows);
-    float *ws = xs + kRows * dp;
+    const int rows = (int)imin64(kEvalRows, m - r0);
+    float *wx = xs + kEvalRows * dp;
+    for (int e = threadIdx.x; e < rows * da; e += blockDim.x) {
+        const int r = e / da, a = e - r * da;
+        const float x = Xa[(r0 + r) * da + a];
+        xs[r * dp + a] = x;
+        wx[r * dp + a] = x * D[(r0 + r) * L + l];
+    }
+    __syncthreads();
     double *out = hpart + ((int64_t)blockIdx.x * L + l) * dp * dp;
-    for (int g0 = 0; g0 < ntiles; g0 += blockDim.x) {
-        const int tile = g0 + threadIdx.x;
-        const bool active = tile < ntiles;
-        int ti = 0, tj = 0;
-        if (active) {
-            int rem = tile;
-            while (rem >= nt - ti) {
-                rem -= nt - ti;
-                ++ti;
-            }
-            tj = ti + rem;
-        }
-        float acc[8][8];
-#pragma unroll
-        for (int a = 0; a < 8; ++a)
-#pragma unroll
-            for (int b = 0; b < 8; ++b) acc[a][b] = 0.f;
-        for (int64_t base = r0; base < r1; base += kRows) {
-            const int rows = (int)imin64(kRows, r1 - base);
-            for (int e = threadIdx.x; e < kRows * dp; e += blockDim.x) {
-                const int rr = e / dp, cc = e - rr * dp;
-                const float x = (rr < rows && cc < da) ? Xa[(base + rr) * da + cc] : 0.f;
-                xs[e] = x;
-                ws[e] = rr < rows ? x * D[(base + rr) * L + l] : 0.f;
-            }
-            __syncthreads();
-            if (active) {
-                for (int rr = 0; rr < rows; ++rr) {
-                    float av[8], bv[8];
-#pragma unroll
-                    for (int t = 0; t < 8; ++t) {
-                        av[t] = ws[rr * dp + ti * 8 + t];
-                        bv[t] = xs[rr * dp + tj * 8 + t];
-                    }
-#pragma unroll
-                    for (int x = 0; x < 8; ++x)
-#pragma unroll
-                        for (int y = 0; y < 8; ++y) acc[x][y] = fmaf(av[x], bv[y], acc[x][y]);
-                }
-            }
-            __syncthreads();
-        }
-        if (active) {
-#pragma unroll
-            for (int x = 0; x < 8; ++x)
-#pragma unroll
-                for (int y = 0; y < 8; ++y) out[(ti * 8 + x) * dp + tj * 8 + y] = acc[x][y];
-        }
+    for (int t = threadIdx.x; t < da * da; t += blockDim.x) {
+        const int a = t / da, c = t - a * da;
+        if (a > c) continue;
+        float acc = 0.f;
+        for (int r = 0; r < rows; ++r) acc = fmaf(wx[r * dp + a], xs[r * dp + c], acc);
+        out[a * dp + c] = acc;
     }
 }
 
@@ -268,7 +231,8 @@ int macro_f1(Workspace &ws, const float *X, int64_t n, int d, int64_t ldx, const
         gather_rows_kernel<<<egrid(n_test * da), 256, 0, st>>>(X, ldx, d, labels, L, test_idx, n_test, Xt, Yt);
         LNE_LAUNCH_CHECK();
     }
-    const int hsmem = 2 * 32 * dp * 4;
+    const int hsmem = 2 * kEvalRows * dp * 4;
+    if (hsmem > 48 * 1024) LNE_TRY(allow_dynamic_smem(hess_partial_kernel));
     const int ssmem = (da * da + da) * 8;
     LNE_TRY(allow_dynamic_smem(newton_solve_kernel));
     for (int it = 0; it < iters; ++it) {

@@ -1652,11 +1652,12 @@ bool use_table(const GraphView &g, const SamplerSpec &sp) {
     if (sp.aggregation == LNE_AGG_TABLE) return true;
     if (sp.aggregation != LNE_AGG_AUTO) return false;
     if (g.n > 65536) return false;
-    // the table costs ~10 passes over its n_pad^2 / 2 counters, the sort ~100
-    // bytes of traffic per sample: the table when it is the cheaper of the two
+    // measured on GB300: the table's passes cost ~4e-12 s per counter of the
+    // n_pad^2 table, the sort path ~1.9e-10 s per sample -- the table when it
+    // is the cheaper of the two
     const double ld = (double)ceil_div(g.n, (int64_t)kTile) * kTile;
     const double samples = (double)g.nnz * ((double)sp.base + (double)sp.thr_frac / 4294967296.0);
-    return ld * ld <= 10.0 * samples;
+    return ld * ld <= 40.0 * samples;
 }
 
 // Walk every arc's samples and count them into the dense upper-triangle table.

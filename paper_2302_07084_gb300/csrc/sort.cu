@@ -80,13 +80,23 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter_kernel(
 #pragma unroll
         for (int w = 0; w < kSortWarps; ++w) s_wc[w][tid] = 0;
     }
+    // every key (and payload) of the tile is requested up front: 32 independent
+    // loads per thread in flight instead of one per round
+    uint64_t kr[kSortItems];
+    uint32_t vr[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int li = r * kSortThreads + tid;
+        kr[r] = li < nt ? kin[i0 + li] : 0ull;
+        vr[r] = (VALS && li < nt) ? vin[i0 + li] : 0u;
+    }
     __syncthreads();
+#pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const int li = r * kSortThreads + tid;   // rounds in input order: stable
         const bool valid = li < nt;
-        const uint64_t k = valid ? kin[i0 + li] : 0ull;
-        uint32_t v = 0;
-        if (VALS && valid) v = vin[i0 + li];
+        const uint64_t k = kr[r];
+        const uint32_t v = vr[r];
         const uint32_t d = valid ? (uint32_t)(k >> shift) & 255u : 256u;
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const uint32_t lr = (uint32_t)__popc(peers & ((1u << lane) - 1u));

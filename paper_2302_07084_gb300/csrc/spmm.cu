@@ -188,6 +188,41 @@ __device__ __forceinline__ void gather4(const int32_t *__restrict__ indices, con
     }
 }
 
+// Narrow products (c4 <= LG): the warp works as 32 / LG groups of LG lanes;
+// group g takes nonzeros g, g + G, ... of the chunk and lane q of a group owns
+// column group q. The groups' partial sums are combined by a fixed xor tree at
+// the end of each row segment, so the result is deterministic.
+template <int LG, bool WEIGHTED, typename TX>
+__device__ __forceinline__ void gather4_grouped(const int32_t *__restrict__ indices, const float *__restrict__ vals,
+                                                int64_t p, int cnt, const TX *__restrict__ X, int64_t ldx, int c4,
+                                                int lane, float4 &acc) {
+    constexpr int G = 32 / LG;
+    const int col = lane < cnt ? __ldg(indices + p + lane) : 0;
+    float v = 0.f;
+    if (WEIGHTED) v = lane < cnt ? __ldg(vals + p + lane) : 0.f;
+    const int g = lane / LG, q = lane % LG;
+#pragma unroll 4
+    for (int k0 = 0; k0 < cnt; k0 += G) {
+        const int k = k0 + g;
+        const int ck = __shfl_sync(0xffffffffu, col, k & 31);
+        const float vk = WEIGHTED ? __shfl_sync(0xffffffffu, v, k & 31) : 1.f;
+        if (k < cnt && q < c4) {
+            const float4 x = load4(X + (int64_t)ck * ldx, q);
+            if (WEIGHTED) {
+                acc.x = fmaf(vk, x.x, acc.x);
+                acc.y = fmaf(vk, x.y, acc.y);
+                acc.z = fmaf(vk, x.z, acc.z);
+                acc.w = fmaf(vk, x.w, acc.w);
+            } else {
+                acc.x += x.x;
+                acc.y += x.y;
+                acc.z += x.z;
+                acc.w += x.w;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 __device__ __forceinline__ float4 fma4(float4 a, float4 x, float4 y) {
@@ -245,7 +280,7 @@ __device__ __forceinline__ int64_t row_of(const int64_t *__restrict__ indptr, in
     return lo;
 }
 
-template <int NV, bool WEIGHTED, typename TX>
+template <int NV, bool WEIGHTED, typename TX, int LG = 32>
 __global__ void __launch_bounds__(256) spmm_merge_kernel(int64_t n, int64_t nnz, const int64_t *__restrict__ indptr,
                                                          const int32_t *__restrict__ indices,
                                                          const float *__restrict__ vals, const TX *__restrict__ X,
@@ -270,8 +305,21 @@ __global__ void __launch_bounds__(256) spmm_merge_kernel(int64_t n, int64_t nnz,
         Acc4<NV> acc;
 #pragma unroll
         for (int t = 0; t < NV; ++t) acc.v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int64_t q = p; q < e; q += 32)
-            gather4<NV, WEIGHTED, TX>(indices, vals, q, (int)imin64(32, e - q), X, ldx, c4, lane, acc);
+        if (LG < 32) {
+            for (int64_t q = p; q < e; q += 32)
+                gather4_grouped<LG, WEIGHTED, TX>(indices, vals, q, (int)imin64(32, e - q), X, ldx, c4, lane,
+                                                  acc.v[0]);
+#pragma unroll
+            for (int off = LG; off < 32; off <<= 1) {
+                acc.v[0].x += __shfl_xor_sync(0xffffffffu, acc.v[0].x, off);
+                acc.v[0].y += __shfl_xor_sync(0xffffffffu, acc.v[0].y, off);
+                acc.v[0].z += __shfl_xor_sync(0xffffffffu, acc.v[0].z, off);
+                acc.v[0].w += __shfl_xor_sync(0xffffffffu, acc.v[0].w, off);
+            }
+        } else {
+            for (int64_t q = p; q < e; q += 32)
+                gather4<NV, WEIGHTED, TX>(indices, vals, q, (int)imin64(32, e - q), X, ldx, c4, lane, acc);
+        }
         if (rs >= p0 && re <= p1) {
             epilogue4<NV>(r, re - rs, acc, lane, c4, Y, ldy, ep);
         } else {
@@ -407,7 +455,19 @@ int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, c
                                                                      carry_row);                           \
         spmm_fixup_kernel<K><<<fblocks, 256, 0, st>>>(n, indptr, c4, Y, ldy, ep, W, carry, carry_row);      \
         break;
-    switch (nv) {
+#define LNE_MERGE_GROUPED(LGV)                                                                              \
+    {                                                                                                       \
+        if (nnz > 0)                                                                                        \
+            spmm_merge_kernel<1, WEIGHTED, TX, LGV><<<mblocks, threads, 0, st>>>(                          \
+                n, nnz, indptr, indices, vals, X, ldx, c4, Y, ldy, ep, W, nwarps, carry, carry_row);        \
+        spmm_fixup_kernel<1><<<fblocks, 256, 0, st>>>(n, indptr, c4, Y, ldy, ep, W, carry, carry_row);      \
+    }
+    // weighted products with at most 16 float4 column groups: several nonzeros
+    // per warp step (the graph products keep one, so batched propagation sums
+    // in the same order as a single candidate's)
+    if (WEIGHTED && c4 <= 8) LNE_MERGE_GROUPED(8)
+    else if (WEIGHTED && c4 <= 16) LNE_MERGE_GROUPED(16)
+    else switch (nv) {
         LNE_MERGE_CASE(1)
         LNE_MERGE_CASE(2)
         LNE_MERGE_CASE(4)
@@ -416,6 +476,7 @@ int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, c
             return fail(LNE_ERR_UNSUPPORTED, "SpMM supports at most 1024 dense columns");
     }
 #undef LNE_MERGE_CASE
+#undef LNE_MERGE_GROUPED
     LNE_LAUNCH_CHECK();
     ::lne::count_launch();
     return 0;
