@@ -490,12 +490,13 @@ int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, c
 // When the sparsifier is dense enough (41% of all pairs on the benchmark),
 // a tiled FP32 product that streams the table once beats gathering a dense
 // X row per nonzero; every product is the same FP32 FMA of the same values.
-// CTA tile: 64 rows x 16 TN columns over one of `ks` slices of the k range,
-// K steps of 16; thread (ty, tx) of 16 x 16 owns rows 4 ty .. 4 ty + 3 and
+// CTA tile: 128 rows x 16 TN columns over one of `ks` slices of the k range,
+// K steps of 16; thread (ty, tx) of 16 x 16 owns rows 8 ty .. 8 ty + 7 and
 // columns tx + 16 j. Slices write partial products that a second kernel adds
 // in slice order (deterministic).
 // ---------------------------------------------------------------------------
-constexpr int kDmRows = 64;
+constexpr int kDmTM = 8;                 // rows per thread
+constexpr int kDmRows = 16 * kDmTM;      // rows per CTA
 constexpr int kDmK = 16;
 constexpr int kDmPad = kDmRows + 4;
 
@@ -520,8 +521,8 @@ __global__ void __launch_bounds__(256) dense_sym_mm_kernel(const float *__restri
 #pragma unroll
         for (int q = 0; q < kAPer; ++q) {
             const int e = q * 256 + tid;
-            const int m = upper ? (e >> 4) : (e & (kDmRows - 1));
-            const int k = upper ? (e & 15) : (e >> 6);
+            const int m = upper ? (e / kDmK) : (e % kDmRows);
+            const int k = upper ? (e % kDmK) : (e / kDmRows);
             const int64_t r = r0 + m, kk = k0 + k;
             ra[q] = (r < n && kk < ke) ? (r <= kk ? T[r * ld + kk] : T[kk * ld + r]) : 0.f;
         }
@@ -538,8 +539,8 @@ __global__ void __launch_bounds__(256) dense_sym_mm_kernel(const float *__restri
 #pragma unroll
         for (int q = 0; q < kAPer; ++q) {
             const int e = q * 256 + tid;
-            const int m = upper ? (e >> 4) : (e & (kDmRows - 1));
-            const int k = upper ? (e & 15) : (e >> 6);
+            const int m = upper ? (e / kDmK) : (e % kDmRows);
+            const int k = upper ? (e % kDmK) : (e / kDmRows);
             As[buf][k][m] = ra[q];
         }
 #pragma unroll
@@ -548,9 +549,9 @@ __global__ void __launch_bounds__(256) dense_sym_mm_kernel(const float *__restri
             if (e < kDmK * 16 * TN) Xs[buf][e / (16 * TN)][e % (16 * TN)] = rx[q];
         }
     };
-    float acc[4][TN];
+    float acc[kDmTM][TN];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < kDmTM; ++i)
 #pragma unroll
         for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
     int buf = 0;
@@ -564,17 +565,22 @@ __global__ void __launch_bounds__(256) dense_sym_mm_kernel(const float *__restri
         if (more) fetch(k0 + kDmK);
 #pragma unroll
         for (int k = 0; k < kDmK; ++k) {
-            const float4 a = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 4]);
+            float a[kDmTM];
+#pragma unroll
+            for (int h = 0; h < kDmTM / 4; ++h) {
+                const float4 a4 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * kDmTM + 4 * h]);
+                a[4 * h] = a4.x;
+                a[4 * h + 1] = a4.y;
+                a[4 * h + 2] = a4.z;
+                a[4 * h + 3] = a4.w;
+            }
             float b[TN];
 #pragma unroll
             for (int j = 0; j < TN; ++j) b[j] = Xs[buf][k][tx + 16 * j];
 #pragma unroll
-            for (int j = 0; j < TN; ++j) {
-                acc[0][j] = fmaf(a.x, b[j], acc[0][j]);
-                acc[1][j] = fmaf(a.y, b[j], acc[1][j]);
-                acc[2][j] = fmaf(a.z, b[j], acc[2][j]);
-                acc[3][j] = fmaf(a.w, b[j], acc[3][j]);
-            }
+            for (int i = 0; i < kDmTM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
         if (more) stash(buf ^ 1, k0 + kDmK);
         __syncthreads();
@@ -582,8 +588,8 @@ __global__ void __launch_bounds__(256) dense_sym_mm_kernel(const float *__restri
     }
     float *Pz = P + (int64_t)blockIdx.y * n * c;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int64_t r = r0 + ty * 4 + i;
+    for (int i = 0; i < kDmTM; ++i) {
+        const int64_t r = r0 + ty * kDmTM + i;
         if (r >= n) continue;
 #pragma unroll
         for (int j = 0; j < TN; ++j) {
