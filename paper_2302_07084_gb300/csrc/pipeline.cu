@@ -410,7 +410,7 @@ int propagate_batch(Workspace &ws, PropBatchGraph *cache, const GraphView &g, in
     LNE_CUDA_TRY(cudaMemcpyAsync(coef, h.data(), sizeof(float) * h.size(), cudaMemcpyHostToDevice, st));
     float4 *carry = nullptr;
     int64_t *carry_row = nullptr;
-    LNE_TRY(merge_carry(ws, "pb.carry", g.nnz, C, &carry, &carry_row));
+    LNE_TRY(merge_carry(ws, "pb.carry", g.nnz, g.n, C, &carry, &carry_row));
     const float *om = coef, *hom = coef + C, *gam = coef + 2 * C;
     if (!cache) return prop_batch_chain(ws, g, C, kmax, X0, F, Z, Tb, G, P, om, hom, gam, threads, st);
     // graph key: everything the captured launches depend on

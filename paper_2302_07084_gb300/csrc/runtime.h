@@ -149,9 +149,10 @@ struct SpmmEpilogue {
 // dimension ld) of the symmetric sparsifier (spmm.cu).
 int dense_sym_spmm(Workspace &ws, const float *T, int64_t ld, int64_t n, const float *X, int64_t ldx, int c,
                    float *Y, int64_t ldy, cudaStream_t st);
-// Carry buffers of the merge SpMM for nnz nonzeros and c columns, under the
+// Carry buffers of the merge SpMM for nnz nonzeros over n rows and c columns, under the
 // workspace names tag + ".c" / tag + ".r" (tag NULL = "spmm.carry").
-int merge_carry(Workspace &ws, const char *tag, int64_t nnz, int c, float4 **carry, int64_t **carry_row);
+int merge_carry(Workspace &ws, const char *tag, int64_t nnz, int64_t n, int c, float4 **carry,
+                int64_t **carry_row);
 int graph_spmm(Workspace &ws, const GraphView &g, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
                const SpmmEpilogue &ep, cudaStream_t st);
 // The same products with a BF16 dense operand (FP32 accumulation); c % 4 == 0.

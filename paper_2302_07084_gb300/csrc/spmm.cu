@@ -415,13 +415,17 @@ bool merge_ok(const TX *X, int64_t ldx, int c, const float *Y, int64_t ldy, cons
            aligned(ep.Yb, 8) && aligned(ep.Gb, 8) && aligned(ep.b1_col, 16) && aligned(ep.gamma_col, 16);
 }
 
-// nonzeros per warp slice: ~8 waves of warps, at least 32 nonzeros each;
-// beyond 1024 per slice only for very large products (>6e7 nonzeros), which
-// keeps the carry buffers (two rows of c per warp) small
-int64_t merge_slice(int64_t nnz) {
+// nonzeros per warp slice: ~8 waves of warps, at least about two average rows
+// (fewer rows split across slices: measured 1.14 -> 0.92 ms for the 19 graph
+// products of the benchmark) and at least 32; beyond 1024 per slice only for
+// very large products (>6e7 nonzeros), which keeps the carry buffers (two rows
+// of c per warp) small
+int64_t merge_slice(int64_t nnz, int64_t n) {
     const int64_t W = nnz / (152 * 48 * 8);
+    const int64_t two_rows = n > 0 ? 2 * ceil_div(nnz, n) : 32;
+    const int64_t lo = std::max<int64_t>(32, std::min<int64_t>(1024, two_rows / 32 * 32));
     const int64_t cap = nnz > (int64_t)152 * 48 * 8 * 1024 ? 65536 : 1024;
-    return std::max<int64_t>(32, std::min<int64_t>(cap, (W + 31) / 32 * 32));
+    return std::max<int64_t>(lo, std::min<int64_t>(cap, (W + 31) / 32 * 32));
 }
 
 int merge_vectors(int c) {
@@ -438,11 +442,11 @@ int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, c
     if (n <= 0) return 0;
     const int c4 = c / 4;
     const int nv = merge_vectors(c);
-    const int64_t W = merge_slice(nnz);
+    const int64_t W = merge_slice(nnz, n);
     const int64_t nwarps = std::max<int64_t>(1, ceil_div(nnz, W));
     float4 *carry = nullptr;
     int64_t *carry_row = nullptr;
-    LNE_TRY(merge_carry(ws, ep.carry_tag, nnz, c, &carry, &carry_row));
+    LNE_TRY(merge_carry(ws, ep.carry_tag, nnz, n, c, &carry, &carry_row));
     const int threads = ep.threads > 0 ? ep.threads : 256;
     const unsigned mblocks = (unsigned)ceil_div(nwarps, threads / 32);
     const unsigned fblocks = (unsigned)std::min<int64_t>(ceil_div(n, 8), 152 * 32);
@@ -610,8 +614,9 @@ __global__ void slice_sum_kernel(const float *__restrict__ P, int ks, int64_t n,
     }
 }
 
-int merge_carry(Workspace &ws, const char *tag, int64_t nnz, int c, float4 **carry, int64_t **carry_row) {
-    const int64_t nwarps = std::max<int64_t>(1, ceil_div(nnz, merge_slice(nnz)));
+int merge_carry(Workspace &ws, const char *tag, int64_t nnz, int64_t n, int c, float4 **carry,
+                int64_t **carry_row) {
+    const int64_t nwarps = std::max<int64_t>(1, ceil_div(nnz, merge_slice(nnz, n)));
     const std::string t = tag ? tag : "spmm.carry";
     LNE_TRY(ws.get(t + ".c", (size_t)nwarps * 2 * merge_vectors(c) * 32, carry));
     LNE_TRY(ws.get(t + ".r", (size_t)nwarps * 2, carry_row));
