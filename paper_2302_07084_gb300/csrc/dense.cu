@@ -468,24 +468,34 @@ __global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__r
 }
 
 // C = op(A) op(B) (+ C0 if given), all c x c row-major FP64; 16 x 16 tile per CTA.
-__global__ void __launch_bounds__(256) dgemm_small_kernel(const double *__restrict__ A, int ta,
-                                                          const double *__restrict__ B, int tb,
-                                                          const double *__restrict__ C0,
-                                                          double *__restrict__ C, int c) {
-    __shared__ double As[16][17], Bs[16][17];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
-    double acc = 0.0;
-    for (int k0 = 0; k0 < c; k0 += 16) {
-        const int ka = k0 + tx;
-        As[ty][tx] = (row < c && ka < c) ? (ta ? A[ka * c + row] : A[row * c + ka]) : 0.0;
-        const int kb = k0 + ty;
-        Bs[ty][tx] = (kb < c && col < c) ? (tb ? B[col * c + kb] : B[kb * c + col]) : 0.0;
-        __syncthreads();
-#pragma unroll
-        for (int k = 0; k < 16; ++k) acc = fma(As[ty][k], Bs[k][tx], acc);
-        __syncthreads();
+// 8 x 8 output tiles (64 threads, one output each; 324 CTAs for c = 144). The
+// CTA's 8 rows of op(A) and 8 columns of op(B) over the whole k range are
+// loaded into shared memory at once (one round of load latency instead of one
+// per k step), then each thread runs its dot product.
+constexpr int kDgTile = 8;
+constexpr int kDgMaxC = 160;
+
+__global__ void __launch_bounds__(kDgTile * kDgTile) dgemm_small_kernel(const double *__restrict__ A, int ta,
+                                                                        const double *__restrict__ B, int tb,
+                                                                        const double *__restrict__ C0,
+                                                                        double *__restrict__ C, int c) {
+    __shared__ double As[kDgTile][kDgMaxC + 1], Bs[kDgMaxC][kDgTile + 1];
+    const int tid = threadIdx.x, tx = tid % kDgTile, ty = tid / kDgTile;
+    const int r0 = blockIdx.y * kDgTile, c0 = blockIdx.x * kDgTile;
+    for (int e = tid; e < kDgTile * c; e += kDgTile * kDgTile) {
+        // op(A)[r0 + i][k]: for ta the k index runs along A's rows
+        const int i = ta ? e % kDgTile : e / c, k = ta ? e / kDgTile : e % c;
+        const int r = r0 + i;
+        As[i][k] = r < c ? (ta ? A[k * c + r] : A[r * c + k]) : 0.0;
+        // op(B)[k][c0 + j]
+        const int j = tb ? e / c : e % kDgTile, kb = tb ? e % c : e / kDgTile;
+        const int cc = c0 + j;
+        Bs[kb][j] = cc < c ? (tb ? B[cc * c + kb] : B[kb * c + cc]) : 0.0;
     }
+    __syncthreads();
+    const int row = r0 + ty, col = c0 + tx;
+    double acc = 0.0;
+    for (int k = 0; k < c; ++k) acc = fma(As[ty][k], Bs[k][tx], acc);
     if (row < c && col < c) C[row * c + col] = C0 ? C0[row * c + col] + acc : acc;
 }
 
@@ -785,9 +795,10 @@ int cholqr2(Workspace &ws, float *Y, int64_t n, int c, int64_t ld, double *Rout,
 
 static int dgemm_small(const double *A, bool ta, const double *B, bool tb, const double *C0, double *C, int c,
                        cudaStream_t st) {
-    dim3 grid((unsigned)ceil_div(c, 16), (unsigned)ceil_div(c, 16));
+    if (c > kDgMaxC) return fail(LNE_ERR_UNSUPPORTED, "small FP64 products support c <= 160");
+    dim3 grid((unsigned)ceil_div(c, kDgTile), (unsigned)ceil_div(c, kDgTile));
     LNE_TRACE("dgemm_small", st);
-    dgemm_small_kernel<<<grid, 256, 0, st>>>(A, ta ? 1 : 0, B, tb ? 1 : 0, C0, C, c);
+    dgemm_small_kernel<<<grid, kDgTile * kDgTile, 0, st>>>(A, ta ? 1 : 0, B, tb ? 1 : 0, C0, C, c);
     LNE_LAUNCH_CHECK();
     return 0;
 }
