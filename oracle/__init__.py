@@ -72,7 +72,7 @@ def lib():
         L.oracle_count_samples.restype = ctypes.c_int64
         L.oracle_sample_trace.argtypes = [ctypes.c_int64, i64p, i32p, ctypes.c_int, f64p,
                                           ctypes.c_double, ctypes.c_uint64, ctypes.c_int64,
-                                          ctypes.c_int64, i64p, i32p, i32p, i64p, i64p]
+                                          ctypes.c_int64, i64p, i32p, i32p, i64p, i64p, u32p]
         L.oracle_sample_trace.restype = ctypes.c_int64
         L.oracle_sketch_words.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, u32p]
         L.oracle_num_threads.restype = ctypes.c_int
@@ -138,8 +138,8 @@ def sample_trace(indptr, indices, T, s, S, seed, a0=0, a1=None, fields=("arc", "
     """Every PathSampling draw of arcs [a0, a1) in (arc, sample) order.
 
     Returns a dict with the requested fields: ``arc``, window ``r``, split
-    ``sigma`` and the ordered endpoints ``u1`` (walked from the arc's source)
-    and ``v1`` (walked from its target).
+    ``sigma``, the ordered endpoints ``u1`` (walked from the arc's source)
+    and ``v1`` (walked from its target), and the downsampling ``coin`` word.
     """
     indptr = np.ascontiguousarray(indptr, dtype=np.int64)
     indices = np.ascontiguousarray(indices, dtype=np.int32)
@@ -154,13 +154,14 @@ def sample_trace(indptr, indices, T, s, S, seed, a0=0, a1=None, fields=("arc", "
         "sigma": np.zeros(total, np.int32) if "sigma" in fields else None,
         "u1": np.zeros(total, np.int64) if "u1" in fields else None,
         "v1": np.zeros(total, np.int64) if "v1" in fields else None,
+        "coin": np.zeros(total, np.uint32) if "coin" in fields else None,
     }
     got = lib().oracle_sample_trace(
         n, _ptr(indptr, ctypes.c_int64), _ptr(indices, ctypes.c_int32), len(s),
         _ptr(s, ctypes.c_double), float(S), int(seed), int(a0), int(a1),
         _ptr(out["arc"], ctypes.c_int64), _ptr(out["r"], ctypes.c_int32),
         _ptr(out["sigma"], ctypes.c_int32), _ptr(out["u1"], ctypes.c_int64),
-        _ptr(out["v1"], ctypes.c_int64))
+        _ptr(out["v1"], ctypes.c_int64), _ptr(out["coin"], ctypes.c_uint32))
     assert got == total
     return {k: v for k, v in out.items() if v is not None}
 
@@ -171,17 +172,49 @@ def sample_pairs(indptr, indices, T, s, S, seed, a0=0, a1=None):
     return np.minimum(tr["u1"], tr["v1"]), np.maximum(tr["u1"], tr["v1"])
 
 
-def sparsifier_counts(indptr, indices, T, s, S, seed):
+def arc_downsample(indptr, indices, C: float):
+    """Edge downsampling (Sec. 4.1, Algorithm 3 lines 5-9) per CSR arc u -> v:
+    p_e = min(1, C (1/d_u + 1/d_v)); the coin keeps a draw iff its word is below
+    thr_e = min(2^32, floor(p_e 2^32)); a kept draw adds the weight 1/p_e, held
+    in fixed point with 2^-32 units, w_e = floor(2^32 / p_e + 1/2), so that
+    sums are exact and independent of their order. Returns (thr_e, w_e) as
+    uint64 arrays over the arcs."""
+    indptr = np.asarray(indptr, dtype=np.int64)
+    indices = np.asarray(indices, dtype=np.int64)
+    n = len(indptr) - 1
+    deg = np.diff(indptr).astype(np.float64)
+    src = np.repeat(np.arange(n), np.diff(indptr))
+    du, dv = deg[src], deg[indices]
+    p = np.minimum(1.0, C * (1.0 / du + 1.0 / dv))
+    thr = np.where(p >= 1.0, 2.0 ** 32, np.floor(p * 4294967296.0)).astype(np.uint64)
+    w = np.floor(4294967296.0 / p + 0.5).astype(np.uint64)
+    return thr, w
+
+
+def sparsifier_counts(indptr, indices, T, s, S, seed, C: float = 0.0):
     """Exact multiplicity K_xy of every sampled unordered pair (x <= y).
 
     The aggregation of Sec. 4.2 (hash table with atomic counts) computes the
     multiset of sampled pairs; here it is a sort and a run-length count.
-    Returns (x, y, count) sorted by (x, y).
+    Returns (x, y, count) sorted by (x, y). With edge downsampling (C > 0) the
+    third array is the pair's summed weight in 2^-32 units (uint64, exact):
+    only draws whose coin comes up heads count, each with weight 1/p_e of its
+    arc (``arc_downsample``).
     """
     n = len(indptr) - 1
-    x, y = sample_pairs(indptr, indices, T, s, S, seed)
-    keys, cnt = np.unique(x * n + y, return_counts=True)
-    return keys // n, keys % n, cnt.astype(np.int64)
+    if C <= 0.0:
+        x, y = sample_pairs(indptr, indices, T, s, S, seed)
+        keys, cnt = np.unique(x * n + y, return_counts=True)
+        return keys // n, keys % n, cnt.astype(np.int64)
+    tr = sample_trace(indptr, indices, T, s, S, seed, fields=("arc", "u1", "v1", "coin"))
+    thr, w = arc_downsample(indptr, indices, C)
+    kept = tr["coin"].astype(np.uint64) < thr[tr["arc"]]
+    x = np.minimum(tr["u1"], tr["v1"])[kept]
+    y = np.maximum(tr["u1"], tr["v1"])[kept]
+    keys, inv = np.unique(x * n + y, return_inverse=True)
+    wsum = np.zeros(len(keys), dtype=np.uint64)
+    np.add.at(wsum, inv, w[tr["arc"][kept]])
+    return keys // n, keys % n, wsum
 
 
 # ----------------------------------------------------------------------------
@@ -200,17 +233,22 @@ def netmf_scale(vol: float, S: float, b: float = 1.0) -> tuple[float, float]:
     return vv / ((2.0 * S) * b), vv / (S * b)
 
 
-def netmf_values(x, y, cnt, deg, S, b=1.0):
+def netmf_values(x, y, cnt, deg, S, b=1.0, weighted=False):
     """Pre-log entries v, keep mask (v > 1) and float32 trunc_log values (Eq. 1).
 
     v = fl(fl(K * alpha) / fl(d_x * d_y)); trunc_log(v) = max(0, log v) is zero
-    unless v > 1, and zero entries are dropped from the sparse matrix.
+    unless v > 1, and zero entries are dropped from the sparse matrix. With
+    ``weighted`` the counts are downsampling weight sums in 2^-32 units and
+    K = fl(double(cnt)) * 2^-32.
     """
     deg = np.asarray(deg, dtype=np.float64)
     vol = float(deg.sum())
     a_off, a_diag = netmf_scale(vol, float(S), float(b))
     alpha = np.where(x == y, a_diag, a_off)
-    v = (np.asarray(cnt, dtype=np.float64) * alpha) / (deg[x] * deg[y])
+    K = np.asarray(cnt, dtype=np.float64)
+    if weighted:
+        K = K * 2.0 ** -32
+    v = (K * alpha) / (deg[x] * deg[y])
     keep = v > 1.0
     val = np.zeros(v.shape, dtype=np.float32)
     val[keep] = np.log(v[keep]).astype(np.float32)
@@ -230,12 +268,13 @@ def sparsifier_csr(n, x, y, val):
     return indptr, cols.astype(np.int32), data
 
 
-def sparsifier(indptr, indices, T, s, S, seed, b=1.0):
-    """Counts -> trunc_log -> CSR. Returns a dict with every intermediate."""
+def sparsifier(indptr, indices, T, s, S, seed, b=1.0, C=0.0):
+    """Counts -> trunc_log -> CSR. Returns a dict with every intermediate
+    (with edge downsampling, C > 0, ``cnt`` holds the weight sums)."""
     n = len(indptr) - 1
     deg = np.diff(indptr)
-    x, y, cnt = sparsifier_counts(indptr, indices, T, s, S, seed)
-    v, keep, val = netmf_values(x, y, cnt, deg, S, b)
+    x, y, cnt = sparsifier_counts(indptr, indices, T, s, S, seed, C)
+    v, keep, val = netmf_values(x, y, cnt, deg, S, b, weighted=C > 0.0)
     mp, mc, mv = sparsifier_csr(n, x[keep], y[keep], val[keep])
     return dict(x=x, y=y, cnt=cnt, v=v, keep=keep, val=val, indptr=mp, indices=mc, data=mv)
 

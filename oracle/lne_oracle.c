@@ -22,8 +22,8 @@
  *       thr_i = min(2^32, floor(2^32 * (s_1+..+s_i) / (s_1+..+s_T)));
  *   - split sigma = word mod r; walk step x <- nbr(x)[word mod deg(x)];
  *   - sample j of arc a uses Philox counter (j, a_lo, a_hi, blk), blk = 0,1,..,
- *     key (seed_lo, seed_hi); its words in order are: r, sigma, coin (drawn and
- *     unused while downsampling is off), then the walk steps, u side first;
+ *     key (seed_lo, seed_hi); its words in order are: r, sigma, the
+ *     downsampling coin, then the walk steps, u side first;
  *   - the arc's Bernoulli word is word 0 of counter
  *     (0xFFFFFFFF, a_lo, a_hi, 0xFFFFFFFF).
  *
@@ -161,7 +161,8 @@ static int64_t walk(const int64_t *indptr, const int32_t *indices, int64_t x, in
 /* One sample: writes r, sigma and the ordered endpoints (u', v'). */
 static void path_sample(const int64_t *indptr, const int32_t *indices, int T,
                         const uint64_t *thr, int64_t u, int64_t v, int64_t a, uint64_t j,
-                        uint64_t seed, int *r_out, int *sigma_out, int64_t *u1, int64_t *v1)
+                        uint64_t seed, int *r_out, int *sigma_out, uint32_t *coin_out,
+                        int64_t *u1, int64_t *v1)
 {
     word_stream st;
     ws_init(&st, j, a, seed);
@@ -171,11 +172,12 @@ static void path_sample(const int64_t *indptr, const int32_t *indices, int T,
         if (thr[i] <= (uint64_t)wr) r += 1;
     uint32_t wsig = ws_next(&st);
     int sigma = (int)(wsig % (uint32_t)r);
-    (void)ws_next(&st);   /* coin word: reserved for edge downsampling */
+    uint32_t coin = ws_next(&st);   /* the downsampling coin (Algorithm 3, line 5) */
     int64_t uu = walk(indptr, indices, u, sigma, &st);
     int64_t vv = walk(indptr, indices, v, r - 1 - sigma, &st);
     *r_out = r;
     *sigma_out = sigma;
+    *coin_out = coin;
     *u1 = uu;
     *v1 = vv;
 }
@@ -194,12 +196,14 @@ int64_t oracle_count_samples(int64_t n_arcs, int64_t a0, int64_t a1, double S, u
  * Every sample of arcs [a0, a1), in (arc, sample) order. Any output pointer may
  * be NULL. Returns the number of samples written.
  *   arc[k], r[k], sigma[k], u1[k], v1[k]: the sample's arc, window, split and
- *   ordered endpoints (u' from the arc's source side, v' from its target side).
+ *   ordered endpoints (u' from the arc's source side, v' from its target side);
+ *   coin[k]: its downsampling coin word (the walk is drawn whatever the coin).
  */
 int64_t oracle_sample_trace(int64_t n, const int64_t *indptr, const int32_t *indices,
                             int T, const double *s, double S, uint64_t seed,
                             int64_t a0, int64_t a1,
-                            int64_t *arc, int32_t *r, int32_t *sigma, int64_t *u1, int64_t *v1)
+                            int64_t *arc, int32_t *r, int32_t *sigma, int64_t *u1, int64_t *v1,
+                            uint32_t *coin)
 {
     int64_t n_arcs = indptr[n];
     uint64_t thr[32];
@@ -222,8 +226,10 @@ int64_t oracle_sample_trace(int64_t n, const int64_t *indptr, const int32_t *ind
         for (int64_t k = off[i]; k < off[i + 1]; ++k) {
             uint64_t j = (uint64_t)(k - off[i]);
             int rr, ss;
+            uint32_t cw;
             int64_t x, y;
-            path_sample(indptr, indices, T, thr, u, v, a, j, seed, &rr, &ss, &x, &y);
+            path_sample(indptr, indices, T, thr, u, v, a, j, seed, &rr, &ss, &cw, &x, &y);
+            if (coin) coin[k] = cw;
             if (arc) arc[k] = a;
             if (r) r[k] = rr;
             if (sigma) sigma[k] = ss;

@@ -229,3 +229,75 @@ def test_sparsifier_csr_structure():
     keep = sp_["keep"]
     ndiag = int((sp_["x"][keep] == sp_["y"][keep]).sum())
     assert M.nnz == 2 * int(keep.sum()) - ndiag
+
+
+# ----------------------------------------------------------------------------
+# edge downsampling (Sec. 4.1; Algorithm 3, lines 5-9)
+# ----------------------------------------------------------------------------
+
+def _star_path():
+    """0 -- 1, 2, 3, 4 and 1 -- 2: degrees 4, 2, 2, 1, 1."""
+    e = [(0, 1), (0, 2), (0, 3), (0, 4), (1, 2)]
+    u = np.array([a for a, b in e])
+    v = np.array([b for a, b in e])
+    indptr, indices = synth.csr_from_edges(5, u, v)
+    return indptr, indices
+
+
+def test_downsample_rule_closed_form():
+    indptr, indices = _star_path()
+    thr, w = oracle.arc_downsample(indptr, indices, 0.5)
+    arcs = {(int(a), int(indices[k])): k for a in range(5) for k in range(indptr[a], indptr[a + 1])}
+    # arc 0 -> 1: p = 0.5 (1/4 + 1/2) = 0.375
+    k = arcs[(0, 1)]
+    assert thr[k] == int(0.375 * 2 ** 32) == 1610612736
+    assert w[k] == 11453246123            # floor(2^32 / 0.375 + 1/2) = floor(11453246122.67 + 0.5)
+    # arc 3 -> 0: p = 0.5 (1 + 1/4) = 0.625
+    k = arcs[(3, 0)]
+    assert thr[k] == 2684354560 and w[k] == 6871947674
+    # C = 2: p = min(1, 2 * 0.75) = 1 -> the coin always keeps, weight exactly 1
+    thr, w = oracle.arc_downsample(indptr, indices, 2.0)
+    k = arcs[(0, 1)]
+    assert thr[k] == 2 ** 32 and w[k] == 2 ** 32
+
+
+def test_downsampling_with_certain_coins_is_the_plain_count():
+    g = synth.sbm(600, 3, 0.05, 0.005, seed=3)
+    s = np.full(10, 0.1)
+    x, y, c = oracle.sparsifier_counts(g.indptr, g.indices, 10, s, 4.0 * g.n_arcs, 7)
+    xw, yw, w = oracle.sparsifier_counts(g.indptr, g.indices, 10, s, 4.0 * g.n_arcs, 7, C=1e6)
+    assert np.array_equal(x, xw) and np.array_equal(y, yw)
+    assert np.array_equal(w, c.astype(np.uint64) * np.uint64(2 ** 32))
+
+
+def test_downsampled_counts_are_unbiased():
+    """Theorem 1's reweighting: E[sum of 1/p_e over kept draws] = E[count]."""
+    g = synth.lollipop_tiny()
+    T = 5
+    s = [0.1, 0.3, 0.2, 0.25, 0.15]
+    S = 20000.0 * g.n_arcs
+    C = 0.5
+    thr, wts = oracle.arc_downsample(g.indptr, g.indices, C)
+    assert np.all(thr < 2 ** 32)             # every arc is really downsampled here
+    x, y, w = oracle.sparsifier_counts(g.indptr, g.indices, T, s, S, seed=31, C=C)
+    K = np.zeros((g.n, g.n))
+    K[x, y] = w.astype(np.float64) * 2.0 ** -32
+    EK = _expected_counts(g, T, s, S)
+    iu = np.triu_indices(g.n)
+    assert np.all(K[iu][EK[iu] == 0] == 0)
+    m = EK[iu] > 0
+    wmax = float(wts.max()) * 2.0 ** -32      # a draw adds at most 1/min p_e
+    z = (K[iu][m] - EK[iu][m]) / np.sqrt(EK[iu][m] * wmax)
+    assert np.max(np.abs(z)) < 6
+
+
+def test_kept_draws_follow_the_coin_law():
+    g = synth.sbm(400, 2, 0.06, 0.01, seed=5)
+    S = 30.0 * g.n_arcs
+    C = 2.0
+    tr = oracle.sample_trace(g.indptr, g.indices, 4, [0.25] * 4, S, 9, fields=("arc", "coin"))
+    thr, _ = oracle.arc_downsample(g.indptr, g.indices, C)
+    p = thr[tr["arc"]].astype(np.float64) / 2.0 ** 32
+    kept = tr["coin"].astype(np.uint64) < thr[tr["arc"]]
+    z = (kept.sum() - p.sum()) / np.sqrt(np.sum(p * (1 - p)))
+    assert abs(z) < 5 and 0 < kept.sum() < len(kept)
