@@ -45,8 +45,8 @@ extern "C" {
 #define LNE_ERR_UNSUPPORTED -5   /* valid input outside what this build handles */
 #define LNE_ERR_NUMERIC     -6   /* Cholesky breakdown or non-finite values */
 
-/* Precision of the dense operand of the sparse products (Algorithm 4 lines 3
- * and 5, the propagation products). Accumulation is FP32 in both; the Gram,
+/* Precision of the dense operand of the sparse products (the products of
+ * Algorithm 4, the propagation products). Accumulation is FP32 in both; the Gram,
  * Cholesky and small SVD are FP64 in both. With LNE_PREC_BF16_MIXED the sketch,
  * the power-iteration bases and the propagation operands are gathered as
  * bfloat16 copies (the recurrences themselves stay FP32); d and d + oversample
@@ -75,6 +75,9 @@ typedef struct {
     double mu;                 /* filter centre mu */
     uint64_t seed;             /* Philox key for sampling and the sketch */
     int32_t precision;         /* LNE_PREC_* */
+    double downsample_C;       /* edge downsampling (Sec. 4.1): 0 = off; C > 0 keeps a draw of arc
+                                  u -> v with probability p_e = min(1, C (1/d_u + 1/d_v)) and
+                                  weighs it 1/p_e; finite, >= 0 */
 } lne_params;
 
 typedef struct {
@@ -89,8 +92,11 @@ typedef struct {
     int64_t nnz;               /* distinct sampled unordered pairs */
     int32_t *x;                /* device [nnz], x <= y, sorted by (x, y) */
     int32_t *y;                /* device [nnz] */
-    uint32_t *count;           /* device [nnz], exact multiplicities */
-    int64_t total_samples;     /* sum of all per-arc sample counts */
+    uint32_t *count;           /* device [nnz], exact multiplicities; NULL with edge downsampling */
+    int64_t total_samples;     /* sum of all per-arc sample counts (dropped draws included) */
+    uint64_t *weight;          /* device [nnz], with edge downsampling: sum of 1/p_e over the pair's
+                                  kept draws in units of 2^-32, each 1/p_e rounded to
+                                  floor(2^32/p_e + 1/2) (exact integer sums); else NULL */
 } lne_counts;
 
 typedef struct lne_ctx lne_ctx;
@@ -128,7 +134,8 @@ int lne_set_option(lne_ctx *ctx, int option, int64_t value);
  * walk from the arc's source, v1_dev[i] the end of the walk from its target.
  * `capacity` is the length of the two output arrays; *count_out receives the
  * number of draws (synchronises). Fails with LNE_ERR_INVALID if capacity is too
- * small (nothing is written then).
+ * small (nothing is written then). With edge downsampling a draw whose coin
+ * drops it keeps its slot and reads (-1, -1).
  */
 int lne_sample_pairs(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
                      int64_t arc_begin, int64_t arc_end, int32_t *u1_dev, int32_t *v1_dev,
@@ -137,7 +144,9 @@ int lne_sample_pairs(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
 /*
  * Exact multiplicity of every sampled unordered pair (x <= y) over all arcs --
  * the aggregation step of Sec. 4.2 ("sparse parallel hashing"). Output buffers
- * are context-owned. Synchronises.
+ * are context-owned. Synchronises. With edge downsampling the pairs are those
+ * of the kept draws and `weight` replaces `count` (table or sort aggregation;
+ * LNE_AGG_BUCKET fails with LNE_ERR_UNSUPPORTED).
  */
 int lne_sparsifier_counts(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
                           lne_counts *out, void *stream);
@@ -147,13 +156,15 @@ int lne_sparsifier_counts(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
  * alpha = vol^2 / (2 S b) off the diagonal and vol^2 / (S b) on it (K the
  * unordered count), kept iff v > 1 (decided exactly as fl(fl(K alpha) /
  * fl(d_x d_y)) > 1 in FP64), value log(v) in float32. Symmetric CSR, both
- * triangles, rows sorted; context-owned. Synchronises.
+ * triangles, rows sorted; context-owned. Synchronises. With edge downsampling K
+ * is the pair's summed weight times 2^-32 (converted to FP64 exactly up to one
+ * rounding) in place of the count.
  */
 int lne_sparsifier_csr(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
                        lne_csr *out, void *stream);
 
 /*
- * Gaussian sketch Omega = randn(n, c) (Algorithm 4, line 2), Box-Muller from
+ * Gaussian sketch Omega = randn(n, c) (Algorithm 4), Box-Muller from
  * Philox4x32-10 words: row i, column block j/4 uses counter (i, j/4, 0, 0) and
  * key (seed_lo ^ 0x4f4d4547, seed_hi). out_dev is [n][ld], ld >= c.
  */
@@ -161,7 +172,7 @@ int lne_gaussian_sketch(lne_ctx *ctx, int64_t n, int32_t c, uint64_t seed, float
                         int64_t ld, void *stream);
 
 /* Y = M X for CSR M (n x n) and X [n][ldx] (c columns), Y [n][ldy] FP32,
- * accumulated in FP32 (Algorithm 4, lines 3 and 5). X_dev is float
+ * accumulated in FP32 (Algorithm 4). X_dev is float
  * (precision LNE_PREC_FP32) or bfloat16 (LNE_PREC_BF16_MIXED; c and ldx must then
  * be multiples of 4). */
 int lne_spmm(lne_ctx *ctx, const lne_csr *M, const void *X_dev, int64_t ldx, int32_t c,

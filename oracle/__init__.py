@@ -12,7 +12,7 @@ FP64, each function citing the passage it follows:
   (per-edge sampling, Sec. 4.2) and the walk-step rule of Sec. 4.2;
 * ``netmf_values`` / ``sparsifier_csr``: Eq. 1 (the NetMF matrix with the
   truncated logarithm) estimated from the sample counts;
-* ``gaussian_sketch``: the Gaussian test matrix of Algorithm 4, line 2;
+* ``gaussian_sketch``: the Gaussian test matrix of Algorithm 4;
 * ``eig_svd``: Algorithm 2 (eigSVD);
 * ``fast_randomized_svd``: Algorithm 4;
 * ``embedding_from_svd``: X = U Sigma^{1/2} (Sec. 3.2);
@@ -106,7 +106,7 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 
 def window_thresholds(s) -> np.ndarray:
-    """thr_1..thr_{T-1} for drawing r ~ Multinomial(s_1..s_T) (Algorithm 3, line 6)."""
+    """thr_1..thr_{T-1} for drawing r ~ Multinomial(s_1..s_T) (Algorithm 3)."""
     s = np.ascontiguousarray(s, dtype=np.float64)
     thr = np.zeros(max(len(s) - 1, 1), dtype=np.uint64)
     lib().oracle_window_thresholds(len(s), _ptr(s, ctypes.c_double), _ptr(thr, ctypes.c_uint64))
@@ -114,7 +114,7 @@ def window_thresholds(s) -> np.ndarray:
 
 
 def arc_rate(S: float, n_arcs: int) -> tuple[int, int]:
-    """(floor(S/2m), floor(frac(S/2m) * 2^32)) -- Algorithm 3, line 3."""
+    """(floor(S/2m), floor(frac(S/2m) * 2^32)) -- Algorithm 3."""
     b = ctypes.c_uint64()
     f = ctypes.c_uint64()
     lib().oracle_arc_rate(float(S), int(n_arcs), ctypes.byref(b), ctypes.byref(f))
@@ -173,7 +173,7 @@ def sample_pairs(indptr, indices, T, s, S, seed, a0=0, a1=None):
 
 
 def arc_downsample(indptr, indices, C: float):
-    """Edge downsampling (Sec. 4.1, Algorithm 3 lines 5-9) per CSR arc u -> v:
+    """Edge downsampling (Sec. 4.1, Algorithm 3) per CSR arc u -> v:
     p_e = min(1, C (1/d_u + 1/d_v)); the coin keeps a draw iff its word is below
     thr_e = min(2^32, floor(p_e 2^32)); a kept draw adds the weight 1/p_e, held
     in fixed point with 2^-32 units, w_e = floor(2^32 / p_e + 1/2), so that
@@ -304,7 +304,7 @@ def netmf_dense(indptr, indices, T, s, b=1.0):
 # ----------------------------------------------------------------------------
 
 def gaussian_sketch(n: int, c: int, seed: int) -> np.ndarray:
-    """Omega = randn(n, c) (Algorithm 4, line 2) by Box-Muller from Philox words.
+    """Omega = randn(n, c) (Algorithm 4) by Box-Muller from Philox words.
 
     Row i, column block cb = col // 4 uses the 4 words of counter (i, cb, 0, 0),
     key (seed_lo ^ 0x4f4d4547, seed_hi); words (w0, w1) give columns 4cb, 4cb+1
@@ -446,9 +446,10 @@ def spectral_propagation(indptr, indices, X0: np.ndarray, k: int, theta: float, 
 # whole method
 # ----------------------------------------------------------------------------
 
-def embed(indptr, indices, T, s, S, d, q, k, theta, mu, seed, oversample=16, b=1.0):
-    """Sparsifier -> randomized SVD -> X0 -> spectral propagation -> X."""
-    sparse = sparsifier(indptr, indices, T, s, S, seed, b)
+def embed(indptr, indices, T, s, S, d, q, k, theta, mu, seed, oversample=16, b=1.0, C=0.0):
+    """Sparsifier (edge-downsampled when C > 0, Sec. 4.1) -> randomized SVD ->
+    X0 -> spectral propagation -> X."""
+    sparse = sparsifier(indptr, indices, T, s, S, seed, b, C)
     rs = fast_randomized_svd(sparse["indptr"], sparse["indices"], sparse["data"], d, q,
                              oversample, seed)
     X0 = embedding_from_svd(rs["U"], rs["sigma"])

@@ -172,7 +172,7 @@ static void path_sample(const int64_t *indptr, const int32_t *indices, int T,
         if (thr[i] <= (uint64_t)wr) r += 1;
     uint32_t wsig = ws_next(&st);
     int sigma = (int)(wsig % (uint32_t)r);
-    uint32_t coin = ws_next(&st);   /* the downsampling coin (Algorithm 3, line 5) */
+    uint32_t coin = ws_next(&st);   /* the downsampling coin (Algorithm 3) */
     int64_t uu = walk(indptr, indices, u, sigma, &st);
     int64_t vv = walk(indptr, indices, v, r - 1 - sigma, &st);
     *r_out = r;

@@ -220,6 +220,8 @@ int check_params(const lne_params *p, bool sampling) {
     }
     if (p->precision != LNE_PREC_FP32 && p->precision != LNE_PREC_BF16_MIXED)
         return lne::fail(LNE_ERR_INVALID, "unknown precision");
+    if (!(p->downsample_C >= 0.0) || !std::isfinite(p->downsample_C))
+        return lne::fail(LNE_ERR_INVALID, "downsample_C must be a finite value >= 0");
     return 0;
 }
 
@@ -375,6 +377,7 @@ int lne_sample_pairs(lne_ctx *ctx, const lne_graph *g, const lne_params *p, int6
     lne::SamplerSpec sp;
     if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
     sp.aggregation = ctx->aggregation;
+    sp.ds_C = p->downsample_C;
     if (rc == 0) rc = lne::sample_pairs(ctx->ws, view(g), sp, arc_begin, arc_end, u1_dev, v1_dev, capacity,
                                         count_out, st);
     return finish(ctx, rc);
@@ -392,6 +395,7 @@ int lne_sparsifier_counts(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
     lne::SamplerSpec sp;
     if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
     sp.aggregation = ctx->aggregation;
+    sp.ds_C = p->downsample_C;
     lne::CountsResult r;
     if (rc == 0) rc = lne::sparsifier_counts(ctx->ws, view(g), sp, &r, st);
     if (rc == 0) {
@@ -400,6 +404,7 @@ int lne_sparsifier_counts(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
         out->y = r.y;
         out->count = r.cnt;
         out->total_samples = r.total_samples;
+        out->weight = r.weight;
     }
     return finish(ctx, rc);
 }
@@ -415,6 +420,7 @@ int lne_sparsifier_csr(lne_ctx *ctx, const lne_graph *g, const lne_params *p, ln
     lne::SamplerSpec sp;
     if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
     sp.aggregation = ctx->aggregation;
+    sp.ds_C = p->downsample_C;
     lne::CsrResult r;
     if (rc == 0) rc = lne::sparsifier_csr(ctx->ws, view(g), sp, &r, st);
     if (rc == 0) {
@@ -537,6 +543,7 @@ int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_de
     lne::SamplerSpec sp;
     if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
     sp.aggregation = ctx->aggregation;
+    sp.ds_C = p->downsample_C;
     lne::CsrResult M;
     if (rc == 0) rc = lne::sparsifier_csr(ctx->ws, view(g), sp, &M, st);
     float *X0 = nullptr;

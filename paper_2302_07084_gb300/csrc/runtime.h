@@ -70,6 +70,7 @@ struct SamplerSpec {
     double alpha_off = 0, alpha_diag = 0;
     float off_hi = 0, off_lo = 0, diag_hi = 0, diag_lo = 0;   // alpha as float pairs
     int aggregation = 0;          // LNE_AGG_* (0 = automatic)
+    double ds_C = 0.0;            // edge downsampling constant C (0 = off)
 };
 
 int make_sampler_spec(const GraphView &g, int T, const double *s, double S, double b, uint64_t seed,
@@ -84,7 +85,8 @@ struct CountsResult {
     int64_t total_samples = 0;
     int32_t *x = nullptr;
     int32_t *y = nullptr;
-    uint32_t *cnt = nullptr;
+    uint32_t *cnt = nullptr;      // multiplicities (no downsampling)
+    uint64_t *weight = nullptr;   // summed 1/p_e in 2^-32 units (edge downsampling)
 };
 int sparsifier_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out,
                       cudaStream_t st);
@@ -257,5 +259,8 @@ int radix_sort_u64(Workspace &ws, uint64_t *keys, uint64_t *keys_alt, uint32_t *
 // Unique keys of a sorted array and their multiplicities.
 int run_length(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t *ukeys, uint32_t *counts,
                int64_t *nunique, cudaStream_t st);
+// Unique keys of a sorted array and, per run, the sum of w[arcs[i]] over it.
+int run_length_weighted(Workspace &ws, const uint64_t *keys, const uint32_t *arcs, const uint64_t *w, int64_t n,
+                        uint64_t *ukeys, uint64_t *wsum, int64_t *nunique, cudaStream_t st);
 
 }  // namespace lne

@@ -1,10 +1,10 @@
 // Sparsifier construction on the GPU (Sec. 4.2 of the paper, re-designed):
 //
 //   1. tile_counts     per-arc sample counts n_a = floor(S/2m) + Bernoulli
-//                      (Algorithm 3, line 3) summed per tile of arcs; scanned
+//                      (Algorithm 3) summed per tile of arcs; scanned
 //                      into tile offsets.
 //   2. walk_emit       one thread per sample: window r ~ Multinomial(s)
-//                      (Algorithm 3, line 6), split sigma ~ U{0..r-1} and the
+//                      (Algorithm 3), split sigma ~ U{0..r-1} and the
 //                      two walks of PathSampling (Algorithm 1), each step
 //                      x <- nbr(x)[word mod deg(x)] (Sec. 4.2). Emits the
 //                      canonical pair key (min << B | max) and a shared-memory
@@ -60,6 +60,10 @@ struct WalkArgs {
     int T_eff;                    // how many thresholds are below 2^32
     uint64_t base_magic;          // ceil(2^64 / base): s / base by a high multiply
     uint64_t rmagic[17];          // ceil(2^64 / r) for r = 1..16 (index r)
+    // edge downsampling (NULL = off): per arc, the coin keeps a draw iff its
+    // coin word < ds_thr[arc]; a kept draw weighs ds_w[arc] (2^-32 units)
+    const uint64_t *ds_thr;
+    const uint64_t *ds_w;
 };
 
 __device__ __forceinline__ uint32_t arc_count(const WalkArgs &A, int64_t arc) {
@@ -188,10 +192,11 @@ struct Draw {
     int32_t v, uend;
 };
 
-// Block 0 of the sample's stream: the window r, the split sigma and word 3.
+// Block 0 of the sample's stream: the window r, the split sigma, the
+// downsampling coin and word 3.
 __device__ __forceinline__ void draw_head(const WalkArgs &A, const uint8_t *__restrict__ rlut,
                                           const uint64_t *__restrict__ rmagic, int64_t arc, uint32_t j, int *r_out,
-                                          int *sigma_out, uint32_t *w3_out) {
+                                          int *sigma_out, uint32_t *coin_out, uint32_t *w3_out) {
     const u32x4 b0 = philox_rk(u32x4{j, (uint32_t)((uint64_t)arc & 0xFFFFFFFFu), (uint32_t)((uint64_t)arc >> 32), 0u},
                                A.rk);
     // r = 1 + #{i : thr_i <= w0}; the table gives it unless a threshold falls
@@ -204,6 +209,7 @@ __device__ __forceinline__ void draw_head(const WalkArgs &A, const uint8_t *__re
     }
     *r_out = r;
     *sigma_out = (int)fastmod32(b0.y, rmagic[r], (uint32_t)r);
+    *coin_out = b0.z;
     *w3_out = b0.w;
 }
 
@@ -385,16 +391,32 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
         }
         j = s - s_off[lo];
     };
-    auto emit = [&](uint32_t s, int32_t pu, int32_t pv) {
+    // a draw the downsampling coin drops leaves a marker at its position:
+    // (-1, -1) for raw draws, a key above every pair key for the sort
+    auto emit_dropped = [&](uint32_t s, int64_t arc) {
+        if (MODE == 0) {
+            u1[out0 + s] = -1;
+            v1[out0 + s] = -1;
+        } else if (MODE == 3) {
+            keys[out0 + s] = ~(KeyT)0;
+            if (u1) reinterpret_cast<uint32_t *>(u1)[out0 + s] = (uint32_t)arc;
+        }
+    };
+    auto emit = [&](uint32_t s, int64_t arc, int32_t pu, int32_t pv) {
         if (MODE == 0) {
             u1[out0 + s] = pu;
             v1[out0 + s] = pv;
         } else if (MODE == 2) {
             const uint32_t x = (uint32_t)min(pu, pv), y = (uint32_t)max(pu, pv);
-            atomicAdd(reinterpret_cast<uint32_t *>(keys) + (size_t)x * (uint32_t)nb_smem + y, 1u);
+            const size_t at = (size_t)x * (uint32_t)nb_smem + y;
+            if (sizeof(KeyT) == 8)   // downsampled: weights, 2^-32 fixed point
+                atomicAdd(reinterpret_cast<unsigned long long *>(keys) + at, (unsigned long long)A.ds_w[arc]);
+            else
+                atomicAdd(reinterpret_cast<uint32_t *>(keys) + at, 1u);
         } else if (MODE == 3) {
             const uint32_t x = (uint32_t)min(pu, pv), y = (uint32_t)max(pu, pv);
             keys[out0 + s] = ((KeyT)x << A.B) | (KeyT)y;
+            if (u1) reinterpret_cast<uint32_t *>(u1)[out0 + s] = (uint32_t)arc;   // the draw's arc
         } else {
             const uint32_t x = (uint32_t)min(pu, pv), y = (uint32_t)max(pu, pv);
             const KeyT key = ((KeyT)x << A.B) | (KeyT)y;
@@ -421,10 +443,15 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
             uint32_t w3 = 0;
             if (idx < cn) {
                 int lo;
-                uint32_t j;
+                uint32_t j, coin;
                 locate(cb + idx, lo, j);
                 s_lo[idx] = (uint16_t)lo;
-                draw_head(A, s_rlut, s_rmagic, a0 + lo, j, &r, &sg, &w3);
+                draw_head(A, s_rlut, s_rmagic, a0 + lo, j, &r, &sg, &coin, &w3);
+                // edge downsampling (Algorithm 3): the draw walks only if its coin comes up heads
+                if (A.ds_thr && (uint64_t)coin >= __ldg(A.ds_thr + a0 + lo)) {
+                    emit_dropped(cb + idx, a0 + lo);
+                    r = 0;
+                }
             }
             const unsigned grp = __match_any_sync(0xffffffffu, r);
             const int leader = __ffs(grp) - 1;
@@ -489,10 +516,10 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
             StepAll<0>::run(A, d0, d1, max(d0.steps, d1.steps));
             int32_t pu, pv;
             draw_end(d0, &pu, &pv);
-            emit(s0, pu, pv);
+            emit(s0, a0 + lo0, pu, pv);
             if (has1) {
                 draw_end(d1, &pu, &pv);
-                emit(s1, pu, pv);
+                emit(s1, a0 + lo1, pu, pv);
             }
         }
         __syncthreads();
@@ -670,6 +697,50 @@ __device__ __forceinline__ float netmf_value(uint32_t cnt, int64_t dx, int64_t d
     return (float)(log(p) - log(q));
 }
 
+// Eq. 1 entry for a downsampled pair: K = (summed 1/p_e, 2^-32 units) * 2^-32,
+// v = fl(fl(K alpha) / fl(d_x d_y)) in FP64, kept iff v > 1, value log v as
+// float32 (log1p of v - 1 below 2, so small logs keep their relative accuracy).
+__device__ __forceinline__ float netmf_value_w(uint64_t wsum, int64_t dx, int64_t dy, bool diag,
+                                               const NetmfConst &k) {
+    const double K = __dmul_rn(__ull2double_rn(wsum), 2.3283064365386963e-10);   // 2^-32
+    const double p = __dmul_rn(K, diag ? k.a_diag : k.a_off);
+    const double v = __ddiv_rn(p, __dmul_rn((double)dx, (double)dy));
+    if (!(v > 1.0)) return 0.f;
+    return v < 2.0 ? log1pf((float)__dsub_rn(v, 1.0)) : logf((float)v);
+}
+
+// Weighted table -> the float-bits value table (upper triangle).
+__global__ void table_values_w_kernel(const uint64_t *__restrict__ W, uint32_t *__restrict__ T, int64_t ld, int n,
+                                      const int64_t *__restrict__ indptr, NetmfConst kc) {
+    const int x = blockIdx.x;
+    const int64_t dx = __ldg(indptr + x + 1) - __ldg(indptr + x);
+    for (int y = x + threadIdx.x; y < n; y += blockDim.x) {
+        const uint64_t w = W[(size_t)x * ld + y];
+        if (w == 0) continue;
+        const int64_t dy = __ldg(indptr + y + 1) - __ldg(indptr + y);
+        T[(size_t)x * ld + y] = __float_as_uint(netmf_value_w(w, dx, dy, x == y, kc));
+    }
+}
+
+// Per arc u -> v: the coin threshold min(2^32, floor(p 2^32)) and the weight
+// floor(2^32 / p + 1/2) of p = min(1, C (1/d_u + 1/d_v)), each FP64 step one
+// IEEE rounding (Sec. 4.1, degree sampling).
+__global__ void downsample_arcs_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict__ indices,
+                                       int64_t n, double C, uint64_t *__restrict__ thr, uint64_t *__restrict__ w) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a0 = indptr[u], a1 = indptr[u + 1];
+        const double iu = __ddiv_rn(1.0, (double)(a1 - a0));
+        for (int64_t a = a0; a < a1; ++a) {
+            const int32_t v = indices[a];
+            const double iv = __ddiv_rn(1.0, (double)(indptr[v + 1] - indptr[v]));
+            double p = __dmul_rn(C, __dadd_rn(iu, iv));
+            if (p >= 1.0) p = 1.0;
+            thr[a] = p >= 1.0 ? (1ull << 32) : (uint64_t)floor(__dmul_rn(p, 4294967296.0));
+            w[a] = (uint64_t)floor(__dadd_rn(__ddiv_rn(4294967296.0, p), 0.5));
+        }
+    }
+}
+
 __global__ void trunclog_kernel(const int32_t *__restrict__ x, const int32_t *__restrict__ y,
                                 const uint32_t *__restrict__ cnt, int64_t nnz,
                                 const int64_t *__restrict__ indptr, NetmfConst kc,
@@ -782,11 +853,11 @@ __global__ void table_values_kernel(uint32_t *__restrict__ T, int64_t ld, int n,
 }
 
 // Distinct pairs per upper-triangle row (for the counts output).
-__global__ void table_row_nnz_kernel(const uint32_t *__restrict__ T, int64_t ld, int n,
-                                     uint32_t *__restrict__ cnt) {
+template <typename E>
+__global__ void table_row_nnz_kernel(const E *__restrict__ T, int64_t ld, int n, uint32_t *__restrict__ cnt) {
     __shared__ uint32_t red[32];
     const int x = blockIdx.x;
-    const uint32_t *row = T + (size_t)x * ld;
+    const E *row = T + (size_t)x * ld;
     uint32_t c = 0;
     for (int y = x + threadIdx.x; y < n; y += blockDim.x) c += row[y] != 0;
 #pragma unroll
@@ -802,20 +873,20 @@ __global__ void table_row_nnz_kernel(const uint32_t *__restrict__ T, int64_t ld,
 
 // (x, y, count) of the upper triangle in (x, y) order: one CTA per row, the
 // row is walked in chunks of blockDim with a block-wide ballot scan.
-__global__ void table_compact_kernel(const uint32_t *__restrict__ T, int64_t ld, int n,
-                                     const int64_t *__restrict__ off, int32_t *__restrict__ ox,
-                                     int32_t *__restrict__ oy, uint32_t *__restrict__ oc) {
+template <typename E>
+__global__ void table_compact_kernel(const E *__restrict__ T, int64_t ld, int n, const int64_t *__restrict__ off,
+                                     int32_t *__restrict__ ox, int32_t *__restrict__ oy, E *__restrict__ oc) {
     __shared__ uint32_t warp_cnt[32];
     __shared__ uint32_t base_s;
     const int x = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const uint32_t *row = T + (size_t)x * ld;
+    const E *row = T + (size_t)x * ld;
     if (threadIdx.x == 0) base_s = 0;
     __syncthreads();
     const int64_t o = off[x];
     for (int y0 = x; y0 < n; y0 += blockDim.x) {
         const int y = y0 + threadIdx.x;
-        const uint32_t c = y < n ? row[y] : 0u;
+        const E c = y < n ? row[y] : (E)0;
         const unsigned bal = __ballot_sync(0xffffffffu, c != 0);
         if (lane == 0) warp_cnt[warp] = __popc(bal);
         __syncthreads();
@@ -975,8 +1046,10 @@ __global__ void degree_kernel(const int64_t *__restrict__ indptr, int64_t n, uin
 
 // Eq. 1 value of every unique pair, written over its count (float bits; 0 =
 // dropped), and per tile the number of kept and of kept off-diagonal pairs.
+// With edge downsampling the value comes from the pair's summed weight wsum.
 __global__ void __launch_bounds__(kPathThreads) path_value_kernel(const uint64_t *__restrict__ uk,
-                                                                  uint32_t *__restrict__ cnt_val, int64_t U, int B,
+                                                                  uint32_t *__restrict__ cnt_val,
+                                                                  const uint64_t *__restrict__ wsum, int64_t U, int B,
                                                                   const uint32_t *__restrict__ deg, NetmfConst kc,
                                                                   uint32_t *__restrict__ tile_kept,
                                                                   uint32_t *__restrict__ tile_mir) {
@@ -990,7 +1063,8 @@ __global__ void __launch_bounds__(kPathThreads) path_value_kernel(const uint64_t
         if (u >= U) break;
         const uint64_t k = uk[u];
         const uint32_t x = (uint32_t)(k >> B), y = (uint32_t)(k & ((1ull << B) - 1ull));
-        const float v = netmf_value(cnt_val[u], __ldg(deg + x), __ldg(deg + y), x == y, kc);
+        const float v = wsum ? netmf_value_w(wsum[u], __ldg(deg + x), __ldg(deg + y), x == y, kc)
+                             : netmf_value(cnt_val[u], __ldg(deg + x), __ldg(deg + y), x == y, kc);
         cnt_val[u] = __float_as_uint(v);
         if (v > 0.f) {
             ++ck;
@@ -1145,6 +1219,8 @@ WalkArgs make_walk_args(const GraphView &g, const SamplerSpec &sp) {
     for (int i = 0; i + 1 < sp.T; ++i)
         if (sp.thr[i] < (1ull << 32)) A.thr32[A.T_eff++] = (uint32_t)sp.thr[i];
     for (int i = A.T_eff; i < 16; ++i) A.thr32[i] = 0xFFFFFFFFu;
+    A.ds_thr = nullptr;
+    A.ds_w = nullptr;
     A.base_magic = sp.base > 0 ? (~0ull) / sp.base + 1ull : 0ull;
     A.rmagic[0] = 0;
     for (int r = 1; r <= 16; ++r) A.rmagic[r] = (~0ull) / (uint64_t)r + 1ull;
@@ -1169,6 +1245,21 @@ int attach_vinfo(Workspace &ws, const GraphView &g, WalkArgs *A, cudaStream_t st
         LNE_LAUNCH_CHECK();
     }
     A->arcrec = ar;
+    return 0;
+}
+
+// Edge downsampling's per-arc coin thresholds and weights (when C > 0).
+int attach_downsample(Workspace &ws, const GraphView &g, const SamplerSpec &sp, WalkArgs *A, cudaStream_t st) {
+    if (!(sp.ds_C > 0.0)) return 0;
+    uint64_t *thr = nullptr, *w = nullptr;
+    LNE_TRY(ws.get("walk.ds_thr", (size_t)std::max<int64_t>(g.nnz, 1), &thr));
+    LNE_TRY(ws.get("walk.ds_w", (size_t)std::max<int64_t>(g.nnz, 1), &w));
+    LNE_TRACE("downsample_arcs", st);
+    downsample_arcs_kernel<<<(unsigned)std::min<int64_t>(ceil_div(g.n, 256), 152 * 8), 256, 0, st>>>(
+        g.indptr, g.indices, g.n, sp.ds_C, thr, w);
+    LNE_LAUNCH_CHECK();
+    A->ds_thr = thr;
+    A->ds_w = w;
     return 0;
 }
 
@@ -1272,6 +1363,7 @@ int sample_pairs(Workspace &ws, const GraphView &g, const SamplerSpec &sp, int64
     if (a0 == a1) return 0;
     WalkArgs A = make_walk_args(g, sp);
     LNE_TRY(attach_vinfo(ws, g, &A, st));
+    LNE_TRY(attach_downsample(ws, g, sp, &A, st));
     const int tile_arcs = choose_tile_arcs(a1 - a0, (double)sp.base + 0.5);
     int64_t *tile_off = nullptr;
     int64_t total = 0;
@@ -1465,7 +1557,8 @@ int bucket_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResu
 namespace {
 
 struct Table {
-    uint32_t *T = nullptr;
+    uint32_t *T = nullptr;    // counts, then the float bits of the Eq. 1 values
+    uint64_t *W = nullptr;    // summed weights (edge downsampling only)
     int64_t ld = 0;
     int nt = 0;
 };
@@ -1474,11 +1567,16 @@ struct Table {
 
 // Samples of every arc as 64-bit keys, sorted, as unique keys with counts.
 // On return the unique keys are in *uk ("sort.k0" or "sort.k1"), counts in
-// "sort.cnt"; the other key buffer and the run starts are released.
+// "sort.cnt"; the other key buffer and the run starts are released. With edge
+// downsampling each key carries its arc, a dropped draw's key is all ones
+// (sorted past every pair: the sort takes one more bit when n = 2^B, where the
+// all-ones pair of B-bit halves is a real vertex pair), and *w gets the summed
+// weights ("sort.w"); "sort.cnt" is then only sized for the values.
 struct SortRaw {
     int64_t total = 0, U = 0;
     uint64_t *uk = nullptr;
     uint32_t *cnt = nullptr;
+    uint64_t *w = nullptr;
     const char *uk_name = nullptr, *spare_name = nullptr;
 };
 
@@ -1486,6 +1584,12 @@ int sort_raw(Workspace &ws, const GraphView &g, const SamplerSpec &sp, SortRaw *
     if (2 * sp.B > 64) return fail(LNE_ERR_UNSUPPORTED, "pair keys need 2 ceil(log2 n) <= 64 bits");
     WalkArgs A = make_walk_args(g, sp);
     LNE_TRY(attach_vinfo(ws, g, &A, st));
+    LNE_TRY(attach_downsample(ws, g, sp, &A, st));
+    const bool ds = A.ds_thr != nullptr;
+    const int bits = 2 * sp.B + ((ds && ((int64_t)1 << sp.B) == g.n) ? 1 : 0);
+    if (bits > 64) return fail(LNE_ERR_UNSUPPORTED, "downsampled pair keys need 2 ceil(log2 n) + 1 <= 64 bits");
+    if (ds && g.nnz > (int64_t)UINT32_MAX)
+        return fail(LNE_ERR_UNSUPPORTED, "edge downsampling on the sort path needs fewer than 2^32 arcs");
     const int tile_arcs = choose_tile_arcs(g.nnz, (double)sp.base + 0.5);
     int64_t *tile_off = nullptr;
     int64_t total = 0;
@@ -1494,21 +1598,40 @@ int sort_raw(Workspace &ws, const GraphView &g, const SamplerSpec &sp, SortRaw *
     uint64_t *k0 = nullptr, *k1 = nullptr;
     LNE_TRY(ws.get("sort.k0", (size_t)std::max<int64_t>(total, 1), &k0));
     LNE_TRY(ws.get("sort.k1", (size_t)std::max<int64_t>(total, 1), &k1));
+    uint32_t *arc0 = nullptr, *arc1 = nullptr;
+    if (ds) {
+        LNE_TRY(ws.get("sort.a0", (size_t)std::max<int64_t>(total, 1), &arc0));
+        LNE_TRY(ws.get("sort.a1", (size_t)std::max<int64_t>(total, 1), &arc1));
+    }
     const int64_t ntiles = ceil_div(g.nnz, tile_arcs);
     const int smem = walk_smem_bytes(tile_arcs, 0);
     LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint64_t, 3>));
     {
         LNE_TRACE("walk_keys", st);
         walk_emit_kernel<uint64_t, 3><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
-            A, 0, g.nnz, tile_arcs, tile_off, k0, nullptr, nullptr, nullptr, 0);
+            A, 0, g.nnz, tile_arcs, tile_off, k0, reinterpret_cast<int32_t *>(arc0), nullptr, nullptr, 0);
         LNE_LAUNCH_CHECK();
     }
     bool in_alt = false;
-    LNE_TRY(radix_sort_u64(ws, k0, k1, nullptr, nullptr, total, 2 * sp.B, &in_alt, st));
+    LNE_TRY(radix_sort_u64(ws, k0, k1, arc0, arc1, total, bits, &in_alt, st));
     uint64_t *sorted = in_alt ? k1 : k0, *spare = in_alt ? k0 : k1;
     ws.release("sort.offs");
-    LNE_TRY(ws.get("sort.cnt", (size_t)std::max<int64_t>(total, 1), &R->cnt));
-    LNE_TRY(run_length(ws, sorted, total, spare, R->cnt, &R->U, st));
+    if (ds) {
+        LNE_TRY(ws.get("sort.w", (size_t)std::max<int64_t>(total, 1), &R->w));
+        LNE_TRY(run_length_weighted(ws, sorted, in_alt ? arc1 : arc0, A.ds_w, total, spare, R->w, &R->U, st));
+        ws.release("sort.a0");
+        ws.release("sort.a1");
+        if (R->U > 0) {   // the dropped draws form the last run
+            uint64_t last = 0;
+            LNE_CUDA_TRY(cudaMemcpyAsync(&last, spare + R->U - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+            LNE_CUDA_TRY(cudaStreamSynchronize(st));
+            if (last == ~0ull) --R->U;
+        }
+        LNE_TRY(ws.get("sort.cnt", (size_t)std::max<int64_t>(R->U, 1), &R->cnt));
+    } else {
+        LNE_TRY(ws.get("sort.cnt", (size_t)std::max<int64_t>(total, 1), &R->cnt));
+        LNE_TRY(run_length(ws, sorted, total, spare, R->cnt, &R->U, st));
+    }
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
     R->uk = spare;
     R->uk_name = in_alt ? "sort.k0" : "sort.k1";
@@ -1518,7 +1641,8 @@ int sort_raw(Workspace &ws, const GraphView &g, const SamplerSpec &sp, SortRaw *
 }
 
 void sort_release(Workspace &ws) {
-    for (const char *n : {"sort.k0", "sort.k1", "sort.cnt", "sort.start", "sort.offs", "sort.mk", "sort.mv",
+    for (const char *n : {"sort.k0", "sort.k1", "sort.cnt", "sort.w", "sort.a0", "sort.a1", "sort.offs", "sort.mk",
+                          "sort.mv",
                           "path.dcol", "path.dval", "path.tk", "path.tm", "path.ko", "path.mo", "path.deg",
                           "path.dlen", "path.rowlen", "path.dstart", "path.first", "path.end"})
         ws.release(n);
@@ -1530,13 +1654,17 @@ int sort_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Counts
     const int64_t u = R.U;
     LNE_TRY(ws.get("counts.x", (size_t)std::max<int64_t>(u, 1), &out->x));
     LNE_TRY(ws.get("counts.y", (size_t)std::max<int64_t>(u, 1), &out->y));
-    LNE_TRY(ws.get("counts.cnt", (size_t)std::max<int64_t>(u, 1), &out->cnt));
+    if (R.w) LNE_TRY(ws.get("counts.w", (size_t)std::max<int64_t>(u, 1), &out->weight));
+    else LNE_TRY(ws.get("counts.cnt", (size_t)std::max<int64_t>(u, 1), &out->cnt));
     if (u > 0) {
         LNE_TRACE("decode_keys", st);
         decode_keys_kernel<<<(unsigned)std::min<int64_t>(ceil_div(u, 256), 152 * 16), 256, 0, st>>>(
             R.uk, u, sp.B, out->x, out->y);
         LNE_LAUNCH_CHECK();
-        LNE_CUDA_TRY(cudaMemcpyAsync(out->cnt, R.cnt, sizeof(uint32_t) * u, cudaMemcpyDeviceToDevice, st));
+        if (R.w)
+            LNE_CUDA_TRY(cudaMemcpyAsync(out->weight, R.w, sizeof(uint64_t) * u, cudaMemcpyDeviceToDevice, st));
+        else
+            LNE_CUDA_TRY(cudaMemcpyAsync(out->cnt, R.cnt, sizeof(uint32_t) * u, cudaMemcpyDeviceToDevice, st));
     }
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
     sort_release(ws);
@@ -1577,8 +1705,8 @@ int sort_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult
         degree_kernel<<<egrid, 256, 0, st>>>(g.indptr, n, deg);
         LNE_LAUNCH_CHECK();
         // values overwrite the counts (the counts are not needed afterwards)
-        path_value_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, U, sp.B, deg, netmf_const(sp),
-                                                                    tk, tm);
+        path_value_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, R.w, U, sp.B, deg,
+                                                                    netmf_const(sp), tk, tm);
         LNE_LAUNCH_CHECK();
     }
     LNE_TRY(scan_exclusive_u32_to_i64(tk, ko, ntiles, st));
@@ -1671,13 +1799,22 @@ int sample_table(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Table
     LNE_CUDA_TRY(cudaMemsetAsync(tb->T, 0, sizeof(uint32_t) * (size_t)(ld * ld), st));
     WalkArgs A = make_walk_args(g, sp);
     LNE_TRY(attach_vinfo(ws, g, &A, st));
+    LNE_TRY(attach_downsample(ws, g, sp, &A, st));
     const int tile_arcs = choose_tile_arcs(g.nnz, (double)sp.base + 0.5);
     const int64_t ntiles = ceil_div(g.nnz, tile_arcs);
     const int smem = walk_smem_bytes(tile_arcs, 0);
-    LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint32_t, 2>));
     LNE_TRACE("walk_count", st);
-    walk_emit_kernel<uint32_t, 2><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
-        A, 0, g.nnz, tile_arcs, nullptr, tb->T, nullptr, nullptr, nullptr, (int)ld);
+    if (A.ds_thr) {   // downsampled: 64-bit weight sums
+        LNE_TRY(ws.get("table.W", (size_t)(ld * ld), &tb->W));
+        LNE_CUDA_TRY(cudaMemsetAsync(tb->W, 0, sizeof(uint64_t) * (size_t)(ld * ld), st));
+        LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint64_t, 2>));
+        walk_emit_kernel<uint64_t, 2><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
+            A, 0, g.nnz, tile_arcs, nullptr, tb->W, nullptr, nullptr, nullptr, (int)ld);
+    } else {
+        LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint32_t, 2>));
+        walk_emit_kernel<uint32_t, 2><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
+            A, 0, g.nnz, tile_arcs, nullptr, tb->T, nullptr, nullptr, nullptr, (int)ld);
+    }
     LNE_LAUNCH_CHECK();
     return 0;
 }
@@ -1698,7 +1835,8 @@ int table_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Count
     LNE_TRY(ws.get("table.rowoff", (size_t)g.n + 1, &off));
     {
         LNE_TRACE("table_row_nnz", st);
-        table_row_nnz_kernel<<<(unsigned)g.n, 256, 0, st>>>(tb.T, tb.ld, (int)g.n, rc);
+        if (tb.W) table_row_nnz_kernel<uint64_t><<<(unsigned)g.n, 256, 0, st>>>(tb.W, tb.ld, (int)g.n, rc);
+        else table_row_nnz_kernel<uint32_t><<<(unsigned)g.n, 256, 0, st>>>(tb.T, tb.ld, (int)g.n, rc);
         LNE_LAUNCH_CHECK();
     }
     LNE_TRY(scan_exclusive_u32_to_i64(rc, off, g.n, st));
@@ -1707,10 +1845,17 @@ int table_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Count
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
     LNE_TRY(ws.get("counts.x", (size_t)std::max<int64_t>(nnz, 1), &out->x));
     LNE_TRY(ws.get("counts.y", (size_t)std::max<int64_t>(nnz, 1), &out->y));
-    LNE_TRY(ws.get("counts.cnt", (size_t)std::max<int64_t>(nnz, 1), &out->cnt));
     {
         LNE_TRACE("table_compact", st);
-        table_compact_kernel<<<(unsigned)g.n, 256, 0, st>>>(tb.T, tb.ld, (int)g.n, off, out->x, out->y, out->cnt);
+        if (tb.W) {
+            LNE_TRY(ws.get("counts.w", (size_t)std::max<int64_t>(nnz, 1), &out->weight));
+            table_compact_kernel<uint64_t><<<(unsigned)g.n, 256, 0, st>>>(tb.W, tb.ld, (int)g.n, off, out->x,
+                                                                          out->y, out->weight);
+        } else {
+            LNE_TRY(ws.get("counts.cnt", (size_t)std::max<int64_t>(nnz, 1), &out->cnt));
+            table_compact_kernel<uint32_t><<<(unsigned)g.n, 256, 0, st>>>(tb.T, tb.ld, (int)g.n, off, out->x,
+                                                                          out->y, out->cnt);
+        }
         LNE_LAUNCH_CHECK();
     }
     out->nnz = nnz;
@@ -1724,7 +1869,8 @@ int table_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResul
     const int n = (int)g.n;
     {
         LNE_TRACE("table_values", st);
-        table_values_kernel<<<(unsigned)n, 256, 0, st>>>(tb.T, tb.ld, n, g.indptr, netmf_const(sp));
+        if (tb.W) table_values_w_kernel<<<(unsigned)n, 256, 0, st>>>(tb.W, tb.T, tb.ld, n, g.indptr, netmf_const(sp));
+        else table_values_kernel<<<(unsigned)n, 256, 0, st>>>(tb.T, tb.ld, n, g.indptr, netmf_const(sp));
         LNE_LAUNCH_CHECK();
     }
     uint32_t *rowtile = nullptr, *rowcnt = nullptr;
@@ -1779,6 +1925,8 @@ CsrView product_view(const CsrResult &M, int dense_mode) {
 
 int sparsifier_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out,
                       cudaStream_t st) {
+    if (sp.ds_C > 0.0 && !use_table(g, sp) && sp.aggregation == LNE_AGG_BUCKET)
+        return fail(LNE_ERR_UNSUPPORTED, "edge downsampling needs the table or the sort aggregation");
     if (use_table(g, sp)) LNE_TRY(table_counts(ws, g, sp, out, st));
     else if (sp.aggregation == LNE_AGG_BUCKET) LNE_TRY(bucket_counts(ws, g, sp, out, st));
     else LNE_TRY(sort_counts(ws, g, sp, out, st));
@@ -1787,6 +1935,8 @@ int sparsifier_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
 }
 
 int sparsifier_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out, cudaStream_t st) {
+    if (sp.ds_C > 0.0 && !use_table(g, sp) && sp.aggregation == LNE_AGG_BUCKET)
+        return fail(LNE_ERR_UNSUPPORTED, "edge downsampling needs the table or the sort aggregation");
     if (use_table(g, sp)) return table_csr(ws, g, sp, out, st);
     if (sp.aggregation == LNE_AGG_BUCKET) return bucket_csr(ws, g, sp, out, st);
     return sort_csr(ws, g, sp, out, st);

@@ -13,7 +13,8 @@
 //            each digit's run contiguously to its global offset.
 // run_length: unique keys of a sorted array and their multiplicities (tile
 // flag counts, one scan over tiles, block scans inside tiles, each run's
-// length counted by the thread owning its first key).
+// length counted by the thread owning its first key); run_length_weighted sums
+// a per-arc 64-bit weight over each run instead (edge downsampling).
 #include "common.cuh"
 #include "runtime.h"
 
@@ -154,11 +155,16 @@ __global__ void __launch_bounds__(kSortThreads) rle_count_kernel(const uint64_t 
 
 // Unique keys and their run lengths (thread-blocked items, block scan); the
 // thread that owns a run's first key walks forward to the run's end, so every
-// key is read about twice in all and no start index array is needed.
+// key is read about twice in all and no start index array is needed. WEIGHTED:
+// instead of the length, the 64-bit sum of w[arc] over the run's payloads.
+template <bool WEIGHTED>
 __global__ void __launch_bounds__(kSortThreads) rle_write_kernel(const uint64_t *__restrict__ keys, int64_t n,
                                                                  const int64_t *__restrict__ tile_off,
                                                                  uint64_t *__restrict__ ukeys,
-                                                                 uint32_t *__restrict__ counts) {
+                                                                 uint32_t *__restrict__ counts,
+                                                                 const uint32_t *__restrict__ arcs,
+                                                                 const uint64_t *__restrict__ w,
+                                                                 uint64_t *__restrict__ wsum) {
     __shared__ int64_t s_warp[kSortWarps];
     const int tid = threadIdx.x;
     const int64_t i0 = (int64_t)blockIdx.x * kSortTile + (int64_t)tid * kSortItems;
@@ -177,9 +183,15 @@ __global__ void __launch_bounds__(kSortThreads) rle_write_kernel(const uint64_t 
             const int64_t g = i0 + j;
             const uint64_t k = keys[g];
             int64_t e = g + 1;
-            while (e < n && keys[e] == k) ++e;
+            if (WEIGHTED) {
+                uint64_t sum = __ldg(w + arcs[g]);
+                for (; e < n && keys[e] == k; ++e) sum += __ldg(w + arcs[e]);
+                wsum[pos] = sum;
+            } else {
+                while (e < n && keys[e] == k) ++e;
+                counts[pos] = (uint32_t)(e - g);
+            }
             ukeys[pos] = k;
-            counts[pos] = (uint32_t)(e - g);
             ++pos;
         }
 }
@@ -217,8 +229,10 @@ int radix_sort_u64(Workspace &ws, uint64_t *keys, uint64_t *keys_alt, uint32_t *
     return 0;
 }
 
-int run_length(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t *ukeys, uint32_t *counts,
-               int64_t *nunique, cudaStream_t st) {
+namespace {
+
+int run_length_impl(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t *ukeys, uint32_t *counts,
+                    const uint32_t *arcs, const uint64_t *w, uint64_t *wsum, int64_t *nunique, cudaStream_t st) {
     *nunique = 0;
     if (n <= 0) return 0;
     const int64_t ntiles = ceil_div(n, (int64_t)kSortTile);
@@ -230,13 +244,30 @@ int run_length(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t *ukeys, 
     rle_count_kernel<<<(unsigned)ntiles, kSortThreads, 0, st>>>(keys, n, tc);
     LNE_LAUNCH_CHECK();
     LNE_TRY(scan_exclusive_u32_to_i64(tc, toff, ntiles, st));
-    rle_write_kernel<<<(unsigned)ntiles, kSortThreads, 0, st>>>(keys, n, toff, ukeys, counts);
+    if (wsum)
+        rle_write_kernel<true><<<(unsigned)ntiles, kSortThreads, 0, st>>>(keys, n, toff, ukeys, nullptr, arcs, w,
+                                                                           wsum);
+    else
+        rle_write_kernel<false><<<(unsigned)ntiles, kSortThreads, 0, st>>>(keys, n, toff, ukeys, counts, nullptr,
+                                                                            nullptr, nullptr);
     LNE_LAUNCH_CHECK();
     int64_t u = 0;
     LNE_CUDA_TRY(cudaMemcpyAsync(&u, toff + ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
     *nunique = u;
     return 0;
+}
+
+}  // namespace
+
+int run_length(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t *ukeys, uint32_t *counts,
+               int64_t *nunique, cudaStream_t st) {
+    return run_length_impl(ws, keys, n, ukeys, counts, nullptr, nullptr, nullptr, nunique, st);
+}
+
+int run_length_weighted(Workspace &ws, const uint64_t *keys, const uint32_t *arcs, const uint64_t *w, int64_t n,
+                        uint64_t *ukeys, uint64_t *wsum, int64_t *nunique, cudaStream_t st) {
+    return run_length_impl(ws, keys, n, ukeys, nullptr, arcs, w, wsum, nunique, st);
 }
 
 }  // namespace lne

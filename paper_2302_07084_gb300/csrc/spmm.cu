@@ -1,5 +1,5 @@
 // Sparse x dense products of the hot path:
-//   * Y = M X with the weighted sparsifier M (Algorithm 4, lines 3 and 5);
+//   * Y = M X with the weighted sparsifier M (Algorithm 4);
 //   * the propagation products with the unweighted graph A, where the row
 //     scale 1/deg(i) (D^-1 A) and the Chebyshev recurrence of Sec. 3.3 are
 //     fused into the epilogue:  out = alpha * rs_i (A X)_i + b1 E1 + b2 E2 + b3 E3,

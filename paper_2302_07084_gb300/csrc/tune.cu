@@ -37,7 +37,7 @@ namespace {
 
 bool same_rsvd_inputs(const lne_params &a, const lne_params &b, int osa, int osb) {
     if (a.T != b.T || a.samples != b.samples || a.b != b.b || a.d != b.d || osa != osb || a.q != b.q ||
-        a.seed != b.seed)
+        a.seed != b.seed || a.downsample_C != b.downsample_C)
         return false;
     for (int i = 0; i < a.T; ++i)
         if (a.s[i] != b.s[i]) return false;
@@ -130,6 +130,7 @@ int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregati
         SamplerSpec sp;
         LNE_TRY(make_sampler_spec(g, p.T, p.s, p.samples, p.b, p.seed, &sp));
         sp.aggregation = aggregation;
+        sp.ds_C = p.downsample_C;
         CsrResult M;
         LNE_TRY(sparsifier_csr(ws, g, sp, &M, st));
         LNE_TRY(rsvd(ws, product_view(M, dense_mode), d, os_of(p), p.q, p.seed, p.precision, nullptr, nullptr,

@@ -61,7 +61,8 @@ class _Params(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int32), ("s", ctypes.POINTER(ctypes.c_double)), ("samples", ctypes.c_double),
                 ("b", ctypes.c_double), ("d", ctypes.c_int32), ("oversample", ctypes.c_int32),
                 ("q", ctypes.c_int32), ("k", ctypes.c_int32), ("theta", ctypes.c_double),
-                ("mu", ctypes.c_double), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32)]
+                ("mu", ctypes.c_double), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
+                ("downsample_C", ctypes.c_double)]
 
 
 class _Csr(ctypes.Structure):
@@ -76,7 +77,7 @@ class _TraceEntry(ctypes.Structure):
 
 class _Counts(ctypes.Structure):
     _fields_ = [("nnz", ctypes.c_int64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
-                ("count", ctypes.c_void_p), ("total_samples", ctypes.c_int64)]
+                ("count", ctypes.c_void_p), ("total_samples", ctypes.c_int64), ("weight", ctypes.c_void_p)]
 
 
 _lib = None
@@ -150,6 +151,7 @@ class Params:
     mu: float = 0.2
     seed: int = 0
     precision: int = PREC_FP32
+    downsample_C: float = 0.0     # edge downsampling constant C (0 = off)
 
     def _c(self):
         s = np.ascontiguousarray(np.asarray(self.s, dtype=np.float64))
@@ -157,7 +159,7 @@ class Params:
         p = _Params(int(self.T), ctypes.cast(arr, ctypes.POINTER(ctypes.c_double)), float(self.samples),
                     float(self.b), int(self.d), int(self.oversample), int(self.q), int(self.k),
                     float(self.theta), float(self.mu), int(self.seed) & 0xFFFFFFFFFFFFFFFF,
-                    int(self.precision))
+                    int(self.precision), float(self.downsample_C))
         return p, arr
 
 
@@ -304,10 +306,16 @@ class Context:
         pc, keep = p._c()
         self._check(self.lib.lne_sparsifier_counts(self.h, ctypes.byref(gc), ctypes.byref(pc), ctypes.byref(out),
                                                    _stream()))
-        return dict(x=_own(out.x, out.nnz, "<i4", torch.int32, self.dev),
-                    y=_own(out.y, out.nnz, "<i4", torch.int32, self.dev),
-                    count=_own(out.count, out.nnz, "<u4", torch.uint32, self.dev),
-                    total_samples=int(out.total_samples))
+        # with edge downsampling `weight` (uint64 bit patterns held in int64)
+        # replaces `count`
+        res = dict(x=_own(out.x, out.nnz, "<i4", torch.int32, self.dev),
+                   y=_own(out.y, out.nnz, "<i4", torch.int32, self.dev),
+                   total_samples=int(out.total_samples))
+        if out.weight:
+            res["weight"] = _own(out.weight, out.nnz, "<i8", torch.int64, self.dev)
+        else:
+            res["count"] = _own(out.count, out.nnz, "<u4", torch.uint32, self.dev)
+        return res
 
     def sparsifier_csr(self, g: DeviceGraph, p: Params, copy: bool = True):
         """The trunc_log sparsifier as a CSR dict. copy=False returns views of

@@ -3,7 +3,7 @@
 * eigSVD (Algorithm 2) recovers planted singular triplets.
 * Fast randomized SVD (Algorithm 4) recovers a planted spectrum with a gap,
   and its mean error respects the Eq. 2 bound.
-* Gaussian sketch moments and normality (Algorithm 4, line 2).
+* Gaussian sketch moments and normality (Algorithm 4).
 * The Chebyshev coefficients expand exp(-theta y) (Bessel generating function).
 * Spectral propagation equals the filter evaluated on the eigenvalues of the
   normalised Laplacian (Sec. 3.3), computed independently from a dense

@@ -232,7 +232,7 @@ def test_sparsifier_csr_structure():
 
 
 # ----------------------------------------------------------------------------
-# edge downsampling (Sec. 4.1; Algorithm 3, lines 5-9)
+# edge downsampling (Sec. 4.1; Algorithm 3)
 # ----------------------------------------------------------------------------
 
 def _star_path():
