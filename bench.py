@@ -84,12 +84,26 @@ def kernel_model(name, g, params, counts):
     n, m2 = g.n, g.n_arcs
     c = params["d"] + params["oversample"]
     if name in ("walk_count", "walk_emit"):
-        return "alu", walk_ops_per_sample(params) * S, "Gop/s"
+        kept = counts.get("kept_draws", S)
+        # a draw the downsampling coin drops costs its head block and bookkeeping only
+        return "alu", walk_ops_per_sample(params) * kept + 52.0 * (S - kept), "Gop/s"
     if name == "spmm":
         return "fma", 2.0 * counts.get("nnz_M", 0) * c, "GFLOP/s"
     if name == "graph_spmm":
         return "fma", 2.0 * m2 * params["d"], "GFLOP/s"
     return None
+
+
+def expected_kept_draws(g, params):
+    """Expected number of draws that survive edge downsampling: sum over arcs of
+    (S / 2m) p_e, p_e = min(1, C (1/d_u + 1/d_v)) (Sec. 4.1); S without it."""
+    C = params.get("downsample_C", 0.0)
+    if not C:
+        return params["samples"]
+    deg = np.diff(g.indptr).astype(np.float64)
+    src = np.repeat(np.arange(g.n), np.diff(g.indptr))
+    pe = np.minimum(1.0, C * (1.0 / deg[src] + 1.0 / deg[g.indices]))
+    return float(params["samples"] / g.n_arcs * pe.sum())
 
 
 def alu_peak_gops(sm_mhz):
@@ -252,6 +266,8 @@ def run_ours(args):
     g, params = workload()
     params = dict(params)
     params["seed"] = params["seed"] + rank
+    if args.downsample:
+        params["downsample_C"] = lne.default_downsample_C(g.n)
     P = lne.Params(**params)
     ctx = lne.Context(local)
     dg = lne.DeviceGraph(g.indptr, g.indices, device=dev)
@@ -269,7 +285,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     counts = ctx.sparsifier_counts(dg, P)
     csr = ctx.sparsifier_csr(dg, P)
-    info = dict(total_samples=counts["total_samples"], nnz_c=int(counts["x"].numel()), nnz_M=int(csr["nnz"]))
+    info = dict(total_samples=counts["total_samples"], nnz_c=int(counts["x"].numel()), nnz_M=int(csr["nnz"]),
+                kept_draws=expected_kept_draws(g, params))
     del counts, csr
     torch.cuda.synchronize()
 
@@ -353,17 +370,19 @@ def run_ours(args):
 
     if rank == 0:
         cpu = None
-        if world == 1 and not args.no_cpu_baseline:
+        if world == 1 and not args.no_cpu_baseline and not args.downsample:
             r = oracle_step(g, params, rep=0)
             cpu = {"value": r["value"], "unit": "samples/s", "cores": r["cores"], "kind": "oracle",
                    "sample": r["sample"]}
         line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "samples": params["samples"], "T": 10,
+                "config": {"workload": WORKLOAD + ("_downsampled_C=ln_n" if args.downsample else ""),
+                           "n": g.n, "m": g.m, "samples": params["samples"], "T": 10,
                            "d": 128, "q": 1, "k": 10, "l2": "flushed (256 MB write) between steps",
                            "parallelism": f"replicas{world}", "nnz_pairs": info["nnz_c"],
-                           "nnz_M": info["nnz_M"]},
+                           "nnz_M": info["nnz_M"],
+                           **({"downsample_C": params["downsample_C"]} if args.downsample else {})},
                 "e2e": {"value": world * params["samples"] / (e2e / 1e3), "unit": "samples/s",
                         "h2d_bytes_per_step": int(g.indptr.nbytes + g.indices.astype(np.int32).nbytes),
                         "d2h_bytes_per_step": int(g.n * P.d * 4), "ms_per_step": e2e},
@@ -604,6 +623,8 @@ def main():
                     help="measure tuning throughput on G graphs of the SBM suite instead of the benchmark")
     ap.add_argument("--surrogate", type=int, default=0, metavar="G",
                     help="measure surrogate-guided search after training on G graphs of the SBM suite")
+    ap.add_argument("--downsample", action="store_true",
+                    help="the benchmark with edge downsampling at C = ln n (draws per second; no CPU baseline)")
     ap.add_argument("--large", action="store_true",
                     help="the 10M-vertex BF16 precision run instead of the benchmark (--scale divides its size)")
     args = ap.parse_args()

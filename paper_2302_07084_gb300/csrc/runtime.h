@@ -259,6 +259,8 @@ int radix_sort_u64(Workspace &ws, uint64_t *keys, uint64_t *keys_alt, uint32_t *
 // Unique keys of a sorted array and their multiplicities.
 int run_length(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t *ukeys, uint32_t *counts,
                int64_t *nunique, cudaStream_t st);
+// Number of keys of a sorted array below `key` (synchronises).
+int count_below(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t key, int64_t *count, cudaStream_t st);
 // Unique keys of a sorted array and, per run, the sum of w[arcs[i]] over it.
 int run_length_weighted(Workspace &ws, const uint64_t *keys, const uint32_t *arcs, const uint64_t *w, int64_t n,
                         uint64_t *ukeys, uint64_t *wsum, int64_t *nunique, cudaStream_t st);

@@ -699,14 +699,37 @@ __device__ __forceinline__ float netmf_value(uint32_t cnt, int64_t dx, int64_t d
 
 // Eq. 1 entry for a downsampled pair: K = (summed 1/p_e, 2^-32 units) * 2^-32,
 // v = fl(fl(K alpha) / fl(d_x d_y)) in FP64, kept iff v > 1, value log v as
-// float32 (log1p of v - 1 below 2, so small logs keep their relative accuracy).
+// float32. Fast path as for counts: the 64-bit sum is split into a float pair
+// (kh + kl, exact to 2^-48 relative), D = K alpha - q in FP32 with fmaf, so D
+// carries an error of ~1e-7 |D| + 1e-14 q; when |D| > 1e-5 q its sign is the
+// FP64 decision. Otherwise the exact FP64 rule (no division) decides.
 __device__ __forceinline__ float netmf_value_w(uint64_t wsum, int64_t dx, int64_t dy, bool diag,
                                                const NetmfConst &k) {
+    const int64_t q64 = dx * dy;
+    if (q64 < (1ll << 24)) {
+        const float kh = __ull2float_rn(wsum);
+        // kh is an integer below 2^64 (unless wsum rounds up to 2^64): the
+        // residual wsum - kh is exact in 64-bit arithmetic
+        const float kl = kh < 1.8446744e19f ? (float)(int64_t)(wsum - __float2ull_rn(kh)) : 0.f;
+        const float two_m32 = 2.3283064e-10f;   // 2^-32 exactly
+        const float khs = kh * two_m32, kls = kl * two_m32;
+        const float qf = (float)q64;
+        const float hi = diag ? k.diag_hi : k.off_hi, lo = diag ? k.diag_lo : k.off_lo;
+        const float dq = fmaf(khs, hi, -qf) + fmaf(khs, lo, kls * hi);
+        if (fabsf(dq) > 1e-5f * qf) return dq > 0.f ? log1pf(__fdiv_rn(dq, qf)) : 0.f;
+    }
     const double K = __dmul_rn(__ull2double_rn(wsum), 2.3283064365386963e-10);   // 2^-32
     const double p = __dmul_rn(K, diag ? k.a_diag : k.a_off);
-    const double v = __ddiv_rn(p, __dmul_rn((double)dx, (double)dy));
-    if (!(v > 1.0)) return 0.f;
-    return v < 2.0 ? log1pf((float)__dsub_rn(v, 1.0)) : logf((float)v);
+    const double q = __ll2double_rn(q64);
+    if (!(p > q)) return 0.f;
+    const double q2 = __dmul_rn(2.0, q);
+    if (p < q2) {
+        const double dd = __dsub_rn(p, q);
+        if (!(__dmul_rn(dd, 9007199254740992.0) > q)) return 0.f;
+        return log1pf(__fdiv_rn((float)dd, (float)q));
+    }
+    if (p < 1e30) return logf(__fdiv_rn((float)p, (float)q));
+    return (float)(log(p) - log(q));
 }
 
 // Weighted table -> the float-bits value table (upper triangle).
@@ -724,15 +747,19 @@ __global__ void table_values_w_kernel(const uint64_t *__restrict__ W, uint32_t *
 
 // Per arc u -> v: the coin threshold min(2^32, floor(p 2^32)) and the weight
 // floor(2^32 / p + 1/2) of p = min(1, C (1/d_u + 1/d_v)), each FP64 step one
-// IEEE rounding (Sec. 4.1, degree sampling).
+// IEEE rounding (Sec. 4.1, degree sampling). A warp per source vertex, its
+// lanes over the vertex's arcs (degrees are skewed).
 __global__ void downsample_arcs_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict__ indices,
                                        int64_t n, double C, uint64_t *__restrict__ thr, uint64_t *__restrict__ w) {
-    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
         const int64_t a0 = indptr[u], a1 = indptr[u + 1];
+        if (a1 == a0) continue;
         const double iu = __ddiv_rn(1.0, (double)(a1 - a0));
-        for (int64_t a = a0; a < a1; ++a) {
-            const int32_t v = indices[a];
-            const double iv = __ddiv_rn(1.0, (double)(indptr[v + 1] - indptr[v]));
+        for (int64_t a = a0 + lane; a < a1; a += 32) {
+            const int32_t v = __ldg(indices + a);
+            const double iv = __ddiv_rn(1.0, (double)(__ldg(indptr + v + 1) - __ldg(indptr + v)));
             double p = __dmul_rn(C, __dadd_rn(iu, iv));
             if (p >= 1.0) p = 1.0;
             thr[a] = p >= 1.0 ? (1ull << 32) : (uint64_t)floor(__dmul_rn(p, 4294967296.0));
@@ -1255,7 +1282,8 @@ int attach_downsample(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
     LNE_TRY(ws.get("walk.ds_thr", (size_t)std::max<int64_t>(g.nnz, 1), &thr));
     LNE_TRY(ws.get("walk.ds_w", (size_t)std::max<int64_t>(g.nnz, 1), &w));
     LNE_TRACE("downsample_arcs", st);
-    downsample_arcs_kernel<<<(unsigned)std::min<int64_t>(ceil_div(g.n, 256), 152 * 8), 256, 0, st>>>(
+    downsample_arcs_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g.n, 8), 152 * 16)), 256, 0,
+                             st>>>(
         g.indptr, g.indices, g.n, sp.ds_C, thr, w);
     LNE_LAUNCH_CHECK();
     A->ds_thr = thr;
@@ -1617,16 +1645,13 @@ int sort_raw(Workspace &ws, const GraphView &g, const SamplerSpec &sp, SortRaw *
     uint64_t *sorted = in_alt ? k1 : k0, *spare = in_alt ? k0 : k1;
     ws.release("sort.offs");
     if (ds) {
-        LNE_TRY(ws.get("sort.w", (size_t)std::max<int64_t>(total, 1), &R->w));
-        LNE_TRY(run_length_weighted(ws, sorted, in_alt ? arc1 : arc0, A.ds_w, total, spare, R->w, &R->U, st));
+        // the dropped draws sort last: run lengths over the kept ones only
+        int64_t kept = 0;
+        LNE_TRY(count_below(ws, sorted, total, ~0ull, &kept, st));
+        LNE_TRY(ws.get("sort.w", (size_t)std::max<int64_t>(kept, 1), &R->w));
+        LNE_TRY(run_length_weighted(ws, sorted, in_alt ? arc1 : arc0, A.ds_w, kept, spare, R->w, &R->U, st));
         ws.release("sort.a0");
         ws.release("sort.a1");
-        if (R->U > 0) {   // the dropped draws form the last run
-            uint64_t last = 0;
-            LNE_CUDA_TRY(cudaMemcpyAsync(&last, spare + R->U - 1, sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
-            LNE_CUDA_TRY(cudaStreamSynchronize(st));
-            if (last == ~0ull) --R->U;
-        }
         LNE_TRY(ws.get("sort.cnt", (size_t)std::max<int64_t>(R->U, 1), &R->cnt));
     } else {
         LNE_TRY(ws.get("sort.cnt", (size_t)std::max<int64_t>(total, 1), &R->cnt));
@@ -1641,8 +1666,8 @@ int sort_raw(Workspace &ws, const GraphView &g, const SamplerSpec &sp, SortRaw *
 }
 
 void sort_release(Workspace &ws) {
-    for (const char *n : {"sort.k0", "sort.k1", "sort.cnt", "sort.w", "sort.a0", "sort.a1", "sort.offs", "sort.mk",
-                          "sort.mv",
+    for (const char *n : {"sort.k0", "sort.k1", "sort.cnt", "sort.w", "sort.a0", "sort.a1", "sort.bound", "sort.offs",
+                          "sort.mk", "sort.mv",
                           "path.dcol", "path.dval", "path.tk", "path.tm", "path.ko", "path.mo", "path.deg",
                           "path.dlen", "path.rowlen", "path.dstart", "path.first", "path.end"})
         ws.release(n);

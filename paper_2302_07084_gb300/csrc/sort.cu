@@ -196,7 +196,28 @@ __global__ void __launch_bounds__(kSortThreads) rle_write_kernel(const uint64_t 
         }
 }
 
+// Number of keys below `key` in a sorted array (one thread, binary search).
+__global__ void lower_bound_kernel(const uint64_t *__restrict__ keys, int64_t n, uint64_t key,
+                                   int64_t *__restrict__ out) {
+    int64_t lo = 0, hi = n;   // keys[0, lo) < key <= keys[hi, n)
+    while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (keys[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    *out = lo;
+}
+
 }  // namespace
+
+int count_below(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t key, int64_t *count, cudaStream_t st) {
+    int64_t *d = nullptr;
+    LNE_TRY(ws.get("sort.bound", 1, &d));
+    lower_bound_kernel<<<1, 1, 0, st>>>(keys, n, key, d);
+    LNE_LAUNCH_CHECK();
+    LNE_CUDA_TRY(cudaMemcpyAsync(count, d, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    return 0;
+}
 
 int radix_sort_u64(Workspace &ws, uint64_t *keys, uint64_t *keys_alt, uint32_t *vals, uint32_t *vals_alt,
                    int64_t n, int bits, bool *in_alt, cudaStream_t st) {

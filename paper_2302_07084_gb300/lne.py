@@ -210,6 +210,11 @@ def _own(ptr, n, typestr, dtype, device):
     return torch.as_tensor(_DevView(ptr, n, typestr), device=device).clone()
 
 
+def default_downsample_C(n: int) -> float:
+    """The downsampling constant the paper takes, C = ln n (Sec. 4.1)."""
+    return float(np.log(max(int(n), 2)))
+
+
 def svd_small_noalloc(R: torch.Tensor, U: torch.Tensor, sigma: torch.Tensor) -> int:
     """lne_svd_small_noalloc: writes U (c x c) and sigma (c) of the FP64 matrix R
     without allocating device memory; returns the library's status code."""

@@ -10,6 +10,8 @@ with weight 1/p_e, held as floor(2^32 / p_e + 1/2) in 2^-32 units:
   key bit; the bucket aggregation refuses downsampling;
 * the trunc_log CSR: structure and keep decisions exact, values within 1e-6;
 * C so large that p_e = 1 everywhere reproduces the plain sparsifier;
+* keep decisions exact for entries placed on v = 1 to the last bits (also
+  without downsampling);
 * the whole method (lne_embed) follows the oracle's downsampled embedding.
 """
 import numpy as np
@@ -159,3 +161,72 @@ def test_embed_downsampled_sbm_small(ctx):
     ref = oracle.embed(g.indptr, g.indices, 10, p.s, p.samples, 32, 1, 10, 0.5, 0.2, 1, C=2.0)
     X = to_np(ctx.embed(lne.DeviceGraph.from_graph(g), p)).astype(np.float64)
     assert oracle.subspace_sin(X[:, :4], ref["X"][:, :4]) <= 1e-3
+
+
+def test_bench_workload_unbiased_and_sparse(ctx):
+    """BlogCatalog-shaped graph, S = 200 T m = 6.68e8 draws, C = ln n (the
+    paper's choice). Properties that hold at any size:
+
+    * Thm 1 (unbiasedness): the summed weights estimate the number of draws,
+      |z| < 6 against the variance sum_draws (1 - p_e) / p_e;
+    * the kept draws number sum_arcs n_e p_e in expectation (|z| < 6), and
+      sum over arcs of p_e <= 2 C n (each vertex's arcs add at most C), the
+      O(n log n) size bound of Sec. 4.1."""
+    g = synth.blogcatalog_like()
+    n = g.n
+    C = lne.default_downsample_C(n)
+    assert C == float(np.log(n))
+    p = make_params(10, synth.dirichlet_weights(10, seed=3), 200.0 * 10 * g.m, seed=2, d=128)
+    p.downsample_C = C
+    dg = lne.DeviceGraph.from_graph(g)
+    res = ctx.sparsifier_counts(dg, p)
+    thr, w = oracle.arc_downsample(g.indptr, g.indices, C)
+    pe = np.minimum(thr.astype(np.float64) / 2.0 ** 32, 1.0)
+    n_e = oracle.arc_samples(g.n_arcs, p.samples, p.seed).astype(np.float64)
+    assert res["total_samples"] == int(n_e.sum())
+    wsum = to_np(res["weight"]).view(np.uint64)
+    est = float(np.sum(wsum.astype(np.float64))) * 2.0 ** -32
+    var = float(np.sum(n_e * (1.0 - pe) / pe))
+    z = (est - n_e.sum()) / np.sqrt(max(var, 1.0))
+    print(f"downsampled weight total {est:.6e} vs draws {n_e.sum():.6e}, z = {z:.2f}")
+    assert abs(z) < 6.0
+    assert np.sum(pe) <= 2.0 * C * n + 1e-6
+    # kept draws per arc from raw output on a few arc ranges (-1 marks a drop)
+    rng = np.random.default_rng(1)
+    kept, mean, v = 0, 0.0, 0.0
+    for _ in range(4):
+        a0 = int(rng.integers(0, g.n_arcs - 20000))
+        u1, _ = ctx.sample_pairs(dg, p, a0, a0 + 20000)
+        kept += int((u1 >= 0).sum())
+        ne, pp = n_e[a0:a0 + 20000], pe[a0:a0 + 20000]
+        mean += float(np.sum(ne * pp))
+        v += float(np.sum(ne * pp * (1.0 - pp)))
+    assert abs(kept - mean) < 6.0 * np.sqrt(max(v, 1.0))
+    out = ctx.sparsifier_csr(dg, p)
+    ip = to_np(out["indptr"])
+    assert ip[0] == 0 and ip[-1] == out["nnz"] and np.all(np.diff(ip) >= 0)
+    assert bool((out["data"] > 0).all())
+
+
+@pytest.mark.parametrize("name", ["ring1024", "sbm600"])
+@pytest.mark.parametrize("C", [0.0, 0.5])
+def test_keep_decisions_at_the_threshold(ctx, name, C):
+    """b chosen so that a common (K, d_x d_y) lands on v = 1 to the last bits:
+    the keep decisions there (fl(fl(K alpha) / fl(d_x d_y)) > 1 in FP64) must
+    equal the oracle's exactly, with and without downsampling."""
+    g = GRAPHS[name]
+    p = _params(g, T=4, rate=6.0, C=C, seed=21)
+    x, y, cnt = oracle.sparsifier_counts(g.indptr, g.indices, p.T, p.s, p.samples, p.seed, C=C)
+    deg = np.diff(g.indptr).astype(np.float64)
+    K = np.asarray(cnt, dtype=np.float64) * (2.0 ** -32 if C > 0 else 1.0)
+    off = np.flatnonzero(x != y)
+    j = off[len(off) // 2]
+    vol = float(g.n_arcs)
+    p.b = float(K[j] * vol * vol / (2.0 * p.samples) / (deg[x[j]] * deg[y[j]]))
+    sp = oracle.sparsifier(g.indptr, g.indices, p.T, p.s, p.samples, p.seed, p.b, C=C)
+    near = np.abs(sp["v"] - 1.0) < 1e-12
+    assert near.sum() >= 1
+    out = ctx.sparsifier_csr(lne.DeviceGraph.from_graph(g), p)
+    assert np.array_equal(to_np(out["indptr"]), sp["indptr"])
+    assert np.array_equal(to_np(out["indices"]).astype(np.int64), sp["indices"])
+    np.testing.assert_allclose(to_np(out["data"]), sp["data"], rtol=VAL_RTOL, atol=VAL_ATOL)
