@@ -12,9 +12,9 @@
 //            warps), stages them grouped by digit in shared memory and writes
 //            each digit's run contiguously to its global offset.
 // run_length: unique keys of a sorted array and their multiplicities (tile
-// flag counts, one scan over tiles, block scans inside tiles, each run's
-// length counted by the thread owning its first key); run_length_weighted sums
-// a per-arc 64-bit weight over each run instead (edge downsampling).
+// flag counts, one scan over tiles, block scans inside tiles, each thread
+// summing the run segments among its own items); run_length_weighted sums a
+// per-arc 64-bit weight over each run instead (edge downsampling).
 #include "common.cuh"
 #include "runtime.h"
 
@@ -153,10 +153,13 @@ __global__ void __launch_bounds__(kSortThreads) rle_count_kernel(const uint64_t 
     if (threadIdx.x == 0) tile_cnt[blockIdx.x] = s;
 }
 
-// Unique keys and their run lengths (thread-blocked items, block scan); the
-// thread that owns a run's first key walks forward to the run's end, so every
-// key is read about twice in all and no start index array is needed. WEIGHTED:
-// instead of the length, the 64-bit sum of w[arc] over the run's payloads.
+// Unique keys and their run lengths (thread-blocked items, block scan). Each
+// thread adds up the segments of runs among its own items: a run that starts
+// and ends among them is stored, a piece of a run that crosses a thread
+// boundary is added atomically (integer sums, so the result does not depend
+// on the order), which keeps a run of any length parallel. The outputs are
+// zeroed beforehand. WEIGHTED: instead of the length, the 64-bit sum of
+// w[arc] over the run's payloads.
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(kSortThreads) rle_write_kernel(const uint64_t *__restrict__ keys, int64_t n,
                                                                  const int64_t *__restrict__ tile_off,
@@ -177,23 +180,33 @@ __global__ void __launch_bounds__(kSortThreads) rle_write_kernel(const uint64_t 
             ++c;
         }
     }
-    int64_t pos = tile_off[blockIdx.x] + block_scan256(c, s_warp);
-    for (int j = 0; j < kSortItems; ++j)
-        if (flags & (1u << j)) {
-            const int64_t g = i0 + j;
-            const uint64_t k = keys[g];
-            int64_t e = g + 1;
-            if (WEIGHTED) {
-                uint64_t sum = __ldg(w + arcs[g]);
-                for (; e < n && keys[e] == k; ++e) sum += __ldg(w + arcs[e]);
-                wsum[pos] = sum;
-            } else {
-                while (e < n && keys[e] == k) ++e;
-                counts[pos] = (uint32_t)(e - g);
-            }
-            ukeys[pos] = k;
-            ++pos;
+    // index of the run holding the item before this thread's first one
+    int64_t run = tile_off[blockIdx.x] + block_scan256(c, s_warp) - 1;
+    if (i0 >= n) return;
+    const int64_t iend = i0 + kSortItems < n ? i0 + kSortItems : n;
+    auto flush = [&](uint64_t acc, bool complete) {
+        if (WEIGHTED) {
+            if (complete) wsum[run] = acc;
+            else atomicAdd(reinterpret_cast<unsigned long long *>(wsum) + run, (unsigned long long)acc);
+        } else {
+            if (complete) counts[run] = (uint32_t)acc;
+            else atomicAdd(counts + run, (uint32_t)acc);
         }
+    };
+    uint64_t acc = 0;
+    bool started_here = false;
+    for (int64_t g = i0; g < iend; ++g) {
+        if (flags & (1u << (int)(g - i0))) {
+            if (g > i0) flush(acc, started_here);   // the segment ends here
+            ++run;
+            ukeys[run] = keys[g];
+            acc = 0;
+            started_here = true;
+        }
+        acc += WEIGHTED ? __ldg(w + arcs[g]) : 1ull;
+    }
+    const bool ends = iend >= n || keys[iend] != keys[iend - 1];
+    flush(acc, started_here && ends);
 }
 
 // Number of keys below `key` in a sorted array (one thread, binary search).
@@ -265,6 +278,11 @@ int run_length_impl(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t *uk
     rle_count_kernel<<<(unsigned)ntiles, kSortThreads, 0, st>>>(keys, n, tc);
     LNE_LAUNCH_CHECK();
     LNE_TRY(scan_exclusive_u32_to_i64(tc, toff, ntiles, st));
+    int64_t u = 0;
+    LNE_CUDA_TRY(cudaMemcpyAsync(&u, toff + ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (wsum) LNE_CUDA_TRY(cudaMemsetAsync(wsum, 0, sizeof(uint64_t) * (size_t)u, st));
+    else LNE_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * (size_t)u, st));
     if (wsum)
         rle_write_kernel<true><<<(unsigned)ntiles, kSortThreads, 0, st>>>(keys, n, toff, ukeys, nullptr, arcs, w,
                                                                            wsum);
@@ -272,8 +290,6 @@ int run_length_impl(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t *uk
         rle_write_kernel<false><<<(unsigned)ntiles, kSortThreads, 0, st>>>(keys, n, toff, ukeys, counts, nullptr,
                                                                             nullptr, nullptr);
     LNE_LAUNCH_CHECK();
-    int64_t u = 0;
-    LNE_CUDA_TRY(cudaMemcpyAsync(&u, toff + ntiles, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
     *nunique = u;
     return 0;

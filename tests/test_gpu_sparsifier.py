@@ -6,7 +6,9 @@
 * the trunc_log CSR (lne_sparsifier_csr): structure and keep decisions exact,
   values within 1e-6 relative (FP32 log vs FP64 log rounded to FP32);
 * the bench workload (BlogCatalog-shaped graph, S = 200 T m) on sampled arc
-  ranges plus whole-run invariants.
+  ranges plus whole-run invariants;
+* a star graph whose hub pairs repeat millions of times (long runs of equal
+  keys on the sort path).
 """
 import numpy as np
 import pytest
@@ -30,6 +32,7 @@ def ctx(request):
     c = lne.Context(0)
     c.set_option(lne.OPT_AGGREGATION, {"table": lne.AGG_TABLE, "bucket": lne.AGG_BUCKET,
                                        "sort": lne.AGG_SORT}[request.param])
+    c.agg_name = request.param
     yield c
     c.close()
 
@@ -182,3 +185,26 @@ def test_bench_workload_sampled(ctx):
     ip = to_np(out["indptr"])
     assert ip[0] == 0 and ip[-1] == out["nnz"] and np.all(np.diff(ip) >= 0)
     assert bool((out["data"] > 0).all())
+
+
+@pytest.mark.parametrize("C", [0.0, 0.3])
+def test_heavy_pairs_star(ctx, C):
+    """A star (hub 0, 3000 leaves): a few pairs gather most draws (every walk
+    passes the hub), so single runs of the sorted keys hold millions of
+    entries; counts (and downsampled weight sums) stay exact."""
+    if ctx.agg_name == "bucket" and C > 0:
+        pytest.skip("the bucket aggregation has no downsampling")
+    leaves = 3000
+    indptr, indices = synth.csr_from_edges(leaves + 1, np.zeros(leaves, np.int64), np.arange(1, leaves + 1))
+    g = synth.Graph(leaves + 1, indptr, indices, None, "star3000")
+    p = make_params(4, [0.1, 0.6, 0.1, 0.2], 1000.0 * g.n_arcs, seed=5)
+    p.downsample_C = C
+    res = ctx.sparsifier_counts(lne.DeviceGraph.from_graph(g), p)
+    x, y, c = oracle.sparsifier_counts(g.indptr, g.indices, p.T, p.s, p.samples, p.seed, C=C)
+    assert np.array_equal(to_np(res["x"]).astype(np.int64), x)
+    assert np.array_equal(to_np(res["y"]).astype(np.int64), y)
+    if C > 0:
+        assert np.array_equal(to_np(res["weight"]).view(np.uint64), c)
+    else:
+        assert np.array_equal(to_np(res["count"]).astype(np.int64), c)
+        assert c.max() > 1_000_000
