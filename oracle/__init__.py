@@ -13,6 +13,9 @@ FP64, each function citing the passage it follows:
 * ``netmf_values`` / ``sparsifier_csr``: Eq. 1 (the NetMF matrix with the
   truncated logarithm) estimated from the sample counts;
 * ``gaussian_sketch``: the Gaussian test matrix of Algorithm 4;
+* ``sparse_sign_sketch``: the sparse sign test matrix that Sec. 3.2 names as
+  an alternative to the Gaussian one (Tropp et al., SISC 2019): zeta
+  nonzeros +-1 per row at distinct columns (Floyd's subset sampling);
 * ``eig_svd``: Algorithm 2 (eigSVD);
 * ``fast_randomized_svd``: Algorithm 4;
 * ``embedding_from_svd``: X = U Sigma^{1/2} (Sec. 3.2);
@@ -75,6 +78,7 @@ def lib():
                                           ctypes.c_int64, i64p, i32p, i32p, i64p, i64p, u32p]
         L.oracle_sample_trace.restype = ctypes.c_int64
         L.oracle_sketch_words.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, u32p]
+        L.oracle_sparse_sign_words.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, u32p]
         L.oracle_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -325,6 +329,45 @@ def gaussian_sketch(n: int, c: int, seed: int) -> np.ndarray:
     return z.reshape(n, nblk * 4)[:, :c].copy()
 
 
+def floyd_subset(t_words: np.ndarray, c: int) -> np.ndarray:
+    """Floyd's algorithm (Bentley & Floyd, CACM 1987) for a uniform zeta-subset
+    of {0..c-1}, row-wise: step k = 0..zeta-1 takes j = c - zeta + k and
+    t = word_k mod (j + 1); it adds t unless t was chosen already, else j.
+    Returns the chosen columns in the order they were added ([rows, zeta])."""
+    t_words = np.asarray(t_words, dtype=np.uint64)
+    rows, zeta = t_words.shape
+    out = np.zeros((rows, zeta), dtype=np.int64)
+    for k in range(zeta):
+        j = c - zeta + k
+        t = (t_words[:, k] % np.uint64(j + 1)).astype(np.int64)
+        taken = (out[:, :k] == t[:, None]).any(axis=1)
+        out[:, k] = np.where(taken, j, t)
+    return out
+
+
+def sparse_sign_sketch(n: int, c: int, zeta: int, seed: int) -> np.ndarray:
+    """Sparse sign test matrix Omega (n x c): row i has exactly zeta nonzeros,
+    +1 or -1, at distinct columns (Sec. 3.2 names it as an alternative to
+    the Gaussian Omega of Algorithm 4; the construction is that of Tropp et
+    al., SISC 2019, applied to the rows of Omega so that M Omega costs zeta
+    terms per nonzero of M).
+
+    Row i reads the words of counters (i, b, 0, 0x53505253), b = 0, 1, ..., key
+    (seed_lo ^ 0x4f4d4547, seed_hi), in order: words 0..zeta-1 drive Floyd's
+    subset sampling (``floyd_subset``), word zeta holds the signs: the k-th
+    chosen column is negative iff bit k is set. Scale 1 (the range of M Omega
+    does not depend on it)."""
+    nblk = (zeta + 1 + 3) // 4
+    words = np.zeros((n, nblk, 4), dtype=np.uint32)
+    lib().oracle_sparse_sign_words(n, nblk, int(seed), _ptr(words, ctypes.c_uint32))
+    w = words.reshape(n, nblk * 4)
+    cols = floyd_subset(w[:, :zeta], c)
+    neg = (w[:, zeta:zeta + 1].astype(np.int64) >> np.arange(zeta)[None, :]) & 1
+    Om = np.zeros((n, c))
+    Om[np.arange(n)[:, None], cols] = 1.0 - 2.0 * neg
+    return Om
+
+
 def fix_signs(U: np.ndarray, *others: np.ndarray):
     """Make the largest-magnitude entry of every column of U positive (first
     index on ties) and flip the matching columns of ``others``."""
@@ -360,17 +403,20 @@ def spmm(indptr, indices, data, X):
 
 
 def fast_randomized_svd(indptr, indices, data, d: int, q: int, oversample: int, seed: int,
-                        Omega: np.ndarray | None = None):
+                        Omega: np.ndarray | None = None, sketch: str = "gaussian", zeta: int = 8):
     """Algorithm 4 (Fast Randomized SVD) on the symmetric sparse M.
 
-    Omega = randn(n, d+s); Y = M Omega; Q = eigSVD(Y).U; q times: Y = M Q,
-    T = Q, [Q, Sigma, V] = eigSVD(Y); return U = Q(:, 1:d), Sigma(1:d),
-    V = T V(:, 1:d). With q = 0 the eigSVD of M Omega supplies Sigma and V.
+    Omega = randn(n, d+s) (or, with sketch="sparse_sign", the sparse sign
+    matrix with zeta nonzeros per row); Y = M Omega; Q = eigSVD(Y).U; q times:
+    Y = M Q, T = Q, [Q, Sigma, V] = eigSVD(Y); return U = Q(:, 1:d),
+    Sigma(1:d), V = T V(:, 1:d). With q = 0 the eigSVD of M Omega supplies
+    Sigma and V.
     """
     n = len(indptr) - 1
     c = d + oversample
     if Omega is None:
-        Omega = gaussian_sketch(n, c, seed)
+        Omega = (sparse_sign_sketch(n, c, zeta, seed) if sketch == "sparse_sign"
+                 else gaussian_sketch(n, c, seed))
     Y = spmm(indptr, indices, data, Omega)
     Q, Sig, V = eig_svd(Y)
     T = Omega

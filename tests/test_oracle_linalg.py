@@ -4,6 +4,9 @@
 * Fast randomized SVD (Algorithm 4) recovers a planted spectrum with a gap,
   and its mean error respects the Eq. 2 bound.
 * Gaussian sketch moments and normality (Algorithm 4).
+* Sparse sign sketch: Floyd's subset sampling exhaustively uniform on a small
+  case, exact row structure, uniform columns, fair signs, E[Omega^T Omega];
+  Algorithm 4 with it recovers a planted spectrum.
 * The Chebyshev coefficients expand exp(-theta y) (Bessel generating function).
 * Spectral propagation equals the filter evaluated on the eigenvalues of the
   normalised Laplacian (Sec. 3.3), computed independently from a dense
@@ -165,3 +168,61 @@ def test_embedding_recovers_blocks():
     W, *_ = np.linalg.lstsq(Xa[tr], Y[tr], rcond=None)
     acc = np.mean(np.argmax(Xa[te] @ W, 1) == y[te])
     assert acc > 0.9
+
+
+# sparse sign test matrix (the alternative Omega of Sec. 3.2; Tropp et al. 2019)
+
+def test_floyd_subset_exhaustive():
+    """Every word combination of Floyd's steps for c = 6, zeta = 3: each of the
+    C(6, 3) = 20 subsets comes out equally often (4 x 5 x 6 / 20 = 6 times),
+    always as distinct columns; words act modulo j + 1."""
+    import itertools
+    c, zeta = 6, 3
+    combos = np.array(list(itertools.product(range(4), range(5), range(6))), dtype=np.uint64)
+    out = oracle.floyd_subset(combos, c)
+    assert np.all([len(set(r)) == zeta for r in out.tolist()])
+    assert out.min() >= 0 and out.max() < c
+    sets, counts = np.unique(np.sort(out, axis=1), axis=0, return_counts=True)
+    assert len(sets) == 20 and np.all(counts == 6)
+    shifted = combos + np.array([4, 5, 6], dtype=np.uint64) * np.uint64(977)
+    np.testing.assert_array_equal(oracle.floyd_subset(shifted, c), out)
+
+
+def test_sparse_sign_sketch_law():
+    n, c, zeta = 20000, 48, 8
+    Om = oracle.sparse_sign_sketch(n, c, zeta, seed=9)
+    nz = Om != 0
+    assert np.all(nz.sum(axis=1) == zeta)
+    assert set(np.unique(Om[nz])) == {-1.0, 1.0}
+    # columns uniform: each is chosen with probability zeta / c
+    colcnt = nz.sum(axis=0)
+    assert st.chisquare(colcnt).pvalue > 1e-4
+    # signs fair and independent of the column
+    neg = (Om < 0).sum()
+    tot = n * zeta
+    assert abs(neg - tot / 2) < 5 * np.sqrt(tot / 4)
+    negc = (Om < 0).sum(axis=0)
+    assert np.all(np.abs(negc - colcnt / 2) < 5 * np.sqrt(colcnt / 4) + 1)
+    # E[Omega^T Omega] / n = (zeta / c) I
+    G = Om.T @ Om / n
+    np.testing.assert_allclose(np.diag(G), zeta / c, atol=6 * np.sqrt(zeta / c / n))
+    pboth = zeta * (zeta - 1) / (c * (c - 1))
+    assert np.max(np.abs(G - np.diag(np.diag(G)))) < 6 * np.sqrt(pboth / n)
+    # deterministic in the seed; another seed gives another matrix
+    np.testing.assert_array_equal(oracle.sparse_sign_sketch(40, c, zeta, 9), Om[:40])
+    assert not np.array_equal(oracle.sparse_sign_sketch(40, c, zeta, 10), Om[:40])
+
+
+@pytest.mark.parametrize("zeta", [1, 4, 8])
+def test_frsvd_sparse_sign_recovers_planted_spectrum(zeta):
+    rng = np.random.default_rng(1)
+    n, d = 300, 12
+    lam = np.concatenate([np.linspace(50, 20, d) * np.where(np.arange(d) % 3 == 0, -1, 1),
+                          rng.uniform(-1, 1, n - d)])
+    Q, M = _planted_symmetric(rng, n, lam)
+    order = np.argsort(-np.abs(lam))
+    out = oracle.fast_randomized_svd(M.indptr.astype(np.int64), M.indices, M.data, d, q=8,
+                                     oversample=8, seed=5, sketch="sparse_sign", zeta=zeta)
+    assert np.count_nonzero(out["Omega"]) == n * zeta
+    np.testing.assert_allclose(out["sigma"], np.abs(lam[order[:d]]), rtol=1e-10)
+    assert oracle.subspace_sin(out["U"], Q[:, order[:d]]) < 1e-9
