@@ -268,6 +268,8 @@ def run_ours(args):
     params["seed"] = params["seed"] + rank
     if args.downsample:
         params["downsample_C"] = lne.default_downsample_C(g.n)
+    if args.sketch == "sparse_sign":
+        params["sketch"] = lne.SKETCH_SPARSE_SIGN
     P = lne.Params(**params)
     ctx = lne.Context(local)
     dg = lne.DeviceGraph(g.indptr, g.indices, device=dev)
@@ -370,14 +372,15 @@ def run_ours(args):
 
     if rank == 0:
         cpu = None
-        if world == 1 and not args.no_cpu_baseline and not args.downsample:
+        if world == 1 and not args.no_cpu_baseline and not args.downsample and args.sketch == "gaussian":
             r = oracle_step(g, params, rep=0)
             cpu = {"value": r["value"], "unit": "samples/s", "cores": r["cores"], "kind": "oracle",
                    "sample": r["sample"]}
         line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD + ("_downsampled_C=ln_n" if args.downsample else ""),
+                "config": {"workload": WORKLOAD + ("_downsampled_C=ln_n" if args.downsample else "")
+                           + ("_sparse_sign_sketch" if args.sketch == "sparse_sign" else ""),
                            "n": g.n, "m": g.m, "samples": params["samples"], "T": 10,
                            "d": 128, "q": 1, "k": 10, "l2": "flushed (256 MB write) between steps",
                            "parallelism": f"replicas{world}", "nnz_pairs": info["nnz_c"],
@@ -404,6 +407,8 @@ def run_case(args):
     g, params = workload()
     params = dict(params)
     params["samples"] = params["samples"] / args.scale
+    if args.sketch == "sparse_sign":
+        params["sketch"] = lne.SKETCH_SPARSE_SIGN
     P = lne.Params(**params)
     ctx = lne.Context(0)
     dg = lne.DeviceGraph(g.indptr, g.indices)
@@ -625,6 +630,8 @@ def main():
                     help="measure surrogate-guided search after training on G graphs of the SBM suite")
     ap.add_argument("--downsample", action="store_true",
                     help="the benchmark with edge downsampling at C = ln n (draws per second; no CPU baseline)")
+    ap.add_argument("--sketch", choices=["gaussian", "sparse_sign"], default="gaussian",
+                    help="test matrix of the randomized SVD (sparse sign: zeta = 8 nonzeros per row)")
     ap.add_argument("--large", action="store_true",
                     help="the 10M-vertex BF16 precision run instead of the benchmark (--scale divides its size)")
     args = ap.parse_args()

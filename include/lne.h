@@ -54,6 +54,10 @@ extern "C" {
 #define LNE_PREC_FP32        0
 #define LNE_PREC_BF16_MIXED  1
 
+/* Test matrix Omega of the randomized SVD (Algorithm 4). */
+#define LNE_SKETCH_GAUSSIAN     0   /* randn(n, c), the paper's default */
+#define LNE_SKETCH_SPARSE_SIGN  1   /* zeta nonzeros +-1 per row (Sec. 3.2's sparse sign alternative) */
+
 typedef struct {
     int64_t n;                 /* vertices */
     int64_t nnz;               /* arcs = 2m = indptr[n] */
@@ -78,6 +82,9 @@ typedef struct {
     double downsample_C;       /* edge downsampling (Sec. 4.1): 0 = off; C > 0 keeps a draw of arc
                                   u -> v with probability p_e = min(1, C (1/d_u + 1/d_v)) and
                                   weighs it 1/p_e; finite, >= 0 */
+    int32_t sketch;            /* LNE_SKETCH_* */
+    int32_t sketch_zeta;       /* nonzeros per row of the sparse sign sketch, 1..min(12, c);
+                                  0 = min(8, c) */
 } lne_params;
 
 typedef struct {
@@ -170,6 +177,29 @@ int lne_sparsifier_csr(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
  */
 int lne_gaussian_sketch(lne_ctx *ctx, int64_t n, int32_t c, uint64_t seed, float *out_dev,
                         int64_t ld, void *stream);
+
+/*
+ * Sparse sign test matrix (the cheaper alternative to the Gaussian Omega that
+ * Sec. 3.2 names; construction of Tropp et al., SISC 2019): row i of out_dev
+ * ([n][ld], ld >= c, float) has exactly zeta entries +-1 at distinct columns,
+ * zeros elsewhere. Columns by Floyd's subset sampling: with words w_0.. of
+ * Philox4x32-10 counters (i, b, 0, 0x53505253), b = 0, 1, .., key
+ * (seed_lo ^ 0x4f4d4547, seed_hi), step k = 0..zeta-1 takes j = c - zeta + k,
+ * t = w_k mod (j + 1) and adds t unless already chosen, else j; the k-th
+ * chosen column is -1 iff bit k of w_zeta is set. 1 <= zeta <= min(12, c),
+ * c <= 255; LNE_ERR_INVALID otherwise.
+ */
+int lne_sparse_sign_sketch(lne_ctx *ctx, int64_t n, int32_t c, int32_t zeta, uint64_t seed, float *out_dev,
+                           int64_t ld, void *stream);
+
+/*
+ * Y_dev = M Omega for the sparse sign Omega of lne_sparse_sign_sketch (never
+ * formed): each entry is the exact sum of its terms (M's values rounded to
+ * multiples of 2^-32, summed in 64-bit fixed point) rounded once to float.
+ * Needs |row sums of M| < 2^31. Y_dev is [n][ldy], ldy >= c, row-major.
+ */
+int lne_sparse_sign_spmm(lne_ctx *ctx, const lne_csr *M, int32_t c, int32_t zeta, uint64_t seed, float *Y_dev,
+                         int64_t ldy, void *stream);
 
 /* Y = M X for CSR M (n x n) and X [n][ldx] (c columns), Y [n][ldy] FP32,
  * accumulated in FP32 (Algorithm 4). X_dev is float

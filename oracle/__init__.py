@@ -492,12 +492,14 @@ def spectral_propagation(indptr, indices, X0: np.ndarray, k: int, theta: float, 
 # whole method
 # ----------------------------------------------------------------------------
 
-def embed(indptr, indices, T, s, S, d, q, k, theta, mu, seed, oversample=16, b=1.0, C=0.0):
-    """Sparsifier (edge-downsampled when C > 0, Sec. 4.1) -> randomized SVD ->
-    X0 -> spectral propagation -> X."""
+def embed(indptr, indices, T, s, S, d, q, k, theta, mu, seed, oversample=16, b=1.0, C=0.0,
+          sketch="gaussian", zeta=8):
+    """Sparsifier (edge-downsampled when C > 0, Sec. 4.1) -> randomized SVD
+    (Gaussian or sparse sign test matrix, Sec. 3.2) -> X0 -> spectral
+    propagation -> X."""
     sparse = sparsifier(indptr, indices, T, s, S, seed, b, C)
     rs = fast_randomized_svd(sparse["indptr"], sparse["indices"], sparse["data"], d, q,
-                             oversample, seed)
+                             oversample, seed, sketch=sketch, zeta=zeta)
     X0 = embedding_from_svd(rs["U"], rs["sigma"])
     prop = spectral_propagation(indptr, indices, X0, k, theta, mu)
     return dict(sparse=sparse, rsvd=rs, X0=X0, prop=prop, X=prop["X"])

@@ -222,10 +222,31 @@ int check_params(const lne_params *p, bool sampling) {
         return lne::fail(LNE_ERR_INVALID, "unknown precision");
     if (!(p->downsample_C >= 0.0) || !std::isfinite(p->downsample_C))
         return lne::fail(LNE_ERR_INVALID, "downsample_C must be a finite value >= 0");
+    if (p->sketch != LNE_SKETCH_GAUSSIAN && p->sketch != LNE_SKETCH_SPARSE_SIGN)
+        return lne::fail(LNE_ERR_INVALID, "unknown sketch");
+    if (p->sketch_zeta < 0 || p->sketch_zeta > lne::kMaxSketchZeta)
+        return lne::fail(LNE_ERR_INVALID, "sketch_zeta must be in 0..12");
     return 0;
 }
 
 int oversample_of(const lne_params *p) { return p->oversample < 0 ? 16 : p->oversample; }
+
+lne::SketchSpec sketch_of(const lne_params *p) {
+    lne::SketchSpec s;
+    s.kind = p->sketch;
+    s.zeta = p->sketch_zeta;
+    return s;
+}
+
+lne::CsrView csr_view(const lne_csr *M) {
+    lne::CsrView v;
+    v.n = M->n;
+    v.nnz = M->nnz;
+    v.indptr = M->indptr;
+    v.indices = M->indices;
+    v.data = M->data;
+    return v;
+}
 
 // Checks the graph's end points on the device (indptr[0] == 0, indptr[n] == nnz).
 int check_graph_device(const lne_graph *g, cudaStream_t st) {
@@ -443,6 +464,25 @@ int lne_gaussian_sketch(lne_ctx *ctx, int64_t n, int32_t c, uint64_t seed, float
     return finish(ctx, rc);
 }
 
+int lne_sparse_sign_sketch(lne_ctx *ctx, int64_t n, int32_t c, int32_t zeta, uint64_t seed, float *out_dev,
+                           int64_t ld, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (n < 0 || (n > 0 && !out_dev))) rc = lne::fail(LNE_ERR_INVALID, "bad sketch arguments");
+    if (rc == 0) rc = lne::sparse_sign_dense(ctx->ws, n, c, zeta, seed, out_dev, ld, as_stream(stream));
+    return finish(ctx, rc);
+}
+
+int lne_sparse_sign_spmm(lne_ctx *ctx, const lne_csr *M, int32_t c, int32_t zeta, uint64_t seed, float *Y_dev,
+                         int64_t ldy, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (!M || M->n < 0 || !M->indptr || (M->n > 0 && !Y_dev)))
+        rc = lne::fail(LNE_ERR_INVALID, "bad sparse sign product arguments");
+    if (rc == 0) rc = lne::sparse_sign_spmm(ctx->ws, csr_view(M), c, zeta, seed, Y_dev, ldy, as_stream(stream));
+    return finish(ctx, rc);
+}
+
 int lne_spmm(lne_ctx *ctx, const lne_csr *M, const void *X_dev, int64_t ldx, int32_t c, float *Y_dev,
              int64_t ldy, int32_t precision, void *stream) {
     if (!ctx) return LNE_ERR_INVALID;
@@ -497,7 +537,7 @@ int lne_rsvd(lne_ctx *ctx, const lne_csr *M, const lne_params *p, float *U_dev, 
         v.indices = M->indices;
         v.data = M->data;
         rc = lne::rsvd(ctx->ws, v, p->d, oversample_of(p), p->q, p->seed, p->precision, U_dev, sigma_dev, X0_dev,
-                       as_stream(stream));
+                       as_stream(stream), sketch_of(p));
     }
     return finish(ctx, rc);
 }
@@ -550,7 +590,7 @@ int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_de
     if (rc == 0) rc = ctx->ws.get("embed.x0", (size_t)g->n * p->d, &X0);
     if (rc == 0) {
         rc = lne::rsvd(ctx->ws, lne::product_view(M, ctx->dense_mode), p->d, oversample_of(p), p->q, p->seed,
-                       p->precision, nullptr, nullptr, X0, st);
+                       p->precision, nullptr, nullptr, X0, st, sketch_of(p));
     }
     if (rc == 0)
         rc = lne::propagate(ctx->ws, view(g), p->d, p->k, p->theta, p->mu, p->precision, X0, X_dev, nullptr, nullptr,

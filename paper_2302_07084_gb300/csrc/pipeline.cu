@@ -66,7 +66,7 @@ std::vector<double> chebyshev_coefficients(int k, double theta) {
 }
 
 int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t seed, int precision, float *U,
-         double *sigma, float *X0, cudaStream_t st) {
+         double *sigma, float *X0, cudaStream_t st, const SketchSpec &sketch) {
     const int64_t n = M.n;
     const int c = d + oversample;
     if (d < 1 || oversample < 0) return fail(LNE_ERR_INVALID, "need d >= 1 and oversample >= 0");
@@ -75,7 +75,6 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
     if (q < 0) return fail(LNE_ERR_INVALID, "q must be >= 0");
     float *Om = nullptr, *Ya = nullptr, *Yb = nullptr, *Ub = nullptr;
     double *sg = nullptr;
-    LNE_TRY(ws.get("rsvd.omega", (size_t)n * c, &Om));
     LNE_TRY(ws.get("rsvd.ya", (size_t)n * c, &Ya));
     LNE_TRY(ws.get("rsvd.yb", (size_t)n * c, &Yb));
     if (!U) LNE_TRY(ws.get("rsvd.u", (size_t)n * d, &Ub));
@@ -90,13 +89,21 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
         if (M.dense) return dense_sym_spmm(ws, M.dense, M.dense_ld, n, X, c, c, Y, c, st);
         return spmm(ws, M, X, c, c, Y, c, st);
     };
-    // Algorithm 4: Omega = randn(n, d+s); Y = M Omega
-    LNE_TRY(gaussian_sketch(n, c, seed, Om, c, st));
-    if (bf16) {
-        LNE_TRY(to_bf16(Om, Xh, n * c, st));
-        LNE_TRY(spmm_bf16(ws, M, Xh, c, c, Ya, c, nullptr, st));
+    // Algorithm 4: Omega = randn(n, d+s); Y = M Omega. The sparse sign Omega
+    // (Sec. 3.2's cheaper alternative) is applied without being formed; its
+    // product is exact up to one rounding, in either precision mode.
+    if (sketch.kind == LNE_SKETCH_SPARSE_SIGN) {
+        const int zeta = sketch.zeta > 0 ? sketch.zeta : std::min(8, c);
+        LNE_TRY(sparse_sign_spmm(ws, M, c, zeta, seed, Ya, c, st));
     } else {
-        LNE_TRY(mprod(Om, Ya));
+        LNE_TRY(ws.get("rsvd.omega", (size_t)n * c, &Om));
+        LNE_TRY(gaussian_sketch(n, c, seed, Om, c, st));
+        if (bf16) {
+            LNE_TRY(to_bf16(Om, Xh, n * c, st));
+            LNE_TRY(spmm_bf16(ws, M, Xh, c, c, Ya, c, nullptr, st));
+        } else {
+            LNE_TRY(mprod(Om, Ya));
+        }
     }
     // power iterations: Q = orth(Y); Y = M Q (q times)
     for (int it = 0; it < q; ++it) {

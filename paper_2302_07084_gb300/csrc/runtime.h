@@ -165,9 +165,25 @@ int graph_spmm_bf16(Workspace &ws, const GraphView &g, const __nv_bfloat16 *X, i
 // out[i] = bf16(in[i]) for count elements.
 int to_bf16(const float *in, __nv_bfloat16 *out, int64_t count, cudaStream_t st);
 
+// Sparse sign test matrix (sketch.cu): zeta nonzeros +-1 per row, each row
+// packed in 16 bytes (column bytes, then sign bits) in the workspace.
+constexpr int kMaxSketchZeta = 12;
+struct SketchSpec {
+    int kind = LNE_SKETCH_GAUSSIAN;
+    int zeta = 0;   // nonzeros per row of the sparse sign sketch; 0 = min(8, c)
+};
+int sparse_sign_sketch(Workspace &ws, int64_t n, int c, int zeta, uint64_t seed, const uint4 **packed,
+                       cudaStream_t st);
+// The sketch written out densely (out[n][ld], ld >= c).
+int sparse_sign_dense(Workspace &ws, int64_t n, int c, int zeta, uint64_t seed, float *out, int64_t ld,
+                      cudaStream_t st);
+// Y = M Omega for the sparse sign Omega (exact 64-bit fixed-point sums).
+int sparse_sign_spmm(Workspace &ws, const CsrView &M, int c, int zeta, uint64_t seed, float *Y, int64_t ldy,
+                     cudaStream_t st);
+
 // Randomized SVD (Algorithm 4) and propagation (Sec. 3.3).
 int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t seed, int precision,
-         float *U, double *sigma, float *X0, cudaStream_t st);
+         float *U, double *sigma, float *X0, cudaStream_t st, const SketchSpec &sketch = SketchSpec());
 int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, double mu, int precision,
               const float *X0, float *X, float *F, float *P, cudaStream_t st);
 

@@ -37,7 +37,8 @@ namespace {
 
 bool same_rsvd_inputs(const lne_params &a, const lne_params &b, int osa, int osb) {
     if (a.T != b.T || a.samples != b.samples || a.b != b.b || a.d != b.d || osa != osb || a.q != b.q ||
-        a.seed != b.seed || a.downsample_C != b.downsample_C)
+        a.seed != b.seed || a.downsample_C != b.downsample_C || a.sketch != b.sketch ||
+        a.sketch_zeta != b.sketch_zeta)
         return false;
     for (int i = 0; i < a.T; ++i)
         if (a.s[i] != b.s[i]) return false;
@@ -133,8 +134,11 @@ int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregati
         sp.ds_C = p.downsample_C;
         CsrResult M;
         LNE_TRY(sparsifier_csr(ws, g, sp, &M, st));
+        SketchSpec sk;
+        sk.kind = p.sketch;
+        sk.zeta = p.sketch_zeta;
         LNE_TRY(rsvd(ws, product_view(M, dense_mode), d, os_of(p), p.q, p.seed, p.precision, nullptr, nullptr,
-                     X0s + (size_t)q * n * d, st));
+                     X0s + (size_t)q * n * d, st, sk));
     }
     float *X = nullptr, *U = nullptr;
     double *R = nullptr, *UR = nullptr, *sig = nullptr;

@@ -22,10 +22,13 @@ ERRORS = {-1: "LNE_ERR_INVALID", -2: "LNE_ERR_OOM", -3: "LNE_ERR_CUDA", -4: "LNE
           -5: "LNE_ERR_UNSUPPORTED", -6: "LNE_ERR_NUMERIC"}
 PREC_FP32 = 0
 PREC_BF16_MIXED = 1
+SKETCH_GAUSSIAN = 0
+SKETCH_SPARSE_SIGN = 1
 
 EXPORTED = [
     "lne_create", "lne_destroy", "lne_last_error", "lne_workspace_bytes", "lne_trim",
     "lne_sample_pairs", "lne_sparsifier_counts", "lne_sparsifier_csr", "lne_gaussian_sketch",
+    "lne_sparse_sign_sketch", "lne_sparse_sign_spmm",
     "lne_spmm", "lne_cholqr2", "lne_rsvd", "lne_propagate", "lne_embed",
     "lne_kernel_launches", "lne_trace_enable", "lne_trace_read", "lne_set_option",
     "lne_svd_small", "lne_svd_small_noalloc", "lne_macro_f1", "lne_tune_batch", "lne_tune_tasks",
@@ -62,7 +65,7 @@ class _Params(ctypes.Structure):
                 ("b", ctypes.c_double), ("d", ctypes.c_int32), ("oversample", ctypes.c_int32),
                 ("q", ctypes.c_int32), ("k", ctypes.c_int32), ("theta", ctypes.c_double),
                 ("mu", ctypes.c_double), ("seed", ctypes.c_uint64), ("precision", ctypes.c_int32),
-                ("downsample_C", ctypes.c_double)]
+                ("downsample_C", ctypes.c_double), ("sketch", ctypes.c_int32), ("sketch_zeta", ctypes.c_int32)]
 
 
 class _Csr(ctypes.Structure):
@@ -106,6 +109,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lne_sparsifier_counts.argtypes = [vp, gp, pp, ctypes.POINTER(_Counts), vp]
     L.lne_sparsifier_csr.argtypes = [vp, gp, pp, ctypes.POINTER(_Csr), vp]
     L.lne_gaussian_sketch.argtypes = [vp, i64, i32, u64, vp, i64, vp]
+    L.lne_sparse_sign_sketch.argtypes = [vp, i64, i32, i32, u64, vp, i64, vp]
+    L.lne_sparse_sign_spmm.argtypes = [vp, ctypes.POINTER(_Csr), i32, i32, u64, vp, i64, vp]
     L.lne_spmm.argtypes = [vp, ctypes.POINTER(_Csr), vp, i64, i32, vp, i64, i32, vp]
     L.lne_cholqr2.argtypes = [vp, vp, i64, i32, i64, vp, vp]
     L.lne_rsvd.argtypes = [vp, ctypes.POINTER(_Csr), pp, vp, vp, vp, vp]
@@ -152,6 +157,8 @@ class Params:
     seed: int = 0
     precision: int = PREC_FP32
     downsample_C: float = 0.0     # edge downsampling constant C (0 = off)
+    sketch: int = SKETCH_GAUSSIAN  # test matrix of the randomized SVD
+    sketch_zeta: int = 0          # nonzeros per row of the sparse sign sketch (0 = min(8, c))
 
     def _c(self):
         s = np.ascontiguousarray(np.asarray(self.s, dtype=np.float64))
@@ -159,7 +166,7 @@ class Params:
         p = _Params(int(self.T), ctypes.cast(arr, ctypes.POINTER(ctypes.c_double)), float(self.samples),
                     float(self.b), int(self.d), int(self.oversample), int(self.q), int(self.k),
                     float(self.theta), float(self.mu), int(self.seed) & 0xFFFFFFFFFFFFFFFF,
-                    int(self.precision), float(self.downsample_C))
+                    int(self.precision), float(self.downsample_C), int(self.sketch), int(self.sketch_zeta))
         return p, arr
 
 
@@ -342,6 +349,21 @@ class Context:
         self._check(self.lib.lne_gaussian_sketch(self.h, n, c, int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out), c,
                                                  _stream()))
         return out
+
+    def sparse_sign_sketch(self, n: int, c: int, zeta: int, seed: int) -> torch.Tensor:
+        """The sparse sign test matrix written out densely (n x c)."""
+        out = torch.empty((n, c), dtype=torch.float32, device=self.dev)
+        self._check(self.lib.lne_sparse_sign_sketch(self.h, n, c, zeta, int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out),
+                                                    c, _stream()))
+        return out
+
+    def sparse_sign_spmm(self, csr: dict, c: int, zeta: int, seed: int) -> torch.Tensor:
+        """Y = M Omega for the sparse sign Omega (never formed)."""
+        Y = torch.empty((int(csr["n"]), c), dtype=torch.float32, device=self.dev)
+        m = self._csr(csr)
+        self._check(self.lib.lne_sparse_sign_spmm(self.h, ctypes.byref(m), c, zeta, int(seed) & 0xFFFFFFFFFFFFFFFF,
+                                                  _ptr(Y), c, _stream()))
+        return Y
 
     @staticmethod
     def _csr(csr: dict) -> _Csr:
