@@ -12,6 +12,8 @@ FP64, each function citing the passage it follows:
   (per-edge sampling, Sec. 4.2) and the walk-step rule of Sec. 4.2;
 * ``netmf_values`` / ``sparsifier_csr``: Eq. 1 (the NetMF matrix with the
   truncated logarithm) estimated from the sample counts;
+* ``stratified_*``: window-stratified counts shared by many weightings s
+  (an unbiased importance-weighted estimate, not in the paper);
 * ``gaussian_sketch``: the Gaussian test matrix of Algorithm 4;
 * ``sparse_sign_sketch``: the sparse sign test matrix that Sec. 3.2 names as
   an alternative to the Gaussian one (Tropp et al., SISC 2019): zeta
@@ -221,6 +223,54 @@ def sparsifier_counts(indptr, indices, T, s, S, seed, C: float = 0.0):
     return keys // n, keys % n, wsum
 
 
+def stratified_counts(indptr, indices, T, S, seed):
+    """Window-stratified counts for sharing one sampling pass among many
+    window weightings s (the survey's proposal for candidate batching, not a
+    procedure of the paper): every draw takes r ~ U{1..T} (Algorithm 3 with
+    s uniform) and the pair counts are kept per window length.
+    Returns (x, y, r, count) sorted by (x, y, r)."""
+    n = len(indptr) - 1
+    tr = sample_trace(indptr, indices, T, np.ones(T), S, seed, fields=("r", "u1", "v1"))
+    x = np.minimum(tr["u1"], tr["v1"])
+    y = np.maximum(tr["u1"], tr["v1"])
+    keys, cnt = np.unique((x * n + y) * T + (tr["r"].astype(np.int64) - 1), return_counts=True)
+    pair, r = keys // T, keys % T + 1
+    return pair // n, pair % n, r, cnt.astype(np.int64)
+
+
+def stratified_weights(s, T) -> np.ndarray:
+    """w_r = floor(T s_r / sum(s) 2^24 + 1/2): the importance weight of window
+    r (its probability under s over its probability 1/T under the uniform
+    draw) in 2^-24 units, exact integers (w_r < 2^28 for T <= 16)."""
+    s = np.asarray(s, dtype=np.float64)[:T]
+    return np.floor(T * (s / s.sum()) * 16777216.0 + 0.5).astype(np.uint64)
+
+
+def stratified_estimate(x, y, r, cnt, s, T):
+    """K_s(x, y) = sum_r w_r C_r(x, y) in 2^-24 units (uint64, exact): an
+    unbiased estimate of the pair count a run with weights s would draw
+    (E[C_r] = (S / T) P_r and w_r 2^-24 / T = s_r up to the rounding of w_r).
+    Returns (x, y, K) over the distinct pairs, sorted by (x, y)."""
+    w = stratified_weights(s, T)
+    n = int(max(np.max(x, initial=0), np.max(y, initial=0))) + 1
+    pair = np.asarray(x, np.int64) * n + np.asarray(y, np.int64)
+    up, inv = np.unique(pair, return_inverse=True)
+    K = np.zeros(len(up), dtype=np.uint64)
+    np.add.at(K, inv, w[np.asarray(r) - 1] * np.asarray(cnt, dtype=np.uint64))
+    return up // n, up % n, K
+
+
+def stratified_sparsifier(indptr, indices, T, s, S, seed, b=1.0):
+    """Eq. 1 from the stratified estimate K_s (K = fl(double(K_s)) 2^-24)."""
+    n = len(indptr) - 1
+    deg = np.diff(indptr)
+    x, y, r, c = stratified_counts(indptr, indices, T, S, seed)
+    px, py, K = stratified_estimate(x, y, r, c, s, T)
+    v, keep, val = netmf_values(px, py, K, deg, S, b, unit=2.0 ** -24)
+    mp, mc, mv = sparsifier_csr(n, px[keep], py[keep], val[keep])
+    return dict(x=px, y=py, K=K, v=v, keep=keep, val=val, indptr=mp, indices=mc, data=mv)
+
+
 # ----------------------------------------------------------------------------
 # Eq. 1: from counts to the truncated-log NetMF estimate
 # ----------------------------------------------------------------------------
@@ -237,13 +287,13 @@ def netmf_scale(vol: float, S: float, b: float = 1.0) -> tuple[float, float]:
     return vv / ((2.0 * S) * b), vv / (S * b)
 
 
-def netmf_values(x, y, cnt, deg, S, b=1.0, weighted=False):
+def netmf_values(x, y, cnt, deg, S, b=1.0, weighted=False, unit=None):
     """Pre-log entries v, keep mask (v > 1) and float32 trunc_log values (Eq. 1).
 
     v = fl(fl(K * alpha) / fl(d_x * d_y)); trunc_log(v) = max(0, log v) is zero
     unless v > 1, and zero entries are dropped from the sparse matrix. With
     ``weighted`` the counts are downsampling weight sums in 2^-32 units and
-    K = fl(double(cnt)) * 2^-32.
+    K = fl(double(cnt)) * 2^-32; ``unit`` gives another power-of-two unit.
     """
     deg = np.asarray(deg, dtype=np.float64)
     vol = float(deg.sum())
@@ -251,7 +301,9 @@ def netmf_values(x, y, cnt, deg, S, b=1.0, weighted=False):
     alpha = np.where(x == y, a_diag, a_off)
     K = np.asarray(cnt, dtype=np.float64)
     if weighted:
-        K = K * 2.0 ** -32
+        unit = 2.0 ** -32
+    if unit is not None:
+        K = K * unit
     v = (K * alpha) / (deg[x] * deg[y])
     keep = v > 1.0
     val = np.zeros(v.shape, dtype=np.float32)

@@ -301,3 +301,73 @@ def test_kept_draws_follow_the_coin_law():
     kept = tr["coin"].astype(np.uint64) < thr[tr["arc"]]
     z = (kept.sum() - p.sum()) / np.sqrt(np.sum(p * (1 - p)))
     assert abs(z) < 5 and 0 < kept.sum() < len(kept)
+
+
+# window-stratified counts (one sampling pass shared by many weightings s)
+
+def test_stratified_weights_closed_form():
+    w = oracle.stratified_weights([1.0, 1.0, 2.0], 3)
+    assert w.tolist() == [round(3 * 0.25 * 2 ** 24), round(3 * 0.25 * 2 ** 24), round(3 * 0.5 * 2 ** 24)]
+    assert oracle.stratified_weights(np.ones(10), 10).tolist() == [2 ** 24] * 10
+    assert oracle.stratified_weights([0.0, 1.0], 2).tolist() == [0, 2 ** 25]
+
+
+def test_stratified_uniform_s_is_the_plain_count():
+    """With s uniform every weight is exactly 2^24: K = 2^24 x the count of
+    the plain sampler with uniform s."""
+    g = synth.sbm(300, 3, 0.06, 0.01, seed=2)
+    T, S = 6, 30.0 * g.n_arcs
+    x, y, r, c = oracle.stratified_counts(g.indptr, g.indices, T, S, 8)
+    assert np.all((r >= 1) & (r <= T))
+    px, py, K = oracle.stratified_estimate(x, y, r, c, np.ones(T), T)
+    qx, qy, qc = oracle.sparsifier_counts(g.indptr, g.indices, T, np.ones(T), S, 8)
+    assert np.array_equal(px, qx) and np.array_equal(py, qy)
+    assert np.array_equal(K, qc.astype(np.uint64) << np.uint64(24))
+    assert int(c.sum()) == oracle.count_samples(g.n_arcs, S, 8)
+
+
+def test_stratified_estimate_is_unbiased():
+    """E[K_s] = S / vol sum_r s~_r [D P^r] (unordered) with s~_r = w_r 2^-24 / T,
+    for a weighting far from uniform; z-scores against the exact law with the
+    variance sum_r (w_r 2^-24)^2 E[C_r]."""
+    g = synth.lollipop_tiny()
+    T = 5
+    s = [0.05, 0.6, 0.0, 0.3, 0.05]
+    S = 40000.0 * g.n_arcs
+    x, y, r, c = oracle.stratified_counts(g.indptr, g.indices, T, S, 31)
+    px, py, K = oracle.stratified_estimate(x, y, r, c, s, T)
+    w = oracle.stratified_weights(s, T).astype(np.float64) * 2.0 ** -24
+    EK = np.zeros((g.n, g.n))
+    VK = np.zeros((g.n, g.n))
+    for rr in range(1, T + 1):
+        e = np.zeros(T)
+        e[rr - 1] = 1.0
+        Er = _expected_counts(g, T, e, S / T)      # E[C_r] (unordered)
+        EK += w[rr - 1] * Er
+        VK += w[rr - 1] ** 2 * Er
+    Kd = np.zeros((g.n, g.n))
+    Kd[px, py] = K.astype(np.float64) * 2.0 ** -24
+    iu = np.triu_indices(g.n)
+    m = VK[iu] > 0
+    z = (Kd[iu][m] - EK[iu][m]) / np.sqrt(VK[iu][m])
+    assert np.max(np.abs(z)) < 6
+    assert np.all(Kd[iu][~m] == 0)
+    # the expectation is the plain sampler's with weights s~ (= s up to rounding)
+    np.testing.assert_allclose(EK[iu], _expected_counts(g, T, s, S)[iu], rtol=1e-6, atol=1e-9)
+
+
+def test_stratified_sparsifier_structure():
+    g = synth.sbm(300, 3, 0.06, 0.01, seed=2)
+    T, S = 6, 30.0 * g.n_arcs
+    sp = oracle.stratified_sparsifier(g.indptr, g.indices, T, [0.5, 0.1, 0.1, 0.1, 0.1, 0.1], S, 8)
+    # the keep rule of Eq. 1 on K = K_s 2^-24
+    deg = np.diff(g.indptr).astype(np.float64)
+    a_off, a_diag = oracle.netmf_scale(deg.sum(), S)
+    alpha = np.where(sp["x"] == sp["y"], a_diag, a_off)
+    v = (sp["K"].astype(np.float64) * 2.0 ** -24 * alpha) / (deg[sp["x"]] * deg[sp["y"]])
+    assert np.array_equal(sp["keep"], v > 1.0)
+    n = g.n
+    M = np.zeros((n, n))
+    for i in range(n):
+        M[i, sp["indices"][sp["indptr"][i]:sp["indptr"][i + 1]]] = sp["data"][sp["indptr"][i]:sp["indptr"][i + 1]]
+    np.testing.assert_array_equal(M, M.T)
