@@ -104,6 +104,8 @@ typedef struct {
     uint64_t *weight;          /* device [nnz], with edge downsampling: sum of 1/p_e over the pair's
                                   kept draws in units of 2^-32, each 1/p_e rounded to
                                   floor(2^32/p_e + 1/2) (exact integer sums); else NULL */
+    uint8_t *window;           /* device [nnz], with LNE_OPT_STRATIFIED: the window length r of
+                                  each (x, y, r) entry (sorted by x, y, r); else NULL */
 } lne_counts;
 
 typedef struct lne_ctx lne_ctx;
@@ -122,6 +124,15 @@ typedef struct lne_ctx lne_ctx;
                                     2 = always; same values, different summation order */
 #define LNE_OPT_TUNE_WORKERS 3   /* host worker threads (each with its own stream and workspace)
                                     of lne_tune_tasks, 1..16 (default 4) */
+#define LNE_OPT_STRATIFIED   5   /* 1: window-stratified sampling (not in the paper): draws take
+                                    r ~ U{1..T} and pair counts C_r are kept per r; a parameter
+                                    set's matrix uses K = sum_r w_r C_r 2^-24 with
+                                    w_r = floor(T (s_r / sum(s)) 2^24 + 1/2), an unbiased
+                                    estimate of its count, so lne_tune_batch / lne_tune_tasks
+                                    sample once per (T, S, seed) for all window weightings.
+                                    lne_sparsifier_counts then returns (x, y, r, count) entries.
+                                    Any n with 2 ceil(log2 n) + 4 <= 64; no edge downsampling.
+                                    0 (default): the paper's sampler */
 
 /* Create a context on CUDA device `device`. The context owns its workspace. */
 int lne_create(lne_ctx **out, int device);

@@ -239,11 +239,15 @@ def stratified_counts(indptr, indices, T, S, seed):
 
 
 def stratified_weights(s, T) -> np.ndarray:
-    """w_r = floor(T s_r / sum(s) 2^24 + 1/2): the importance weight of window
+    """w_r = floor(T (s_r / sum(s)) 2^24 + 1/2), each step one FP64 rounding and
+    the sum taken left to right: the importance weight of window
     r (its probability under s over its probability 1/T under the uniform
     draw) in 2^-24 units, exact integers (w_r < 2^28 for T <= 16)."""
     s = np.asarray(s, dtype=np.float64)[:T]
-    return np.floor(T * (s / s.sum()) * 16777216.0 + 0.5).astype(np.uint64)
+    tot = 0.0
+    for v in s:              # left to right, as the window thresholds sum
+        tot += float(v)
+    return np.floor(T * (s / tot) * 16777216.0 + 0.5).astype(np.uint64)
 
 
 def stratified_estimate(x, y, r, cnt, s, T):

@@ -168,6 +168,7 @@ struct lne_ctx {
     lne::PropBatchGraph *prop_graph = nullptr;
     int tune_workers = 4;
     int dense_mode = 0;
+    int stratified = 0;
     std::vector<std::unique_ptr<lne::TuneWorker>> workers;
     lne::Surrogate surrogate;
 };
@@ -315,6 +316,11 @@ int lne_set_option(lne_ctx *ctx, int option, int64_t value) {
         ctx->dense_mode = (int)value;
         return LNE_OK;
     }
+    if (option == LNE_OPT_STRATIFIED) {
+        if (value != 0 && value != 1) return finish(ctx, lne::fail(LNE_ERR_INVALID, "stratified must be 0 or 1"));
+        ctx->stratified = (int)value;
+        return LNE_OK;
+    }
     if (option == LNE_OPT_TUNE_WORKERS) {
         if (value < 1 || value > 16) return finish(ctx, lne::fail(LNE_ERR_INVALID, "tuning workers must be 1..16"));
         ctx->tune_workers = (int)value;
@@ -399,6 +405,7 @@ int lne_sample_pairs(lne_ctx *ctx, const lne_graph *g, const lne_params *p, int6
     if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
     sp.aggregation = ctx->aggregation;
     sp.ds_C = p->downsample_C;
+    sp.stratified = ctx->stratified;
     if (rc == 0) rc = lne::sample_pairs(ctx->ws, view(g), sp, arc_begin, arc_end, u1_dev, v1_dev, capacity,
                                         count_out, st);
     return finish(ctx, rc);
@@ -417,6 +424,7 @@ int lne_sparsifier_counts(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
     if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
     sp.aggregation = ctx->aggregation;
     sp.ds_C = p->downsample_C;
+    sp.stratified = ctx->stratified;
     lne::CountsResult r;
     if (rc == 0) rc = lne::sparsifier_counts(ctx->ws, view(g), sp, &r, st);
     if (rc == 0) {
@@ -426,6 +434,7 @@ int lne_sparsifier_counts(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
         out->count = r.cnt;
         out->total_samples = r.total_samples;
         out->weight = r.weight;
+        out->window = r.window;
     }
     return finish(ctx, rc);
 }
@@ -442,6 +451,7 @@ int lne_sparsifier_csr(lne_ctx *ctx, const lne_graph *g, const lne_params *p, ln
     if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
     sp.aggregation = ctx->aggregation;
     sp.ds_C = p->downsample_C;
+    sp.stratified = ctx->stratified;
     lne::CsrResult r;
     if (rc == 0) rc = lne::sparsifier_csr(ctx->ws, view(g), sp, &r, st);
     if (rc == 0) {
@@ -584,6 +594,7 @@ int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_de
     if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
     sp.aggregation = ctx->aggregation;
     sp.ds_C = p->downsample_C;
+    sp.stratified = ctx->stratified;
     lne::CsrResult M;
     if (rc == 0) rc = lne::sparsifier_csr(ctx->ws, view(g), sp, &M, st);
     float *X0 = nullptr;
@@ -614,7 +625,8 @@ int lne_tune_batch(lne_ctx *ctx, const lne_graph *g, const lne_params *cands, in
     if (rc == 0) rc = check_graph_device(g, st);
     if (rc == 0 && !ctx->prop_graph) ctx->prop_graph = lne::new_prop_cache();
     if (rc == 0)
-        rc = lne::tune_batch(ctx->ws, ctx->prop_graph, ctx->spmm_tune, ctx->aggregation, ctx->dense_mode, view(g),
+        rc = lne::tune_batch(ctx->ws, ctx->prop_graph, ctx->spmm_tune, ctx->aggregation, ctx->dense_mode,
+                             ctx->stratified, view(g),
                              cands, ncand,
                              labels_dev, L, train_dev, n_train, test_dev, n_test, C, iters, macro_f1, micro_f1,
                              X_dev, st);
@@ -654,7 +666,8 @@ int lne_tune_tasks(lne_ctx *ctx, const lne_task *tasks, int32_t ntasks, const ln
     }
     if (rc == 0)
         rc = lne::tune_tasks(ctx->workers, ctx->tune_workers, ctx->device, ctx->spmm_tune.forced, ctx->aggregation,
-                             ctx->dense_mode, tt.data(), ntasks, cands, ncand, C, iters, macro_f1, micro_f1);
+                             ctx->dense_mode, ctx->stratified, tt.data(), ntasks, cands, ncand, C, iters, macro_f1,
+                             micro_f1);
     return finish(ctx, rc);
 }
 

@@ -71,6 +71,12 @@ struct SamplerSpec {
     float off_hi = 0, off_lo = 0, diag_hi = 0, diag_lo = 0;   // alpha as float pairs
     int aggregation = 0;          // LNE_AGG_* (0 = automatic)
     double ds_C = 0.0;            // edge downsampling constant C (0 = off)
+    // the arguments the spec was built from (window-stratified sampling
+    // samples with uniform s and applies these weights afterwards)
+    double s_raw[16] = {0};
+    double S = 0.0, b = 1.0;
+    uint64_t seed = 0;
+    int stratified = 0;           // 1: M from window-stratified counts
 };
 
 int make_sampler_spec(const GraphView &g, int T, const double *s, double S, double b, uint64_t seed,
@@ -87,6 +93,7 @@ struct CountsResult {
     int32_t *y = nullptr;
     uint32_t *cnt = nullptr;      // multiplicities (no downsampling)
     uint64_t *weight = nullptr;   // summed 1/p_e in 2^-32 units (edge downsampling)
+    uint8_t *window = nullptr;    // window length r of each entry (stratified counts)
 };
 int sparsifier_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out,
                       cudaStream_t st);
@@ -205,7 +212,10 @@ struct SpmmTune {
 int spmm_threads_for(SpmmTune &tc, Workspace &ws, const GraphView &g, const float *X, int C, float *Y,
                      cudaStream_t st);
 // Batched tuning over ncand candidate parameter sets (tune.cu).
-int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregation, int dense_mode, const GraphView &g,
+// stratified: the candidates' sparsifiers come from window-stratified counts,
+// sampled once per (T, S, seed) and shared.
+int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregation, int dense_mode, int stratified,
+               const GraphView &g,
                const lne_params *cands, int ncand, const uint8_t *labels, int L, const int32_t *train,
                int64_t n_train, const int32_t *test, int64_t n_test, double Creg, int iters, double *macro,
                double *micro, float *X_out, cudaStream_t st);
@@ -228,8 +238,8 @@ struct TuneTask {
     int64_t n_test = 0;
 };
 int tune_tasks(std::vector<std::unique_ptr<TuneWorker>> &workers, int nworkers, int device, int forced_threads,
-               int aggregation, int dense_mode, const TuneTask *tasks, int ntasks, const lne_params *cands, int ncand, double Creg,
-               int iters, double *macro, double *micro);
+               int aggregation, int dense_mode, int stratified, const TuneTask *tasks, int ntasks,
+               const lne_params *cands, int ncand, double Creg, int iters, double *macro, double *micro);
 
 // Surrogate regression network of the tuning search (surrogate.cu):
 // 30 -> 256 ReLU -> 256 ReLU -> 1, FP32 master weights, bfloat16 copies.
@@ -275,6 +285,32 @@ int radix_sort_u64(Workspace &ws, uint64_t *keys, uint64_t *keys_alt, uint32_t *
 // Unique keys of a sorted array and their multiplicities.
 int run_length(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t *ukeys, uint32_t *counts,
                int64_t *nunique, cudaStream_t st);
+// Window-stratified counts (sampler.cu): draws take r ~ U{1..T}; per distinct
+// pair its (r, count) entries. One sampling pass serves every weighting s: a
+// candidate's matrix uses K_s = sum_r w_r C_r, w_r = floor(T s_r / sum(s)
+// 2^24 + 1/2) (2^-24 units). Buffers live in the workspace ("strat.*").
+struct Strata {
+    int64_t total = 0;                 // draws
+    int64_t U = 0;                     // distinct (pair, r)
+    int64_t P = 0;                     // distinct pairs
+    const uint64_t *pair = nullptr;    // [P] (x << B) | y, ascending
+    const int64_t *seg = nullptr;      // [P + 1] entries of pair p: seg[p] .. seg[p + 1] - 1
+    const uint8_t *r = nullptr;        // [U] window length of each entry
+    const uint32_t *cnt = nullptr;     // [U] its count
+    int T = 0, B = 0;
+    double S = 0.0;
+    uint64_t seed = 0;
+    const int64_t *g_indptr = nullptr;   // the graph the strata belong to
+    int64_t g_n = 0, g_nnz = 0;
+};
+// Samples the strata for sp's (T, S, seed) (the window weights of sp are
+// ignored; the draw of r is uniform).
+int stratified_sample(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Strata *out, cudaStream_t st);
+// The candidate sp's sparsifier (its s, b) from the strata.
+int stratified_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, const Strata &S, CsrResult *out,
+                   cudaStream_t st);
+void stratified_release(Workspace &ws);
+
 // Number of keys of a sorted array below `key` (synchronises).
 int count_below(Workspace &ws, const uint64_t *keys, int64_t n, uint64_t key, int64_t *count, cudaStream_t st);
 // Unique keys of a sorted array and, per run, the sum of w[arcs[i]] over it.

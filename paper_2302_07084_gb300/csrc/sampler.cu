@@ -64,6 +64,7 @@ struct WalkArgs {
     // coin word < ds_thr[arc]; a kept draw weighs ds_w[arc] (2^-32 units)
     const uint64_t *ds_thr;
     const uint64_t *ds_w;
+    int strat;                    // MODE 3 keys carry r - 1 in 4 low bits
 };
 
 __device__ __forceinline__ uint32_t arc_count(const WalkArgs &A, int64_t arc) {
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
             if (u1) reinterpret_cast<uint32_t *>(u1)[out0 + s] = (uint32_t)arc;
         }
     };
-    auto emit = [&](uint32_t s, int64_t arc, int32_t pu, int32_t pv) {
+    auto emit = [&](uint32_t s, int64_t arc, int32_t pu, int32_t pv, uint32_t r) {
         if (MODE == 0) {
             u1[out0 + s] = pu;
             v1[out0 + s] = pv;
@@ -415,7 +416,8 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
                 atomicAdd(reinterpret_cast<uint32_t *>(keys) + at, 1u);
         } else if (MODE == 3) {
             const uint32_t x = (uint32_t)min(pu, pv), y = (uint32_t)max(pu, pv);
-            keys[out0 + s] = ((KeyT)x << A.B) | (KeyT)y;
+            const KeyT key = ((KeyT)x << A.B) | (KeyT)y;
+            keys[out0 + s] = A.strat ? (key << 4) | (KeyT)(r - 1u) : key;
             if (u1) reinterpret_cast<uint32_t *>(u1)[out0 + s] = (uint32_t)arc;   // the draw's arc
         } else {
             const uint32_t x = (uint32_t)min(pu, pv), y = (uint32_t)max(pu, pv);
@@ -516,10 +518,10 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
             StepAll<0>::run(A, d0, d1, max(d0.steps, d1.steps));
             int32_t pu, pv;
             draw_end(d0, &pu, &pv);
-            emit(s0, a0 + lo0, pu, pv);
+            emit(s0, a0 + lo0, pu, pv, (pk0 >> 11) & 31);
             if (has1) {
                 draw_end(d1, &pu, &pv);
-                emit(s1, a0 + lo1, pu, pv);
+                emit(s1, a0 + lo1, pu, pv, (pk1 >> 11) & 31);
             }
         }
         __syncthreads();
@@ -697,28 +699,29 @@ __device__ __forceinline__ float netmf_value(uint32_t cnt, int64_t dx, int64_t d
     return (float)(log(p) - log(q));
 }
 
-// Eq. 1 entry for a downsampled pair: K = (summed 1/p_e, 2^-32 units) * 2^-32,
+// Eq. 1 entry from a fixed-point count: K = wsum * unit (2^-32 for summed
+// downsampling weights 1/p_e, 2^-24 for stratified estimates),
 // v = fl(fl(K alpha) / fl(d_x d_y)) in FP64, kept iff v > 1, value log v as
 // float32. Fast path as for counts: the 64-bit sum is split into a float pair
 // (kh + kl, exact to 2^-48 relative), D = K alpha - q in FP32 with fmaf, so D
 // carries an error of ~1e-7 |D| + 1e-14 q; when |D| > 1e-5 q its sign is the
 // FP64 decision. Otherwise the exact FP64 rule (no division) decides.
-__device__ __forceinline__ float netmf_value_w(uint64_t wsum, int64_t dx, int64_t dy, bool diag,
-                                               const NetmfConst &k) {
+// unit_f / unit_d: the power of two that one unit of wsum stands for.
+__device__ __forceinline__ float netmf_value_fixed(uint64_t wsum, float unit_f, double unit_d, int64_t dx,
+                                                   int64_t dy, bool diag, const NetmfConst &k) {
     const int64_t q64 = dx * dy;
     if (q64 < (1ll << 24)) {
         const float kh = __ull2float_rn(wsum);
         // kh is an integer below 2^64 (unless wsum rounds up to 2^64): the
         // residual wsum - kh is exact in 64-bit arithmetic
         const float kl = kh < 1.8446744e19f ? (float)(int64_t)(wsum - __float2ull_rn(kh)) : 0.f;
-        const float two_m32 = 2.3283064e-10f;   // 2^-32 exactly
-        const float khs = kh * two_m32, kls = kl * two_m32;
+        const float khs = kh * unit_f, kls = kl * unit_f;
         const float qf = (float)q64;
         const float hi = diag ? k.diag_hi : k.off_hi, lo = diag ? k.diag_lo : k.off_lo;
         const float dq = fmaf(khs, hi, -qf) + fmaf(khs, lo, kls * hi);
         if (fabsf(dq) > 1e-5f * qf) return dq > 0.f ? log1pf(__fdiv_rn(dq, qf)) : 0.f;
     }
-    const double K = __dmul_rn(__ull2double_rn(wsum), 2.3283064365386963e-10);   // 2^-32
+    const double K = __dmul_rn(__ull2double_rn(wsum), unit_d);
     const double p = __dmul_rn(K, diag ? k.a_diag : k.a_off);
     const double q = __ll2double_rn(q64);
     if (!(p > q)) return 0.f;
@@ -730,6 +733,11 @@ __device__ __forceinline__ float netmf_value_w(uint64_t wsum, int64_t dx, int64_
     }
     if (p < 1e30) return logf(__fdiv_rn((float)p, (float)q));
     return (float)(log(p) - log(q));
+}
+
+__device__ __forceinline__ float netmf_value_w(uint64_t wsum, int64_t dx, int64_t dy, bool diag,
+                                               const NetmfConst &k) {
+    return netmf_value_fixed(wsum, 2.3283064e-10f, 2.3283064365386963e-10, dx, dy, diag, k);   // 2^-32
 }
 
 // Weighted table -> the float-bits value table (upper triangle).
@@ -1248,6 +1256,7 @@ WalkArgs make_walk_args(const GraphView &g, const SamplerSpec &sp) {
     for (int i = A.T_eff; i < 16; ++i) A.thr32[i] = 0xFFFFFFFFu;
     A.ds_thr = nullptr;
     A.ds_w = nullptr;
+    A.strat = sp.stratified;
     A.base_magic = sp.base > 0 ? (~0ull) / sp.base + 1ull : 0ull;
     A.rmagic[0] = 0;
     for (int r = 1; r <= 16; ++r) A.rmagic[r] = (~0ull) / (uint64_t)r + 1ull;
@@ -1349,6 +1358,10 @@ int make_sampler_spec(const GraphView &g, int T, const double *s, double S, doub
     sp.k0 = (uint32_t)(seed & 0xFFFFFFFFu);
     sp.k1 = (uint32_t)(seed >> 32);
     sp.T = T;
+    for (int t = 0; t < T; ++t) sp.s_raw[t] = s[t];
+    sp.S = S;
+    sp.b = b;
+    sp.seed = seed;
     double total = 0.0;
     for (int t = 0; t < T; ++t) {
         if (!(s[t] >= 0.0)) return fail(LNE_ERR_INVALID, "window weights must be >= 0");
@@ -1698,24 +1711,21 @@ int sort_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Counts
     return 0;
 }
 
-int sort_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out, cudaStream_t st) {
-    // a previous sparsifier's arrays are rebuilt below: free them before the
-    // sort's peak (tens of GB for billions of samples)
-    ws.release("csr.indices");
-    ws.release("csr.data");
-    SortRaw R;
-    LNE_TRY(sort_raw(ws, g, sp, &R, st));
-    const int64_t U = R.U, n = g.n;
+// Symmetric CSR from U ascending unique pair keys uk and their Eq. 1 value
+// bits val (0 = dropped), with per-tile (kPathTile) kept / kept off-diagonal
+// counts tk / tm. uk and val (workspace buffers uk_name / val_name) serve as
+// spare buffers of the mirrored sort and are released.
+int assemble_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, uint64_t *uk, uint32_t *val, int64_t U,
+                 const uint32_t *tk, const uint32_t *tm, const char *uk_name, const char *val_name, CsrResult *out,
+                 cudaStream_t st) {
+    const int64_t n = g.n;
     const int64_t ntiles = std::max<int64_t>(1, ceil_div(U, (int64_t)kPathTile));
     const unsigned egrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 152 * 16));
-    uint32_t *tk = nullptr, *tm = nullptr, *deg = nullptr, *dlen = nullptr, *rowlen = nullptr;
+    uint32_t *dlen = nullptr, *rowlen = nullptr;
     int64_t *ko = nullptr, *mo = nullptr, *first = nullptr, *end = nullptr;
     unsigned long long *dstart = nullptr;
-    LNE_TRY(ws.get("path.tk", (size_t)ntiles, &tk));
-    LNE_TRY(ws.get("path.tm", (size_t)ntiles, &tm));
     LNE_TRY(ws.get("path.ko", (size_t)ntiles + 1, &ko));
     LNE_TRY(ws.get("path.mo", (size_t)ntiles + 1, &mo));
-    LNE_TRY(ws.get("path.deg", (size_t)n, &deg));
     LNE_TRY(ws.get("path.dlen", (size_t)n, &dlen));
     LNE_TRY(ws.get("path.rowlen", (size_t)n, &rowlen));
     LNE_TRY(ws.get("path.dstart", (size_t)n, &dstart));
@@ -1725,15 +1735,6 @@ int sort_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult
     LNE_CUDA_TRY(cudaMemsetAsync(dlen, 0, sizeof(uint32_t) * n, st));
     LNE_CUDA_TRY(cudaMemsetAsync(end, 0, sizeof(int64_t) * n, st));
     LNE_CUDA_TRY(cudaMemsetAsync(dstart, 0xFF, sizeof(unsigned long long) * n, st));
-    {
-        LNE_TRACE("path_value", st);
-        degree_kernel<<<egrid, 256, 0, st>>>(g.indptr, n, deg);
-        LNE_LAUNCH_CHECK();
-        // values overwrite the counts (the counts are not needed afterwards)
-        path_value_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, R.w, U, sp.B, deg,
-                                                                    netmf_const(sp), tk, tm);
-        LNE_LAUNCH_CHECK();
-    }
     LNE_TRY(scan_exclusive_u32_to_i64(tk, ko, ntiles, st));
     LNE_TRY(scan_exclusive_u32_to_i64(tm, mo, ntiles, st));
     int64_t nk = 0, nm = 0;
@@ -1749,16 +1750,16 @@ int sort_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult
     LNE_TRY(ws.get("sort.mv", (size_t)std::max<int64_t>(nm, 1), &mv));
     {
         LNE_TRACE("path_rows", st);
-        path_rows_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, U, sp.B, ko, mo, dlen, dstart,
-                                                                   dcol, dval, mk, mv);
+        path_rows_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(uk, val, U, sp.B, ko, mo, dlen, dstart, dcol,
+                                                                   dval, mk, mv);
         LNE_LAUNCH_CHECK();
     }
     // mirrored entries sorted by (row y, column x); the unique keys and the
     // values are no longer needed and serve as the sort's spare buffers
     bool in_alt = false;
-    LNE_TRY(radix_sort_u64(ws, mk, R.uk, mv, R.cnt, nm, 2 * sp.B, &in_alt, st));
-    const uint64_t *smk = in_alt ? R.uk : mk;
-    const uint32_t *smv = in_alt ? R.cnt : mv;
+    LNE_TRY(radix_sort_u64(ws, mk, uk, mv, val, nm, 2 * sp.B, &in_alt, st));
+    const uint64_t *smk = in_alt ? uk : mk;
+    const uint32_t *smv = in_alt ? val : mv;
     const unsigned mgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nm, 256), 152 * 16));
     {
         LNE_TRACE("path_rows", st);
@@ -1778,8 +1779,8 @@ int sort_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult
         ws.release("sort.mk");
         ws.release("sort.mv");
     } else {
-        ws.release(R.uk_name);
-        ws.release("sort.cnt");
+        ws.release(uk_name);
+        ws.release(val_name);
     }
     LNE_TRY(ws.get("csr.indices", (size_t)std::max<int64_t>(nnz, 1), &out->indices));
     LNE_TRY(ws.get("csr.data", (size_t)std::max<int64_t>(nnz, 1), &out->data));
@@ -1796,9 +1797,37 @@ int sort_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult
     }
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
     sort_release(ws);
+    ws.release(uk_name);
+    ws.release(val_name);
     out->n = n;
     out->nnz = nnz;
     return 0;
+}
+
+int sort_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out, cudaStream_t st) {
+    // a previous sparsifier's arrays are rebuilt below: free them before the
+    // sort's peak (tens of GB for billions of samples)
+    ws.release("csr.indices");
+    ws.release("csr.data");
+    SortRaw R;
+    LNE_TRY(sort_raw(ws, g, sp, &R, st));
+    const int64_t U = R.U, n = g.n;
+    const int64_t ntiles = std::max<int64_t>(1, ceil_div(U, (int64_t)kPathTile));
+    const unsigned egrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 152 * 16));
+    uint32_t *tk = nullptr, *tm = nullptr, *deg = nullptr;
+    LNE_TRY(ws.get("path.tk", (size_t)ntiles, &tk));
+    LNE_TRY(ws.get("path.tm", (size_t)ntiles, &tm));
+    LNE_TRY(ws.get("path.deg", (size_t)n, &deg));
+    {
+        LNE_TRACE("path_value", st);
+        degree_kernel<<<egrid, 256, 0, st>>>(g.indptr, n, deg);
+        LNE_LAUNCH_CHECK();
+        // values overwrite the counts (the counts are not needed afterwards)
+        path_value_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, R.w, U, sp.B, deg,
+                                                                    netmf_const(sp), tk, tm);
+        LNE_LAUNCH_CHECK();
+    }
+    return assemble_csr(ws, g, sp, R.uk, R.cnt, U, tk, tm, R.uk_name, "sort.cnt", out, st);
 }
 
 bool use_table(const GraphView &g, const SamplerSpec &sp) {
@@ -1931,6 +1960,123 @@ int table_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResul
     return 0;
 }
 
+// ---- window-stratified counts --------------------------------------------
+
+struct StratW {
+    uint32_t w[16];   // w_r for r = 1..T (index r - 1), 2^-24 units
+};
+
+// Sorted unique (pair << 4 | r - 1) keys -> pair keys (for the run lengths of
+// the pairs) and window lengths.
+__global__ void strat_split_kernel(const uint64_t *__restrict__ ukr, int64_t U, uint64_t *__restrict__ pairkey,
+                                   uint8_t *__restrict__ r) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < U; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = ukr[i];
+        pairkey[i] = k >> 4;
+        r[i] = (uint8_t)((k & 15u) + 1u);
+    }
+}
+
+// Stratified counts as (x, y, r, count) entries.
+__global__ void strat_decode_kernel(const uint64_t *__restrict__ ukr, int64_t U, int B, int32_t *__restrict__ x,
+                                    int32_t *__restrict__ y, uint8_t *__restrict__ r) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < U; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = ukr[i];
+        x[i] = (int32_t)(k >> (B + 4));
+        y[i] = (int32_t)((k >> 4) & ((1ull << B) - 1ull));
+        r[i] = (uint8_t)((k & 15u) + 1u);
+    }
+}
+
+// K_s = sum over the pair's entries of w_r C_r (exact 64-bit sum), its Eq. 1
+// value bits, and per tile the kept and kept off-diagonal pair counts (the
+// layout path_value_kernel gives the CSR assembly).
+__global__ void __launch_bounds__(kPathThreads) strat_value_kernel(
+    const uint64_t *__restrict__ pair, const int64_t *__restrict__ seg, const uint8_t *__restrict__ rr,
+    const uint32_t *__restrict__ cnt, int64_t P, int B, const uint32_t *__restrict__ deg, NetmfConst kc, StratW w,
+    uint32_t *__restrict__ val, uint32_t *__restrict__ tile_kept, uint32_t *__restrict__ tile_mir) {
+    __shared__ uint32_t s_k, s_m;
+    if (threadIdx.x == 0) s_k = s_m = 0;
+    __syncthreads();
+    uint32_t ck = 0, cm = 0;
+    const int64_t t0 = (int64_t)blockIdx.x * kPathTile;
+    for (int j = threadIdx.x; j < kPathTile; j += kPathThreads) {
+        const int64_t u = t0 + j;
+        if (u >= P) break;
+        uint64_t K = 0;
+        for (int64_t e = seg[u]; e < seg[u + 1]; ++e) K += (uint64_t)w.w[rr[e] - 1] * cnt[e];
+        const uint64_t k = pair[u];
+        const uint32_t x = (uint32_t)(k >> B), y = (uint32_t)(k & ((1ull << B) - 1ull));
+        const float v = netmf_value_fixed(K, 5.9604645e-8f, 5.9604644775390625e-08, __ldg(deg + x), __ldg(deg + y),
+                                          x == y, kc);   // 2^-24
+        val[u] = __float_as_uint(v);
+        if (v > 0.f) {
+            ++ck;
+            cm += x != y;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ck += __shfl_xor_sync(0xffffffffu, ck, o);
+        cm += __shfl_xor_sync(0xffffffffu, cm, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&s_k, ck);
+        atomicAdd(&s_m, cm);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tile_kept[blockIdx.x] = s_k;
+        tile_mir[blockIdx.x] = s_m;
+    }
+}
+
+// Draws with r ~ U{1..T} as keys (pair << 4 | r - 1), sorted, as unique keys
+// ("sort.k0"/"sort.k1", named in *uk_name) with counts ("sort.cnt").
+int strat_keys(Workspace &ws, const GraphView &g, const SamplerSpec &sp, int64_t *total_out, uint64_t **ukr,
+               uint64_t **spare, uint32_t **cnt, int64_t *U, cudaStream_t st) {
+    if (2 * sp.B + 4 > 64) return fail(LNE_ERR_UNSUPPORTED, "stratified keys need 2 ceil(log2 n) + 4 <= 64 bits");
+    if (sp.ds_C > 0.0) return fail(LNE_ERR_UNSUPPORTED, "stratified counts do not combine with edge downsampling");
+    SamplerSpec su;
+    std::vector<double> ones((size_t)sp.T, 1.0);
+    LNE_TRY(make_sampler_spec(g, sp.T, ones.data(), sp.S, sp.b, sp.seed, &su));
+    su.stratified = 1;
+    WalkArgs A = make_walk_args(g, su);
+    LNE_TRY(attach_vinfo(ws, g, &A, st));
+    const int tile_arcs = choose_tile_arcs(g.nnz, (double)su.base + 0.5);
+    int64_t *tile_off = nullptr;
+    int64_t total = 0;
+    LNE_TRY(tile_offsets(ws, A, 0, g.nnz, tile_arcs, &tile_off, &total, st));
+    uint64_t *k0 = nullptr, *k1 = nullptr;
+    LNE_TRY(ws.get("sort.k0", (size_t)std::max<int64_t>(total, 1), &k0));
+    LNE_TRY(ws.get("sort.k1", (size_t)std::max<int64_t>(total, 1), &k1));
+    const int64_t ntiles = ceil_div(g.nnz, tile_arcs);
+    LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint64_t, 3>));
+    {
+        LNE_TRACE("walk_keys", st);
+        walk_emit_kernel<uint64_t, 3><<<(unsigned)ntiles, kWalkThreads, walk_smem_bytes(tile_arcs, 0), st>>>(
+            A, 0, g.nnz, tile_arcs, tile_off, k0, nullptr, nullptr, nullptr, 0);
+        LNE_LAUNCH_CHECK();
+    }
+    bool in_alt = false;
+    LNE_TRY(radix_sort_u64(ws, k0, k1, nullptr, nullptr, total, 2 * su.B + 4, &in_alt, st));
+    uint64_t *sorted = in_alt ? k1 : k0, *other = in_alt ? k0 : k1;
+    ws.release("sort.offs");
+    LNE_TRY(ws.get("sort.cnt", (size_t)std::max<int64_t>(total, 1), cnt));
+    LNE_TRY(run_length(ws, sorted, total, other, *cnt, U, st));
+    *total_out = total;
+    *ukr = other;
+    *spare = sorted;
+    return 0;
+}
+
+uint32_t strat_weight(const SamplerSpec &sp, int r) {
+    // w_r = floor(T (s_r / sum(s)) 2^24 + 1/2), the sum left to right
+    double tot = 0.0;
+    for (int t = 0; t < sp.T; ++t) tot += sp.s_raw[t];
+    return (uint32_t)std::floor((double)sp.T * (sp.s_raw[r] / tot) * 16777216.0 + 0.5);
+}
+
 }  // namespace
 
 CsrView product_view(const CsrResult &M, int dense_mode) {
@@ -1948,8 +2094,118 @@ CsrView product_view(const CsrResult &M, int dense_mode) {
     return v;
 }
 
+int stratified_sample(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Strata *out, cudaStream_t st) {
+    stratified_release(ws);
+    int64_t total = 0, U = 0, P = 0;
+    uint64_t *ukr = nullptr, *spare = nullptr;
+    uint32_t *cnt = nullptr;
+    LNE_TRY(strat_keys(ws, g, sp, &total, &ukr, &spare, &cnt, &U, st));
+    uint8_t *r = nullptr;
+    uint32_t *scnt = nullptr, *seglen = nullptr;
+    uint64_t *pair = nullptr;
+    int64_t *seg = nullptr;
+    LNE_TRY(ws.get("strat.r", (size_t)std::max<int64_t>(U, 1), &r));
+    LNE_TRY(ws.get("strat.cnt", (size_t)std::max<int64_t>(U, 1), &scnt));
+    if (U > 0) {
+        LNE_TRACE("strat_split", st);
+        strat_split_kernel<<<(unsigned)std::min<int64_t>(ceil_div(U, 256), 152 * 16), 256, 0, st>>>(ukr, U, spare,
+                                                                                                      r);
+        LNE_LAUNCH_CHECK();
+        LNE_CUDA_TRY(cudaMemcpyAsync(scnt, cnt, sizeof(uint32_t) * U, cudaMemcpyDeviceToDevice, st));
+    }
+    // the pair keys are sorted with their windows: pairs are runs of them
+    LNE_TRY(ws.get("strat.pair", (size_t)std::max<int64_t>(U, 1), &pair));
+    LNE_TRY(ws.get("strat.seglen", (size_t)std::max<int64_t>(U, 1), &seglen));
+    LNE_TRY(run_length(ws, spare, U, pair, seglen, &P, st));
+    LNE_TRY(ws.get("strat.seg", (size_t)P + 1, &seg));
+    LNE_TRY(scan_exclusive_u32_to_i64(seglen, seg, P, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    for (const char *nm : {"sort.k0", "sort.k1", "sort.cnt", "strat.seglen", "rle.tile_cnt", "rle.tile_off"})
+        ws.release(nm);
+    out->total = total;
+    out->U = U;
+    out->P = P;
+    out->pair = pair;
+    out->seg = seg;
+    out->r = r;
+    out->cnt = scnt;
+    out->T = sp.T;
+    out->B = sp.B;
+    out->S = sp.S;
+    out->seed = sp.seed;
+    out->g_indptr = g.indptr;
+    out->g_n = g.n;
+    out->g_nnz = g.nnz;
+    return 0;
+}
+
+int stratified_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, const Strata &S, CsrResult *out,
+                   cudaStream_t st) {
+    if (S.T != sp.T || S.B != sp.B || S.g_n != g.n || S.g_nnz != g.nnz)
+        return fail(LNE_ERR_INVALID, "strata belong to another graph or window size");
+    ws.release("csr.indices");
+    ws.release("csr.data");
+    StratW w = {};
+    for (int r = 0; r < sp.T; ++r) w.w[r] = strat_weight(sp, r);
+    const int64_t P = S.P, n = g.n;
+    const int64_t ntiles = std::max<int64_t>(1, ceil_div(P, (int64_t)kPathTile));
+    const unsigned egrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 152 * 16));
+    uint32_t *tk = nullptr, *tm = nullptr, *deg = nullptr, *val = nullptr;
+    uint64_t *uk = nullptr;
+    LNE_TRY(ws.get("path.tk", (size_t)ntiles, &tk));
+    LNE_TRY(ws.get("path.tm", (size_t)ntiles, &tm));
+    LNE_TRY(ws.get("path.deg", (size_t)n, &deg));
+    LNE_TRY(ws.get("strat.cuk", (size_t)std::max<int64_t>(P, 1), &uk));
+    LNE_TRY(ws.get("strat.cval", (size_t)std::max<int64_t>(P, 1), &val));
+    if (P > 0) LNE_CUDA_TRY(cudaMemcpyAsync(uk, S.pair, sizeof(uint64_t) * P, cudaMemcpyDeviceToDevice, st));
+    {
+        LNE_TRACE("path_value", st);
+        degree_kernel<<<egrid, 256, 0, st>>>(g.indptr, n, deg);
+        LNE_LAUNCH_CHECK();
+        strat_value_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(S.pair, S.seg, S.r, S.cnt, P, sp.B, deg,
+                                                                     netmf_const(sp), w, val, tk, tm);
+        LNE_LAUNCH_CHECK();
+    }
+    return assemble_csr(ws, g, sp, uk, val, P, tk, tm, "strat.cuk", "strat.cval", out, st);
+}
+
+void stratified_release(Workspace &ws) {
+    for (const char *nm : {"strat.r", "strat.cnt", "strat.pair", "strat.seglen", "strat.seg", "strat.cuk",
+                           "strat.cval"})
+        ws.release(nm);
+}
+
+namespace {
+
+// (x, y, r, count) of every distinct (pair, window) entry, sorted.
+int strat_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out, cudaStream_t st) {
+    int64_t total = 0, U = 0;
+    uint64_t *ukr = nullptr, *spare = nullptr;
+    uint32_t *cnt = nullptr;
+    LNE_TRY(strat_keys(ws, g, sp, &total, &ukr, &spare, &cnt, &U, st));
+    LNE_TRY(ws.get("counts.x", (size_t)std::max<int64_t>(U, 1), &out->x));
+    LNE_TRY(ws.get("counts.y", (size_t)std::max<int64_t>(U, 1), &out->y));
+    LNE_TRY(ws.get("counts.cnt", (size_t)std::max<int64_t>(U, 1), &out->cnt));
+    LNE_TRY(ws.get("counts.r", (size_t)std::max<int64_t>(U, 1), &out->window));
+    if (U > 0) {
+        LNE_TRACE("decode_keys", st);
+        strat_decode_kernel<<<(unsigned)std::min<int64_t>(ceil_div(U, 256), 152 * 16), 256, 0, st>>>(
+            ukr, U, sp.B, out->x, out->y, out->window);
+        LNE_LAUNCH_CHECK();
+        LNE_CUDA_TRY(cudaMemcpyAsync(out->cnt, cnt, sizeof(uint32_t) * U, cudaMemcpyDeviceToDevice, st));
+    }
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    sort_release(ws);
+    out->nnz = U;
+    out->total_samples = total;
+    return 0;
+}
+
+}  // namespace
+
 int sparsifier_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CountsResult *out,
                       cudaStream_t st) {
+    if (sp.stratified) return strat_counts(ws, g, sp, out, st);
     if (sp.ds_C > 0.0 && !use_table(g, sp) && sp.aggregation == LNE_AGG_BUCKET)
         return fail(LNE_ERR_UNSUPPORTED, "edge downsampling needs the table or the sort aggregation");
     if (use_table(g, sp)) LNE_TRY(table_counts(ws, g, sp, out, st));
@@ -1960,6 +2216,13 @@ int sparsifier_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
 }
 
 int sparsifier_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out, cudaStream_t st) {
+    if (sp.stratified) {
+        Strata S;
+        LNE_TRY(stratified_sample(ws, g, sp, &S, st));
+        const int rc = stratified_csr(ws, g, sp, S, out, st);
+        stratified_release(ws);
+        return rc;
+    }
     if (sp.ds_C > 0.0 && !use_table(g, sp) && sp.aggregation == LNE_AGG_BUCKET)
         return fail(LNE_ERR_UNSUPPORTED, "edge downsampling needs the table or the sort aggregation");
     if (use_table(g, sp)) return table_csr(ws, g, sp, out, st);

@@ -95,7 +95,8 @@ int spmm_threads_for(SpmmTune &tc, Workspace &ws, const GraphView &g, const floa
     return best;
 }
 
-int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregation, int dense_mode, const GraphView &g,
+int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregation, int dense_mode, int stratified,
+               const GraphView &g,
                const lne_params *cands, int ncand, const uint8_t *labels, int L, const int32_t *train,
                int64_t n_train, const int32_t *test, int64_t n_test, double Creg, int iters, double *macro,
                double *micro, float *X_out, cudaStream_t st) {
@@ -126,6 +127,8 @@ int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregati
     }
     float *X0s = nullptr;
     LNE_TRY(ws.get("tune.x0", (size_t)leader.size() * n * d, &X0s));
+    Strata strata;   // shared by the candidates with the same (T, S, seed)
+    bool have_strata = false;
     for (int q = 0; q < (int)leader.size(); ++q) {
         const lne_params &p = cands[leader[q]];
         SamplerSpec sp;
@@ -133,13 +136,22 @@ int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregati
         sp.aggregation = aggregation;
         sp.ds_C = p.downsample_C;
         CsrResult M;
-        LNE_TRY(sparsifier_csr(ws, g, sp, &M, st));
+        if (stratified) {
+            if (!have_strata || strata.T != sp.T || strata.S != sp.S || strata.seed != sp.seed) {
+                LNE_TRY(stratified_sample(ws, g, sp, &strata, st));
+                have_strata = true;
+            }
+            LNE_TRY(stratified_csr(ws, g, sp, strata, &M, st));
+        } else {
+            LNE_TRY(sparsifier_csr(ws, g, sp, &M, st));
+        }
         SketchSpec sk;
         sk.kind = p.sketch;
         sk.zeta = p.sketch_zeta;
         LNE_TRY(rsvd(ws, product_view(M, dense_mode), d, os_of(p), p.q, p.seed, p.precision, nullptr, nullptr,
                      X0s + (size_t)q * n * d, st, sk));
     }
+    if (have_strata) stratified_release(ws);
     float *X = nullptr, *U = nullptr;
     double *R = nullptr, *UR = nullptr, *sig = nullptr;
     LNE_TRY(ws.get("tune.x", (size_t)n * d, &X));
@@ -210,8 +222,8 @@ TuneWorker::~TuneWorker() {
 }
 
 int tune_tasks(std::vector<std::unique_ptr<TuneWorker>> &workers, int nworkers, int device, int forced_threads,
-               int aggregation, int dense_mode, const TuneTask *tasks, int ntasks, const lne_params *cands, int ncand, double Creg,
-               int iters, double *macro, double *micro) {
+               int aggregation, int dense_mode, int stratified, const TuneTask *tasks, int ntasks,
+               const lne_params *cands, int ncand, double Creg, int iters, double *macro, double *micro) {
     nworkers = std::max(1, std::min(nworkers, ntasks));
     while ((int)workers.size() < nworkers) {
         auto w = std::make_unique<TuneWorker>();
@@ -231,7 +243,8 @@ int tune_tasks(std::vector<std::unique_ptr<TuneWorker>> &workers, int nworkers, 
         w->tune.forced = forced_threads;
         for (int t; rc == 0 && !stop.load() && (t = next.fetch_add(1)) < ntasks;) {
             const TuneTask &k = tasks[t];
-            rc = tune_batch(w->ws, nullptr, w->tune, aggregation, dense_mode, k.g, cands + (size_t)t * ncand, ncand, k.labels,
+            rc = tune_batch(w->ws, nullptr, w->tune, aggregation, dense_mode, stratified, k.g,
+                            cands + (size_t)t * ncand, ncand, k.labels,
                             k.L, k.train, k.n_train, k.test, k.n_test, Creg, iters, macro + (size_t)t * ncand,
                             micro + (size_t)t * ncand, nullptr, w->st);
         }

@@ -41,6 +41,7 @@ OPT_AGGREGATION = 1
 OPT_SPMM_THREADS = 2
 OPT_TUNE_WORKERS = 3
 OPT_DENSE_PRODUCT = 4
+OPT_STRATIFIED = 5
 AGG_AUTO, AGG_TABLE, AGG_BUCKET, AGG_SORT = 0, 1, 2, 3
 
 
@@ -80,7 +81,8 @@ class _TraceEntry(ctypes.Structure):
 
 class _Counts(ctypes.Structure):
     _fields_ = [("nnz", ctypes.c_int64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p),
-                ("count", ctypes.c_void_p), ("total_samples", ctypes.c_int64), ("weight", ctypes.c_void_p)]
+                ("count", ctypes.c_void_p), ("total_samples", ctypes.c_int64), ("weight", ctypes.c_void_p),
+                ("window", ctypes.c_void_p)]
 
 
 _lib = None
@@ -327,6 +329,8 @@ class Context:
             res["weight"] = _own(out.weight, out.nnz, "<i8", torch.int64, self.dev)
         else:
             res["count"] = _own(out.count, out.nnz, "<u4", torch.uint32, self.dev)
+        if out.window:   # window-stratified counts: (x, y, r, count) entries
+            res["window"] = _own(out.window, out.nnz, "|u1", torch.uint8, self.dev)
         return res
 
     def sparsifier_csr(self, g: DeviceGraph, p: Params, copy: bool = True):
