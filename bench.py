@@ -40,7 +40,7 @@ WORKLOAD = "blogcatalog_like_chunglu_n10312_m333983_T10_S200Tm_d128_q1_k10"
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernel on this workload (profiles/walk_count_blogcatalog_S200Tm.md); to be
 # removed from here whenever the kernel changes.
-RECORDED_TRAFFIC = {"walk_count": 10.039976e9 + 10.386777e9}
+RECORDED_TRAFFIC = {}
 
 
 def workload():
@@ -459,6 +459,18 @@ def run_tune(args):
         out[f"batched_workers{w}"] = G * per / dt
     out["value"] = max(out[f"batched_workers{w}"] for w in (1, 4, 8))
     out["best_macro_f1_mean"] = float(ma.max(axis=1).mean())
+    # window-stratified sampling: one sampling pass per graph for all 32 s
+    ctx.set_option(lne.OPT_STRATIFIED, 1)
+    ctx.tune_tasks(tasks[:2], cands[:2])
+    for w in (4, 8):
+        ctx.set_option(lne.OPT_TUNE_WORKERS, w)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ma_s, _ = ctx.tune_tasks(tasks, cands)
+        dt = time.perf_counter() - t0
+        out[f"stratified_workers{w}"] = G * per / dt
+    out["stratified_best_macro_f1_mean"] = float(ma_s.max(axis=1).mean())
+    ctx.set_option(lne.OPT_STRATIFIED, 0)
     Gp = min(G, 2)
     for j in range(2):                             # warm-up of the plain path
         X = ctx.embed(tasks[0][0], cands[0][j])
