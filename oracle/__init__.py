@@ -9,7 +9,9 @@ Plain, slow, obviously checkable restatement of what the method computes, in
 FP64, each function citing the passage it follows:
 
 * sampling (C, ``lne_oracle.c``): Algorithm 1 (PathSampling), Algorithm 3
-  (per-edge sampling, Sec. 4.2) and the walk-step rule of Sec. 4.2;
+  (per-edge sampling, Sec. 4.2) and the walk-step rule of Sec. 4.2, on
+  unweighted graphs and on graphs with positive integer arc weights (walks
+  on D^-1 A with weighted D, samples per arc proportional to its weight);
 * ``netmf_values`` / ``sparsifier_csr``: Eq. 1 (the NetMF matrix with the
   truncated logarithm) estimated from the sample counts;
 * ``stratified_*``: window-stratified counts shared by many weightings s
@@ -75,11 +77,17 @@ def lib():
         L.oracle_count_samples.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                            ctypes.c_double, ctypes.c_uint64]
         L.oracle_count_samples.restype = ctypes.c_int64
-        L.oracle_sample_trace.argtypes = [ctypes.c_int64, i64p, i32p, ctypes.c_int, f64p,
+        L.oracle_sample_trace.argtypes = [ctypes.c_int64, i64p, i32p, u32p, ctypes.c_int, f64p,
                                           ctypes.c_double, ctypes.c_uint64, ctypes.c_int64,
                                           ctypes.c_int64, i64p, i32p, i32p, i64p, i64p, u32p]
         L.oracle_sample_trace.restype = ctypes.c_int64
         L.oracle_sketch_words.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, u32p]
+        L.oracle_weighted_choice.argtypes = [u32p, ctypes.c_int64, ctypes.c_uint32]
+        L.oracle_weighted_choice.restype = ctypes.c_int64
+        L.oracle_count_samples_w.argtypes = [u32p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_double,
+                                             ctypes.c_uint64]
+        L.oracle_count_samples_w.restype = ctypes.c_int64
+        L.oracle_arc_rate_w.argtypes = [ctypes.c_double, ctypes.c_uint32, ctypes.c_double, u64p, u64p]
         L.oracle_sparse_sign_words.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, u32p]
         L.oracle_num_threads.restype = ctypes.c_int
         _lib = L
@@ -127,25 +135,75 @@ def arc_rate(S: float, n_arcs: int) -> tuple[int, int]:
     return int(b.value), int(f.value)
 
 
-def arc_samples(n_arcs: int, S: float, seed: int, a0: int = 0, a1: int | None = None) -> np.ndarray:
+def _weights(weights, n_arcs=None):
+    if weights is None:
+        return None
+    w = np.ascontiguousarray(weights, dtype=np.uint32)
+    assert n_arcs is None or len(w) == n_arcs
+    assert np.all(w > 0), "arc weights are positive integers"
+    return w
+
+
+def weighted_degrees(indptr, weights) -> np.ndarray:
+    """d_u = sum of the weights of u's arcs (float64, exact below 2^53)."""
+    indptr = np.asarray(indptr, dtype=np.int64)
+    n = len(indptr) - 1
+    if weights is None:
+        return np.diff(indptr).astype(np.float64)
+    src = np.repeat(np.arange(n), np.diff(indptr))
+    return np.bincount(src, weights=np.asarray(weights, dtype=np.float64), minlength=n)
+
+
+def arc_rate_w(S: float, weight: int, vol: float) -> tuple[int, int]:
+    """Weighted graphs: (floor(rate), floor(frac(rate) 2^32)) of
+    rate = fl(fl(S A_a) / vol), the arc's share S A_a / vol of the samples."""
+    b = ctypes.c_uint64()
+    f = ctypes.c_uint64()
+    lib().oracle_arc_rate_w(float(S), int(weight), float(vol), ctypes.byref(b), ctypes.byref(f))
+    return b.value, f.value
+
+
+def weighted_choice(w, word: int) -> int:
+    """The weighted walk step's arc for a 32-bit word (inverse CDF with
+    thresholds floor(2^32 P_j / d))."""
+    w = np.ascontiguousarray(w, dtype=np.uint32)
+    return int(lib().oracle_weighted_choice(_ptr(w, ctypes.c_uint32), len(w), int(word)))
+
+
+def arc_samples(n_arcs: int, S: float, seed: int, a0: int = 0, a1: int | None = None, weights=None) -> np.ndarray:
     """n_a for arcs [a0, a1)."""
     a1 = n_arcs if a1 is None else a1
-    base, thr = arc_rate(S, n_arcs)
     L = lib()
+    w = _weights(weights, n_arcs)
+    if w is not None:
+        vol = float(np.sum(w, dtype=np.uint64))
+        out = []
+        for a in range(a0, a1):
+            base, thr = arc_rate_w(S, int(w[a]), vol)
+            out.append(L.oracle_arc_samples(a, base, thr, seed))
+        return np.array(out, dtype=np.int64)
+    base, thr = arc_rate(S, n_arcs)
     return np.array([L.oracle_arc_samples(a, base, thr, seed) for a in range(a0, a1)], dtype=np.int64)
 
 
-def count_samples(n_arcs: int, S: float, seed: int, a0: int = 0, a1: int | None = None) -> int:
+def count_samples(n_arcs: int, S: float, seed: int, a0: int = 0, a1: int | None = None, weights=None) -> int:
     a1 = n_arcs if a1 is None else a1
+    w = _weights(weights, n_arcs)
+    if w is not None:
+        return int(lib().oracle_count_samples_w(_ptr(w, ctypes.c_uint32), n_arcs, a0, a1, float(S), seed))
     return int(lib().oracle_count_samples(n_arcs, a0, a1, float(S), seed))
 
 
-def sample_trace(indptr, indices, T, s, S, seed, a0=0, a1=None, fields=("arc", "r", "sigma", "u1", "v1")):
+def sample_trace(indptr, indices, T, s, S, seed, a0=0, a1=None, fields=("arc", "r", "sigma", "u1", "v1"),
+                 weights=None):
     """Every PathSampling draw of arcs [a0, a1) in (arc, sample) order.
 
     Returns a dict with the requested fields: ``arc``, window ``r``, split
     ``sigma``, the ordered endpoints ``u1`` (walked from the arc's source)
     and ``v1`` (walked from its target), and the downsampling ``coin`` word.
+    With ``weights`` (positive integer arc weights, symmetric) arc a draws
+    S A_a / vol samples in expectation and a walk step takes an arc with
+    probability proportional to its weight (``weighted_choice``).
     """
     indptr = np.ascontiguousarray(indptr, dtype=np.int64)
     indices = np.ascontiguousarray(indices, dtype=np.int32)
@@ -153,7 +211,8 @@ def sample_trace(indptr, indices, T, s, S, seed, a0=0, a1=None, fields=("arc", "
     n = indptr.shape[0] - 1
     n_arcs = int(indptr[-1])
     a1 = n_arcs if a1 is None else a1
-    total = count_samples(n_arcs, S, seed, a0, a1)
+    w = _weights(weights, n_arcs)
+    total = count_samples(n_arcs, S, seed, a0, a1, weights=w)
     out = {
         "arc": np.zeros(total, np.int64) if "arc" in fields else None,
         "r": np.zeros(total, np.int32) if "r" in fields else None,
@@ -163,7 +222,7 @@ def sample_trace(indptr, indices, T, s, S, seed, a0=0, a1=None, fields=("arc", "
         "coin": np.zeros(total, np.uint32) if "coin" in fields else None,
     }
     got = lib().oracle_sample_trace(
-        n, _ptr(indptr, ctypes.c_int64), _ptr(indices, ctypes.c_int32), len(s),
+        n, _ptr(indptr, ctypes.c_int64), _ptr(indices, ctypes.c_int32), _ptr(w, ctypes.c_uint32), len(s),
         _ptr(s, ctypes.c_double), float(S), int(seed), int(a0), int(a1),
         _ptr(out["arc"], ctypes.c_int64), _ptr(out["r"], ctypes.c_int32),
         _ptr(out["sigma"], ctypes.c_int32), _ptr(out["u1"], ctypes.c_int64),
@@ -172,13 +231,13 @@ def sample_trace(indptr, indices, T, s, S, seed, a0=0, a1=None, fields=("arc", "
     return {k: v for k, v in out.items() if v is not None}
 
 
-def sample_pairs(indptr, indices, T, s, S, seed, a0=0, a1=None):
+def sample_pairs(indptr, indices, T, s, S, seed, a0=0, a1=None, weights=None):
     """Canonical endpoint pairs (x = min, y = max) of every draw of arcs [a0, a1)."""
-    tr = sample_trace(indptr, indices, T, s, S, seed, a0, a1, fields=("u1", "v1"))
+    tr = sample_trace(indptr, indices, T, s, S, seed, a0, a1, fields=("u1", "v1"), weights=weights)
     return np.minimum(tr["u1"], tr["v1"]), np.maximum(tr["u1"], tr["v1"])
 
 
-def arc_downsample(indptr, indices, C: float):
+def arc_downsample(indptr, indices, C: float, weights=None):
     """Edge downsampling (Sec. 4.1, Algorithm 3) per CSR arc u -> v:
     p_e = min(1, C (1/d_u + 1/d_v)); the coin keeps a draw iff its word is below
     thr_e = min(2^32, floor(p_e 2^32)); a kept draw adds the weight 1/p_e, held
@@ -188,16 +247,19 @@ def arc_downsample(indptr, indices, C: float):
     indptr = np.asarray(indptr, dtype=np.int64)
     indices = np.asarray(indices, dtype=np.int64)
     n = len(indptr) - 1
-    deg = np.diff(indptr).astype(np.float64)
+    deg = weighted_degrees(indptr, weights)
     src = np.repeat(np.arange(n), np.diff(indptr))
     du, dv = deg[src], deg[indices]
-    p = np.minimum(1.0, C * (1.0 / du + 1.0 / dv))
+    p = C * (1.0 / du + 1.0 / dv)
+    if weights is not None:           # p_e = min(1, A_uv (C (1/d_u + 1/d_v))), Sec. 4.1
+        p = np.asarray(weights, dtype=np.float64) * p
+    p = np.minimum(1.0, p)
     thr = np.where(p >= 1.0, 2.0 ** 32, np.floor(p * 4294967296.0)).astype(np.uint64)
     w = np.floor(4294967296.0 / p + 0.5).astype(np.uint64)
     return thr, w
 
 
-def sparsifier_counts(indptr, indices, T, s, S, seed, C: float = 0.0):
+def sparsifier_counts(indptr, indices, T, s, S, seed, C: float = 0.0, weights=None):
     """Exact multiplicity K_xy of every sampled unordered pair (x <= y).
 
     The aggregation of Sec. 4.2 (hash table with atomic counts) computes the
@@ -209,11 +271,11 @@ def sparsifier_counts(indptr, indices, T, s, S, seed, C: float = 0.0):
     """
     n = len(indptr) - 1
     if C <= 0.0:
-        x, y = sample_pairs(indptr, indices, T, s, S, seed)
+        x, y = sample_pairs(indptr, indices, T, s, S, seed, weights=weights)
         keys, cnt = np.unique(x * n + y, return_counts=True)
         return keys // n, keys % n, cnt.astype(np.int64)
-    tr = sample_trace(indptr, indices, T, s, S, seed, fields=("arc", "u1", "v1", "coin"))
-    thr, w = arc_downsample(indptr, indices, C)
+    tr = sample_trace(indptr, indices, T, s, S, seed, fields=("arc", "u1", "v1", "coin"), weights=weights)
+    thr, w = arc_downsample(indptr, indices, C, weights)
     kept = tr["coin"].astype(np.uint64) < thr[tr["arc"]]
     x = np.minimum(tr["u1"], tr["v1"])[kept]
     y = np.maximum(tr["u1"], tr["v1"])[kept]
@@ -223,14 +285,14 @@ def sparsifier_counts(indptr, indices, T, s, S, seed, C: float = 0.0):
     return keys // n, keys % n, wsum
 
 
-def stratified_counts(indptr, indices, T, S, seed):
+def stratified_counts(indptr, indices, T, S, seed, weights=None):
     """Window-stratified counts for sharing one sampling pass among many
     window weightings s (the survey's proposal for candidate batching, not a
     procedure of the paper): every draw takes r ~ U{1..T} (Algorithm 3 with
     s uniform) and the pair counts are kept per window length.
     Returns (x, y, r, count) sorted by (x, y, r)."""
     n = len(indptr) - 1
-    tr = sample_trace(indptr, indices, T, np.ones(T), S, seed, fields=("r", "u1", "v1"))
+    tr = sample_trace(indptr, indices, T, np.ones(T), S, seed, fields=("r", "u1", "v1"), weights=weights)
     x = np.minimum(tr["u1"], tr["v1"])
     y = np.maximum(tr["u1"], tr["v1"])
     keys, cnt = np.unique((x * n + y) * T + (tr["r"].astype(np.int64) - 1), return_counts=True)
@@ -264,11 +326,11 @@ def stratified_estimate(x, y, r, cnt, s, T):
     return up // n, up % n, K
 
 
-def stratified_sparsifier(indptr, indices, T, s, S, seed, b=1.0):
+def stratified_sparsifier(indptr, indices, T, s, S, seed, b=1.0, weights=None):
     """Eq. 1 from the stratified estimate K_s (K = fl(double(K_s)) 2^-24)."""
     n = len(indptr) - 1
-    deg = np.diff(indptr)
-    x, y, r, c = stratified_counts(indptr, indices, T, S, seed)
+    deg = weighted_degrees(indptr, weights)
+    x, y, r, c = stratified_counts(indptr, indices, T, S, seed, weights=weights)
     px, py, K = stratified_estimate(x, y, r, c, s, T)
     v, keep, val = netmf_values(px, py, K, deg, S, b, unit=2.0 ** -24)
     mp, mc, mv = sparsifier_csr(n, px[keep], py[keep], val[keep])
@@ -328,24 +390,26 @@ def sparsifier_csr(n, x, y, val):
     return indptr, cols.astype(np.int32), data
 
 
-def sparsifier(indptr, indices, T, s, S, seed, b=1.0, C=0.0):
+def sparsifier(indptr, indices, T, s, S, seed, b=1.0, C=0.0, weights=None):
     """Counts -> trunc_log -> CSR. Returns a dict with every intermediate
-    (with edge downsampling, C > 0, ``cnt`` holds the weight sums)."""
+    (with edge downsampling, C > 0, ``cnt`` holds the weight sums). On a
+    weighted graph vol and the degrees of Eq. 1 are the weighted ones."""
     n = len(indptr) - 1
-    deg = np.diff(indptr)
-    x, y, cnt = sparsifier_counts(indptr, indices, T, s, S, seed, C)
+    deg = weighted_degrees(indptr, weights)
+    x, y, cnt = sparsifier_counts(indptr, indices, T, s, S, seed, C, weights=weights)
     v, keep, val = netmf_values(x, y, cnt, deg, S, b, weighted=C > 0.0)
     mp, mc, mv = sparsifier_csr(n, x[keep], y[keep], val[keep])
     return dict(x=x, y=y, cnt=cnt, v=v, keep=keep, val=val, indptr=mp, indices=mc, data=mv)
 
 
-def netmf_dense(indptr, indices, T, s, b=1.0):
+def netmf_dense(indptr, indices, T, s, b=1.0, weights=None):
     """Eq. 1 inside the truncated log, densely: vol/b * sum_r s_r (D^-1 A)^r D^-1.
 
     For tiny graphs only (n <= a few hundred). ``s`` is normalised to sum 1.
     """
     n = len(indptr) - 1
-    A = sp.csr_matrix((np.ones(len(indices)), indices, indptr), shape=(n, n)).toarray()
+    vals = np.ones(len(indices)) if weights is None else np.asarray(weights, dtype=np.float64)
+    A = sp.csr_matrix((vals, indices, indptr), shape=(n, n)).toarray()
     d = A.sum(1)
     vol = d.sum()
     P = A / d[:, None]
@@ -505,7 +569,7 @@ def chebyshev_coefficients(k: int, theta: float) -> np.ndarray:
     return c
 
 
-def spectral_propagation(indptr, indices, X0: np.ndarray, k: int, theta: float, mu: float):
+def spectral_propagation(indptr, indices, X0: np.ndarray, k: int, theta: float, mu: float, weights=None):
     """Chebyshev spectral propagation of X0 on the graph.
 
     With Lap = I - D^-1 A (the paper's normalised Laplacian, Sec. 3.3) and
@@ -518,7 +582,8 @@ def spectral_propagation(indptr, indices, X0: np.ndarray, k: int, theta: float, 
     n = len(indptr) - 1
     if k <= 0:
         return dict(F=None, P=None, X=X0.copy())
-    A = sp.csr_matrix((np.ones(len(indices)), indices, indptr), shape=(n, n))
+    vals = np.ones(len(indices)) if weights is None else np.asarray(weights, dtype=np.float64)
+    A = sp.csr_matrix((vals, indices, indptr), shape=(n, n))
     deg = np.asarray(A.sum(1)).ravel()
     dinv = np.where(deg > 0, 1.0 / np.where(deg > 0, deg, 1.0), 0.0)
     DA = sp.diags(dinv) @ A
@@ -549,15 +614,15 @@ def spectral_propagation(indptr, indices, X0: np.ndarray, k: int, theta: float, 
 # ----------------------------------------------------------------------------
 
 def embed(indptr, indices, T, s, S, d, q, k, theta, mu, seed, oversample=16, b=1.0, C=0.0,
-          sketch="gaussian", zeta=8):
+          sketch="gaussian", zeta=8, weights=None):
     """Sparsifier (edge-downsampled when C > 0, Sec. 4.1) -> randomized SVD
     (Gaussian or sparse sign test matrix, Sec. 3.2) -> X0 -> spectral
     propagation -> X."""
-    sparse = sparsifier(indptr, indices, T, s, S, seed, b, C)
+    sparse = sparsifier(indptr, indices, T, s, S, seed, b, C, weights=weights)
     rs = fast_randomized_svd(sparse["indptr"], sparse["indices"], sparse["data"], d, q,
                              oversample, seed, sketch=sketch, zeta=zeta)
     X0 = embedding_from_svd(rs["U"], rs["sigma"])
-    prop = spectral_propagation(indptr, indices, X0, k, theta, mu)
+    prop = spectral_propagation(indptr, indices, X0, k, theta, mu, weights=weights)
     return dict(sparse=sparse, rsvd=rs, X0=X0, prop=prop, X=prop["X"])
 
 

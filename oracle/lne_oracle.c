@@ -147,19 +147,37 @@ static int64_t arc_source(int64_t n, const int64_t *indptr, int64_t a)
     return lo;
 }
 
-static int64_t walk(const int64_t *indptr, const int32_t *indices, int64_t x, int steps,
-                    word_stream *st)
+/* Weighted step (weighted graphs): with d = w_0 + .. + w_{deg-1} (< 2^32) and
+ * prefixes P_j = w_0 + .. + w_j, the arc taken is the first j < deg - 1 with
+ * word < floor(2^32 P_j / d), else the last: arc j with probability
+ * w_j / d up to the 2^-32 rounding of the thresholds (inverse CDF). */
+int64_t oracle_weighted_choice(const uint32_t *w, int64_t deg, uint32_t word)
+{
+    uint64_t d = 0;
+    for (int64_t j = 0; j < deg; ++j) d += w[j];
+    uint64_t prefix = 0;
+    for (int64_t j = 0; j + 1 < deg; ++j) {
+        prefix += w[j];
+        if ((uint64_t)word < (prefix << 32) / d) return j;
+    }
+    return deg - 1;
+}
+
+static int64_t walk(const int64_t *indptr, const int32_t *indices, const uint32_t *weights, int64_t x,
+                    int steps, word_stream *st)
 {
     for (int t = 0; t < steps; ++t) {
         uint32_t w = ws_next(st);
-        uint64_t deg = (uint64_t)(indptr[x + 1] - indptr[x]);
-        x = indices[indptr[x] + (int64_t)((uint64_t)w % deg)];
+        int64_t deg = indptr[x + 1] - indptr[x];
+        int64_t j = weights ? oracle_weighted_choice(weights + indptr[x], deg, w)
+                            : (int64_t)((uint64_t)w % (uint64_t)deg);
+        x = indices[indptr[x] + j];
     }
     return x;
 }
 
 /* One sample: writes r, sigma and the ordered endpoints (u', v'). */
-static void path_sample(const int64_t *indptr, const int32_t *indices, int T,
+static void path_sample(const int64_t *indptr, const int32_t *indices, const uint32_t *weights, int T,
                         const uint64_t *thr, int64_t u, int64_t v, int64_t a, uint64_t j,
                         uint64_t seed, int *r_out, int *sigma_out, uint32_t *coin_out,
                         int64_t *u1, int64_t *v1)
@@ -173,13 +191,48 @@ static void path_sample(const int64_t *indptr, const int32_t *indices, int T,
     uint32_t wsig = ws_next(&st);
     int sigma = (int)(wsig % (uint32_t)r);
     uint32_t coin = ws_next(&st);   /* the downsampling coin (Algorithm 3) */
-    int64_t uu = walk(indptr, indices, u, sigma, &st);
-    int64_t vv = walk(indptr, indices, v, r - 1 - sigma, &st);
+    int64_t uu = walk(indptr, indices, weights, u, sigma, &st);
+    int64_t vv = walk(indptr, indices, weights, v, r - 1 - sigma, &st);
     *r_out = r;
     *sigma_out = sigma;
     *coin_out = coin;
     *u1 = uu;
     *v1 = vv;
+}
+
+/* Weighted graphs: arc a of weight A_a draws S A_a / vol samples in
+ * expectation (vol = sum of all arc weights), rate = fl(fl(S A_a) / vol). */
+void oracle_arc_rate_w(double S, uint32_t weight, double vol, uint64_t *base, uint64_t *thr_frac)
+{
+    double rate = (S * (double)weight) / vol;
+    double b = floor(rate);
+    double frac = rate - b;
+    *base = (uint64_t)b;
+    *thr_frac = (uint64_t)floor(frac * 4294967296.0);
+}
+
+static double weight_volume(const uint32_t *weights, int64_t n_arcs)
+{
+    uint64_t vol = 0;
+    for (int64_t a = 0; a < n_arcs; ++a) vol += weights[a];
+    return (double)vol;
+}
+
+static uint64_t arc_samples_any(const uint32_t *weights, double vol, int64_t a, uint64_t base, uint64_t thr_frac,
+                                double S, uint64_t seed)
+{
+    if (weights) oracle_arc_rate_w(S, weights[a], vol, &base, &thr_frac);
+    return oracle_arc_samples(a, base, thr_frac, seed);
+}
+
+/* Total samples drawn by arcs [a0, a1) of a weighted graph. */
+int64_t oracle_count_samples_w(const uint32_t *weights, int64_t n_arcs, int64_t a0, int64_t a1, double S,
+                               uint64_t seed)
+{
+    double vol = weight_volume(weights, n_arcs);
+    int64_t total = 0;
+    for (int64_t a = a0; a < a1; ++a) total += (int64_t)arc_samples_any(weights, vol, a, 0, 0, S, seed);
+    return total;
 }
 
 /* Total samples drawn by arcs [a0, a1). */
@@ -199,7 +252,7 @@ int64_t oracle_count_samples(int64_t n_arcs, int64_t a0, int64_t a1, double S, u
  *   ordered endpoints (u' from the arc's source side, v' from its target side);
  *   coin[k]: its downsampling coin word (the walk is drawn whatever the coin).
  */
-int64_t oracle_sample_trace(int64_t n, const int64_t *indptr, const int32_t *indices,
+int64_t oracle_sample_trace(int64_t n, const int64_t *indptr, const int32_t *indices, const uint32_t *weights,
                             int T, const double *s, double S, uint64_t seed,
                             int64_t a0, int64_t a1,
                             int64_t *arc, int32_t *r, int32_t *sigma, int64_t *u1, int64_t *v1,
@@ -210,13 +263,14 @@ int64_t oracle_sample_trace(int64_t n, const int64_t *indptr, const int32_t *ind
     oracle_window_thresholds(T, s, thr);
     uint64_t base, thr_frac;
     oracle_arc_rate(S, n_arcs, &base, &thr_frac);
+    double vol = weights ? weight_volume(weights, n_arcs) : 0.0;
 
     /* per-arc output offsets */
     int64_t count = a1 - a0;
     int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(count + 1));
     off[0] = 0;
     for (int64_t i = 0; i < count; ++i)
-        off[i + 1] = off[i] + (int64_t)oracle_arc_samples(a0 + i, base, thr_frac, seed);
+        off[i + 1] = off[i] + (int64_t)arc_samples_any(weights, vol, a0 + i, base, thr_frac, S, seed);
 
 #pragma omp parallel for schedule(dynamic, 64)
     for (int64_t i = 0; i < count; ++i) {
@@ -228,7 +282,7 @@ int64_t oracle_sample_trace(int64_t n, const int64_t *indptr, const int32_t *ind
             int rr, ss;
             uint32_t cw;
             int64_t x, y;
-            path_sample(indptr, indices, T, thr, u, v, a, j, seed, &rr, &ss, &cw, &x, &y);
+            path_sample(indptr, indices, weights, T, thr, u, v, a, j, seed, &rr, &ss, &cw, &x, &y);
             if (coin) coin[k] = cw;
             if (arc) arc[k] = a;
             if (r) r[k] = rr;

@@ -241,6 +241,20 @@ def blogcatalog_like(seed: int = 2) -> Graph:
     return chung_lu(10_312, 333_983, 2.1, seed, n_labels=39, name="blogcatalog_like")
 
 
+def edge_weights(g: Graph, lo: int, hi: int, seed: int) -> np.ndarray:
+    """Integer arc weights in [lo, hi], equal on both arcs of an edge (a
+    seeded hash of the unordered pair), in the graph's CSR arc order."""
+    src = np.repeat(np.arange(g.n, dtype=np.uint64), np.diff(g.indptr))
+    dst = np.asarray(g.indices, dtype=np.uint64)
+    key = np.minimum(src, dst) * np.uint64(g.n) + np.maximum(src, dst)
+    z = key + np.uint64((0x9E3779B97F4A7C15 * (seed + 1)) & 0xFFFFFFFFFFFFFFFF)
+    with np.errstate(over="ignore"):   # splitmix64 finaliser, mod 2^64
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return (np.uint64(lo) + z % np.uint64(hi - lo + 1)).astype(np.uint32)
+
+
 def dirichlet_weights(T: int, seed: int) -> np.ndarray:
     """Window weights s_1..s_T drawn from Dirichlet(1,...,1)."""
     return np.random.default_rng(seed).dirichlet(np.ones(T))
