@@ -63,6 +63,13 @@ typedef struct {
     int64_t nnz;               /* arcs = 2m = indptr[n] */
     const int64_t *indptr;     /* device, [n+1] */
     const int32_t *indices;    /* device, [nnz] */
+    const uint32_t *weights;   /* device, [nnz] positive integer arc weights A_uv (equal on both arcs of
+                                  an edge; weighted degrees below 2^31), or NULL for an unweighted
+                                  graph. Weighted: arc a draws S A_a / vol samples in expectation
+                                  (rate fl(fl(S A_a) / vol)), a walk step takes arc j of x for words
+                                  below floor(2^32 (A_0 + .. + A_j) / d_x) (inverse CDF), and Eq. 1,
+                                  edge downsampling (p_e = min(1, A_uv (C (1/d_u + 1/d_v)))) and the
+                                  propagation (D^-1 A) use the weighted degrees and volume. */
 } lne_graph;
 
 /* Parameters in the paper's notation (notation table of Sec. 3). */

@@ -208,6 +208,7 @@ lne::GraphView view(const lne_graph *g) {
     v.nnz = g->nnz;
     v.indptr = g->indptr;
     v.indices = g->indices;
+    v.w = g->weights;
     return v;
 }
 
@@ -401,12 +402,14 @@ int lne_sample_pairs(lne_ctx *ctx, const lne_graph *g, const lne_params *p, int6
         rc = lne::fail(LNE_ERR_INVALID, "NULL output");
     cudaStream_t st = as_stream(stream);
     if (rc == 0) rc = check_graph_device(g, st);
+    lne::GraphView gv = view(g);
+    if (rc == 0) rc = lne::prepare_weighted(ctx->ws, &gv, st);
     lne::SamplerSpec sp;
-    if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
+    if (rc == 0) rc = lne::make_sampler_spec(gv, p->T, p->s, p->samples, p->b, p->seed, &sp);
     sp.aggregation = ctx->aggregation;
     sp.ds_C = p->downsample_C;
     sp.stratified = ctx->stratified;
-    if (rc == 0) rc = lne::sample_pairs(ctx->ws, view(g), sp, arc_begin, arc_end, u1_dev, v1_dev, capacity,
+    if (rc == 0) rc = lne::sample_pairs(ctx->ws, gv, sp, arc_begin, arc_end, u1_dev, v1_dev, capacity,
                                         count_out, st);
     return finish(ctx, rc);
 }
@@ -420,13 +423,15 @@ int lne_sparsifier_counts(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
     if (rc == 0 && !out) rc = lne::fail(LNE_ERR_INVALID, "NULL output");
     cudaStream_t st = as_stream(stream);
     if (rc == 0) rc = check_graph_device(g, st);
+    lne::GraphView gv = view(g);
+    if (rc == 0) rc = lne::prepare_weighted(ctx->ws, &gv, st);
     lne::SamplerSpec sp;
-    if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
+    if (rc == 0) rc = lne::make_sampler_spec(gv, p->T, p->s, p->samples, p->b, p->seed, &sp);
     sp.aggregation = ctx->aggregation;
     sp.ds_C = p->downsample_C;
     sp.stratified = ctx->stratified;
     lne::CountsResult r;
-    if (rc == 0) rc = lne::sparsifier_counts(ctx->ws, view(g), sp, &r, st);
+    if (rc == 0) rc = lne::sparsifier_counts(ctx->ws, gv, sp, &r, st);
     if (rc == 0) {
         out->nnz = r.nnz;
         out->x = r.x;
@@ -447,13 +452,15 @@ int lne_sparsifier_csr(lne_ctx *ctx, const lne_graph *g, const lne_params *p, ln
     if (rc == 0 && !out) rc = lne::fail(LNE_ERR_INVALID, "NULL output");
     cudaStream_t st = as_stream(stream);
     if (rc == 0) rc = check_graph_device(g, st);
+    lne::GraphView gv = view(g);
+    if (rc == 0) rc = lne::prepare_weighted(ctx->ws, &gv, st);
     lne::SamplerSpec sp;
-    if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
+    if (rc == 0) rc = lne::make_sampler_spec(gv, p->T, p->s, p->samples, p->b, p->seed, &sp);
     sp.aggregation = ctx->aggregation;
     sp.ds_C = p->downsample_C;
     sp.stratified = ctx->stratified;
     lne::CsrResult r;
-    if (rc == 0) rc = lne::sparsifier_csr(ctx->ws, view(g), sp, &r, st);
+    if (rc == 0) rc = lne::sparsifier_csr(ctx->ws, gv, sp, &r, st);
     if (rc == 0) {
         out->n = r.n;
         out->nnz = r.nnz;
@@ -562,8 +569,10 @@ int lne_propagate(lne_ctx *ctx, const lne_graph *g, const lne_params *p, const f
     if (rc == 0 && (p->k < 0 || !std::isfinite(p->theta) || !std::isfinite(p->mu)))
         rc = lne::fail(LNE_ERR_INVALID, "need k >= 0 and finite theta, mu");
     if (rc == 0 && p->d < 1) rc = lne::fail(LNE_ERR_INVALID, "need d >= 1");
+    lne::GraphView gv = view(g);
+    if (rc == 0) rc = lne::prepare_weighted(ctx->ws, &gv, as_stream(stream));
     if (rc == 0)
-        rc = lne::propagate(ctx->ws, view(g), p->d, p->k, p->theta, p->mu, p->precision, X0_dev, X_dev, F_dev,
+        rc = lne::propagate(ctx->ws, gv, p->d, p->k, p->theta, p->mu, p->precision, X0_dev, X_dev, F_dev,
                             P_dev, as_stream(stream));
     return finish(ctx, rc);
 }
@@ -590,13 +599,15 @@ int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_de
     if (rc == 0 && (p->k < 0 || p->q < 0 || p->d < 1)) rc = lne::fail(LNE_ERR_INVALID, "need d >= 1, q >= 0, k >= 0");
     cudaStream_t st = as_stream(stream);
     if (rc == 0) rc = check_graph_device(g, st);
+    lne::GraphView gv = view(g);
+    if (rc == 0) rc = lne::prepare_weighted(ctx->ws, &gv, st);
     lne::SamplerSpec sp;
-    if (rc == 0) rc = lne::make_sampler_spec(view(g), p->T, p->s, p->samples, p->b, p->seed, &sp);
+    if (rc == 0) rc = lne::make_sampler_spec(gv, p->T, p->s, p->samples, p->b, p->seed, &sp);
     sp.aggregation = ctx->aggregation;
     sp.ds_C = p->downsample_C;
     sp.stratified = ctx->stratified;
     lne::CsrResult M;
-    if (rc == 0) rc = lne::sparsifier_csr(ctx->ws, view(g), sp, &M, st);
+    if (rc == 0) rc = lne::sparsifier_csr(ctx->ws, gv, sp, &M, st);
     float *X0 = nullptr;
     if (rc == 0) rc = ctx->ws.get("embed.x0", (size_t)g->n * p->d, &X0);
     if (rc == 0) {
@@ -604,7 +615,7 @@ int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_de
                        p->precision, nullptr, nullptr, X0, st, sketch_of(p));
     }
     if (rc == 0)
-        rc = lne::propagate(ctx->ws, view(g), p->d, p->k, p->theta, p->mu, p->precision, X0, X_dev, nullptr, nullptr,
+        rc = lne::propagate(ctx->ws, gv, p->d, p->k, p->theta, p->mu, p->precision, X0, X_dev, nullptr, nullptr,
                             st);
     return finish(ctx, rc);
 }
@@ -623,10 +634,12 @@ int lne_tune_batch(lne_ctx *ctx, const lne_graph *g, const lne_params *cands, in
         rc = lne::fail(LNE_ERR_INVALID, "bad evaluation split or labels");
     cudaStream_t st = as_stream(stream);
     if (rc == 0) rc = check_graph_device(g, st);
+    lne::GraphView gv = view(g);
+    if (rc == 0) rc = lne::prepare_weighted(ctx->ws, &gv, st);
     if (rc == 0 && !ctx->prop_graph) ctx->prop_graph = lne::new_prop_cache();
     if (rc == 0)
         rc = lne::tune_batch(ctx->ws, ctx->prop_graph, ctx->spmm_tune, ctx->aggregation, ctx->dense_mode,
-                             ctx->stratified, view(g),
+                             ctx->stratified, gv,
                              cands, ncand,
                              labels_dev, L, train_dev, n_train, test_dev, n_test, C, iters, macro_f1, micro_f1,
                              X_dev, st);

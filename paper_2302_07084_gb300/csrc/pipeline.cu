@@ -425,7 +425,7 @@ int propagate_batch(Workspace &ws, PropBatchGraph *cache, const GraphView &g, in
                                   (uintptr_t)C,        (uintptr_t)kmax,      (uintptr_t)X0,   (uintptr_t)P,
                                   (uintptr_t)coef,     (uintptr_t)F,         (uintptr_t)Z,    (uintptr_t)G,
                                   (uintptr_t)Tb[0],    (uintptr_t)Tb[1],     (uintptr_t)Tb[2], (uintptr_t)threads,
-                                  (uintptr_t)carry,    (uintptr_t)carry_row};
+                                  (uintptr_t)carry,    (uintptr_t)carry_row, (uintptr_t)g.wf, (uintptr_t)g.dinv};
     if (cache->valid && cache->key == key) {
         LNE_TRACE("propagate_batch_graph", st);
         LNE_CUDA_TRY(cudaGraphLaunch(cache->exec, st));

@@ -44,7 +44,18 @@ struct GraphView {
     int64_t nnz = 0;
     const int64_t *indptr = nullptr;
     const int32_t *indices = nullptr;
+    // weighted graphs (w = NULL: unweighted); the rest is derived from w by
+    // prepare_weighted
+    const uint32_t *w = nullptr;      // [nnz] positive integer arc weights, symmetric
+    const uint32_t *wdeg = nullptr;   // [n] weighted degrees d_u (< 2^31)
+    const float *wf = nullptr;        // [nnz] the weights as float (graph products)
+    const float *dinv = nullptr;      // [n] 1 / d_u as float (graph products)
+    double vol = 0.0;                 // sum of all arc weights
+    uint32_t wmax = 0;                // largest arc weight
 };
+// Weighted degrees, volume and the float copies of a weighted graph into the
+// workspace ("wg.*"); no-op for unweighted graphs. Synchronises.
+int prepare_weighted(Workspace &ws, GraphView *g, cudaStream_t st);
 
 struct CsrView {
     int64_t n = 0;
@@ -77,6 +88,7 @@ struct SamplerSpec {
     double S = 0.0, b = 1.0;
     uint64_t seed = 0;
     int stratified = 0;           // 1: M from window-stratified counts
+    const uint32_t *wdeg = nullptr;   // weighted degrees for Eq. 1 (weighted graphs)
 };
 
 int make_sampler_spec(const GraphView &g, int T, const double *s, double S, double b, uint64_t seed,
@@ -134,6 +146,7 @@ int sign_fix_embed(Workspace &ws, float *U, int64_t n, int d, int64_t ld, const 
 struct SpmmEpilogue {
     float alpha = 1.f;
     bool dinv = false;                  // multiply (A X)_i by 1 / deg(i)
+    const float *dinv_w = nullptr;      // with dinv: per-row 1 / d_i (weighted graphs) instead
     const float *E1 = nullptr;
     float b1 = 0.f;
     const float *E2 = nullptr;

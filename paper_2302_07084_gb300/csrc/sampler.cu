@@ -65,14 +65,28 @@ struct WalkArgs {
     const uint64_t *ds_thr;
     const uint64_t *ds_w;
     int strat;                    // MODE 3 keys carry r - 1 in 4 low bits
+    // weighted graphs (w = NULL: unweighted): arc a draws S w_a / vol samples
+    // in expectation, and a step takes arc j of x with probability w_j / d_x
+    // (first j with word < cum[off + j], cum = floor(2^32 prefix_j / d_x))
+    const uint32_t *w;
+    const uint32_t *cum;
+    double S, vol;
+    uint32_t wmax;                // host copy of the largest weight (tile size bounds)
 };
 
 __device__ __forceinline__ uint32_t arc_count(const WalkArgs &A, int64_t arc) {
-    if (A.thr_frac == 0) return A.base;
+    uint32_t base = A.base, thr = A.thr_frac;
+    if (A.w) {   // rate = fl(fl(S w_a) / vol): floor and Bernoulli threshold of the fraction
+        const double rate = __ddiv_rn(__dmul_rn(A.S, (double)__ldg(A.w + arc)), A.vol);
+        const double b = floor(rate);
+        base = (uint32_t)b;
+        thr = (uint32_t)floor(__dmul_rn(__dsub_rn(rate, b), 4294967296.0));
+    }
+    if (thr == 0) return base;
     u32x4 c = {0xFFFFFFFFu, (uint32_t)((uint64_t)arc & 0xFFFFFFFFu), (uint32_t)((uint64_t)arc >> 32),
                0xFFFFFFFFu};
     u32x4 w = philox10(c, A.k0, A.k1);
-    return A.base + (w.x < A.thr_frac ? 1u : 0u);
+    return base + (w.x < thr ? 1u : 0u);
 }
 
 // Philox4x32-10 with precomputed round keys; each 32 x 32 -> 64 product is one
@@ -133,6 +147,34 @@ __global__ void build_arcrec_kernel(const int32_t *__restrict__ indices, int64_t
     }
 }
 
+// Weighted graphs: per arc j of vertex x the walk threshold
+// floor(2^32 (w_0 + .. + w_j) / d_x) (exact: prefix < 2^31, so prefix 2^32
+// fits 64 bits). A warp per vertex; its lanes scan the prefix in chunks of 32.
+__global__ void build_cum_kernel(const int64_t *__restrict__ indptr, const uint32_t *__restrict__ w,
+                                 const uint32_t *__restrict__ wdeg, int64_t n, uint32_t *__restrict__ cum) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); x < n; x += warps) {
+        const int64_t a0 = indptr[x], a1 = indptr[x + 1];
+        const uint64_t d = __ldg(wdeg + x);
+        uint64_t carry = 0;
+        for (int64_t base = a0; base < a1; base += 32) {
+            const int64_t a = base + lane;
+            uint64_t v = a < a1 ? (uint64_t)__ldg(w + a) : 0ull;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            const uint64_t prefix = carry + v;
+            // the last arc's threshold would be 2^32: it is never read
+            const uint64_t t = (prefix << 32) / d;
+            if (a < a1) cum[a] = t > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)t;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+}
+
 __device__ __forceinline__ int32_t arc_source(const int64_t *__restrict__ indptr, int64_t n,
                                               int64_t a) {
     int64_t lo = 0, hi = n;   // indptr[lo] <= a < indptr[hi]
@@ -170,8 +212,15 @@ __device__ __forceinline__ void walk_step(const WalkArgs &A, WalkCur &c, uint32_
     const int64_t off = (int64_t)c.off_lo | ((int64_t)(c.hidg & 0xFF) << 32);
     if (deg == 0) return;   // only on graphs that break the contract
     uint32_t j;
-    if (deg == 0xFFFFFFu) {
-        deg = (uint32_t)(__ldg(A.indptr + c.x + 1) - __ldg(A.indptr + c.x));
+    if (deg == 0xFFFFFFu) deg = (uint32_t)(__ldg(A.indptr + c.x + 1) - __ldg(A.indptr + c.x));
+    if (A.cum) {   // weighted: inverse CDF over the vertex's thresholds (the last is 2^32)
+        uint32_t lo = 0, hi = deg - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (w < __ldg(A.cum + off + mid)) hi = mid; else lo = mid + 1;
+        }
+        j = lo;
+    } else if ((c.hidg >> 8) == 0xFFFFFFu) {
         j = w % deg;
     } else {
         j = deg == 1 ? 0u : barrett_mod(w, c.m, deg);
@@ -376,7 +425,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
     if (tid == 0) s_off[na] = total;
     __syncthreads();
     const int64_t out0 = tile_off ? tile_off[blockIdx.x] : 0;
-    const bool uniform = A.thr_frac == 0;
+    const bool uniform = A.thr_frac == 0 && !A.w;
     // sample s of the tile -> (arc within the tile, sample index j on that arc)
     auto locate = [&](uint32_t s, int &lo, uint32_t &j) {
         if (uniform) {
@@ -665,7 +714,13 @@ __global__ void compact_kernel(const KeyT *__restrict__ rkey, const uint32_t *__
 struct NetmfConst {
     double a_off, a_diag;              // alpha = vol^2 / (2 S b), vol^2 / (S b)
     float off_hi, off_lo, diag_hi, diag_lo;
+    const uint32_t *wdeg;              // weighted degrees (weighted graphs), else NULL
 };
+
+// The degree of Eq. 1: weighted when the graph is, else the arc count.
+__device__ __forceinline__ int64_t eq1_degree(const NetmfConst &k, const int64_t *__restrict__ indptr, int64_t x) {
+    return k.wdeg ? (int64_t)__ldg(k.wdeg + x) : __ldg(indptr + x + 1) - __ldg(indptr + x);
+}
 
 // Eq. 1 entry with the truncated log for count K of pair (x, y):
 // v = fl(fl(K alpha) / fl(d_x d_y)), kept iff v > 1, value log(v) as float32
@@ -744,11 +799,11 @@ __device__ __forceinline__ float netmf_value_w(uint64_t wsum, int64_t dx, int64_
 __global__ void table_values_w_kernel(const uint64_t *__restrict__ W, uint32_t *__restrict__ T, int64_t ld, int n,
                                       const int64_t *__restrict__ indptr, NetmfConst kc) {
     const int x = blockIdx.x;
-    const int64_t dx = __ldg(indptr + x + 1) - __ldg(indptr + x);
+    const int64_t dx = eq1_degree(kc, indptr, x);
     for (int y = x + threadIdx.x; y < n; y += blockDim.x) {
         const uint64_t w = W[(size_t)x * ld + y];
         if (w == 0) continue;
-        const int64_t dy = __ldg(indptr + y + 1) - __ldg(indptr + y);
+        const int64_t dy = eq1_degree(kc, indptr, y);
         T[(size_t)x * ld + y] = __float_as_uint(netmf_value_w(w, dx, dy, x == y, kc));
     }
 }
@@ -758,17 +813,20 @@ __global__ void table_values_w_kernel(const uint64_t *__restrict__ W, uint32_t *
 // IEEE rounding (Sec. 4.1, degree sampling). A warp per source vertex, its
 // lanes over the vertex's arcs (degrees are skewed).
 __global__ void downsample_arcs_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict__ indices,
+                                       const uint32_t *__restrict__ aw, const uint32_t *__restrict__ wdeg,
                                        int64_t n, double C, uint64_t *__restrict__ thr, uint64_t *__restrict__ w) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t u = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); u < n; u += warps) {
         const int64_t a0 = indptr[u], a1 = indptr[u + 1];
         if (a1 == a0) continue;
-        const double iu = __ddiv_rn(1.0, (double)(a1 - a0));
+        const double iu = __ddiv_rn(1.0, wdeg ? (double)__ldg(wdeg + u) : (double)(a1 - a0));
         for (int64_t a = a0 + lane; a < a1; a += 32) {
             const int32_t v = __ldg(indices + a);
-            const double iv = __ddiv_rn(1.0, (double)(__ldg(indptr + v + 1) - __ldg(indptr + v)));
+            const double dv = wdeg ? (double)__ldg(wdeg + v) : (double)(__ldg(indptr + v + 1) - __ldg(indptr + v));
+            const double iv = __ddiv_rn(1.0, dv);
             double p = __dmul_rn(C, __dadd_rn(iu, iv));
+            if (aw) p = __dmul_rn((double)__ldg(aw + a), p);   // p_e = min(1, A_uv (C (1/d_u + 1/d_v)))
             if (p >= 1.0) p = 1.0;
             thr[a] = p >= 1.0 ? (1ull << 32) : (uint64_t)floor(__dmul_rn(p, 4294967296.0));
             w[a] = (uint64_t)floor(__dadd_rn(__ddiv_rn(4294967296.0, p), 0.5));
@@ -784,8 +842,8 @@ __global__ void trunclog_kernel(const int32_t *__restrict__ x, const int32_t *__
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t xi = x[i], yi = y[i];
-        const int64_t dx = __ldg(indptr + xi + 1) - __ldg(indptr + xi);
-        const int64_t dy = __ldg(indptr + yi + 1) - __ldg(indptr + yi);
+        const int64_t dx = eq1_degree(kc, indptr, xi);
+        const int64_t dy = eq1_degree(kc, indptr, yi);
         const float v = netmf_value(cnt[i], dx, dy, xi == yi, kc);
         const bool k = v > 0.f;
         if (k) {
@@ -877,12 +935,12 @@ constexpr int kTile = 64;
 __global__ void table_values_kernel(uint32_t *__restrict__ T, int64_t ld, int n,
                                     const int64_t *__restrict__ indptr, NetmfConst kc) {
     const int x = blockIdx.x;
-    const int64_t dx = __ldg(indptr + x + 1) - __ldg(indptr + x);
+    const int64_t dx = eq1_degree(kc, indptr, x);
     uint32_t *row = T + (size_t)x * ld;
     for (int y = x + threadIdx.x; y < n; y += blockDim.x) {
         const uint32_t c = row[y];
         if (c == 0) continue;
-        const int64_t dy = __ldg(indptr + y + 1) - __ldg(indptr + y);
+        const int64_t dy = eq1_degree(kc, indptr, y);
         row[y] = __float_as_uint(netmf_value(c, dx, dy, x == y, kc));
     }
 }
@@ -1257,6 +1315,11 @@ WalkArgs make_walk_args(const GraphView &g, const SamplerSpec &sp) {
     A.ds_thr = nullptr;
     A.ds_w = nullptr;
     A.strat = sp.stratified;
+    A.w = g.w;
+    A.cum = nullptr;
+    A.S = sp.S;
+    A.vol = g.vol;
+    A.wmax = g.wmax;
     A.base_magic = sp.base > 0 ? (~0ull) / sp.base + 1ull : 0ull;
     A.rmagic[0] = 0;
     for (int r = 1; r <= 16; ++r) A.rmagic[r] = (~0ull) / (uint64_t)r + 1ull;
@@ -1281,6 +1344,15 @@ int attach_vinfo(Workspace &ws, const GraphView &g, WalkArgs *A, cudaStream_t st
         LNE_LAUNCH_CHECK();
     }
     A->arcrec = ar;
+    if (g.w) {
+        uint32_t *cum = nullptr;
+        LNE_TRY(ws.get("walk.cum", (size_t)std::max<int64_t>(g.nnz, 1), &cum));
+        LNE_TRACE("build_vinfo", st);
+        build_cum_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g.n, 8), 152 * 16)), 256, 0,
+                           st>>>(g.indptr, g.w, g.wdeg, g.n, cum);
+        LNE_LAUNCH_CHECK();
+        A->cum = cum;
+    }
     return 0;
 }
 
@@ -1293,7 +1365,7 @@ int attach_downsample(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
     LNE_TRACE("downsample_arcs", st);
     downsample_arcs_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g.n, 8), 152 * 16)), 256, 0,
                              st>>>(
-        g.indptr, g.indices, g.n, sp.ds_C, thr, w);
+        g.indptr, g.indices, g.w, g.wdeg, g.n, sp.ds_C, thr, w);
     LNE_LAUNCH_CHECK();
     A->ds_thr = thr;
     A->ds_w = w;
@@ -1321,6 +1393,7 @@ NetmfConst netmf_const(const SamplerSpec &sp) {
     k.off_lo = sp.off_lo;
     k.diag_hi = sp.diag_hi;
     k.diag_lo = sp.diag_lo;
+    k.wdeg = sp.wdeg;
     return k;
 }
 
@@ -1331,6 +1404,11 @@ int walk_smem_bytes(int tile_arcs, int nb_smem) {
 // Per-tile offsets of arcs [a0, a1): returns the total number of samples.
 int tile_offsets(Workspace &ws, const WalkArgs &A, int64_t a0, int64_t a1, int tile_arcs,
                  int64_t **tile_off, int64_t *total, cudaStream_t st) {
+    if (A.w) {   // a tile's sample count is a 32-bit sum: bound it by the heaviest arc
+        const double max_rate = A.S * (double)A.wmax / A.vol;
+        if ((max_rate + 1.0) * (double)tile_arcs >= 2147483648.0)
+            return fail(LNE_ERR_UNSUPPORTED, "an arc's weight share of S is too large for the sample tiles");
+    }
     const int64_t ntiles = ceil_div(a1 - a0, tile_arcs);
     uint32_t *tile_cnt = nullptr;
     LNE_TRY(ws.get("walk.tile_cnt", (size_t)ntiles, &tile_cnt));
@@ -1385,7 +1463,8 @@ int make_sampler_spec(const GraphView &g, int T, const double *s, double S, doub
     while (((int64_t)1 << B) < g.n) ++B;
     sp.B = B;
     if (b <= 0.0) b = 1.0;
-    const double vol = (double)g.nnz;
+    const double vol = g.w ? g.vol : (double)g.nnz;
+    sp.wdeg = g.wdeg;
     const double vv = vol * vol;
     sp.alpha_off = vv / ((2.0 * S) * b);
     sp.alpha_diag = vv / (S * b);
@@ -1820,11 +1899,13 @@ int sort_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult
     LNE_TRY(ws.get("path.deg", (size_t)n, &deg));
     {
         LNE_TRACE("path_value", st);
-        degree_kernel<<<egrid, 256, 0, st>>>(g.indptr, n, deg);
-        LNE_LAUNCH_CHECK();
+        if (!g.wdeg) {
+            degree_kernel<<<egrid, 256, 0, st>>>(g.indptr, n, deg);
+            LNE_LAUNCH_CHECK();
+        }
         // values overwrite the counts (the counts are not needed afterwards)
-        path_value_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, R.w, U, sp.B, deg,
-                                                                    netmf_const(sp), tk, tm);
+        path_value_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(R.uk, R.cnt, R.w, U, sp.B,
+                                                                    g.wdeg ? g.wdeg : deg, netmf_const(sp), tk, tm);
         LNE_LAUNCH_CHECK();
     }
     return assemble_csr(ws, g, sp, R.uk, R.cnt, U, tk, tm, R.uk_name, "sort.cnt", out, st);
@@ -1958,6 +2039,44 @@ int table_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResul
     out->dense = reinterpret_cast<const float *>(tb.T);
     out->dense_ld = tb.ld;
     return 0;
+}
+
+// ---- weighted graphs ----------------------------------------------------------
+
+// A warp per vertex: d_u = sum of its arc weights (exact, 64-bit), 1 / d_u and
+// the float weights for the graph products, d_u added into the volume. flags
+// bit 0: a zero weight, bit 1: a degree of 2^31 or more.
+__global__ void weighted_prep_kernel(const int64_t *__restrict__ indptr, const uint32_t *__restrict__ w, int64_t n,
+                                     uint32_t *__restrict__ wdeg, float *__restrict__ dinv, float *__restrict__ wf,
+                                     unsigned long long *__restrict__ vol, unsigned int *__restrict__ flags,
+                                     unsigned int *__restrict__ wmax) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); x < n; x += warps) {
+        const int64_t a0 = indptr[x], a1 = indptr[x + 1];
+        uint64_t d = 0;
+        bool zero = false;
+        uint32_t mx = 0;
+        for (int64_t a = a0 + lane; a < a1; a += 32) {
+            const uint32_t v = __ldg(w + a);
+            zero |= v == 0u;
+            d += v;
+            mx = v > mx ? v : mx;
+            wf[a] = (float)v;
+        }
+        if (mx) atomicMax(wmax, mx);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        zero = __any_sync(0xffffffffu, zero);
+        if (lane == 0) {
+            const bool big = d >= (1ull << 31);
+            wdeg[x] = big ? 0u : (uint32_t)d;
+            dinv[x] = d > 0 ? 1.f / (float)d : 0.f;
+            atomicAdd(vol, (unsigned long long)d);
+            if (zero) atomicOr(flags, 1u);
+            if (big) atomicOr(flags, 2u);
+        }
+    }
 }
 
 // ---- window-stratified counts --------------------------------------------
@@ -2094,6 +2213,37 @@ CsrView product_view(const CsrResult &M, int dense_mode) {
     return v;
 }
 
+int prepare_weighted(Workspace &ws, GraphView *g, cudaStream_t st) {
+    if (!g->w) return 0;
+    uint32_t *wdeg = nullptr;
+    float *dinv = nullptr, *wf = nullptr;
+    unsigned long long *acc = nullptr;
+    LNE_TRY(ws.get("wg.deg", (size_t)std::max<int64_t>(g->n, 1), &wdeg));
+    LNE_TRY(ws.get("wg.dinv", (size_t)std::max<int64_t>(g->n, 1), &dinv));
+    LNE_TRY(ws.get("wg.wf", (size_t)std::max<int64_t>(g->nnz, 1), &wf));
+    LNE_TRY(ws.get("wg.acc", 3, &acc));   // [0] volume, [1] flags, [2] largest weight
+    LNE_CUDA_TRY(cudaMemsetAsync(acc, 0, 3 * sizeof(unsigned long long), st));
+    if (g->n > 0) {
+        LNE_TRACE("build_vinfo", st);
+        weighted_prep_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g->n, 8), 152 * 16)), 256, 0,
+                               st>>>(g->indptr, g->w, g->n, wdeg, dinv, wf, acc,
+                                     reinterpret_cast<unsigned int *>(acc + 1),
+                                     reinterpret_cast<unsigned int *>(acc + 2));
+        LNE_LAUNCH_CHECK();
+    }
+    unsigned long long h[3] = {0, 0, 0};
+    LNE_CUDA_TRY(cudaMemcpyAsync(h, acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h[1] & 1ull) return fail(LNE_ERR_INVALID, "arc weights must be positive integers");
+    if (h[1] & 2ull) return fail(LNE_ERR_UNSUPPORTED, "weighted degrees must stay below 2^31");
+    g->wdeg = wdeg;
+    g->dinv = dinv;
+    g->wf = wf;
+    g->vol = (double)h[0];
+    g->wmax = (uint32_t)h[2];
+    return 0;
+}
+
 int stratified_sample(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Strata *out, cudaStream_t st) {
     stratified_release(ws);
     int64_t total = 0, U = 0, P = 0;
@@ -2160,10 +2310,13 @@ int stratified_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, con
     if (P > 0) LNE_CUDA_TRY(cudaMemcpyAsync(uk, S.pair, sizeof(uint64_t) * P, cudaMemcpyDeviceToDevice, st));
     {
         LNE_TRACE("path_value", st);
-        degree_kernel<<<egrid, 256, 0, st>>>(g.indptr, n, deg);
-        LNE_LAUNCH_CHECK();
-        strat_value_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(S.pair, S.seg, S.r, S.cnt, P, sp.B, deg,
-                                                                     netmf_const(sp), w, val, tk, tm);
+        if (!g.wdeg) {
+            degree_kernel<<<egrid, 256, 0, st>>>(g.indptr, n, deg);
+            LNE_LAUNCH_CHECK();
+        }
+        strat_value_kernel<<<(unsigned)ntiles, kPathThreads, 0, st>>>(S.pair, S.seg, S.r, S.cnt, P, sp.B,
+                                                                     g.wdeg ? g.wdeg : deg, netmf_const(sp), w,
+                                                                     val, tk, tm);
         LNE_LAUNCH_CHECK();
     }
     return assemble_csr(ws, g, sp, uk, val, P, tk, tm, "strat.cuk", "strat.cval", out, st);

@@ -59,7 +59,7 @@ template <int NT>
 __device__ __forceinline__ void epilogue(int64_t i, int64_t deg, const float (&acc)[NT], int lane, int c,
                                          float *__restrict__ Y, int64_t ldy, const SpmmEpilogue &ep) {
     float rs = ep.alpha;
-    if (ep.dinv) rs = deg > 0 ? ep.alpha / (float)deg : 0.f;
+    if (ep.dinv) rs = ep.dinv_w ? ep.alpha * __ldg(ep.dinv_w + i) : deg > 0 ? ep.alpha / (float)deg : 0.f;
 #pragma unroll
     for (int t = 0; t < NT; ++t) {
         const int cc = lane + 32 * t;
@@ -244,7 +244,7 @@ template <int NV>
 __device__ __forceinline__ void epilogue4(int64_t i, int64_t deg, const Acc4<NV> &acc, int lane, int c4,
                                           float *__restrict__ Y, int64_t ldy, const SpmmEpilogue &ep) {
     float rs = ep.alpha;
-    if (ep.dinv) rs = deg > 0 ? ep.alpha / (float)deg : 0.f;
+    if (ep.dinv) rs = ep.dinv_w ? ep.alpha * __ldg(ep.dinv_w + i) : deg > 0 ? ep.alpha / (float)deg : 0.f;
 #pragma unroll
     for (int t = 0; t < NV; ++t) {
         const int q = lane + 32 * t;
@@ -675,6 +675,12 @@ int spmm_bf16(Workspace &ws, const CsrView &M, const __nv_bfloat16 *X, int64_t l
 int graph_spmm_bf16(Workspace &ws, const GraphView &g, const __nv_bfloat16 *X, int64_t ldx, int c, float *Y,
                     int64_t ldy, const SpmmEpilogue &ep, cudaStream_t st) {
     if (!merge_ok(X, ldx, c, Y, ldy, ep)) return fail(LNE_ERR_UNSUPPORTED, "BF16 operands need c and ld multiples of 4");
+    if (g.w) {   // weighted: sum_y A_xy X_y, scaled by 1 / d_x
+        SpmmEpilogue ew = ep;
+        ew.dinv_w = ep.dinv ? g.dinv : nullptr;
+        return launch_merge<true, __nv_bfloat16>(ws, g.n, g.nnz, g.indptr, g.indices, g.wf, X, ldx, c, Y, ldy, ew,
+                                                 st);
+    }
     return launch_merge<false, __nv_bfloat16>(ws, g.n, g.nnz, g.indptr, g.indices, nullptr, X, ldx, c, Y, ldy, ep, st);
 }
 
@@ -695,6 +701,13 @@ int to_bf16(const float *in, __nv_bfloat16 *out, int64_t count, cudaStream_t st)
 
 int graph_spmm(Workspace &ws, const GraphView &g, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
                const SpmmEpilogue &ep, cudaStream_t st) {
+    if (g.w) {   // weighted: sum_y A_xy X_y, scaled by 1 / d_x
+        SpmmEpilogue ew = ep;
+        ew.dinv_w = ep.dinv ? g.dinv : nullptr;
+        if (merge_ok(X, ldx, c, Y, ldy, ew))
+            return launch_merge<true, float>(ws, g.n, g.nnz, g.indptr, g.indices, g.wf, X, ldx, c, Y, ldy, ew, st);
+        return launch_spmm<true>(g.n, g.indptr, g.indices, g.wf, X, ldx, c, Y, ldy, ew, st);
+    }
     if (merge_ok(X, ldx, c, Y, ldy, ep))
         return launch_merge<false, float>(ws, g.n, g.nnz, g.indptr, g.indices, nullptr, X, ldx, c, Y, ldy, ep, st);
     return launch_spmm<false>(g.n, g.indptr, g.indices, nullptr, X, ldx, c, Y, ldy, ep, st);

@@ -243,7 +243,10 @@ int tune_tasks(std::vector<std::unique_ptr<TuneWorker>> &workers, int nworkers, 
         w->tune.forced = forced_threads;
         for (int t; rc == 0 && !stop.load() && (t = next.fetch_add(1)) < ntasks;) {
             const TuneTask &k = tasks[t];
-            rc = tune_batch(w->ws, nullptr, w->tune, aggregation, dense_mode, stratified, k.g,
+            GraphView gk = k.g;
+            rc = prepare_weighted(w->ws, &gk, w->st);
+            if (rc == 0)
+                rc = tune_batch(w->ws, nullptr, w->tune, aggregation, dense_mode, stratified, gk,
                             cands + (size_t)t * ncand, ncand, k.labels,
                             k.L, k.train, k.n_train, k.test, k.n_test, Creg, iters, macro + (size_t)t * ncand,
                             micro + (size_t)t * ncand, nullptr, w->st);

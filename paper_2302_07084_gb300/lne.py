@@ -53,7 +53,7 @@ class LneError(RuntimeError):
 
 class _Graph(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("indptr", ctypes.c_void_p),
-                ("indices", ctypes.c_void_p)]
+                ("indices", ctypes.c_void_p), ("weights", ctypes.c_void_p)]
 
 
 class _Task(ctypes.Structure):
@@ -173,17 +173,22 @@ class Params:
 
 
 class DeviceGraph:
-    """A CSR graph resident on the GPU (int64 indptr, int32 indices)."""
+    """A CSR graph resident on the GPU (int64 indptr, int32 indices, optional
+    positive integer arc weights held as their uint32 bits)."""
 
-    def __init__(self, indptr, indices, device="cuda"):
+    def __init__(self, indptr, indices, device="cuda", weights=None):
         self.indptr = torch.as_tensor(np.asarray(indptr, dtype=np.int64)).to(device)
         self.indices = torch.as_tensor(np.asarray(indices, dtype=np.int32)).to(device)
         self.n = int(self.indptr.numel() - 1)
         self.nnz = int(self.indices.numel())
+        self.weights = None
+        if weights is not None:
+            w = np.ascontiguousarray(weights, dtype=np.uint32)
+            self.weights = torch.as_tensor(w.view(np.int32)).to(device)
 
     @classmethod
-    def from_graph(cls, g, device="cuda"):
-        return cls(g.indptr, g.indices, device)
+    def from_graph(cls, g, device="cuda", weights=None):
+        return cls(g.indptr, g.indices, device, weights=weights)
 
     @classmethod
     def from_tensors(cls, indptr: torch.Tensor, indices: torch.Tensor):
@@ -193,10 +198,12 @@ class DeviceGraph:
         g.indices = indices.contiguous()
         g.n = int(indptr.numel() - 1)
         g.nnz = int(indices.numel())
+        g.weights = None
         return g
 
     def _c(self):
-        return _Graph(self.n, self.nnz, self.indptr.data_ptr(), self.indices.data_ptr() if self.nnz else None)
+        w = self.weights.data_ptr() if self.weights is not None and self.nnz else None
+        return _Graph(self.n, self.nnz, self.indptr.data_ptr(), self.indices.data_ptr() if self.nnz else None, w)
 
 
 class _DevView:
@@ -303,8 +310,11 @@ class Context:
                      capacity: Optional[int] = None):
         arc_end = g.nnz if arc_end is None else arc_end
         if capacity is None:
-            rate = float(p.samples) / max(g.nnz, 1)
-            capacity = int((arc_end - arc_begin) * (np.floor(rate) + 1)) + 1
+            if getattr(g, "weights", None) is not None:   # per-arc rates vary: S + one per arc bounds them
+                capacity = int(np.ceil(float(p.samples))) + (arc_end - arc_begin) + 1
+            else:
+                rate = float(p.samples) / max(g.nnz, 1)
+                capacity = int((arc_end - arc_begin) * (np.floor(rate) + 1)) + 1
         u1 = torch.empty(capacity, dtype=torch.int32, device=self.dev)
         v1 = torch.empty(capacity, dtype=torch.int32, device=self.dev)
         cnt = ctypes.c_int64()
