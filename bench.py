@@ -272,7 +272,11 @@ def run_ours(args):
         params["sketch"] = lne.SKETCH_SPARSE_SIGN
     P = lne.Params(**params)
     ctx = lne.Context(local)
-    dg = lne.DeviceGraph(g.indptr, g.indices, device=dev)
+    weights = None
+    if args.weighted:   # integer weights 1..9 on both arcs of every edge (seeded)
+        from paper_2302_07084_gb300 import synth
+        weights = synth.edge_weights(g, 1, 9, seed=2)
+    dg = lne.DeviceGraph(g.indptr, g.indices, device=dev, weights=weights)
     X = torch.empty((g.n, P.d), dtype=torch.float32, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream()
@@ -326,6 +330,7 @@ def run_ours(args):
     # ---- e2e: host buffers, copies inside the timed region ----
     indptr_h = torch.from_numpy(g.indptr.astype(np.int64)).pin_memory()
     indices_h = torch.from_numpy(g.indices.astype(np.int32)).pin_memory()
+    weights_h = torch.from_numpy(weights.view(np.int32)).pin_memory() if weights is not None else None
     X_h = torch.empty((g.n, P.d), dtype=torch.float32).pin_memory()
     e2e_ms = []
     for _ in range(max(1, min(args.steps, 5))):
@@ -335,6 +340,8 @@ def run_ours(args):
         e0.record(stream)
         dg.indptr.copy_(indptr_h, non_blocking=True)
         dg.indices.copy_(indices_h, non_blocking=True)
+        if weights_h is not None:
+            dg.weights.copy_(weights_h, non_blocking=True)
         ctx.embed(dg, P, out=X)
         X_h.copy_(X, non_blocking=True)
         e1.record(stream)
@@ -372,7 +379,8 @@ def run_ours(args):
 
     if rank == 0:
         cpu = None
-        if world == 1 and not args.no_cpu_baseline and not args.downsample and args.sketch == "gaussian":
+        if (world == 1 and not args.no_cpu_baseline and not args.downsample and args.sketch == "gaussian"
+                and not args.weighted):
             r = oracle_step(g, params, rep=0)
             cpu = {"value": r["value"], "unit": "samples/s", "cores": r["cores"], "kind": "oracle",
                    "sample": r["sample"]}
@@ -380,14 +388,16 @@ def run_ours(args):
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WORKLOAD + ("_downsampled_C=ln_n" if args.downsample else "")
-                           + ("_sparse_sign_sketch" if args.sketch == "sparse_sign" else ""),
+                           + ("_sparse_sign_sketch" if args.sketch == "sparse_sign" else "")
+                           + ("_weighted_1to9" if args.weighted else ""),
                            "n": g.n, "m": g.m, "samples": params["samples"], "T": 10,
                            "d": 128, "q": 1, "k": 10, "l2": "flushed (256 MB write) between steps",
                            "parallelism": f"replicas{world}", "nnz_pairs": info["nnz_c"],
                            "nnz_M": info["nnz_M"],
                            **({"downsample_C": params["downsample_C"]} if args.downsample else {})},
                 "e2e": {"value": world * params["samples"] / (e2e / 1e3), "unit": "samples/s",
-                        "h2d_bytes_per_step": int(g.indptr.nbytes + g.indices.astype(np.int32).nbytes),
+                        "h2d_bytes_per_step": int(g.indptr.nbytes + g.indices.astype(np.int32).nbytes
+                                                  + (weights.nbytes if weights is not None else 0)),
                         "d2h_bytes_per_step": int(g.n * P.d * 4), "ms_per_step": e2e},
                 "gpu_launches": int(launches), "roofline": roof, "cpu_baseline": cpu, "clocks": clk,
                 "kernel_ms_per_step": breakdown}
@@ -644,6 +654,8 @@ def main():
                     help="the benchmark with edge downsampling at C = ln n (draws per second; no CPU baseline)")
     ap.add_argument("--sketch", choices=["gaussian", "sparse_sign"], default="gaussian",
                     help="test matrix of the randomized SVD (sparse sign: zeta = 8 nonzeros per row)")
+    ap.add_argument("--weighted", action="store_true",
+                    help="the benchmark graph with integer edge weights 1..9 (draws per second; no CPU baseline)")
     ap.add_argument("--large", action="store_true",
                     help="the 10M-vertex BF16 precision run instead of the benchmark (--scale divides its size)")
     args = ap.parse_args()
