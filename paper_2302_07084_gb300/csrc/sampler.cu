@@ -70,6 +70,7 @@ struct WalkArgs {
     // (first j with word < cum[off + j], cum = floor(2^32 prefix_j / d_x))
     const uint32_t *w;
     const uint32_t *cum;
+    const uint32_t *guide;        // per arc b of x: the answer for the smallest word of bucket b
     double S, vol;
     uint32_t wmax;                // host copy of the largest weight (tile size bounds)
 };
@@ -175,6 +176,29 @@ __global__ void build_cum_kernel(const int64_t *__restrict__ indptr, const uint3
     }
 }
 
+// Guide of the weighted step: for bucket b of vertex x (words w with
+// floor(w deg / 2^32) = b) the answer for the bucket's smallest word
+// ceil(b 2^32 / deg); the inverse CDF is monotone in w, so a word of bucket b
+// takes an arc between guide[b] and guide[b + 1] (or the last arc).
+__global__ void build_guide_kernel(const int64_t *__restrict__ indptr, const uint32_t *__restrict__ cum, int64_t n,
+                                   uint32_t *__restrict__ guide) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t x = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); x < n; x += warps) {
+        const int64_t a0 = indptr[x];
+        const uint64_t deg = (uint64_t)(indptr[x + 1] - a0);
+        for (uint64_t b = lane; b < deg; b += 32) {
+            const uint64_t w0 = ((b << 32) + deg - 1) / deg;   // ceil(b 2^32 / deg) < 2^32
+            uint32_t lo = 0, hi = (uint32_t)deg - 1;           // first j with w0 < cum[j], else the last
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (w0 < (uint64_t)cum[a0 + mid]) hi = mid; else lo = mid + 1;
+            }
+            guide[a0 + (int64_t)b] = lo;
+        }
+    }
+}
+
 __device__ __forceinline__ int32_t arc_source(const int64_t *__restrict__ indptr, int64_t n,
                                               int64_t a) {
     int64_t lo = 0, hi = n;   // indptr[lo] <= a < indptr[hi]
@@ -206,15 +230,21 @@ __device__ __forceinline__ uint32_t barrett_mod(uint32_t w, uint32_t m, uint32_t
 }
 
 // One walk step: x <- nbr(x)[w mod deg(x)] (Sec. 4.2), reading the taken
-// arc's record.
+// arc's record. GEN: the variant that also handles weighted graphs.
+template <bool GEN>
 __device__ __forceinline__ void walk_step(const WalkArgs &A, WalkCur &c, uint32_t w) {
     uint32_t deg = c.hidg >> 8;
     const int64_t off = (int64_t)c.off_lo | ((int64_t)(c.hidg & 0xFF) << 32);
     if (deg == 0) return;   // only on graphs that break the contract
     uint32_t j;
     if (deg == 0xFFFFFFu) deg = (uint32_t)(__ldg(A.indptr + c.x + 1) - __ldg(A.indptr + c.x));
-    if (A.cum) {   // weighted: inverse CDF over the vertex's thresholds (the last is 2^32)
-        uint32_t lo = 0, hi = deg - 1;
+    if (GEN && A.cum) {
+        // weighted: inverse CDF over the vertex's thresholds (the last is
+        // 2^32). The word's bucket b = floor(w deg / 2^32) brackets the
+        // answer between the guides of buckets b and b + 1, usually one arc.
+        const uint32_t b = __umulhi(w, deg);
+        uint32_t lo = __ldg(A.guide + off + b);
+        uint32_t hi = b + 1 < deg ? __ldg(A.guide + off + b + 1) : deg - 1;
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
             if (w < __ldg(A.cum + off + mid)) hi = mid; else lo = mid + 1;
@@ -278,13 +308,13 @@ __device__ __forceinline__ void draw_begin(const WalkArgs &A, int64_t arc, uint3
 }
 
 // Step k (word 3 + k) of the draw, if it has one.
-template <int K>
+template <int K, bool GEN>
 __device__ __forceinline__ void draw_step(const WalkArgs &A, Draw &d) {
     if (K >= d.steps) return;
     constexpr int widx = 3 + K;
     if ((widx & 3) == 0) d.nb = philox_rk(u32x4{d.j, d.c1, d.c2, (uint32_t)(widx >> 2)}, A.rk);
     const uint32_t w = (widx & 3) == 0 ? d.nb.x : (widx & 3) == 1 ? d.nb.y : (widx & 3) == 2 ? d.nb.z : d.nb.w;
-    walk_step(A, d.cur, w);
+    walk_step<GEN>(A, d.cur, w);
     if (K + 1 == d.sigma && K + 1 < d.steps) {   // u side done: continue from v
         d.uend = d.cur.x;
         d.cur = walk_start(A, d.v);
@@ -301,17 +331,17 @@ __device__ __forceinline__ void draw_end(const Draw &d, int32_t *pu, int32_t *pv
     }
 }
 
-template <int K>
+template <int K, bool GEN>
 struct StepAll {
     __device__ __forceinline__ static void run(const WalkArgs &A, Draw &a, Draw &b, int kmax) {
         if (K >= kmax) return;
-        draw_step<K>(A, a);
-        draw_step<K>(A, b);
-        StepAll<K + 1>::run(A, a, b, kmax);
+        draw_step<K, GEN>(A, a);
+        draw_step<K, GEN>(A, b);
+        StepAll<K + 1, GEN>::run(A, a, b, kmax);
     }
 };
-template <>
-struct StepAll<15> {
+template <bool GEN>
+struct StepAll<15, GEN> {
     __device__ __forceinline__ static void run(const WalkArgs &, Draw &, Draw &, int) {}
 };
 
@@ -381,8 +411,10 @@ __global__ void __launch_bounds__(kWalkThreads) tile_counts_kernel(WalkArgs A, i
 // MODE 0: write ordered endpoint pairs (u1, v1). MODE 1: write canonical keys
 // and count key buckets. MODE 2: add the pair into the dense count table
 // table[x * ld + y] (x <= y); `keys` is the table, ld = nb_smem. MODE 3: write
-// the canonical key at the sample's position (no counting).
-template <typename KeyT, int MODE>
+// the canonical key at the sample's position (no counting). GEN = false is the
+// variant for unweighted graphs without downsampling or window strata (the
+// checks for those compiled out); GEN = true handles everything.
+template <typename KeyT, int MODE, bool GEN>
 __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_kernel(
     WalkArgs A, int64_t a_begin, int64_t a_end, int tile_arcs, const int64_t *__restrict__ tile_off,
     KeyT *__restrict__ keys, int32_t *__restrict__ u1, int32_t *__restrict__ v1,
@@ -425,7 +457,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
     if (tid == 0) s_off[na] = total;
     __syncthreads();
     const int64_t out0 = tile_off ? tile_off[blockIdx.x] : 0;
-    const bool uniform = A.thr_frac == 0 && !A.w;
+    const bool uniform = A.thr_frac == 0 && !(GEN && A.w);
     // sample s of the tile -> (arc within the tile, sample index j on that arc)
     auto locate = [&](uint32_t s, int &lo, uint32_t &j) {
         if (uniform) {
@@ -466,7 +498,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
         } else if (MODE == 3) {
             const uint32_t x = (uint32_t)min(pu, pv), y = (uint32_t)max(pu, pv);
             const KeyT key = ((KeyT)x << A.B) | (KeyT)y;
-            keys[out0 + s] = A.strat ? (key << 4) | (KeyT)(r - 1u) : key;
+            keys[out0 + s] = (GEN && A.strat) ? (key << 4) | (KeyT)(r - 1u) : key;
             if (u1) reinterpret_cast<uint32_t *>(u1)[out0 + s] = (uint32_t)arc;   // the draw's arc
         } else {
             const uint32_t x = (uint32_t)min(pu, pv), y = (uint32_t)max(pu, pv);
@@ -499,7 +531,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
                 s_lo[idx] = (uint16_t)lo;
                 draw_head(A, s_rlut, s_rmagic, a0 + lo, j, &r, &sg, &coin, &w3);
                 // edge downsampling (Algorithm 3): the draw walks only if its coin comes up heads
-                if (A.ds_thr && (uint64_t)coin >= __ldg(A.ds_thr + a0 + lo)) {
+                if (GEN && A.ds_thr && (uint64_t)coin >= __ldg(A.ds_thr + a0 + lo)) {
                     emit_dropped(cb + idx, a0 + lo);
                     r = 0;
                 }
@@ -564,7 +596,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
             draw_begin(A, a0 + lo1, j1, (int)((pk1 >> 11) & 31), (int)((pk1 >> 16) & 15), s_w3[has1 ? q1 : q0],
                        s_src[lo1], s_dst[lo1], d1);
             if (!has1) d1.steps = 0;
-            StepAll<0>::run(A, d0, d1, max(d0.steps, d1.steps));
+            StepAll<0, GEN>::run(A, d0, d1, max(d0.steps, d1.steps));
             int32_t pu, pv;
             draw_end(d0, &pu, &pv);
             emit(s0, a0 + lo0, pu, pv, (pk0 >> 11) & 31);
@@ -1317,6 +1349,7 @@ WalkArgs make_walk_args(const GraphView &g, const SamplerSpec &sp) {
     A.strat = sp.stratified;
     A.w = g.w;
     A.cum = nullptr;
+    A.guide = nullptr;
     A.S = sp.S;
     A.vol = g.vol;
     A.wmax = g.wmax;
@@ -1351,7 +1384,13 @@ int attach_vinfo(Workspace &ws, const GraphView &g, WalkArgs *A, cudaStream_t st
         build_cum_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g.n, 8), 152 * 16)), 256, 0,
                            st>>>(g.indptr, g.w, g.wdeg, g.n, cum);
         LNE_LAUNCH_CHECK();
+        uint32_t *guide = nullptr;
+        LNE_TRY(ws.get("walk.guide", (size_t)std::max<int64_t>(g.nnz, 1), &guide));
+        build_guide_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g.n, 8), 152 * 16)), 256, 0,
+                             st>>>(g.indptr, cum, g.n, guide);
+        LNE_LAUNCH_CHECK();
         A->cum = cum;
+        A->guide = guide;
     }
     return 0;
 }
@@ -1402,6 +1441,24 @@ int walk_smem_bytes(int tile_arcs, int nb_smem) {
 }
 
 // Per-tile offsets of arcs [a0, a1): returns the total number of samples.
+// Launches the walk kernel variant the arguments need (see walk_emit_kernel).
+template <typename KeyT, int MODE>
+int launch_walk_emit(const WalkArgs &A, unsigned grid, int smem, cudaStream_t st, int64_t a_begin, int64_t a_end,
+                     int tile_arcs, const int64_t *tile_off, KeyT *keys, int32_t *u1, int32_t *v1,
+                     uint32_t *bucket_cnt, int nb_smem) {
+    if (A.ds_thr || A.cum || A.w || A.strat) {
+        LNE_TRY(allow_dynamic_smem(walk_emit_kernel<KeyT, MODE, true>));
+        walk_emit_kernel<KeyT, MODE, true><<<grid, kWalkThreads, smem, st>>>(A, a_begin, a_end, tile_arcs, tile_off,
+                                                                            keys, u1, v1, bucket_cnt, nb_smem);
+    } else {
+        LNE_TRY(allow_dynamic_smem(walk_emit_kernel<KeyT, MODE, false>));
+        walk_emit_kernel<KeyT, MODE, false><<<grid, kWalkThreads, smem, st>>>(A, a_begin, a_end, tile_arcs, tile_off,
+                                                                             keys, u1, v1, bucket_cnt, nb_smem);
+    }
+    LNE_LAUNCH_CHECK();
+    return 0;
+}
+
 int tile_offsets(Workspace &ws, const WalkArgs &A, int64_t a0, int64_t a1, int tile_arcs,
                  int64_t **tile_off, int64_t *total, cudaStream_t st) {
     if (A.w) {   // a tile's sample count is a 32-bit sum: bound it by the heaviest arc
@@ -1493,12 +1550,10 @@ int sample_pairs(Workspace &ws, const GraphView &g, const SamplerSpec &sp, int64
     const int64_t ntiles = ceil_div(a1 - a0, tile_arcs);
     const int smem = walk_smem_bytes(tile_arcs, 0);
     // dynamic shared memory comes on top of the kernel's static tables
-    LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint32_t, 0>));
     {
         LNE_TRACE("walk_emit", st);
-        walk_emit_kernel<uint32_t, 0><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
-            A, a0, a1, tile_arcs, tile_off, nullptr, u1, v1, nullptr, 0);
-        LNE_LAUNCH_CHECK();
+        LNE_TRY((launch_walk_emit<uint32_t, 0>(A, (unsigned)ntiles, smem, st, a0, a1, tile_arcs, tile_off, nullptr, u1,
+                                              v1, nullptr, 0)));
     }
     return 0;
 }
@@ -1542,12 +1597,10 @@ int sample_and_reduce(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
     const int nb_smem = nb <= kMaxSmemBuckets ? nb : 0;
     const int smem = walk_smem_bytes(tile_arcs, nb_smem);
     // dynamic shared memory comes on top of the kernel's static tables
-    LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint32_t, 1>));
     {
         LNE_TRACE("walk_emit", st);
-        walk_emit_kernel<uint32_t, 1><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
-            A, 0, g.nnz, tile_arcs, tile_off, keys0, nullptr, nullptr, bucket_cnt, nb_smem);
-        LNE_LAUNCH_CHECK();
+        LNE_TRY((launch_walk_emit<uint32_t, 1>(A, (unsigned)ntiles, smem, st, 0, g.nnz, tile_arcs, tile_off, keys0,
+                                              nullptr, nullptr, bucket_cnt, nb_smem)));
     }
     LNE_TRY(scan_exclusive_u32_to_i64(bucket_cnt, R->bucket_off, nb, st));
     static_assert(sizeof(unsigned long long) == sizeof(int64_t), "cursor layout");
@@ -1725,12 +1778,10 @@ int sort_raw(Workspace &ws, const GraphView &g, const SamplerSpec &sp, SortRaw *
     }
     const int64_t ntiles = ceil_div(g.nnz, tile_arcs);
     const int smem = walk_smem_bytes(tile_arcs, 0);
-    LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint64_t, 3>));
     {
         LNE_TRACE("walk_keys", st);
-        walk_emit_kernel<uint64_t, 3><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
-            A, 0, g.nnz, tile_arcs, tile_off, k0, reinterpret_cast<int32_t *>(arc0), nullptr, nullptr, 0);
-        LNE_LAUNCH_CHECK();
+        LNE_TRY((launch_walk_emit<uint64_t, 3>(A, (unsigned)ntiles, smem, st, 0, g.nnz, tile_arcs, tile_off, k0,
+                                              reinterpret_cast<int32_t *>(arc0), nullptr, nullptr, 0)));
     }
     bool in_alt = false;
     LNE_TRY(radix_sort_u64(ws, k0, k1, arc0, arc1, total, bits, &in_alt, st));
@@ -1942,15 +1993,12 @@ int sample_table(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Table
     if (A.ds_thr) {   // downsampled: 64-bit weight sums
         LNE_TRY(ws.get("table.W", (size_t)(ld * ld), &tb->W));
         LNE_CUDA_TRY(cudaMemsetAsync(tb->W, 0, sizeof(uint64_t) * (size_t)(ld * ld), st));
-        LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint64_t, 2>));
-        walk_emit_kernel<uint64_t, 2><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
-            A, 0, g.nnz, tile_arcs, nullptr, tb->W, nullptr, nullptr, nullptr, (int)ld);
+        LNE_TRY((launch_walk_emit<uint64_t, 2>(A, (unsigned)ntiles, smem, st, 0, g.nnz, tile_arcs, nullptr, tb->W,
+                                              nullptr, nullptr, nullptr, (int)ld)));
     } else {
-        LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint32_t, 2>));
-        walk_emit_kernel<uint32_t, 2><<<(unsigned)ntiles, kWalkThreads, smem, st>>>(
-            A, 0, g.nnz, tile_arcs, nullptr, tb->T, nullptr, nullptr, nullptr, (int)ld);
+        LNE_TRY((launch_walk_emit<uint32_t, 2>(A, (unsigned)ntiles, smem, st, 0, g.nnz, tile_arcs, nullptr, tb->T,
+                                              nullptr, nullptr, nullptr, (int)ld)));
     }
-    LNE_LAUNCH_CHECK();
     return 0;
 }
 
@@ -2170,12 +2218,10 @@ int strat_keys(Workspace &ws, const GraphView &g, const SamplerSpec &sp, int64_t
     LNE_TRY(ws.get("sort.k0", (size_t)std::max<int64_t>(total, 1), &k0));
     LNE_TRY(ws.get("sort.k1", (size_t)std::max<int64_t>(total, 1), &k1));
     const int64_t ntiles = ceil_div(g.nnz, tile_arcs);
-    LNE_TRY(allow_dynamic_smem(walk_emit_kernel<uint64_t, 3>));
     {
         LNE_TRACE("walk_keys", st);
-        walk_emit_kernel<uint64_t, 3><<<(unsigned)ntiles, kWalkThreads, walk_smem_bytes(tile_arcs, 0), st>>>(
-            A, 0, g.nnz, tile_arcs, tile_off, k0, nullptr, nullptr, nullptr, 0);
-        LNE_LAUNCH_CHECK();
+        LNE_TRY((launch_walk_emit<uint64_t, 3>(A, (unsigned)ntiles, walk_smem_bytes(tile_arcs, 0), st, 0, g.nnz,
+                                              tile_arcs, tile_off, k0, nullptr, nullptr, nullptr, 0)));
     }
     bool in_alt = false;
     LNE_TRY(radix_sort_u64(ws, k0, k1, nullptr, nullptr, total, 2 * su.B + 4, &in_alt, st));
