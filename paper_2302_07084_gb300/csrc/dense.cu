@@ -767,6 +767,18 @@ static int trsm_rows(const float *Y, int64_t n, int c, int64_t ldy, const double
     return 0;
 }
 
+int cholqr1(Workspace &ws, const float *Y, int64_t n, int c, int64_t ld, float *Q, int64_t ldq, cudaStream_t st) {
+    if (c <= 0 || c > 256) return fail(LNE_ERR_INVALID, "CholeskyQR needs 1 <= c <= 256");
+    if (n < c) return fail(LNE_ERR_INVALID, "CholeskyQR needs at least as many rows as columns");
+    if ((size_t)(c * c + c) * 4 > 227 * 1024) return fail(LNE_ERR_UNSUPPORTED, "CholeskyQR column count too large");
+    double *G = nullptr, *R1 = nullptr;
+    LNE_TRY(ws.get("qr.G", (size_t)c * c, &G));
+    LNE_TRY(ws.get("qr.R1", (size_t)c * c, &R1));
+    LNE_TRY(gram(ws, Y, n, c, ld, G, st));
+    LNE_TRY(chol(ws, G, c, R1, st));
+    return trsm_rows(Y, n, c, ld, R1, Q, ldq, st);
+}
+
 int cholqr2(Workspace &ws, float *Y, int64_t n, int c, int64_t ld, double *Rout, cudaStream_t st) {
     if (c <= 0 || c > 256) return fail(LNE_ERR_INVALID, "CholeskyQR2 needs 1 <= c <= 256");
     if (n < c) return fail(LNE_ERR_INVALID, "CholeskyQR2 needs at least as many rows as columns");

@@ -105,16 +105,17 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
             LNE_TRY(mprod(Om, Ya));
         }
     }
-    // power iterations: Q = orth(Y); Y = M Q (q times)
+    // power iterations: Q = orth(Y); Y = M Q (q times). Q only has to span
+    // range(Y) well conditioned (the paper's eigSVD Q is FP32 as well): one
+    // CholeskyQR pass; the final factorisation below takes two.
     for (int it = 0; it < q; ++it) {
-        LNE_TRY(cholqr2(ws, Ya, n, c, c, nullptr, st));
+        LNE_TRY(cholqr1(ws, Ya, n, c, c, Yb, c, st));
         if (bf16) {
-            LNE_TRY(to_bf16(Ya, Xh, n * c, st));
-            LNE_TRY(spmm_bf16(ws, M, Xh, c, c, Yb, c, nullptr, st));
+            LNE_TRY(to_bf16(Yb, Xh, n * c, st));
+            LNE_TRY(spmm_bf16(ws, M, Xh, c, c, Ya, c, nullptr, st));
         } else {
-            LNE_TRY(mprod(Ya, Yb));
+            LNE_TRY(mprod(Yb, Ya));
         }
-        std::swap(Ya, Yb);
     }
     // final eigSVD of Y: U = Q(:, 1:d), Sigma(1:d)
     LNE_TRY(tall_svd(ws, Ya, n, c, d, Uo, so, st));

@@ -131,6 +131,8 @@ int spmm(Workspace &ws, const CsrView &M, const float *X, int64_t ldx, int c, fl
          cudaStream_t st);
 // Y := Q in place; R (optional, device FP64 [c][c]) receives the upper factor.
 int cholqr2(Workspace &ws, float *Y, int64_t n, int c, int64_t ld, double *R, cudaStream_t st);
+// One CholeskyQR pass: Q = Y chol(Y^T Y)^-1 (FP64 Gram and Cholesky, FP32 Q).
+int cholqr1(Workspace &ws, const float *Y, int64_t n, int c, int64_t ld, float *Q, int64_t ldq, cudaStream_t st);
 // SVD of an upper-triangular c x c FP64 R: U_R [c][c] FP64, sigma [c] descending.
 int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma, cudaStream_t st);
 // out[n][dout] = Y[n][c] * W[c][dout] (W FP64 row-major with leading dim ldw),
