@@ -568,13 +568,12 @@ def run_large(args):
     """Large-graph precision run: Chung-Lu with 10M vertices and 200M edges
     (exponent 2.2, generated on the GPU), T = 5, s_r = 0.2, S = 5 T m = 5e9,
     d = 128, q = 2, k = 10, BF16 dense operand (FP32 accumulation, FP64-accurate
-    Gram / Cholesky / small SVD). Times whole embeddings, checks sampled draws
-    bit for bit against the oracle, and reports per stage how far the BF16
-    operand path lands from the FP32 path at full size (the FP32 path's own
-    distance to the FP64 oracle is pinned on the 10k-vertex SBM by the tests).
-    `--scale` divides n and m."""
+    Gram / Cholesky / small SVD). Times whole embeddings and reports per stage
+    how far the BF16 operand path lands from the FP32 path at full size (the
+    FP32 path's own distance to the FP64 oracle is pinned on the 10k-vertex
+    SBM by the tests, and this graph's sampled draws by
+    tests/test_gpu_large.py). `--scale` divides n and m."""
     import torch
-    import oracle
     from paper_2302_07084_gb300 import lne, synth
     n, m = int(10_000_000 / args.scale), int(200_000_000 / args.scale)
     indptr, indices = synth.chung_lu_device(n, m, 2.2, seed=4)
@@ -605,17 +604,6 @@ def run_large(args):
     ctx.embed(g, p16)
     out["stage_ms"] = {r["name"]: round(r["ms"], 2) for r in ctx.trace_read()}
     ctx.trace(False)
-    # sampled draws against the oracle
-    hp, hi = indptr.cpu().numpy(), indices.cpu().numpy().astype(np.int32)
-    exact, drawn = True, 0
-    for a0 in (0, g.nnz // 2, g.nnz - 2000):
-        u1, v1 = ctx.sample_pairs(g, p16, a0, a0 + 2000)
-        tr = oracle.sample_trace(hp, hi, 5, base["s"], base["samples"], base["seed"], a0, a0 + 2000,
-                                 fields=("u1", "v1"))
-        exact &= np.array_equal(u1.cpu().numpy().astype(np.int64), tr["u1"])
-        exact &= np.array_equal(v1.cpu().numpy().astype(np.int64), tr["v1"])
-        drawn += int(u1.numel())
-    out["draws_bit_exact"] = {"ok": bool(exact), "draws": drawn, "arc_ranges": 3}
     # per-stage distance of the BF16 path from the FP32 path
     csr = ctx.sparsifier_csr(g, p32, copy=False)
     out["config"]["nnz_M"] = csr["nnz"]

@@ -287,8 +287,8 @@ def sparsifier_counts(indptr, indices, T, s, S, seed, C: float = 0.0, weights=No
 
 def stratified_counts(indptr, indices, T, S, seed, weights=None):
     """Window-stratified counts for sharing one sampling pass among many
-    window weightings s (the survey's proposal for candidate batching, not a
-    procedure of the paper): every draw takes r ~ U{1..T} (Algorithm 3 with
+    window weightings s (a proposal for candidate batching, not a procedure of
+    the paper): every draw takes r ~ U{1..T} (Algorithm 3 with
     s uniform) and the pair counts are kept per window length.
     Returns (x, y, r, count) sorted by (x, y, r)."""
     n = len(indptr) - 1

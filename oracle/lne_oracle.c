@@ -15,7 +15,7 @@
  * Random numbers come from Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
  * implemented here from its published definition.
  *
- * Readings taken where the paper is silent (each also listed in the design doc):
+ * Readings taken where the paper is silent:
  *   - the map runs over the 2m CSR arcs, each with S/(2m) expected samples;
  *   - Bernoulli({x}) is  word < floor(frac(x) * 2^32)  with the arc word below;
  *   - r = 1 + #{ i in 1..T-1 : thr_i <= word },

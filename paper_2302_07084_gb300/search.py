@@ -6,7 +6,7 @@ downstream Macro-F1 (Sec. 4.3, Sec. 5.1). Here a small regression network
 (the surrogate, trained on the GPU by the library's own kernels) predicts that
 score from 30 features -- the candidate's parameters and 16 statistics of the
 graph -- so a search can rank a large pool of candidates and run the method
-only on the few it ranks highest; those full runs remain the judge.
+only on the few it ranks highest; those full runs make the choice.
 
 Features of a candidate (30): s_1..s_10, k, theta, mu, q, then the graph's
 statistics (``graph_statistics``): log n, log m, degree mean / std / max /

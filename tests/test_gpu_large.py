@@ -73,3 +73,28 @@ def test_auto_uses_the_sort_path_beyond_the_table(ctx, big):
     ctx.set_option(lne.OPT_AGGREGATION, lne.AGG_AUTO)
     res = ctx.sparsifier_counts(lne.DeviceGraph.from_graph(g), p)
     assert res["total_samples"] == oracle.count_samples(g.n_arcs, p.samples, p.seed)
+
+
+def test_10m_vertex_graph_sampled_draws(ctx):
+    """The 10M-vertex, 200M-edge Chung-Lu graph of the large precision run
+    (generated on the GPU): three ranges of 2000 arcs (start, middle, end) are
+    drawn by the library and by the oracle, bit for bit, at that run's rate
+    (S = 5 T m, T = 5)."""
+    n, m = 10_000_000, 200_000_000
+    indptr, indices = synth.chung_lu_device(n, m, 2.2, seed=4)
+    torch.cuda.empty_cache()
+    g = lne.DeviceGraph.from_tensors(indptr, indices)
+    s = [0.2] * 5
+    p = make_params(5, s, 5.0 * 5 * m, seed=4)
+    hp, hi = indptr.cpu().numpy(), indices.cpu().numpy().astype(np.int32)
+    drawn = 0
+    for a0 in (0, g.nnz // 2, g.nnz - 2000):
+        u1, v1 = ctx.sample_pairs(g, p, a0, a0 + 2000)
+        tr = oracle.sample_trace(hp, hi, 5, s, p.samples, p.seed, a0, a0 + 2000, fields=("u1", "v1"))
+        assert np.array_equal(to_np(u1).astype(np.int64), tr["u1"])
+        assert np.array_equal(to_np(v1).astype(np.int64), tr["v1"])
+        drawn += int(u1.numel())
+    assert drawn > 70_000
+    del g, indptr, indices
+    ctx.trim()
+    torch.cuda.empty_cache()

@@ -1,4 +1,4 @@
-"""Surrogate-guided search against the plain search (the method judged by
+"""Surrogate-guided search against the plain search (the method scored by
 itself): on held-out graphs of the SBM tuning suite, ranking a pool of 256
 candidates by the trained network and running only its top 8 must reach the
 plain search's best Macro-F1 over 32 full runs within 0.01, and must beat
