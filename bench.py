@@ -218,6 +218,22 @@ def oracle_step(g, params, rep: int = 0):
 # main
 # ---------------------------------------------------------------------------
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest value of x over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, ms: float) -> float:
+    """Units all ranks processed per second over the slowest rank's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def dist_setup(n_gpus):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -319,13 +335,8 @@ def run_ours(args):
     trace = ctx.trace_read()
     ctx.trace(False)
     clk = clocks.stop()
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * params["samples"] / (ms / 1e3)
+    ms = max_over_ranks(float(np.mean(step_ms)), world, dev)
+    value = whole_job_rate(world, params["samples"], ms)
 
     # ---- e2e: host buffers, copies inside the timed region ----
     indptr_h = torch.from_numpy(g.indptr.astype(np.int64)).pin_memory()
@@ -347,12 +358,7 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e = float(np.mean(e2e_ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e = max_over_ranks(float(np.mean(e2e_ms)), world, dev)
 
     # ---- roofline of the dominant kernel (CUDA events on the launching stream) ----
     hbm, bf16, src = read_peaks()
@@ -395,7 +401,7 @@ def run_ours(args):
                            "parallelism": f"replicas{world}", "nnz_pairs": info["nnz_c"],
                            "nnz_M": info["nnz_M"],
                            **({"downsample_C": params["downsample_C"]} if args.downsample else {})},
-                "e2e": {"value": world * params["samples"] / (e2e / 1e3), "unit": "samples/s",
+                "e2e": {"value": whole_job_rate(world, params["samples"], e2e), "unit": "samples/s",
                         "h2d_bytes_per_step": int(g.indptr.nbytes + g.indices.astype(np.int32).nbytes
                                                   + (weights.nbytes if weights is not None else 0)),
                         "d2h_bytes_per_step": int(g.n * P.d * 4), "ms_per_step": e2e},
