@@ -743,7 +743,10 @@ static int trsm_rows(const float *Y, int64_t n, int c, int64_t ldy, const double
                      cudaStream_t st) {
     const int nt = (c + 31) / 32;
     const int smem = (c * c + c) * 4;
-    const int blocks = (int)std::min<int64_t>(ceil_div(n, 8), 152 * 8);
+    // every CTA stages R in shared memory: one wave of resident CTAs, each
+    // walking many rows, loads it the fewest times
+    const int per_sm = std::max(1, std::min(8, (227 * 1024) / std::max(smem, 1)));
+    const int blocks = (int)std::min<int64_t>(ceil_div(n, 8), 152 * per_sm);
     LNE_TRACE("trsm_rows", st);
 #define LNE_TRSM_CASE(K)                                                                               \
     case K:                                                                                            \
