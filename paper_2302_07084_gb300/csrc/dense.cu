@@ -700,7 +700,13 @@ static int gram(Workspace &ws, const float *Y, int64_t n, int c, int64_t ld, dou
     const int ntiles = nt * (nt + 1) / 2;
     (void)ntiles;
     const int threads = kGramThreads;
-    int64_t nblk = std::min<int64_t>(304, std::max<int64_t>(1, ceil_div(n, 64)));
+    // whole waves of resident CTAs (one per SM at this kernel's register use)
+    int per_sm = 1;
+    LNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram_partial_kernel, threads,
+                                                             kGramRows * cp * 4));
+    const int64_t slots = 152 * (int64_t)std::max(1, per_sm);
+    int64_t nblk = std::min<int64_t>(2 * slots, std::max<int64_t>(1, ceil_div(n, 64)));
+    if (nblk > slots) nblk = (nblk / slots) * slots;
     const int64_t rows_per = ceil_div(std::max<int64_t>(n, 1), nblk);
     nblk = ceil_div(std::max<int64_t>(n, 1), rows_per);
     double *partial = nullptr;

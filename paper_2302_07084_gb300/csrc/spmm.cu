@@ -628,12 +628,34 @@ int dense_sym_spmm(Workspace &ws, const float *T, int64_t ld, int64_t n, const f
     if (n <= 0) return 0;
     if (c < 1 || c > 160) return fail(LNE_ERR_UNSUPPORTED, "dense-table product supports 1..160 columns");
     const int64_t rb = ceil_div(n, (int64_t)kDmRows);
-    // about four CTAs per SM: split the k range when there are few row blocks
-    const int ks = (int)std::max<int64_t>(1, std::min<int64_t>(16, (152 * 4 + rb - 1) / rb));
+    const int tn = (c + 15) / 16;
+    // split the k range into slices so that row blocks x slices fill whole
+    // waves of resident CTAs (the wide variants hold one CTA per SM)
+    const void *kern = nullptr;
+#define LNE_DM_KERN(K) \
+    case K: kern = reinterpret_cast<const void *>(dense_sym_mm_kernel<K>); break;
+    switch (tn) {
+        LNE_DM_KERN(1) LNE_DM_KERN(2) LNE_DM_KERN(3) LNE_DM_KERN(4) LNE_DM_KERN(5)
+        LNE_DM_KERN(6) LNE_DM_KERN(7) LNE_DM_KERN(8) LNE_DM_KERN(9) LNE_DM_KERN(10)
+        default:
+            return fail(LNE_ERR_UNSUPPORTED, "dense-table product supports 1..160 columns");
+    }
+#undef LNE_DM_KERN
+    int per_sm = 1;
+    LNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
+    const int64_t slots = 152 * (int64_t)std::max(1, per_sm);
+    int ks = 1;
+    double best = 1e300;
+    for (int cand = 1; cand <= 16; ++cand) {   // time ~ waves x (one slice's work)
+        const double t = (double)ceil_div(rb * cand, slots) / cand;
+        if (t < best - 1e-12) {
+            best = t;
+            ks = cand;
+        }
+    }
     const int64_t kslice = ceil_div(ceil_div(n, (int64_t)ks), (int64_t)kDmK) * kDmK;
     float *P = nullptr;
     LNE_TRY(ws.get("dense.partial", (size_t)ks * n * c, &P));
-    const int tn = (c + 15) / 16;
     dim3 grid((unsigned)rb, (unsigned)ceil_div(n, kslice));
     LNE_TRACE("dense_sym_mm", st);
 #define LNE_DM_CASE(K)                                                                                     \
