@@ -211,6 +211,92 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel(const double *__rest
     if (tid == 0) *status = bad;
 }
 
+// Blocked Cholesky over many SMs (FP64), for the matrix sizes where the
+// one-CTA kernel is bound by a single SM's FP64 rate. Panels of kCholB rows:
+// chol_panel_kernel (one CTA) factors the diagonal block, R11^T R11 = A11, and
+// solves R11^T R12 = A12 for the panel's row block; chol_update_kernel (one
+// CTA per 16 x 16 upper tile) subtracts R12^T R12 from the trailing matrix.
+// A is the working copy (row-major, upper triangle significant) and ends as R.
+constexpr int kCholB = 16;
+
+__global__ void __launch_bounds__(256) chol_panel_kernel(double *__restrict__ A, int c, int k0,
+                                                         int *__restrict__ status) {
+    __shared__ double s11[kCholB][kCholB + 1];
+    __shared__ double sinv[kCholB];
+    const int tid = threadIdx.x;
+    const int bs = min(kCholB, c - k0), k1 = k0 + bs;
+    for (int e = tid; e < bs * bs; e += blockDim.x) {
+        const int i = e / bs, j = e - i * bs;
+        s11[i][j] = A[(size_t)(k0 + i) * c + k0 + j];
+    }
+    __syncthreads();
+    if (tid < 32) {   // one warp: unblocked factorisation of the diagonal block
+        const int lane = tid;
+        for (int t = 0; t < bs; ++t) {
+            const double att = s11[t][t];
+            double d = 1.0;
+            if (!(att > 0.0) || !isfinite(att)) {
+                if (lane == 0 && *status == 0) *status = k0 + t + 1;
+            } else {
+                d = sqrt(att);
+            }
+            __syncwarp();
+            const double inv = 1.0 / d;
+            if (lane == 0) {
+                s11[t][t] = d;
+                sinv[t] = inv;
+            }
+            if (lane > t && lane < bs) s11[t][lane] *= inv;
+            __syncwarp();
+            // trailing block update: lanes over the entries of row i
+            for (int i = t + 1; i < bs; ++i)
+                if (lane >= i && lane < bs) s11[i][lane] = fma(-s11[t][i], s11[t][lane], s11[i][lane]);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    // R12: column j of the panel's row block by forward substitution with R11^T
+    for (int j = k1 + tid; j < c; j += blockDim.x) {
+        double r[kCholB];
+#pragma unroll
+        for (int i = 0; i < kCholB; ++i) {
+            if (i >= bs) break;
+            double x = A[(size_t)(k0 + i) * c + j];
+            for (int t = 0; t < i; ++t) x = fma(-s11[t][i], r[t], x);
+            r[i] = x * sinv[i];
+            A[(size_t)(k0 + i) * c + j] = r[i];
+        }
+    }
+    // R11 back, and zeros left of the diagonal in the panel's rows
+    for (int e = tid; e < bs * k1; e += blockDim.x) {
+        const int i = e / k1, j = e - i * k1;   // row k0 + i, column j < k1
+        double v = 0.0;
+        if (j >= k0 + i) v = s11[i][j - k0];
+        A[(size_t)(k0 + i) * c + j] = v;
+    }
+}
+
+__global__ void __launch_bounds__(256) chol_update_kernel(double *__restrict__ A, int c, int k0, int k1) {
+    const int I = blockIdx.y, J = blockIdx.x;
+    if (I > J) return;
+    __shared__ double ri[kCholB][16], rj[kCholB][16];
+    const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+    const int bs = k1 - k0;
+    const int i0 = k1 + 16 * I, j0 = k1 + 16 * J;
+    for (int e = tid; e < kCholB * 16; e += 256) {
+        const int t = e >> 4, q = e & 15;
+        ri[t][q] = (t < bs && i0 + q < c) ? A[(size_t)(k0 + t) * c + i0 + q] : 0.0;
+        rj[t][q] = (t < bs && j0 + q < c) ? A[(size_t)(k0 + t) * c + j0 + q] : 0.0;
+    }
+    __syncthreads();
+    const int i = i0 + ti, j = j0 + tj;
+    if (i < c && j < c && i <= j) {
+        double a = A[(size_t)i * c + j];
+        for (int t = 0; t < bs; ++t) a = fma(-ri[t][ti], rj[t][tj], a);
+        A[(size_t)i * c + j] = a;
+    }
+}
+
 // Q = Y R^-1 for upper-triangular R (FP64, rounded to FP32): one warp per row
 // solves q R = y by forward substitution; lane l keeps the running sums of
 // columns l, l + 32, ...
@@ -730,10 +816,24 @@ static int gram(Workspace &ws, const float *Y, int64_t n, int c, int64_t ld, dou
 static int chol(Workspace &ws, const double *G, int c, double *R, cudaStream_t st) {
     int *status = nullptr;
     LNE_TRY(ws.get("chol.status", 1, &status));
-    const int smem = c <= kMaxSmemC ? c * c * 8 : 0;
-    if (smem > 48 * 1024)
-        LNE_TRY(allow_dynamic_smem(chol_kernel));
-    {
+    if (c >= 64) {   // blocked over many SMs
+        LNE_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
+        LNE_CUDA_TRY(cudaMemcpyAsync(R, G, sizeof(double) * (size_t)c * c, cudaMemcpyDeviceToDevice, st));
+        LNE_TRACE("chol", st);
+        for (int k0 = 0; k0 < c; k0 += kCholB) {
+            chol_panel_kernel<<<1, 256, 0, st>>>(R, c, k0, status);
+            LNE_LAUNCH_CHECK();
+            const int k1 = std::min(c, k0 + kCholB);
+            if (k1 < c) {
+                const unsigned nb = (unsigned)ceil_div(c - k1, 16);
+                chol_update_kernel<<<dim3(nb, nb), 256, 0, st>>>(R, c, k0, k1);
+                LNE_LAUNCH_CHECK();
+            }
+        }
+    } else {
+        const int smem = c <= kMaxSmemC ? c * c * 8 : 0;
+        if (smem > 48 * 1024)
+            LNE_TRY(allow_dynamic_smem(chol_kernel));
         LNE_TRACE("chol", st);
         chol_kernel<<<1, kCholThreads, smem, st>>>(G, c, R, status);
         LNE_LAUNCH_CHECK();
