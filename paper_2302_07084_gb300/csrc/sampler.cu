@@ -422,7 +422,10 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
     extern __shared__ uint32_t smem[];
     __shared__ uint8_t s_rlut[4096];
     __shared__ uint64_t s_rmagic[17];
-    __shared__ uint32_t s_upack[kChunk], s_uw3[kChunk], s_pack[kChunk], s_w3[kChunk];
+    // s_upack: per chunk sample its index, r, sigma and rank; s_uw3: its word 3
+    // (phase 2 reads it through the index, so no permuted copy takes shared
+    // memory that the L1 cache can use); s_pack: the samples in r order
+    __shared__ uint32_t s_upack[kChunk], s_uw3[kChunk], s_pack[kChunk];
     __shared__ uint16_t s_lo[kChunk];   // arc within the tile of each chunk sample (phase 1 -> phase 2)
     __shared__ uint32_t s_wcnt[17 * kWalkWarps];
 
@@ -573,7 +576,6 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
             const uint32_t r = (pk >> 11) & 31;
             const uint32_t pos = s_wcnt[r * kWalkWarps + warp] + (pk >> 20);
             s_pack[pos] = pk;
-            s_w3[pos] = s_uw3[idx];
         }
         __syncthreads();
         // empty slots (r = 0) sort first: skip them. Two draws per thread,
@@ -591,9 +593,9 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_ker
             j0 = s0 - s_off[lo0];
             j1 = s1 - s_off[lo1];
             Draw d0, d1;
-            draw_begin(A, a0 + lo0, j0, (int)((pk0 >> 11) & 31), (int)((pk0 >> 16) & 15), s_w3[q0], s_src[lo0],
+            draw_begin(A, a0 + lo0, j0, (int)((pk0 >> 11) & 31), (int)((pk0 >> 16) & 15), s_uw3[pk0 & 0x7FFu], s_src[lo0],
                        s_dst[lo0], d0);
-            draw_begin(A, a0 + lo1, j1, (int)((pk1 >> 11) & 31), (int)((pk1 >> 16) & 15), s_w3[has1 ? q1 : q0],
+            draw_begin(A, a0 + lo1, j1, (int)((pk1 >> 11) & 31), (int)((pk1 >> 16) & 15), s_uw3[pk1 & 0x7FFu],
                        s_src[lo1], s_dst[lo1], d1);
             if (!has1) d1.steps = 0;
             StepAll<0, GEN>::run(A, d0, d1, max(d0.steps, d1.steps));
