@@ -37,9 +37,9 @@ namespace {
 
 constexpr int kBucketBits = 15;                 // keys per reduce bucket = 2^15
 constexpr int kMaxSmemBuckets = 12288;          // walk/scatter histogram capacity
-constexpr int kWalkThreads = 256;
+constexpr int kWalkThreads = 128;
 constexpr int kWalkWarps = kWalkThreads / 32;
-constexpr int kChunk = 1024;                     // samples ranked by window length at a time
+constexpr int kChunk = 512;                     // samples ranked by window length at a time
 
 struct WalkArgs {
     const int64_t *indptr;
@@ -415,7 +415,7 @@ __global__ void __launch_bounds__(kWalkThreads) tile_counts_kernel(WalkArgs A, i
 // variant for unweighted graphs without downsampling or window strata (the
 // checks for those compiled out); GEN = true handles everything.
 template <typename KeyT, int MODE, bool GEN>
-__global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 5 : 4) walk_emit_kernel(
+__global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 10 : 8) walk_emit_kernel(
     WalkArgs A, int64_t a_begin, int64_t a_end, int tile_arcs, const int64_t *__restrict__ tile_off,
     KeyT *__restrict__ keys, int32_t *__restrict__ u1, int32_t *__restrict__ v1,
     uint32_t *__restrict__ bucket_cnt, int nb_smem) {
