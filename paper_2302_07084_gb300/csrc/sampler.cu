@@ -40,6 +40,7 @@ constexpr int kMaxSmemBuckets = 12288;          // walk/scatter histogram capaci
 constexpr int kWalkThreads = 128;
 constexpr int kWalkWarps = kWalkThreads / 32;
 constexpr int kChunk = 512;                     // samples ranked by window length at a time
+static_assert(kChunk <= 2048 && kChunk % kWalkThreads == 0, "a chunk index fits the 11 low bits of a packed sample");
 
 struct WalkArgs {
     const int64_t *indptr;
