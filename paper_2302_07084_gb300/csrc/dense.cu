@@ -553,6 +553,260 @@ __global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__r
     if (tid == 0 && sweeps_out) *sweeps_out = sweep;
 }
 
+// Register-resident variant of the same Jacobi (c <= 144). Each 8-thread
+// group holds its pair of columns of A and of the rotations in registers
+// (E elements per column and thread, as float2 chunks: element 16 q + 2 sub
+// + {0, 1}), so a round reads nothing from shared memory; columns move
+// between groups through a shared exchange buffer only when the pairing
+// changes. The pairing order is chosen so that most rounds move one column of
+// each pair instead of both: a sweep over m = 2G columns takes the columns in
+// slot 0 as a set X and those in slot 1 as Y, and pairs X[i] with
+// Y[(i + r) mod G] for r = 0..G-1 (only Y moves, one group along); then X and
+// Y are each split in halves and the same is done inside X and inside Y in
+// parallel, and so on while the set size is even. Sets of odd size s then
+// finish with s rounds of the circle method (one column of each set idle per
+// round). Every pair meets exactly once per sweep; the layout a sweep ends
+// with is the next sweep's starting point, and a label per column records
+// which column of R^T it started as.
+template <int E>
+__host__ __device__ constexpr int jreg_stride() { return ((16 * E + 31) / 32) * 32 + 16; }
+
+template <int E>
+__global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__restrict__ R, int c,
+                                                               double *__restrict__ Uout,
+                                                               double *__restrict__ Vout, int max_sweeps,
+                                                               int *__restrict__ sweeps_out) {
+    constexpr int CP = 8 * E;            // padded column length
+    constexpr int NQ = E / 2;            // float2 chunks per column and thread
+    constexpr int ST = jreg_stride<E>(); // floats per exchange entry (= 16 mod 32: conflict-free float2)
+    extern __shared__ float xb[];        // 2 G entries: A part [CP], rotation part [CP], label at 2 CP
+    __shared__ float red[32];
+    __shared__ int s_done;
+    const int m = c + (c & 1), G = m / 2;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = tid >> 3, sub = tid & 7;
+    const bool real = g < G;             // groups past G only fill the last warp
+    float a0[E], a1[E], w0[E], w1[E];
+    int lab0 = g, lab1 = g + G;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+            const int i = 16 * q + 2 * sub + t, e = 2 * q + t;
+            a0[e] = real && lab0 < c && i < c ? (float)R[(size_t)lab0 * c + i] : 0.f;   // column lab0 of R^T
+            a1[e] = real && lab1 < c && i < c ? (float)R[(size_t)lab1 * c + i] : 0.f;
+            w0[e] = real && i == lab0 ? 1.f : 0.f;
+            w1[e] = real && i == lab1 ? 1.f : 0.f;
+        }
+    const float tol = 4.f * (float)c * 5.9604645e-8f;
+    int tz = 0;
+    while (((m >> tz) & 1) == 0) ++tz;
+    const int s_odd = m >> tz;           // set size the halving ends at
+    float local_max = 0.f;
+
+    auto put = [&](int entry, const float (&a)[E], const float (&w)[E], int lab) {
+        float *eb = xb + (size_t)entry * ST;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            *reinterpret_cast<float2 *>(eb + 16 * q + 2 * sub) = make_float2(a[2 * q], a[2 * q + 1]);
+            *reinterpret_cast<float2 *>(eb + CP + 16 * q + 2 * sub) = make_float2(w[2 * q], w[2 * q + 1]);
+        }
+        if (sub == 0) reinterpret_cast<int *>(eb)[2 * CP] = lab;
+    };
+    auto take = [&](int entry, float (&a)[E], float (&w)[E], int &lab) {
+        const float *eb = xb + (size_t)entry * ST;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const float2 x = *reinterpret_cast<const float2 *>(eb + 16 * q + 2 * sub);
+            const float2 y = *reinterpret_cast<const float2 *>(eb + CP + 16 * q + 2 * sub);
+            a[2 * q] = x.x;
+            a[2 * q + 1] = x.y;
+            w[2 * q] = y.x;
+            w[2 * q + 1] = y.y;
+        }
+        lab = reinterpret_cast<const int *>(eb)[2 * CP];
+    };
+    // both columns of every group move (sources as group * 2 + slot)
+    auto move_both = [&](int src0, int src1) {
+        __syncthreads();
+        if (real) {
+            put(2 * g, a0, w0, lab0);
+            put(2 * g + 1, a1, w1, lab1);
+        }
+        __syncthreads();
+        if (real) {
+            take(src0, a0, w0, lab0);
+            take(src1, a1, w1, lab1);
+        }
+        __syncthreads();
+    };
+    // one rotation of the group's pair (every lane takes part in the shuffles)
+    auto rotate = [&](bool active) {
+        float al = 0.f, be = 0.f, ga = 0.f;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            al = fmaf(a0[e], a0[e], al);
+            be = fmaf(a1[e], a1[e], be);
+            ga = fmaf(a0[e], a1[e], ga);
+        }
+#pragma unroll
+        for (int off = 1; off < 8; off <<= 1) {
+            al += __shfl_xor_sync(0xffffffffu, al, off);
+            be += __shfl_xor_sync(0xffffffffu, be, off);
+            ga += __shfl_xor_sync(0xffffffffu, ga, off);
+        }
+        if (active && ga != 0.f && al > 0.f && be > 0.f) {
+            const float rel = fabsf(ga) * rsqrtf(al * be);
+            local_max = fmaxf(local_max, rel);
+            if (rel > tol) {
+                const float zeta = (be - al) / (2.f * ga);
+                const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+                const float cs = rsqrtf(1.f + t * t);
+                const float sn = cs * t;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const float x = a0[e], y = a1[e];
+                    a0[e] = cs * x - sn * y;
+                    a1[e] = sn * x + cs * y;
+                    const float u = w0[e], v = w1[e];
+                    w0[e] = cs * u - sn * v;
+                    w1[e] = sn * u + cs * v;
+                }
+            }
+        }
+    };
+
+    int sweep = 0, par = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        local_max = 0.f;
+        for (int lev = 0; lev < tz; ++lev) {
+            const int h = m >> (lev + 1);   // ring length: pairs per set and rounds of this level
+            if (lev > 0) {
+                // the two halves of each set of the level before become two sets
+                const int H = 2 * h, jp = g / H, x = g - jp * H, half = x >= h ? 1 : 0, ip = x - half * h;
+                const int src0 = half ? (jp * H + (ip + 1) % H) * 2 + 1 : (jp * H + ip) * 2;
+                const int src1 = half ? (jp * H + (h + ip + 1) % H) * 2 + 1 : (jp * H + h + ip) * 2;
+                move_both(src0, src1);   // every thread reaches the same barriers
+            }
+            const int j = g / h, i = g - j * h;
+            const int ks = j * h + (i + 1 == h ? 0 : i + 1);   // slot-1 column comes from the next group
+            for (int r = 0; r < h; ++r) {
+                if (r > 0) {
+                    // double-buffered halves: one barrier per round
+                    if (real) put(par * G + g, a1, w1, lab1);
+                    __syncthreads();
+                    if (real) take(par * G + ks, a1, w1, lab1);
+                    par ^= 1;
+                }
+                rotate(true);
+            }
+        }
+        if (s_odd > 1) {
+            // circle method inside each set of odd size s: positions 1..k paired
+            // with s-1..k+1 in k groups per set, position 0 idle (the two sets
+            // that share a parent put their idle columns in one group)
+            const int s = s_odd, k = (s - 1) / 2, base = (g / s) * s, x = g - base;
+            const bool idle = x == s - 1;
+            const int sub0 = idle ? 0 : x / k, p0 = idle ? 0 : x - sub0 * k + 1;
+            const int sub1 = idle ? 1 : sub0, p1 = idle ? 0 : s - p0;
+            auto posmap = [&](int sb, int p) {
+                return p == 0 ? (base + s - 1) * 2 + sb
+                              : p <= k ? (base + sb * k + p - 1) * 2 : (base + sb * k + (s - p) - 1) * 2 + 1;
+            };
+            auto entry_src = [&](int sb, int y) {   // member y of a set, at the end of the last ring level
+                return sb == 0 ? (base + y) * 2 : (base + (y + 1) % s) * 2 + 1;
+            };
+            const int e0 = entry_src(sub0, p0), e1 = entry_src(sub1, p1);
+            const int r0 = posmap(sub0, (p0 + 1) % s), r1 = posmap(sub1, (p1 + 1) % s);
+            for (int r = 0; r < s; ++r) {
+                move_both(r == 0 ? e0 : r0, r == 0 ? e1 : r1);
+                rotate(!idle);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) local_max = fmaxf(local_max, __shfl_xor_sync(0xffffffffu, local_max, off));
+        if (lane == 0) red[warp] = local_max;
+        __syncthreads();
+        if (tid == 0) {
+            float mx = 0.f;
+            for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) mx = fmaxf(mx, red[w]);
+            s_done = mx <= tol;
+        }
+        __syncthreads();
+        if (s_done) {
+            ++sweep;
+            break;
+        }
+    }
+    // outputs by label: U = rotations, V = normalised columns of R^T W
+    float n0 = 0.f, n1 = 0.f;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        n0 = fmaf(a0[e], a0[e], n0);
+        n1 = fmaf(a1[e], a1[e], n1);
+    }
+#pragma unroll
+    for (int off = 1; off < 8; off <<= 1) {
+        n0 += __shfl_xor_sync(0xffffffffu, n0, off);
+        n1 += __shfl_xor_sync(0xffffffffu, n1, off);
+    }
+    const float r0 = n0 > 0.f ? rsqrtf(n0) : 0.f, r1 = n1 > 0.f ? rsqrtf(n1) : 0.f;
+    if (real) {
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int i = 16 * q + 2 * sub + t, e = 2 * q + t;
+                if (i < c && lab0 < c) {
+                    Uout[(size_t)i * c + lab0] = (double)w0[e];
+                    Vout[(size_t)i * c + lab0] = (double)(a0[e] * r0);
+                }
+                if (i < c && lab1 < c) {
+                    Uout[(size_t)i * c + lab1] = (double)w1[e];
+                    Vout[(size_t)i * c + lab1] = (double)(a1[e] * r1);
+                }
+            }
+    }
+    if (tid == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+constexpr int kJacRegMaxC = 144;
+
+template <int E>
+int launch_jacobi_reg_e(const double *R, int c, double *U, double *V, int *sweeps, cudaStream_t st) {
+    const int m = c + (c & 1);
+    const int threads = ((m / 2) * 8 + 31) / 32 * 32;
+    const int smem = m * jreg_stride<E>() * (int)sizeof(float);
+    if (smem > 48 * 1024) LNE_TRY(allow_dynamic_smem(jacobi_reg_kernel<E>));
+    jacobi_reg_kernel<E><<<1, threads, smem, st>>>(R, c, U, V, 20, sweeps);
+    LNE_LAUNCH_CHECK();
+    return 0;
+}
+
+// FP32 Jacobi start of the small SVD: the register-resident kernel up to
+// c = 144, the shared-memory one above.
+int launch_jacobi(const double *R, int c, double *U, double *V, int *sweeps, cudaStream_t st) {
+    switch ((c + 15) / 16) {
+    case 1: return launch_jacobi_reg_e<2>(R, c, U, V, sweeps, st);
+    case 2: return launch_jacobi_reg_e<4>(R, c, U, V, sweeps, st);
+    case 3: return launch_jacobi_reg_e<6>(R, c, U, V, sweeps, st);
+    case 4: return launch_jacobi_reg_e<8>(R, c, U, V, sweeps, st);
+    case 5: return launch_jacobi_reg_e<10>(R, c, U, V, sweeps, st);
+    case 6: return launch_jacobi_reg_e<12>(R, c, U, V, sweeps, st);
+    case 7: return launch_jacobi_reg_e<14>(R, c, U, V, sweeps, st);
+    case 8: return launch_jacobi_reg_e<16>(R, c, U, V, sweeps, st);
+    case 9: return launch_jacobi_reg_e<18>(R, c, U, V, sweeps, st);
+    default: break;
+    }
+    const int m = c + (c & 1);
+    const int threads = std::max(32, std::min(1024, (m / 2 * kJacTPP + 31) / 32 * 32));
+    const int smem = 2 * c * jac_ld(c) * 4;
+    if (smem > 48 * 1024) LNE_TRY(allow_dynamic_smem(jacobi32_kernel));
+    jacobi32_kernel<<<1, threads, smem, st>>>(R, c, U, V, 20, sweeps);
+    LNE_LAUNCH_CHECK();
+    return 0;
+}
+
 // C = op(A) op(B) (+ C0 if given), all c x c row-major FP64; 16 x 16 tile per CTA.
 // 8 x 8 output tiles (64 threads, one output each; 324 CTAs for c = 144). The
 // CTA's 8 rows of op(A) and 8 columns of op(B) over the whole k range are
@@ -945,15 +1199,9 @@ int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma,
     LNE_TRY(ws.get("svd.delta", 1, &dl));
     LNE_TRY(ws.get("svd.sweeps", 1, &sweeps));
     // starting point: FP32 one-sided Jacobi on R (U, V in FP64 storage)
-    const int m = c + (c & 1);
-    const int threads = std::max(32, std::min(1024, (m / 2 * kJacTPP + 31) / 32 * 32));
-    const int smem = 2 * c * jac_ld(c) * 4;
-    if (smem > 48 * 1024)
-        LNE_TRY(allow_dynamic_smem(jacobi32_kernel));
     {
         LNE_TRACE("jacobi32", st);
-        jacobi32_kernel<<<1, threads, smem, st>>>(R, c, U, V, 20, sweeps);
-        LNE_LAUNCH_CHECK();
+        LNE_TRY(launch_jacobi(R, c, U, V, sweeps, st));
     }
     // FP64 refinement of the SVD of R itself (quadratic convergence; the FP32
     // start may be loose in directions FP32 cannot resolve, hence four steps)
@@ -1069,13 +1317,7 @@ extern "C" int lne_svd_small_noalloc(const double *R_dev, int32_t c, double *U_d
     double *sg = base + 10 * kNoAllocMat;
     double *dl = sg + kNoAllocMaxC;
     int *sweeps = reinterpret_cast<int *>(dl + 8);
-    const int m = c + (c & 1);
-    const int threads = std::max(32, std::min(1024, (m / 2 * kJacTPP + 31) / 32 * 32));
-    const int smem = 2 * c * jac_ld(c) * 4;
-    if (smem > 48 * 1024)
-        LNE_TRY(allow_dynamic_smem(jacobi32_kernel));
-    jacobi32_kernel<<<1, threads, smem, st>>>(R_dev, c, U, V, 20, sweeps);
-    LNE_LAUNCH_CHECK();
+    LNE_TRY(launch_jacobi(R_dev, c, U, V, sweeps, st));
     for (int it = 0; it < 4; ++it) {
         LNE_TRY(dgemm_small(U, true, U, false, nullptr, P, c, st));
         LNE_TRY(dgemm_small(V, true, V, false, nullptr, Q, c, st));
