@@ -252,7 +252,7 @@ int lne_svd_small(lne_ctx *ctx, const double *R_dev, int32_t c, double *U_dev, d
  * another allocator up front, or a service that forbids allocation after
  * start-up). It needs no context: same arguments and results as lne_svd_small,
  * c <= 160 (larger c returns LNE_ERR_INVALID and does nothing).
- * Scratch: a fixed ~2 MB array in device memory that every GPU which loads the
+ * Scratch: a fixed ~4.5 MB array in device memory that every GPU which loads the
  * library holds until the process exits; its device address is looked up on
  * the first call on each device, so make that first call before any stream
  * capture. All calls on a device share the array: calls that overlap on the GPU

@@ -554,39 +554,54 @@ __global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__r
 }
 
 // Register-resident variant of the same Jacobi (c <= 144). Each 8-thread
-// group holds its pair of columns of A and of the rotations in registers
-// (E elements per column and thread, as float2 chunks: element 16 q + 2 sub
-// + {0, 1}), so a round reads nothing from shared memory; columns move
-// between groups through a shared exchange buffer only when the pairing
-// changes. The pairing order is chosen so that most rounds move one column of
-// each pair instead of both: a sweep over m = 2G columns takes the columns in
-// slot 0 as a set X and those in slot 1 as Y, and pairs X[i] with
-// Y[(i + r) mod G] for r = 0..G-1 (only Y moves, one group along); then X and
-// Y are each split in halves and the same is done inside X and inside Y in
-// parallel, and so on while the set size is even. Sets of odd size s then
-// finish with s rounds of the circle method (one column of each set idle per
-// round). Every pair meets exactly once per sweep; the layout a sweep ends
-// with is the next sweep's starting point, and a label per column records
-// which column of R^T it started as.
+// group holds its pair of columns of A in registers (E elements per column
+// and thread, as float2 chunks: element 16 q + 2 sub + {0, 1}), so a round
+// reads nothing from shared memory; columns move between groups through a
+// shared exchange buffer only when the pairing changes. The rotations W are
+// not accumulated here: every round's (cos, sin) and column labels are
+// recorded, and jacobi_replay_kernel applies them to the identity afterwards,
+// one row of W per warp on many SMs (the rows of W evolve independently).
+//
+// The pairing order is chosen so that most rounds move one column of each
+// pair instead of both: a sweep over m = 2G columns takes the columns in slot
+// 0 as a set X and those in slot 1 as Y, and pairs X[i] with Y[(i + r) mod G]
+// for r = 0..G-1 (only Y moves, one group along); then X and Y are each split
+// in halves and the same is done inside X and inside Y in parallel, and so on
+// while the set size is even. Sets of odd size s then finish with s rounds of
+// the circle method (one column of each set idle per round). Every pair meets
+// exactly once per sweep; the layout a sweep ends with is the next sweep's
+// starting point, and a label per column records which column of R^T it
+// started as.
+constexpr int kJacRegMaxC = 144;
+constexpr int kJacMaxSweeps = 20;
+
 template <int E>
-__host__ __device__ constexpr int jreg_stride() { return ((16 * E + 31) / 32) * 32 + 16; }
+__host__ __device__ constexpr int jreg_stride() { return ((8 * E + 31) / 32) * 32 + 16; }
+
+// rounds per sweep of the order above for m (even) columns
+__host__ __device__ inline int jreg_rounds(int m) {
+    int tz = 0;
+    while (((m >> tz) & 1) == 0) ++tz;
+    return (m >> tz) > 1 ? m : m - 1;
+}
 
 template <int E>
 __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__restrict__ R, int c,
-                                                               double *__restrict__ Uout,
-                                                               double *__restrict__ Vout, int max_sweeps,
+                                                               double *__restrict__ Vout,
+                                                               float2 *__restrict__ rot,
+                                                               uint32_t *__restrict__ rlab, int max_sweeps,
                                                                int *__restrict__ sweeps_out) {
     constexpr int CP = 8 * E;            // padded column length
     constexpr int NQ = E / 2;            // float2 chunks per column and thread
     constexpr int ST = jreg_stride<E>(); // floats per exchange entry (= 16 mod 32: conflict-free float2)
-    extern __shared__ float xb[];        // 2 G entries: A part [CP], rotation part [CP], label at 2 CP
+    extern __shared__ float xb[];        // 2 G entries: column [CP], label at CP
     __shared__ float red[32];
     __shared__ int s_done;
-    const int m = c + (c & 1), G = m / 2;
+    const int m = c + (c & 1), G = m / 2, RD = jreg_rounds(m);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = tid >> 3, sub = tid & 7;
     const bool real = g < G;             // groups past G only fill the last warp
-    float a0[E], a1[E], w0[E], w1[E];
+    float a0[E], a1[E];
     int lab0 = g, lab1 = g + G;
 #pragma unroll
     for (int q = 0; q < NQ; ++q)
@@ -595,52 +610,47 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
             const int i = 16 * q + 2 * sub + t, e = 2 * q + t;
             a0[e] = real && lab0 < c && i < c ? (float)R[(size_t)lab0 * c + i] : 0.f;   // column lab0 of R^T
             a1[e] = real && lab1 < c && i < c ? (float)R[(size_t)lab1 * c + i] : 0.f;
-            w0[e] = real && i == lab0 ? 1.f : 0.f;
-            w1[e] = real && i == lab1 ? 1.f : 0.f;
         }
     const float tol = 4.f * (float)c * 5.9604645e-8f;
     int tz = 0;
     while (((m >> tz) & 1) == 0) ++tz;
     const int s_odd = m >> tz;           // set size the halving ends at
     float local_max = 0.f;
+    int rec = 0;                         // record index of this round's group 0
 
-    auto put = [&](int entry, const float (&a)[E], const float (&w)[E], int lab) {
+    auto put = [&](int entry, const float (&a)[E], int lab) {
         float *eb = xb + (size_t)entry * ST;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
+        for (int q = 0; q < NQ; ++q)
             *reinterpret_cast<float2 *>(eb + 16 * q + 2 * sub) = make_float2(a[2 * q], a[2 * q + 1]);
-            *reinterpret_cast<float2 *>(eb + CP + 16 * q + 2 * sub) = make_float2(w[2 * q], w[2 * q + 1]);
-        }
-        if (sub == 0) reinterpret_cast<int *>(eb)[2 * CP] = lab;
+        if (sub == 0) reinterpret_cast<int *>(eb)[CP] = lab;
     };
-    auto take = [&](int entry, float (&a)[E], float (&w)[E], int &lab) {
+    auto take = [&](int entry, float (&a)[E], int &lab) {
         const float *eb = xb + (size_t)entry * ST;
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
             const float2 x = *reinterpret_cast<const float2 *>(eb + 16 * q + 2 * sub);
-            const float2 y = *reinterpret_cast<const float2 *>(eb + CP + 16 * q + 2 * sub);
             a[2 * q] = x.x;
             a[2 * q + 1] = x.y;
-            w[2 * q] = y.x;
-            w[2 * q + 1] = y.y;
         }
-        lab = reinterpret_cast<const int *>(eb)[2 * CP];
+        lab = reinterpret_cast<const int *>(eb)[CP];
     };
     // both columns of every group move (sources as group * 2 + slot)
     auto move_both = [&](int src0, int src1) {
         __syncthreads();
         if (real) {
-            put(2 * g, a0, w0, lab0);
-            put(2 * g + 1, a1, w1, lab1);
+            put(2 * g, a0, lab0);
+            put(2 * g + 1, a1, lab1);
         }
         __syncthreads();
         if (real) {
-            take(src0, a0, w0, lab0);
-            take(src1, a1, w1, lab1);
+            take(src0, a0, lab0);
+            take(src1, a1, lab1);
         }
         __syncthreads();
     };
-    // one rotation of the group's pair (every lane takes part in the shuffles)
+    // one rotation of the group's pair (every lane takes part in the shuffles),
+    // recorded as (cos, sin) = (1, 0) when the pair is left as it is
     auto rotate = [&](bool active) {
         float al = 0.f, be = 0.f, ga = 0.f;
 #pragma unroll
@@ -655,30 +665,34 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
             be += __shfl_xor_sync(0xffffffffu, be, off);
             ga += __shfl_xor_sync(0xffffffffu, ga, off);
         }
+        float cs = 1.f, sn = 0.f;
         if (active && ga != 0.f && al > 0.f && be > 0.f) {
             const float rel = fabsf(ga) * rsqrtf(al * be);
             local_max = fmaxf(local_max, rel);
             if (rel > tol) {
                 const float zeta = (be - al) / (2.f * ga);
                 const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-                const float cs = rsqrtf(1.f + t * t);
-                const float sn = cs * t;
+                cs = rsqrtf(1.f + t * t);
+                sn = cs * t;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const float x = a0[e], y = a1[e];
                     a0[e] = cs * x - sn * y;
                     a1[e] = sn * x + cs * y;
-                    const float u = w0[e], v = w1[e];
-                    w0[e] = cs * u - sn * v;
-                    w1[e] = sn * u + cs * v;
                 }
             }
         }
+        if (real && sub == 0) {
+            rot[(size_t)rec + g] = make_float2(cs, sn);
+            rlab[(size_t)rec + g] = (uint32_t)lab0 | ((uint32_t)lab1 << 16);
+        }
+        rec += G;
     };
 
     int sweep = 0, par = 0;
     for (; sweep < max_sweeps; ++sweep) {
         local_max = 0.f;
+        rec = sweep * RD * G;
         for (int lev = 0; lev < tz; ++lev) {
             const int h = m >> (lev + 1);   // ring length: pairs per set and rounds of this level
             if (lev > 0) {
@@ -693,9 +707,9 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
             for (int r = 0; r < h; ++r) {
                 if (r > 0) {
                     // double-buffered halves: one barrier per round
-                    if (real) put(par * G + g, a1, w1, lab1);
+                    if (real) put(par * G + g, a1, lab1);
                     __syncthreads();
-                    if (real) take(par * G + ks, a1, w1, lab1);
+                    if (real) take(par * G + ks, a1, lab1);
                     par ^= 1;
                 }
                 rotate(true);
@@ -738,7 +752,7 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
             break;
         }
     }
-    // outputs by label: U = rotations, V = normalised columns of R^T W
+    // right singular vectors of R: normalised columns of R^T W, by label
     float n0 = 0.f, n1 = 0.f;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -750,59 +764,117 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
         n0 += __shfl_xor_sync(0xffffffffu, n0, off);
         n1 += __shfl_xor_sync(0xffffffffu, n1, off);
     }
-    const float r0 = n0 > 0.f ? rsqrtf(n0) : 0.f, r1 = n1 > 0.f ? rsqrtf(n1) : 0.f;
+    const float q0 = n0 > 0.f ? rsqrtf(n0) : 0.f, q1 = n1 > 0.f ? rsqrtf(n1) : 0.f;
     if (real) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q)
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
                 const int i = 16 * q + 2 * sub + t, e = 2 * q + t;
-                if (i < c && lab0 < c) {
-                    Uout[(size_t)i * c + lab0] = (double)w0[e];
-                    Vout[(size_t)i * c + lab0] = (double)(a0[e] * r0);
-                }
-                if (i < c && lab1 < c) {
-                    Uout[(size_t)i * c + lab1] = (double)w1[e];
-                    Vout[(size_t)i * c + lab1] = (double)(a1[e] * r1);
-                }
+                if (i < c && lab0 < c) Vout[(size_t)i * c + lab0] = (double)(a0[e] * q0);
+                if (i < c && lab1 < c) Vout[(size_t)i * c + lab1] = (double)(a1[e] * q1);
             }
     }
     if (tid == 0 && sweeps_out) *sweeps_out = sweep;
 }
 
-constexpr int kJacRegMaxC = 144;
+// W = the recorded rotations applied to the identity, in order: warp w of a
+// CTA owns row i of W in shared memory; in every round its lanes take the
+// round's records (disjoint column pairs), loaded four rounds ahead.
+constexpr int kRpWarps = 4;
+constexpr int kRpPer = 3;   // records per lane and round: G <= 96
+static_assert(kJacRegMaxC / 2 <= 32 * kRpPer, "records of a round fit the lanes");
+
+__global__ void __launch_bounds__(kRpWarps * 32) jacobi_replay_kernel(const float2 *__restrict__ rot,
+                                                                      const uint32_t *__restrict__ rlab, int G,
+                                                                      int RD, const int *__restrict__ sweeps,
+                                                                      int c, double *__restrict__ Uout) {
+    __shared__ float rows[kRpWarps][kJacRegMaxC + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * kRpWarps + warp;
+    if (i >= c) return;   // whole warps leave; no CTA barrier below
+    float *row = rows[warp];
+    for (int j = lane; j < c; j += 32) row[j] = i == j ? 1.f : 0.f;
+    __syncwarp();
+    const int total = *sweeps * RD;
+    float2 pr[4][kRpPer];
+    uint32_t pl[4][kRpPer];
+    auto load = [&](int t, float2 (&r)[kRpPer], uint32_t (&l)[kRpPer]) {
+#pragma unroll
+        for (int k = 0; k < kRpPer; ++k) {
+            const int gg = lane + 32 * k;
+            const bool in = t < total && gg < G;
+            r[k] = in ? rot[(size_t)t * G + gg] : make_float2(1.f, 0.f);
+            l[k] = in ? rlab[(size_t)t * G + gg] : 0u;
+        }
+    };
+#pragma unroll
+    for (int d = 0; d < 4; ++d) load(d, pr[d], pl[d]);
+    for (int t0 = 0; t0 < total; t0 += 4) {
+#pragma unroll
+        for (int d = 0; d < 4; ++d) {
+            if (t0 + d < total) {
+#pragma unroll
+                for (int k = 0; k < kRpPer; ++k) {
+                    const float cs = pr[d][k].x, sn = pr[d][k].y;
+                    if (sn != 0.f) {
+                        const int p = (int)(pl[d][k] & 0xFFFFu), q = (int)(pl[d][k] >> 16);
+                        const float u = row[p], v = row[q];
+                        row[p] = cs * u - sn * v;
+                        row[q] = sn * u + cs * v;
+                    }
+                }
+                __syncwarp();
+            }
+            load(t0 + d + 4, pr[d], pl[d]);
+        }
+    }
+    for (int j = lane; j < c; j += 32) Uout[(size_t)i * c + j] = (double)row[j];
+}
+
+// records a Jacobi run on c <= kJacRegMaxC columns may write
+inline size_t jreg_records(int c) {
+    const int m = c + (c & 1);
+    return (size_t)kJacMaxSweeps * jreg_rounds(m) * (m / 2);
+}
 
 template <int E>
-int launch_jacobi_reg_e(const double *R, int c, double *U, double *V, int *sweeps, cudaStream_t st) {
+int launch_jacobi_reg_e(const double *R, int c, double *U, double *V, float2 *rot, uint32_t *rlab, int *sweeps,
+                        cudaStream_t st) {
     const int m = c + (c & 1);
     const int threads = ((m / 2) * 8 + 31) / 32 * 32;
     const int smem = m * jreg_stride<E>() * (int)sizeof(float);
     if (smem > 48 * 1024) LNE_TRY(allow_dynamic_smem(jacobi_reg_kernel<E>));
-    jacobi_reg_kernel<E><<<1, threads, smem, st>>>(R, c, U, V, 20, sweeps);
+    jacobi_reg_kernel<E><<<1, threads, smem, st>>>(R, c, V, rot, rlab, kJacMaxSweeps, sweeps);
+    LNE_LAUNCH_CHECK();
+    jacobi_replay_kernel<<<(unsigned)ceil_div(c, kRpWarps), kRpWarps * 32, 0, st>>>(rot, rlab, m / 2,
+                                                                                  jreg_rounds(m), sweeps, c, U);
     LNE_LAUNCH_CHECK();
     return 0;
 }
 
-// FP32 Jacobi start of the small SVD: the register-resident kernel up to
-// c = 144, the shared-memory one above.
-int launch_jacobi(const double *R, int c, double *U, double *V, int *sweeps, cudaStream_t st) {
+// FP32 Jacobi start of the small SVD: the register-resident kernel (with its
+// replay; rot / rlab hold jreg_records(c) records) up to c = 144, the
+// shared-memory one above.
+int launch_jacobi(const double *R, int c, double *U, double *V, float2 *rot, uint32_t *rlab, int *sweeps,
+                  cudaStream_t st) {
     switch ((c + 15) / 16) {
-    case 1: return launch_jacobi_reg_e<2>(R, c, U, V, sweeps, st);
-    case 2: return launch_jacobi_reg_e<4>(R, c, U, V, sweeps, st);
-    case 3: return launch_jacobi_reg_e<6>(R, c, U, V, sweeps, st);
-    case 4: return launch_jacobi_reg_e<8>(R, c, U, V, sweeps, st);
-    case 5: return launch_jacobi_reg_e<10>(R, c, U, V, sweeps, st);
-    case 6: return launch_jacobi_reg_e<12>(R, c, U, V, sweeps, st);
-    case 7: return launch_jacobi_reg_e<14>(R, c, U, V, sweeps, st);
-    case 8: return launch_jacobi_reg_e<16>(R, c, U, V, sweeps, st);
-    case 9: return launch_jacobi_reg_e<18>(R, c, U, V, sweeps, st);
+    case 1: return launch_jacobi_reg_e<2>(R, c, U, V, rot, rlab, sweeps, st);
+    case 2: return launch_jacobi_reg_e<4>(R, c, U, V, rot, rlab, sweeps, st);
+    case 3: return launch_jacobi_reg_e<6>(R, c, U, V, rot, rlab, sweeps, st);
+    case 4: return launch_jacobi_reg_e<8>(R, c, U, V, rot, rlab, sweeps, st);
+    case 5: return launch_jacobi_reg_e<10>(R, c, U, V, rot, rlab, sweeps, st);
+    case 6: return launch_jacobi_reg_e<12>(R, c, U, V, rot, rlab, sweeps, st);
+    case 7: return launch_jacobi_reg_e<14>(R, c, U, V, rot, rlab, sweeps, st);
+    case 8: return launch_jacobi_reg_e<16>(R, c, U, V, rot, rlab, sweeps, st);
+    case 9: return launch_jacobi_reg_e<18>(R, c, U, V, rot, rlab, sweeps, st);
     default: break;
     }
     const int m = c + (c & 1);
     const int threads = std::max(32, std::min(1024, (m / 2 * kJacTPP + 31) / 32 * 32));
     const int smem = 2 * c * jac_ld(c) * 4;
     if (smem > 48 * 1024) LNE_TRY(allow_dynamic_smem(jacobi32_kernel));
-    jacobi32_kernel<<<1, threads, smem, st>>>(R, c, U, V, 20, sweeps);
+    jacobi32_kernel<<<1, threads, smem, st>>>(R, c, U, V, kJacMaxSweeps, sweeps);
     LNE_LAUNCH_CHECK();
     return 0;
 }
@@ -1198,10 +1270,16 @@ int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma,
     double *dl = nullptr;
     LNE_TRY(ws.get("svd.delta", 1, &dl));
     LNE_TRY(ws.get("svd.sweeps", 1, &sweeps));
+    float2 *jrot = nullptr;
+    uint32_t *jlab = nullptr;
+    if (c <= kJacRegMaxC) {
+        LNE_TRY(ws.get("svd.jrot", jreg_records(c), &jrot));
+        LNE_TRY(ws.get("svd.jlab", jreg_records(c), &jlab));
+    }
     // starting point: FP32 one-sided Jacobi on R (U, V in FP64 storage)
     {
         LNE_TRACE("jacobi32", st);
-        LNE_TRY(launch_jacobi(R, c, U, V, sweeps, st));
+        LNE_TRY(launch_jacobi(R, c, U, V, jrot, jlab, sweeps, st));
     }
     // FP64 refinement of the SVD of R itself (quadratic convergence; the FP32
     // start may be loose in directions FP32 cannot resolve, hence four steps)
@@ -1267,8 +1345,8 @@ int sign_fix_embed(Workspace &ws, float *U, int64_t n, int d, int64_t ld, const 
 // For callers that must not allocate device memory when they call in -- for
 // example a process whose device memory is wholly handed to another allocator
 // up front, or a latency-bound service that forbids allocation after start-up.
-// Its scratch (ten c x c FP64 matrices plus a few scalars, c <= 160: about
-// 2 MB) is a file-scope __device__ array that every GPU which loads this
+// Its scratch (ten c x c FP64 matrices, a few scalars and the Jacobi's
+// rotation records, c <= 160: about 4.5 MB) is a file-scope __device__ array that every GPU which loads this
 // library holds until the process exits. In host code the array's name is only
 // a stand-in for it, so its device address is looked up with
 // cudaGetSymbolAddress once per device, on that device's first call.
@@ -1277,7 +1355,8 @@ namespace {
 
 constexpr int kNoAllocMaxC = 160;
 constexpr size_t kNoAllocMat = (size_t)kNoAllocMaxC * kNoAllocMaxC;
-constexpr size_t kNoAllocDoubles = 10 * kNoAllocMat + kNoAllocMaxC + 64;
+constexpr size_t kNoAllocRec = (size_t)kJacMaxSweeps * kJacRegMaxC * (kJacRegMaxC / 2);   // >= jreg_records(c)
+constexpr size_t kNoAllocDoubles = 10 * kNoAllocMat + kNoAllocMaxC + 64 + kNoAllocRec + kNoAllocRec / 2;
 static __device__ __align__(256) double g_svd_scratch[kNoAllocDoubles];
 
 constexpr int kNoAllocMaxDevices = 64;
@@ -1317,7 +1396,9 @@ extern "C" int lne_svd_small_noalloc(const double *R_dev, int32_t c, double *U_d
     double *sg = base + 10 * kNoAllocMat;
     double *dl = sg + kNoAllocMaxC;
     int *sweeps = reinterpret_cast<int *>(dl + 8);
-    LNE_TRY(launch_jacobi(R_dev, c, U, V, sweeps, st));
+    float2 *jrot = reinterpret_cast<float2 *>(base + 10 * kNoAllocMat + kNoAllocMaxC + 64);
+    uint32_t *jlab = reinterpret_cast<uint32_t *>(jrot + kNoAllocRec);
+    LNE_TRY(launch_jacobi(R_dev, c, U, V, jrot, jlab, sweeps, st));
     for (int it = 0; it < 4; ++it) {
         LNE_TRY(dgemm_small(U, true, U, false, nullptr, P, c, st));
         LNE_TRY(dgemm_small(V, true, V, false, nullptr, Q, c, st));
