@@ -935,24 +935,33 @@ __device__ double block_sum(double v, double *red) {
 // taken as (p_ij / 2, q_ij / 2) when |s_i - s_j| <= delta (near-equal values),
 // delta = 2 (||offdiag T|| + max|s| (||P|| + ||Q||)). A itself is never squared,
 // so the accuracy does not depend on the condition number of A.
-__global__ void svd_oa_norms_kernel(const double *__restrict__ P, const double *__restrict__ Q,
-                                    const double *__restrict__ T, int c, double *__restrict__ sig,
-                                    double *__restrict__ delta_out) {
+// Also turns the Gram products into P := I - U^T U, Q := I - V^T V in place.
+// kOaParts CTAs each reduce a fixed slice of the c x c entries (FP64 is slow
+// on this GPU, so the three sums are spread over several SMs) and write
+// their partial sums; svd_oa_fg_kernel adds the partials in a fixed order,
+// so delta is the same on every run.
+constexpr int kOaParts = 16;
+
+__global__ void svd_oa_norms_kernel(double *__restrict__ P, double *__restrict__ Q, const double *__restrict__ T,
+                                    int c, double *__restrict__ sig, double *__restrict__ part) {
     __shared__ double red[32];
-    __shared__ double s_sig[256];
-    const int tid = threadIdx.x;
-    for (int i = tid; i < c; i += blockDim.x)
-        s_sig[i] = T[i * c + i] / (1.0 - 0.5 * (P[i * c + i] + Q[i * c + i]));
-    __syncthreads();
     double o2 = 0.0, p2 = 0.0, q2 = 0.0, smax = 0.0;
-    for (int e = tid; e < c * c; e += blockDim.x) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c * c; e += gridDim.x * blockDim.x) {
         const int i = e / c, j = e - i * c;
-        const double t = i == j ? 0.0 : T[e];
-        o2 = fma(t, t, o2);
-        p2 = fma(P[e], P[e], p2);
-        q2 = fma(Q[e], Q[e], q2);
+        const double d = i == j ? 1.0 : 0.0;
+        const double p = d - P[e], q = d - Q[e], t = T[e];
+        P[e] = p;
+        Q[e] = q;
+        if (i == j) {
+            const double sv = t / (1.0 - 0.5 * (p + q));
+            sig[i] = sv;
+            smax = fmax(smax, fabs(sv));
+        } else {
+            o2 = fma(t, t, o2);
+        }
+        p2 = fma(p, p, p2);
+        q2 = fma(q, q, q2);
     }
-    for (int i = tid; i < c; i += blockDim.x) smax = fmax(smax, fabs(s_sig[i]));
     o2 = block_sum(o2, red);
     p2 = block_sum(p2, red);
     q2 = block_sum(q2, red);
@@ -967,14 +976,32 @@ __global__ void svd_oa_norms_kernel(const double *__restrict__ P, const double *
         for (int w = 0; w < (int)(blockDim.x + 31) / 32; ++w) m = fmax(m, red[w]);
         smax = m;
     }
-    for (int i = tid; i < c; i += blockDim.x) sig[i] = s_sig[i];
-    if (tid == 0) *delta_out = 2.0 * (sqrt(o2) + smax * (sqrt(p2) + sqrt(q2)));
+    if (threadIdx.x == 0) {
+        double *o = part + 4 * blockIdx.x;
+        o[0] = o2;
+        o[1] = p2;
+        o[2] = q2;
+        o[3] = smax;
+    }
 }
 
 // F, G of the update, one element per thread (the divisions spread over the GPU).
 __global__ void svd_oa_fg_kernel(const double *__restrict__ P, const double *__restrict__ Q,
                                  const double *__restrict__ T, int c, const double *__restrict__ sig,
-                                 const double *__restrict__ delta_in, double *__restrict__ F, double *__restrict__ Gm) {
+                                 const double *__restrict__ part, double *__restrict__ F, double *__restrict__ Gm) {
+    __shared__ double s_delta;
+    if (threadIdx.x == 0) {
+        double o2 = 0.0, p2 = 0.0, q2 = 0.0, smax = 0.0;
+        for (int b = 0; b < kOaParts; ++b) {
+            o2 += part[4 * b];
+            p2 += part[4 * b + 1];
+            q2 += part[4 * b + 2];
+            smax = fmax(smax, part[4 * b + 3]);
+        }
+        s_delta = 2.0 * (sqrt(o2) + smax * (sqrt(p2) + sqrt(q2)));
+    }
+    __syncthreads();
+    const double delta = s_delta;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= c * c) return;
     const int i = e / c, j = e - i * c;
@@ -982,7 +1009,7 @@ __global__ void svd_oa_fg_kernel(const double *__restrict__ P, const double *__r
     double f = 0.5 * pij, g = 0.5 * qij;
     if (i != j) {
         const double si = sig[i], sj = sig[j];
-        if (fabs(sj - si) > *delta_in) {
+        if (fabs(sj - si) > delta) {
             const double r1 = T[e] + pij * sj;
             const double r2 = T[j * c + i] + qij * sj;
             const double inv = 1.0 / ((sj - si) * (sj + si));
@@ -997,16 +1024,6 @@ __global__ void svd_oa_fg_kernel(const double *__restrict__ P, const double *__r
     }
     F[e] = f;
     Gm[e] = g;
-}
-
-// P := I - P and Q := I - Q in place (from the Gram products U^T U, V^T V).
-__global__ void svd_ia_kernel_prep(double *__restrict__ P, double *__restrict__ Q, int c) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= c * c) return;
-    const int i = e / c, j = e - i * c;
-    const double d = i == j ? 1.0 : 0.0;
-    P[e] = d - P[e];
-    Q[e] = d - Q[e];
 }
 
 // sigma sorted descending; U_R[:, rank_j] = sign(s_j) U[:, j].
@@ -1268,7 +1285,7 @@ int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma,
     LNE_TRY(ws.get("svd.G", cc, &Gm));
     LNE_TRY(ws.get("svd.sg", (size_t)c, &sg));
     double *dl = nullptr;
-    LNE_TRY(ws.get("svd.delta", 1, &dl));
+    LNE_TRY(ws.get("svd.delta", 4 * kOaParts, &dl));
     LNE_TRY(ws.get("svd.sweeps", 1, &sweeps));
     float2 *jrot = nullptr;
     uint32_t *jlab = nullptr;
@@ -1290,9 +1307,7 @@ int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma,
         LNE_TRY(dgemm_small(U, true, W, false, nullptr, T, c, st));   // T = U^T R V
         {
             LNE_TRACE("svd_oa_update", st);
-            svd_ia_kernel_prep<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(P, Q, c);
-            LNE_LAUNCH_CHECK();
-            svd_oa_norms_kernel<<<1, 256, 0, st>>>(P, Q, T, c, sg, dl);
+            svd_oa_norms_kernel<<<kOaParts, 256, 0, st>>>(P, Q, T, c, sg, dl);
             LNE_LAUNCH_CHECK();
             svd_oa_fg_kernel<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(P, Q, T, c, sg, dl, F, Gm);
             LNE_LAUNCH_CHECK();
@@ -1356,7 +1371,8 @@ namespace {
 constexpr int kNoAllocMaxC = 160;
 constexpr size_t kNoAllocMat = (size_t)kNoAllocMaxC * kNoAllocMaxC;
 constexpr size_t kNoAllocRec = (size_t)kJacMaxSweeps * kJacRegMaxC * (kJacRegMaxC / 2);   // >= jreg_records(c)
-constexpr size_t kNoAllocDoubles = 10 * kNoAllocMat + kNoAllocMaxC + 64 + kNoAllocRec + kNoAllocRec / 2;
+constexpr size_t kNoAllocDoubles = 10 * kNoAllocMat + kNoAllocMaxC + 128 + kNoAllocRec + kNoAllocRec / 2;
+static_assert(4 * kOaParts + 8 <= 128, "partial sums and sweep count fit the reserve");
 static __device__ __align__(256) double g_svd_scratch[kNoAllocDoubles];
 
 constexpr int kNoAllocMaxDevices = 64;
@@ -1395,8 +1411,8 @@ extern "C" int lne_svd_small_noalloc(const double *R_dev, int32_t c, double *U_d
            *T = base + 5 * cc, *P = base + 6 * cc, *Q = base + 7 * cc, *F = base + 8 * cc, *Gm = base + 9 * cc;
     double *sg = base + 10 * kNoAllocMat;
     double *dl = sg + kNoAllocMaxC;
-    int *sweeps = reinterpret_cast<int *>(dl + 8);
-    float2 *jrot = reinterpret_cast<float2 *>(base + 10 * kNoAllocMat + kNoAllocMaxC + 64);
+    int *sweeps = reinterpret_cast<int *>(dl + 4 * kOaParts);
+    float2 *jrot = reinterpret_cast<float2 *>(base + 10 * kNoAllocMat + kNoAllocMaxC + 128);
     uint32_t *jlab = reinterpret_cast<uint32_t *>(jrot + kNoAllocRec);
     LNE_TRY(launch_jacobi(R_dev, c, U, V, jrot, jlab, sweeps, st));
     for (int it = 0; it < 4; ++it) {
@@ -1404,9 +1420,7 @@ extern "C" int lne_svd_small_noalloc(const double *R_dev, int32_t c, double *U_d
         LNE_TRY(dgemm_small(V, true, V, false, nullptr, Q, c, st));
         LNE_TRY(dgemm_small(R_dev, false, V, false, nullptr, W, c, st));
         LNE_TRY(dgemm_small(U, true, W, false, nullptr, T, c, st));
-        svd_ia_kernel_prep<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(P, Q, c);
-        LNE_LAUNCH_CHECK();
-        svd_oa_norms_kernel<<<1, 256, 0, st>>>(P, Q, T, c, sg, dl);
+        svd_oa_norms_kernel<<<kOaParts, 256, 0, st>>>(P, Q, T, c, sg, dl);
         LNE_LAUNCH_CHECK();
         svd_oa_fg_kernel<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(P, Q, T, c, sg, dl, F, Gm);
         LNE_LAUNCH_CHECK();
