@@ -86,7 +86,8 @@ def test_cholqr2_rank_deficient_reports_numeric_error(ctx):
     assert e.value.code == -6
 
 
-@pytest.mark.parametrize("c,cond", [(144, 1e4), (128, 1e2), (48, 1e6), (16, 10.0), (7, 3.0), (160, 1e3)])
+@pytest.mark.parametrize("c,cond", [(144, 1e4), (128, 1e2), (48, 1e6), (16, 10.0), (7, 3.0), (160, 1e3),
+                                    (1, 1.0), (2, 5.0), (33, 1e3), (99, 1e5), (130, 1e4), (145, 1e2)])
 def test_svd_small_fp64_accuracy(ctx, c, cond):
     """The small SVD is FP64-accurate at any conditioning: singular values to
     1e-12 relative, U orthonormal to 1e-12, U^T R R^T U diagonal to
