@@ -213,14 +213,21 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel(const double *__rest
 
 // Blocked Cholesky over many SMs (FP64), for the matrix sizes where the
 // one-CTA kernel is bound by a single SM's FP64 rate. Panels of kCholB rows:
-// chol_panel_kernel (one CTA) factors the diagonal block, R11^T R11 = A11, and
-// solves R11^T R12 = A12 for the panel's row block; chol_update_kernel (one
-// CTA per 16 x 16 upper tile) subtracts R12^T R12 from the trailing matrix.
-// A is the working copy (row-major, upper triangle significant) and ends as R.
+// chol_panel_kernel factors the diagonal block, R11^T R11 = A11, and solves
+// R11^T R12 = A12 for the panel's row block; chol_update_kernel (one CTA per
+// 16 x 16 upper tile) subtracts R12^T R12 from the trailing matrix. A is the
+// working copy (row-major, upper triangle significant) and ends as R.
+//
+// The panel's row block is spread over ceil((c - k1) / 16) CTAs, 16 columns
+// each; every CTA factors the small diagonal block itself (identically), so
+// no CTA waits for another. Since other CTAs may still be reading A11 while
+// one has finished, R11 goes to a scratch block (written by CTA 0) and is
+// copied into A by the update kernel, or directly by a panel that runs as a
+// single CTA.
 constexpr int kCholB = 16;
 
 __global__ void __launch_bounds__(256) chol_panel_kernel(double *__restrict__ A, int c, int k0,
-                                                         int *__restrict__ status) {
+                                                         int *__restrict__ status, double *__restrict__ r11) {
     __shared__ double s11[kCholB][kCholB + 1];
     __shared__ double sinv[kCholB];
     const int tid = threadIdx.x;
@@ -230,58 +237,67 @@ __global__ void __launch_bounds__(256) chol_panel_kernel(double *__restrict__ A,
         s11[i][j] = A[(size_t)(k0 + i) * c + k0 + j];
     }
     __syncthreads();
-    if (tid < 32) {   // one warp: unblocked factorisation of the diagonal block
-        const int lane = tid;
-        for (int t = 0; t < bs; ++t) {
+    // unblocked factorisation of the diagonal block, one entry (ti, tj) per thread
+    const int ti = tid >> 4, tj = tid & 15;
+    for (int t = 0; t < bs; ++t) {
+        if (tid == 0) {
             const double att = s11[t][t];
             double d = 1.0;
             if (!(att > 0.0) || !isfinite(att)) {
-                if (lane == 0 && *status == 0) *status = k0 + t + 1;
+                if (blockIdx.x == 0 && *status == 0) *status = k0 + t + 1;
             } else {
                 d = sqrt(att);
             }
-            __syncwarp();
-            const double inv = 1.0 / d;
-            if (lane == 0) {
-                s11[t][t] = d;
-                sinv[t] = inv;
-            }
-            if (lane > t && lane < bs) s11[t][lane] *= inv;
-            __syncwarp();
-            // trailing block update: lanes over the entries of row i
-            for (int i = t + 1; i < bs; ++i)
-                if (lane >= i && lane < bs) s11[i][lane] = fma(-s11[t][i], s11[t][lane], s11[i][lane]);
-            __syncwarp();
+            s11[t][t] = d;
+            sinv[t] = 1.0 / d;
         }
+        __syncthreads();
+        if (ti == t && tj > t && tj < bs) s11[t][tj] *= sinv[t];
+        __syncthreads();
+        if (ti > t && tj >= ti && tj < bs) s11[ti][tj] = fma(-s11[t][ti], s11[t][tj], s11[ti][tj]);
+        __syncthreads();
     }
-    __syncthreads();
-    // R12: column j of the panel's row block by forward substitution with R11^T
-    for (int j = k1 + tid; j < c; j += blockDim.x) {
-        double r[kCholB];
-#pragma unroll
-        for (int i = 0; i < kCholB; ++i) {
-            if (i >= bs) break;
-            double x = A[(size_t)(k0 + i) * c + j];
-            for (int t = 0; t < i; ++t) x = fma(-s11[t][i], r[t], x);
-            r[i] = x * sinv[i];
-            A[(size_t)(k0 + i) * c + j] = r[i];
+    // R12: 16 lanes per column; lane i holds x_i and subtracts r_ti x_t as
+    // soon as x_t is final (the same terms in the same order as a row-by-row
+    // forward substitution)
+    {
+        const int li = tid & 15;
+        const int j = k1 + blockIdx.x * 16 + (tid >> 4);
+        const bool live = j < c && li < bs;
+        double x = live ? A[(size_t)(k0 + li) * c + j] : 0.0;
+        for (int t = 0; t < bs; ++t) {
+            if (li == t) x *= sinv[t];
+            const double xt = __shfl_sync(0xffffffffu, x, t, 16);
+            if (li > t && li < bs) x = fma(-s11[t][li], xt, x);
         }
+        if (live) A[(size_t)(k0 + li) * c + j] = x;
     }
-    // R11 back, and zeros left of the diagonal in the panel's rows
-    for (int e = tid; e < bs * k1; e += blockDim.x) {
-        const int i = e / k1, j = e - i * k1;   // row k0 + i, column j < k1
-        double v = 0.0;
-        if (j >= k0 + i) v = s11[i][j - k0];
-        A[(size_t)(k0 + i) * c + j] = v;
-    }
+    // R11 (and zeros left of the diagonal in the panel's rows)
+    if (blockIdx.x == 0)
+        for (int e = tid; e < bs * bs; e += blockDim.x) {
+            const int i = e / bs, j = e - i * bs;
+            r11[e] = j >= i ? s11[i][j] : 0.0;
+        }
+    if (gridDim.x == 1)
+        for (int e = tid; e < bs * k1; e += blockDim.x) {
+            const int i = e / k1, j = e - i * k1;   // row k0 + i, column j < k1
+            A[(size_t)(k0 + i) * c + j] = j >= k0 + i ? s11[i][j - k0] : 0.0;
+        }
 }
 
-__global__ void __launch_bounds__(256) chol_update_kernel(double *__restrict__ A, int c, int k0, int k1) {
+__global__ void __launch_bounds__(256) chol_update_kernel(double *__restrict__ A, int c, int k0, int k1,
+                                                          const double *__restrict__ r11) {
     const int I = blockIdx.y, J = blockIdx.x;
     if (I > J) return;
-    __shared__ double ri[kCholB][16], rj[kCholB][16];
-    const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+    const int tid = threadIdx.x;
     const int bs = k1 - k0;
+    if (I == 0 && J == 0)   // the panel's R11 from its scratch block (these entries are not read below)
+        for (int e = tid; e < bs * k1; e += blockDim.x) {
+            const int i = e / k1, j = e - i * k1;
+            A[(size_t)(k0 + i) * c + j] = j >= k0 ? r11[i * bs + (j - k0)] : 0.0;
+        }
+    __shared__ double ri[kCholB][16], rj[kCholB][16];
+    const int ti = tid >> 4, tj = tid & 15;
     const int i0 = k1 + 16 * I, j0 = k1 + 16 * J;
     for (int e = tid; e < kCholB * 16; e += 256) {
         const int t = e >> 4, q = e & 15;
@@ -887,10 +903,22 @@ int launch_jacobi(const double *R, int c, double *U, double *V, float2 *rot, uin
 constexpr int kDgTile = 8;
 constexpr int kDgMaxC = 160;
 
+// Two products with the same transposes may share a launch: blockIdx.z = 1
+// takes the second operand set (A2, B2, C02, C2).
 __global__ void __launch_bounds__(kDgTile * kDgTile) dgemm_small_kernel(const double *__restrict__ A, int ta,
                                                                         const double *__restrict__ B, int tb,
                                                                         const double *__restrict__ C0,
-                                                                        double *__restrict__ C, int c) {
+                                                                        double *__restrict__ C, int c,
+                                                                        const double *__restrict__ A2,
+                                                                        const double *__restrict__ B2,
+                                                                        const double *__restrict__ C02,
+                                                                        double *__restrict__ C2) {
+    if (blockIdx.z == 1) {
+        A = A2;
+        B = B2;
+        C0 = C02;
+        C = C2;
+    }
     __shared__ double As[kDgTile][kDgMaxC + 1], Bs[kDgMaxC][kDgTile + 1];
     const int tid = threadIdx.x, tx = tid % kDgTile, ty = tid / kDgTile;
     const int r0 = blockIdx.y * kDgTile, c0 = blockIdx.x * kDgTile;
@@ -1160,16 +1188,18 @@ static int chol(Workspace &ws, const double *G, int c, double *R, cudaStream_t s
     int *status = nullptr;
     LNE_TRY(ws.get("chol.status", 1, &status));
     if (c >= 64) {   // blocked over many SMs
+        double *r11 = nullptr;
+        LNE_TRY(ws.get("chol.r11", (size_t)kCholB * kCholB, &r11));
         LNE_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
         LNE_CUDA_TRY(cudaMemcpyAsync(R, G, sizeof(double) * (size_t)c * c, cudaMemcpyDeviceToDevice, st));
         LNE_TRACE("chol", st);
         for (int k0 = 0; k0 < c; k0 += kCholB) {
-            chol_panel_kernel<<<1, 256, 0, st>>>(R, c, k0, status);
-            LNE_LAUNCH_CHECK();
             const int k1 = std::min(c, k0 + kCholB);
+            const unsigned nb = (unsigned)std::max<int64_t>(1, ceil_div(c - k1, 16));
+            chol_panel_kernel<<<nb, 256, 0, st>>>(R, c, k0, status, r11);
+            LNE_LAUNCH_CHECK();
             if (k1 < c) {
-                const unsigned nb = (unsigned)ceil_div(c - k1, 16);
-                chol_update_kernel<<<dim3(nb, nb), 256, 0, st>>>(R, c, k0, k1);
+                chol_update_kernel<<<dim3(nb, nb), 256, 0, st>>>(R, c, k0, k1, r11);
                 LNE_LAUNCH_CHECK();
             }
         }
@@ -1257,12 +1287,16 @@ int cholqr2(Workspace &ws, float *Y, int64_t n, int c, int64_t ld, double *Rout,
     return 0;
 }
 
+// C = op(A) op(B) (+ C0), and when A2 is given also C2 = op(A2) op(B2) (+ C02)
+// in the same launch.
 static int dgemm_small(const double *A, bool ta, const double *B, bool tb, const double *C0, double *C, int c,
-                       cudaStream_t st) {
+                       cudaStream_t st, const double *A2 = nullptr, const double *B2 = nullptr,
+                       const double *C02 = nullptr, double *C2 = nullptr) {
     if (c > kDgMaxC) return fail(LNE_ERR_UNSUPPORTED, "small FP64 products support c <= 160");
-    dim3 grid((unsigned)ceil_div(c, kDgTile), (unsigned)ceil_div(c, kDgTile));
+    dim3 grid((unsigned)ceil_div(c, kDgTile), (unsigned)ceil_div(c, kDgTile), A2 ? 2u : 1u);
     LNE_TRACE("dgemm_small", st);
-    dgemm_small_kernel<<<grid, kDgTile * kDgTile, 0, st>>>(A, ta ? 1 : 0, B, tb ? 1 : 0, C0, C, c);
+    dgemm_small_kernel<<<grid, kDgTile * kDgTile, 0, st>>>(A, ta ? 1 : 0, B, tb ? 1 : 0, C0, C, c, A2, B2, C02,
+                                                            C2);
     LNE_LAUNCH_CHECK();
     return 0;
 }
@@ -1301,8 +1335,8 @@ int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma,
     // FP64 refinement of the SVD of R itself (quadratic convergence; the FP32
     // start may be loose in directions FP32 cannot resolve, hence four steps)
     for (int it = 0; it < 4; ++it) {
-        LNE_TRY(dgemm_small(U, true, U, false, nullptr, P, c, st));   // P = U^T U (I - P below)
-        LNE_TRY(dgemm_small(V, true, V, false, nullptr, Q, c, st));   // Q = V^T V
+        // P = U^T U and Q = V^T V (I - P, I - Q below)
+        LNE_TRY(dgemm_small(U, true, U, false, nullptr, P, c, st, V, V, nullptr, Q));
         LNE_TRY(dgemm_small(R, false, V, false, nullptr, W, c, st));  // W = R V
         LNE_TRY(dgemm_small(U, true, W, false, nullptr, T, c, st));   // T = U^T R V
         {
@@ -1312,8 +1346,7 @@ int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma,
             svd_oa_fg_kernel<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(P, Q, T, c, sg, dl, F, Gm);
             LNE_LAUNCH_CHECK();
         }
-        LNE_TRY(dgemm_small(U, false, F, false, U, U2, c, st));       // U2 = U + U F
-        LNE_TRY(dgemm_small(V, false, Gm, false, V, V2, c, st));      // V2 = V + V G
+        LNE_TRY(dgemm_small(U, false, F, false, U, U2, c, st, V, Gm, V, V2));   // U2 = U + U F, V2 = V + V G
         std::swap(U, U2);
         std::swap(V, V2);
     }
@@ -1416,16 +1449,14 @@ extern "C" int lne_svd_small_noalloc(const double *R_dev, int32_t c, double *U_d
     uint32_t *jlab = reinterpret_cast<uint32_t *>(jrot + kNoAllocRec);
     LNE_TRY(launch_jacobi(R_dev, c, U, V, jrot, jlab, sweeps, st));
     for (int it = 0; it < 4; ++it) {
-        LNE_TRY(dgemm_small(U, true, U, false, nullptr, P, c, st));
-        LNE_TRY(dgemm_small(V, true, V, false, nullptr, Q, c, st));
+        LNE_TRY(dgemm_small(U, true, U, false, nullptr, P, c, st, V, V, nullptr, Q));
         LNE_TRY(dgemm_small(R_dev, false, V, false, nullptr, W, c, st));
         LNE_TRY(dgemm_small(U, true, W, false, nullptr, T, c, st));
         svd_oa_norms_kernel<<<kOaParts, 256, 0, st>>>(P, Q, T, c, sg, dl);
         LNE_LAUNCH_CHECK();
         svd_oa_fg_kernel<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(P, Q, T, c, sg, dl, F, Gm);
         LNE_LAUNCH_CHECK();
-        LNE_TRY(dgemm_small(U, false, F, false, U, U2, c, st));
-        LNE_TRY(dgemm_small(V, false, Gm, false, V, V2, c, st));
+        LNE_TRY(dgemm_small(U, false, F, false, U, U2, c, st, V, Gm, V, V2));
         std::swap(U, U2);
         std::swap(V, V2);
     }
