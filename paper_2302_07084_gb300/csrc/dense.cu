@@ -796,56 +796,84 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
 
 // W = the recorded rotations applied to the identity, in order: warp w of a
 // CTA owns row i of W in shared memory; in every round its lanes take the
-// round's records (disjoint column pairs), loaded four rounds ahead.
+// round's records (disjoint column pairs). The CTA stages the records in
+// chunks of kRpChunk rounds through shared memory, loading the next chunk
+// into registers while it applies the current one.
 constexpr int kRpWarps = 4;
-constexpr int kRpPer = 3;   // records per lane and round: G <= 96
-static_assert(kJacRegMaxC / 2 <= 32 * kRpPer, "records of a round fit the lanes");
+constexpr int kRpPer = 3;      // records per lane and round: G <= 96
+constexpr int kRpChunk = 16;   // rounds per staged chunk
+constexpr int kRpMaxG = kJacRegMaxC / 2;
+constexpr int kRpLoads = (kRpChunk * kRpMaxG + kRpWarps * 32 - 1) / (kRpWarps * 32);
+static_assert(kRpMaxG <= 32 * kRpPer, "records of a round fit the lanes");
 
 __global__ void __launch_bounds__(kRpWarps * 32) jacobi_replay_kernel(const float2 *__restrict__ rot,
                                                                       const uint32_t *__restrict__ rlab, int G,
                                                                       int RD, const int *__restrict__ sweeps,
                                                                       int c, double *__restrict__ Uout) {
     __shared__ float rows[kRpWarps][kJacRegMaxC + 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ float2 srot[2][kRpChunk * kRpMaxG];
+    __shared__ uint32_t slab[2][kRpChunk * kRpMaxG];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int i = blockIdx.x * kRpWarps + warp;
-    if (i >= c) return;   // whole warps leave; no CTA barrier below
+    const bool live = i < c;   // warps past the last row still stage records and meet the barriers
     float *row = rows[warp];
     for (int j = lane; j < c; j += 32) row[j] = i == j ? 1.f : 0.f;
-    __syncwarp();
     const int total = *sweeps * RD;
-    float2 pr[4][kRpPer];
-    uint32_t pl[4][kRpPer];
-    auto load = [&](int t, float2 (&r)[kRpPer], uint32_t (&l)[kRpPer]) {
+    const int per = kRpChunk * G;   // records per chunk
+    float2 rr[kRpLoads];
+    uint32_t rl[kRpLoads];
+    auto fetch = [&](int ch) {   // chunk ch's records into registers
+        const size_t base = (size_t)ch * per, end = (size_t)total * G;
 #pragma unroll
-        for (int k = 0; k < kRpPer; ++k) {
-            const int gg = lane + 32 * k;
-            const bool in = t < total && gg < G;
-            r[k] = in ? rot[(size_t)t * G + gg] : make_float2(1.f, 0.f);
-            l[k] = in ? rlab[(size_t)t * G + gg] : 0u;
+        for (int u = 0; u < kRpLoads; ++u) {
+            const int e = tid + u * kRpWarps * 32;
+            const bool in = e < per && base + e < end;
+            rr[u] = in ? rot[base + e] : make_float2(1.f, 0.f);
+            rl[u] = in ? rlab[base + e] : 0u;
         }
     };
+    auto stash = [&](int b) {
 #pragma unroll
-    for (int d = 0; d < 4; ++d) load(d, pr[d], pl[d]);
-    for (int t0 = 0; t0 < total; t0 += 4) {
-#pragma unroll
-        for (int d = 0; d < 4; ++d) {
-            if (t0 + d < total) {
+        for (int u = 0; u < kRpLoads; ++u) {
+            const int e = tid + u * kRpWarps * 32;
+            if (e < per) {
+                srot[b][e] = rr[u];
+                slab[b][e] = rl[u];
+            }
+        }
+    };
+    const int nch = (total + kRpChunk - 1) / kRpChunk;
+    fetch(0);
+    stash(0);
+    __syncthreads();
+    for (int ch = 0; ch < nch; ++ch) {
+        const int b = ch & 1;
+        if (ch + 1 < nch) fetch(ch + 1);
+        if (live) {
+            const int nr = min(kRpChunk, total - ch * kRpChunk);
+            for (int r = 0; r < nr; ++r) {
 #pragma unroll
                 for (int k = 0; k < kRpPer; ++k) {
-                    const float cs = pr[d][k].x, sn = pr[d][k].y;
-                    if (sn != 0.f) {
-                        const int p = (int)(pl[d][k] & 0xFFFFu), q = (int)(pl[d][k] >> 16);
-                        const float u = row[p], v = row[q];
-                        row[p] = cs * u - sn * v;
-                        row[q] = sn * u + cs * v;
+                    const int g = lane + 32 * k;
+                    if (g < G) {
+                        const float2 cs_sn = srot[b][r * G + g];
+                        if (cs_sn.y != 0.f) {
+                            const uint32_t pq = slab[b][r * G + g];
+                            const int p = (int)(pq & 0xFFFFu), q = (int)(pq >> 16);
+                            const float u = row[p], v = row[q];
+                            row[p] = cs_sn.x * u - cs_sn.y * v;
+                            row[q] = cs_sn.y * u + cs_sn.x * v;
+                        }
                     }
                 }
                 __syncwarp();
             }
-            load(t0 + d + 4, pr[d], pl[d]);
         }
+        if (ch + 1 < nch) stash(b ^ 1);
+        __syncthreads();
     }
-    for (int j = lane; j < c; j += 32) Uout[(size_t)i * c + j] = (double)row[j];
+    if (live)
+        for (int j = lane; j < c; j += 32) Uout[(size_t)i * c + j] = (double)row[j];
 }
 
 // records a Jacobi run on c <= kJacRegMaxC columns may write
