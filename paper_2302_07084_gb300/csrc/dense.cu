@@ -852,20 +852,29 @@ __global__ void __launch_bounds__(kRpWarps * 32) jacobi_replay_kernel(const floa
         if (live) {
             const int nr = min(kRpChunk, total - ch * kRpChunk);
             for (int r = 0; r < nr; ++r) {
+                // the round's pairs are disjoint: all reads first, then all writes
+                float2 cn[kRpPer];
+                int p[kRpPer], q[kRpPer];
+                float u[kRpPer], v[kRpPer];
 #pragma unroll
                 for (int k = 0; k < kRpPer; ++k) {
                     const int g = lane + 32 * k;
-                    if (g < G) {
-                        const float2 cs_sn = srot[b][r * G + g];
-                        if (cs_sn.y != 0.f) {
-                            const uint32_t pq = slab[b][r * G + g];
-                            const int p = (int)(pq & 0xFFFFu), q = (int)(pq >> 16);
-                            const float u = row[p], v = row[q];
-                            row[p] = cs_sn.x * u - cs_sn.y * v;
-                            row[q] = cs_sn.y * u + cs_sn.x * v;
-                        }
-                    }
+                    cn[k] = g < G ? srot[b][r * G + g] : make_float2(1.f, 0.f);
+                    const uint32_t pq = g < G ? slab[b][r * G + g] : 0u;
+                    p[k] = (int)(pq & 0xFFFFu);
+                    q[k] = (int)(pq >> 16);
                 }
+#pragma unroll
+                for (int k = 0; k < kRpPer; ++k) {
+                    u[k] = cn[k].y != 0.f ? row[p[k]] : 0.f;
+                    v[k] = cn[k].y != 0.f ? row[q[k]] : 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < kRpPer; ++k)
+                    if (cn[k].y != 0.f) {
+                        row[p[k]] = cn[k].x * u[k] - cn[k].y * v[k];
+                        row[q[k]] = cn[k].y * u[k] + cn[k].x * v[k];
+                    }
                 __syncwarp();
             }
         }
