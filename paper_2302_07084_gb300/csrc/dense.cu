@@ -20,6 +20,7 @@
 #include <cmath>
 #include <mutex>
 
+#include "jacobi_order.h"
 #include "runtime.h"
 
 namespace lne {
@@ -595,11 +596,7 @@ template <int E>
 __host__ __device__ constexpr int jreg_stride() { return ((8 * E + 31) / 32) * 32 + 16; }
 
 // rounds per sweep of the order above for m (even) columns
-__host__ __device__ inline int jreg_rounds(int m) {
-    int tz = 0;
-    while (((m >> tz) & 1) == 0) ++tz;
-    return (m >> tz) > 1 ? m : m - 1;
-}
+__host__ __device__ inline int jreg_rounds(int m) { return jorder_rounds(m); }
 
 template <int E>
 __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__restrict__ R, int c,
@@ -628,8 +625,7 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
             a1[e] = real && lab1 < c && i < c ? (float)R[(size_t)lab1 * c + i] : 0.f;
         }
     const float tol = 4.f * (float)c * 5.9604645e-8f;
-    int tz = 0;
-    while (((m >> tz) & 1) == 0) ++tz;
+    const int tz = jorder_levels(m);
     const int s_odd = m >> tz;           // set size the halving ends at
     float local_max = 0.f;
     int rec = 0;                         // record index of this round's group 0
@@ -713,13 +709,11 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
             const int h = m >> (lev + 1);   // ring length: pairs per set and rounds of this level
             if (lev > 0) {
                 // the two halves of each set of the level before become two sets
-                const int H = 2 * h, jp = g / H, x = g - jp * H, half = x >= h ? 1 : 0, ip = x - half * h;
-                const int src0 = half ? (jp * H + (ip + 1) % H) * 2 + 1 : (jp * H + ip) * 2;
-                const int src1 = half ? (jp * H + (h + ip + 1) % H) * 2 + 1 : (jp * H + h + ip) * 2;
+                int src0, src1;
+                jorder_split_sources(g, h, src0, src1);
                 move_both(src0, src1);   // every thread reaches the same barriers
             }
-            const int j = g / h, i = g - j * h;
-            const int ks = j * h + (i + 1 == h ? 0 : i + 1);   // slot-1 column comes from the next group
+            const int ks = jorder_ring_source(g, h);   // slot-1 column comes from the next group
             for (int r = 0; r < h; ++r) {
                 if (r > 0) {
                     // double-buffered halves: one barrier per round
@@ -735,19 +729,10 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
             // circle method inside each set of odd size s: positions 1..k paired
             // with s-1..k+1 in k groups per set, position 0 idle (the two sets
             // that share a parent put their idle columns in one group)
-            const int s = s_odd, k = (s - 1) / 2, base = (g / s) * s, x = g - base;
-            const bool idle = x == s - 1;
-            const int sub0 = idle ? 0 : x / k, p0 = idle ? 0 : x - sub0 * k + 1;
-            const int sub1 = idle ? 1 : sub0, p1 = idle ? 0 : s - p0;
-            auto posmap = [&](int sb, int p) {
-                return p == 0 ? (base + s - 1) * 2 + sb
-                              : p <= k ? (base + sb * k + p - 1) * 2 : (base + sb * k + (s - p) - 1) * 2 + 1;
-            };
-            auto entry_src = [&](int sb, int y) {   // member y of a set, at the end of the last ring level
-                return sb == 0 ? (base + y) * 2 : (base + (y + 1) % s) * 2 + 1;
-            };
-            const int e0 = entry_src(sub0, p0), e1 = entry_src(sub1, p1);
-            const int r0 = posmap(sub0, (p0 + 1) % s), r1 = posmap(sub1, (p1 + 1) % s);
+            const int s = s_odd;
+            int e0, e1, r0, r1;
+            bool idle;
+            jorder_tail_sources(g, s, e0, e1, r0, r1, idle);
             for (int r = 0; r < s; ++r) {
                 move_both(r == 0 ? e0 : r0, r == 0 ? e1 : r1);
                 rotate(!idle);
