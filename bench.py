@@ -37,10 +37,29 @@ METRIC = "samples/s (end-to-end embed, S=200Tm)"
 WORKLOAD = "blogcatalog_like_chunglu_n10312_m333983_T10_S200Tm_d128_q1_k10"
 
 
-# DRAM bytes (read + write) per launch from one ncu capture of the current
-# kernel on this workload (profiles/walk_count_blogcatalog_S200Tm.md); to be
-# removed from here whenever the kernel changes.
-RECORDED_TRAFFIC = {"walk_count": 10.755427e9 + 11.028228e9}
+# DRAM bytes (read + write) per launch of a kernel from one ncu capture on
+# this workload, with the SHA-256 (first 16 hex digits) of the source files
+# that define the kernel at the time of the capture. The figure is reported
+# only while those files are unchanged; otherwise traffic is null.
+RECORDED_TRAFFIC = {
+    "walk_count": {"bytes": None, "sources": ("csrc/sampler.cu", "csrc/common.cuh"), "sha16": None},
+}
+
+
+def source_sha16(paths):
+    import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, "paper_2302_07084_gb300", rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(name):
+    rec = RECORDED_TRAFFIC.get(name)
+    if not rec or rec["bytes"] is None or source_sha16(rec["sources"]) != rec["sha16"]:
+        return None
+    return rec["bytes"]
 
 
 def workload():
@@ -73,25 +92,39 @@ def walk_ops_per_sample(params):
 
 
 def kernel_model(name, g, params, counts):
-    """(bound, algorithmic amount per launch, unit) of a kernel, or None.
+    """(bound, algorithmic amount per launch, unit, per-unit description) of a
+    kernel, or None. The byte models are the survey's algorithmic ones:
 
-    walk_count / walk_emit: ALU -- walk_ops_per_sample * samples (lane-ops).
-    spmm:       FMA -- 2 * nnz(M) * c flops (FP32).
-    graph_spmm: FMA -- 2 * nnz(A) * d flops (FP32).
-    gram_partial: FP64 -- n * c * (c + 1) flops (upper half of Y^T Y).
+    walk_count / walk_emit (sampling into the pair table): HBM -- 8 B per
+        sample (4 B key write + 4 B key read of the aggregation; the walk's
+        record reads hit L2 on this graph).
+    spmm (CSR product Y = M X): HBM -- 8 B per nonzero of M (index + value)
+        + one read of the dense operand row and one write of Y's row
+        (c x (operand bytes + 4)) per row.
+    graph_spmm: HBM -- 8 B per arc + d x 8 B per row.
     """
     S = counts["total_samples"]
     n, m2 = g.n, g.n_arcs
     c = params["d"] + params["oversample"]
     if name in ("walk_count", "walk_emit"):
         kept = counts.get("kept_draws", S)
-        # a draw the downsampling coin drops costs its head block and bookkeeping only
-        return "alu", walk_ops_per_sample(params) * kept + 52.0 * (S - kept), "Gop/s"
+        return "hbm", 8.0 * kept, "GB/s", "8 B per sample x samples"
     if name == "spmm":
-        return "fma", 2.0 * counts.get("nnz_M", 0) * c, "GFLOP/s"
+        xb = 2 if params.get("precision", 0) == 1 else 4
+        return ("hbm", 8.0 * counts.get("nnz_M", 0) + n * c * (xb + 4.0), "GB/s",
+                "8 B per nonzero of M + c (operand + 4) B per row")
     if name == "graph_spmm":
-        return "fma", 2.0 * m2 * params["d"], "GFLOP/s"
+        return "hbm", 8.0 * m2 + n * params["d"] * 8.0, "GB/s", "8 B per arc + 8 d B per row"
     return None
+
+
+def walk_lane_ops(params, counts):
+    """Integer lane-operations of the walk (a secondary, ALU view): per draw
+    walk_ops_per_sample; a draw that the downsampling coin drops costs its
+    head block and bookkeeping only (52)."""
+    S = counts["total_samples"]
+    kept = counts.get("kept_draws", S)
+    return walk_ops_per_sample(params) * kept + 52.0 * (S - kept)
 
 
 def expected_kept_draws(g, params):
@@ -106,9 +139,11 @@ def expected_kept_draws(g, params):
     return float(params["samples"] / g.n_arcs * pe.sum())
 
 
-def alu_peak_gops(sm_mhz):
-    """152 SMs x 4 sub-partitions x 32 lanes, one instruction per clock."""
-    return 152 * 128 * sm_mhz * 1e6 / 1e9
+def alu_peak_gops(sm_count, sm_mhz):
+    """Integer lane-operations per second if every one of the 4 x 32 lanes of
+    each SM issued one per clock (an upper bound: the 32 x 32 -> 64 multiplies
+    of Philox issue at a lower rate)."""
+    return sm_count * 128 * sm_mhz * 1e6 / 1e9
 
 
 def read_peaks():
@@ -180,38 +215,92 @@ class ClockSampler:
 # the CPU oracle, timed (cpu_baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_step(g, params, rep: int = 0):
-    """Oracle throughput on a bounded sample of the workload.
+class OracleBaseline:
+    """The CPU oracle timed on the workload, on the host's cores.
 
-    Sampling and aggregation are timed on a slice of arcs at the workload's own
-    per-arc rate (cost per sample); the rest (trunc_log, CSR, randomized SVD,
-    propagation) is timed once on a full-graph run at S/256. The estimate for
-    the whole workload is cost_per_sample * S + rest.
+    Set-up (once, before any timed share) runs the oracle's sparsifier of the
+    whole workload: all S draws sampled and counted (``sparsifier_counts_dense``),
+    Eq. 1 values and the CSR of M; each of those stages is timed at full size.
+    A timed share k of F is then a bounded, proportional piece of the whole
+    workload, every part measured on the full-size data:
+      * sampling + aggregation (sample_pairs + the sort-and-count of
+        ``sparsifier_counts``) of the k-th of F arc ranges;
+      * Eq. 1 values + CSR (netmf_values, sparsifier_csr) of the k-th of F
+        ranges of the full pair list;
+      * the randomized SVD's q + 1 products (oracle.spmm) of the k-th of F row
+        blocks of the full M with the n x c dense operand, that block's share of
+        the Gram and of U = Y V S^-1, plus the whole c x c eigensolves;
+      * propagation's 2k - 1 products of the k-th row block of D^-1 A and its
+        share of the last Gram.
+    Shares are processed S / F samples' worth of the workload each, so a share's
+    rate in samples/s is (S / F) / its time; F shares make the whole workload.
     """
-    import oracle
-    S = params["samples"]
-    rate = S / g.n_arcs
-    arcs = max(1, int(4.0e6 / rate))
-    a0 = (rep * 7919 * arcs) % max(1, g.n_arcs - arcs)
-    t0 = time.perf_counter()
-    x, y = oracle.sample_pairs(g.indptr, g.indices, params["T"], params["s"], S, params["seed"], a0, a0 + arcs)
-    np.unique(x * g.n + y, return_counts=True)
-    t_samp = time.perf_counter() - t0
-    per_sample = t_samp / max(1, x.size)
-    S_red = S / 256.0
-    sp = oracle.sparsifier(g.indptr, g.indices, params["T"], params["s"], S_red, params["seed"])
-    t1 = time.perf_counter()
-    oracle.netmf_values(sp["x"], sp["y"], sp["cnt"], g.degrees(), S_red)
-    rs = oracle.fast_randomized_svd(sp["indptr"], sp["indices"], sp["data"], params["d"], params["q"],
-                                    params["oversample"], params["seed"])
-    X0 = oracle.embedding_from_svd(rs["U"], rs["sigma"])
-    oracle.spectral_propagation(g.indptr, g.indices, X0, params["k"], params["theta"], params["mu"])
-    t_rest = time.perf_counter() - t1
-    est = per_sample * S + t_rest
-    sample = (f"sampling+aggregation of {x.size} draws (arcs {a0}..{a0 + arcs} at the workload rate "
-              f"{rate:.0f}/arc) extrapolated to S={S:.3g}; trunc_log+CSR+RSVD+propagation timed on a "
-              f"full-graph run at S/256")
-    return dict(value=S / est, est_s=est, measured_s=t_samp + t_rest, sample=sample, cores=oracle.num_threads())
+
+    def __init__(self, g, params, F: int = 64):
+        import oracle
+        self.oracle = oracle
+        self.g, self.p, self.F = g, params, F
+        S = params["samples"]
+        t0 = time.perf_counter()
+        x, y, cnt = oracle.sparsifier_counts_dense(g.indptr, g.indices, params["T"], params["s"], S,
+                                                   params["seed"])
+        t1 = time.perf_counter()
+        self.deg = g.degrees()
+        v, keep, val = oracle.netmf_values(x, y, cnt, self.deg, S, params["b"])
+        self.M = oracle.sparsifier_csr(g.n, x[keep], y[keep], val[keep])
+        t2 = time.perf_counter()
+        self.pairs = (x, y, cnt)
+        self.setup = {"sampling_aggregation_s": t1 - t0, "values_csr_s": t2 - t1, "nnz_M": int(self.M[0][-1]),
+                      "nnz_pairs": int(x.size)}
+        c = params["d"] + params["oversample"]
+        rng = np.random.default_rng(0)
+        self.Xc = rng.standard_normal((g.n, c))           # stands for Omega / Q (same shape)
+        self.Xd = rng.standard_normal((g.n, params["d"]))  # stands for X0 / T_i
+        self.cores = oracle.num_threads()
+
+    def share(self, k: int) -> float:
+        """Run share k mod F; returns its wall time in seconds."""
+        oracle, g, p, F = self.oracle, self.g, self.p, self.F
+        k %= F
+        n, S = g.n, p["samples"]
+        t0 = time.perf_counter()
+        # sampling + aggregation of arc range k
+        a0, a1 = k * g.n_arcs // F, (k + 1) * g.n_arcs // F
+        x, y = oracle.sample_pairs(g.indptr, g.indices, p["T"], p["s"], S, p["seed"], a0, a1)
+        np.unique(x * n + y, return_counts=True)
+        del x, y
+        # Eq. 1 values + CSR of pair range k
+        px, py, pc = self.pairs
+        b0, b1 = k * px.size // F, (k + 1) * px.size // F
+        v, keep, val = oracle.netmf_values(px[b0:b1], py[b0:b1], pc[b0:b1], self.deg, S, p["b"])
+        oracle.sparsifier_csr(n, px[b0:b1][keep], py[b0:b1][keep], val[keep])
+        # randomized SVD: q + 1 products of row block k of M, its Gram share, the eigensolves
+        r0, r1 = k * n // F, (k + 1) * n // F
+        ip, ix, dv = self.M
+        blk_ip = ip[r0:r1 + 1] - ip[r0]
+        blk_ix, blk_dv = ix[ip[r0]:ip[r1]], dv[ip[r0]:ip[r1]]
+        for _ in range(p["q"] + 1):
+            Yb = oracle.spmm(blk_ip, blk_ix, blk_dv, self.Xc)
+            C = Yb.T @ Yb
+            D, V = np.linalg.eigh(C)
+            Yb @ (V / np.sqrt(np.maximum(D, 1e-300)))
+        # propagation: 2k - 1 products of row block k of D^-1 A, the last Gram share
+        gp = g.indptr[r0:r1 + 1] - g.indptr[r0]
+        gi = g.indices[g.indptr[r0]:g.indptr[r1]]
+        gv = np.repeat(1.0 / np.maximum(self.deg[r0:r1], 1), np.diff(g.indptr[r0:r1 + 1]))
+        for _ in range(max(0, 2 * p["k"] - 1)):
+            oracle.spmm(gp, gi, gv, self.Xd)
+        Pb = oracle.spmm(gp, gi, gv, self.Xd)
+        np.linalg.eigh(Pb.T @ Pb)
+        return time.perf_counter() - t0
+
+    def describe(self) -> str:
+        return (f"{self.F} proportional shares of the whole workload (each: sampling+aggregation of 1/{self.F} "
+                f"of the arcs, Eq. 1 values+CSR of 1/{self.F} of the pairs, the randomized SVD's products and "
+                f"propagation's products on 1/{self.F} of the rows of the full-size M (nnz "
+                f"{self.setup['nnz_M']}) and of D^-1 A); the full-size M was built by the oracle at set-up "
+                f"(sampling+aggregation of all S draws {self.setup['sampling_aggregation_s']:.1f} s, values+CSR "
+                f"{self.setup['values_csr_s']:.1f} s, measured)")
 
 
 # ---------------------------------------------------------------------------
@@ -246,30 +335,36 @@ def dist_setup(n_gpus):
     return world, rank, local
 
 
+def bench_config(g, params, world):
+    """The workload's config dict, identical on both arms."""
+    return {"workload": WORKLOAD, "n": g.n, "m": g.m, "samples": params["samples"], "T": params["T"],
+            "d": params["d"], "q": params["q"], "k": params["k"],
+            "l2": "flushed (256 MB write) between steps", "parallelism": f"replicas{world}"}
+
+
 def run_reference(args):
+    """The oracle on the host's cores: set-up builds the full-size sparsifier,
+    then W untimed and K timed proportional shares (OracleBaseline)."""
     world, rank, _ = dist_setup(args.gpus) if int(os.environ.get("WORLD_SIZE", "1")) > 1 else (1, 0, 0)
     if rank != 0:
         return
     g, params = workload()
-    for w in range(args.warmup):
-        oracle_step(g, params, rep=w)
-    vals, t_meas = [], 0.0
     t0 = time.perf_counter()
-    for k in range(args.steps):
-        r = oracle_step(g, params, rep=args.warmup + k)
-        vals.append(r["value"])
-        t_meas += r["measured_s"]
-    wall = time.perf_counter() - t0
-    est_ms = 1e3 * params["samples"] / statistics.mean(vals)
-    v = params["samples"] / (est_ms / 1e3)
+    ob = OracleBaseline(g, params)
+    setup_s = time.perf_counter() - t0
+    for w in range(args.warmup):
+        ob.share(w)
+    times = [ob.share(args.warmup + k) for k in range(args.steps)]
+    ms = 1e3 * float(np.mean(times))
+    v = (params["samples"] / ob.F) / (ms / 1e3)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "samples/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": est_ms, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": g.n, "m": g.m, "samples": params["samples"]},
-            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": r["cores"], "kind": "oracle",
-                             "sample": r["sample"]},
+            "config": bench_config(g, params, world),
+            "cpu_baseline": {"value": v, "unit": "samples/s", "cores": ob.cores, "kind": "oracle",
+                             "sample": ob.describe()},
             "e2e": {"value": v, "unit": "samples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": wall}
+            "samples_per_step": params["samples"] / ob.F, "setup_s": setup_s, "setup": ob.setup}
     print(json.dumps(line), flush=True)
 
 
@@ -362,45 +457,54 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (CUDA events on the launching stream) ----
     hbm, bf16, src = read_peaks()
-    per_launch = {}
-    for t in trace:
-        per_launch[t["name"]] = t
     dom = max(trace, key=lambda t: t["ms"])
     model = kernel_model(dom["name"], g, params, info)
     sm_mhz = clk.get("sm_mhz") or 2070.0
-    peaks = {"alu": (alu_peak_gops(sm_mhz), "derived: 152 SMs x 128 lanes x median SM clock"),
-             "fma": (2 * alu_peak_gops(sm_mhz), "derived: 152 SMs x 128 FP32 lanes x 2 flops x median SM clock"),
-             "hbm": (hbm, src)}
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    avg_s = dom["ms"] / max(1, dom["regions"]) / 1e3
+    traffic = recorded_traffic(dom["name"])
     roof = {"kernel": dom["name"], "bound": None, "achieved": None, "peak": None, "unit": None, "frac": None,
-            "traffic": RECORDED_TRAFFIC.get(dom["name"]), "avg_launch_ms": dom["ms"] / max(1, dom["regions"])}
+            "traffic": traffic, "avg_launch_ms": avg_s * 1e3}
+    if traffic is None:
+        roof["traffic_note"] = "no ncu capture of the current source of this kernel"
     if model is not None:
-        bound, amount, unit = model
-        avg_s = dom["ms"] / max(1, dom["regions"]) / 1e3
+        bound, amount, unit, per_unit = model
         achieved = amount / avg_s / 1e9
-        peak, psrc = peaks[bound]
-        roof.update({"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                     "peak_source": psrc, "work_per_launch": amount})
+        roof.update({"bound": bound, "achieved": achieved, "peak": hbm, "unit": unit, "frac": achieved / hbm,
+                     "peak_source": f"{src}: MEASURED_PEAKS hbm_gbs (copy, burst)" if src == "measured"
+                     else "fallback 6.8 TB/s", "work_per_launch": amount, "work_model": per_unit})
+        if traffic is not None:
+            roof["traffic_over_algorithmic"] = traffic / amount
+    if dom["name"] in ("walk_count", "walk_emit"):
+        ops = walk_lane_ops(params, info)
+        peak_alu = alu_peak_gops(sm_count, sm_mhz)
+        roof["alu"] = {"achieved": ops / avg_s / 1e9, "peak": peak_alu, "unit": "Gop/s",
+                       "frac": ops / avg_s / 1e9 / peak_alu,
+                       "peak_source": f"derived: {sm_count} SMs (queried) x 128 lanes x median SM clock"}
     step_total = sum(t["ms"] for t in trace if t["name"] not in ("scan_exclusive",)) / max(1, args.steps)
     breakdown = {t["name"]: round(t["ms"] / max(1, args.steps), 4) for t in trace}
 
+    cfg = bench_config(g, params, world)
+    if args.downsample or args.sketch == "sparse_sign" or args.weighted:
+        cfg["workload"] = (WORKLOAD + ("_downsampled_C=ln_n" if args.downsample else "")
+                           + ("_sparse_sign_sketch" if args.sketch == "sparse_sign" else "")
+                           + ("_weighted_1to9" if args.weighted else ""))
+        if args.downsample:
+            cfg["downsample_C"] = params["downsample_C"]
     if rank == 0:
         cpu = None
         if (world == 1 and not args.no_cpu_baseline and not args.downsample and args.sketch == "gaussian"
                 and not args.weighted):
-            r = oracle_step(g, params, rep=0)
-            cpu = {"value": r["value"], "unit": "samples/s", "cores": r["cores"], "kind": "oracle",
-                   "sample": r["sample"]}
+            ob = OracleBaseline(g, params)
+            times = [ob.share(k) for k in range(args.cpu_shares)]
+            v = (params["samples"] / ob.F) / float(np.mean(times))
+            cpu = {"value": v, "unit": "samples/s", "cores": ob.cores, "kind": "oracle",
+                   "sample": f"{args.cpu_shares} of " + ob.describe()}
         line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD + ("_downsampled_C=ln_n" if args.downsample else "")
-                           + ("_sparse_sign_sketch" if args.sketch == "sparse_sign" else "")
-                           + ("_weighted_1to9" if args.weighted else ""),
-                           "n": g.n, "m": g.m, "samples": params["samples"], "T": 10,
-                           "d": 128, "q": 1, "k": 10, "l2": "flushed (256 MB write) between steps",
-                           "parallelism": f"replicas{world}", "nnz_pairs": info["nnz_c"],
-                           "nnz_M": info["nnz_M"],
-                           **({"downsample_C": params["downsample_C"]} if args.downsample else {})},
+                "config": cfg,
+                "workload_stats": {"nnz_pairs": info["nnz_c"], "nnz_M": info["nnz_M"]},
                 "e2e": {"value": whole_job_rate(world, params["samples"], e2e), "unit": "samples/s",
                         "h2d_bytes_per_step": int(g.indptr.nbytes + g.indices.astype(np.int32).nbytes
                                                   + (weights.nbytes if weights is not None else 0)),
@@ -638,6 +742,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-shares", type=int, default=4, help="oracle shares timed for cpu_baseline")
     ap.add_argument("--scale", type=float, default=10.0, help="sample-count divisor of --case runs")
     ap.add_argument("--case", choices=["sparsifier", "rsvd", "propagate", "embed"], default=None,
                     help="run one stage on a reduced workload (for profilers) instead of the benchmark")

@@ -285,6 +285,29 @@ def sparsifier_counts(indptr, indices, T, s, S, seed, C: float = 0.0, weights=No
     return keys // n, keys % n, wsum
 
 
+def sparsifier_counts_dense(indptr, indices, T, s, S, seed, chunk_samples: float = 5.0e7):
+    """The same (x, y, count) as ``sparsifier_counts`` (C = 0), for graphs whose
+    n x n pair space fits host memory (n up to a few ten thousand) and sample
+    counts too large to hold at once: the draws of consecutive arc ranges of
+    about ``chunk_samples`` draws each are counted into one dense table of
+    unordered pairs (index x n + y, x <= y), which is then read out in (x, y)
+    order. Counting is order-independent, so the result is the multiset of
+    all draws however the arcs are split."""
+    indptr = np.ascontiguousarray(indptr, dtype=np.int64)
+    n = len(indptr) - 1
+    n_arcs = int(indptr[-1])
+    per_arc = max(float(S) / max(n_arcs, 1), 1e-9)
+    step = max(1, int(chunk_samples / per_arc))
+    table = np.zeros(n * n, dtype=np.int64)
+    for a0 in range(0, n_arcs, step):
+        a1 = min(n_arcs, a0 + step)
+        x, y = sample_pairs(indptr, indices, T, s, S, seed, a0, a1)
+        table += np.bincount(x * n + y, minlength=n * n)
+        del x, y
+    keys = np.flatnonzero(table)
+    return keys // n, keys % n, table[keys]
+
+
 def stratified_counts(indptr, indices, T, S, seed, weights=None):
     """Window-stratified counts for sharing one sampling pass among many
     window weightings s (a proposal for candidate batching, not a procedure of

@@ -119,6 +119,10 @@ inline int allow_dynamic_smem(Kernel kernel) {
     return 0;
 }
 
+// Streaming multiprocessors of the current device (queried once per device
+// and cached): grids are sized in multiples of it.
+int num_sms();
+
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 __host__ __device__ __forceinline__ int64_t imax64(int64_t a, int64_t b) { return a > b ? a : b; }

@@ -1143,7 +1143,7 @@ __global__ void sign_scale_kernel(float *__restrict__ U, int64_t n, int d, int64
 
 int grid_for(int64_t work, int threads) {
     int64_t g = ceil_div(std::max<int64_t>(work, 1), threads);
-    return (int)std::min<int64_t>(g, 152 * 32);
+    return (int)std::min<int64_t>(g, num_sms() * 32);
 }
 
 }  // namespace
@@ -1183,7 +1183,7 @@ static int gram(Workspace &ws, const float *Y, int64_t n, int c, int64_t ld, dou
     int per_sm = 1;
     LNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, gram_partial_kernel, threads,
                                                              kGramRows * cp * 4));
-    const int64_t slots = 152 * (int64_t)std::max(1, per_sm);
+    const int64_t slots = num_sms() * (int64_t)std::max(1, per_sm);
     int64_t nblk = std::min<int64_t>(2 * slots, std::max<int64_t>(1, ceil_div(n, 64)));
     if (nblk > slots) nblk = (nblk / slots) * slots;
     const int64_t rows_per = ceil_div(std::max<int64_t>(n, 1), nblk);
@@ -1247,7 +1247,7 @@ static int trsm_rows(const float *Y, int64_t n, int c, int64_t ldy, const double
     // every CTA stages R in shared memory: one wave of resident CTAs, each
     // walking many rows, loads it the fewest times
     const int per_sm = std::max(1, std::min(8, (227 * 1024) / std::max(smem, 1)));
-    const int blocks = (int)std::min<int64_t>(ceil_div(n, 8), 152 * per_sm);
+    const int blocks = (int)std::min<int64_t>(ceil_div(n, 8), num_sms() * per_sm);
     LNE_TRACE("trsm_rows", st);
 #define LNE_TRSM_CASE(K)                                                                               \
     case K:                                                                                            \
@@ -1390,7 +1390,7 @@ int sign_fix_embed(Workspace &ws, float *U, int64_t n, int d, int64_t ld, const 
     LNE_TRY(ws.get("sign.scale", (size_t)d, &scale));
     LNE_CUDA_TRY(cudaMemsetAsync(best, 0, sizeof(unsigned long long) * d, st));
     const int sub = 256 / d;
-    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, sub), 152 * 8));
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, sub), num_sms() * 8));
     {
         LNE_TRACE("col_absmax", st);
         col_absmax_kernel<<<blocks, 256, 0, st>>>(U, n, d, ld, best);

@@ -190,7 +190,7 @@ __global__ void topk_f1_kernel(const float *__restrict__ S, const float *__restr
     }
 }
 
-int egrid(int64_t work) { return (int)std::min<int64_t>(ceil_div(std::max<int64_t>(work, 1), 256), 152 * 16); }
+int egrid(int64_t work) { return (int)std::min<int64_t>(ceil_div(std::max<int64_t>(work, 1), 256), num_sms() * 16); }
 
 }  // namespace
 

@@ -22,7 +22,7 @@ __global__ void sub_kernel(const float *__restrict__ A, const float *__restrict_
 }
 
 int elem_grid(int64_t count) {
-    return (int)std::min<int64_t>(ceil_div(std::max<int64_t>(count, 1), 256), 152 * 16);
+    return (int)std::min<int64_t>(ceil_div(std::max<int64_t>(count, 1), 256), num_sms() * 16);
 }
 
 // I_nu(x) from its power series sum_m (x/2)^(2m+nu) / (m! (m+nu)!).

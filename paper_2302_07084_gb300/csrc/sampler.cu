@@ -1367,7 +1367,7 @@ int attach_vinfo(Workspace &ws, const GraphView &g, WalkArgs *A, cudaStream_t st
     uint4 *vi = nullptr;
     LNE_TRY(ws.get("walk.vinfo", (size_t)std::max<int64_t>(g.n, 1), &vi));
     LNE_TRACE("build_vinfo", st);
-    build_vinfo_kernel<<<(unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(g.n, 1), 256), 152 * 8), 256, 0, st>>>(
+    build_vinfo_kernel<<<(unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(g.n, 1), 256), num_sms() * 8), 256, 0, st>>>(
         g.indptr, g.n, vi);
     LNE_LAUNCH_CHECK();
     A->vinfo = vi;
@@ -1375,7 +1375,7 @@ int attach_vinfo(Workspace &ws, const GraphView &g, WalkArgs *A, cudaStream_t st
     LNE_TRY(ws.get("walk.arcrec", (size_t)std::max<int64_t>(g.nnz, 1), &ar));
     {
         LNE_TRACE("build_arcrec", st);
-        build_arcrec_kernel<<<(unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(g.nnz, 1), 256), 152 * 16), 256, 0,
+        build_arcrec_kernel<<<(unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(g.nnz, 1), 256), num_sms() * 16), 256, 0,
                               st>>>(g.indices, g.nnz, vi, ar);
         LNE_LAUNCH_CHECK();
     }
@@ -1384,12 +1384,12 @@ int attach_vinfo(Workspace &ws, const GraphView &g, WalkArgs *A, cudaStream_t st
         uint32_t *cum = nullptr;
         LNE_TRY(ws.get("walk.cum", (size_t)std::max<int64_t>(g.nnz, 1), &cum));
         LNE_TRACE("build_vinfo", st);
-        build_cum_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g.n, 8), 152 * 16)), 256, 0,
+        build_cum_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g.n, 8), num_sms() * 16)), 256, 0,
                            st>>>(g.indptr, g.w, g.wdeg, g.n, cum);
         LNE_LAUNCH_CHECK();
         uint32_t *guide = nullptr;
         LNE_TRY(ws.get("walk.guide", (size_t)std::max<int64_t>(g.nnz, 1), &guide));
-        build_guide_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g.n, 8), 152 * 16)), 256, 0,
+        build_guide_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g.n, 8), num_sms() * 16)), 256, 0,
                              st>>>(g.indptr, cum, g.n, guide);
         LNE_LAUNCH_CHECK();
         A->cum = cum;
@@ -1405,7 +1405,7 @@ int attach_downsample(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
     LNE_TRY(ws.get("walk.ds_thr", (size_t)std::max<int64_t>(g.nnz, 1), &thr));
     LNE_TRY(ws.get("walk.ds_w", (size_t)std::max<int64_t>(g.nnz, 1), &w));
     LNE_TRACE("downsample_arcs", st);
-    downsample_arcs_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g.n, 8), 152 * 16)), 256, 0,
+    downsample_arcs_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g.n, 8), num_sms() * 16)), 256, 0,
                              st>>>(
         g.indptr, g.indices, g.w, g.wdeg, g.n, sp.ds_C, thr, w);
     LNE_LAUNCH_CHECK();
@@ -1418,7 +1418,7 @@ int attach_downsample(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
 int choose_tile_arcs(int64_t n_arcs, double rate) {
     double per_arc = rate < 1.0 ? 1.0 : rate;
     double total = per_arc * (double)n_arcs;
-    double want = total / (152.0 * 8.0);
+    double want = total / ((double)num_sms() * 8.0);
     if (want > 32768.0) want = 32768.0;
     if (want < 2048.0) want = 2048.0;
     int64_t t = (int64_t)(want / per_arc);
@@ -1621,7 +1621,7 @@ int sample_and_reduce(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
             LNE_LAUNCH_CHECK();
         } else {
             LNE_TRACE("bucket_scatter", st);
-            bucket_scatter_global_kernel<uint32_t><<<152 * 8, 256, 0, st>>>(keys0, total, keys1, cursor);
+            bucket_scatter_global_kernel<uint32_t><<<(unsigned)num_sms() * 8, 256, 0, st>>>(keys0, total, keys1, cursor);
             LNE_LAUNCH_CHECK();
         }
     }
@@ -1689,7 +1689,7 @@ int bucket_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResu
     LNE_TRY(ws.get("csr.rowcnt", (size_t)g.n, &rowcnt));
     LNE_TRY(ws.get("csr.indptr", (size_t)g.n + 1, &out->indptr));
     LNE_CUDA_TRY(cudaMemsetAsync(rowcnt, 0, sizeof(uint32_t) * g.n, st));
-    const int grid = (int)std::min<int64_t>(ceil_div(std::max<int64_t>(nnz_c, 1), 256), 152 * 16);
+    const int grid = (int)std::min<int64_t>(ceil_div(std::max<int64_t>(nnz_c, 1), 256), num_sms() * 16);
     {
         LNE_TRACE("trunclog", st);
         trunclog_kernel<<<grid, 256, 0, st>>>(C.x, C.y, C.cnt, nnz_c, g.indptr, netmf_const(sp), val, keep,
@@ -1829,7 +1829,7 @@ int sort_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Counts
     else LNE_TRY(ws.get("counts.cnt", (size_t)std::max<int64_t>(u, 1), &out->cnt));
     if (u > 0) {
         LNE_TRACE("decode_keys", st);
-        decode_keys_kernel<<<(unsigned)std::min<int64_t>(ceil_div(u, 256), 152 * 16), 256, 0, st>>>(
+        decode_keys_kernel<<<(unsigned)std::min<int64_t>(ceil_div(u, 256), num_sms() * 16), 256, 0, st>>>(
             R.uk, u, sp.B, out->x, out->y);
         LNE_LAUNCH_CHECK();
         if (R.w)
@@ -1853,7 +1853,7 @@ int assemble_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, uint6
                  cudaStream_t st) {
     const int64_t n = g.n;
     const int64_t ntiles = std::max<int64_t>(1, ceil_div(U, (int64_t)kPathTile));
-    const unsigned egrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 152 * 16));
+    const unsigned egrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), num_sms() * 16));
     uint32_t *dlen = nullptr, *rowlen = nullptr;
     int64_t *ko = nullptr, *mo = nullptr, *first = nullptr, *end = nullptr;
     unsigned long long *dstart = nullptr;
@@ -1893,7 +1893,7 @@ int assemble_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, uint6
     LNE_TRY(radix_sort_u64(ws, mk, uk, mv, val, nm, 2 * sp.B, &in_alt, st));
     const uint64_t *smk = in_alt ? uk : mk;
     const uint32_t *smv = in_alt ? val : mv;
-    const unsigned mgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nm, 256), 152 * 16));
+    const unsigned mgrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(nm, 256), num_sms() * 16));
     {
         LNE_TRACE("path_rows", st);
         if (nm > 0) {
@@ -1946,7 +1946,7 @@ int sort_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult
     LNE_TRY(sort_raw(ws, g, sp, &R, st));
     const int64_t U = R.U, n = g.n;
     const int64_t ntiles = std::max<int64_t>(1, ceil_div(U, (int64_t)kPathTile));
-    const unsigned egrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 152 * 16));
+    const unsigned egrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), num_sms() * 16));
     uint32_t *tk = nullptr, *tm = nullptr, *deg = nullptr;
     LNE_TRY(ws.get("path.tk", (size_t)ntiles, &tk));
     LNE_TRY(ws.get("path.tm", (size_t)ntiles, &tm));
@@ -2274,7 +2274,7 @@ int prepare_weighted(Workspace &ws, GraphView *g, cudaStream_t st) {
     LNE_CUDA_TRY(cudaMemsetAsync(acc, 0, 3 * sizeof(unsigned long long), st));
     if (g->n > 0) {
         LNE_TRACE("build_vinfo", st);
-        weighted_prep_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g->n, 8), 152 * 16)), 256, 0,
+        weighted_prep_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g->n, 8), num_sms() * 16)), 256, 0,
                                st>>>(g->indptr, g->w, g->n, wdeg, dinv, wf, acc,
                                      reinterpret_cast<unsigned int *>(acc + 1),
                                      reinterpret_cast<unsigned int *>(acc + 2));
@@ -2307,7 +2307,7 @@ int stratified_sample(Workspace &ws, const GraphView &g, const SamplerSpec &sp, 
     LNE_TRY(ws.get("strat.cnt", (size_t)std::max<int64_t>(U, 1), &scnt));
     if (U > 0) {
         LNE_TRACE("strat_split", st);
-        strat_split_kernel<<<(unsigned)std::min<int64_t>(ceil_div(U, 256), 152 * 16), 256, 0, st>>>(ukr, U, spare,
+        strat_split_kernel<<<(unsigned)std::min<int64_t>(ceil_div(U, 256), num_sms() * 16), 256, 0, st>>>(ukr, U, spare,
                                                                                                       r);
         LNE_LAUNCH_CHECK();
         LNE_CUDA_TRY(cudaMemcpyAsync(scnt, cnt, sizeof(uint32_t) * U, cudaMemcpyDeviceToDevice, st));
@@ -2348,7 +2348,7 @@ int stratified_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, con
     for (int r = 0; r < sp.T; ++r) w.w[r] = strat_weight(sp, r);
     const int64_t P = S.P, n = g.n;
     const int64_t ntiles = std::max<int64_t>(1, ceil_div(P, (int64_t)kPathTile));
-    const unsigned egrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), 152 * 16));
+    const unsigned egrid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 256), num_sms() * 16));
     uint32_t *tk = nullptr, *tm = nullptr, *deg = nullptr, *val = nullptr;
     uint64_t *uk = nullptr;
     LNE_TRY(ws.get("path.tk", (size_t)ntiles, &tk));
@@ -2391,7 +2391,7 @@ int strat_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Count
     LNE_TRY(ws.get("counts.r", (size_t)std::max<int64_t>(U, 1), &out->window));
     if (U > 0) {
         LNE_TRACE("decode_keys", st);
-        strat_decode_kernel<<<(unsigned)std::min<int64_t>(ceil_div(U, 256), 152 * 16), 256, 0, st>>>(
+        strat_decode_kernel<<<(unsigned)std::min<int64_t>(ceil_div(U, 256), num_sms() * 16), 256, 0, st>>>(
             ukr, U, sp.B, out->x, out->y, out->window);
         LNE_LAUNCH_CHECK();
         LNE_CUDA_TRY(cudaMemcpyAsync(out->cnt, cnt, sizeof(uint32_t) * U, cudaMemcpyDeviceToDevice, st));

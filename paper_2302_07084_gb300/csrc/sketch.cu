@@ -171,7 +171,7 @@ int check_sparse_sign(int64_t n, int c, int zeta) {
 }
 
 unsigned rows_grid(int64_t n, int per_block) {
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, (int64_t)per_block), 152 * 16));
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, (int64_t)per_block), num_sms() * 16));
 }
 
 }  // namespace

@@ -377,8 +377,8 @@ int launch_spmm(int64_t n, const int64_t *indptr, const int32_t *indices, const 
                 cudaStream_t st) {
     if (n <= 0) return 0;
     const int nt = (c + 31) / 32;
-    const int wblocks = (int)std::min<int64_t>(ceil_div(n, 8), 152 * 64);
-    const int cblocks = (int)std::min<int64_t>(n, 152 * 16);
+    const int wblocks = (int)std::min<int64_t>(ceil_div(n, 8), num_sms() * 64);
+    const int cblocks = (int)std::min<int64_t>(n, num_sms() * 16);
     LNE_TRACE(WEIGHTED ? "spmm" : "graph_spmm", st);
 #define LNE_SPMM_CASE(K)                                                                              \
     case K:                                                                                           \
@@ -421,10 +421,10 @@ bool merge_ok(const TX *X, int64_t ldx, int c, const float *Y, int64_t ldy, cons
 // very large products (>6e7 nonzeros), which keeps the carry buffers (two rows
 // of c per warp) small
 int64_t merge_slice(int64_t nnz, int64_t n) {
-    const int64_t W = nnz / (152 * 48 * 8);
+    const int64_t W = nnz / ((int64_t)num_sms() * 48 * 8);
     const int64_t two_rows = n > 0 ? 2 * ceil_div(nnz, n) : 32;
     const int64_t lo = std::max<int64_t>(32, std::min<int64_t>(1024, two_rows / 32 * 32));
-    const int64_t cap = nnz > (int64_t)152 * 48 * 8 * 1024 ? 65536 : 1024;
+    const int64_t cap = nnz > (int64_t)num_sms() * 48 * 8 * 1024 ? 65536 : 1024;
     return std::max<int64_t>(lo, std::min<int64_t>(cap, (W + 31) / 32 * 32));
 }
 
@@ -449,7 +449,7 @@ int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, c
     LNE_TRY(merge_carry(ws, ep.carry_tag, nnz, n, c, &carry, &carry_row));
     const int threads = ep.threads > 0 ? ep.threads : 256;
     const unsigned mblocks = (unsigned)ceil_div(nwarps, threads / 32);
-    const unsigned fblocks = (unsigned)std::min<int64_t>(ceil_div(n, 8), 152 * 32);
+    const unsigned fblocks = (unsigned)std::min<int64_t>(ceil_div(n, 8), num_sms() * 32);
     LNE_TRACE(WEIGHTED ? "spmm" : "graph_spmm", st);
 #define LNE_MERGE_CASE(K)                                                                                  \
     case K:                                                                                                \
@@ -691,7 +691,7 @@ int dense_sym_spmm(Workspace &ws, const float *T, int64_t ld, int64_t n, const f
     LNE_TRY(allow_dynamic_smem(kern));
     int per_sm = 1;
     LNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, msmem));
-    const int64_t slots = 152 * (int64_t)std::max(1, per_sm);
+    const int64_t slots = num_sms() * (int64_t)std::max(1, per_sm);
     int ks = 1;
     double best = 1e300;
     for (int cand = 1; cand <= 16; ++cand) {   // time ~ waves x (one slice's work)
@@ -717,7 +717,7 @@ int dense_sym_spmm(Workspace &ws, const float *T, int64_t ld, int64_t n, const f
     }
 #undef LNE_MMA_CASE
     LNE_LAUNCH_CHECK();
-    slice_sum_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n * c, 256), 152 * 16), 256, 0, st>>>(
+    slice_sum_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n * c, 256), num_sms() * 16), 256, 0, st>>>(
         P, (int)grid.y, n, c, Y, ldy);
     LNE_LAUNCH_CHECK();
     return 0;
@@ -763,7 +763,7 @@ __global__ void to_bf16_kernel(const float *__restrict__ in, __nv_bfloat16 *__re
 int to_bf16(const float *in, __nv_bfloat16 *out, int64_t count, cudaStream_t st) {
     if (count <= 0) return 0;
     LNE_TRACE("to_bf16", st);
-    to_bf16_kernel<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), 152 * 16), 256, 0, st>>>(in, out, count);
+    to_bf16_kernel<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), num_sms() * 16), 256, 0, st>>>(in, out, count);
     LNE_LAUNCH_CHECK();
     return 0;
 }

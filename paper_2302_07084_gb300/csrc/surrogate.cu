@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(256) sur_mse_kernel(const float *__restrict__ 
 
 constexpr int kFwdSmem = (kRows * 32 + 2 * kRows * kHid) * 4;
 constexpr int kBwdSmem = (kRows * kHid + kRows) * 4;
-constexpr int kParamGrid = 152 * 2;
+inline int param_grid() { return 2 * num_sms(); }
 
 }  // namespace
 
@@ -339,7 +339,7 @@ namespace {
 
 int refresh_copies(Surrogate &S, cudaStream_t st) {
     LNE_TRACE("sur_cast", st);
-    sur_cast_kernel<<<kParamGrid, 256, 0, st>>>(S.w, S.wb, S.w2t);
+    sur_cast_kernel<<<param_grid(), 256, 0, st>>>(S.w, S.wb, S.w2t);
     LNE_LAUNCH_CHECK();
     return 0;
 }
@@ -400,7 +400,7 @@ int adam(Surrogate &S, float lr, cudaStream_t st) {
     const float c1 = (float)(1.0 - std::pow(b1, (double)S.step));
     const float c2 = (float)(1.0 - std::pow(b2, (double)S.step));
     LNE_TRACE("sur_adam", st);
-    sur_adam_kernel<<<kParamGrid, 256, 0, st>>>(S.w, S.m, S.v, S.g, lr, (float)b1, (float)b2, 1e-8f, c1, c2, S.wb,
+    sur_adam_kernel<<<param_grid(), 256, 0, st>>>(S.w, S.m, S.v, S.g, lr, (float)b1, (float)b2, 1e-8f, c1, c2, S.wb,
                                                 S.w2t);
     LNE_LAUNCH_CHECK();
     return 0;
@@ -413,7 +413,7 @@ int surrogate_init(Surrogate &S, uint64_t seed, cudaStream_t st) {
     LNE_TRY(set_smem_attributes());
     {
         LNE_TRACE("sur_init", st);
-        sur_init_kernel<<<kParamGrid, 256, 0, st>>>(S.w, (uint32_t)seed, (uint32_t)(seed >> 32));
+        sur_init_kernel<<<param_grid(), 256, 0, st>>>(S.w, (uint32_t)seed, (uint32_t)(seed >> 32));
         LNE_LAUNCH_CHECK();
     }
     const std::vector<float> zero(kIn, 0.f), one(kIn, 1.f);

@@ -233,9 +233,24 @@ def default_downsample_C(n: int) -> float:
 
 def svd_small_noalloc(R: torch.Tensor, U: torch.Tensor, sigma: torch.Tensor) -> int:
     """lne_svd_small_noalloc: writes U (c x c) and sigma (c) of the FP64 matrix R
-    without allocating device memory; returns the library's status code."""
+    without allocating device memory; returns the library's status code.
+
+    The library reads c x c doubles from R and writes c x c into U and c into
+    sigma through raw pointers, so the shapes, dtypes and device are checked
+    here before the call (a mismatch raises ValueError, nothing is launched)."""
     L = load_library()
+    if R.dim() != 2 or R.shape[0] != R.shape[1]:
+        raise ValueError(f"R must be square, got shape {tuple(R.shape)}")
     c = int(R.shape[0])
+    for name, t, shape in (("R", R, (c, c)), ("U", U, (c, c)), ("sigma", sigma, (c,))):
+        if t.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64, got {t.dtype}")
+        if tuple(t.shape) != shape:
+            raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} is on {t.device}, not on the current device")
     return int(L.lne_svd_small_noalloc(_ptr(R), c, _ptr(U), _ptr(sigma), _stream()))
 
 

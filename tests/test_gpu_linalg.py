@@ -18,7 +18,7 @@ import torch
 
 import oracle
 from paper_2302_07084_gb300 import lne, synth
-from gpu_common import col_align, make_params, to_np
+from gpu_common import assert_subspace, col_align, make_params, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -147,8 +147,7 @@ def test_rsvd_on_sparsifier_workload(ctx):
     np.testing.assert_allclose(sig, ref["sigma"], rtol=1e-4)
     # the leading columns (with a gap to the rest) agree to the gate
     k = 4   # the four block directions
-    assert oracle.subspace_sin(U[:, :k], ref["U"][:, :k]) <= 1e-3
-    assert ang <= 1e-3 or gap < 1e-2
+    assert_subspace(U, ref["U"], k, tag="sbm10k rsvd")
 
 
 @pytest.mark.parametrize("k,theta,mu", [(10, 0.5, 0.2), (1, 0.5, 0.2), (2, 0.7, 0.4), (15, 0.3, 0.5), (0, 0.5, 0.2)])
@@ -200,7 +199,7 @@ def test_embed_end_to_end_sbm_small(ctx):
         W, *_ = np.linalg.lstsq(Ea[tr], np.eye(4)[y[tr]], rcond=None)
         return np.mean(np.argmax(Ea[te] @ W, 1) == y[te])
     assert abs(acc(X) - acc(ref["X"])) <= 0.005
-    assert oracle.subspace_sin(X[:, :4], ref["X"][:, :4]) <= 1e-3
+    assert_subspace(X, ref["X"], tag="sbm10k embed")
 
 
 def test_embed_rejects_bad_sizes(ctx):

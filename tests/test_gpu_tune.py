@@ -1,4 +1,9 @@
-"""Batched tuning (lne_tune_batch) against one-candidate runs.
+"""Batched tuning (lne_tune_batch, lne_tune_tasks) against the CPU oracle and
+against one-candidate runs.
+
+Every batched candidate's embedding and Macro-F1 must match the oracle's
+(oracle.embed + oracle.macro_f1) for that candidate: the subspace gate on the
+embedding and 0.005 on the score.
 
 Every candidate's embedding and scores must equal what lne_embed followed by
 lne_macro_f1 gives for that candidate alone: the batch shares the sparsifier
@@ -13,7 +18,8 @@ import pytest
 import torch
 
 from paper_2302_07084_gb300 import lne, synth
-from gpu_common import make_params, to_np
+import oracle
+from gpu_common import full_span_bound, leading_gap_index, make_params, to_np
 
 pytestmark = pytest.mark.gpu
 
@@ -175,3 +181,57 @@ def test_tasks_report_the_failing_task(ctx):
     assert e.value.code == -1 and "dimension" in str(e.value)
     with pytest.raises(lne.LneError):
         ctx.set_option(lne.OPT_TUNE_WORKERS, 0)
+
+
+def _oracle_candidate(g, p, tr, te):
+    ref = oracle.embed(g.indptr, g.indices, p.T, p.s, p.samples, p.d, p.q, p.k, p.theta, p.mu, p.seed,
+                       oversample=p.oversample)
+    f_ref = oracle.macro_f1(ref["X"], g.labels, tr, te)[0]
+    return ref, f_ref
+
+
+def _check_against_oracle(g, p, X, f_gpu, ref, f_ref, tag):
+    X = np.asarray(X, dtype=np.float64)
+    bound, gap = full_span_bound(ref["rsvd"]["sigma_all"], p.d)
+    sig_x = ref["prop"]["sigma"] if ref["prop"]["P"] is not None else ref["rsvd"]["sigma"]
+    k, _ = leading_gap_index(sig_x, kmax=min(16, p.d - 1))
+    a_lead = oracle.subspace_sin(X[:, :k], ref["X"][:, :k])
+    a_full = oracle.subspace_sin(X, ref["X"])
+    print(f"{tag}: leading {k} sin {a_lead:.2e}, all {p.d} sin {a_full:.2e} (gap at d {gap:.2e}); "
+          f"Macro-F1 {f_gpu:.4f} vs oracle {f_ref:.4f}")
+    assert a_lead <= 1e-3 and a_full <= bound, (a_lead, a_full, bound)
+    assert abs(f_gpu - f_ref) <= 0.005
+
+
+def test_batch_matches_oracle(ctx):
+    """Four candidates with distinct (k, theta, mu), two window weightings s
+    (so two sparsifiers and randomized SVDs are shared), against the oracle."""
+    g, (dg, lab, tr_t, te_t) = _task(230, 2400, 4)
+    tr, te = to_np(tr_t), to_np(te_t)
+    s_dir = synth.dirichlet_weights(10, seed=5)
+    cands = [make_params(10, np.full(10, 0.1), 20.0 * g.m, d=32, q=1, k=10, theta=0.5, mu=0.2, seed=7),
+             make_params(10, np.full(10, 0.1), 20.0 * g.m, d=32, q=1, k=4, theta=0.9, mu=0.4, seed=7),
+             make_params(10, s_dir, 20.0 * g.m, d=32, q=1, k=15, theta=0.3, mu=0.0, seed=7),
+             make_params(10, s_dir, 20.0 * g.m, d=32, q=1, k=1, theta=0.7, mu=0.3, seed=7)]
+    ma, mi, X = ctx.tune_batch(dg, cands, lab, tr_t, te_t, want_embeddings=True)
+    for j, p in enumerate(cands):
+        ref, f_ref = _oracle_candidate(g, p, tr, te)
+        _check_against_oracle(g, p, to_np(X[j]), ma[j], ref, f_ref, f"tune_batch candidate {j}")
+
+
+def test_tasks_match_oracle(ctx):
+    """lne_tune_tasks over two graphs of different sizes, two candidates each,
+    against the oracle."""
+    tasks = [_task(240 + t, n, b) for t, (n, b) in enumerate([(1800, 3), (2600, 5)])]
+    cands = [[make_params(10, synth.dirichlet_weights(10, seed=11 + t), 20.0 * g.m, d=32, q=1, k=k, theta=th,
+                          mu=mu, seed=9 + t) for (k, th, mu) in [(10, 0.5, 0.2), (6, 0.8, 0.45)]]
+             for t, (g, _) in enumerate(tasks)]
+    ctx.set_option(lne.OPT_TUNE_WORKERS, 2)
+    ma, _ = ctx.tune_tasks([dev for _, dev in tasks], cands)
+    ctx.set_option(lne.OPT_TUNE_WORKERS, 4)
+    for t, (g, (dg, lab, tr_t, te_t)) in enumerate(tasks):
+        tr, te = to_np(tr_t), to_np(te_t)
+        for j, p in enumerate(cands[t]):
+            ref, f_ref = _oracle_candidate(g, p, tr, te)
+            X = to_np(ctx.embed(dg, p))
+            _check_against_oracle(g, p, X, ma[t, j], ref, f_ref, f"tune_tasks graph {t} candidate {j}")

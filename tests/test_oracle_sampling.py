@@ -114,6 +114,39 @@ def test_T1_returns_own_arc(small_graph):
     assert np.all(np.asarray(A[x, y]).ravel() == 1)
 
 
+def test_chunked_dense_counts_T1_closed_form(small_graph):
+    """The chunked dense-table count (for sample counts too large to hold at
+    once): with T = 1 every edge is counted exactly n_{u->v} + n_{v->u} times,
+    however the arcs are split into chunks."""
+    g = small_graph
+    S = 5.0 * g.n_arcs
+    x, y, cnt = oracle.sparsifier_counts_dense(g.indptr, g.indices, 1, [1.0], S, seed=2,
+                                               chunk_samples=7 * 5)   # 7 arcs per chunk
+    assert np.all(cnt == 10) and x.size == g.m
+    assert np.all(x <= y) and np.all(np.diff(x * g.n + y) > 0)
+    A = sp.csr_matrix((np.ones(g.n_arcs), g.indices, g.indptr), shape=(g.n, g.n))
+    assert np.all(np.asarray(A[x, y]).ravel() == 1)
+
+
+def test_chunked_dense_counts_match_exact_expectation():
+    """The chunked count against the exact expectation S/vol sum_r s_r D P^r
+    (z-scores), with a chunk size that splits the arcs unevenly."""
+    g = synth.lollipop_tiny()
+    T = 5
+    s = [0.1, 0.3, 0.2, 0.25, 0.15]
+    S = 20000.0 * g.n_arcs
+    x, y, cnt = oracle.sparsifier_counts_dense(g.indptr, g.indices, T, s, S, seed=23, chunk_samples=3 * 20000.0)
+    K = np.zeros((g.n, g.n))
+    K[x, y] = cnt
+    EK = _expected_counts(g, T, s, S)
+    iu = np.triu_indices(g.n)
+    assert np.all(K[iu][EK[iu] == 0] == 0)
+    m = EK[iu] > 0
+    z = (K[iu][m] - EK[iu][m]) / np.sqrt(EK[iu][m])
+    assert np.max(np.abs(z)) < 6
+    assert int(cnt.sum()) == oracle.count_samples(g.n_arcs, S, 23)
+
+
 def _dense_P(g):
     A = sp.csr_matrix((np.ones(g.n_arcs), g.indices, g.indptr), shape=(g.n, g.n)).toarray()
     d = A.sum(1)

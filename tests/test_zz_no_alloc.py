@@ -24,7 +24,10 @@ def test_noalloc_small_svd_matches_allocating_entry_point():
     build.build()
     ctx = lne.Context(0)
     try:
-        for c, cond, seed in [(144, 1e4, 1), (48, 1e2, 2)]:
+        # 144 and 48: the register-resident Jacobi; 33 (odd): its padding
+        # column; 151 and 160 (the top of the fixed array): the FP32
+        # shared-memory Jacobi taken above 144 columns
+        for c, cond, seed in [(144, 1e4, 1), (48, 1e2, 2), (33, 1e2, 4), (151, 1e3, 3), (160, 1e3, 5)]:
             R = torch.as_tensor(_triangular(c, cond, seed)).cuda()
             U_ref, s_ref = ctx.svd_small(R)
             U_ref, s_ref = U_ref.cpu().numpy(), s_ref.cpu().numpy()
@@ -45,5 +48,15 @@ def test_noalloc_small_svd_matches_allocating_entry_point():
         assert lne.svd_small_noalloc(big, out, sig) == -1
         torch.cuda.synchronize()
         assert bool((out == 7.0).all()) and bool((sig == 7.0).all())
+        # wrong dtype or shape: refused in the binding before any launch
+        c = R.shape[0]
+        U = torch.empty((c, c), dtype=torch.float64, device="cuda")
+        s = torch.empty(c, dtype=torch.float64, device="cuda")
+        with pytest.raises(ValueError):
+            lne.svd_small_noalloc(R.float(), U, s)
+        with pytest.raises(ValueError):
+            lne.svd_small_noalloc(R, U[:, : c - 1].contiguous(), s)
+        with pytest.raises(ValueError):
+            lne.svd_small_noalloc(R, U, s[: c - 1])
     finally:
         ctx.close()
