@@ -35,7 +35,9 @@ def test_dense_table_products_match_csr_products(ctx, d, q):
     ctx.set_option(lne.OPT_DENSE_PRODUCT, 0)
     ctx.set_option(lne.OPT_AGGREGATION, lne.AGG_AUTO)
     lead = 4
-    assert_subspace(out[1], out[2], lead, 1e-5, 1e-5, tag=f"table vs csr d={d} q={q}")
+    # two FP32 paths summing in different orders: the leading directions agree
+    # to 1e-5, the whole d-column span (small gap at d) to 1e-4
+    assert_subspace(out[1], out[2], lead, 1e-5, 1e-4, tag=f"table vs csr d={d} q={q}")
     ref = oracle.embed(g.indptr, g.indices, 10, s, p.samples, d, q, 10, 0.5, 0.2, 1)
     for mode in (1, 2):
         assert_subspace(out[mode], ref["X"], lead, tag=f"mode {mode} vs oracle d={d} q={q}")
