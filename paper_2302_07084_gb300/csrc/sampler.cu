@@ -59,6 +59,7 @@ struct WalkArgs {
     uint32_t rk[20];              // Philox round keys (k0 + i W0, k1 + i W1), i = 0..9
     uint32_t thr32[16];           // thresholds below 2^32, ascending
     int T_eff;                    // how many thresholds are below 2^32
+    const uint8_t *rlut;          // window-length table (build_rlut_kernel), 4096 entries
     uint64_t base_magic;          // ceil(2^64 / base): s / base by a high multiply
     uint64_t rmagic[17];          // ceil(2^64 / r) for r = 1..16 (index r)
     // edge downsampling (NULL = off): per arc, the coin keeps a draw iff its
@@ -123,16 +124,19 @@ __device__ __forceinline__ uint32_t fastdiv32(uint32_t a, uint64_t M) {
 }
 
 // Per-vertex walk record {offset bits 0..31, offset bits 32..39 | degree << 8,
-// m = floor(2^32 / degree) (0 for degree < 2), 0}. Degrees of 2^24 and more are
-// marked 0xFFFFFF and read from indptr.
+// m, the vertex} with m = floor(2^32 / degree) for degree >= 2, m = 2^32 - 1 for
+// degree 1 (then the Barrett step below yields 0 without a special case) and
+// 0 for degree 0. Degrees of 2^24 and more are marked 0xFFFFFF and read from
+// indptr.
 __global__ void build_vinfo_kernel(const int64_t *__restrict__ indptr, int64_t n, uint4 *__restrict__ vinfo) {
     for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         const int64_t off = indptr[x];
         const int64_t deg = indptr[x + 1] - off;
         const uint32_t dfield = deg >= 0xFFFFFF ? 0xFFFFFFu : (uint32_t)deg;
-        const uint32_t m = (deg >= 2 && deg < 0xFFFFFF) ? (uint32_t)((1ull << 32) / (uint64_t)deg) : 0u;
-        vinfo[x] = make_uint4((uint32_t)off, (uint32_t)((off >> 32) & 0xFF) | (dfield << 8), m, 0u);
+        const uint32_t m = (deg >= 2 && deg < 0xFFFFFF) ? (uint32_t)((1ull << 32) / (uint64_t)deg)
+                           : deg == 1 ? 0xFFFFFFFFu : 0u;
+        vinfo[x] = make_uint4((uint32_t)off, (uint32_t)((off >> 32) & 0xFF) | (dfield << 8), m, (uint32_t)x);
     }
 }
 
@@ -147,6 +151,23 @@ __global__ void build_arcrec_kernel(const int32_t *__restrict__ indices, int64_t
         const uint4 r = vinfo[v];
         arcrec[p] = make_uint4((uint32_t)v, r.x, r.y, r.z);
     }
+}
+
+// Window-length table over the top 12 bits of a word: entry b holds
+// r = 1 + #{i : thr_i <= b 2^20} (Algorithm 3's multinomial draw by
+// thresholds), with bit 7 set when a threshold falls inside the bucket
+// (b 2^20, b 2^20 + 2^20 - 1], where the draw counts thresholds itself.
+__global__ void build_rlut_kernel(WalkArgs A, uint8_t *__restrict__ lut) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= 4096) return;
+    const uint32_t lo = (uint32_t)b << 20, hi = lo | 0xFFFFFu;
+    int r = 1;
+    bool amb = false;
+    for (int i = 0; i < A.T_eff; ++i) {
+        r += lo >= A.thr32[i] ? 1 : 0;
+        amb |= (A.thr32[i] > lo) && (A.thr32[i] <= hi);
+    }
+    lut[b] = (uint8_t)(r | (amb ? 0x80 : 0));
 }
 
 // Weighted graphs: per arc j of vertex x the walk threshold
@@ -421,7 +442,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 10 : 8) walk_emit_ke
     KeyT *__restrict__ keys, int32_t *__restrict__ u1, int32_t *__restrict__ v1,
     uint32_t *__restrict__ bucket_cnt, int nb_smem) {
     extern __shared__ uint32_t smem[];
-    __shared__ uint8_t s_rlut[4096];
+    __shared__ __align__(16) uint8_t s_rlut[4096];
     __shared__ uint64_t s_rmagic[17];
     // s_upack: per chunk sample its index, r, sigma and rank; s_uw3: its word 3
     // (phase 2 reads it through the index, so no permuted copy takes shared
@@ -435,17 +456,9 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 10 : 8) walk_emit_ke
     int32_t *s_dst = s_src + tile_arcs;
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(s_dst + tile_arcs);
     const int tid = threadIdx.x;
-    // window-length table over the top 12 bits of the word
-    for (int b = tid; b < 4096; b += kWalkThreads) {
-        const uint32_t lo = (uint32_t)b << 20, hi = lo | 0xFFFFFu;
-        int r = 1;
-        bool amb = false;
-        for (int i = 0; i < A.T_eff; ++i) {
-            r += lo >= A.thr32[i] ? 1 : 0;
-            amb |= (A.thr32[i] > lo) && (A.thr32[i] <= hi);
-        }
-        s_rlut[b] = (uint8_t)(r | (amb ? 0x80 : 0));
-    }
+    // window-length table (built once per launch)
+    for (int b = tid; b < 4096 / 16; b += kWalkThreads)
+        reinterpret_cast<uint4 *>(s_rlut)[b] = __ldg(reinterpret_cast<const uint4 *>(A.rlut) + b);
     if (tid < 17) s_rmagic[tid] = A.rmagic[tid];
     const int64_t a0 = a_begin + (int64_t)blockIdx.x * tile_arcs;
     const int na = (int)imin64(tile_arcs, a_end - a0);
@@ -615,6 +628,309 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 10 : 8) walk_emit_ke
         for (int i = tid; i < nb_smem; i += kWalkThreads) {
             uint32_t c = s_hist[i];
             if (c) atomicAdd(&bucket_cnt[i], c);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The dense-table walk of unweighted graphs without downsampling or window
+// strata (the benchmark's case). Same draws as walk_emit_kernel<.., 2, false>
+// (Algorithms 1 and 3, the same Philox words), organised for fewer
+// instructions and less DRAM traffic per draw:
+//
+// * each warp works alone on batches of kTabBatch consecutive samples of the
+//   CTA's arc tile: it draws the heads (block 0: r, sigma, word 3), ranks the
+//   batch by window length r in warp-private shared memory (__match_any
+//   groups, one 17-bin scan), then walks the batch in r order with two draws
+//   per lane taken from adjacent ranked positions, so a lane's two chains and
+//   the lanes of a warp take nearly the same number of steps; no CTA barrier
+//   after the tile set-up;
+// * the target vertex's record is loaded with the source's when a draw
+//   starts, so switching from the u side to the v side is a register move;
+// * n <= 65536: arc offsets fit 32 bits and degrees 16, so a step is a
+//   Barrett reduction, one 32-bit add and one 16-byte load;
+// * counts go into narrow counters packed 32 / BITS to a 32-bit word (8 bits:
+//   a quarter of the table's bytes, so it stays in L2): every increment is a
+//   returning atomic add, and the rare add that wraps a field records the wrap
+//   (and those of the fields its carry runs into) in the 32-bit table;
+//   table_decode_kernel turns fields and wraps into exact 32-bit counts.
+// ---------------------------------------------------------------------------
+constexpr int kTabThreads = 128;
+constexpr int kTabWarps = kTabThreads / 32;
+constexpr int kTabBatch = 256;
+constexpr int kTabMaxTileArcs = 128;   // arcs per CTA tile (their walk records: 32 B each in shared memory)
+constexpr int kTabMinBlocks = 10;      // CTAs per SM (48 registers a thread)
+constexpr int kTabBits = 8;            // bits per packed counter (measured: 8 bits 12.6 ms, 16 bits 13.3 ms)
+static_assert(kTabBatch == 256, "ranks and batch indices are packed in 8 bits");
+
+struct TabDraw {
+    uint32_t j, arc;            // Philox counter words 0 and 1 (arc < 2^32)
+    int steps, sigma;
+    u32x4 nb;                   // current Philox block
+    uint32_t cx, coff, chd, cm; // current vertex: id, arc offset, degree << 8, Barrett m
+    uint32_t v, voff, vhd, vm;  // the arc's target and its record
+    uint32_t uend;
+};
+
+// ru, rv: the walk records of the arc's source u and target v (vertex in .w).
+__device__ __forceinline__ void tab_begin(uint32_t arc, uint32_t j, int r, int sigma, uint32_t w3, uint4 ru,
+                                          uint4 rv, TabDraw &d) {
+    d.j = j;
+    d.arc = arc;
+    d.steps = r - 1;
+    d.sigma = sigma;
+    d.nb = u32x4{0u, 0u, 0u, w3};
+    d.v = rv.w;
+    d.voff = rv.x;
+    d.vhd = rv.y;
+    d.vm = rv.z;
+    d.uend = ru.w;
+    const bool from_v = sigma == 0 && d.steps > 0;
+    d.cx = from_v ? rv.w : ru.w;
+    d.coff = from_v ? rv.x : ru.x;
+    d.chd = from_v ? rv.y : ru.y;
+    d.cm = from_v ? rv.z : ru.z;
+}
+
+// Step K (word 3 + K) of the draw, if it has one.
+template <int K>
+__device__ __forceinline__ void tab_step(const WalkArgs &A, TabDraw &d) {
+    if (K >= d.steps) return;
+    constexpr int widx = 3 + K;
+    if ((widx & 3) == 0) d.nb = philox_rk(u32x4{d.j, d.arc, 0u, (uint32_t)(widx >> 2)}, A.rk);
+    const uint32_t w = (widx & 3) == 0 ? d.nb.x : (widx & 3) == 1 ? d.nb.y : (widx & 3) == 2 ? d.nb.z : d.nb.w;
+    const uint32_t deg = d.chd >> 8;
+    if (deg != 0) {   // degree 0 only on graphs that break the symmetry contract: stay
+        // w mod deg by Barrett (m = floor(2^32 / deg), 2^32 - 1 for deg = 1):
+        // the estimate is the remainder or the remainder + deg
+        const uint32_t q = __umulhi(w, d.cm);
+        const uint32_t rr = w - q * deg;
+        const uint32_t jj = min(rr, rr - deg);
+        const uint4 ra = __ldg(A.arcrec + (d.coff + jj));
+        d.cx = ra.x;
+        d.coff = ra.y;
+        d.chd = ra.z;
+        d.cm = ra.w;
+    }
+    if (K + 1 == d.sigma && K + 1 < d.steps) {   // u side done: continue from v
+        d.uend = d.cx;
+        d.cx = d.v;
+        d.coff = d.voff;
+        d.chd = d.vhd;
+        d.cm = d.vm;
+    }
+}
+
+template <int K>
+struct TabSteps {
+    __device__ __forceinline__ static void run(const WalkArgs &A, TabDraw &a, TabDraw &b, int kmax) {
+        if (K >= kmax) return;
+        tab_step<K>(A, a);
+        tab_step<K>(A, b);
+        TabSteps<K + 1>::run(A, a, b, kmax);
+    }
+};
+template <>
+struct TabSteps<15> {
+    __device__ __forceinline__ static void run(const WalkArgs &, TabDraw &, TabDraw &, int) {}
+};
+
+__device__ __forceinline__ void tab_end(const TabDraw &d, uint32_t *x, uint32_t *y) {
+    uint32_t pu, pv;
+    if (d.sigma >= d.steps) {   // every step on the u side (or none at all)
+        pu = d.steps > 0 ? d.cx : d.uend;
+        pv = d.v;
+    } else {
+        pu = d.uend;
+        pv = d.cx;
+    }
+    *x = min(pu, pv);
+    *y = max(pu, pv);
+}
+
+// Packed narrow counters: 32 / BITS counters per 32-bit word, counter i in
+// bits [BITS (i mod P), BITS (i mod P) + BITS) of word i / P.
+template <int BITS>
+struct TabPack {
+    static constexpr int P = 32 / BITS;
+    static constexpr uint32_t mask = (1u << BITS) - 1u;
+};
+
+// Counts one draw of counter `at` (= x ld + y) into the packed table; returns
+// the word's previous value for tab_wraps (checked later, so that the atomic's
+// round trip overlaps the next draws' walks).
+template <int BITS>
+__device__ __forceinline__ uint32_t tab_count(uint32_t *__restrict__ tp, uint32_t at) {
+    constexpr int P = TabPack<BITS>::P;
+    return atomicAdd(tp + at / P, 1u << (BITS * (at % P)));
+}
+
+// Records the wraps caused by the increment of counter `at` that found `old`:
+// the counter's field wraps when it held all ones, its carry then moves into
+// the next field of the word, which wraps in turn if it held all ones, and so
+// on (a carry out of the word's top bit is lost). carry[i] counts the wraps of
+// counter i's field.
+template <int BITS>
+__device__ __forceinline__ void tab_wraps(uint32_t *__restrict__ carry, uint32_t at, uint32_t old) {
+    constexpr int P = TabPack<BITS>::P;
+    constexpr uint32_t mask = TabPack<BITS>::mask;
+    const uint32_t f = at % P;
+    if (((old >> (BITS * f)) & mask) != mask) return;
+    const uint32_t base = at - f;
+    for (uint32_t i = f; i < (uint32_t)P; ++i) {
+        if (((old >> (BITS * i)) & mask) != mask) break;
+        atomicAdd(carry + base + i, 1u);
+    }
+}
+
+template <int BITS>
+__global__ void __launch_bounds__(kTabThreads, kTabMinBlocks) walk_table_kernel(WalkArgs A, int tile_arcs,
+                                                                     uint32_t *__restrict__ tp,
+                                                                     uint32_t *__restrict__ carry, uint32_t ld) {
+    extern __shared__ uint4 smem4[];
+    __shared__ __align__(16) uint8_t s_rlut[4096];
+    __shared__ uint64_t s_rmagic[17];
+    __shared__ uint32_t s_ent[kTabWarps][kTabBatch];    // arc in tile | r << 12 | sigma << 17 | rank << 21
+    __shared__ uint32_t s_w3[kTabWarps][kTabBatch];     // word 3 of each draw
+    __shared__ uint8_t s_sorted[kTabWarps][kTabBatch];  // batch index at each ranked position
+    __shared__ uint32_t s_hist[kTabWarps][32];          // draws per r so far in the batch
+
+    uint4 *s_rec = smem4;                                        // 2 tile_arcs: records of u and v
+    uint32_t *s_off = reinterpret_cast<uint32_t *>(smem4 + 2 * tile_arcs);   // tile_arcs + 1
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int b = tid; b < 4096 / 16; b += kTabThreads)
+        reinterpret_cast<uint4 *>(s_rlut)[b] = __ldg(reinterpret_cast<const uint4 *>(A.rlut) + b);
+    if (tid < 17) s_rmagic[tid] = A.rmagic[tid];
+    s_hist[warp][lane] = 0;
+    const int64_t a0 = (int64_t)blockIdx.x * tile_arcs;
+    const int na = (int)imin64(tile_arcs, A.n_arcs - a0);
+    for (int i = tid; i < na; i += kTabThreads) {
+        s_off[i] = arc_count(A, a0 + i);
+        s_rec[2 * i] = __ldg(A.vinfo + arc_source(A.indptr, A.n, a0 + i));
+        s_rec[2 * i + 1] = __ldg(A.vinfo + __ldg(A.indices + a0 + i));
+    }
+    __syncthreads();
+    const uint32_t total = block_exclusive_scan<kTabThreads>(s_off, na);
+    if (tid == 0) s_off[na] = total;
+    __syncthreads();
+    const bool uniform = A.thr_frac == 0;
+    uint32_t *ent = s_ent[warp];
+    uint32_t *w3s = s_w3[warp];
+    uint8_t *sorted = s_sorted[warp];
+    uint32_t *hist = s_hist[warp];
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    const uint32_t nbatch = (total + kTabBatch - 1) / kTabBatch;
+    for (uint32_t bt = warp; bt < nbatch; bt += kTabWarps) {
+        const uint32_t bbase = bt * kTabBatch;
+        // heads and ranks by r (r = 0: past the tile's last sample)
+#pragma unroll 1
+        for (int t = 0; t < kTabBatch / 32; ++t) {
+            const uint32_t idx = (uint32_t)t * 32 + lane;
+            const uint32_t s = bbase + idx;
+            int r = 0, sg = 0, lo = 0;
+            uint32_t w3 = 0;
+            if (s < total) {
+                if (uniform) {
+                    lo = A.base == 1 ? (int)s : (int)fastdiv32(s, A.base_magic);
+                } else {
+                    int hi = na;   // s_off[lo] <= s < s_off[hi]
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (s_off[mid] <= s) lo = mid; else hi = mid;
+                    }
+                }
+                uint32_t coin;
+                draw_head(A, s_rlut, s_rmagic, a0 + lo, s - s_off[lo], &r, &sg, &coin, &w3);
+            }
+            const unsigned grp = __match_any_sync(0xffffffffu, r);
+            const int leader = __ffs(grp) - 1;
+            uint32_t base = 0;
+            if (lane == leader) {
+                base = hist[r];
+                hist[r] = base + (uint32_t)__popc(grp);
+            }
+            base = __shfl_sync(0xffffffffu, base, leader);
+            const uint32_t rank = base + (uint32_t)__popc(grp & lt_mask);
+            ent[idx] = (uint32_t)lo | ((uint32_t)r << 12) | ((uint32_t)sg << 17) | (rank << 21);
+            w3s[idx] = w3;
+            __syncwarp();   // the next group leader reads what this one wrote
+        }
+        // exclusive scan of the 17 bins: lane r holds the first position of r
+        const uint32_t h = lane < 17 ? hist[lane] : 0u;
+        uint32_t incl = h;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t start = incl - h;
+        hist[lane] = 0;
+#pragma unroll 1
+        for (int t = 0; t < kTabBatch / 32; ++t) {
+            const uint32_t idx = (uint32_t)t * 32 + lane;
+            const uint32_t e = ent[idx];
+            const uint32_t pos = __shfl_sync(0xffffffffu, start, (e >> 12) & 31) + (e >> 21);
+            sorted[pos] = (uint8_t)idx;
+        }
+        __syncwarp();
+        // walks in r order, two adjacent ranked draws per lane
+        const uint32_t first = __shfl_sync(0xffffffffu, start, 1);
+        // the previous pair's counters and the words their increments found
+        uint32_t at0 = 0, at1 = 0, old0 = 0, old1 = 0;
+        bool pend0 = false, pend1 = false;
+#pragma unroll 1
+        for (uint32_t q = first + 2 * (uint32_t)lane; q < (uint32_t)kTabBatch; q += 64) {
+            const bool has1 = q + 1 < (uint32_t)kTabBatch;
+            const uint32_t i0 = sorted[q], i1 = sorted[has1 ? q + 1 : q];
+            const uint32_t e0 = ent[i0], e1 = ent[i1];
+            const uint32_t lo0 = e0 & 0xFFFu, lo1 = e1 & 0xFFFu;
+            TabDraw d0, d1;
+            tab_begin((uint32_t)(a0 + lo0), bbase + i0 - s_off[lo0], (int)((e0 >> 12) & 31), (int)((e0 >> 17) & 15),
+                      w3s[i0], s_rec[2 * lo0], s_rec[2 * lo0 + 1], d0);
+            tab_begin((uint32_t)(a0 + lo1), bbase + i1 - s_off[lo1], (int)((e1 >> 12) & 31), (int)((e1 >> 17) & 15),
+                      w3s[i1], s_rec[2 * lo1], s_rec[2 * lo1 + 1], d1);
+            if (!has1) d1.steps = 0;
+            TabSteps<0>::run(A, d0, d1, max(d0.steps, d1.steps));
+            if (pend0) tab_wraps<BITS>(carry, at0, old0);
+            if (pend1) tab_wraps<BITS>(carry, at1, old1);
+            uint32_t x, y;
+            tab_end(d0, &x, &y);
+            at0 = x * ld + y;   // < 2^32: ld <= 65536
+            old0 = tab_count<BITS>(tp, at0);
+            pend0 = true;
+            pend1 = has1;
+            if (has1) {
+                tab_end(d1, &x, &y);
+                at1 = x * ld + y;
+                old1 = tab_count<BITS>(tp, at1);
+            }
+        }
+        if (pend0) tab_wraps<BITS>(carry, at0, old0);
+        if (pend1) tab_wraps<BITS>(carry, at1, old1);
+        __syncwarp();
+    }
+}
+
+// Exact 32-bit counts from the packed table and its wrap records, in place in
+// the 32-bit table (upper triangle only: nothing else was counted). Field i
+// of a word received its counter's c_i increments plus one carry per wrap of
+// field i - 1 (none for i = 0), and wrapped carry[i] times, so
+// c_i = field_i + 2^BITS carry[i] - carry[i - 1].
+template <int BITS>
+__global__ void table_decode_kernel(const uint32_t *__restrict__ tp, uint32_t *__restrict__ tab, int n, int64_t ld) {
+    constexpr int P = TabPack<BITS>::P;
+    constexpr uint32_t mask = TabPack<BITS>::mask;
+    for (int x = blockIdx.x; x < n; x += gridDim.x) {
+        const int64_t k0 = ((int64_t)x * ld + x) / P, k1 = ((int64_t)x * ld + ld) / P;
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+            const uint32_t w = tp[k];
+            uint32_t prev = 0;
+#pragma unroll
+            for (int i = 0; i < P; ++i) {
+                const uint32_t wr = tab[P * k + i];
+                tab[P * k + i] = ((w >> (BITS * i)) & mask) + (wr << BITS) - prev;
+                prev = wr;
+            }
         }
     }
 }
@@ -1335,6 +1651,7 @@ WalkArgs make_walk_args(const GraphView &g, const SamplerSpec &sp) {
     A.T = sp.T;
     A.B = sp.B;
     A.vinfo = nullptr;
+    A.rlut = nullptr;
     for (int i = 0; i < 16; ++i) A.thr[i] = sp.thr[i];
     uint32_t k0 = sp.k0, k1 = sp.k1;
     for (int r = 0; r < 10; ++r) {
@@ -1380,6 +1697,11 @@ int attach_vinfo(Workspace &ws, const GraphView &g, WalkArgs *A, cudaStream_t st
         LNE_LAUNCH_CHECK();
     }
     A->arcrec = ar;
+    uint8_t *lut = nullptr;
+    LNE_TRY(ws.get("walk.rlut", 4096, &lut));
+    build_rlut_kernel<<<16, 256, 0, st>>>(*A, lut);
+    LNE_LAUNCH_CHECK();
+    A->rlut = lut;
     if (g.w) {
         uint32_t *cum = nullptr;
         LNE_TRY(ws.get("walk.cum", (size_t)std::max<int64_t>(g.nnz, 1), &cum));
@@ -1992,6 +2314,30 @@ int sample_table(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Table
     const int tile_arcs = choose_tile_arcs(g.nnz, (double)sp.base + 0.5);
     const int64_t ntiles = ceil_div(g.nnz, tile_arcs);
     const int smem = walk_smem_bytes(tile_arcs, 0);
+    if (!A.ds_thr && !A.w && !A.strat) {
+        // tiles of at most kTabMaxTileArcs arcs, whose walk records sit in shared memory
+        const int tab_arcs = std::min(tile_arcs, kTabMaxTileArcs);
+        const int64_t tab_tiles = ceil_div(g.nnz, tab_arcs);
+        const int tab_smem = tab_arcs * 32 + (tab_arcs + 1) * 4;
+        // packed narrow counters, decoded into the 32-bit table afterwards
+        constexpr int BITS = kTabBits;
+        constexpr int P = TabPack<BITS>::P;
+        uint32_t *tp = nullptr;
+        LNE_TRY(ws.get("table.packed", (size_t)(ld * ld / P), &tp));
+        LNE_CUDA_TRY(cudaMemsetAsync(tp, 0, sizeof(uint32_t) * (size_t)(ld * ld / P), st));
+        {
+            LNE_TRACE("walk_count", st);
+            LNE_TRY(allow_dynamic_smem(walk_table_kernel<BITS>));
+            walk_table_kernel<BITS><<<(unsigned)tab_tiles, kTabThreads, tab_smem, st>>>(A, tab_arcs, tp, tb->T,
+                                                                                         (uint32_t)ld);
+            LNE_LAUNCH_CHECK();
+        }
+        LNE_TRACE("table_decode", st);
+        table_decode_kernel<BITS><<<(unsigned)std::min<int64_t>(g.n, num_sms() * 8), 256, 0, st>>>(tp, tb->T,
+                                                                                                    (int)g.n, ld);
+        LNE_LAUNCH_CHECK();
+        return 0;
+    }
     LNE_TRACE("walk_count", st);
     if (A.ds_thr) {   // downsampled: 64-bit weight sums
         LNE_TRY(ws.get("table.W", (size_t)(ld * ld), &tb->W));

@@ -187,6 +187,24 @@ def test_bench_workload_sampled(ctx):
     assert bool((out["data"] > 0).all())
 
 
+def test_two_hub_counts_past_16_bits(ctx):
+    """K_{2,500}: the pairs of the two hubs, (0, 0), (0, 1) and (1, 1), are
+    counted 1.9e5 to 3.8e5 times, past 16 bits, and (0, 0) and (0, 1) are
+    neighbours in the count table; every count stays exact."""
+    L = 500
+    u = np.concatenate([np.zeros(L, np.int64), np.ones(L, np.int64)])
+    v = np.concatenate([np.arange(2, L + 2), np.arange(2, L + 2)])
+    indptr, indices = synth.csr_from_edges(L + 2, u, v)
+    g = synth.Graph(L + 2, indptr, indices, None, "k2_500")
+    p = make_params(3, [0.2, 0.5, 0.3], 1500.0 * g.n_arcs, seed=5)
+    res = ctx.sparsifier_counts(lne.DeviceGraph.from_graph(g), p)
+    x, y, c = oracle.sparsifier_counts(g.indptr, g.indices, p.T, p.s, p.samples, p.seed)
+    assert np.array_equal(to_np(res["x"]).astype(np.int64), x)
+    assert np.array_equal(to_np(res["y"]).astype(np.int64), y)
+    assert np.array_equal(to_np(res["count"]).astype(np.int64), c)
+    assert c[(x == 0) & (y == 1)][0] > 3 * 65536 and c[(x == 0) & (y == 0)][0] > 2 * 65536
+
+
 @pytest.mark.parametrize("C", [0.0, 0.3])
 def test_heavy_pairs_star(ctx, C):
     """A star (hub 0, 3000 leaves): a few pairs gather most draws (every walk
