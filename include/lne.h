@@ -128,7 +128,9 @@ typedef struct lne_ctx lne_ctx;
 #define LNE_OPT_DENSE_PRODUCT 4  /* products of the randomized SVD (FP32) on the dense count table
                                     instead of the CSR, when the table aggregation ran: 0 = when at
                                     least 10% of all pairs are present (default), 1 = never,
-                                    2 = always; same values, different summation order */
+                                    2 = always. The dense product runs on the tcgen05 tensor cores
+                                    (TF32 hi / lo split, three MMAs per product: FP32 accuracy);
+                                    same values as the CSR product, summed in another order */
 #define LNE_OPT_TUNE_WORKERS 3   /* host worker threads (each with its own stream and workspace)
                                     of lne_tune_tasks, 1..16 (default 4) */
 #define LNE_OPT_STRATIFIED   5   /* 1: window-stratified sampling (not in the paper): draws take

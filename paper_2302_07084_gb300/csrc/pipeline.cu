@@ -84,9 +84,13 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
     const bool bf16 = precision == LNE_PREC_BF16_MIXED;
     __nv_bfloat16 *Xh = nullptr;   // BF16 dense operand of the products
     if (bf16) LNE_TRY(ws.get("rsvd.xh", (size_t)n * c, &Xh));
-    // FP32 products: the dense upper triangle when the caller supplied it
+    // FP32 products: the dense table on the tensor cores when the caller
+    // supplied it (its TF32 hi / lo parts prepared once for all products)
+    const float *a_hi = nullptr, *a_lo = nullptr;
+    const bool dense_tc = M.dense && !bf16 && (sketch.kind != LNE_SKETCH_SPARSE_SIGN || q > 0);
+    if (dense_tc) LNE_TRY(dense_tc_prepare(ws, M.dense, M.dense_ld, &a_hi, &a_lo, st));
     auto mprod = [&](const float *X, float *Y) -> int {
-        if (M.dense) return dense_sym_spmm(ws, M.dense, M.dense_ld, n, X, c, c, Y, c, st);
+        if (dense_tc) return dense_tc_spmm(ws, a_hi, a_lo, M.dense_ld, n, X, c, c, Y, c, st);
         return spmm(ws, M, X, c, c, Y, c, st);
     };
     // Algorithm 4: Omega = randn(n, d+s); Y = M Omega. The sparse sign Omega

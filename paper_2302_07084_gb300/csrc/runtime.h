@@ -169,10 +169,15 @@ struct SpmmEpilogue {
     int threads = 0;                    // CTA size of the merge kernel (0 = default)
     const char *carry_tag = nullptr;    // workspace name of the merge carry buffers (NULL = shared)
 };
-// Y = M X for M held as the dense upper triangle T (float bits, leading
-// dimension ld) of the symmetric sparsifier (spmm.cu).
-int dense_sym_spmm(Workspace &ws, const float *T, int64_t ld, int64_t n, const float *X, int64_t ldx, int c,
-                   float *Y, int64_t ldy, cudaStream_t st);
+// Partial products of ks k-slices (P[z][n][c]) added in slice order into Y.
+int slice_sum(const float *P, int ks, int64_t n, int c, float *Y, int64_t ldy, cudaStream_t st);
+// The tensor-core (tcgen05) dense product: dense_tc_prepare splits the
+// upper-triangle table into the full symmetric matrix's TF32 hi / lo parts
+// (workspace "tc.ahi" / "tc.alo"); dense_tc_spmm computes Y = M X from them.
+int dense_tc_prepare(Workspace &ws, const float *T, int64_t ld, const float **hi, const float **lo,
+                     cudaStream_t st);
+int dense_tc_spmm(Workspace &ws, const float *Ahi, const float *Alo, int64_t ld, int64_t n, const float *X,
+                  int64_t ldx, int c, float *Y, int64_t ldy, cudaStream_t st);
 // Carry buffers of the merge SpMM for nnz nonzeros over n rows and c columns, under the
 // workspace names tag + ".c" / tag + ".r" (tag NULL = "spmm.carry").
 int merge_carry(Workspace &ws, const char *tag, int64_t nnz, int64_t n, int c, float4 **carry,

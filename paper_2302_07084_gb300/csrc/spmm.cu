@@ -488,165 +488,8 @@ int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, c
 
 }  // namespace
 
-// ---------------------------------------------------------------------------
-// Y = M X with M held as the dense upper triangle of the count table after
-// Eq. 1 (float bits, zero where no pair survived): M[i][k] = T[min][max].
-// When the sparsifier is dense enough (41% of all pairs on the benchmark),
-// a tiled product that streams the table once beats gathering a dense X row
-// per nonzero. It runs on the tensor cores: each FP32 value is split into two
-// TF32 parts, a = a_hi + a_lo (a_hi = a rounded to TF32, a_lo = the exact
-// remainder rounded to TF32), and a b ~ a_lo b_hi + a_hi b_lo + a_hi b_hi
-// (the dropped a_lo b_lo is ~2^-22 of a b), three m16n8k8 TF32 MMAs with FP32
-// accumulation: FP32 accuracy. CTA tile 128 rows x all columns (NT8 tiles of
-// 8) over one of `ks` slices of the k range, K steps of 16 double-buffered
-// through registers; the 8 warps form 4 x 2: warp (wm, wn) owns rows 32 wm ..
-// 32 wm + 31 (two m16 tiles, so each B fragment feeds two MMAs) and half of
-// the column tiles; X is split once per CTA into hi / lo shared copies.
-// Slices write partial products that a second kernel adds in slice order
-// (deterministic).
-// ---------------------------------------------------------------------------
-constexpr int kDmRows = 128;             // rows per CTA
-constexpr int kDmK = 16;
-constexpr int kMmaAPad = kDmRows + 8;   // row stride = 8 (mod 32): conflict-free fragment loads
-
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-                 "{%0,%1,%2,%3};\n"
-                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
-__host__ __device__ constexpr int mma_x_ld(int nt8) { return ((8 * nt8 + 31) / 32) * 32 + 8; }
-
-template <int NT8>
-__global__ void __launch_bounds__(256) dense_sym_mma_kernel(const float *__restrict__ T, int64_t ld, int64_t n,
-                                                            const float *__restrict__ X, int64_t ldx, int c,
-                                                            int64_t kslice, float *__restrict__ P) {
-    constexpr int NC = 8 * NT8;
-    constexpr int XLD = mma_x_ld(NT8);
-    __shared__ __align__(16) float As[2][kDmK][kMmaAPad];   // As[k][m] = M[r0 + m][k0 + k]
-    extern __shared__ uint32_t xsm[];                       // [2 buffers][hi, lo][kDmK][XLD]
-    constexpr int kAPer = kDmRows * kDmK / 256;
-    constexpr int kXPer = (kDmK * NC + 255) / 256;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int g = lane >> 2, t4 = lane & 3;
-    const int64_t r0 = (int64_t)blockIdx.x * kDmRows;
-    const int64_t kb = (int64_t)blockIdx.y * kslice, ke = imin64(n, kb + kslice);
-    float ra[kAPer], rx[kXPer];
-    auto fetch = [&](int64_t k0) {
-        const bool upper = r0 + kDmRows - 1 <= k0;
-#pragma unroll
-        for (int q = 0; q < kAPer; ++q) {
-            const int e = q * 256 + tid;
-            const int m = upper ? (e / kDmK) : (e % kDmRows);
-            const int k = upper ? (e % kDmK) : (e / kDmRows);
-            const int64_t r = r0 + m, kk = k0 + k;
-            ra[q] = (r < n && kk < ke) ? (r <= kk ? T[r * ld + kk] : T[kk * ld + r]) : 0.f;
-        }
-#pragma unroll
-        for (int q = 0; q < kXPer; ++q) {
-            const int e = q * 256 + tid;
-            const int k = e / NC, j = e - k * NC;
-            const int64_t kk = k0 + k;
-            rx[q] = (e < kDmK * NC && kk < ke && j < c) ? X[kk * ldx + j] : 0.f;
-        }
-    };
-    auto stash = [&](int buf, int64_t k0) {
-        const bool upper = r0 + kDmRows - 1 <= k0;
-#pragma unroll
-        for (int q = 0; q < kAPer; ++q) {
-            const int e = q * 256 + tid;
-            const int m = upper ? (e / kDmK) : (e % kDmRows);
-            const int k = upper ? (e % kDmK) : (e / kDmRows);
-            As[buf][k][m] = ra[q];
-        }
-        uint32_t *xh = xsm + (size_t)buf * 2 * kDmK * XLD, *xl = xh + kDmK * XLD;
-#pragma unroll
-        for (int q = 0; q < kXPer; ++q) {
-            const int e = q * 256 + tid;
-            if (e < kDmK * NC) {
-                const int k = e / NC, j = e - k * NC;
-                const uint32_t h = to_tf32(rx[q]);
-                xh[k * XLD + j] = h;
-                xl[k * XLD + j] = to_tf32(rx[q] - __uint_as_float(h));
-            }
-        }
-    };
-    constexpr int NTH = (NT8 + 1) / 2;
-    float acc[2][NTH][4];
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int j = 0; j < NTH; ++j)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[mt][j][v] = 0.f;
-    int buf = 0;
-    if (kb < ke) {
-        fetch(kb);
-        stash(0, kb);
-    }
-    __syncthreads();
-    const int m0 = (warp >> 1) * 32, j0 = (warp & 1) * NTH;
-    for (int64_t k0 = kb; k0 < ke; k0 += kDmK) {
-        const bool more = k0 + kDmK < ke;
-        if (more) fetch(k0 + kDmK);
-        const uint32_t *xh = xsm + (size_t)buf * 2 * kDmK * XLD, *xl = xh + kDmK * XLD;
-#pragma unroll
-        for (int kk = 0; kk < kDmK; kk += 8) {
-            // A fragments of the two m16 tiles (rows + g / + 8, columns kk + t4 / + 4)
-            uint32_t ah[2][4], al[2][4];
-#pragma unroll
-            for (int mt = 0; mt < 2; ++mt) {
-                const int mb = m0 + 16 * mt;
-                const float av[4] = {As[buf][kk + t4][mb + g], As[buf][kk + t4][mb + g + 8],
-                                     As[buf][kk + t4 + 4][mb + g], As[buf][kk + t4 + 4][mb + g + 8]};
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    ah[mt][v] = to_tf32(av[v]);
-                    al[mt][v] = to_tf32(av[v] - __uint_as_float(ah[mt][v]));
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < NTH; ++j) {
-                if (j0 + j >= NT8) break;
-                const int col = 8 * (j0 + j) + g;
-                const uint32_t bh0 = xh[(kk + t4) * XLD + col], bh1 = xh[(kk + t4 + 4) * XLD + col];
-                const uint32_t bl0 = xl[(kk + t4) * XLD + col], bl1 = xl[(kk + t4 + 4) * XLD + col];
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    mma_tf32(acc[mt][j], al[mt], bh0, bh1);
-                    mma_tf32(acc[mt][j], ah[mt], bl0, bl1);
-                    mma_tf32(acc[mt][j], ah[mt], bh0, bh1);
-                }
-            }
-        }
-        if (more) stash(buf ^ 1, k0 + kDmK);
-        __syncthreads();
-        buf ^= 1;
-    }
-    float *Pz = P + (int64_t)blockIdx.y * n * c;
-#pragma unroll
-    for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int j = 0; j < NTH; ++j) {
-            if (j0 + j >= NT8) break;
-            const int col = 8 * (j0 + j) + 2 * t4;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t r = r0 + m0 + 16 * mt + g + 8 * h;
-                if (r >= n) continue;
-                if (col < c) Pz[r * c + col] = acc[mt][j][2 * h];
-                if (col + 1 < c) Pz[r * c + col + 1] = acc[mt][j][2 * h + 1];
-            }
-        }
-}
-
+// Partial products of k-slices (P[z] = the slice's n x c block, z = 0..ks-1)
+// summed in slice order into Y: deterministic.
 __global__ void slice_sum_kernel(const float *__restrict__ P, int ks, int64_t n, int c, float *__restrict__ Y,
                                  int64_t ldy) {
     const int64_t total = n * c;
@@ -658,6 +501,14 @@ __global__ void slice_sum_kernel(const float *__restrict__ P, int ks, int64_t n,
     }
 }
 
+int slice_sum(const float *P, int ks, int64_t n, int c, float *Y, int64_t ldy, cudaStream_t st) {
+    LNE_TRACE("slice_sum", st);
+    slice_sum_kernel<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n * c, 256), num_sms() * 16)), 256, 0,
+                       st>>>(P, ks, n, c, Y, ldy);
+    LNE_LAUNCH_CHECK();
+    return 0;
+}
+
 int merge_carry(Workspace &ws, const char *tag, int64_t nnz, int64_t n, int c, float4 **carry,
                 int64_t **carry_row) {
     const int64_t nwarps = std::max<int64_t>(1, ceil_div(nnz, merge_slice(nnz, n)));
@@ -667,61 +518,6 @@ int merge_carry(Workspace &ws, const char *tag, int64_t nnz, int64_t n, int c, f
     return 0;
 }
 
-int dense_sym_spmm(Workspace &ws, const float *T, int64_t ld, int64_t n, const float *X, int64_t ldx, int c,
-                   float *Y, int64_t ldy, cudaStream_t st) {
-    if (n <= 0) return 0;
-    if (c < 1 || c > 160) return fail(LNE_ERR_UNSUPPORTED, "dense-table product supports 1..160 columns");
-    const int64_t rb = ceil_div(n, (int64_t)kDmRows);
-    const int tn = (c + 15) / 16;
-    // tensor-core variant: NT8 tiles of 8 columns (c rounded up to a listed width)
-    const int nt8 = c <= 32 ? 4 : c <= 64 ? 8 : c <= 96 ? 12 : c <= 128 ? 16 : c <= 144 ? 18 : 20;
-    const int msmem = 2 * 2 * kDmK * mma_x_ld(nt8) * (int)sizeof(uint32_t);
-    // split the k range into slices so that row blocks x slices fill whole
-    // waves of resident CTAs (the wide variants hold one CTA per SM)
-    const void *kern = nullptr;
-#define LNE_MMA_KERN(K) \
-    case K: kern = reinterpret_cast<const void *>(dense_sym_mma_kernel<K>); break;
-    switch (nt8) {
-        LNE_MMA_KERN(4) LNE_MMA_KERN(8) LNE_MMA_KERN(12) LNE_MMA_KERN(16) LNE_MMA_KERN(18) LNE_MMA_KERN(20)
-        default:
-            return fail(LNE_ERR_UNSUPPORTED, "dense-table product supports 1..160 columns");
-    }
-#undef LNE_MMA_KERN
-    (void)tn;
-    LNE_TRY(allow_dynamic_smem(kern));
-    int per_sm = 1;
-    LNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, msmem));
-    const int64_t slots = num_sms() * (int64_t)std::max(1, per_sm);
-    int ks = 1;
-    double best = 1e300;
-    for (int cand = 1; cand <= 16; ++cand) {   // time ~ waves x (one slice's work)
-        const double t = (double)ceil_div(rb * cand, slots) / cand;
-        if (t < best - 1e-12) {
-            best = t;
-            ks = cand;
-        }
-    }
-    const int64_t kslice = ceil_div(ceil_div(n, (int64_t)ks), (int64_t)kDmK) * kDmK;
-    float *P = nullptr;
-    LNE_TRY(ws.get("dense.partial", (size_t)ks * n * c, &P));
-    dim3 grid((unsigned)rb, (unsigned)ceil_div(n, kslice));
-    LNE_TRACE("dense_sym_mm", st);
-#define LNE_MMA_CASE(K)                                                                                    \
-    case K:                                                                                                \
-        dense_sym_mma_kernel<K><<<grid, 256, msmem, st>>>(T, ld, n, X, ldx, c, kslice, P);                 \
-        break;
-    switch (nt8) {
-        LNE_MMA_CASE(4) LNE_MMA_CASE(8) LNE_MMA_CASE(12) LNE_MMA_CASE(16) LNE_MMA_CASE(18) LNE_MMA_CASE(20)
-        default:
-            return fail(LNE_ERR_UNSUPPORTED, "dense-table product supports 1..160 columns");
-    }
-#undef LNE_MMA_CASE
-    LNE_LAUNCH_CHECK();
-    slice_sum_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n * c, 256), num_sms() * 16), 256, 0, st>>>(
-        P, (int)grid.y, n, c, Y, ldy);
-    LNE_LAUNCH_CHECK();
-    return 0;
-}
 
 int spmm(Workspace &ws, const CsrView &M, const float *X, int64_t ldx, int c, float *Y, int64_t ldy,
          cudaStream_t st) {

@@ -1,7 +1,9 @@
-"""The randomized SVD's products on the dense count table (LNE_OPT_DENSE_PRODUCT)
-against the same products on the CSR: the same FP32 values and FMAs summed in
-another order, so embeddings agree to FP32 rounding (1e-5 on the leading
-subspace), and both stay within the oracle's 1e-3 subspace bound."""
+"""The randomized SVD's products on the dense count table (LNE_OPT_DENSE_PRODUCT:
+the tcgen05 tensor-core product with TF32 hi / lo splitting) against the same
+products on the CSR: the same values and FP32-accurate sums in another order,
+so embeddings agree to FP32 rounding (1e-5 on the leading subspace), and both
+stay within the oracle's 1e-3 subspace bound; c from 40 (padded to the MMA's
+48 columns) to 144 (the benchmark's width)."""
 import numpy as np
 import pytest
 
@@ -21,7 +23,7 @@ def ctx():
     c.close()
 
 
-@pytest.mark.parametrize("d,q", [(32, 1), (24, 2)])
+@pytest.mark.parametrize("d,q", [(32, 1), (24, 2), (128, 1)])
 def test_dense_table_products_match_csr_products(ctx, d, q):
     g = synth.sbm_small()
     s = np.full(10, 0.1)
