@@ -545,6 +545,7 @@ int lne_cholqr2(lne_ctx *ctx, float *Y_dev, int64_t n, int32_t c, int64_t ld, do
     int rc = enter(ctx);
     if (rc == 0 && (!Y_dev || ld < c)) rc = lne::fail(LNE_ERR_INVALID, "bad CholeskyQR2 arguments");
     if (rc == 0) rc = lne::cholqr2(ctx->ws, Y_dev, n, c, ld, R_dev, as_stream(stream));
+    if (rc == 0) rc = lne::status_check(ctx->ws, as_stream(stream));
     return finish(ctx, rc);
 }
 

@@ -209,7 +209,7 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel(const double *__rest
         if (in_smem) R[e] = j >= i ? A[e] : 0.0;
         else if (j < i) R[e] = 0.0;
     }
-    if (tid == 0) *status = bad;
+    if (tid == 0 && bad && *status == 0) *status = bad;   // sticky: only a breakdown writes
 }
 
 // Blocked Cholesky over many SMs (FP64), for the matrix sizes where the
@@ -1206,13 +1206,15 @@ static int gram(Workspace &ws, const float *Y, int64_t n, int c, int64_t ld, dou
     return 0;
 }
 
+// A breakdown (a pivot that is not positive) is recorded in the device status
+// word read by status_check, without a host synchronisation here; the
+// factorisation goes on with a unit pivot, so later kernels see finite values.
 static int chol(Workspace &ws, const double *G, int c, double *R, cudaStream_t st) {
     int *status = nullptr;
-    LNE_TRY(ws.get("chol.status", 1, &status));
+    LNE_TRY(device_status(ws, &status, st));
     if (c >= 64) {   // blocked over many SMs
         double *r11 = nullptr;
         LNE_TRY(ws.get("chol.r11", (size_t)kCholB * kCholB, &r11));
-        LNE_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
         LNE_CUDA_TRY(cudaMemcpyAsync(R, G, sizeof(double) * (size_t)c * c, cudaMemcpyDeviceToDevice, st));
         LNE_TRACE("chol", st);
         for (int k0 = 0; k0 < c; k0 += kCholB) {
@@ -1233,11 +1235,27 @@ static int chol(Workspace &ws, const double *G, int c, double *R, cudaStream_t s
         chol_kernel<<<1, kCholThreads, smem, st>>>(G, c, R, status);
         LNE_LAUNCH_CHECK();
     }
-    int h = 0;
-    LNE_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LNE_CUDA_TRY(cudaStreamSynchronize(st));
-    if (h != 0) return fail(LNE_ERR_NUMERIC, "Cholesky breakdown in CholeskyQR (Gram not positive definite)");
     return 0;
+}
+
+int device_status(Workspace &ws, int **status, cudaStream_t st) {
+    const bool fresh = !ws.has("dev.status");
+    LNE_TRY(ws.get("dev.status", 2, status));
+    if (fresh) LNE_CUDA_TRY(cudaMemsetAsync(*status, 0, 2 * sizeof(int), st));
+    return 0;
+}
+
+int status_check(Workspace &ws, cudaStream_t st) {
+    if (!ws.has("dev.status")) return 0;
+    int *status = nullptr;
+    LNE_TRY(ws.get("dev.status", 2, &status));
+    int h[2] = {0, 0};
+    LNE_CUDA_TRY(cudaMemcpyAsync(h, status, sizeof(h), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h[0] == 0 && h[1] == 0) return 0;
+    LNE_CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(int), st));
+    if (h[1] != 0) return fail(LNE_ERR_TIMEOUT, "tensor-core dense product: a pipeline wait expired");
+    return fail(LNE_ERR_NUMERIC, "Cholesky breakdown in CholeskyQR (Gram not positive definite)");
 }
 
 static int trsm_rows(const float *Y, int64_t n, int c, int64_t ldy, const double *R, float *Q, int64_t ldq,

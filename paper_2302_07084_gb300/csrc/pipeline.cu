@@ -124,7 +124,7 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
     // final eigSVD of Y: U = Q(:, 1:d), Sigma(1:d)
     LNE_TRY(tall_svd(ws, Ya, n, c, d, Uo, so, st));
     LNE_TRY(sign_fix_embed(ws, Uo, n, d, d, so, X0, d, st));
-    return 0;
+    return status_check(ws, st);
 }
 
 int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, double mu, int precision,
@@ -271,7 +271,7 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
     LNE_CUDA_TRY(cudaMemcpyAsync(Qb, Pb, sizeof(float) * cnt, cudaMemcpyDeviceToDevice, st));
     LNE_TRY(tall_svd(ws, Qb, n, d, d, Ub, sig, st));
     LNE_TRY(sign_fix_embed(ws, Ub, n, d, d, sig, X, d, st));
-    return 0;
+    return status_check(ws, st);
 }
 
 }  // namespace lne

@@ -27,6 +27,8 @@ public:
         return get(name, count * sizeof(T), reinterpret_cast<void **>(ptr));
     }
     void release();
+    // Whether a buffer of that name exists.
+    bool has(const std::string &name) const { return bufs_.count(name) != 0; }
     // Frees one named buffer (no-op if absent).
     void release(const std::string &name);
     int64_t bytes() const;
@@ -169,6 +171,13 @@ struct SpmmEpilogue {
     int threads = 0;                    // CTA size of the merge kernel (0 = default)
     const char *carry_tag = nullptr;    // workspace name of the merge carry buffers (NULL = shared)
 };
+// Device status words of the context (workspace "dev.status", zeroed when
+// created): [0] the first Cholesky breakdown, [1] a tensor-core pipeline wait
+// that expired. Kernels only ever set them; status_check reads them once
+// (one host synchronisation), clears them and returns LNE_ERR_NUMERIC /
+// LNE_ERR_TIMEOUT if either was set.
+int device_status(Workspace &ws, int **status, cudaStream_t st);
+int status_check(Workspace &ws, cudaStream_t st);
 // Partial products of ks k-slices (P[z][n][c]) added in slice order into Y.
 int slice_sum(const float *P, int ks, int64_t n, int c, float *Y, int64_t ldy, cudaStream_t st);
 // The tensor-core (tcgen05) dense product: dense_tc_prepare splits the

@@ -25,7 +25,8 @@
 // tcgen05.commit; at the end all four warps read their 32 TMEM lanes
 // (tcgen05.ld) and write the slice's partial product, which slice_sum adds in
 // slice order (deterministic). Every mbarrier wait is bounded: on expiry the
-// kernel raises an error flag instead of hanging.
+// kernel sets the context's device status word (read by status_check) instead
+// of hanging.
 #include <cuda.h>
 
 #include "runtime.h"
@@ -376,23 +377,18 @@ int dense_tc_spmm(Workspace &ws, const float *Ahi, const float *Alo, int64_t ld,
     const int slice_chunks = (int)ceil_div(nchunks, ks);
     ks = (int)ceil_div(nchunks, slice_chunks);
     float *part = nullptr;
-    int *err = nullptr;
+    int *status = nullptr;
     LNE_TRY(ws.get("tc.part", (size_t)ks * n * c, &part));
-    LNE_TRY(ws.get("tc.err", 1, &err));
-    LNE_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+    LNE_TRY(device_status(ws, &status, st));
     {
         LNE_TRACE("dense_tc", st);
         dense_tc_kernel<<<dim3((unsigned)rb, (unsigned)ks), kTcThreads, smem, st>>>(m_ahi, m_alo, m_bhi, m_blo, n,
                                                                                   nchunks, slice_chunks, npad, c, part,
-                                                                                  err);
+                                                                                  status + 1);
         LNE_LAUNCH_CHECK();
     }
-    LNE_TRY(slice_sum(part, ks, n, c, Y, ldy, st));
-    int herr = 0;
-    LNE_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    LNE_CUDA_TRY(cudaStreamSynchronize(st));
-    if (herr) return fail(LNE_ERR_TIMEOUT, "tensor-core dense product: a pipeline wait expired");
-    return 0;
+    // a wait that expired is reported by the caller's status_check
+    return slice_sum(part, ks, n, c, Y, ldy, st);
 }
 
 }  // namespace lne

@@ -204,6 +204,7 @@ int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregati
             LNE_TRY(sign_fix_embed(ws, U, n, d, d, sig, X, d, st));
             LNE_TRY(score(prop[b0 + t], X));
         }
+        LNE_TRY(status_check(ws, st));
     }
     return 0;
 }
