@@ -125,6 +125,10 @@ typedef struct lne_ctx lne_ctx;
 #define LNE_AGG_SORT         3   /*   64-bit keys, radix sort and run lengths (any n < 2^31) */
 #define LNE_OPT_SPMM_THREADS 2   /* CTA size of the batched-tuning SpMM: 0 = picked by timing
                                     (default), or 64 / 128 / 256; results do not depend on it */
+#define LNE_OPT_SPMM_COLBLOCK 6  /* column-block width of the batched-tuning SpMM: 0 = picked by
+                                    timing together with the CTA size (default), -1 = all columns
+                                    in one pass, or a multiple of 4 up to 1024; results do not
+                                    depend on it */
 #define LNE_OPT_DENSE_PRODUCT 4  /* products of the randomized SVD (FP32) on the dense count table
                                     instead of the CSR, when the table aggregation ran: 0 = when at
                                     least 10% of all pairs are present (default), 1 = never,

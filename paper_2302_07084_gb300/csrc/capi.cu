@@ -328,6 +328,14 @@ int lne_set_option(lne_ctx *ctx, int option, int64_t value) {
         ctx->spmm_tune.forced = (int)value;
         return LNE_OK;
     }
+    if (option == LNE_OPT_SPMM_COLBLOCK) {
+        if (value != 0 && value != -1 && !(value > 0 && value <= 1024 && value % 4 == 0))
+            return finish(ctx, lne::fail(LNE_ERR_INVALID,
+                                         "SpMM column block must be 0 (timed), -1 (none) or a multiple of 4 up to 1024"));
+        ctx->spmm_tune.forced_block = (int)value;
+        ctx->spmm_tune.best.clear();
+        return LNE_OK;
+    }
     if (option == LNE_OPT_DENSE_PRODUCT) {
         if (value < 0 || value > 2) return finish(ctx, lne::fail(LNE_ERR_INVALID, "dense product mode must be 0..2"));
         ctx->dense_mode = (int)value;
@@ -695,7 +703,8 @@ int lne_tune_tasks(lne_ctx *ctx, const lne_task *tasks, int32_t ntasks, const ln
         if (e != cudaSuccess) rc = lne::cuda_fail("cudaStreamSynchronize", e, __FILE__, __LINE__);
     }
     if (rc == 0)
-        rc = lne::tune_tasks(ctx->workers, ctx->tune_workers, ctx->device, ctx->spmm_tune.forced, ctx->aggregation,
+        rc = lne::tune_tasks(ctx->workers, ctx->tune_workers, ctx->device, ctx->spmm_tune.forced,
+                             ctx->spmm_tune.forced_block, ctx->aggregation,
                              ctx->dense_mode, ctx->stratified, tt.data(), ntasks, cands, ncand, C, iters, macro_f1,
                              micro_f1);
     return finish(ctx, rc);

@@ -309,7 +309,7 @@ struct PropBatchGraph {
 
 static int prop_batch_chain(Workspace &ws, const GraphView &g, int C, int kmax, const float *X0, float *F, float *Z,
                             float *Tbuf[3], float *G, float *P, const float *om, const float *hom, const float *gam,
-                            int threads, cudaStream_t st) {
+                            SpmmTile tile, cudaStream_t st) {
     const int64_t cnt = g.n * C;
     {
         LNE_TRACE("scale_cols", st);
@@ -323,7 +323,8 @@ static int prop_batch_chain(Workspace &ws, const GraphView &g, int C, int kmax, 
         e1.E1 = X0;
         e1.b1_col = om;
         e1.lde = C;
-        e1.threads = threads;
+        e1.threads = tile.threads;
+        e1.col_block = tile.col_block;
         e1.carry_tag = "pb.carry";
         LNE_TRY(graph_spmm(ws, g, X0, C, C, Z, C, e1, st));
         SpmmEpilogue e2;
@@ -336,7 +337,8 @@ static int prop_batch_chain(Workspace &ws, const GraphView &g, int C, int kmax, 
         e2.lde = C;
         e2.F = F;
         e2.gamma_col = gam + C;
-        e2.threads = threads;
+        e2.threads = tile.threads;
+        e2.col_block = tile.col_block;
         e2.carry_tag = "pb.carry";
         LNE_TRY(graph_spmm(ws, g, Z, C, C, Tbuf[0], C, e2, st));
         const float *prev = X0;
@@ -354,7 +356,8 @@ static int prop_batch_chain(Workspace &ws, const GraphView &g, int C, int kmax, 
             ez.E1 = cur;
             ez.b1_col = om;
             ez.lde = C;
-            ez.threads = threads;
+            ez.threads = tile.threads;
+        ez.col_block = tile.col_block;
             ez.carry_tag = "pb.carry";
             LNE_TRY(graph_spmm(ws, g, cur, C, C, Z, C, ez, st));
             SpmmEpilogue e;
@@ -369,7 +372,8 @@ static int prop_batch_chain(Workspace &ws, const GraphView &g, int C, int kmax, 
             e.lde = C;
             e.F = F;
             e.gamma_col = gam + (int64_t)i * C;
-            e.threads = threads;
+            e.threads = tile.threads;
+        e.col_block = tile.col_block;
             e.carry_tag = "pb.carry";
             LNE_TRY(graph_spmm(ws, g, Z, C, C, nxt, C, e, st));
             prev = cur;
@@ -385,13 +389,15 @@ static int prop_batch_chain(Workspace &ws, const GraphView &g, int C, int kmax, 
     ep.alpha = 1.f;
     ep.dinv = true;
     ep.lde = C;
-    ep.threads = threads;
+    ep.threads = tile.threads;
+    ep.col_block = tile.col_block;
     ep.carry_tag = "pb.carry";
     return graph_spmm(ws, g, G, C, C, P, C, ep, st);
 }
 
 int propagate_batch(Workspace &ws, PropBatchGraph *cache, const GraphView &g, int d, int ncand, const int *k,
-                    const double *theta, const double *mu, const float *X0, float *P, int threads, cudaStream_t st) {
+                    const double *theta, const double *mu, const float *X0, float *P, SpmmTile tile,
+                    cudaStream_t st) {
     const int C = d * ncand;
     if (C % 4 != 0 || C > 1024) return fail(LNE_ERR_UNSUPPORTED, "batched propagation needs d * ncand <= 1024, % 4");
     int kmax = 1;
@@ -424,12 +430,13 @@ int propagate_batch(Workspace &ws, PropBatchGraph *cache, const GraphView &g, in
     int64_t *carry_row = nullptr;
     LNE_TRY(merge_carry(ws, "pb.carry", g.nnz, g.n, C, &carry, &carry_row));
     const float *om = coef, *hom = coef + C, *gam = coef + 2 * C;
-    if (!cache) return prop_batch_chain(ws, g, C, kmax, X0, F, Z, Tb, G, P, om, hom, gam, threads, st);
+    if (!cache) return prop_batch_chain(ws, g, C, kmax, X0, F, Z, Tb, G, P, om, hom, gam, tile, st);
     // graph key: everything the captured launches depend on
     std::vector<uintptr_t> key = {(uintptr_t)g.indptr, (uintptr_t)g.indices, (uintptr_t)g.n,  (uintptr_t)g.nnz,
                                   (uintptr_t)C,        (uintptr_t)kmax,      (uintptr_t)X0,   (uintptr_t)P,
                                   (uintptr_t)coef,     (uintptr_t)F,         (uintptr_t)Z,    (uintptr_t)G,
-                                  (uintptr_t)Tb[0],    (uintptr_t)Tb[1],     (uintptr_t)Tb[2], (uintptr_t)threads,
+                                  (uintptr_t)Tb[0],    (uintptr_t)Tb[1],     (uintptr_t)Tb[2], (uintptr_t)tile.threads,
+                                  (uintptr_t)tile.col_block,
                                   (uintptr_t)carry,    (uintptr_t)carry_row, (uintptr_t)g.wf, (uintptr_t)g.dinv};
     if (cache->valid && cache->key == key) {
         LNE_TRACE("propagate_batch_graph", st);
@@ -444,7 +451,7 @@ int propagate_batch(Workspace &ws, PropBatchGraph *cache, const GraphView &g, in
     }
     if (cache->seen == 0) {   // first run: eager (allocates every buffer the chain needs)
         cache->seen = 1;
-        return prop_batch_chain(ws, g, C, kmax, X0, F, Z, Tb, G, P, om, hom, gam, threads, st);
+        return prop_batch_chain(ws, g, C, kmax, X0, F, Z, Tb, G, P, om, hom, gam, tile, st);
     }
     // second run with the same key: capture, instantiate, launch
     if (cache->exec) {
@@ -459,7 +466,7 @@ int propagate_batch(Workspace &ws, PropBatchGraph *cache, const GraphView &g, in
     if (!cache->capture) LNE_CUDA_TRY(cudaStreamCreateWithFlags(&cache->capture, cudaStreamNonBlocking));
     const int64_t before = launches_now();
     LNE_CUDA_TRY(cudaStreamBeginCapture(cache->capture, cudaStreamCaptureModeThreadLocal));
-    int rc = prop_batch_chain(ws, g, C, kmax, X0, F, Z, Tb, G, P, om, hom, gam, threads, cache->capture);
+    int rc = prop_batch_chain(ws, g, C, kmax, X0, F, Z, Tb, G, P, om, hom, gam, tile, cache->capture);
     cudaError_t e = cudaStreamEndCapture(cache->capture, &graph);
     set_tracer(tracer);
     cache->kernels = launches_now() - before;

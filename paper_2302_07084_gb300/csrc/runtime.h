@@ -169,6 +169,7 @@ struct SpmmEpilogue {
     const float *b1_col = nullptr;
     const float *gamma_col = nullptr;
     int threads = 0;                    // CTA size of the merge kernel (0 = default)
+    int col_block = 0;                  // merge products of more columns run in blocks of this many (0 = one)
     const char *carry_tag = nullptr;    // workspace name of the merge carry buffers (NULL = shared)
 };
 // Device status words of the context (workspace "dev.status", zeroed when
@@ -228,18 +229,29 @@ int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, dou
 struct PropBatchGraph;
 PropBatchGraph *new_prop_cache();
 void destroy_prop_cache(PropBatchGraph *c);
+// Tile shape of the batched merge SpMM: CTA size (0 = 256) and column-block
+// width (0 = all columns at once). Neither changes any column's arithmetic.
+struct SpmmTile {
+    int threads = 0;
+    int col_block = 0;
+};
 int propagate_batch(Workspace &ws, PropBatchGraph *cache, const GraphView &g, int d, int ncand, const int *k,
-                    const double *theta, const double *mu, const float *X0, float *P, int threads, cudaStream_t st);
+                    const double *theta, const double *mu, const float *X0, float *P, SpmmTile tile,
+                    cudaStream_t st);
 std::vector<double> chebyshev_coefficients(int k, double theta);
 
-// CTA size of the merge SpMM, picked by timing per (row-length bucket, nnz
-// bucket, width bucket) unless forced; results do not depend on it.
+// The batched merge SpMM's tile shape, picked by timing every candidate
+// (CTA size 64 / 128 / 256 x column blocks of 128 / 256 / 512 / all columns)
+// once per (row-length bucket, nnz bucket, width) and cached; `forced` fixes
+// the CTA size. Results do not depend on the choice.
 struct SpmmTune {
-    int forced = 0;
-    std::map<uint64_t, int> best;
+    int forced = 0;         // CTA size (0 = tuned)
+    int forced_block = 0;   // column-block width (0 = tuned, -1 = all columns at once)
+    std::map<uint64_t, SpmmTile> best;
 };
-int spmm_threads_for(SpmmTune &tc, Workspace &ws, const GraphView &g, const float *X, int C, float *Y,
-                     cudaStream_t st);
+// Returns 0 and sets *tile, or an error code.
+int spmm_tile_for(SpmmTune &tc, Workspace &ws, const GraphView &g, const float *X, int C, float *Y, SpmmTile *tile,
+                  cudaStream_t st);
 // Batched tuning over ncand candidate parameter sets (tune.cu).
 // stratified: the candidates' sparsifiers come from window-stratified counts,
 // sampled once per (T, S, seed) and shared.
@@ -267,6 +279,7 @@ struct TuneTask {
     int64_t n_test = 0;
 };
 int tune_tasks(std::vector<std::unique_ptr<TuneWorker>> &workers, int nworkers, int device, int forced_threads,
+               int forced_block,
                int aggregation, int dense_mode, int stratified, const TuneTask *tasks, int ntasks,
                const lne_params *cands, int ncand, double Creg, int iters, double *macro, double *micro);
 

@@ -440,6 +440,29 @@ int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, c
                  const float *vals, const TX *X, int64_t ldx, int c, float *Y, int64_t ldy, const SpmmEpilogue &ep,
                  cudaStream_t st) {
     if (n <= 0) return 0;
+    if (ep.col_block > 0 && ep.col_block < c && ep.col_block % 4 == 0) {
+        // column blocks, one after another on the stream (they share the
+        // carry buffers); every column gets the same terms in the same order
+        for (int cb = 0; cb < c; cb += ep.col_block) {
+            const int w = std::min(ep.col_block, c - cb);
+            SpmmEpilogue eb = ep;
+            eb.col_block = 0;
+            auto shift = [cb](auto *p) { return p ? p + cb : p; };
+            eb.E1 = shift(ep.E1);
+            eb.E2 = shift(ep.E2);
+            eb.E3 = shift(ep.E3);
+            eb.F = shift(ep.F);
+            eb.X0 = shift(ep.X0);
+            eb.G = shift(ep.G);
+            eb.Gb = shift(ep.Gb);
+            eb.b1_col = shift(ep.b1_col);
+            eb.gamma_col = shift(ep.gamma_col);
+            eb.Yb = shift(ep.Yb);
+            LNE_TRY((launch_merge<WEIGHTED, TX>(ws, n, nnz, indptr, indices, vals, X + cb, ldx, w, Y + cb, ldy, eb,
+                                                st)));
+        }
+        return 0;
+    }
     const int c4 = c / 4;
     const int nv = merge_vectors(c);
     const int64_t W = merge_slice(nnz, n);

@@ -47,30 +47,47 @@ bool same_rsvd_inputs(const lne_params &a, const lne_params &b, int osa, int osb
 
 }  // namespace
 
-int spmm_threads_for(SpmmTune &tc, Workspace &ws, const GraphView &g, const float *X, int C, float *Y,
-                     cudaStream_t st) {
-    if (tc.forced > 0) return tc.forced;
+int spmm_tile_for(SpmmTune &tc, Workspace &ws, const GraphView &g, const float *X, int C, float *Y, SpmmTile *tile,
+                  cudaStream_t st) {
     const int64_t avg = g.n > 0 ? std::max<int64_t>(1, g.nnz / g.n) : 1;
     int dbucket = 0;
     while ((int64_t(1) << (dbucket + 1)) <= avg) ++dbucket;
     int nbucket = 0;
     while ((int64_t(1) << (nbucket + 1)) <= std::max<int64_t>(1, g.nnz)) ++nbucket;
-    const uint64_t key = (uint64_t)dbucket | ((uint64_t)nbucket << 8) | ((uint64_t)((C / 4 + 31) / 32) << 16);
+    const uint64_t key = (uint64_t)dbucket | ((uint64_t)nbucket << 8) | ((uint64_t)C << 16) |
+                         ((uint64_t)tc.forced << 32) | ((uint64_t)(tc.forced_block + 1) << 44);
     auto it = tc.best.find(key);
-    if (it != tc.best.end()) return it->second;
+    if (it != tc.best.end()) {
+        *tile = it->second;
+        return 0;
+    }
+    // candidates: CTA sizes x column-block widths (0 = all columns at once)
+    std::vector<int> ts, bs;
+    if (tc.forced > 0) ts = {tc.forced};
+    else ts = {64, 128, 256};
+    if (tc.forced_block < 0) bs = {0};
+    else if (tc.forced_block > 0) bs = {tc.forced_block < C ? tc.forced_block : 0};
+    else {
+        bs = {0};
+        for (int b : {512, 256, 128})
+            if (b < C) bs.push_back(b);
+    }
+    std::vector<SpmmTile> cands;
+    for (int t : ts)
+        for (int b : bs) cands.push_back(SpmmTile{t, b});
     cudaEvent_t e0, e1;
     LNE_CUDA_TRY(cudaEventCreate(&e0));
     LNE_CUDA_TRY(cudaEventCreate(&e1));
-    const int cand[3] = {64, 128, 256};
-    int best = 256;
+    SpmmTile best = cands.front();
     float best_ms = 1e30f;
     int rc = 0;
-    for (int t : cand) {
+    for (const SpmmTile &cand : cands) {
         SpmmEpilogue ep;
         ep.alpha = 1.f;
         ep.dinv = true;
         ep.lde = C;
-        ep.threads = t;
+        ep.threads = cand.threads;
+        ep.col_block = cand.col_block;
         if ((rc = graph_spmm(ws, g, X, C, C, Y, C, ep, st)) != 0) break;   // warm-up
         cudaEventRecord(e0, st);
         for (int r = 0; r < 3 && rc == 0; ++r) rc = graph_spmm(ws, g, X, C, C, Y, C, ep, st);
@@ -85,14 +102,15 @@ int spmm_threads_for(SpmmTune &tc, Workspace &ws, const GraphView &g, const floa
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best_ms) {
             best_ms = ms;
-            best = t;
+            best = cand;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc != 0) return -1;
+    if (rc != 0) return rc;
     tc.best[key] = best;
-    return best;
+    *tile = best;
+    return 0;
 }
 
 int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregation, int dense_mode, int stratified,
@@ -192,9 +210,9 @@ int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregati
                                            X0s + (size_t)group[prop[b0 + t]] * n * d, sizeof(float) * d,
                                            sizeof(float) * d, n, cudaMemcpyDeviceToDevice, st));
         }
-        const int threads = spmm_threads_for(tc, ws, g, X0r, C, P, st);
-        if (threads < 0) return -1;
-        LNE_TRY(propagate_batch(ws, cache, g, d, m, ks.data(), th.data(), mu.data(), X0r, P, threads, st));
+        SpmmTile tile;
+        LNE_TRY(spmm_tile_for(tc, ws, g, X0r, C, P, &tile, st));
+        LNE_TRY(propagate_batch(ws, cache, g, d, m, ks.data(), th.data(), mu.data(), X0r, P, tile, st));
         // per candidate: X = U_P Sigma_P^{1/2} from the economic SVD of its block of P
         for (int t = 0; t < m; ++t) {
             float *Pj = P + (size_t)t * d;
@@ -223,7 +241,7 @@ TuneWorker::~TuneWorker() {
 }
 
 int tune_tasks(std::vector<std::unique_ptr<TuneWorker>> &workers, int nworkers, int device, int forced_threads,
-               int aggregation, int dense_mode, int stratified, const TuneTask *tasks, int ntasks,
+               int forced_block, int aggregation, int dense_mode, int stratified, const TuneTask *tasks, int ntasks,
                const lne_params *cands, int ncand, double Creg, int iters, double *macro, double *micro) {
     nworkers = std::max(1, std::min(nworkers, ntasks));
     while ((int)workers.size() < nworkers) {
@@ -241,7 +259,9 @@ int tune_tasks(std::vector<std::unique_ptr<TuneWorker>> &workers, int nworkers, 
         set_tracer(nullptr);
         cudaError_t e = cudaSetDevice(device);
         int rc = e == cudaSuccess ? 0 : cuda_fail("cudaSetDevice", e, __FILE__, __LINE__);
+        if (w->tune.forced != forced_threads || w->tune.forced_block != forced_block) w->tune.best.clear();
         w->tune.forced = forced_threads;
+        w->tune.forced_block = forced_block;
         for (int t; rc == 0 && !stop.load() && (t = next.fetch_add(1)) < ntasks;) {
             const TuneTask &k = tasks[t];
             GraphView gk = k.g;

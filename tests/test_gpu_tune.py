@@ -109,6 +109,24 @@ def test_cta_size_does_not_change_results(ctx, case):
         assert np.array_equal(o[0], outs[0][0])
 
 
+def test_column_block_does_not_change_results(ctx, case):
+    """The autotuner's column-block widths (and no blocking) give bit-identical
+    batched results: every column gets the same terms in the same order."""
+    g, dev = case
+    spec = [(3 + j, 0.5 + 0.1 * j, 0.1 * j, 3) for j in range(4)]   # 4 x d = 128: 512 columns
+    cands = _cands(g, 128, spec)
+    outs = []
+    for b in (-1, 128, 256, 0):
+        ctx.set_option(lne.OPT_SPMM_COLBLOCK, b)
+        outs.append(ctx.tune_batch(dev["g"], cands, dev["labels"], dev["tr"], dev["te"], want_embeddings=True))
+    ctx.set_option(lne.OPT_SPMM_COLBLOCK, 0)
+    for o in outs[1:]:
+        assert torch.equal(o[2], outs[0][2])
+        assert np.array_equal(o[0], outs[0][0])
+    with pytest.raises(lne.LneError):
+        ctx.set_option(lne.OPT_SPMM_COLBLOCK, 130)
+
+
 def test_several_column_blocks(ctx, case):
     g, dev = case
     # d = 128: 8 candidates per block, so 9 propagating candidates need two blocks
