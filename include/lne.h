@@ -57,6 +57,8 @@ extern "C" {
 /* Test matrix Omega of the randomized SVD (Algorithm 4). */
 #define LNE_SKETCH_GAUSSIAN     0   /* randn(n, c), the paper's default */
 #define LNE_SKETCH_SPARSE_SIGN  1   /* zeta nonzeros +-1 per row (Sec. 3.2's sparse sign alternative) */
+#define LNE_SKETCH_VERY_SPARSE  2   /* entries +-1 with probability 1/(2s) each (Sec. 4.2's very
+                                       sparse random projection); s = sketch_zeta, 0 = sqrt(n) */
 
 typedef struct {
     int64_t n;                 /* vertices */
@@ -90,8 +92,9 @@ typedef struct {
                                   u -> v with probability p_e = min(1, C (1/d_u + 1/d_v)) and
                                   weighs it 1/p_e; finite, >= 0 */
     int32_t sketch;            /* LNE_SKETCH_* */
-    int32_t sketch_zeta;       /* nonzeros per row of the sparse sign sketch, 1..min(12, c);
-                                  0 = min(8, c) */
+    int32_t sketch_zeta;       /* LNE_SKETCH_SPARSE_SIGN: nonzeros per row, 1..min(12, c),
+                                  0 = min(8, c); LNE_SKETCH_VERY_SPARSE: the sparsity s >= 1,
+                                  0 = sqrt(n) */
 } lne_params;
 
 typedef struct {
@@ -223,6 +226,29 @@ int lne_sparse_sign_sketch(lne_ctx *ctx, int64_t n, int32_t c, int32_t zeta, uin
  * Needs |row sums of M| < 2^31. Y_dev is [n][ldy], ldy >= c, row-major.
  */
 int lne_sparse_sign_spmm(lne_ctx *ctx, const lne_csr *M, int32_t c, int32_t zeta, uint64_t seed, float *Y_dev,
+                         int64_t ldy, void *stream);
+
+/*
+ * Very sparse random projection (Sec. 4.2 names it beside the sparse sign
+ * matrix as a cheaper Omega for Algorithm 4; construction of Li, Hastie and
+ * Church, KDD 2006, at scale 1): out_dev ([n][ld], ld >= c, float) gets entry
+ * (i, j) = +1 if word j mod 4 of Philox4x32-10 counter (i, j / 4, 0,
+ * 0x56535250) under key (seed_lo ^ 0x4f4d4547, seed_hi) is below
+ * thr = floor(2^32 / (2 s)), -1 if it is in [thr, 2 thr), else 0. s >= 1
+ * (s <= 0 means sqrt(n), the "very sparse" choice); c <= 255. A row with more
+ * than 12 nonzeros is refused with LNE_ERR_UNSUPPORTED (raise s);
+ * LNE_ERR_INVALID for other bad arguments. Synchronises the stream.
+ */
+int lne_very_sparse_sketch(lne_ctx *ctx, int64_t n, int32_t c, double s, uint64_t seed, float *out_dev, int64_t ld,
+                           void *stream);
+
+/*
+ * Y_dev = M Omega for the very sparse Omega of lne_very_sparse_sketch (never
+ * formed), exact in 64-bit fixed point as lne_sparse_sign_spmm, then rounded
+ * once to float. Y_dev is [n][ldy], ldy >= c, row-major. Synchronises the
+ * stream (the row-count check).
+ */
+int lne_very_sparse_spmm(lne_ctx *ctx, const lne_csr *M, int32_t c, double s, uint64_t seed, float *Y_dev,
                          int64_t ldy, void *stream);
 
 /* Y = M X for CSR M (n x n) and X [n][ldx] (c columns), Y [n][ldy] FP32,

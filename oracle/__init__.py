@@ -20,6 +20,9 @@ FP64, each function citing the passage it follows:
 * ``sparse_sign_sketch``: the sparse sign test matrix that Sec. 3.2 names as
   an alternative to the Gaussian one (Tropp et al., SISC 2019): zeta
   nonzeros +-1 per row at distinct columns (Floyd's subset sampling);
+* ``very_sparse_sketch``: the very sparse random projection named beside it
+  (Li, Hastie and Church, KDD 2006): entries +-1 with probability 1/(2s)
+  each, 0 otherwise;
 * ``eig_svd``: Algorithm 2 (eigSVD);
 * ``fast_randomized_svd``: Algorithm 4;
 * ``embedding_from_svd``: X = U Sigma^{1/2} (Sec. 3.2);
@@ -89,6 +92,7 @@ def lib():
         L.oracle_count_samples_w.restype = ctypes.c_int64
         L.oracle_arc_rate_w.argtypes = [ctypes.c_double, ctypes.c_uint32, ctypes.c_double, u64p, u64p]
         L.oracle_sparse_sign_words.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, u32p]
+        L.oracle_very_sparse_words.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64, u32p]
         L.oracle_num_threads.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -511,6 +515,35 @@ def sparse_sign_sketch(n: int, c: int, zeta: int, seed: int) -> np.ndarray:
     return Om
 
 
+def very_sparse_threshold(n: int, s: float = 0.0) -> int:
+    """thr = floor(2^32 / (2 s)) in FP64 for the very sparse projection, s the
+    sparsity (s = sqrt(n) when s <= 0, the "very sparse" choice of Li, Hastie
+    and Church, KDD 2006); each entry is +1 with probability thr / 2^32 and -1
+    with the same probability. Needs s >= 1."""
+    s = float(s) if s > 0 else float(np.sqrt(float(n)))
+    if s < 1.0:
+        raise ValueError("very sparse projection needs s >= 1")
+    return int(np.floor(4294967296.0 / (2.0 * s)))
+
+
+def very_sparse_sketch(n: int, c: int, s: float, seed: int) -> np.ndarray:
+    """Very sparse random projection Omega (n x c), Sec. 4.2's other
+    alternative to the Gaussian Omega of Algorithm 4 (Li, Hastie and Church,
+    KDD 2006): every entry is independently +1, 0 or -1 with probabilities
+    1/(2s), 1 - 1/s, 1/(2s) (scale 1: the range of M Omega does not depend on
+    the scale sqrt(s) of the original construction).
+
+    Entry (i, j) reads word j mod 4 of counter (i, j // 4, 0, 0x56535250), key
+    (seed_lo ^ 0x4f4d4547, seed_hi): +1 if word < thr, -1 if thr <= word <
+    2 thr, else 0, with thr = ``very_sparse_threshold(n, s)``."""
+    thr = very_sparse_threshold(n, s)
+    nblk = (c + 3) // 4
+    words = np.zeros((n, nblk, 4), dtype=np.uint32)
+    lib().oracle_very_sparse_words(n, nblk, int(seed), _ptr(words, ctypes.c_uint32))
+    w = words.reshape(n, nblk * 4)[:, :c].astype(np.int64)
+    return np.where(w < thr, 1.0, np.where(w < 2 * thr, -1.0, 0.0))
+
+
 def fix_signs(U: np.ndarray, *others: np.ndarray):
     """Make the largest-magnitude entry of every column of U positive (first
     index on ties) and flip the matching columns of ``others``."""
@@ -546,11 +579,13 @@ def spmm(indptr, indices, data, X):
 
 
 def fast_randomized_svd(indptr, indices, data, d: int, q: int, oversample: int, seed: int,
-                        Omega: np.ndarray | None = None, sketch: str = "gaussian", zeta: int = 8):
+                        Omega: np.ndarray | None = None, sketch: str = "gaussian", zeta: int = 8,
+                        sparsity: float = 0.0):
     """Algorithm 4 (Fast Randomized SVD) on the symmetric sparse M.
 
     Omega = randn(n, d+s) (or, with sketch="sparse_sign", the sparse sign
-    matrix with zeta nonzeros per row); Y = M Omega; Q = eigSVD(Y).U; q times:
+    matrix with zeta nonzeros per row; with sketch="very_sparse", the very
+    sparse projection of sparsity ``sparsity``, 0 = sqrt(n)); Y = M Omega; Q = eigSVD(Y).U; q times:
     Y = M Q, T = Q, [Q, Sigma, V] = eigSVD(Y); return U = Q(:, 1:d),
     Sigma(1:d), V = T V(:, 1:d). With q = 0 the eigSVD of M Omega supplies
     Sigma and V.
@@ -558,8 +593,12 @@ def fast_randomized_svd(indptr, indices, data, d: int, q: int, oversample: int, 
     n = len(indptr) - 1
     c = d + oversample
     if Omega is None:
-        Omega = (sparse_sign_sketch(n, c, zeta, seed) if sketch == "sparse_sign"
-                 else gaussian_sketch(n, c, seed))
+        if sketch == "sparse_sign":
+            Omega = sparse_sign_sketch(n, c, zeta, seed)
+        elif sketch == "very_sparse":
+            Omega = very_sparse_sketch(n, c, sparsity, seed)
+        else:
+            Omega = gaussian_sketch(n, c, seed)
     Y = spmm(indptr, indices, data, Omega)
     Q, Sig, V = eig_svd(Y)
     T = Omega
@@ -637,13 +676,13 @@ def spectral_propagation(indptr, indices, X0: np.ndarray, k: int, theta: float, 
 # ----------------------------------------------------------------------------
 
 def embed(indptr, indices, T, s, S, d, q, k, theta, mu, seed, oversample=16, b=1.0, C=0.0,
-          sketch="gaussian", zeta=8, weights=None):
+          sketch="gaussian", zeta=8, weights=None, sparsity=0.0):
     """Sparsifier (edge-downsampled when C > 0, Sec. 4.1) -> randomized SVD
     (Gaussian or sparse sign test matrix, Sec. 3.2) -> X0 -> spectral
     propagation -> X."""
     sparse = sparsifier(indptr, indices, T, s, S, seed, b, C, weights=weights)
     rs = fast_randomized_svd(sparse["indptr"], sparse["indices"], sparse["data"], d, q,
-                             oversample, seed, sketch=sketch, zeta=zeta)
+                             oversample, seed, sketch=sketch, zeta=zeta, sparsity=sparsity)
     X0 = embedding_from_svd(rs["U"], rs["sigma"])
     prop = spectral_propagation(indptr, indices, X0, k, theta, mu, weights=weights)
     return dict(sparse=sparse, rsvd=rs, X0=X0, prop=prop, X=prop["X"])

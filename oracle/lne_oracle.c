@@ -326,6 +326,21 @@ void oracle_sparse_sign_words(int64_t n, int64_t nblk, uint64_t seed, uint32_t *
     }
 }
 
+/* Raw Philox words of the very sparse projection: row i, block b uses counter
+ * (i, b, 0, 0x56535250) and the Gaussian sketch's key. Writes
+ * words[(i * nblk + b) * 4 + t]. */
+void oracle_very_sparse_words(int64_t n, int64_t nblk, uint64_t seed, uint32_t *words)
+{
+    uint32_t key[2] = {seed_lo(seed) ^ 0x4f4d4547u, seed_hi(seed)};
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+        for (int64_t b = 0; b < nblk; ++b) {
+            uint32_t ctr[4] = {(uint32_t)i, (uint32_t)b, 0u, 0x56535250u};
+            oracle_philox4x32_10(ctr, key, &words[(i * nblk + b) * 4]);
+        }
+    }
+}
+
 int oracle_num_threads(void)
 {
 #ifdef _OPENMP

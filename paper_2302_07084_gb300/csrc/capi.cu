@@ -240,10 +240,12 @@ int check_params(const lne_params *p, bool sampling) {
         return lne::fail(LNE_ERR_INVALID, "unknown precision");
     if (!(p->downsample_C >= 0.0) || !std::isfinite(p->downsample_C))
         return lne::fail(LNE_ERR_INVALID, "downsample_C must be a finite value >= 0");
-    if (p->sketch != LNE_SKETCH_GAUSSIAN && p->sketch != LNE_SKETCH_SPARSE_SIGN)
+    if (p->sketch != LNE_SKETCH_GAUSSIAN && p->sketch != LNE_SKETCH_SPARSE_SIGN && p->sketch != LNE_SKETCH_VERY_SPARSE)
         return lne::fail(LNE_ERR_INVALID, "unknown sketch");
-    if (p->sketch_zeta < 0 || p->sketch_zeta > lne::kMaxSketchZeta)
+    if (p->sketch == LNE_SKETCH_SPARSE_SIGN && (p->sketch_zeta < 0 || p->sketch_zeta > lne::kMaxSketchZeta))
         return lne::fail(LNE_ERR_INVALID, "sketch_zeta must be in 0..12");
+    if (p->sketch == LNE_SKETCH_VERY_SPARSE && p->sketch_zeta < 0)
+        return lne::fail(LNE_ERR_INVALID, "the very sparse projection's s (sketch_zeta) must be >= 0");
     return 0;
 }
 
@@ -252,7 +254,8 @@ int oversample_of(const lne_params *p) { return p->oversample < 0 ? 16 : p->over
 lne::SketchSpec sketch_of(const lne_params *p) {
     lne::SketchSpec s;
     s.kind = p->sketch;
-    s.zeta = p->sketch_zeta;
+    s.zeta = p->sketch == LNE_SKETCH_SPARSE_SIGN ? p->sketch_zeta : 0;
+    s.sparsity = p->sketch == LNE_SKETCH_VERY_SPARSE ? (double)p->sketch_zeta : 0.0;
     return s;
 }
 
@@ -511,6 +514,26 @@ int lne_sparse_sign_sketch(lne_ctx *ctx, int64_t n, int32_t c, int32_t zeta, uin
     int rc = enter(ctx);
     if (rc == 0 && (n < 0 || (n > 0 && !out_dev))) rc = lne::fail(LNE_ERR_INVALID, "bad sketch arguments");
     if (rc == 0) rc = lne::sparse_sign_dense(ctx->ws, n, c, zeta, seed, out_dev, ld, as_stream(stream));
+    return finish(ctx, rc);
+}
+
+int lne_very_sparse_sketch(lne_ctx *ctx, int64_t n, int32_t c, double s, uint64_t seed, float *out_dev, int64_t ld,
+                           void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (n < 0 || (n > 0 && !out_dev))) rc = lne::fail(LNE_ERR_INVALID, "bad sketch arguments");
+    if (rc == 0) rc = lne::very_sparse_dense(ctx->ws, n, c, s, seed, out_dev, ld, as_stream(stream));
+    return finish(ctx, rc);
+}
+
+int lne_very_sparse_spmm(lne_ctx *ctx, const lne_csr *M, int32_t c, double s, uint64_t seed, float *Y_dev,
+                         int64_t ldy, void *stream) {
+    if (!ctx) return LNE_ERR_INVALID;
+    int rc = enter(ctx);
+    if (rc == 0 && (!M || M->n < 0 || !M->indptr || (M->n > 0 && !Y_dev)))
+        rc = lne::fail(LNE_ERR_INVALID, "bad very sparse product arguments");
+    if (rc == 0) rc = lne::very_sparse_spmm(ctx->ws, csr_view(M), c, s, seed, Y_dev, ldy, as_stream(stream));
+    if (rc == 0) rc = lne::status_check(ctx->ws, as_stream(stream));
     return finish(ctx, rc);
 }
 

@@ -1240,21 +1240,23 @@ static int chol(Workspace &ws, const double *G, int c, double *R, cudaStream_t s
 
 int device_status(Workspace &ws, int **status, cudaStream_t st) {
     const bool fresh = !ws.has("dev.status");
-    LNE_TRY(ws.get("dev.status", 2, status));
-    if (fresh) LNE_CUDA_TRY(cudaMemsetAsync(*status, 0, 2 * sizeof(int), st));
+    LNE_TRY(ws.get("dev.status", 4, status));
+    if (fresh) LNE_CUDA_TRY(cudaMemsetAsync(*status, 0, 4 * sizeof(int), st));
     return 0;
 }
 
 int status_check(Workspace &ws, cudaStream_t st) {
     if (!ws.has("dev.status")) return 0;
     int *status = nullptr;
-    LNE_TRY(ws.get("dev.status", 2, &status));
-    int h[2] = {0, 0};
+    LNE_TRY(ws.get("dev.status", 4, &status));
+    int h[4] = {0, 0, 0, 0};
     LNE_CUDA_TRY(cudaMemcpyAsync(h, status, sizeof(h), cudaMemcpyDeviceToHost, st));
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
-    if (h[0] == 0 && h[1] == 0) return 0;
-    LNE_CUDA_TRY(cudaMemsetAsync(status, 0, 2 * sizeof(int), st));
+    if (h[0] == 0 && h[1] == 0 && h[2] == 0) return 0;
+    LNE_CUDA_TRY(cudaMemsetAsync(status, 0, 4 * sizeof(int), st));
     if (h[1] != 0) return fail(LNE_ERR_TIMEOUT, "tensor-core dense product: a pipeline wait expired");
+    if (h[2] != 0)
+        return fail(LNE_ERR_UNSUPPORTED, "a row of the very sparse projection has more than 12 nonzeros (raise s)");
     return fail(LNE_ERR_NUMERIC, "Cholesky breakdown in CholeskyQR (Gram not positive definite)");
 }
 

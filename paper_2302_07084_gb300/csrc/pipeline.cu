@@ -87,7 +87,7 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
     // FP32 products: the dense table on the tensor cores when the caller
     // supplied it (its TF32 hi / lo parts prepared once for all products)
     const float *a_hi = nullptr, *a_lo = nullptr;
-    const bool dense_tc = M.dense && !bf16 && (sketch.kind != LNE_SKETCH_SPARSE_SIGN || q > 0);
+    const bool dense_tc = M.dense && !bf16 && (sketch.kind == LNE_SKETCH_GAUSSIAN || q > 0);
     if (dense_tc) LNE_TRY(dense_tc_prepare(ws, M.dense, M.dense_ld, &a_hi, &a_lo, st));
     auto mprod = [&](const float *X, float *Y) -> int {
         if (dense_tc) return dense_tc_spmm(ws, a_hi, a_lo, M.dense_ld, n, X, c, c, Y, c, st);
@@ -99,6 +99,8 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
     if (sketch.kind == LNE_SKETCH_SPARSE_SIGN) {
         const int zeta = sketch.zeta > 0 ? sketch.zeta : std::min(8, c);
         LNE_TRY(sparse_sign_spmm(ws, M, c, zeta, seed, Ya, c, st));
+    } else if (sketch.kind == LNE_SKETCH_VERY_SPARSE) {
+        LNE_TRY(very_sparse_spmm(ws, M, c, sketch.sparsity, seed, Ya, c, st));
     } else {
         LNE_TRY(ws.get("rsvd.omega", (size_t)n * c, &Om));
         LNE_TRY(gaussian_sketch(n, c, seed, Om, c, st));

@@ -174,9 +174,10 @@ struct SpmmEpilogue {
 };
 // Device status words of the context (workspace "dev.status", zeroed when
 // created): [0] the first Cholesky breakdown, [1] a tensor-core pipeline wait
-// that expired. Kernels only ever set them; status_check reads them once
-// (one host synchronisation), clears them and returns LNE_ERR_NUMERIC /
-// LNE_ERR_TIMEOUT if either was set.
+// that expired, [2] a very sparse projection row with more than 12 nonzeros.
+// Kernels only ever set them; status_check reads them once (one host
+// synchronisation), clears them and returns LNE_ERR_TIMEOUT /
+// LNE_ERR_UNSUPPORTED / LNE_ERR_NUMERIC if one was set.
 int device_status(Workspace &ws, int **status, cudaStream_t st);
 int status_check(Workspace &ws, cudaStream_t st);
 // Partial products of ks k-slices (P[z][n][c]) added in slice order into Y.
@@ -207,8 +208,19 @@ int to_bf16(const float *in, __nv_bfloat16 *out, int64_t count, cudaStream_t st)
 constexpr int kMaxSketchZeta = 12;
 struct SketchSpec {
     int kind = LNE_SKETCH_GAUSSIAN;
-    int zeta = 0;   // nonzeros per row of the sparse sign sketch; 0 = min(8, c)
+    int zeta = 0;             // nonzeros per row of the sparse sign sketch; 0 = min(8, c)
+    double sparsity = 0.0;    // s of the very sparse projection; 0 = sqrt(n)
 };
+// Very sparse projection (sketch.cu): entries +-1 with probability 1/(2s)
+// each, packed like the sparse sign rows (at most 12 nonzeros a row; more
+// sets device status word 2). s <= 0 means sqrt(n).
+double very_sparse_s(int64_t n, double s);
+int very_sparse_sketch(Workspace &ws, int64_t n, int c, double s, uint64_t seed, const uint4 **packed,
+                       cudaStream_t st);
+int very_sparse_dense(Workspace &ws, int64_t n, int c, double s, uint64_t seed, float *out, int64_t ld,
+                      cudaStream_t st);
+int very_sparse_spmm(Workspace &ws, const CsrView &M, int c, double s, uint64_t seed, float *Y, int64_t ldy,
+                     cudaStream_t st);
 int sparse_sign_sketch(Workspace &ws, int64_t n, int c, int zeta, uint64_t seed, const uint4 **packed,
                        cudaStream_t st);
 // The sketch written out densely (out[n][ld], ld >= c).

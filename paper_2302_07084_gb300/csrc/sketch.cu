@@ -14,6 +14,8 @@
 // the zeta columns of Omega row k. The sums are kept in 64-bit fixed point
 // (2^-32 units) in shared memory, so they are exact and independent of the
 // order; each entry of Y is the sum rounded once to FP32.
+#include <cmath>
+
 #include "common.cuh"
 #include "runtime.h"
 
@@ -21,6 +23,7 @@ namespace lne {
 namespace {
 
 constexpr uint32_t kSparseSignTag = 0x53505253u;
+constexpr uint32_t kVerySparseTag = 0x56535250u;
 constexpr int kSsWarps = 2;
 constexpr int kSsUnroll = 4;
 
@@ -62,6 +65,41 @@ __global__ void sparse_sign_kernel(int64_t n, int c, int zeta, uint32_t k0, uint
     }
 }
 
+// Very sparse projection (Li, Hastie and Church, KDD 2006; Sec. 4.2 names it
+// beside the sparse sign matrix): entry (i, j) is +1 if word j mod 4 of counter
+// (i, j / 4, 0, 0x56535250) is below thr = floor(2^32 / (2 s)), -1 if it is in
+// [thr, 2 thr), else 0. Row i is packed like a sparse sign row, with its
+// nonzero count in bits 16..19 of .w; a row with more than kMaxSketchZeta
+// nonzeros sets status[2] (its extra entries are dropped).
+__global__ void very_sparse_kernel(int64_t n, int c, uint32_t thr, uint32_t k0, uint32_t k1,
+                                   uint4 *__restrict__ packed, int *__restrict__ status) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint4 pk = make_uint4(0u, 0u, 0u, 0u);
+        int cnt = 0;
+        for (int b = 0; b < (c + 3) / 4; ++b) {
+            const u32x4 blk = philox10(u32x4{(uint32_t)i, (uint32_t)b, 0u, kVerySparseTag}, k0, k1);
+            const uint32_t ws[4] = {blk.x, blk.y, blk.z, blk.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int j = 4 * b + t;
+                const uint32_t w = ws[t];
+                const bool pos = w < thr, neg = !pos && (w - thr) < thr;
+                if (j >= c || !(pos || neg)) continue;
+                if (cnt == kMaxSketchZeta) {
+                    atomicExch(status + 2, 1);
+                    continue;
+                }
+                const uint32_t v = (uint32_t)j << (8 * (cnt & 3));
+                if (cnt < 4) pk.x |= v; else if (cnt < 8) pk.y |= v; else pk.z |= v;
+                if (neg) pk.w |= 1u << cnt;
+                ++cnt;
+            }
+        }
+        pk.w |= (uint32_t)cnt << 16;
+        packed[i] = pk;
+    }
+}
+
 __device__ __forceinline__ int packed_col(const uint4 &pk, int k) {
     const uint32_t w = k < 4 ? pk.x : k < 8 ? pk.y : pk.z;
     return (int)((w >> (8 * (k & 3))) & 255u);
@@ -73,7 +111,8 @@ __global__ void sparse_sign_dense_kernel(int64_t n, int c, int zeta, const uint4
         float *row = out + i * ld;
         for (int j = 0; j < c; ++j) row[j] = 0.f;
         const uint4 pk = packed[i];
-        for (int k = 0; k < zeta; ++k) row[packed_col(pk, k)] = (pk.w >> k) & 1u ? -1.f : 1.f;
+        const int z = zeta > 0 ? zeta : (int)((pk.w >> 16) & 15u);
+        for (int k = 0; k < z; ++k) row[packed_col(pk, k)] = (pk.w >> k) & 1u ? -1.f : 1.f;
     }
 }
 
@@ -130,13 +169,14 @@ __global__ void __launch_bounds__(kSsWarps * 32) sparse_sign_product_kernel(
                 // the zeta columns of one Omega row are distinct: their loads,
                 // adds and stores are independent of one another (only the
                 // next nonzero's may touch the same entries)
+                const int z = zeta > 0 ? zeta : (int)((pc[u].w >> 16) & 15u);   // 0: per-row count
                 long long v[kMaxSketchZeta];
 #pragma unroll
                 for (int k = 0; k < kMaxSketchZeta; ++k)
-                    if (k < zeta) v[k] = wacc[packed_col(pc[u], k) * 32 + lane];
+                    if (k < z) v[k] = wacc[packed_col(pc[u], k) * 32 + lane];
 #pragma unroll
                 for (int k = 0; k < kMaxSketchZeta; ++k)
-                    if (k < zeta) wacc[packed_col(pc[u], k) * 32 + lane] = v[k] + ((pc[u].w >> k) & 1u ? -q : q);
+                    if (k < z) wacc[packed_col(pc[u], k) * 32 + lane] = v[k] + ((pc[u].w >> k) & 1u ? -q : q);
             }
 #pragma unroll
             for (int u = 0; u < kSsUnroll; ++u) {
@@ -174,7 +214,64 @@ unsigned rows_grid(int64_t n, int per_block) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, (int64_t)per_block), num_sms() * 16));
 }
 
+int check_very_sparse(int64_t n, int c, double s) {
+    if (n < 0 || c < 1 || c > 255) return fail(LNE_ERR_INVALID, "very sparse projection needs 1 <= c <= 255");
+    if (!(s >= 1.0) || !std::isfinite(s)) return fail(LNE_ERR_INVALID, "very sparse projection needs s >= 1");
+    return 0;
+}
+
 }  // namespace
+
+double very_sparse_s(int64_t n, double s) { return s > 0.0 ? s : std::sqrt((double)std::max<int64_t>(n, 1)); }
+
+int very_sparse_sketch(Workspace &ws, int64_t n, int c, double s, uint64_t seed, const uint4 **packed,
+                       cudaStream_t st) {
+    s = very_sparse_s(n, s);
+    LNE_TRY(check_very_sparse(n, c, s));
+    uint4 *pk = nullptr;
+    int *status = nullptr;
+    LNE_TRY(ws.get("sketch.packed", (size_t)std::max<int64_t>(n, 1), &pk));
+    LNE_TRY(device_status(ws, &status, st));
+    const uint32_t thr = (uint32_t)std::floor(4294967296.0 / (2.0 * s));
+    const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu) ^ 0x4f4d4547u;
+    const uint32_t k1 = (uint32_t)(seed >> 32);
+    if (n > 0) {
+        LNE_TRACE("sketch", st);
+        very_sparse_kernel<<<rows_grid(n, 256), 256, 0, st>>>(n, c, thr, k0, k1, pk, status);
+        LNE_LAUNCH_CHECK();
+    }
+    *packed = pk;
+    return 0;
+}
+
+int very_sparse_dense(Workspace &ws, int64_t n, int c, double s, uint64_t seed, float *out, int64_t ld,
+                      cudaStream_t st) {
+    if (ld < c) return fail(LNE_ERR_INVALID, "ld must be >= c");
+    const uint4 *pk = nullptr;
+    LNE_TRY(very_sparse_sketch(ws, n, c, s, seed, &pk, st));
+    if (n > 0) {
+        LNE_TRACE("sketch", st);
+        sparse_sign_dense_kernel<<<rows_grid(n, 256), 256, 0, st>>>(n, c, 0, pk, out, ld);
+        LNE_LAUNCH_CHECK();
+    }
+    return status_check(ws, st);
+}
+
+int very_sparse_spmm(Workspace &ws, const CsrView &M, int c, double s, uint64_t seed, float *Y, int64_t ldy,
+                     cudaStream_t st) {
+    if (ldy < c) return fail(LNE_ERR_INVALID, "ldy must be >= c");
+    const uint4 *pk = nullptr;
+    LNE_TRY(very_sparse_sketch(ws, M.n, c, s, seed, &pk, st));
+    if (M.n > 0) {
+        LNE_TRACE("sparse_sign_spmm", st);
+        const int smem = kSsWarps * 32 * c * (int)sizeof(long long);
+        LNE_TRY(allow_dynamic_smem(sparse_sign_product_kernel));
+        sparse_sign_product_kernel<<<rows_grid(M.n, kSsWarps), kSsWarps * 32, smem, st>>>(
+            M.n, M.indptr, M.indices, M.data, pk, 0, c, Y, ldy);
+        LNE_LAUNCH_CHECK();
+    }
+    return 0;
+}
 
 int sparse_sign_sketch(Workspace &ws, int64_t n, int c, int zeta, uint64_t seed, const uint4 **packed,
                        cudaStream_t st) {

@@ -24,11 +24,12 @@ PREC_FP32 = 0
 PREC_BF16_MIXED = 1
 SKETCH_GAUSSIAN = 0
 SKETCH_SPARSE_SIGN = 1
+SKETCH_VERY_SPARSE = 2
 
 EXPORTED = [
     "lne_create", "lne_destroy", "lne_last_error", "lne_workspace_bytes", "lne_trim",
     "lne_sample_pairs", "lne_sparsifier_counts", "lne_sparsifier_csr", "lne_gaussian_sketch",
-    "lne_sparse_sign_sketch", "lne_sparse_sign_spmm",
+    "lne_sparse_sign_sketch", "lne_sparse_sign_spmm", "lne_very_sparse_sketch", "lne_very_sparse_spmm",
     "lne_spmm", "lne_cholqr2", "lne_rsvd", "lne_propagate", "lne_embed",
     "lne_kernel_launches", "lne_trace_enable", "lne_trace_read", "lne_set_option",
     "lne_svd_small", "lne_svd_small_noalloc", "lne_macro_f1", "lne_tune_batch", "lne_tune_tasks",
@@ -114,6 +115,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.lne_gaussian_sketch.argtypes = [vp, i64, i32, u64, vp, i64, vp]
     L.lne_sparse_sign_sketch.argtypes = [vp, i64, i32, i32, u64, vp, i64, vp]
     L.lne_sparse_sign_spmm.argtypes = [vp, ctypes.POINTER(_Csr), i32, i32, u64, vp, i64, vp]
+    L.lne_very_sparse_sketch.argtypes = [vp, i64, i32, ctypes.c_double, u64, vp, i64, vp]
+    L.lne_very_sparse_spmm.argtypes = [vp, ctypes.POINTER(_Csr), i32, ctypes.c_double, u64, vp, i64, vp]
     L.lne_spmm.argtypes = [vp, ctypes.POINTER(_Csr), vp, i64, i32, vp, i64, i32, vp]
     L.lne_cholqr2.argtypes = [vp, vp, i64, i32, i64, vp, vp]
     L.lne_rsvd.argtypes = [vp, ctypes.POINTER(_Csr), pp, vp, vp, vp, vp]
@@ -161,7 +164,7 @@ class Params:
     precision: int = PREC_FP32
     downsample_C: float = 0.0     # edge downsampling constant C (0 = off)
     sketch: int = SKETCH_GAUSSIAN  # test matrix of the randomized SVD
-    sketch_zeta: int = 0          # nonzeros per row of the sparse sign sketch (0 = min(8, c))
+    sketch_zeta: int = 0          # sparse sign: nonzeros per row (0 = min(8, c)); very sparse: s (0 = sqrt(n))
 
     def _c(self):
         s = np.ascontiguousarray(np.asarray(self.s, dtype=np.float64))
@@ -393,6 +396,21 @@ class Context:
         m = self._csr(csr)
         self._check(self.lib.lne_sparse_sign_spmm(self.h, ctypes.byref(m), c, zeta, int(seed) & 0xFFFFFFFFFFFFFFFF,
                                                   _ptr(Y), c, _stream()))
+        return Y
+
+    def very_sparse_sketch(self, n: int, c: int, s: float, seed: int) -> torch.Tensor:
+        """The very sparse projection written out densely (n x c); s <= 0: sqrt(n)."""
+        out = torch.empty((n, c), dtype=torch.float32, device=self.dev)
+        self._check(self.lib.lne_very_sparse_sketch(self.h, n, c, float(s), int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(out),
+                                                    c, _stream()))
+        return out
+
+    def very_sparse_spmm(self, csr: dict, c: int, s: float, seed: int) -> torch.Tensor:
+        """Y = M Omega for the very sparse Omega (never formed)."""
+        Y = torch.empty((int(csr["n"]), c), dtype=torch.float32, device=self.dev)
+        m = self._csr(csr)
+        self._check(self.lib.lne_very_sparse_spmm(self.h, ctypes.byref(m), c, float(s),
+                                                  int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(Y), c, _stream()))
         return Y
 
     @staticmethod

@@ -213,6 +213,63 @@ def test_sparse_sign_sketch_law():
     assert not np.array_equal(oracle.sparse_sign_sketch(40, c, zeta, 10), Om[:40])
 
 
+def test_very_sparse_words_follow_the_stream_layout():
+    """Entry (i, j) of the very sparse projection is decided by word j mod 4 of
+    Philox counter (i, j // 4, 0, 0x56535250) under the sketch key (the
+    known-answer-pinned Philox), against the threshold floor(2^32 / (2 s))."""
+    n, c, s, seed = 5, 10, 2.5, 0x1234567890ABCDEF
+    thr = oracle.very_sparse_threshold(n, s)
+    assert thr == int(np.floor(4294967296.0 / 5.0))
+    key = [(seed & 0xFFFFFFFF) ^ 0x4F4D4547, seed >> 32]
+    Om = oracle.very_sparse_sketch(n, c, s, seed)
+    for i in range(n):
+        for j in range(c):
+            w = int(oracle.philox4x32_10([i, j // 4, 0, 0x56535250], key)[j % 4])
+            want = 1.0 if w < thr else (-1.0 if w < 2 * thr else 0.0)
+            assert Om[i, j] == want
+    assert oracle.very_sparse_threshold(10000, 0.0) == int(np.floor(4294967296.0 / 200.0))
+    with pytest.raises(ValueError):
+        oracle.very_sparse_threshold(10, 0.5)
+
+
+def test_very_sparse_sketch_law():
+    """Li, Hastie and Church's law: +1 and -1 with probability 1/(2s) each,
+    independently per entry; E[Omega^T Omega] / n = (1/s) I."""
+    n, c, s = 40000, 32, 6.0
+    Om = oracle.very_sparse_sketch(n, c, s, seed=9)
+    p = oracle.very_sparse_threshold(n, s) / 4294967296.0
+    assert abs(p - 1.0 / (2 * s)) < 1e-9
+    tot = n * c
+    for v in (1.0, -1.0):
+        k = int((Om == v).sum())
+        assert abs(k - tot * p) < 5 * np.sqrt(tot * p * (1 - p))
+    # per column the same law
+    colnz = (Om != 0).sum(axis=0)
+    assert st.chisquare(colnz).pvalue > 1e-4
+    # nonzeros per row ~ Binomial(c, 2p)
+    rownz = (Om != 0).sum(axis=1)
+    assert abs(rownz.mean() - 2 * p * c) < 5 * np.sqrt(2 * p * c / n)
+    assert abs(rownz.var() - c * 2 * p * (1 - 2 * p)) < 0.05 * c * 2 * p
+    G = Om.T @ Om / n
+    np.testing.assert_allclose(np.diag(G), 2 * p, atol=6 * np.sqrt(2 * p / n))
+    assert np.max(np.abs(G - np.diag(np.diag(G)))) < 6 * np.sqrt(4 * p * p / n) + 6 / n
+    np.testing.assert_array_equal(oracle.very_sparse_sketch(40, c, s, 9), Om[:40])
+    assert not np.array_equal(oracle.very_sparse_sketch(40, c, s, 10), Om[:40])
+
+
+def test_frsvd_very_sparse_recovers_planted_spectrum():
+    rng = np.random.default_rng(1)
+    n, d = 400, 12
+    lam = np.concatenate([np.linspace(50, 20, d) * np.where(np.arange(d) % 3 == 0, -1, 1),
+                          rng.uniform(-1, 1, n - d)])
+    Q, M = _planted_symmetric(rng, n, lam)
+    order = np.argsort(-np.abs(lam))
+    out = oracle.fast_randomized_svd(M.indptr.astype(np.int64), M.indices, M.data, d, q=8,
+                                     oversample=8, seed=5, sketch="very_sparse", sparsity=4.0)
+    np.testing.assert_allclose(out["sigma"], np.abs(lam[order[:d]]), rtol=1e-10)
+    assert oracle.subspace_sin(out["U"], Q[:, order[:d]]) < 1e-9
+
+
 @pytest.mark.parametrize("zeta", [1, 4, 8])
 def test_frsvd_sparse_sign_recovers_planted_spectrum(zeta):
     rng = np.random.default_rng(1)
