@@ -382,6 +382,8 @@ def run_ours(args):
         params["downsample_C"] = lne.default_downsample_C(g.n)
     if args.sketch == "sparse_sign":
         params["sketch"] = lne.SKETCH_SPARSE_SIGN
+    elif args.sketch == "very_sparse":
+        params["sketch"] = lne.SKETCH_VERY_SPARSE
     P = lne.Params(**params)
     ctx = lne.Context(local)
     weights = None
@@ -486,9 +488,10 @@ def run_ours(args):
     breakdown = {t["name"]: round(t["ms"] / max(1, args.steps), 4) for t in trace}
 
     cfg = bench_config(g, params, world)
-    if args.downsample or args.sketch == "sparse_sign" or args.weighted:
+    if args.downsample or args.sketch != "gaussian" or args.weighted:
         cfg["workload"] = (WORKLOAD + ("_downsampled_C=ln_n" if args.downsample else "")
                            + ("_sparse_sign_sketch" if args.sketch == "sparse_sign" else "")
+                           + ("_very_sparse_sketch" if args.sketch == "very_sparse" else "")
                            + ("_weighted_1to9" if args.weighted else ""))
         if args.downsample:
             cfg["downsample_C"] = params["downsample_C"]
@@ -796,8 +799,9 @@ def main():
                     help="measure surrogate-guided search after training on G graphs of the SBM suite")
     ap.add_argument("--downsample", action="store_true",
                     help="the benchmark with edge downsampling at C = ln n (draws per second; no CPU baseline)")
-    ap.add_argument("--sketch", choices=["gaussian", "sparse_sign"], default="gaussian",
-                    help="test matrix of the randomized SVD (sparse sign: zeta = 8 nonzeros per row)")
+    ap.add_argument("--sketch", choices=["gaussian", "sparse_sign", "very_sparse"], default="gaussian",
+                    help="test matrix of the randomized SVD (sparse sign: zeta = 8 nonzeros per row; "
+                         "very sparse: s = sqrt(n))")
     ap.add_argument("--weighted", action="store_true",
                     help="the benchmark graph with integer edge weights 1..9 (draws per second; no CPU baseline)")
     ap.add_argument("--large", action="store_true",
