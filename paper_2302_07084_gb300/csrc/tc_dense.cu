@@ -38,7 +38,8 @@ namespace {
 constexpr int kTcRows = 128;          // MMA M: rows of Y per CTA
 constexpr int kTcKc = 32;             // k per stage: one 128-byte row of FP32
 constexpr int kTcStages = 3;
-constexpr int kTcThreads = 128;
+constexpr int kTcEpiWarps = 4;                 // warps 2..5 (one per TMEM lane quadrant)
+constexpr int kTcThreads = 32 * (2 + kTcEpiWarps);   // warp 0: TMA, warp 1: MMA, then the epilogue
 constexpr int kTcATile = kTcRows * kTcKc * 4;   // 16 KB
 constexpr uint64_t kTcWaitNs = 2000000000ull;   // a pipeline wait gives up after 2 s
 
@@ -132,17 +133,27 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent: one CTA per SM walks the work items t = blockIdx.x, + gridDim.x,
+// ... (item t = k-slice t / rbs of row block t % rbs). The TMA producer and the
+// MMA issuer run ahead across items through the shared-memory ring; two TMEM
+// accumulators let the epilogue of one item overlap the MMAs of the next.
 __global__ void __launch_bounds__(kTcThreads, 1) dense_tc_kernel(
     const __grid_constant__ CUtensorMap tm_ahi, const __grid_constant__ CUtensorMap tm_alo,
     const __grid_constant__ CUtensorMap tm_bhi, const __grid_constant__ CUtensorMap tm_blo, int64_t n,
-    int nchunks, int slice_chunks, int npad, int c, float *__restrict__ P, int *__restrict__ err) {
+    int nchunks, int slice_chunks, int rbs, int items, int npad, int c, float *__restrict__ P,
+    int *__restrict__ err) {
     extern __shared__ uint8_t tc_smem_raw[];
-    __shared__ __align__(8) uint64_t s_full[kTcStages], s_empty[kTcStages], s_acc;
+    __shared__ __align__(8) uint64_t s_full[kTcStages], s_empty[kTcStages], s_accf[2], s_acce[2];
     __shared__ uint32_t s_tmem;
     // stage tiles at 1024-byte boundaries of the shared window (the swizzle atom)
     uint8_t *smem = tc_smem_raw + ((1024u - (smem_u32(tc_smem_raw) & 1023u)) & 1023u);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t ncols = tc_tmem_cols(npad);
+    const uint32_t acc_cols = tc_tmem_cols(npad);   // columns of one accumulator
+    const uint32_t ncols = 2 * acc_cols;
     const int stage_bytes = tc_stage_bytes(npad);
     const int b_tile = npad * kTcKc * 4;
     if (warp == 0) {
@@ -156,7 +167,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) dense_tc_kernel(
             mbar_init(smem_u32(&s_full[s]), 1);
             mbar_init(smem_u32(&s_empty[s]), 1);
         }
-        mbar_init(smem_u32(&s_acc), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&s_accf[b]), 1);                  // tcgen05.commit of the item's MMAs
+            mbar_init(smem_u32(&s_acce[b]), kTcEpiWarps);        // one lane of each epilogue warp
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -164,68 +178,96 @@ __global__ void __launch_bounds__(kTcThreads, 1) dense_tc_kernel(
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = s_tmem;
-    const int r0 = blockIdx.x * kTcRows;
-    const int c0 = blockIdx.y * slice_chunks;
-    const int nk = max(0, min(nchunks, c0 + slice_chunks) - c0);
     const uint32_t idesc = tc_idesc(npad);
+    auto item_range = [&](int t, int &r0, int &z, int &c0, int &nk) {
+        const int rb = t % rbs;
+        z = t / rbs;
+        r0 = rb * kTcRows;
+        c0 = z * slice_chunks;
+        nk = max(0, min(nchunks, c0 + slice_chunks) - c0);
+    };
     bool ok = true;
     if (warp == 0) {
-        if (lane == 0) {   // producer: TMA loads of the k chunks into the ring
-            for (int i = 0; i < nk && ok; ++i) {
-                const int s = i % kTcStages;
-                if (i >= kTcStages) ok = mbar_wait(smem_u32(&s_empty[s]), (uint32_t)((i / kTcStages) + 1) & 1u, err);
-                if (!ok) break;
-                uint8_t *st = smem + (size_t)s * stage_bytes;
-                const uint32_t bar = smem_u32(&s_full[s]);
-                mbar_expect_tx(bar, (uint32_t)stage_bytes);
-                const int k = (c0 + i) * kTcKc;
-                tma_load_2d(smem_u32(st), &tm_ahi, k, r0, bar);
-                tma_load_2d(smem_u32(st + kTcATile), &tm_alo, k, r0, bar);
-                tma_load_2d(smem_u32(st + 2 * kTcATile), &tm_bhi, k, 0, bar);
-                tma_load_2d(smem_u32(st + 2 * kTcATile + b_tile), &tm_blo, k, 0, bar);
+        if (lane == 0) {   // producer: TMA loads of every item's k chunks into the ring
+            uint32_t g = 0;
+            for (int t = blockIdx.x; t < items && ok; t += gridDim.x) {
+                int r0, z, c0, nk;
+                item_range(t, r0, z, c0, nk);
+                for (int i = 0; i < nk; ++i, ++g) {
+                    const uint32_t s = g % kTcStages;
+                    if (g >= kTcStages) ok = mbar_wait(smem_u32(&s_empty[s]), (g / kTcStages + 1) & 1u, err);
+                    if (!ok) break;
+                    uint8_t *st = smem + (size_t)s * stage_bytes;
+                    const uint32_t bar = smem_u32(&s_full[s]);
+                    mbar_expect_tx(bar, (uint32_t)stage_bytes);
+                    const int k = (c0 + i) * kTcKc;
+                    tma_load_2d(smem_u32(st), &tm_ahi, k, r0, bar);
+                    tma_load_2d(smem_u32(st + kTcATile), &tm_alo, k, r0, bar);
+                    tma_load_2d(smem_u32(st + 2 * kTcATile), &tm_bhi, k, 0, bar);
+                    tma_load_2d(smem_u32(st + 2 * kTcATile + b_tile), &tm_blo, k, 0, bar);
+                }
             }
         }
         __syncwarp();
     } else if (warp == 1) {
         if (lane == 0) {   // MMA issuer
-            for (int i = 0; i < nk && ok; ++i) {
-                const int s = i % kTcStages;
-                ok = mbar_wait(smem_u32(&s_full[s]), (uint32_t)(i / kTcStages) & 1u, err);
+            uint32_t g = 0, j = 0;
+            for (int t = blockIdx.x; t < items && ok; t += gridDim.x, ++j) {
+                int r0, z, c0, nk;
+                item_range(t, r0, z, c0, nk);
+                const uint32_t b = j & 1u;
+                // the epilogue has drained this accumulator's previous item
+                if (j >= 2) ok = mbar_wait(smem_u32(&s_acce[b]), ((j >> 1) + 1) & 1u, err);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t a_hi = smem_u32(smem + (size_t)s * stage_bytes);
-                const uint32_t a_lo = a_hi + kTcATile, b_hi = a_hi + 2 * kTcATile, b_lo = b_hi + b_tile;
+                const uint32_t acc = tmem + b * acc_cols;
+                for (int i = 0; i < nk; ++i, ++g) {
+                    const uint32_t s = g % kTcStages;
+                    ok = mbar_wait(smem_u32(&s_full[s]), (g / kTcStages) & 1u, err);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t a_hi = smem_u32(smem + (size_t)s * stage_bytes);
+                    const uint32_t a_lo = a_hi + kTcATile, b_hi = a_hi + 2 * kTcATile, b_lo = b_hi + b_tile;
 #pragma unroll
-                for (int kk = 0; kk < kTcKc / 8; ++kk) {   // K = 8 TF32 = 32 bytes per MMA
-                    const uint32_t off = 32u * kk;
-                    tc_mma(tmem, tc_sdesc(a_lo + off), tc_sdesc(b_hi + off), idesc, (i > 0 || kk > 0) ? 1u : 0u);
-                    tc_mma(tmem, tc_sdesc(a_hi + off), tc_sdesc(b_lo + off), idesc, 1u);
-                    tc_mma(tmem, tc_sdesc(a_hi + off), tc_sdesc(b_hi + off), idesc, 1u);
+                    for (int kk = 0; kk < kTcKc / 8; ++kk) {   // K = 8 TF32 = 32 bytes per MMA
+                        const uint32_t off = 32u * kk;
+                        tc_mma(acc, tc_sdesc(a_lo + off), tc_sdesc(b_hi + off), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                        tc_mma(acc, tc_sdesc(a_hi + off), tc_sdesc(b_lo + off), idesc, 1u);
+                        tc_mma(acc, tc_sdesc(a_hi + off), tc_sdesc(b_hi + off), idesc, 1u);
+                    }
+                    tc_commit(smem_u32(&s_empty[s]));   // the stage is free once these MMAs have read it
                 }
-                tc_commit(smem_u32(&s_empty[s]));   // the stage is free once these MMAs have read it
+                tc_commit(smem_u32(&s_accf[b]));        // the item's accumulator is complete
             }
-            tc_commit(smem_u32(&s_acc));
         }
         __syncwarp();
-    }
-    // epilogue: every warp reads its 32 TMEM lanes (rows r0 + 32 warp + lane)
-    bool acc_ok = nk > 0 && mbar_wait(smem_u32(&s_acc), 0u, err);
-    acc_ok = __all_sync(0xffffffffu, acc_ok);   // tcgen05.ld is warp-collective
-    tc_fence_after();
-    const int64_t row = (int64_t)r0 + 32 * warp + lane;
-    float *out = P + ((int64_t)blockIdx.y * n + row) * c;
-    for (int col0 = 0; col0 < npad; col0 += 16) {
-        float v[16];
-        if (acc_ok) {
-            tc_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)col0, v);
-        } else {
+    } else {
+        // epilogue warps: warp w reads TMEM lanes 32 (w % 4) .. + 31, rows r0 + 32 (w % 4) + lane
+        const int q = warp & 3;
+        uint32_t j = 0;
+        for (int t = blockIdx.x; t < items; t += gridDim.x, ++j) {
+            int r0, z, c0, nk;
+            item_range(t, r0, z, c0, nk);
+            const uint32_t b = j & 1u;
+            bool acc_ok = mbar_wait(smem_u32(&s_accf[b]), (j >> 1) & 1u, err);
+            acc_ok = __all_sync(0xffffffffu, acc_ok);   // tcgen05.ld is warp-collective
+            if (!acc_ok) break;
+            tc_fence_after();
+            const int64_t row = (int64_t)r0 + 32 * q + lane;
+            float *out = P + ((int64_t)z * n + row) * c;
+            const uint32_t base = tmem + b * acc_cols + ((uint32_t)(32 * q) << 16);
+            for (int col0 = 0; col0 < npad; col0 += 16) {
+                float v[16];
+                tc_ld16(base + (uint32_t)col0, v);
+                if (row < n) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = 0.f;
-        }
-        if (row < n) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-                if (col0 + i < c) out[col0 + i] = v[i];
+                    for (int i = 0; i < 16; ++i)
+                        if (col0 + i < c) out[col0 + i] = v[i];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&s_acce[b]));
         }
     }
     tc_fence_before();
@@ -363,7 +405,8 @@ int dense_tc_spmm(Workspace &ws, const float *Ahi, const float *Alo, int64_t ld,
     LNE_CUDA_TRY(cudaFuncSetAttribute(dense_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int rb = (int)ceil_div(n, (int64_t)kTcRows);
     const int nchunks = (int)(ld / kTcKc);
-    // slices of the k range: row blocks x slices fill whole waves of one CTA per SM
+    // k-slices: row blocks x slices, as items of the persistent CTAs, give every
+    // SM the same number of items (slices of equal length)
     const int64_t slots = num_sms();
     int ks = 1;
     double best = 1e300;
@@ -376,15 +419,16 @@ int dense_tc_spmm(Workspace &ws, const float *Ahi, const float *Alo, int64_t ld,
     }
     const int slice_chunks = (int)ceil_div(nchunks, ks);
     ks = (int)ceil_div(nchunks, slice_chunks);
+    const int items = rb * ks;
     float *part = nullptr;
     int *status = nullptr;
     LNE_TRY(ws.get("tc.part", (size_t)ks * n * c, &part));
     LNE_TRY(device_status(ws, &status, st));
     {
         LNE_TRACE("dense_tc", st);
-        dense_tc_kernel<<<dim3((unsigned)rb, (unsigned)ks), kTcThreads, smem, st>>>(m_ahi, m_alo, m_bhi, m_blo, n,
-                                                                                  nchunks, slice_chunks, npad, c, part,
-                                                                                  status + 1);
+        const unsigned grid = (unsigned)std::min<int64_t>(items, slots);
+        dense_tc_kernel<<<grid, kTcThreads, smem, st>>>(m_ahi, m_alo, m_bhi, m_blo, n, nchunks, slice_chunks, rb,
+                                                         items, npad, c, part, status + 1);
         LNE_LAUNCH_CHECK();
     }
     // a wait that expired is reported by the caller's status_check
