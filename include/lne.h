@@ -134,7 +134,8 @@ typedef struct lne_ctx lne_ctx;
                                     depend on it */
 #define LNE_OPT_DENSE_PRODUCT 4  /* products of the randomized SVD (FP32) on the dense count table
                                     instead of the CSR, when the table aggregation ran: 0 = when at
-                                    least 10% of all pairs are present (default), 1 = never,
+                                    least a fraction 8 / (d + oversample) of all pairs is present
+                                    (default), 1 = never,
                                     2 = always. The dense product runs on the tcgen05 tensor cores
                                     (TF32 hi / lo split, three MMAs per product: FP32 accuracy);
                                     same values as the CSR product, summed in another order */

@@ -659,7 +659,7 @@ int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_de
     float *X0 = nullptr;
     if (rc == 0) rc = ctx->ws.get("embed.x0", (size_t)g->n * p->d, &X0);
     if (rc == 0) {
-        rc = lne::rsvd(ctx->ws, lne::product_view(M, ctx->dense_mode), p->d, oversample_of(p), p->q, p->seed,
+        rc = lne::rsvd(ctx->ws, lne::product_view(M, ctx->dense_mode, p->d + oversample_of(p)), p->d, oversample_of(p), p->q, p->seed,
                        p->precision, nullptr, nullptr, X0, st, sketch_of(p));
     }
     if (rc == 0)

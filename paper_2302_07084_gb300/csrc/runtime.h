@@ -121,9 +121,9 @@ struct CsrResult {
     int64_t dense_ld = 0;
 };
 // The view the randomized SVD's products use: the dense table when there is
-// one and mode allows (0 = when at least 10% of the pairs are present,
-// 1 = never, 2 = always), else the CSR.
-CsrView product_view(const CsrResult &M, int dense_mode);
+// one and mode allows (0 = when at least a fraction 8 / c of all pairs is
+// present, c the products' width; 1 = never; 2 = always), else the CSR.
+CsrView product_view(const CsrResult &M, int dense_mode, int c);
 int sparsifier_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out,
                    cudaStream_t st);
 

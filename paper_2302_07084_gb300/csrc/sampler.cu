@@ -2593,15 +2593,19 @@ uint32_t strat_weight(const SamplerSpec &sp, int r) {
 
 }  // namespace
 
-CsrView product_view(const CsrResult &M, int dense_mode) {
+CsrView product_view(const CsrResult &M, int dense_mode, int c) {
     CsrView v;
     v.n = M.n;
     v.nnz = M.nnz;
     v.indptr = M.indptr;
     v.indices = M.indices;
     v.data = M.data;
+    // the CSR product gathers c values per nonzero, the tensor-core product
+    // streams 8 bytes per table entry (plus its hi / lo split): measured on
+    // GB300, the table is the faster once the density reaches ~8 / c (c = 48:
+    // CSR faster at 0.11, table at 0.23; c = 144: table at 0.41)
     const double dens = M.n > 0 ? (double)M.nnz / ((double)M.n * (double)M.n) : 0.0;
-    if (M.dense && (dense_mode == 2 || (dense_mode == 0 && dens >= 0.1))) {
+    if (M.dense && (dense_mode == 2 || (dense_mode == 0 && dens >= 8.0 / std::max(c, 1)))) {
         v.dense = M.dense;
         v.dense_ld = M.dense_ld;
     }

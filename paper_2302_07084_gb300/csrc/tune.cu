@@ -166,7 +166,7 @@ int tune_batch(Workspace &ws, PropBatchGraph *cache, SpmmTune &tc, int aggregati
         SketchSpec sk;
         sk.kind = p.sketch;
         sk.zeta = p.sketch_zeta;
-        LNE_TRY(rsvd(ws, product_view(M, dense_mode), d, os_of(p), p.q, p.seed, p.precision, nullptr, nullptr,
+        LNE_TRY(rsvd(ws, product_view(M, dense_mode, d + os_of(p)), d, os_of(p), p.q, p.seed, p.precision, nullptr, nullptr,
                      X0s + (size_t)q * n * d, st, sk));
     }
     if (have_strata) stratified_release(ws);
