@@ -1296,6 +1296,37 @@ __global__ void table_values_kernel(uint32_t *__restrict__ T, int64_t ld, int n,
     }
 }
 
+// table_decode_kernel and table_values_kernel in one pass, for the CSR: the
+// exact count of each upper-triangle counter from its packed field and wrap
+// records (see table_decode_kernel), then its Eq. 1 value written as float
+// bits in place of the wrap record (which is 0 where nothing was counted).
+template <int BITS>
+__global__ void table_decode_values_kernel(const uint32_t *__restrict__ tp, uint32_t *__restrict__ T, int64_t ld,
+                                           int n, const int64_t *__restrict__ indptr, NetmfConst kc) {
+    constexpr int P = TabPack<BITS>::P;
+    constexpr uint32_t mask = TabPack<BITS>::mask;
+    const int x = blockIdx.x;
+    const int64_t dx = eq1_degree(kc, indptr, x);
+    const int64_t k0 = ((int64_t)x * ld + x) / P, k1 = ((int64_t)x * ld + ld) / P;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const uint32_t w = tp[k];
+        uint32_t wr[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) wr[i] = T[P * k + i];
+        uint32_t prev = 0;
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+            const uint32_t cnt = ((w >> (BITS * i)) & mask) + (wr[i] << BITS) - prev;
+            prev = wr[i];
+            const int64_t y = P * k + i - (int64_t)x * ld;
+            // left of the diagonal, padding, or nothing counted (then no wraps
+            // either: the record is already 0)
+            if (y < x || y >= n || cnt == 0) continue;
+            T[P * k + i] = __float_as_uint(netmf_value(cnt, dx, eq1_degree(kc, indptr, y), x == y, kc));
+        }
+    }
+}
+
 // Distinct pairs per upper-triangle row (for the counts output).
 template <typename E>
 __global__ void table_row_nnz_kernel(const E *__restrict__ T, int64_t ld, int n, uint32_t *__restrict__ cnt) {
@@ -2057,6 +2088,7 @@ namespace {
 struct Table {
     uint32_t *T = nullptr;    // counts, then the float bits of the Eq. 1 values
     uint64_t *W = nullptr;    // summed weights (edge downsampling only)
+    uint32_t *packed = nullptr;   // packed narrow counters not yet decoded into T (plain walks)
     int64_t ld = 0;
     int nt = 0;
 };
@@ -2300,7 +2332,10 @@ bool use_table(const GraphView &g, const SamplerSpec &sp) {
 }
 
 // Walk every arc's samples and count them into the dense upper-triangle table.
-int sample_table(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Table *tb, cudaStream_t st) {
+// decode = false leaves the plain walk's packed counters in tb->packed for
+// table_decode_values_kernel (otherwise T holds the exact counts on return).
+int sample_table(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Table *tb, cudaStream_t st,
+                 bool decode = true) {
     if (g.n > 65536) return fail(LNE_ERR_UNSUPPORTED, "the dense count table needs n <= 65536");
     const int nt = (int)ceil_div(g.n, kTile);
     const int64_t ld = (int64_t)nt * kTile;
@@ -2331,6 +2366,10 @@ int sample_table(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Table
             walk_table_kernel<BITS><<<(unsigned)tab_tiles, kTabThreads, tab_smem, st>>>(A, tab_arcs, tp, tb->T,
                                                                                          (uint32_t)ld);
             LNE_LAUNCH_CHECK();
+        }
+        if (!decode) {
+            tb->packed = tp;
+            return 0;
         }
         LNE_TRACE("table_decode", st);
         table_decode_kernel<BITS><<<(unsigned)std::min<int64_t>(g.n, num_sms() * 8), 256, 0, st>>>(tp, tb->T,
@@ -2397,11 +2436,14 @@ int table_counts(Workspace &ws, const GraphView &g, const SamplerSpec &sp, Count
 
 int table_csr(Workspace &ws, const GraphView &g, const SamplerSpec &sp, CsrResult *out, cudaStream_t st) {
     Table tb;
-    LNE_TRY(sample_table(ws, g, sp, &tb, st));
+    LNE_TRY(sample_table(ws, g, sp, &tb, st, false));
     const int n = (int)g.n;
     {
         LNE_TRACE("table_values", st);
         if (tb.W) table_values_w_kernel<<<(unsigned)n, 256, 0, st>>>(tb.W, tb.T, tb.ld, n, g.indptr, netmf_const(sp));
+        else if (tb.packed)
+            table_decode_values_kernel<kTabBits><<<(unsigned)n, 256, 0, st>>>(tb.packed, tb.T, tb.ld, n, g.indptr,
+                                                                             netmf_const(sp));
         else table_values_kernel<<<(unsigned)n, 256, 0, st>>>(tb.T, tb.ld, n, g.indptr, netmf_const(sp));
         LNE_LAUNCH_CHECK();
     }
