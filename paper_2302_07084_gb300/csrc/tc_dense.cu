@@ -29,6 +29,8 @@
 // of hanging.
 #include <cuda.h>
 
+#include <utility>
+
 #include "runtime.h"
 #include "tc_desc.h"
 
@@ -335,16 +337,17 @@ using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t,
                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 int get_encoder(EncodeTiled *fn) {
-    static EncodeTiled cached = nullptr;
-    if (!cached) {
+    // resolved once per process (thread-safe static initialisation)
+    static const std::pair<EncodeTiled, cudaError_t> entry = [] {
         void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
         cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q);
-        if (e != cudaSuccess) return cuda_fail("cudaGetDriverEntryPointByVersion", e, __FILE__, __LINE__);
-        if (q != cudaDriverEntryPointSuccess || !p) return fail(LNE_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
-        cached = reinterpret_cast<EncodeTiled>(p);
-    }
-    *fn = cached;
+        if (e == cudaSuccess && (q != cudaDriverEntryPointSuccess || !p)) e = cudaErrorSymbolNotFound;
+        return std::make_pair(reinterpret_cast<EncodeTiled>(p), e);
+    }();
+    if (entry.second != cudaSuccess)
+        return cuda_fail("cudaGetDriverEntryPointByVersion(cuTensorMapEncodeTiled)", entry.second, __FILE__, __LINE__);
+    *fn = entry.first;
     return 0;
 }
 
