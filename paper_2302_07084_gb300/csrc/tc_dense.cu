@@ -281,31 +281,51 @@ __global__ void __launch_bounds__(kTcThreads, 1) dense_tc_kernel(
 }
 
 // The full symmetric matrix from the upper-triangle table, split into TF32
-// hi / lo parts: 32 x 32 tiles through shared memory (a tile below the
-// diagonal is the transpose of its mirror tile above it).
+// hi / lo parts: one CTA per 64 x 64 tile on or above the diagonal reads it
+// once (16-byte loads) and writes it and its mirror below the diagonal
+// (16-byte stores, the mirror through a shared-memory transpose); a diagonal
+// tile takes its lower half from its upper half.
+__device__ __forceinline__ void split_store4(float *hi, float *lo, float4 v) {
+    float4 h;
+    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+    *reinterpret_cast<float4 *>(hi) = h;
+    *reinterpret_cast<float4 *>(lo) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+}
+
 __global__ void __launch_bounds__(256) table_split_kernel(const float *__restrict__ T, int64_t ld,
                                                           float *__restrict__ hi, float *__restrict__ lo) {
-    __shared__ float S[32][33];
+    __shared__ float S[64][65];
     const int bi = blockIdx.y, bk = blockIdx.x;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    for (int y = ty; y < 32; y += 8) {
-        const int64_t i = (int64_t)bi * 32 + y, k = (int64_t)bk * 32 + tx;
-        if (bi < bk) {
-            S[y][tx] = T[i * ld + k];
-        } else if (bi > bk) {
-            // row (bk 32 + y) of the mirror tile, stored transposed
-            S[tx][y] = T[((int64_t)bk * 32 + y) * ld + (int64_t)bi * 32 + tx];
-        } else {
-            S[y][tx] = T[min(i, k) * ld + max(i, k)];
-        }
+    if (bi > bk) return;   // the mirror of an upper tile is written by that tile's CTA
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int64_t r0 = (int64_t)bi * 64, c0 = (int64_t)bk * 64;
+    for (int y = ty; y < 64; y += 16) {
+        const float4 v = *reinterpret_cast<const float4 *>(T + (r0 + y) * ld + c0 + 4 * tx);
+        S[y][4 * tx] = v.x;
+        S[y][4 * tx + 1] = v.y;
+        S[y][4 * tx + 2] = v.z;
+        S[y][4 * tx + 3] = v.w;
     }
     __syncthreads();
-    for (int y = ty; y < 32; y += 8) {
-        const int64_t at = ((int64_t)bi * 32 + y) * ld + (int64_t)bk * 32 + tx;
-        const float v = S[y][tx];
-        const float h = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-        hi[at] = h;
-        lo[at] = v - h;
+    if (bi == bk) {   // only the upper half of a diagonal tile is in the table
+        for (int e = threadIdx.x; e < 64 * 64; e += 256) {
+            const int y = e >> 6, x = e & 63;
+            if (y > x) S[y][x] = S[x][y];
+        }
+        __syncthreads();
+    }
+    for (int y = ty; y < 64; y += 16) {
+        const int64_t at = (r0 + y) * ld + c0 + 4 * tx;
+        split_store4(hi + at, lo + at, make_float4(S[y][4 * tx], S[y][4 * tx + 1], S[y][4 * tx + 2], S[y][4 * tx + 3]));
+    }
+    if (bi == bk) return;
+    for (int y = ty; y < 64; y += 16) {   // row c0 + y of the mirror tile = column y of this one
+        const int64_t at = (c0 + y) * ld + r0 + 4 * tx;
+        split_store4(hi + at, lo + at,
+                     make_float4(S[4 * tx][y], S[4 * tx + 1][y], S[4 * tx + 2][y], S[4 * tx + 3][y]));
     }
 }
 
@@ -376,7 +396,7 @@ int dense_tc_prepare(Workspace &ws, const float *T, int64_t ld, const float **hi
     LNE_TRY(ws.get("tc.ahi", (size_t)(ld * ld), &h));
     LNE_TRY(ws.get("tc.alo", (size_t)(ld * ld), &l));
     LNE_TRACE("table_split", st);
-    const dim3 grid((unsigned)(ld / 32), (unsigned)(ld / 32));
+    const dim3 grid((unsigned)(ld / 64), (unsigned)(ld / 64));
     table_split_kernel<<<grid, 256, 0, st>>>(T, ld, h, l);
     LNE_LAUNCH_CHECK();
     *hi = h;
