@@ -227,8 +227,9 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel(const double *__rest
 // single CTA.
 constexpr int kCholB = 16;
 
-__global__ void __launch_bounds__(256) chol_panel_kernel(double *__restrict__ A, int c, int k0,
-                                                         int *__restrict__ status, double *__restrict__ r11) {
+// The panel of rows k0.. for the 16-column block bx of R12 (nb blocks).
+__device__ __forceinline__ void chol_panel_body(double *__restrict__ A, int c, int k0, int *__restrict__ status,
+                                                double *__restrict__ r11, int bx, int nb) {
     __shared__ double s11[kCholB][kCholB + 1];
     __shared__ double sinv[kCholB];
     const int tid = threadIdx.x;
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(256) chol_panel_kernel(double *__restrict__ A,
             const double att = s11[t][t];
             double d = 1.0;
             if (!(att > 0.0) || !isfinite(att)) {
-                if (blockIdx.x == 0 && *status == 0) *status = k0 + t + 1;
+                if (bx == 0 && *status == 0) *status = k0 + t + 1;
             } else {
                 d = sqrt(att);
             }
@@ -263,7 +264,7 @@ __global__ void __launch_bounds__(256) chol_panel_kernel(double *__restrict__ A,
     // forward substitution)
     {
         const int li = tid & 15;
-        const int j = k1 + blockIdx.x * 16 + (tid >> 4);
+        const int j = k1 + bx * 16 + (tid >> 4);
         const bool live = j < c && li < bs;
         double x = live ? A[(size_t)(k0 + li) * c + j] : 0.0;
         for (int t = 0; t < bs; ++t) {
@@ -274,28 +275,34 @@ __global__ void __launch_bounds__(256) chol_panel_kernel(double *__restrict__ A,
         if (live) A[(size_t)(k0 + li) * c + j] = x;
     }
     // R11 (and zeros left of the diagonal in the panel's rows)
-    if (blockIdx.x == 0)
+    if (bx == 0)
         for (int e = tid; e < bs * bs; e += blockDim.x) {
             const int i = e / bs, j = e - i * bs;
             r11[e] = j >= i ? s11[i][j] : 0.0;
         }
-    if (gridDim.x == 1)
+    if (nb == 1)
         for (int e = tid; e < bs * k1; e += blockDim.x) {
             const int i = e / k1, j = e - i * k1;   // row k0 + i, column j < k1
             A[(size_t)(k0 + i) * c + j] = j >= k0 + i ? s11[i][j - k0] : 0.0;
         }
 }
 
-__global__ void __launch_bounds__(256) chol_update_kernel(double *__restrict__ A, int c, int k0, int k1,
-                                                          const double *__restrict__ r11) {
-    const int I = blockIdx.y, J = blockIdx.x;
+__global__ void __launch_bounds__(256) chol_panel_kernel(double *__restrict__ A, int c, int k0,
+                                                         int *__restrict__ status, double *__restrict__ r11) {
+    chol_panel_body(A, c, k0, status, r11, blockIdx.x, gridDim.x);
+}
+
+// r11 is read with ld.global.cg: in the cooperative launch it was written by
+// another CTA of the same launch, so it must not come through the read-only path.
+__device__ __forceinline__ void chol_update_body(double *__restrict__ A, int c, int k0, int k1, const double *r11,
+                                                 int I, int J) {
     if (I > J) return;
     const int tid = threadIdx.x;
     const int bs = k1 - k0;
     if (I == 0 && J == 0)   // the panel's R11 from its scratch block (these entries are not read below)
         for (int e = tid; e < bs * k1; e += blockDim.x) {
             const int i = e / k1, j = e - i * k1;
-            A[(size_t)(k0 + i) * c + j] = j >= k0 ? r11[i * bs + (j - k0)] : 0.0;
+            A[(size_t)(k0 + i) * c + j] = j >= k0 ? __ldcg(r11 + i * bs + (j - k0)) : 0.0;
         }
     __shared__ double ri[kCholB][16], rj[kCholB][16];
     const int ti = tid >> 4, tj = tid & 15;
@@ -311,6 +318,59 @@ __global__ void __launch_bounds__(256) chol_update_kernel(double *__restrict__ A
         double a = A[(size_t)i * c + j];
         for (int t = 0; t < bs; ++t) a = fma(-ri[t][ti], rj[t][tj], a);
         A[(size_t)i * c + j] = a;
+    }
+}
+
+__global__ void __launch_bounds__(256) chol_update_kernel(double *__restrict__ A, int c, int k0, int k1,
+                                                          const double *__restrict__ r11) {
+    chol_update_body(A, c, k0, k1, r11, blockIdx.y, blockIdx.x);
+}
+
+// All panels in one cooperative launch: the panel and update phases of each
+// panel are separated by grid-wide barriers (every CTA is resident, so the
+// barriers only wait for running CTAs; each gives up after 2 s and sets the
+// status word [1]). The same work in the same order as the per-panel launches.
+__device__ __forceinline__ void grid_barrier(unsigned *bar, unsigned &target, int *status) {
+    __syncthreads();
+    target += gridDim.x;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        uint64_t t0;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+            if (v >= target) break;
+            uint64_t t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if (t - t0 > 2000000000ull) {
+                atomicExch(status + 1, 1);
+                break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) chol_coop_kernel(double *__restrict__ A, int c, int *__restrict__ status,
+                                                        double *__restrict__ r11, unsigned *__restrict__ bar) {
+    unsigned target = 0;
+    for (int k0 = 0; k0 < c; k0 += kCholB) {
+        const int k1 = min(c, k0 + kCholB);
+        const int nb = max(1, (c - k1 + 15) / 16);
+        for (int bx = blockIdx.x; bx < nb; bx += gridDim.x) {
+            chol_panel_body(A, c, k0, status, r11, bx, nb);
+            __syncthreads();
+        }
+        if (k1 >= c) break;
+        grid_barrier(bar, target, status);
+        for (int t = blockIdx.x; t < nb * nb; t += gridDim.x) {
+            chol_update_body(A, c, k0, k1, r11, t / nb, t % nb);
+            __syncthreads();
+        }
+        grid_barrier(bar, target, status);
     }
 }
 
@@ -1212,21 +1272,23 @@ static int gram(Workspace &ws, const float *Y, int64_t n, int c, int64_t ld, dou
 static int chol(Workspace &ws, const double *G, int c, double *R, cudaStream_t st) {
     int *status = nullptr;
     LNE_TRY(device_status(ws, &status, st));
-    if (c >= 64) {   // blocked over many SMs
+    if (c >= 64) {   // blocked over many SMs: one cooperative launch for all panels
         double *r11 = nullptr;
+        unsigned *bar = nullptr;
         LNE_TRY(ws.get("chol.r11", (size_t)kCholB * kCholB, &r11));
+        LNE_TRY(ws.get("chol.bar", 1, &bar));
         LNE_CUDA_TRY(cudaMemcpyAsync(R, G, sizeof(double) * (size_t)c * c, cudaMemcpyDeviceToDevice, st));
+        LNE_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(unsigned), st));
         LNE_TRACE("chol", st);
-        for (int k0 = 0; k0 < c; k0 += kCholB) {
-            const int k1 = std::min(c, k0 + kCholB);
-            const unsigned nb = (unsigned)std::max<int64_t>(1, ceil_div(c - k1, 16));
-            chol_panel_kernel<<<nb, 256, 0, st>>>(R, c, k0, status, r11);
-            LNE_LAUNCH_CHECK();
-            if (k1 < c) {
-                chol_update_kernel<<<dim3(nb, nb), 256, 0, st>>>(R, c, k0, k1, r11);
-                LNE_LAUNCH_CHECK();
-            }
-        }
+        const int nb0 = (int)std::max<int64_t>(1, ceil_div(c - kCholB, 16));
+        int per_sm = 0;
+        LNE_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, chol_coop_kernel, 256, 0));
+        const int grid = std::min(nb0 * nb0, std::max(1, per_sm) * num_sms());
+        int ci = c;
+        void *args[] = {&R, &ci, &status, &r11, &bar};
+        LNE_CUDA_TRY(cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(chol_coop_kernel), dim3(grid),
+                                                 dim3(256), args, 0, st));
+        LNE_LAUNCH_CHECK();
     } else {
         const int smem = c <= kMaxSmemC ? c * c * 8 : 0;
         if (smem > 48 * 1024)
@@ -1254,7 +1316,7 @@ int status_check(Workspace &ws, cudaStream_t st) {
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
     if (h[0] == 0 && h[1] == 0 && h[2] == 0) return 0;
     LNE_CUDA_TRY(cudaMemsetAsync(status, 0, 4 * sizeof(int), st));
-    if (h[1] != 0) return fail(LNE_ERR_TIMEOUT, "tensor-core dense product: a pipeline wait expired");
+    if (h[1] != 0) return fail(LNE_ERR_TIMEOUT, "a bounded device wait expired (tensor-core pipeline or Cholesky grid barrier)");
     if (h[2] != 0)
         return fail(LNE_ERR_UNSUPPORTED, "a row of the very sparse projection has more than 12 nonzeros (raise s)");
     return fail(LNE_ERR_NUMERIC, "Cholesky breakdown in CholeskyQR (Gram not positive definite)");
