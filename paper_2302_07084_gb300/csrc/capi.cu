@@ -5,6 +5,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "lne.h"
 #include "runtime.h"
@@ -50,6 +53,21 @@ int num_sms() {
     if (cudaDeviceGetAttribute(&q, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || q <= 0) q = 1;
     g_sm_count[dev].store(q, std::memory_order_relaxed);
     return q;
+}
+
+namespace {
+std::mutex g_smem_mu;
+std::set<std::pair<const void *, int>> g_smem_raised;
+}  // namespace
+
+bool smem_limit_raised(const void *kernel, int dev) {
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    return g_smem_raised.count({kernel, dev}) != 0;
+}
+
+void mark_smem_limit_raised(const void *kernel, int dev) {
+    std::lock_guard<std::mutex> lock(g_smem_mu);
+    g_smem_raised.insert({kernel, dev});
 }
 
 // Per-context record of timed regions (CUDA event pairs).

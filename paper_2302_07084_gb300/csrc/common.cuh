@@ -101,21 +101,32 @@ int fail(int code, const std::string &msg);
 const std::string &last_message();
 void clear_message();
 
+// Whether (kernel, device) has had its dynamic shared-memory limit raised,
+// and the mark set once it has (thread-safe).
+bool smem_limit_raised(const void *kernel, int dev);
+void mark_smem_limit_raised(const void *kernel, int dev);
+
 // Let `kernel` use as much dynamic shared memory as the device allows beside
 // its static shared memory. The value is the same on every call, so host
 // threads that launch the kernel concurrently cannot lower the limit under one
-// another's launch.
+// another's launch; it is set once per kernel and device (the attribute
+// calls take microseconds of host time, which would stall a stream of short
+// kernels).
 template <typename Kernel>
 inline int allow_dynamic_smem(Kernel kernel) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail("cudaGetDevice", e, __FILE__, __LINE__);
+    if (smem_limit_raised(reinterpret_cast<const void *>(kernel), dev)) return 0;
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
-    int dev = 0, optin = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    int optin = 0;
+    e = cudaFuncGetAttributes(&fa, kernel);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  optin - (int)fa.sharedSizeBytes);
     if (e != cudaSuccess) return cuda_fail("cudaFuncSetAttribute", e, __FILE__, __LINE__);
+    mark_smem_limit_raised(reinterpret_cast<const void *>(kernel), dev);
     return 0;
 }
 

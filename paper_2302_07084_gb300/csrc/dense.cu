@@ -214,16 +214,18 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel(const double *__rest
 
 // Blocked Cholesky over many SMs (FP64), for the matrix sizes where the
 // one-CTA kernel is bound by a single SM's FP64 rate. Panels of kCholB rows:
-// chol_panel_kernel factors the diagonal block, R11^T R11 = A11, and solves
-// R11^T R12 = A12 for the panel's row block; chol_update_kernel (one CTA per
-// 16 x 16 upper tile) subtracts R12^T R12 from the trailing matrix. A is the
-// working copy (row-major, upper triangle significant) and ends as R.
+// the panel phase (chol_panel_body) factors the diagonal block,
+// R11^T R11 = A11, and solves R11^T R12 = A12 for the panel's row block; the
+// update phase (chol_update_body, one CTA per 16 x 16 upper tile) subtracts
+// R12^T R12 from the trailing matrix. A is the working copy (row-major, upper
+// triangle significant) and ends as R. Both phases of every panel run in one
+// cooperative launch (chol_coop_kernel), separated by grid barriers.
 //
 // The panel's row block is spread over ceil((c - k1) / 16) CTAs, 16 columns
 // each; every CTA factors the small diagonal block itself (identically), so
 // no CTA waits for another. Since other CTAs may still be reading A11 while
 // one has finished, R11 goes to a scratch block (written by CTA 0) and is
-// copied into A by the update kernel, or directly by a panel that runs as a
+// copied into A in the update phase, or directly by a panel that runs as a
 // single CTA.
 constexpr int kCholB = 16;
 
@@ -287,11 +289,6 @@ __device__ __forceinline__ void chol_panel_body(double *__restrict__ A, int c, i
         }
 }
 
-__global__ void __launch_bounds__(256) chol_panel_kernel(double *__restrict__ A, int c, int k0,
-                                                         int *__restrict__ status, double *__restrict__ r11) {
-    chol_panel_body(A, c, k0, status, r11, blockIdx.x, gridDim.x);
-}
-
 // r11 is read with ld.global.cg: in the cooperative launch it was written by
 // another CTA of the same launch, so it must not come through the read-only path.
 __device__ __forceinline__ void chol_update_body(double *__restrict__ A, int c, int k0, int k1, const double *r11,
@@ -319,11 +316,6 @@ __device__ __forceinline__ void chol_update_body(double *__restrict__ A, int c, 
         for (int t = 0; t < bs; ++t) a = fma(-ri[t][ti], rj[t][tj], a);
         A[(size_t)i * c + j] = a;
     }
-}
-
-__global__ void __launch_bounds__(256) chol_update_kernel(double *__restrict__ A, int c, int k0, int k1,
-                                                          const double *__restrict__ r11) {
-    chol_update_body(A, c, k0, k1, r11, blockIdx.y, blockIdx.x);
 }
 
 // All panels in one cooperative launch: the panel and update phases of each
@@ -354,7 +346,7 @@ __device__ __forceinline__ void grid_barrier(unsigned *bar, unsigned &target, in
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(256) chol_coop_kernel(double *__restrict__ A, int c, int *__restrict__ status,
+__global__ void __launch_bounds__(256, 1) chol_coop_kernel(double *__restrict__ A, int c, int *__restrict__ status,
                                                         double *__restrict__ r11, unsigned *__restrict__ bar) {
     unsigned target = 0;
     for (int k0 = 0; k0 < c; k0 += kCholB) {
@@ -537,7 +529,9 @@ __global__ void jacobi32_kernel(const double *__restrict__ R, int c, double *__r
     const int pairs = m / 2;
     const int pi = tid / kJacTPP, sub = tid % kJacTPP;
     // FP32 round-off floor of |a_p . a_q| / (|a_p| |a_q|) is about c * 2^-24
-    const float tol = 4.f * (float)c * 5.9604645e-8f;
+    // stop at cosines of 0.4 c ulp (at least 8 ulp): the FP64 refinement's first-order
+    // step needs the start's rotations this close where singular values are dense
+    const float tol = fmaxf(0.4f * (float)c, 8.f) * 5.9604645e-8f;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         float local_max = 0.f;
@@ -658,6 +652,24 @@ __host__ __device__ constexpr int jreg_stride() { return ((8 * E + 31) / 32) * 3
 // rounds per sweep of the order above for m (even) columns
 __host__ __device__ inline int jreg_rounds(int m) { return jorder_rounds(m); }
 
+// Paired FP32 arithmetic (fma.rn.f32x2 / mul.rn.f32x2, sm_100 and later):
+// one instruction for two lanes of a float2, each rounded as the scalar op.
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const uint64_t *>(&a)), "l"(*reinterpret_cast<const uint64_t *>(&b)),
+          "l"(*reinterpret_cast<const uint64_t *>(&c)));
+    return *reinterpret_cast<const float2 *>(&d);
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;"
+        : "=l"(d)
+        : "l"(*reinterpret_cast<const uint64_t *>(&a)), "l"(*reinterpret_cast<const uint64_t *>(&b)));
+    return *reinterpret_cast<const float2 *>(&d);
+}
+
 template <int E>
 __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__restrict__ R, int c,
                                                                double *__restrict__ Vout,
@@ -666,6 +678,7 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
                                                                int *__restrict__ sweeps_out) {
     constexpr int CP = 8 * E;            // padded column length
     constexpr int NQ = E / 2;            // float2 chunks per column and thread
+    static_assert(E % 2 == 0, "columns are held as float2 chunks");
     constexpr int ST = jreg_stride<E>(); // floats per exchange entry (= 16 mod 32: conflict-free float2)
     extern __shared__ float xb[];        // 2 G entries: column [CP], label at CP
     __shared__ float red[32];
@@ -674,37 +687,36 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = tid >> 3, sub = tid & 7;
     const bool real = g < G;             // groups past G only fill the last warp
-    float a0[E], a1[E];
+    // element 2 q + t of a column is component t of chunk q (rows 16 q + 2 sub + t)
+    float2 a0[NQ], a1[NQ];
     int lab0 = g, lab1 = g + G;
 #pragma unroll
-    for (int q = 0; q < NQ; ++q)
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-            const int i = 16 * q + 2 * sub + t, e = 2 * q + t;
-            a0[e] = real && lab0 < c && i < c ? (float)R[(size_t)lab0 * c + i] : 0.f;   // column lab0 of R^T
-            a1[e] = real && lab1 < c && i < c ? (float)R[(size_t)lab1 * c + i] : 0.f;
-        }
-    const float tol = 4.f * (float)c * 5.9604645e-8f;
+    for (int q = 0; q < NQ; ++q) {
+        const int i = 16 * q + 2 * sub;
+        const bool r0 = real && lab0 < c, r1 = real && lab1 < c;   // column lab of R^T
+        a0[q].x = r0 && i < c ? (float)R[(size_t)lab0 * c + i] : 0.f;
+        a0[q].y = r0 && i + 1 < c ? (float)R[(size_t)lab0 * c + i + 1] : 0.f;
+        a1[q].x = r1 && i < c ? (float)R[(size_t)lab1 * c + i] : 0.f;
+        a1[q].y = r1 && i + 1 < c ? (float)R[(size_t)lab1 * c + i + 1] : 0.f;
+    }
+    // stop at cosines of 0.4 c ulp (at least 8 ulp): the FP64 refinement's first-order
+    // step needs the start's rotations this close where singular values are dense
+    const float tol = fmaxf(0.4f * (float)c, 8.f) * 5.9604645e-8f;
     const int tz = jorder_levels(m);
     const int s_odd = m >> tz;           // set size the halving ends at
     float local_max = 0.f;
     int rec = 0;                         // record index of this round's group 0
 
-    auto put = [&](int entry, const float (&a)[E], int lab) {
+    auto put = [&](int entry, const float2 (&a)[NQ], int lab) {
         float *eb = xb + (size_t)entry * ST;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q)
-            *reinterpret_cast<float2 *>(eb + 16 * q + 2 * sub) = make_float2(a[2 * q], a[2 * q + 1]);
+        for (int q = 0; q < NQ; ++q) *reinterpret_cast<float2 *>(eb + 16 * q + 2 * sub) = a[q];
         if (sub == 0) reinterpret_cast<int *>(eb)[CP] = lab;
     };
-    auto take = [&](int entry, float (&a)[E], int &lab) {
+    auto take = [&](int entry, float2 (&a)[NQ], int &lab) {
         const float *eb = xb + (size_t)entry * ST;
 #pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-            const float2 x = *reinterpret_cast<const float2 *>(eb + 16 * q + 2 * sub);
-            a[2 * q] = x.x;
-            a[2 * q + 1] = x.y;
-        }
+        for (int q = 0; q < NQ; ++q) a[q] = *reinterpret_cast<const float2 *>(eb + 16 * q + 2 * sub);
         lab = reinterpret_cast<const int *>(eb)[CP];
     };
     // both columns of every group move (sources as group * 2 + slot)
@@ -724,13 +736,14 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
     // one rotation of the group's pair (every lane takes part in the shuffles),
     // recorded as (cos, sin) = (1, 0) when the pair is left as it is
     auto rotate = [&](bool active) {
-        float al = 0.f, be = 0.f, ga = 0.f;
+        float2 al2 = make_float2(0.f, 0.f), be2 = al2, ga2 = al2;
 #pragma unroll
-        for (int e = 0; e < E; ++e) {
-            al = fmaf(a0[e], a0[e], al);
-            be = fmaf(a1[e], a1[e], be);
-            ga = fmaf(a0[e], a1[e], ga);
+        for (int q = 0; q < NQ; ++q) {
+            al2 = f2_fma(a0[q], a0[q], al2);
+            be2 = f2_fma(a1[q], a1[q], be2);
+            ga2 = f2_fma(a0[q], a1[q], ga2);
         }
+        float al = al2.x + al2.y, be = be2.x + be2.y, ga = ga2.x + ga2.y;
 #pragma unroll
         for (int off = 1; off < 8; off <<= 1) {
             al += __shfl_xor_sync(0xffffffffu, al, off);
@@ -746,11 +759,12 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
                 const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
                 cs = rsqrtf(1.f + t * t);
                 sn = cs * t;
+                const float2 c2 = make_float2(cs, cs), s2 = make_float2(sn, sn), ms2 = make_float2(-sn, -sn);
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const float x = a0[e], y = a1[e];
-                    a0[e] = cs * x - sn * y;
-                    a1[e] = sn * x + cs * y;
+                for (int q = 0; q < NQ; ++q) {
+                    const float2 x = a0[q], y = a1[q];
+                    a0[q] = f2_fma(c2, x, f2_mul(ms2, y));   // cs x - sn y
+                    a1[q] = f2_fma(c2, y, f2_mul(s2, x));    // sn x + cs y
                 }
             }
         }
@@ -814,12 +828,13 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
         }
     }
     // right singular vectors of R: normalised columns of R^T W, by label
-    float n0 = 0.f, n1 = 0.f;
+    float2 n02 = make_float2(0.f, 0.f), n12 = n02;
 #pragma unroll
-    for (int e = 0; e < E; ++e) {
-        n0 = fmaf(a0[e], a0[e], n0);
-        n1 = fmaf(a1[e], a1[e], n1);
+    for (int q = 0; q < NQ; ++q) {
+        n02 = f2_fma(a0[q], a0[q], n02);
+        n12 = f2_fma(a1[q], a1[q], n12);
     }
+    float n0 = n02.x + n02.y, n1 = n12.x + n12.y;
 #pragma unroll
     for (int off = 1; off < 8; off <<= 1) {
         n0 += __shfl_xor_sync(0xffffffffu, n0, off);
@@ -831,9 +846,10 @@ __global__ void __launch_bounds__(32 * E, 1) jacobi_reg_kernel(const double *__r
         for (int q = 0; q < NQ; ++q)
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
-                const int i = 16 * q + 2 * sub + t, e = 2 * q + t;
-                if (i < c && lab0 < c) Vout[(size_t)i * c + lab0] = (double)(a0[e] * q0);
-                if (i < c && lab1 < c) Vout[(size_t)i * c + lab1] = (double)(a1[e] * q1);
+                const int i = 16 * q + 2 * sub + t;
+                const float x0 = t ? a0[q].y : a0[q].x, x1 = t ? a1[q].y : a1[q].x;
+                if (i < c && lab0 < c) Vout[(size_t)i * c + lab0] = (double)(x0 * q0);
+                if (i < c && lab1 < c) Vout[(size_t)i * c + lab1] = (double)(x1 * q1);
             }
     }
     if (tid == 0 && sweeps_out) *sweeps_out = sweep;
@@ -1125,8 +1141,11 @@ __global__ void svd_oa_fg_kernel(const double *__restrict__ P, const double *__r
             const double inv = 1.0 / ((sj - si) * (sj + si));
             const double ff = (sj * r1 + si * r2) * inv;
             const double gg = (si * r1 + sj * r2) * inv;
-            // outside the first-order regime this step only restores orthogonality
-            if (fabs(ff) <= 0.25 && fabs(gg) <= 0.25) {
+            // outside the first-order regime this step only restores orthogonality:
+            // the correction must be small against the pair's relative gap, or its
+            // second-order error (|f|^2 (s_i + s_j) / |s_i - s_j|) would exceed it
+            const double mf = fmax(fabs(ff), fabs(gg));
+            if (mf <= 0.25 && mf * (fabs(si) + fabs(sj)) <= 0.25 * fabs(sj - si)) {
                 f = ff;
                 g = gg;
             }
@@ -1134,6 +1153,262 @@ __global__ void svd_oa_fg_kernel(const double *__restrict__ P, const double *__r
     }
     F[e] = f;
     Gm[e] = g;
+}
+
+// The pairs the first-order step leaves (near-equal singular values, or a
+// start not yet close enough for their gap) keep off-diagonal entries in
+// T = U^T A V. They are resolved exactly: a two-sided Jacobi in FP64 on the
+// block of T over the indices K of such pairs (entries above 2^-42 max|s|),
+// each 2 x 2 block [t_ii t_ij; t_ji t_jj] diagonalised by a left and a right
+// plane rotation (a rotation that makes it symmetric, then the symmetric
+// Jacobi rotation), the left rotations also applied to the columns of U.
+// The rotation angles are taken in FP32 and the rotations renormalised in
+// FP64, so they are orthogonal to FP64 rounding (U stays orthonormal) and
+// leave at most ~1e-7 of a pair's off-diagonal entries, which the next sweep
+// removes. sigma_i = t_ii for i in K. T comes from the last refinement step
+// (before its update, which is below the threshold). Entries between K and
+// the rest are below the threshold and stay there (a rotation mixes two of
+// them).
+//
+// One CTA. Each sweep takes the pairs above the threshold at its start and
+// splits them into rounds of disjoint pairs (first-fit in (a, b) order, up to
+// 64 rounds and kClusterList pairs a pass; the rest go to the next pass); in a
+// round each warp takes a pair, all rows are rotated before all columns (left
+// and right rotations commute, and the pairs of a round share no row or
+// column, so the order of the pairs does not change the result). Sweeps until
+// no entry is above the threshold (at most kClusterSweeps).
+constexpr int kClusterSweeps = 16;
+constexpr int kClusterThreads = 256;
+constexpr int kClusterWarps = kClusterThreads / 32;
+constexpr int kClusterList = 1024;                 // pairs coloured in one pass
+constexpr int kClusterRowsPerLane = (kMaxSmemC + 31) / 32;
+
+// |x| > thr for thr >= 0 by the ordering of IEEE-754 bit patterns (integer
+// compares: FP64 instructions are slow on this GPU)
+__device__ __forceinline__ bool above(double x, long long thr_bits) {
+    return (__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll) > thr_bits;
+}
+
+// (c, s) from FP32 made a unit vector in FP64: multiplied by the series of
+// (1 + d)^-1/2 to second order, d = c^2 + s^2 - 1 (|d| ~ 1e-7, so the
+// third-order term is below FP64 rounding)
+__device__ __forceinline__ void unit_fp64(double &c, double &s) {
+    const double d = fma(c, c, fma(s, s, -1.0));
+    const double n = fma(d, fma(0.375, d, -0.5), 1.0);
+    c *= n;
+    s *= n;
+}
+
+// The rotations of one 2 x 2 block M = [taa tab; tba tbb]: left
+// L = [al be; -be al] = G J and right J = [cs sn; -sn cs], L^T M J diagonal up
+// to the FP32 angles. G = [cf -sf; sf cf] makes G^T M symmetric; J is the
+// symmetric Jacobi rotation of G^T M. inv scales the block to about unit size
+// for the FP32 arithmetic (a power of two).
+__device__ __forceinline__ void cluster_rotation(double taa, double tab, double tba, double tbb, double inv,
+                                                 double &al, double &be, double &cs, double &sn) {
+    const float x = (float)((taa + tbb) * inv), y = (float)((tba - tab) * inv);
+    const float h = hypotf(x, y);
+    const float cf = h > 0.f ? x / h : 1.f, sf = h > 0.f ? y / h : 0.f;
+    // G^T M = [p q'; q'' r]: q = (q' + q'') / 2, r - p, from the differences
+    const double d = tbb - taa, e = tab + tba;
+    const double rp = fma((double)cf, d, -(double)sf * e);
+    const double q = 0.5 * fma((double)cf, e, (double)sf * d);
+    float c32 = 1.f, s32 = 0.f;
+    const float qf = (float)(q * inv);
+    if (qf != 0.f) {
+        const float zeta = (float)(rp * inv) / (2.f * qf);
+        const float az = fabsf(zeta);
+        const float t = (zeta >= 0.f ? 1.f : -1.f) * (az > 1e18f ? 0.5f / az : 1.f / (az + sqrtf(1.f + zeta * zeta)));
+        c32 = rsqrtf(1.f + t * t);
+        s32 = c32 * t;
+    }
+    cs = c32;
+    sn = s32;
+    unit_fp64(cs, sn);
+    al = (double)(cf * c32 + sf * s32);
+    be = (double)(cf * s32 - sf * c32);
+    unit_fp64(al, be);
+}
+
+__global__ void __launch_bounds__(kClusterThreads) svd_cluster_kernel(const double *__restrict__ T, int c,
+                                                                     double *__restrict__ U,
+                                                                     double *__restrict__ sg) {
+    extern __shared__ double sT[];       // nK x nK block of T
+    constexpr int kWords = (kMaxSmemC + 31) / 32;
+    __shared__ int sK[kMaxSmemC];        // block index -> index of T
+    __shared__ int s_act[kMaxSmemC];
+    __shared__ uint32_t s_mask[kMaxSmemC][kWords];   // row a: bit b > a set for a pair left in the sweep
+    __shared__ unsigned long long s_used[kMaxSmemC]; // rounds of the pass that index a takes part in
+    __shared__ uint32_t s_list[kClusterList];        // round << 16 | a << 8 | b
+    __shared__ uint32_t s_round[kMaxSmemC / 2];      // a << 8 | b
+    __shared__ double s_rcs[kMaxSmemC / 2][2];       // each round pair's right rotation (cs, sn)
+    __shared__ int s_rgo[kMaxSmemC / 2];             // ... and whether it rotated
+    __shared__ long long red[kClusterWarps];
+    __shared__ int s_nK, s_any, s_np, s_rounds, s_nr;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // max |sigma| by the integer order of the bit patterns
+    long long mb = 0;
+    for (int i = tid; i < c; i += blockDim.x) mb = max(mb, __double_as_longlong(sg[i]) & 0x7FFFFFFFFFFFFFFFll);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mb = max(mb, __shfl_xor_sync(0xffffffffu, mb, off));
+    if (lane == 0) red[warp] = mb;
+    for (int i = tid; i < c; i += blockDim.x) s_act[i] = 0;
+    __syncthreads();
+    mb = 0;
+    for (int w = 0; w < kClusterWarps; ++w) mb = max(mb, red[w]);
+    if (mb == 0 || mb >= 0x7FF0000000000000ll) return;   // a zero matrix, or not finite
+    const double smax = __longlong_as_double(mb);
+    const double thr = 0x1p-42 * smax;
+    const long long thr_bits = __double_as_longlong(thr);
+    const long long ex = min((mb >> 52) & 0x7FF, 2045ll);
+    const double inv = __longlong_as_double((2046ll - ex) << 52);   // 2^(1023 - exponent of smax)
+    // indices with an entry above the threshold in their row or column (a warp
+    // per row, two rows at a time, every load of the two rows issued at once)
+    for (int i0 = 2 * warp; i0 < c; i0 += 2 * kClusterWarps) {
+        double v[2][kClusterRowsPerLane];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int q = 0; q < kClusterRowsPerLane; ++q) {
+                const int i = i0 + h, j = lane + 32 * q;
+                v[h][q] = i < c && j < c ? T[(size_t)i * c + j] : 0.0;
+            }
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = i0 + h;
+            bool rowbig = false;
+#pragma unroll
+            for (int q = 0; q < kClusterRowsPerLane; ++q) {
+                const int j = lane + 32 * q;
+                if (i < c && j < c && j != i && above(v[h][q], thr_bits)) {
+                    s_act[j] = 1;
+                    rowbig = true;
+                }
+            }
+            if (__any_sync(0xffffffffu, rowbig) && lane == 0) s_act[i] = 1;
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int n = 0;
+        for (int j0 = 0; j0 < c; j0 += 32) {
+            const int j = j0 + lane;
+            const bool f = j < c && s_act[j];
+            const unsigned bal = __ballot_sync(0xffffffffu, f);
+            if (f) sK[n + __popc(bal & ((1u << lane) - 1u))] = j;
+            n += __popc(bal);
+        }
+        if (lane == 0) s_nK = n;
+    }
+    __syncthreads();
+    const int nK = s_nK;
+    if (nK == 0) return;
+    for (int a = warp; a < nK; a += kClusterWarps)
+        for (int b = lane; b < nK; b += 32) sT[a * nK + b] = T[(size_t)sK[a] * c + sK[b]];
+    const int words = (nK + 31) / 32;
+    for (int sweep = 0; sweep < kClusterSweeps; ++sweep) {
+        // the pairs above the threshold at the start of the sweep (a warp per row)
+        if (tid == 0) s_any = 0;
+        __syncthreads();
+        for (int a = warp; a < nK; a += kClusterWarps)
+            for (int w = 0; w < words; ++w) {
+                const int b = 32 * w + lane;
+                const bool big = b > a && b < nK && (above(sT[a * nK + b], thr_bits) || above(sT[b * nK + a], thr_bits));
+                const unsigned m = __ballot_sync(0xffffffffu, big);
+                if (lane == 0) {
+                    s_mask[a][w] = m;
+                    if (m) s_any = 1;
+                }
+            }
+        __syncthreads();
+        if (!s_any) break;
+        for (;;) {   // passes: up to 64 rounds of disjoint pairs each
+            if (tid == 0) {
+                for (int a = 0; a < nK; ++a) s_used[a] = 0ull;
+                int np = 0, rounds = 0;
+                for (int a = 0; a < nK && np < kClusterList; ++a)
+                    for (int w = 0; w < words && np < kClusterList; ++w) {
+                        uint32_t m = s_mask[a][w];
+                        while (m && np < kClusterList) {
+                            const int bit = __ffs(m) - 1;
+                            m &= m - 1u;
+                            const int b = 32 * w + bit;
+                            const unsigned long long fr = ~(s_used[a] | s_used[b]);
+                            if (fr == 0ull) continue;   // stays for the next pass
+                            const int r = __ffsll((long long)fr) - 1;
+                            s_used[a] |= 1ull << r;
+                            s_used[b] |= 1ull << r;
+                            s_mask[a][w] &= ~(1u << bit);
+                            s_list[np++] = ((uint32_t)r << 16) | ((uint32_t)a << 8) | (uint32_t)b;
+                            rounds = max(rounds, r + 1);
+                        }
+                    }
+                s_np = np;
+                s_rounds = rounds;
+            }
+            __syncthreads();
+            const int np = s_np, rounds = s_rounds;
+            if (np == 0) break;
+            for (int r = 0; r < rounds; ++r) {
+                if (tid == 0) s_nr = 0;
+                __syncthreads();
+                for (int k = tid; k < np; k += blockDim.x)
+                    if ((int)(s_list[k] >> 16) == r) s_round[atomicAdd(&s_nr, 1)] = s_list[k] & 0xFFFFu;
+                __syncthreads();
+                const int nr = s_nr;
+                // rows of the block and columns of U, a warp per pair (rows disjoint)
+                for (int k = warp; k < nr; k += kClusterWarps) {
+                    const int a = (int)(s_round[k] >> 8), b = (int)(s_round[k] & 0xFFu);
+                    const double taa = sT[a * nK + a], tab = sT[a * nK + b], tba = sT[b * nK + a],
+                                 tbb = sT[b * nK + b];
+                    const bool go = above(tab, thr_bits) || above(tba, thr_bits);
+                    if (lane == 0) s_rgo[k] = go;
+                    if (!go) continue;
+                    double al, be, cs, sn;
+                    cluster_rotation(taa, tab, tba, tbb, inv, al, be, cs, sn);
+                    for (int k2 = lane; k2 < nK; k2 += 32) {   // rows a, b: L^T
+                        const double u = sT[a * nK + k2], v = sT[b * nK + k2];
+                        sT[a * nK + k2] = al * u - be * v;
+                        sT[b * nK + k2] = be * u + al * v;
+                    }
+                    const int ia = sK[a], ib = sK[b];
+                    double uu[kClusterRowsPerLane], vv[kClusterRowsPerLane];
+#pragma unroll
+                    for (int q = 0; q < kClusterRowsPerLane; ++q) {   // columns ia, ib of U: U L
+                        const int k2 = lane + 32 * q;
+                        uu[q] = k2 < c ? U[(size_t)k2 * c + ia] : 0.0;
+                        vv[q] = k2 < c ? U[(size_t)k2 * c + ib] : 0.0;
+                    }
+#pragma unroll
+                    for (int q = 0; q < kClusterRowsPerLane; ++q) {
+                        const int k2 = lane + 32 * q;
+                        if (k2 < c) {
+                            U[(size_t)k2 * c + ia] = al * uu[q] - be * vv[q];
+                            U[(size_t)k2 * c + ib] = be * uu[q] + al * vv[q];
+                        }
+                    }
+                    if (lane == 0) {
+                        s_rcs[k][0] = cs;
+                        s_rcs[k][1] = sn;
+                    }
+                }
+                __syncthreads();
+                // columns of the block, a warp per pair (columns disjoint): J
+                for (int k = warp; k < nr; k += kClusterWarps) {
+                    if (!s_rgo[k]) continue;
+                    const int a = (int)(s_round[k] >> 8), b = (int)(s_round[k] & 0xFFu);
+                    const double cs = s_rcs[k][0], sn = s_rcs[k][1];
+                    for (int k2 = lane; k2 < nK; k2 += 32) {
+                        const double u = sT[k2 * nK + a], v = sT[k2 * nK + b];
+                        sT[k2 * nK + a] = cs * u - sn * v;
+                        sT[k2 * nK + b] = sn * u + cs * v;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+    }
+    for (int a = tid; a < nK; a += blockDim.x) sg[sK[a]] = sT[a * nK + a];
 }
 
 // sigma sorted descending; U_R[:, rank_j] = sign(s_j) U[:, j].
@@ -1405,6 +1680,50 @@ static int dgemm_small(const double *A, bool ta, const double *B, bool tb, const
     return 0;
 }
 
+// FP64 scratch of the refinement: ten c x c matrices, sigma (c) and the
+// norm partials (4 kOaParts).
+struct SvdScratch {
+    double *U, *U2, *V, *V2, *W, *T, *P, *Q, *F, *Gm, *sg, *dl;
+};
+
+// Refines the FP32 start (sc.U, sc.V) into the SVD of R in FP64 and writes
+// U_R and sigma (sorted descending).
+static int svd_refine_finish(const double *R, int c, SvdScratch sc, double *U_R, double *sigma, cudaStream_t st) {
+    const size_t cc = (size_t)c * c;
+    double *U = sc.U, *U2 = sc.U2, *V = sc.V, *V2 = sc.V2;
+    // FP64 refinement of the SVD of R itself (quadratic convergence; the FP32
+    // start may be loose in directions FP32 cannot resolve, hence four steps)
+    for (int it = 0; it < 4; ++it) {
+        // P = U^T U and Q = V^T V (I - P, I - Q below)
+        LNE_TRY(dgemm_small(U, true, U, false, nullptr, sc.P, c, st, V, V, nullptr, sc.Q));
+        LNE_TRY(dgemm_small(R, false, V, false, nullptr, sc.W, c, st));   // W = R V
+        LNE_TRY(dgemm_small(U, true, sc.W, false, nullptr, sc.T, c, st)); // T = U^T R V
+        {
+            LNE_TRACE("svd_oa_update", st);
+            svd_oa_norms_kernel<<<kOaParts, 256, 0, st>>>(sc.P, sc.Q, sc.T, c, sc.sg, sc.dl);
+            LNE_LAUNCH_CHECK();
+            svd_oa_fg_kernel<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(sc.P, sc.Q, sc.T, c, sc.sg,
+                                                                                  sc.dl, sc.F, sc.Gm);
+            LNE_LAUNCH_CHECK();
+        }
+        LNE_TRY(dgemm_small(U, false, sc.F, false, U, U2, c, st, V, sc.Gm, V, V2));   // U2 = U + U F, V2 = V + V G
+        std::swap(U, U2);
+        std::swap(V, V2);
+    }
+    {
+        LNE_TRACE("svd_cluster", st);
+        LNE_TRY(allow_dynamic_smem(svd_cluster_kernel));
+        svd_cluster_kernel<<<1, kClusterThreads, sizeof(double) * cc, st>>>(sc.T, c, U, sc.sg);
+        LNE_LAUNCH_CHECK();
+    }
+    {
+        LNE_TRACE("svd_finish", st);
+        svd_finish_kernel<<<1, 256, 0, st>>>(U, sc.sg, c, U_R, sigma);
+        LNE_LAUNCH_CHECK();
+    }
+    return 0;
+}
+
 int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma, cudaStream_t st) {
     if (c > kMaxSmemC) return fail(LNE_ERR_UNSUPPORTED, "small SVD supports c <= 160");
     double *U = nullptr, *U2 = nullptr, *V = nullptr, *V2 = nullptr, *W = nullptr, *T = nullptr, *P = nullptr,
@@ -1436,30 +1755,8 @@ int small_svd(Workspace &ws, const double *R, int c, double *U_R, double *sigma,
         LNE_TRACE("jacobi32", st);
         LNE_TRY(launch_jacobi(R, c, U, V, jrot, jlab, sweeps, st));
     }
-    // FP64 refinement of the SVD of R itself (quadratic convergence; the FP32
-    // start may be loose in directions FP32 cannot resolve, hence four steps)
-    for (int it = 0; it < 4; ++it) {
-        // P = U^T U and Q = V^T V (I - P, I - Q below)
-        LNE_TRY(dgemm_small(U, true, U, false, nullptr, P, c, st, V, V, nullptr, Q));
-        LNE_TRY(dgemm_small(R, false, V, false, nullptr, W, c, st));  // W = R V
-        LNE_TRY(dgemm_small(U, true, W, false, nullptr, T, c, st));   // T = U^T R V
-        {
-            LNE_TRACE("svd_oa_update", st);
-            svd_oa_norms_kernel<<<kOaParts, 256, 0, st>>>(P, Q, T, c, sg, dl);
-            LNE_LAUNCH_CHECK();
-            svd_oa_fg_kernel<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(P, Q, T, c, sg, dl, F, Gm);
-            LNE_LAUNCH_CHECK();
-        }
-        LNE_TRY(dgemm_small(U, false, F, false, U, U2, c, st, V, Gm, V, V2));   // U2 = U + U F, V2 = V + V G
-        std::swap(U, U2);
-        std::swap(V, V2);
-    }
-    {
-        LNE_TRACE("svd_finish", st);
-        svd_finish_kernel<<<1, 256, 0, st>>>(U, sg, c, U_R, sigma);
-        LNE_LAUNCH_CHECK();
-    }
-    return 0;
+    SvdScratch sc{U, U2, V, V2, W, T, P, Q, F, Gm, sg, dl};
+    return svd_refine_finish(R, c, sc, U_R, sigma, st);
 }
 
 int sign_fix_embed(Workspace &ws, float *U, int64_t n, int d, int64_t ld, const double *sigma, float *X,
@@ -1552,19 +1849,7 @@ extern "C" int lne_svd_small_noalloc(const double *R_dev, int32_t c, double *U_d
     float2 *jrot = reinterpret_cast<float2 *>(base + 10 * kNoAllocMat + kNoAllocMaxC + 128);
     uint32_t *jlab = reinterpret_cast<uint32_t *>(jrot + kNoAllocRec);
     LNE_TRY(launch_jacobi(R_dev, c, U, V, jrot, jlab, sweeps, st));
-    for (int it = 0; it < 4; ++it) {
-        LNE_TRY(dgemm_small(U, true, U, false, nullptr, P, c, st, V, V, nullptr, Q));
-        LNE_TRY(dgemm_small(R_dev, false, V, false, nullptr, W, c, st));
-        LNE_TRY(dgemm_small(U, true, W, false, nullptr, T, c, st));
-        svd_oa_norms_kernel<<<kOaParts, 256, 0, st>>>(P, Q, T, c, sg, dl);
-        LNE_LAUNCH_CHECK();
-        svd_oa_fg_kernel<<<(unsigned)ceil_div((int64_t)cc, 256), 256, 0, st>>>(P, Q, T, c, sg, dl, F, Gm);
-        LNE_LAUNCH_CHECK();
-        LNE_TRY(dgemm_small(U, false, F, false, U, U2, c, st, V, Gm, V, V2));
-        std::swap(U, U2);
-        std::swap(V, V2);
-    }
-    svd_finish_kernel<<<1, 256, 0, st>>>(U, sg, c, U_dev, sigma_dev);
-    LNE_LAUNCH_CHECK();
+    SvdScratch sc{U, U2, V, V2, W, T, P, Q, F, Gm, sg, dl};
+    LNE_TRY(svd_refine_finish(R_dev, c, sc, U_dev, sigma_dev, st));
     return LNE_OK;
 }

@@ -109,6 +109,44 @@ def test_svd_small_fp64_accuracy(ctx, c, cond):
     assert np.max(np.abs(off)) <= 1e-12 * ref[0] ** 2, np.max(np.abs(off)) / ref[0] ** 2
 
 
+def _spectrum_case(kind, c, seed):
+    """Upper-triangular factors whose spectra have the structure of a
+    randomized SVD's factor on a NetMF matrix: a few large values over a dense
+    tail (relative gaps down to 1e-6), or tight clusters."""
+    rng = np.random.default_rng(seed)
+    if kind == "dense_tail":
+        s = np.concatenate([np.geomspace(1500.0, 100.0, 16), rng.uniform(40.0, 100.0, c - 16)])
+    elif kind == "cluster":   # half the values within 1e-3 of one another
+        s = np.concatenate([np.geomspace(10.0, 2.0, c // 2), 1.0 + 1e-3 * rng.random(c - c // 2)])
+    else:                     # equal values in three groups, some within 1e-9
+        s = np.repeat([3.0, 2.0, 1.0], c // 3 + 1)[:c] * (1.0 + 1e-9 * rng.random(c))
+    s = np.sort(s)[::-1]
+    Ua, _ = np.linalg.qr(rng.standard_normal((c, c)))
+    Vb, _ = np.linalg.qr(rng.standard_normal((c, c)))
+    return np.triu(np.linalg.qr((Ua * s) @ Vb.T)[1])
+
+
+@pytest.mark.parametrize("kind,c,seed", [("dense_tail", 144, 0), ("dense_tail", 144, 2), ("dense_tail", 128, 0),
+                                         ("dense_tail", 160, 1), ("cluster", 64, 1), ("cluster", 144, 3),
+                                         ("groups", 48, 4)])
+def test_svd_small_dense_and_clustered_spectra(ctx, kind, c, seed):
+    """The same FP64 bar where singular values are dense or clustered: the
+    first-order refinement steps are guarded by each pair's relative gap, and
+    the pairs they leave are resolved by the exact FP64 two-sided Jacobi on
+    T = U^T R V."""
+    R = _spectrum_case(kind, c, seed)
+    U, sig = ctx.svd_small(torch.as_tensor(R).cuda())
+    U, sig = to_np(U), to_np(sig)
+    ref = np.linalg.svd(R, compute_uv=False)
+    assert np.all(np.diff(sig) <= 0)
+    np.testing.assert_allclose(sig, ref, rtol=1e-12)
+    orth = np.max(np.abs(U.T @ U - np.eye(c)))
+    assert orth <= 1e-12, orth
+    B = U.T @ R @ R.T @ U
+    off = B - np.diag(np.diag(B))
+    assert np.max(np.abs(off)) <= 1e-12 * ref[0] ** 2, np.max(np.abs(off)) / ref[0] ** 2
+
+
 def _rsvd_compare(ctx, indptr, indices, data, d, p_os, q, seed):
     ref = oracle.fast_randomized_svd(indptr, indices, data, d, q, p_os, seed)
     p = make_params(1, [1.0], 1.0, d=d, oversample=p_os, q=q, seed=seed)

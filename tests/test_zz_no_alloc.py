@@ -15,7 +15,10 @@ def _triangular(c, cond, seed):
     rng = np.random.default_rng(seed)
     Ua, _ = np.linalg.qr(rng.standard_normal((c, c)))
     Vb, _ = np.linalg.qr(rng.standard_normal((c, c)))
-    s = np.geomspace(1.0, 1.0 / cond, c)
+    if cond == "dense_tail":   # a dense tail of singular values: the exact cluster step runs
+        s = np.sort(np.concatenate([np.geomspace(1500.0, 100.0, 16), rng.uniform(40.0, 100.0, c - 16)]))[::-1]
+    else:
+        s = np.geomspace(1.0, 1.0 / cond, c)
     return np.triu(np.linalg.qr((Ua * s) @ Vb.T)[1])
 
 
@@ -26,8 +29,10 @@ def test_noalloc_small_svd_matches_allocating_entry_point():
     try:
         # 144 and 48: the register-resident Jacobi; 33 (odd): its padding
         # column; 151 and 160 (the top of the fixed array): the FP32
-        # shared-memory Jacobi taken above 144 columns
-        for c, cond, seed in [(144, 1e4, 1), (48, 1e2, 2), (33, 1e2, 4), (151, 1e3, 3), (160, 1e3, 5)]:
+        # shared-memory Jacobi taken above 144 columns; a dense tail of
+        # singular values: the refinement's exact cluster step
+        for c, cond, seed in [(144, 1e4, 1), (48, 1e2, 2), (33, 1e2, 4), (151, 1e3, 3), (160, 1e3, 5),
+                              (144, "dense_tail", 0)]:
             R = torch.as_tensor(_triangular(c, cond, seed)).cuda()
             U_ref, s_ref = ctx.svd_small(R)
             U_ref, s_ref = U_ref.cpu().numpy(), s_ref.cpu().numpy()
