@@ -150,6 +150,19 @@ typedef struct lne_ctx lne_ctx;
                                     lne_sparsifier_counts then returns (x, y, r, count) entries.
                                     Any n with 2 ceil(log2 n) + 4 <= 64; no edge downsampling.
                                     0 (default): the paper's sampler */
+#define LNE_OPT_SPMM_VBLOCK  7   /* column blocking of the CSR products with the sparsifier
+                                    (lne_rsvd, lne_embed, lne_spmm): the columns are taken in
+                                    vertex blocks [b 2^s, (b + 1) 2^s), one block's partial
+                                    product added to Y at a time in block order, so the dense
+                                    operand rows one block gathers are a bounded region.
+                                    0 (default): when the operand (n x c) does not fit in L2,
+                                    with blocks of at most 2.5 times L2 (the measured best on
+                                    a 10M-vertex graph: 10% off its products); -1: never;
+                                    s in 1..30: blocks of 2^s
+                                    vertices. Needs columns sorted within rows (a matrix with
+                                    unsorted rows is multiplied unblocked). The sum order per
+                                    entry differs from the unblocked product (block by block):
+                                    both are within the FP32 bound */
 
 /* Create a context on CUDA device `device`. The context owns its workspace. */
 int lne_create(lne_ctx **out, int device);

@@ -202,6 +202,7 @@ struct lne_ctx {
     lne::PropBatchGraph *prop_graph = nullptr;
     int tune_workers = 4;
     int dense_mode = 0;
+    int vblock = 0;   // LNE_OPT_SPMM_VBLOCK
     int stratified = 0;
     std::vector<std::unique_ptr<lne::TuneWorker>> workers;
     lne::Surrogate surrogate;
@@ -355,6 +356,12 @@ int lne_set_option(lne_ctx *ctx, int option, int64_t value) {
                                          "SpMM column block must be 0 (timed), -1 (none) or a multiple of 4 up to 1024"));
         ctx->spmm_tune.forced_block = (int)value;
         ctx->spmm_tune.best.clear();
+        return LNE_OK;
+    }
+    if (option == LNE_OPT_SPMM_VBLOCK) {
+        if (value < -1 || value > 30)
+            return finish(ctx, lne::fail(LNE_ERR_INVALID, "vertex block must be 0 (auto), -1 (off) or a shift 1..30"));
+        ctx->vblock = (int)value;
         return LNE_OK;
     }
     if (option == LNE_OPT_DENSE_PRODUCT) {
@@ -580,10 +587,17 @@ int lne_spmm(lne_ctx *ctx, const lne_csr *M, const void *X_dev, int64_t ldx, int
         v.indptr = M->indptr;
         v.indices = M->indices;
         v.data = M->data;
-        if (precision == LNE_PREC_BF16_MIXED)
+        // column blocks by vertex ranges when the operand does not fit in L2
+        // (or as the option forces); matrices with unsorted rows go unblocked
+        lne::VBlocks vbs;
+        const int shift = lne::vblock_shift_for(ctx->vblock, v.n, c, precision == LNE_PREC_BF16_MIXED ? 2 : 4);
+        bool ok = false;
+        if (shift > 0 && v.nnz > 0) rc = lne::vblocks_build(ctx->ws, v, shift, &vbs, &ok, as_stream(stream));
+        if (ok) v.vb = &vbs;
+        if (rc == 0 && precision == LNE_PREC_BF16_MIXED)
             rc = lne::spmm_bf16(ctx->ws, v, static_cast<const __nv_bfloat16 *>(X_dev), ldx, c, Y_dev, ldy, nullptr,
                                 as_stream(stream));
-        else
+        else if (rc == 0)
             rc = lne::spmm(ctx->ws, v, static_cast<const float *>(X_dev), ldx, c, Y_dev, ldy, as_stream(stream));
     }
     return finish(ctx, rc);
@@ -619,6 +633,7 @@ int lne_rsvd(lne_ctx *ctx, const lne_csr *M, const lne_params *p, float *U_dev, 
         v.indptr = M->indptr;
         v.indices = M->indices;
         v.data = M->data;
+        v.vblock = ctx->vblock;
         rc = lne::rsvd(ctx->ws, v, p->d, oversample_of(p), p->q, p->seed, p->precision, U_dev, sigma_dev, X0_dev,
                        as_stream(stream), sketch_of(p));
     }
@@ -677,8 +692,10 @@ int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_de
     float *X0 = nullptr;
     if (rc == 0) rc = ctx->ws.get("embed.x0", (size_t)g->n * p->d, &X0);
     if (rc == 0) {
-        rc = lne::rsvd(ctx->ws, lne::product_view(M, ctx->dense_mode, p->d + oversample_of(p)), p->d, oversample_of(p), p->q, p->seed,
-                       p->precision, nullptr, nullptr, X0, st, sketch_of(p));
+        lne::CsrView mv = lne::product_view(M, ctx->dense_mode, p->d + oversample_of(p));
+        mv.vblock = ctx->vblock;
+        rc = lne::rsvd(ctx->ws, mv, p->d, oversample_of(p), p->q, p->seed, p->precision, nullptr, nullptr, X0, st,
+                       sketch_of(p));
     }
     if (rc == 0)
         rc = lne::propagate(ctx->ws, gv, p->d, p->k, p->theta, p->mu, p->precision, X0, X_dev, nullptr, nullptr,

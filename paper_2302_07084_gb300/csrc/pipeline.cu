@@ -89,9 +89,19 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
     const float *a_hi = nullptr, *a_lo = nullptr;
     const bool dense_tc = M.dense && !bf16 && (sketch.kind == LNE_SKETCH_GAUSSIAN || q > 0);
     if (dense_tc) LNE_TRY(dense_tc_prepare(ws, M.dense, M.dense_ld, &a_hi, &a_lo, st));
+    // CSR products whose operand does not fit in L2 go by vertex blocks of
+    // the columns (built once for the q + 1 products)
+    CsrView Mb = M;
+    VBlocks vbs;
+    if (!dense_tc) {
+        const int shift = vblock_shift_for(M.vblock, n, c, bf16 ? 2 : 4);
+        bool ok = false;
+        if (shift > 0) LNE_TRY(vblocks_build(ws, M, shift, &vbs, &ok, st));
+        if (ok) Mb.vb = &vbs;
+    }
     auto mprod = [&](const float *X, float *Y) -> int {
         if (dense_tc) return dense_tc_spmm(ws, a_hi, a_lo, M.dense_ld, n, X, c, c, Y, c, st);
-        return spmm(ws, M, X, c, c, Y, c, st);
+        return spmm(ws, Mb, X, c, c, Y, c, st);
     };
     // Algorithm 4: Omega = randn(n, d+s); Y = M Omega. The sparse sign Omega
     // (Sec. 3.2's cheaper alternative) is applied without being formed; its
@@ -106,7 +116,7 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
         LNE_TRY(gaussian_sketch(n, c, seed, Om, c, st));
         if (bf16) {
             LNE_TRY(to_bf16(Om, Xh, n * c, st));
-            LNE_TRY(spmm_bf16(ws, M, Xh, c, c, Ya, c, nullptr, st));
+            LNE_TRY(spmm_bf16(ws, Mb, Xh, c, c, Ya, c, nullptr, st));
         } else {
             LNE_TRY(mprod(Om, Ya));
         }
@@ -118,7 +128,7 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
         LNE_TRY(cholqr1(ws, Ya, n, c, c, Yb, c, st));
         if (bf16) {
             LNE_TRY(to_bf16(Yb, Xh, n * c, st));
-            LNE_TRY(spmm_bf16(ws, M, Xh, c, c, Ya, c, nullptr, st));
+            LNE_TRY(spmm_bf16(ws, Mb, Xh, c, c, Ya, c, nullptr, st));
         } else {
             LNE_TRY(mprod(Yb, Ya));
         }

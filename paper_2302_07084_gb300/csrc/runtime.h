@@ -59,6 +59,19 @@ struct GraphView {
 // workspace ("wg.*"); no-op for unweighted graphs. Synchronises.
 int prepare_weighted(Workspace &ws, GraphView *g, cudaStream_t st);
 
+// Column blocks of a CSR matrix (columns sorted within rows) by vertex ranges
+// [b << shift, (b + 1) << shift): row i's nonzeros in block b are positions
+// seg[b n + i] .. seg[(b + 1) n + i] of the row; V[b (n + 1) + i] is the
+// exclusive prefix sum of those segment lengths over rows (V[b (n + 1) + n]
+// = nnz[b]). Built by vblocks_build; products with a CSR view that carries it
+// go block by block, so the operand rows a block gathers are a bounded region.
+struct VBlocks {
+    int shift = 0, nb = 0;
+    const uint32_t *seg = nullptr;   // (nb + 1) x n
+    const int64_t *V = nullptr;      // nb x (n + 1)
+    std::vector<int64_t> nnz;        // per block
+};
+
 struct CsrView {
     int64_t n = 0;
     int64_t nnz = 0;
@@ -69,7 +82,16 @@ struct CsrView {
     // dense_ld), when the products should use it instead of the CSR
     const float *dense = nullptr;
     int64_t dense_ld = 0;
+    // column blocking of the CSR products: 0 = when the operand does not fit
+    // in L2, -1 = never, s > 0 = blocks of 2^s vertices; vb = the blocks in use
+    int vblock = 0;
+    const VBlocks *vb = nullptr;
 };
+// the block shift for a product with n x c operand rows of elem_bytes each
+// (0 = no blocking) and the block structure of M (ok = false when M has
+// unsorted rows or a single block)
+int vblock_shift_for(int mode, int64_t n, int c, int elem_bytes);
+int vblocks_build(Workspace &ws, const CsrView &M, int shift, VBlocks *vb, bool *ok, cudaStream_t st);
 
 // Host-derived constants of the sampler (Algorithm 3 with the readings of the
 // window draw, the per-arc Bernoulli and the Philox stream layout).

@@ -155,13 +155,15 @@ __device__ __forceinline__ float4 load4(const __nv_bfloat16 *__restrict__ row, i
                        __uint_as_float(raw.y << 16), __uint_as_float(raw.y & 0xffff0000u));
 }
 
-template <int NV, bool WEIGHTED, typename TX>
+// STREAM: the matrix, read once, goes through L2 with the evict-first
+// (streaming) policy and leaves the gathered operand rows their place
+template <int NV, bool WEIGHTED, typename TX, bool STREAM = false>
 __device__ __forceinline__ void gather4(const int32_t *__restrict__ indices, const float *__restrict__ vals,
                                         int64_t p, int cnt, const TX *__restrict__ X, int64_t ldx, int c4,
                                         int lane, Acc4<NV> &acc) {
-    const int col = lane < cnt ? __ldg(indices + p + lane) : 0;
+    const int col = lane < cnt ? (STREAM ? __ldcs(indices + p + lane) : __ldg(indices + p + lane)) : 0;
     float v = 0.f;
-    if (WEIGHTED) v = lane < cnt ? __ldg(vals + p + lane) : 0.f;
+    if (WEIGHTED) v = lane < cnt ? (STREAM ? __ldcs(vals + p + lane) : __ldg(vals + p + lane)) : 0.f;
 #pragma unroll 4
     for (int k = 0; k < cnt; ++k) {
         const int ck = __shfl_sync(0xffffffffu, col, k);
@@ -240,7 +242,9 @@ __device__ __forceinline__ void st4_bf16(__nv_bfloat16 *p, float4 v) {
 // The epilogue on four consecutive columns 4q..4q+3 of row i, with 16-byte
 // loads and stores (every operand is 16-byte aligned, leading dimensions are
 // multiples of 4); per element the same FMA chain as a scalar epilogue.
-template <int NV>
+// STREAM: E1 is read and Y written with the evict-first (streaming) policy
+// (the column-blocked product's running sum, touched once per block)
+template <int NV, bool STREAM = false>
 __device__ __forceinline__ void epilogue4(int64_t i, int64_t deg, const Acc4<NV> &acc, int lane, int c4,
                                           float *__restrict__ Y, int64_t ldy, const SpmmEpilogue &ep) {
     float rs = ep.alpha;
@@ -253,10 +257,15 @@ __device__ __forceinline__ void epilogue4(int64_t i, int64_t deg, const Acc4<NV>
         const int64_t yo = i * ldy + 4 * q;
         const float4 a = acc.v[t];
         float4 o = make_float4(rs * a.x, rs * a.y, rs * a.z, rs * a.w);
-        if (ep.E1) o = fma4(ep.b1_col ? ld4(ep.b1_col + 4 * q) : splat4(ep.b1), ld4(ep.E1 + e), o);
+        if (ep.E1)
+            o = fma4(ep.b1_col ? ld4(ep.b1_col + 4 * q) : splat4(ep.b1),
+                     STREAM ? __ldcs(reinterpret_cast<const float4 *>(ep.E1 + e)) : ld4(ep.E1 + e), o);
         if (ep.E2) o = fma4(splat4(ep.b2), ld4(ep.E2 + e), o);
         if (ep.E3) o = fma4(splat4(ep.b3), ld4(ep.E3 + e), o);
-        if (ep.store) st4(Y + yo, o);
+        if (ep.store) {
+            if (STREAM) __stcs(reinterpret_cast<float4 *>(Y + yo), o);
+            else st4(Y + yo, o);
+        }
         if (ep.Yb) st4_bf16(ep.Yb + yo, o);
         if (ep.F) {
             const float4 f = fma4(ep.gamma_col ? ld4(ep.gamma_col + 4 * q) : splat4(ep.gamma), o, ld4(ep.F + e));
@@ -280,13 +289,19 @@ __device__ __forceinline__ int64_t row_of(const int64_t *__restrict__ indptr, in
     return lo;
 }
 
-template <int NV, bool WEIGHTED, typename TX, int LG = 32>
+// VB (one vertex block of a column-blocked product): indptr holds the
+// block's virtual row offsets V (prefix sums of the rows' segment lengths);
+// row r's segment starts at indptr0[r] + segb[r] of indices / vals, so
+// position p of the row maps to p + indptr0[r] + segb[r] - V[r].
+template <int NV, bool WEIGHTED, typename TX, int LG = 32, bool VB = false>
 __global__ void __launch_bounds__(256) spmm_merge_kernel(int64_t n, int64_t nnz, const int64_t *__restrict__ indptr,
                                                          const int32_t *__restrict__ indices,
                                                          const float *__restrict__ vals, const TX *__restrict__ X,
                                                          int64_t ldx, int c4, float *__restrict__ Y, int64_t ldy,
                                                          SpmmEpilogue ep, int64_t W, int64_t nwarps,
-                                                         float4 *__restrict__ carry, int64_t *__restrict__ carry_row) {
+                                                         float4 *__restrict__ carry, int64_t *__restrict__ carry_row,
+                                                         const int64_t *__restrict__ indptr0 = nullptr,
+                                                         const uint32_t *__restrict__ segb = nullptr) {
     const int lane = threadIdx.x & 31;
     const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (w >= nwarps) return;
@@ -300,15 +315,22 @@ __global__ void __launch_bounds__(256) spmm_merge_kernel(int64_t n, int64_t nnz,
     while (r + 1 < n && __ldg(indptr + r + 1) <= p0) ++r;
     int64_t p = p0;
     while (p < p1) {
-        const int64_t rs = __ldg(indptr + r), re = __ldg(indptr + r + 1);
+        const int64_t rs = VB ? __ldcs(indptr + r) : __ldg(indptr + r);
+        const int64_t re = VB ? __ldcs(indptr + r + 1) : __ldg(indptr + r + 1);
         const int64_t e = imin64(re, p1);
+        const int32_t *ind = indices;
+        const float *val = vals;
+        if (VB) {
+            const int64_t phys = __ldcs(indptr0 + r) + (int64_t)__ldcs(segb + r) - rs;
+            ind = indices + phys;
+            val = vals + phys;
+        }
         Acc4<NV> acc;
 #pragma unroll
         for (int t = 0; t < NV; ++t) acc.v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (LG < 32) {
             for (int64_t q = p; q < e; q += 32)
-                gather4_grouped<LG, WEIGHTED, TX>(indices, vals, q, (int)imin64(32, e - q), X, ldx, c4, lane,
-                                                  acc.v[0]);
+                gather4_grouped<LG, WEIGHTED, TX>(ind, val, q, (int)imin64(32, e - q), X, ldx, c4, lane, acc.v[0]);
 #pragma unroll
             for (int off = LG; off < 32; off <<= 1) {
                 acc.v[0].x += __shfl_xor_sync(0xffffffffu, acc.v[0].x, off);
@@ -318,10 +340,10 @@ __global__ void __launch_bounds__(256) spmm_merge_kernel(int64_t n, int64_t nnz,
             }
         } else {
             for (int64_t q = p; q < e; q += 32)
-                gather4<NV, WEIGHTED, TX>(indices, vals, q, (int)imin64(32, e - q), X, ldx, c4, lane, acc);
+                gather4<NV, WEIGHTED, TX, VB>(ind, val, q, (int)imin64(32, e - q), X, ldx, c4, lane, acc);
         }
         if (rs >= p0 && re <= p1) {
-            epilogue4<NV>(r, re - rs, acc, lane, c4, Y, ldy, ep);
+            epilogue4<NV, VB>(r, re - rs, acc, lane, c4, Y, ldy, ep);
         } else {
             const int slot = rs < p0 ? 0 : 1;
             float4 *dst = carry + (w * 2 + slot) * (int64_t)(NV * 32);
@@ -337,7 +359,7 @@ __global__ void __launch_bounds__(256) spmm_merge_kernel(int64_t n, int64_t nnz,
 }
 
 // Rows that are empty or cross slice boundaries: sum the partials in slice order.
-template <int NV>
+template <int NV, bool STREAM = false>
 __global__ void __launch_bounds__(256) spmm_fixup_kernel(int64_t n, const int64_t *__restrict__ indptr, int c4,
                                                          float *__restrict__ Y, int64_t ldy, SpmmEpilogue ep, int64_t W,
                                                          const float4 *__restrict__ carry,
@@ -345,7 +367,7 @@ __global__ void __launch_bounds__(256) spmm_fixup_kernel(int64_t n, const int64_
     const int lane = threadIdx.x & 31;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n; r += warps) {
-        const int64_t rs = indptr[r], re = indptr[r + 1];
+        const int64_t rs = STREAM ? __ldcs(indptr + r) : indptr[r], re = STREAM ? __ldcs(indptr + r + 1) : indptr[r + 1];
         Acc4<NV> acc;
 #pragma unroll
         for (int t = 0; t < NV; ++t) acc.v[t] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -367,7 +389,7 @@ __global__ void __launch_bounds__(256) spmm_fixup_kernel(int64_t n, const int64_
                 }
             }
         }
-        epilogue4<NV>(r, re - rs, acc, lane, c4, Y, ldy, ep);
+        epilogue4<NV, STREAM>(r, re - rs, acc, lane, c4, Y, ldy, ep);
     }
 }
 
@@ -509,7 +531,169 @@ int launch_merge(Workspace &ws, int64_t n, int64_t nnz, const int64_t *indptr, c
     return 0;
 }
 
+// Segments of the rows of a CSR matrix (columns sorted within rows) by
+// vertex blocks [b << shift, (b + 1) << shift): seg[b n + i] = the number of
+// row i's nonzeros with column < b << shift (b = 0..nb). A warp per row;
+// unsorted rows set *unsorted.
+__global__ void __launch_bounds__(256) vblock_seg_kernel(int64_t n, const int64_t *__restrict__ indptr,
+                                                         const int32_t *__restrict__ indices, int shift, int nb,
+                                                         uint32_t *__restrict__ seg, int *__restrict__ unsorted) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+        const int64_t rs = __ldg(indptr + i), len = __ldg(indptr + i + 1) - rs;
+        if (lane == 0) seg[i] = 0;   // block 0
+        int prev = 0;                // block of the element before the chunk (0 before the first)
+        for (int64_t k0 = 0; k0 < len; k0 += 32) {
+            const int64_t k = k0 + lane;
+            const bool valid = k < len;
+            const int col = valid ? __ldg(indices + rs + k) : 0;
+            if (valid && (col < 0 || (int64_t)col >= n)) *unsorted = 1;   // not a valid column: no blocking
+            const int blk = valid ? min(max(col, 0) >> shift, nb - 1) : nb;
+            int before = __shfl_up_sync(0xffffffffu, blk, 1);
+            if (lane == 0) before = prev;
+            if (valid) {
+                if (blk < before) *unsorted = 1;
+                for (int b = before + 1; b <= blk; ++b) seg[(int64_t)b * n + i] = (uint32_t)k;
+            }
+            prev = __shfl_sync(0xffffffffu, blk, 31);
+        }
+        const int last = len > 0 ? min(max(__ldg(indices + rs + len - 1), 0) >> shift, nb - 1) : 0;
+        for (int b = last + 1 + lane; b <= nb; b += 32) seg[(int64_t)b * n + i] = (uint32_t)len;
+    }
+}
+
+// V[b (n + 1) + i] = the length of row i's segment in block b (scanned in place afterwards)
+__global__ void vblock_len_kernel(int64_t n, int nb, const uint32_t *__restrict__ seg, int64_t *__restrict__ V) {
+    const int64_t total = (int64_t)nb * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = e / n, i = e - b * n;
+        V[b * (n + 1) + i] = (int64_t)(seg[(b + 1) * n + i] - seg[b * n + i]);
+    }
+}
+
+__global__ void vblock_totals_kernel(int64_t n, int nb, const int64_t *__restrict__ V, int64_t *__restrict__ out) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) out[b] = V[(int64_t)b * (n + 1) + n];
+}
+
+// The column-blocked product Y = alpha M X: vertex block b of the columns
+// (a bounded region of operand rows) at a time, each block's partial product added
+// to Y in block order by the epilogue (Y = partial + Y for b > 0); the last
+// block also writes the BF16 copy. Deterministic: fixed block order, and
+// within a block the merge kernel's fixed order.
+template <typename TX>
+int launch_merge_vb(Workspace &ws, const CsrView &M, const TX *X, int64_t ldx, int c, float *Y, int64_t ldy,
+                    const SpmmEpilogue &ep, cudaStream_t st) {
+    const VBlocks &vb = *M.vb;
+    const int64_t n = M.n;
+    const int c4 = c / 4;
+    const int nv = merge_vectors(c);
+    for (int b = 0; b < vb.nb; ++b) {
+        const int64_t nnzb = vb.nnz[(size_t)b];
+        const int64_t *V = vb.V + (int64_t)b * (n + 1);
+        const uint32_t *segb = vb.seg + (int64_t)b * n;
+        SpmmEpilogue eb;
+        eb.lde = ldy;
+        eb.alpha = ep.alpha;
+        eb.threads = ep.threads;
+        eb.carry_tag = ep.carry_tag;
+        if (b > 0) {
+            eb.E1 = Y;
+            eb.b1 = 1.f;
+        }
+        if (b == vb.nb - 1) eb.Yb = ep.Yb;
+        const int64_t W = merge_slice(nnzb, n);
+        const int64_t nwarps = std::max<int64_t>(1, ceil_div(nnzb, W));
+        float4 *carry = nullptr;
+        int64_t *carry_row = nullptr;
+        LNE_TRY(merge_carry(ws, eb.carry_tag, nnzb, n, c, &carry, &carry_row));
+        const int threads = eb.threads > 0 ? eb.threads : 256;
+        const unsigned mblocks = (unsigned)ceil_div(nwarps, threads / 32);
+        const unsigned fblocks = (unsigned)std::min<int64_t>(ceil_div(n, 8), num_sms() * 32);
+        LNE_TRACE("spmm", st);
+#define LNE_VB_CASE(K)                                                                                           \
+    case K:                                                                                                      \
+        if (nnzb > 0)                                                                                            \
+            spmm_merge_kernel<K, true, TX, 32, true><<<mblocks, threads, 0, st>>>(                               \
+                n, nnzb, V, M.indices, M.data, X, ldx, c4, Y, ldy, eb, W, nwarps, carry, carry_row, M.indptr, segb); \
+        spmm_fixup_kernel<K, true><<<fblocks, 256, 0, st>>>(n, V, c4, Y, ldy, eb, W, carry, carry_row);         \
+        break;
+        switch (nv) {
+            LNE_VB_CASE(1)
+            LNE_VB_CASE(2)
+            LNE_VB_CASE(4)
+            LNE_VB_CASE(8)
+            default:
+                return fail(LNE_ERR_UNSUPPORTED, "SpMM supports at most 1024 dense columns");
+        }
+#undef LNE_VB_CASE
+        LNE_LAUNCH_CHECK();
+        ::lne::count_launch();
+    }
+    return 0;
+}
+
+
 }  // namespace
+
+int vblock_shift_for(int mode, int64_t n, int c, int elem_bytes) {
+    if (mode < 0 || n <= 0) return 0;
+    if (mode > 0) return (int64_t)1 << mode < n ? mode : 0;
+    int dev = 0, l2 = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess)
+        return 0;
+    const double row = (double)c * elem_bytes;
+    if ((double)n * row <= (double)l2) return 0;   // the whole operand fits in L2
+    // the largest blocks whose operand rows take at most 2.5 times L2:
+    // measured on a 10M-vertex graph (c = 144, BF16 operand), blocks of
+    // 0.6, 1.2, 2.4 and 4.8 times L2 took the products from 614 ms to 614,
+    // 558, 550 and 574 ms; L2-sized blocks do not help, the random row
+    // gathers are bound by the memory system's request throughput, not by
+    // DRAM bytes, and more passes over Y cost more than the hits save
+    int shift = 10;
+    while (shift < 30 && (double)((int64_t)1 << (shift + 1)) * row <= 2.5 * (double)l2) ++shift;
+    return (int64_t)1 << shift < n ? shift : 0;
+}
+
+int vblocks_build(Workspace &ws, const CsrView &M, int shift, VBlocks *vb, bool *ok, cudaStream_t st) {
+    *ok = false;
+    const int64_t n = M.n;
+    if (shift <= 0 || n <= 0 || M.nnz <= 0) return 0;
+    const int nb = (int)ceil_div(n, (int64_t)1 << shift);
+    if (nb < 2) return 0;
+    uint32_t *seg = nullptr;
+    int64_t *V = nullptr, *tot = nullptr;
+    int *flag = nullptr;
+    LNE_TRY(ws.get("vb.seg", (size_t)(nb + 1) * (size_t)n, &seg));
+    LNE_TRY(ws.get("vb.V", (size_t)nb * (size_t)(n + 1), &V));
+    LNE_TRY(ws.get("vb.tot", (size_t)nb, &tot));
+    LNE_TRY(ws.get("vb.flag", 1, &flag));
+    LNE_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    {
+        LNE_TRACE("vblock_seg", st);
+        const unsigned blocks = (unsigned)std::min<int64_t>(ceil_div(n, 8), num_sms() * 32);
+        vblock_seg_kernel<<<blocks, 256, 0, st>>>(n, M.indptr, M.indices, shift, nb, seg, flag);
+        LNE_LAUNCH_CHECK();
+        vblock_len_kernel<<<(unsigned)(num_sms() * 16), 256, 0, st>>>(n, nb, seg, V);
+        LNE_LAUNCH_CHECK();
+    }
+    LNE_TRY(scan_exclusive_rows_i64(V, nb, n, st));
+    vblock_totals_kernel<<<1, 256, 0, st>>>(n, nb, V, tot);
+    LNE_LAUNCH_CHECK();
+    std::vector<int64_t> h((size_t)nb);
+    int unsorted = 0;
+    LNE_CUDA_TRY(cudaMemcpyAsync(h.data(), tot, sizeof(int64_t) * (size_t)nb, cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaMemcpyAsync(&unsorted, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (unsorted) return 0;
+    vb->shift = shift;
+    vb->nb = nb;
+    vb->seg = seg;
+    vb->V = V;
+    vb->nnz = std::move(h);
+    *ok = true;
+    return 0;
+}
 
 // Partial products of k-slices (P[z] = the slice's n x c block, z = 0..ks-1)
 // summed in slice order into Y: deterministic.
@@ -546,6 +730,7 @@ int spmm(Workspace &ws, const CsrView &M, const float *X, int64_t ldx, int c, fl
          cudaStream_t st) {
     SpmmEpilogue ep;
     ep.lde = ldy;
+    if (M.vb && merge_ok(X, ldx, c, Y, ldy, ep)) return launch_merge_vb<float>(ws, M, X, ldx, c, Y, ldy, ep, st);
     if (merge_ok(X, ldx, c, Y, ldy, ep))
         return launch_merge<true, float>(ws, M.n, M.nnz, M.indptr, M.indices, M.data, X, ldx, c, Y, ldy, ep, st);
     return launch_spmm<true>(M.n, M.indptr, M.indices, M.data, X, ldx, c, Y, ldy, ep, st);
@@ -557,6 +742,7 @@ int spmm_bf16(Workspace &ws, const CsrView &M, const __nv_bfloat16 *X, int64_t l
     ep.lde = ldy;
     ep.Yb = Yb;
     if (!merge_ok(X, ldx, c, Y, ldy, ep)) return fail(LNE_ERR_UNSUPPORTED, "BF16 operands need c and ld multiples of 4");
+    if (M.vb) return launch_merge_vb<__nv_bfloat16>(ws, M, X, ldx, c, Y, ldy, ep, st);
     return launch_merge<true, __nv_bfloat16>(ws, M.n, M.nnz, M.indptr, M.indices, M.data, X, ldx, c, Y, ldy, ep, st);
 }
 

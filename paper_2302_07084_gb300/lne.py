@@ -44,6 +44,7 @@ OPT_TUNE_WORKERS = 3
 OPT_DENSE_PRODUCT = 4
 OPT_STRATIFIED = 5
 OPT_SPMM_COLBLOCK = 6
+OPT_SPMM_VBLOCK = 7
 AGG_AUTO, AGG_TABLE, AGG_BUCKET, AGG_SORT = 0, 1, 2, 3
 
 
