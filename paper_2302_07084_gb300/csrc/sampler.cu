@@ -1319,9 +1319,14 @@ __global__ void table_decode_values_kernel(const uint32_t *__restrict__ tp, uint
             const uint32_t cnt = ((w >> (BITS * i)) & mask) + (wr[i] << BITS) - prev;
             prev = wr[i];
             const int64_t y = P * k + i - (int64_t)x * ld;
-            // left of the diagonal, padding, or nothing counted (then no wraps
-            // either: the record is already 0)
-            if (y < x || y >= n || cnt == 0) continue;
+            // left of the diagonal, padding, or nothing counted: value 0. The
+            // record is 0 there unless the field took the carries of a
+            // neighbour that wrapped 2^BITS times and wrapped itself (a
+            // neighbour past 2^16 counts): clear it
+            if (y < x || y >= n || cnt == 0) {
+                if (wr[i] != 0u) T[P * k + i] = 0u;
+                continue;
+            }
             T[P * k + i] = __float_as_uint(netmf_value(cnt, dx, eq1_degree(kc, indptr, y), x == y, kc));
         }
     }
