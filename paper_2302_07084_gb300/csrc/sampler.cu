@@ -1388,24 +1388,19 @@ __global__ void table_compact_kernel(const E *__restrict__ T, int64_t ld, int n,
     }
 }
 
-// Loads the 64 x 64 tile (bx, by) of the symmetric value matrix into S
-// (S[i][j] = M[bx*64 + i][by*64 + j]); the table holds the upper triangle.
-__device__ __forceinline__ void load_sym_tile(const uint32_t *__restrict__ T, int64_t ld, int bx, int by,
-                                              uint32_t (*S)[kTile + 1]) {
-    if (bx < by) {
-        const uint32_t *base = T + (size_t)bx * kTile * ld + (size_t)by * kTile;
+// The upper tile (u, v), u <= v, of the stored upper triangle, once: S[i][j]
+// = T(u kTile + i, v kTile + j); on the diagonal tile the lower half is the
+// mirror of the upper. Its rows give the tile (u, v) of the symmetric matrix
+// and its columns (u < v) the tile (v, u), so each stored tile is read once.
+__device__ __forceinline__ void load_upper_tile(const uint32_t *__restrict__ T, int64_t ld, int u, int v,
+                                                uint32_t (*S)[kTile + 1]) {
+    const uint32_t *base = T + (size_t)u * kTile * ld + (size_t)v * kTile;
+    if (u < v) {
         for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
             const int i = e / kTile, j = e % kTile;
             S[i][j] = base[(size_t)i * ld + j];
         }
-    } else if (bx > by) {
-        const uint32_t *base = T + (size_t)by * kTile * ld + (size_t)bx * kTile;
-        for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
-            const int i = e / kTile, j = e % kTile;
-            S[j][i] = base[(size_t)i * ld + j];
-        }
     } else {
-        const uint32_t *base = T + (size_t)bx * kTile * ld + (size_t)by * kTile;
         for (int e = threadIdx.x; e < kTile * kTile; e += blockDim.x) {
             const int i = e / kTile, j = e % kTile;
             S[i][j] = base[(size_t)min(i, j) * ld + max(i, j)];
@@ -1413,20 +1408,30 @@ __device__ __forceinline__ void load_sym_tile(const uint32_t *__restrict__ T, in
     }
 }
 
-// Kept entries per (row, column tile) of the symmetric matrix.
+// Kept entries per (row, column tile) of the symmetric matrix: a CTA per
+// upper tile (the grid's other half returns at once) counts the tile's rows
+// for (u, v) and, off the diagonal, its columns for (v, u).
 __global__ void __launch_bounds__(256) tile_count_kernel(const uint32_t *__restrict__ T, int64_t ld, int n, int nt,
                                                          uint32_t *__restrict__ rowtile) {
     __shared__ uint32_t S[kTile][kTile + 1];
-    const int bx = blockIdx.y, by = blockIdx.x;
-    load_sym_tile(T, ld, bx, by, S);
+    const int u = blockIdx.y, v = blockIdx.x;
+    if (u > v) return;
+    load_upper_tile(T, ld, u, v, S);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = warp; i < kTile; i += 8) {
-        const int r = bx * kTile + i;
-        if (r >= n) break;
-        const unsigned b0 = __ballot_sync(0xffffffffu, S[i][lane] != 0u);
-        const unsigned b1 = __ballot_sync(0xffffffffu, S[i][lane + 32] != 0u);
-        if (lane == 0) rowtile[(size_t)r * nt + by] = __popc(b0) + __popc(b1);
+        const int r = u * kTile + i;
+        if (r < n) {
+            const unsigned b0 = __ballot_sync(0xffffffffu, S[i][lane] != 0u);
+            const unsigned b1 = __ballot_sync(0xffffffffu, S[i][lane + 32] != 0u);
+            if (lane == 0) rowtile[(size_t)r * nt + v] = __popc(b0) + __popc(b1);
+        }
+        const int rt = v * kTile + i;   // row i of the tile (v, u): column i of S
+        if (u < v && rt < n) {
+            const unsigned b0 = __ballot_sync(0xffffffffu, S[lane][i] != 0u);
+            const unsigned b1 = __ballot_sync(0xffffffffu, S[lane + 32][i] != 0u);
+            if (lane == 0) rowtile[(size_t)rt * nt + u] = __popc(b0) + __popc(b1);
+        }
     }
 }
 
@@ -1453,34 +1458,45 @@ __global__ void row_tile_scan_kernel(uint32_t *__restrict__ rowtile, int n, int 
     if (lane == 0) rowcnt[r] = carry;
 }
 
-// Writes every kept entry of the tile at its sorted position in the CSR.
+// Writes every kept entry of the upper tile at its sorted position in the
+// CSR: the tile's rows into (u, v) and, off the diagonal, its columns into
+// (v, u) (a row of the tile (v, u) takes S's column in row order, which is
+// its column order).
+__device__ __forceinline__ void fill_row(int64_t base, uint32_t v0, uint32_t v1, int col0, int lane,
+                                         int32_t *__restrict__ col, float *__restrict__ data) {
+    const unsigned b0 = __ballot_sync(0xffffffffu, v0 != 0u);
+    const unsigned b1 = __ballot_sync(0xffffffffu, v1 != 0u);
+    const unsigned below = (1u << lane) - 1u;
+    if (v0) {
+        const int64_t pos = base + __popc(b0 & below);
+        col[pos] = col0 + lane;
+        data[pos] = __uint_as_float(v0);
+    }
+    if (v1) {
+        const int64_t pos = base + __popc(b0) + __popc(b1 & below);
+        col[pos] = col0 + 32 + lane;
+        data[pos] = __uint_as_float(v1);
+    }
+}
+
 __global__ void __launch_bounds__(256) tile_fill_kernel(const uint32_t *__restrict__ T, int64_t ld, int n, int nt,
                                                         const uint32_t *__restrict__ rowtile,
                                                         const int64_t *__restrict__ indptr,
                                                         int32_t *__restrict__ col, float *__restrict__ data) {
     __shared__ uint32_t S[kTile][kTile + 1];
-    const int bx = blockIdx.y, by = blockIdx.x;
-    load_sym_tile(T, ld, bx, by, S);
+    const int u = blockIdx.y, v = blockIdx.x;
+    if (u > v) return;
+    load_upper_tile(T, ld, u, v, S);
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = warp; i < kTile; i += 8) {
-        const int r = bx * kTile + i;
-        if (r >= n) break;
-        const int64_t base = indptr[r] + rowtile[(size_t)r * nt + by];
-        const uint32_t v0 = S[i][lane], v1 = S[i][lane + 32];
-        const unsigned b0 = __ballot_sync(0xffffffffu, v0 != 0u);
-        const unsigned b1 = __ballot_sync(0xffffffffu, v1 != 0u);
-        const unsigned below = (1u << lane) - 1u;
-        if (v0) {
-            const int64_t pos = base + __popc(b0 & below);
-            col[pos] = by * kTile + lane;
-            data[pos] = __uint_as_float(v0);
-        }
-        if (v1) {
-            const int64_t pos = base + __popc(b0) + __popc(b1 & below);
-            col[pos] = by * kTile + 32 + lane;
-            data[pos] = __uint_as_float(v1);
-        }
+        const int r = u * kTile + i;
+        if (r < n) fill_row(indptr[r] + rowtile[(size_t)r * nt + v], S[i][lane], S[i][lane + 32], v * kTile, lane,
+                            col, data);
+        const int rt = v * kTile + i;
+        if (u < v && rt < n)
+            fill_row(indptr[rt] + rowtile[(size_t)rt * nt + u], S[lane][i], S[lane + 32][i], u * kTile, lane, col,
+                     data);
     }
 }
 
