@@ -205,16 +205,20 @@ def test_two_hub_counts_past_16_bits(ctx):
     assert c[(x == 0) & (y == 1)][0] > 3 * 65536 and c[(x == 0) & (y == 0)][0] > 2 * 65536
 
 
-def test_csr_beside_a_count_past_16_bits(ctx):
+@pytest.mark.parametrize("isolated", [0, 7000])
+def test_csr_beside_a_count_past_16_bits(ctx, isolated):
     """K_{2,L} with hubs 0 and 2 and a separate edge (1, 3): the pair (0, 0)
     is counted past 2^16 times and its neighbour in the count table, (0, 1),
     never; the carries that (0, 0)'s wraps push into (0, 1)'s field wrap it
-    in turn. The CSR must hold (0, 0) with its value and no (0, 1) entry."""
+    in turn. The CSR must hold (0, 0) with its value and no (0, 1) entry.
+    With 7000 isolated vertices the table is sparse (the value pass that
+    queues its counters)."""
     L = 500
     u = np.concatenate([np.zeros(L, np.int64), np.full(L, 2, np.int64), [1]])
     v = np.concatenate([np.arange(4, L + 4), np.arange(4, L + 4), [3]])
     indptr, indices = synth.csr_from_edges(L + 4, u, v)
-    g = synth.Graph(L + 4, indptr, indices, None, "k2_500_split")
+    indptr = np.concatenate([indptr, np.full(isolated, indptr[-1])])
+    g = synth.Graph(L + 4 + isolated, indptr, indices, None, "k2_500_split")
     p = make_params(3, [0.2, 0.5, 0.3], 1500.0 * g.n_arcs, seed=5)
     x, y, c = oracle.sparsifier_counts(g.indptr, g.indices, p.T, p.s, p.samples, p.seed)
     assert c[(x == 0) & (y == 0)][0] > 65536 and not np.any((x == 0) & (y == 1))
