@@ -147,18 +147,43 @@ __global__ void __launch_bounds__(kGramThreads) gram_partial_kernel(const float 
     }
 }
 
-// G[i][j] = sum over CTAs of the partials (fixed order), mirrored to i > j.
+// G[a][b] = G[b][a] = sum over CTAs of the partials of the upper entry
+// (a, b): 8 lanes per entry, lane q summing partials q, q + 8, ..., then a
+// fixed shuffle tree, so the order is the same on every run. (The (a, b)
+// entry lives in tile (a/8, b/8); tiles with a/8 == b/8 hold both orders,
+// tiles above the diagonal only (a, b).)
+constexpr int kGramRedLanes = 8;
+
 __global__ void gram_reduce_kernel(const double *__restrict__ partial, int nblk, int c,
                                    double *__restrict__ G) {
+    constexpr int kPerWarp = 32 / kGramRedLanes;   // entries per warp and step
     const int cp = (c + 7) & ~7;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c * c; e += gridDim.x * blockDim.x) {
-        int i = e / c, j = e - i * c;
-        int a = min(i, j), b = max(i, j);
-        // the (a, b) entry lives in tile (a/8, b/8); tiles with a/8 == b/8 hold
-        // both orders, tiles above the diagonal only (a, b).
+    const int nup = c * (c + 1) / 2;
+    const int lane = threadIdx.x & 31, q = lane % kGramRedLanes;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // the warp's lanes take the same trip count (the shuffles need all of them)
+    for (int64_t ub = warp * kPerWarp; ub < nup; ub += nwarps * kPerWarp) {
+        const int64_t u = ub + lane / kGramRedLanes;
+        const bool live = u < nup;
+        int a = 0, b = 0;
+        if (live) {   // u-th upper entry in row order: row a holds c - a entries
+            int rem = (int)u;
+            while (rem >= c - a) {
+                rem -= c - a;
+                ++a;
+            }
+            b = a + rem;
+        }
         double s = 0.0;
-        for (int k = 0; k < nblk; ++k) s += partial[(int64_t)k * cp * cp + a * cp + b];
-        G[e] = s;
+        if (live)
+            for (int k = q; k < nblk; k += kGramRedLanes) s += partial[(int64_t)k * cp * cp + a * cp + b];
+#pragma unroll
+        for (int off = kGramRedLanes / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (live && q == 0) {
+            G[a * c + b] = s;
+            G[b * c + a] = s;
+        }
     }
 }
 
@@ -1535,7 +1560,8 @@ static int gram(Workspace &ws, const float *Y, int64_t n, int c, int64_t ld, dou
     }
     {
         LNE_TRACE("gram_reduce", st);
-        gram_reduce_kernel<<<grid_for((int64_t)c * c, 256), 256, 0, st>>>(partial, (int)nblk, c, G);
+        gram_reduce_kernel<<<grid_for((int64_t)c * (c + 1) / 2 * kGramRedLanes, 256), 256, 0, st>>>(partial,
+                                                                                                (int)nblk, c, G);
         LNE_LAUNCH_CHECK();
     }
     return 0;
