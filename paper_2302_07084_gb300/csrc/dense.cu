@@ -106,6 +106,7 @@ __global__ void __launch_bounds__(kGramThreads) gram_partial_kernel(const float 
             for (int b = 0; b < 8; ++b) hi[a][b] = lo[a][b] = 0.f;
         for (int64_t base = r0; base < r1; base += kGramRows) {
             const int rows = (int)imin64(kGramRows, r1 - base);
+#pragma unroll 4
             for (int e = tid; e < kGramRows * cp; e += kGramThreads) {
                 int rr = e / cp, cc = e - rr * cp;
                 ys[e] = (rr < rows && cc < c) ? Y[(base + rr) * ld + cc] : 0.f;
@@ -400,7 +401,10 @@ __global__ void __launch_bounds__(256) trsm_rows_kernel(const float *__restrict_
                                                         int64_t ldq) {
     extern __shared__ float Rs[];   // c x c, row-major, plus the reciprocal diagonal
     float *rdiag = Rs + c * c;
-    for (int e = threadIdx.x; e < c * c; e += blockDim.x) Rs[e] = (float)R[e];
+    // staged 8 loads at a time per thread: independent loads in flight instead
+    // of one L2 round trip per element
+#pragma unroll 8
+    for (int e = threadIdx.x; e < c * c; e += blockDim.x) Rs[e] = (float)__ldg(R + e);
     for (int j = threadIdx.x; j < c; j += blockDim.x) rdiag[j] = (float)(1.0 / R[j * c + j]);
     __syncthreads();
     const int lane = threadIdx.x & 31;
@@ -1045,6 +1049,7 @@ __global__ void __launch_bounds__(kDgTile * kDgTile) dgemm_small_kernel(const do
     __shared__ double As[kDgTile][kDgMaxC + 1], Bs[kDgMaxC][kDgTile + 1];
     const int tid = threadIdx.x, tx = tid % kDgTile, ty = tid / kDgTile;
     const int r0 = blockIdx.y * kDgTile, c0 = blockIdx.x * kDgTile;
+#pragma unroll 6
     for (int e = tid; e < kDgTile * c; e += kDgTile * kDgTile) {
         // op(A)[r0 + i][k]: for ta the k index runs along A's rows
         const int i = ta ? e % kDgTile : e / c, k = ta ? e / kDgTile : e % c;
@@ -1329,6 +1334,7 @@ __global__ void __launch_bounds__(kClusterThreads) svd_cluster_kernel(const doub
     const int nK = s_nK;
     if (nK == 0) return;
     for (int a = warp; a < nK; a += kClusterWarps)
+#pragma unroll 5
         for (int b = lane; b < nK; b += 32) sT[a * nK + b] = T[(size_t)sK[a] * c + sK[b]];
     const int words = (nK + 31) / 32;
     for (int sweep = 0; sweep < kClusterSweeps; ++sweep) {
@@ -1437,19 +1443,35 @@ __global__ void __launch_bounds__(kClusterThreads) svd_cluster_kernel(const doub
 }
 
 // sigma sorted descending; U_R[:, rank_j] = sign(s_j) U[:, j].
+// Ranks first, then the columns copied by all threads over the flat index,
+// so the loads of the whole matrix are in flight together. Magnitudes are
+// compared and signs flipped on the bit patterns (non-negative doubles order
+// as their bits; integer operations instead of the slow FP64 pipe).
 __global__ void svd_finish_kernel(const double *__restrict__ U, const double *__restrict__ sg, int c,
                                   double *__restrict__ UR, double *__restrict__ sigma) {
-    __shared__ double s_sig[256];
+    __shared__ long long s_abs[256];
+    __shared__ int s_rank[256];
+    __shared__ unsigned long long s_flip[256];
     const int tid = threadIdx.x;
-    for (int j = tid; j < c; j += blockDim.x) s_sig[j] = fabs(sg[j]);
+    for (int j = tid; j < c; j += blockDim.x) {
+        const long long b = __double_as_longlong(sg[j]);
+        s_abs[j] = b & 0x7FFFFFFFFFFFFFFFll;
+        s_flip[j] = (unsigned long long)b & 0x8000000000000000ull;   // the sign of sg[j]
+    }
     __syncthreads();
     for (int j = tid; j < c; j += blockDim.x) {
-        const double sj = s_sig[j];
+        const long long sj = s_abs[j];
         int rank = 0;
-        for (int i = 0; i < c; ++i) rank += (s_sig[i] > sj) || (s_sig[i] == sj && i < j);
-        sigma[rank] = sj;
-        const double sgn = sg[j] < 0.0 ? -1.0 : 1.0;
-        for (int i = 0; i < c; ++i) UR[i * c + rank] = U[i * c + j] * sgn;
+        for (int i = 0; i < c; ++i) rank += (s_abs[i] > sj) || (s_abs[i] == sj && i < j);
+        sigma[rank] = __longlong_as_double(sj);
+        s_rank[j] = rank;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int e = tid; e < c * c; e += blockDim.x) {
+        const int i = e / c, j = e - i * c;
+        UR[i * c + s_rank[j]] =
+            __longlong_as_double((long long)((unsigned long long)__double_as_longlong(__ldg(U + e)) ^ s_flip[j]));
     }
 }
 
