@@ -271,15 +271,22 @@ __device__ __forceinline__ void chol_panel_body(double *__restrict__ A, int c, i
     const int ti = tid >> 4, tj = tid & 15;
     for (int t = 0; t < bs; ++t) {
         if (tid == 0) {
+            // the pivot's 1/sqrt by Newton's iteration y <- y (3 - a y^2) / 2
+            // from the FP32 estimate (two steps take its 24 bits past FP64's
+            // 53): no FP64 square root or division on this GPU's narrow FP64 pipe
             const double att = s11[t][t];
-            double d = 1.0;
+            double d = 1.0, y = 1.0;
             if (!(att > 0.0) || !isfinite(att)) {
                 if (bx == 0 && *status == 0) *status = k0 + t + 1;
             } else {
-                d = sqrt(att);
+                y = (double)rsqrtf((float)att);
+                if (!(y > 0.0) || !isfinite(y)) y = 1.0 / sqrt(att);   // outside FP32's range
+                y = y * fma(-0.5 * att, y * y, 1.5);
+                y = y * fma(-0.5 * att, y * y, 1.5);
+                d = att * y;
             }
             s11[t][t] = d;
-            sinv[t] = 1.0 / d;
+            sinv[t] = y;
         }
         __syncthreads();
         if (ti == t && tj > t && tj < bs) s11[t][tj] *= sinv[t];
