@@ -188,6 +188,17 @@ __global__ void gram_reduce_kernel(const double *__restrict__ partial, int nblk,
     }
 }
 
+// 1/sqrt(a) of a positive finite FP64 pivot by two Newton steps
+// y <- y (3 - a y^2) / 2 from the FP32 estimate (which has 24 bits; two steps
+// pass FP64's 53), so no FP64 square root or division runs on this GPU's
+// narrow FP64 pipe; pivots outside FP32's range take the plain route.
+__device__ __forceinline__ double pivot_rsqrt(double a) {
+    double y = (double)rsqrtf((float)a);
+    if (!(y > 0.0) || !isfinite(y)) return 1.0 / sqrt(a);
+    y = y * fma(-0.5 * a, y * y, 1.5);
+    return y * fma(-0.5 * a, y * y, 1.5);
+}
+
 // ---------------------------------------------------------------------------
 // Cholesky (upper, G = R^T R), one CTA, FP64. Right-looking: for each k the
 // pivot row is scaled by 1/sqrt(pivot) and the trailing upper triangle takes
@@ -215,9 +226,9 @@ __global__ void __launch_bounds__(kCholThreads) chol_kernel(const double *__rest
                 A[k * c + k] = 1.0;
                 s_inv = 1.0;
             } else {
-                const double dk = sqrt(akk);
-                A[k * c + k] = dk;
-                s_inv = 1.0 / dk;
+                const double y = pivot_rsqrt(akk);
+                A[k * c + k] = akk * y;
+                s_inv = y;
             }
         }
         __syncthreads();
@@ -271,18 +282,12 @@ __device__ __forceinline__ void chol_panel_body(double *__restrict__ A, int c, i
     const int ti = tid >> 4, tj = tid & 15;
     for (int t = 0; t < bs; ++t) {
         if (tid == 0) {
-            // the pivot's 1/sqrt by Newton's iteration y <- y (3 - a y^2) / 2
-            // from the FP32 estimate (two steps take its 24 bits past FP64's
-            // 53): no FP64 square root or division on this GPU's narrow FP64 pipe
             const double att = s11[t][t];
             double d = 1.0, y = 1.0;
             if (!(att > 0.0) || !isfinite(att)) {
                 if (bx == 0 && *status == 0) *status = k0 + t + 1;
             } else {
-                y = (double)rsqrtf((float)att);
-                if (!(y > 0.0) || !isfinite(y)) y = 1.0 / sqrt(att);   // outside FP32's range
-                y = y * fma(-0.5 * att, y * y, 1.5);
-                y = y * fma(-0.5 * att, y * y, 1.5);
+                y = pivot_rsqrt(att);
                 d = att * y;
             }
             s11[t][t] = d;
