@@ -57,3 +57,22 @@ def test_binding_raises_without_library(tmp_path):
             lne.load_library(str(tmp_path / "missing.so"))
     finally:
         lne._lib = saved
+
+
+def _header_defines():
+    src = open(os.path.join(ROOT, "include", "lne.h")).read()
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"^#define (LNE_[A-Z0-9_]+)\s+(-?\d+)", src, re.M)}
+
+
+def test_binding_constants_match_header():
+    """Every option, aggregation, sketch and precision constant of the binding
+    has the value the header defines (the binding passes them through)."""
+    from paper_2302_07084_gb300 import lne
+    h = _header_defines()
+    pairs = {name[4:]: value for name, value in h.items()
+             if name.startswith(("LNE_OPT_", "LNE_AGG_", "LNE_SKETCH_", "LNE_PREC_"))}
+    assert len(pairs) >= 15
+    for short, value in pairs.items():
+        assert getattr(lne, short) == value, short
+    for code, name in lne.ERRORS.items():
+        assert h[name] == code, name
