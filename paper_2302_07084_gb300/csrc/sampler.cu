@@ -61,7 +61,7 @@ struct WalkArgs {
     int T_eff;                    // how many thresholds are below 2^32
     const uint8_t *rlut;          // window-length table (build_rlut_kernel), 4096 entries
     uint64_t base_magic;          // ceil(2^64 / base): s / base by a high multiply
-    uint64_t rmagic[17];          // ceil(2^64 / r) for r = 1..16 (index r)
+    uint32_t rmod[17];            // barrett_mod multipliers for r = 1..16 (index r)
     // edge downsampling (NULL = off): per arc, the coin keeps a draw iff its
     // coin word < ds_thr[arc]; a kept draw weighs ds_w[arc] (2^-32 units)
     const uint64_t *ds_thr;
@@ -109,16 +109,9 @@ __device__ __forceinline__ u32x4 philox_rk(u32x4 c, const uint32_t *rk) {
     return c;
 }
 
-// a mod d and a / d for 32-bit a, d >= 1 with M = ceil(2^64 / d) (Lemire, Kaser
-// and Kurz, "Faster remainder by direct computation", 2019): the low 64 bits
-// of M a, times d, keep the remainder in their top 32 bits; M a >> 64 is the
-// quotient.
-__device__ __forceinline__ uint32_t fastmod32(uint32_t a, uint64_t M, uint32_t d) {
-    const uint64_t low = M * (uint64_t)a;
-    const uint64_t t = (uint64_t)(uint32_t)low * d;
-    const uint64_t u = (low >> 32) * (uint64_t)d + (t >> 32);
-    return (uint32_t)(u >> 32);
-}
+// a / d for 32-bit a and d >= 1 with M = ceil(2^64 / d): the high 64 bits of
+// M a are the quotient (Lemire, Kaser and Kurz, "Faster remainder by direct
+// computation", 2019).
 __device__ __forceinline__ uint32_t fastdiv32(uint32_t a, uint64_t M) {
     return (uint32_t)__umul64hi(M, (uint64_t)a);
 }
@@ -244,7 +237,8 @@ __device__ __forceinline__ WalkCur walk_start(const WalkArgs &A, int32_t x) {
 
 // w mod d for 2 <= d < 2^24 with m = floor(2^32 / d) (Barrett reduction):
 // q = floor(w m / 2^32) is the true quotient or one less, so one conditional
-// subtraction finishes the remainder.
+// subtraction finishes the remainder. d = 1 takes m = 2^32 - 1 (q = w - 1 for
+// w >= 1, then one subtraction; q = 0 for w = 0): the remainder is 0.
 __device__ __forceinline__ uint32_t barrett_mod(uint32_t w, uint32_t m, uint32_t d) {
     const uint32_t q = __umulhi(w, m);
     uint32_t r = w - q * d;
@@ -297,7 +291,7 @@ struct Draw {
 // Block 0 of the sample's stream: the window r, the split sigma, the
 // downsampling coin and word 3.
 __device__ __forceinline__ void draw_head(const WalkArgs &A, const uint8_t *__restrict__ rlut,
-                                          const uint64_t *__restrict__ rmagic, int64_t arc, uint32_t j, int *r_out,
+                                          const uint32_t *__restrict__ rmod, int64_t arc, uint32_t j, int *r_out,
                                           int *sigma_out, uint32_t *coin_out, uint32_t *w3_out) {
     const u32x4 b0 = philox_rk(u32x4{j, (uint32_t)((uint64_t)arc & 0xFFFFFFFFu), (uint32_t)((uint64_t)arc >> 32), 0u},
                                A.rk);
@@ -310,7 +304,7 @@ __device__ __forceinline__ void draw_head(const WalkArgs &A, const uint8_t *__re
         for (int i = 0; i < A.T_eff; ++i) r += b0.x >= A.thr32[i] ? 1 : 0;
     }
     *r_out = r;
-    *sigma_out = (int)fastmod32(b0.y, rmagic[r], (uint32_t)r);
+    *sigma_out = (int)barrett_mod(b0.y, rmod[r], (uint32_t)r);
     *coin_out = b0.z;
     *w3_out = b0.w;
 }
@@ -443,7 +437,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 10 : 8) walk_emit_ke
     uint32_t *__restrict__ bucket_cnt, int nb_smem) {
     extern __shared__ uint32_t smem[];
     __shared__ __align__(16) uint8_t s_rlut[4096];
-    __shared__ uint64_t s_rmagic[17];
+    __shared__ uint32_t s_rmod[17];
     // s_upack: per chunk sample its index, r, sigma and rank; s_uw3: its word 3
     // (phase 2 reads it through the index, so no permuted copy takes shared
     // memory that the L1 cache can use); s_pack: the samples in r order
@@ -459,7 +453,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 10 : 8) walk_emit_ke
     // window-length table (built once per launch)
     for (int b = tid; b < 4096 / 16; b += kWalkThreads)
         reinterpret_cast<uint4 *>(s_rlut)[b] = __ldg(reinterpret_cast<const uint4 *>(A.rlut) + b);
-    if (tid < 17) s_rmagic[tid] = A.rmagic[tid];
+    if (tid < 17) s_rmod[tid] = A.rmod[tid];
     const int64_t a0 = a_begin + (int64_t)blockIdx.x * tile_arcs;
     const int na = (int)imin64(tile_arcs, a_end - a0);
     if (MODE == 1 && nb_smem > 0)
@@ -546,7 +540,7 @@ __global__ void __launch_bounds__(kWalkThreads, MODE == 2 ? 10 : 8) walk_emit_ke
                 uint32_t j, coin;
                 locate(cb + idx, lo, j);
                 s_lo[idx] = (uint16_t)lo;
-                draw_head(A, s_rlut, s_rmagic, a0 + lo, j, &r, &sg, &coin, &w3);
+                draw_head(A, s_rlut, s_rmod, a0 + lo, j, &r, &sg, &coin, &w3);
                 // edge downsampling (Algorithm 3): the draw walks only if its coin comes up heads
                 if (GEN && A.ds_thr && (uint64_t)coin >= __ldg(A.ds_thr + a0 + lo)) {
                     emit_dropped(cb + idx, a0 + lo);
@@ -659,7 +653,7 @@ constexpr int kTabThreads = 128;
 constexpr int kTabWarps = kTabThreads / 32;
 constexpr int kTabBatch = 256;
 constexpr int kTabMaxTileArcs = 128;   // arcs per CTA tile (their walk records: 32 B each in shared memory)
-constexpr int kTabMinBlocks = 10;      // CTAs per SM (48 registers a thread)
+constexpr int kTabMinBlocks = 9;       // CTAs per SM (56 registers a thread; 10 CTAs: 48 with spills, 1% slower)
 constexpr int kTabBits = 8;            // bits per packed counter (measured: 8 bits 12.6 ms, 16 bits 13.3 ms)
 static_assert(kTabBatch == 256, "ranks and batch indices are packed in 8 bits");
 
@@ -789,7 +783,7 @@ __global__ void __launch_bounds__(kTabThreads, kTabMinBlocks) walk_table_kernel(
                                                                      uint32_t *__restrict__ carry, uint32_t ld) {
     extern __shared__ uint4 smem4[];
     __shared__ __align__(16) uint8_t s_rlut[4096];
-    __shared__ uint64_t s_rmagic[17];
+    __shared__ uint32_t s_rmod[17];
     __shared__ uint32_t s_ent[kTabWarps][kTabBatch];    // arc in tile | r << 12 | sigma << 17 | rank << 21
     __shared__ uint32_t s_w3[kTabWarps][kTabBatch];     // word 3 of each draw
     __shared__ uint8_t s_sorted[kTabWarps][kTabBatch];  // batch index at each ranked position
@@ -800,7 +794,7 @@ __global__ void __launch_bounds__(kTabThreads, kTabMinBlocks) walk_table_kernel(
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int b = tid; b < 4096 / 16; b += kTabThreads)
         reinterpret_cast<uint4 *>(s_rlut)[b] = __ldg(reinterpret_cast<const uint4 *>(A.rlut) + b);
-    if (tid < 17) s_rmagic[tid] = A.rmagic[tid];
+    if (tid < 17) s_rmod[tid] = A.rmod[tid];
     s_hist[warp][lane] = 0;
     const int64_t a0 = (int64_t)blockIdx.x * tile_arcs;
     const int na = (int)imin64(tile_arcs, A.n_arcs - a0);
@@ -823,7 +817,7 @@ __global__ void __launch_bounds__(kTabThreads, kTabMinBlocks) walk_table_kernel(
     for (uint32_t bt = warp; bt < nbatch; bt += kTabWarps) {
         const uint32_t bbase = bt * kTabBatch;
         // heads and ranks by r (r = 0: past the tile's last sample)
-#pragma unroll 1
+#pragma unroll 2   // two heads' Philox chains interleaved (1% off the walk)
         for (int t = 0; t < kTabBatch / 32; ++t) {
             const uint32_t idx = (uint32_t)t * 32 + lane;
             const uint32_t s = bbase + idx;
@@ -840,7 +834,7 @@ __global__ void __launch_bounds__(kTabThreads, kTabMinBlocks) walk_table_kernel(
                     }
                 }
                 uint32_t coin;
-                draw_head(A, s_rlut, s_rmagic, a0 + lo, s - s_off[lo], &r, &sg, &coin, &w3);
+                draw_head(A, s_rlut, s_rmod, a0 + lo, s - s_off[lo], &r, &sg, &coin, &w3);
             }
             const unsigned grp = __match_any_sync(0xffffffffu, r);
             const int leader = __ffs(grp) - 1;
@@ -1795,8 +1789,9 @@ WalkArgs make_walk_args(const GraphView &g, const SamplerSpec &sp) {
     A.vol = g.vol;
     A.wmax = g.wmax;
     A.base_magic = sp.base > 0 ? (~0ull) / sp.base + 1ull : 0ull;
-    A.rmagic[0] = 0;
-    for (int r = 1; r <= 16; ++r) A.rmagic[r] = (~0ull) / (uint64_t)r + 1ull;
+    A.rmod[0] = 0;
+    A.rmod[1] = 0xFFFFFFFFu;
+    for (int r = 2; r <= 16; ++r) A.rmod[r] = (uint32_t)((1ull << 32) / (uint64_t)r);
     return A;
 }
 
