@@ -2,7 +2,7 @@
 
 One step = the whole method on one graph: per-edge PathSampling -> exact pair
 counts -> trunc_log CSR (Eq. 1) -> fast randomized SVD (Algorithm 4) ->
-spectral propagation (Sec. 3.3). Workload: the BlogCatalog-shaped Chung-Lu
+spectral propagation (Sec. 4.3). Workload: the BlogCatalog-shaped Chung-Lu
 graph (n=10,312, m=333,983, exponent 2.1, 39 labels), T=10 with Dirichlet
 window weights, S = 200 T m = 6.68e8 samples, d=128, q=1, k=10.
 
@@ -43,7 +43,7 @@ WORKLOAD = "blogcatalog_like_chunglu_n10312_m333983_T10_S200Tm_d128_q1_k10"
 # only while those files are unchanged; otherwise traffic is null.
 RECORDED_TRAFFIC = {
     "walk_count": {"bytes": 78.70e6 + 754.08e6, "sources": ("csrc/sampler.cu", "csrc/common.cuh"),
-                   "sha16": "ce8e1f4bd3e35a03"},
+                   "sha16": "e6d222c4b30065fe"},
 }
 
 

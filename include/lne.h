@@ -4,12 +4,12 @@
  * The method (Qiu et al., "Towards Lightweight and Automated Representation
  * Learning System for Networks", LightNE 2.0):
  *   1. sparsifier construction: per-edge PathSampling (Algorithms 1 and 3,
- *      Sec. 4.2) aggregated into exact pair counts, scaled and passed through
+ *      Sec. 5.2) aggregated into exact pair counts, scaled and passed through
  *      the truncated logarithm of Eq. 1;
  *   2. fast randomized SVD of that sparse matrix (Algorithm 4) giving the
- *      initial embedding X0 = U Sigma^{1/2} (Sec. 3.2);
+ *      initial embedding X0 = U Sigma^{1/2} (Sec. 4.2);
  *   3. spectral propagation of X0 by a Chebyshev filter in the normalised
- *      Laplacian I - D^-1 A, followed by an economic SVD (Sec. 3.3, Sec. 5.4).
+ *      Laplacian I - D^-1 A, followed by an economic SVD (Sec. 4.3, Sec. 6.3).
  *
  * Conventions shared by every entry point:
  *   - Every pointer named *_dev is CUDA device memory on the context's device;
@@ -56,7 +56,7 @@ extern "C" {
 
 /* Test matrix Omega of the randomized SVD (Algorithm 4). */
 #define LNE_SKETCH_GAUSSIAN     0   /* randn(n, c), the paper's default */
-#define LNE_SKETCH_SPARSE_SIGN  1   /* zeta nonzeros +-1 per row (Sec. 3.2's sparse sign alternative) */
+#define LNE_SKETCH_SPARSE_SIGN  1   /* zeta nonzeros +-1 per row (Sec. 4.2's sparse sign alternative) */
 #define LNE_SKETCH_VERY_SPARSE  2   /* entries +-1 with probability 1/(2s) each (Sec. 4.2's very
                                        sparse random projection); s = sketch_zeta, 0 = sqrt(n) */
 
@@ -191,7 +191,7 @@ int lne_sample_pairs(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
 
 /*
  * Exact multiplicity of every sampled unordered pair (x <= y) over all arcs --
- * the aggregation step of Sec. 4.2 ("sparse parallel hashing"). Output buffers
+ * the aggregation step of Sec. 5.2 ("sparse parallel hashing"). Output buffers
  * are context-owned. Synchronises. With edge downsampling the pairs are those
  * of the kept draws and `weight` replaces `count` (table or sort aggregation;
  * LNE_AGG_BUCKET fails with LNE_ERR_UNSUPPORTED).
@@ -221,7 +221,7 @@ int lne_gaussian_sketch(lne_ctx *ctx, int64_t n, int32_t c, uint64_t seed, float
 
 /*
  * Sparse sign test matrix (the cheaper alternative to the Gaussian Omega that
- * Sec. 3.2 names; construction of Tropp et al., SISC 2019): row i of out_dev
+ * Sec. 4.2 names; construction of Tropp et al., SISC 2019): row i of out_dev
  * ([n][ld], ld >= c, float) has exactly zeta entries +-1 at distinct columns,
  * zeros elsewhere. Columns by Floyd's subset sampling: with words w_0.. of
  * Philox4x32-10 counters (i, b, 0, 0x53505253), b = 0, 1, .., key
@@ -317,17 +317,17 @@ int lne_rsvd(lne_ctx *ctx, const lne_csr *M, const lne_params *p, float *U_dev,
              double *sigma_dev, float *X0_dev, void *stream);
 
 /*
- * Spectral propagation (Sec. 3.3): with Lap = I - D^-1 A and
+ * Spectral propagation (Sec. 4.3): with Lap = I - D^-1 A and
  * Yop = (Lap - mu I)^2 / 2 - I, F = sum_{i<k} c_i T_i(Yop) X0 where
  * c_0 = I_0(theta), c_i = 2 (-1)^i I_i(theta); P = D^-1 A (X0 - F); X = U_P
- * Sigma_P^{1/2} from the SVD of P (Sec. 5.4). X0_dev and X_dev are [n][d]. With
+ * Sigma_P^{1/2} from the SVD of P (Sec. 6.3). X0_dev and X_dev are [n][d]. With
  * k = 0, X = X0. F_dev / P_dev, when not NULL, receive F and P ([n][d]).
  */
 int lne_propagate(lne_ctx *ctx, const lne_graph *g, const lne_params *p, const float *X0_dev,
                   float *X_dev, float *F_dev, float *P_dev, void *stream);
 
 /*
- * Downstream objective of the embedding (Sec. 5.1): one-vs-rest L2-regularised
+ * Downstream objective of the embedding (Sec. 6.1): one-vs-rest L2-regularised
  * logistic regression (the LIBLINEAR model: for each label minimise
  * 1/2 |w|^2 + C sum log(1 + exp(-y w.x)), x with a constant-1 bias feature),
  * trained by `iters` Newton steps from w = 0 on the rows train_dev[0..n_train),
@@ -346,7 +346,7 @@ int lne_macro_f1(lne_ctx *ctx, const float *X_dev, int64_t n, int32_t d, int64_t
 int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_dev, void *stream);
 
 /*
- * Batched hyper-parameter tuning (Sec. 4.3: the method's parameters are tuned
+ * Batched hyper-parameter tuning (Sec. 4.4: the method's parameters are tuned
  * per data set by scoring many configurations on the downstream task). Each of
  * the ncand host candidates cands[j] is a full parameter set; the result for
  * candidate j equals lne_embed(cands[j]) followed by lne_macro_f1 on the given
@@ -367,7 +367,7 @@ int lne_tune_batch(lne_ctx *ctx, const lne_graph *g, const lne_params *cands, in
                    double *micro_f1, float *X_dev, void *stream);
 
 /*
- * Many independent tuning tasks (Sec. 4.3 tuning, repeated over data sets):
+ * Many independent tuning tasks (Sec. 4.4 tuning, repeated over data sets):
  * task t is a graph with its labels and split (the evaluation arguments of
  * lne_macro_f1); its ncand candidates are cands[t * ncand .. t * ncand + ncand)
  * and its scores land in macro_f1 / micro_f1[t * ncand + j] (host). Each task is
@@ -392,7 +392,7 @@ int lne_tune_tasks(lne_ctx *ctx, const lne_task *tasks, int32_t ntasks, const ln
 
 /*
  * Surrogate of the tuning search. The paper tunes its hyper-parameters per data
- * set with an AutoML search over full runs (Sec. 4.3); this regression network
+ * set with an AutoML search over full runs (Sec. 4.4); this regression network
  * predicts a candidate's downstream score from 30 features (s_1..s_10, k,
  * theta, mu, q and 16 graph statistics) so that the search runs only the
  * candidates it ranks highest. One network per context:
@@ -429,7 +429,7 @@ int lne_surrogate_grad(lne_ctx *ctx, const float *X_dev, const float *y_dev, int
 
 /*
  * Instrumentation (no counterpart in the paper, which reports wall-clock time
- * per stage only, Table "time distribution" of Sec. 5.4).
+ * per stage only, Table "time distribution" of Sec. 6.3).
  *
  * lne_kernel_launches: kernels launched by this library in this process so far.
  * lne_trace_enable: start (on != 0) or stop recording named regions; clears

@@ -9,7 +9,7 @@ Plain, slow, obviously checkable restatement of what the method computes, in
 FP64, each function citing the passage it follows:
 
 * sampling (C, ``lne_oracle.c``): Algorithm 1 (PathSampling), Algorithm 3
-  (per-edge sampling, Sec. 4.2) and the walk-step rule of Sec. 4.2, on
+  (per-edge sampling, Sec. 5.2) and the walk-step rule of Sec. 5.2, on
   unweighted graphs and on graphs with positive integer arc weights (walks
   on D^-1 A with weighted D, samples per arc proportional to its weight);
 * ``netmf_values`` / ``sparsifier_csr``: Eq. 1 (the NetMF matrix with the
@@ -17,7 +17,7 @@ FP64, each function citing the passage it follows:
 * ``stratified_*``: window-stratified counts shared by many weightings s
   (an unbiased importance-weighted estimate, not in the paper);
 * ``gaussian_sketch``: the Gaussian test matrix of Algorithm 4;
-* ``sparse_sign_sketch``: the sparse sign test matrix that Sec. 3.2 names as
+* ``sparse_sign_sketch``: the sparse sign test matrix that Sec. 4.2 names as
   an alternative to the Gaussian one (Tropp et al., SISC 2019): zeta
   nonzeros +-1 per row at distinct columns (Floyd's subset sampling);
 * ``very_sparse_sketch``: the very sparse random projection named beside it
@@ -25,9 +25,9 @@ FP64, each function citing the passage it follows:
   each, 0 otherwise;
 * ``eig_svd``: Algorithm 2 (eigSVD);
 * ``fast_randomized_svd``: Algorithm 4;
-* ``embedding_from_svd``: X = U Sigma^{1/2} (Sec. 3.2);
-* ``spectral_propagation``: Sec. 3.3 (Chebyshev filter in the normalised
-  Laplacian, then the economic SVD of the last stage, Sec. 5.4);
+* ``embedding_from_svd``: X = U Sigma^{1/2} (Sec. 4.2);
+* ``spectral_propagation``: Sec. 4.3 (Chebyshev filter in the normalised
+  Laplacian, then the economic SVD of the last stage, Sec. 6.3);
 * ``netmf_dense``: Eq. 1 evaluated densely, for tiny graphs.
 
 Library primitives used as single steps: numpy sort/unique, scipy sparse
@@ -266,7 +266,7 @@ def arc_downsample(indptr, indices, C: float, weights=None):
 def sparsifier_counts(indptr, indices, T, s, S, seed, C: float = 0.0, weights=None):
     """Exact multiplicity K_xy of every sampled unordered pair (x <= y).
 
-    The aggregation of Sec. 4.2 (hash table with atomic counts) computes the
+    The aggregation of Sec. 5.2 (hash table with atomic counts) computes the
     multiset of sampled pairs; here it is a sort and a run-length count.
     Returns (x, y, count) sorted by (x, y). With edge downsampling (C > 0) the
     third array is the pair's summed weight in 2^-32 units (uint64, exact):
@@ -494,7 +494,7 @@ def floyd_subset(t_words: np.ndarray, c: int) -> np.ndarray:
 
 def sparse_sign_sketch(n: int, c: int, zeta: int, seed: int) -> np.ndarray:
     """Sparse sign test matrix Omega (n x c): row i has exactly zeta nonzeros,
-    +1 or -1, at distinct columns (Sec. 3.2 names it as an alternative to
+    +1 or -1, at distinct columns (Sec. 4.2 names it as an alternative to
     the Gaussian Omega of Algorithm 4; the construction is that of Tropp et
     al., SISC 2019, applied to the rows of Omega so that M Omega costs zeta
     terms per nonzero of M).
@@ -612,12 +612,12 @@ def fast_randomized_svd(indptr, indices, data, d: int, q: int, oversample: int, 
 
 
 def embedding_from_svd(U: np.ndarray, sigma: np.ndarray) -> np.ndarray:
-    """X = U Sigma^{1/2} (Sec. 3.2)."""
+    """X = U Sigma^{1/2} (Sec. 4.2)."""
     return U * np.sqrt(sigma)[None, :]
 
 
 # ----------------------------------------------------------------------------
-# spectral propagation (Sec. 3.3)
+# spectral propagation (Sec. 4.3)
 # ----------------------------------------------------------------------------
 
 def chebyshev_coefficients(k: int, theta: float) -> np.ndarray:
@@ -634,11 +634,11 @@ def chebyshev_coefficients(k: int, theta: float) -> np.ndarray:
 def spectral_propagation(indptr, indices, X0: np.ndarray, k: int, theta: float, mu: float, weights=None):
     """Chebyshev spectral propagation of X0 on the graph.
 
-    With Lap = I - D^-1 A (the paper's normalised Laplacian, Sec. 3.3) and
+    With Lap = I - D^-1 A (the paper's normalised Laplacian, Sec. 4.3) and
     Yop = 1/2 (Lap - mu I)^2 - I (spectrum inside [-1, 1]):
       F = sum_{i<k} c_i T_i(Yop) X0,  T_0 = X0, T_1 = Yop X0,
       T_{i+1} = 2 Yop T_i - T_{i-1};
-      P = D^-1 A (X0 - F);  X = U_P Sigma_P^{1/2} from eigSVD(P) (Sec. 5.4).
+      P = D^-1 A (X0 - F);  X = U_P Sigma_P^{1/2} from eigSVD(P) (Sec. 6.3).
     k = 0 turns propagation off (X = X0). Degree-0 rows of D^-1 A are zero.
     """
     n = len(indptr) - 1
@@ -678,7 +678,7 @@ def spectral_propagation(indptr, indices, X0: np.ndarray, k: int, theta: float, 
 def embed(indptr, indices, T, s, S, d, q, k, theta, mu, seed, oversample=16, b=1.0, C=0.0,
           sketch="gaussian", zeta=8, weights=None, sparsity=0.0):
     """Sparsifier (edge-downsampled when C > 0, Sec. 4.1) -> randomized SVD
-    (Gaussian or sparse sign test matrix, Sec. 3.2) -> X0 -> spectral
+    (Gaussian or sparse sign test matrix, Sec. 4.2) -> X0 -> spectral
     propagation -> X."""
     sparse = sparsifier(indptr, indices, T, s, S, seed, b, C, weights=weights)
     rs = fast_randomized_svd(sparse["indptr"], sparse["indices"], sparse["data"], d, q,
@@ -698,12 +698,12 @@ def subspace_sin(U1: np.ndarray, U2: np.ndarray) -> float:
 
 
 # ----------------------------------------------------------------------------
-# downstream objective: one-vs-rest logistic regression, Macro-F1 (Sec. 5.1)
+# downstream objective: one-vs-rest logistic regression, Macro-F1 (Sec. 6.1)
 # ----------------------------------------------------------------------------
 
 def logreg_ovr(X: np.ndarray, Y: np.ndarray, C: float = 1.0, iters: int = 10) -> np.ndarray:
     """One-vs-rest L2-regularised logistic regression (the LIBLINEAR model of
-    Sec. 5.1): for each label l, minimise 1/2 |w|^2 + C sum_i log(1 + exp(-y_il w.x_i))
+    Sec. 6.1): for each label l, minimise 1/2 |w|^2 + C sum_i log(1 + exp(-y_il w.x_i))
     with y in {-1, +1} and a constant-1 bias feature appended to x. Solved by
     `iters` Newton steps from w = 0 (a library solve per step). Returns W of
     shape (d + 1, L)."""

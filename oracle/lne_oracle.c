@@ -7,10 +7,10 @@
  * A plain, slow restatement of the paper's sampling steps, written from:
  *   - Algorithm 1 (PathSampling): split s uniform in [0, r-1], walk u for s
  *     steps, walk v for r-1-s steps, return (u', v').
- *   - Algorithm 3 (per-edge PathSampling, Sec. 4.2): map over the edges; edge e
+ *   - Algorithm 3 (per-edge PathSampling, Sec. 5.2): map over the edges; edge e
  *     gets n_e = floor(M/m) + Bernoulli({M/m}) samples; each sample draws the
  *     window length r from Multinomial(s_1..s_T).
- *   - Sec. 4.2, last paragraph: one walk step takes a uniform 32-bit value
+ *   - Sec. 5.2, fetching a vertex's i-th edge: one walk step takes a uniform 32-bit value
  *     modulo the vertex degree.
  * Random numbers come from Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11),
  * implemented here from its published definition.

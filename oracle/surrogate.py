@@ -3,7 +3,7 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU legs may
 import this module; the product never does.
 
-The paper tunes its hyper-parameters with an external AutoML search (Sec. 4.3);
+The paper tunes its hyper-parameters with an external AutoML search (Sec. 4.4);
 the GPU library replaces most of the full runs of that search with a small
 regression network trained on the scores that full runs produce. This module
 states that network plainly:

@@ -15,7 +15,7 @@
 //                  Ogita-Aishima refinement in FP64, so Y = Q R gives left
 //                  singular vectors Q U_R -- the final eigSVD of Algorithm 4.
 //   sign_fix_embed largest-magnitude entry of each column made positive, and
-//                  X = U Sigma^{1/2} (Sec. 3.2).
+//                  X = U Sigma^{1/2} (Sec. 4.2).
 #include <algorithm>
 #include <cmath>
 #include <mutex>

@@ -1,4 +1,4 @@
-// Downstream objective (Sec. 5.1): one-vs-rest L2-regularised logistic
+// Downstream objective (Sec. 6.1): one-vs-rest L2-regularised logistic
 // regression on the embedding, then Micro/Macro-F1 with the top-k rule (each
 // test node predicts its k highest-scoring labels, k = its number of labels).
 //

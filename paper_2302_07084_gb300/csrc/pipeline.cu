@@ -1,5 +1,5 @@
 // Composition of the stages: fast randomized SVD (Algorithm 4) and spectral
-// propagation (Sec. 3.3 / Sec. 5.4).
+// propagation (Sec. 4.3 / Sec. 5.4).
 #include <cmath>
 #include <utility>
 
@@ -104,7 +104,7 @@ int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t
         return spmm(ws, Mb, X, c, c, Y, c, st);
     };
     // Algorithm 4: Omega = randn(n, d+s); Y = M Omega. The sparse sign Omega
-    // (Sec. 3.2's cheaper alternative) is applied without being formed; its
+    // (Sec. 4.2's cheaper alternative) is applied without being formed; its
     // product is exact up to one rounding, in either precision mode.
     if (sketch.kind == LNE_SKETCH_SPARSE_SIGN) {
         const int zeta = sketch.zeta > 0 ? sketch.zeta : std::min(8, c);

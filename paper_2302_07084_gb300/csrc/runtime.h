@@ -252,7 +252,7 @@ int sparse_sign_dense(Workspace &ws, int64_t n, int c, int zeta, uint64_t seed, 
 int sparse_sign_spmm(Workspace &ws, const CsrView &M, int c, int zeta, uint64_t seed, float *Y, int64_t ldy,
                      cudaStream_t st);
 
-// Randomized SVD (Algorithm 4) and propagation (Sec. 3.3).
+// Randomized SVD (Algorithm 4) and propagation (Sec. 4.3).
 int rsvd(Workspace &ws, const CsrView &M, int d, int oversample, int q, uint64_t seed, int precision,
          float *U, double *sigma, float *X0, cudaStream_t st, const SketchSpec &sketch = SketchSpec());
 int propagate(Workspace &ws, const GraphView &g, int d, int k, double theta, double mu, int precision,

@@ -1,4 +1,4 @@
-// Sparsifier construction on the GPU (Sec. 4.2 of the paper, re-designed):
+// Sparsifier construction on the GPU (Sec. 5.2 of the paper, re-designed):
 //
 //   1. tile_counts     per-arc sample counts n_a = floor(S/2m) + Bernoulli
 //                      (Algorithm 3) summed per tile of arcs; scanned
@@ -6,7 +6,7 @@
 //   2. walk_emit       one thread per sample: window r ~ Multinomial(s)
 //                      (Algorithm 3), split sigma ~ U{0..r-1} and the
 //                      two walks of PathSampling (Algorithm 1), each step
-//                      x <- nbr(x)[word mod deg(x)] (Sec. 4.2). Emits the
+//                      x <- nbr(x)[word mod deg(x)] (Sec. 5.2). Emits the
 //                      canonical pair key (min << B | max) and a shared-memory
 //                      histogram of key buckets.
 //   3. bucket_scatter  moves keys into their bucket's region (CTA-aggregated
@@ -245,7 +245,7 @@ __device__ __forceinline__ uint32_t barrett_mod(uint32_t w, uint32_t m, uint32_t
     return r >= d ? r - d : r;
 }
 
-// One walk step: x <- nbr(x)[w mod deg(x)] (Sec. 4.2), reading the taken
+// One walk step: x <- nbr(x)[w mod deg(x)] (Sec. 5.2), reading the taken
 // arc's record. GEN: the variant that also handles weighted graphs.
 template <bool GEN>
 __device__ __forceinline__ void walk_step(const WalkArgs &A, WalkCur &c, uint32_t w) {

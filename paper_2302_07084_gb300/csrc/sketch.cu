@@ -1,4 +1,4 @@
-// Sparse sign test matrix for the randomized SVD (Algorithm 4; Sec. 3.2
+// Sparse sign test matrix for the randomized SVD (Algorithm 4; Sec. 4.2
 // names very sparse and sparse sign projections as cheaper alternatives to
 // the Gaussian Omega; the construction follows Tropp et al., SISC 2019).
 //

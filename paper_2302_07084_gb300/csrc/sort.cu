@@ -1,5 +1,5 @@
 // Sorting and run-length counting of 64-bit pair keys, for graphs whose pair
-// space does not fit a dense count table (the hash aggregation of Sec. 4.2
+// space does not fit a dense count table (the hash aggregation of Sec. 5.2
 // done as sort + run-length instead: exact counts, deterministic order).
 //
 // radix_sort_u64: stable LSD radix sort, 8 bits per pass over the low `bits`

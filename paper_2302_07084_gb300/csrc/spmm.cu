@@ -1,7 +1,7 @@
 // Sparse x dense products of the hot path:
 //   * Y = M X with the weighted sparsifier M (Algorithm 4);
 //   * the propagation products with the unweighted graph A, where the row
-//     scale 1/deg(i) (D^-1 A) and the Chebyshev recurrence of Sec. 3.3 are
+//     scale 1/deg(i) (D^-1 A) and the Chebyshev recurrence of Sec. 4.3 are
 //     fused into the epilogue:  out = alpha * rs_i (A X)_i + b1 E1 + b2 E2 + b3 E3,
 //     optionally F += gamma * out and G = X0 - F.
 //

@@ -1,4 +1,4 @@
-// Surrogate of the tuning search (Sec. 4.3 tunes the method's hyper-parameters
+// Surrogate of the tuning search (Sec. 4.4 tunes the method's hyper-parameters
 // by scoring many configurations; a regression network trained on scores of
 // full runs ranks candidates so that only the most promising ones are run).
 //

@@ -1,4 +1,4 @@
-// Batched parameter tuning (Sec. 4.3: the hyper-parameters of the method --
+// Batched parameter tuning (Sec. 4.4: the hyper-parameters of the method --
 // window weights, sample count, filter k / theta / mu -- are tuned by running
 // many candidate configurations on one graph and keeping the best downstream
 // Macro-F1).
@@ -16,7 +16,7 @@
 //     candidate set of the same shape;
 //   * the merge SpMM's CTA size is picked by timing (results do not depend on
 //     it: every warp owns the same nonzero slice whatever the CTA size).
-// Each candidate then gets its own final SVD (Sec. 5.4 economic SVD of P) and
+// Each candidate then gets its own final SVD (Sec. 6.3: eigSVD as the economic SVD of P) and
 // its own Macro-F1.
 #include <algorithm>
 #include <atomic>

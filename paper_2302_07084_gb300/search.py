@@ -2,7 +2,7 @@
 
 The paper tunes T-window weights s_r, the filter (k, theta, mu) and q per data
 set with an AutoML search in which every trial is a full run scored by the
-downstream Macro-F1 (Sec. 4.3, Sec. 5.1). Here a small regression network
+downstream Macro-F1 (Sec. 4.4, Sec. 6.1). Here a small regression network
 (the surrogate, trained on the GPU by the library's own kernels) predicts that
 score from 30 features -- the candidate's parameters and 16 statistics of the
 graph -- so a search can rank a large pool of candidates and run the method

@@ -5,7 +5,7 @@ planted labels. It holds none of the embedding method's arithmetic, so both the
 CUDA path and the CPU oracle can be fed from it.
 
 Graph families (the paper's datasets are not available, Table "Datasets
-statistics" in Sec. 5.1 gives their shapes):
+statistics" in Sec. 6.1 gives their shapes):
 
 * ``sbm``            -- stochastic block model with equal or given block sizes.
 * ``chung_lu``       -- power-law expected-degree graph (Chung-Lu), optionally with

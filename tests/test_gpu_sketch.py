@@ -1,5 +1,5 @@
 """The sparse sign test matrix of the randomized SVD (the alternative to the
-Gaussian Omega named in Sec. 3.2; Tropp et al. 2019) on the GPU against the
+Gaussian Omega named in Sec. 4.2; Tropp et al. 2019) on the GPU against the
 oracle:
 
 * the matrix itself bit-exact (every +-1 at the oracle's place), including

@@ -1,4 +1,4 @@
-"""Pins of the oracle's downstream objective (Sec. 5.1: one-vs-rest logistic
+"""Pins of the oracle's downstream objective (Sec. 6.1: one-vs-rest logistic
 regression, Micro/Macro-F1) against scikit-learn, an implementation the oracle
 does not use, and against hand-counted cases."""
 import numpy as np

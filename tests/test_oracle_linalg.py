@@ -9,7 +9,7 @@
   Algorithm 4 with it recovers a planted spectrum.
 * The Chebyshev coefficients expand exp(-theta y) (Bessel generating function).
 * Spectral propagation equals the filter evaluated on the eigenvalues of the
-  normalised Laplacian (Sec. 3.3), computed independently from a dense
+  normalised Laplacian (Sec. 4.3), computed independently from a dense
   eigendecomposition and cos(i arccos y).
 """
 import numpy as np
@@ -170,7 +170,7 @@ def test_embedding_recovers_blocks():
     assert acc > 0.9
 
 
-# sparse sign test matrix (the alternative Omega of Sec. 3.2; Tropp et al. 2019)
+# sparse sign test matrix (the alternative Omega of Sec. 4.2; Tropp et al. 2019)
 
 def test_floyd_subset_exhaustive():
     """Every word combination of Floyd's steps for c = 6, zeta = 3: each of the
