@@ -335,8 +335,9 @@ int lne_propagate(lne_ctx *ctx, const lne_graph *g, const lne_params *p, const f
  * number of true labels). X_dev [n][ldx] float (d columns used, d <= 159);
  * labels_dev [n][L] uint8 0/1; train/test row indices int32 on the device.
  * *macro_f1 = mean over labels of 2TP / (2TP + FP + FN) (0 for a label with no
- * positives or predictions), *micro_f1 = the same on pooled counts. Host
- * outputs: synchronises.
+ * positives or predictions), *micro_f1 = the same on pooled counts. A train
+ * or test index outside [0, n) is not read: the call returns LNE_ERR_INVALID.
+ * Host outputs: synchronises.
  */
 int lne_macro_f1(lne_ctx *ctx, const float *X_dev, int64_t n, int32_t d, int64_t ldx, const uint8_t *labels_dev,
                  int32_t L, const int32_t *train_dev, int64_t n_train, const int32_t *test_dev, int64_t n_test,

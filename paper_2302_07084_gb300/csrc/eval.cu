@@ -21,20 +21,29 @@ namespace {
 
 constexpr int kEvalRows = 128;   // rows per FP32 partial sum (and per CTA)
 
-// Xa[i] = (X[idx[i]], 1), Ys[i][l] = +1 / -1.
-__global__ void gather_rows_kernel(const float *__restrict__ X, int64_t ldx, int d, const uint8_t *__restrict__ lab,
-                                   int L, const int32_t *__restrict__ idx, int64_t m, float *__restrict__ Xa,
-                                   float *__restrict__ Ys) {
+// Xa[i] = (X[idx[i]], 1), Ys[i][l] = +1 / -1. A row index outside [0, n) is
+// not read: its row becomes zeros (label -1) and status bit 2 is set, which
+// the host turns into LNE_ERR_INVALID.
+__global__ void gather_rows_kernel(const float *__restrict__ X, int64_t n, int64_t ldx, int d,
+                                   const uint8_t *__restrict__ lab, int L, const int32_t *__restrict__ idx, int64_t m,
+                                   float *__restrict__ Xa, float *__restrict__ Ys, int *__restrict__ status) {
     const int da = d + 1;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * da; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e / da;
         const int j = (int)(e - i * da);
-        Xa[e] = j < d ? X[(int64_t)idx[i] * ldx + j] : 1.0f;
+        const int64_t r = idx[i];
+        if (r < 0 || r >= n) {
+            if (j == 0) atomicOr(status, 2);
+            Xa[e] = 0.0f;
+            continue;
+        }
+        Xa[e] = j < d ? X[r * ldx + j] : 1.0f;
     }
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * L; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e / L;
         const int l = (int)(e - i * L);
-        Ys[e] = lab[(int64_t)idx[i] * L + l] ? 1.0f : -1.0f;
+        const int64_t r = idx[i];
+        Ys[e] = (r >= 0 && r < n && lab[r * L + l]) ? 1.0f : -1.0f;
     }
 }
 
@@ -135,7 +144,7 @@ __global__ void __launch_bounds__(512) newton_solve_kernel(const double *__restr
         if (tid == 0) {
             const double akk = A[k * da + k];
             if (!(akk > 0.0)) {
-                atomicExch(status, 1);
+                atomicOr(status, 1);
                 A[k * da + k] = 1.0;
                 s_inv = 1.0;
             } else {
@@ -226,9 +235,11 @@ int macro_f1(Workspace &ws, const float *X, int64_t n, int d, int64_t ldx, const
     LNE_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), st));
     {
         LNE_TRACE("eval_gather", st);
-        gather_rows_kernel<<<egrid(n_train * da), 256, 0, st>>>(X, ldx, d, labels, L, train_idx, n_train, Xa, Ys);
+        gather_rows_kernel<<<egrid(n_train * da), 256, 0, st>>>(X, n, ldx, d, labels, L, train_idx, n_train, Xa, Ys,
+                                                                status);
         LNE_LAUNCH_CHECK();
-        gather_rows_kernel<<<egrid(n_test * da), 256, 0, st>>>(X, ldx, d, labels, L, test_idx, n_test, Xt, Yt);
+        gather_rows_kernel<<<egrid(n_test * da), 256, 0, st>>>(X, n, ldx, d, labels, L, test_idx, n_test, Xt, Yt,
+                                                               status);
         LNE_LAUNCH_CHECK();
     }
     const int hsmem = 2 * kEvalRows * dp * 4;
@@ -263,6 +274,7 @@ int macro_f1(Workspace &ws, const float *X, int64_t n, int d, int64_t ldx, const
     LNE_CUDA_TRY(cudaMemcpyAsync(h.data(), cnt, sizeof(unsigned long long) * 3 * L, cudaMemcpyDeviceToHost, st));
     LNE_CUDA_TRY(cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st));
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hs & 2) return fail(LNE_ERR_INVALID, "a train or test row index is outside [0, n)");
     if (hs) return fail(LNE_ERR_NUMERIC, "a logistic-regression Hessian was not positive definite");
     double f1sum = 0.0, tp = 0, fp = 0, fn = 0;
     for (int l = 0; l < L; ++l) {

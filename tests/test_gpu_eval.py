@@ -75,3 +75,24 @@ def test_macro_f1_rejects_bad_args(ctx):
     idx = torch.arange(5, dtype=torch.int32, device="cuda")
     with pytest.raises(lne.LneError):
         ctx.macro_f1(X, lab, idx, idx, C=-1.0)
+
+
+def test_macro_f1_rejects_row_index_outside_n(ctx):
+    """Row indices outside [0, n) are caught by the gather kernel's own bounds
+    check (nothing is read there) and reported as LNE_ERR_INVALID; the context
+    stays usable."""
+    n, d, L = 40, 4, 2
+    gen = torch.Generator().manual_seed(5)
+    X = torch.randn((n, d), generator=gen).cuda()
+    lab = torch.zeros((n, L), dtype=torch.uint8)
+    lab[: n // 2, 0] = 1
+    lab[n // 2:, 1] = 1
+    lab = lab.cuda()
+    good = torch.arange(n, dtype=torch.int32, device="cuda")
+    for bad_train, bad_test in ((True, False), (False, True)):
+        bad = good.clone()
+        bad[3] = n if bad_train else -1
+        with pytest.raises(lne.LneError, match="outside"):
+            ctx.macro_f1(X, lab, bad if bad_train else good, bad if bad_test else good)
+    ma, mi = ctx.macro_f1(X, lab, good, good)
+    assert 0.0 <= ma <= 1.0 and 0.0 <= mi <= 1.0
