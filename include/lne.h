@@ -24,9 +24,15 @@
  *     the last failure is returned by lne_last_error. A failed call leaves the
  *     context usable.
  *   - Graphs are undirected and unweighted: symmetric CSR, no self-loops, no
- *     duplicate edges, rows sorted. Only cheap checks are made (sizes, indptr
- *     monotone end points); a graph that breaks the contract gives undefined
- *     (but memory-safe within the stated sizes) results.
+ *     duplicate edges, rows sorted. Every call that takes an lne_graph checks
+ *     its structure on the device first (one pass over indptr and indices):
+ *     indptr starts at 0, ends at nnz and never decreases, and every index
+ *     lies in [0, n); otherwise it returns LNE_ERR_INVALID before any kernel
+ *     walks the graph. Symmetry, self-loops, duplicates and row order are not
+ *     checked: a graph that breaks them gives undefined results.
+ *   - A CSR matrix handed to lne_spmm / lne_rsvd (lne_csr) is not checked (the
+ *     calls stay asynchronous): its indptr must be non-decreasing from 0 to
+ *     nnz and its indices must lie in [0, n).
  */
 #ifndef LNE_H
 #define LNE_H

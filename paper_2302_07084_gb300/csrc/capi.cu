@@ -288,14 +288,46 @@ lne::CsrView csr_view(const lne_csr *M) {
     return v;
 }
 
-// Checks the graph's end points on the device (indptr[0] == 0, indptr[n] == nnz).
-int check_graph_device(const lne_graph *g, cudaStream_t st) {
+// The CSR structure of a graph: bit 1 of *bad for an indptr entry below its
+// predecessor, bit 2 for a column index outside [0, n). Reads indptr[0..n]
+// and indices[0..nnz) only. With indptr[0] = 0 and indptr[n] = nnz (checked
+// on the host), a non-decreasing indptr keeps every row inside [0, nnz).
+__global__ void csr_structure_kernel(const int64_t *__restrict__ indptr, int64_t n,
+                                     const int32_t *__restrict__ indices, int64_t nnz, int *__restrict__ bad) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int f = 0;
+    for (int64_t i = t0; i < n; i += stride)
+        if (indptr[i + 1] < indptr[i]) f |= 1;
+    for (int64_t e = t0; e < nnz; e += stride) {
+        const int32_t v = indices[e];
+        if (v < 0 || (int64_t)v >= n) f |= 2;
+    }
+    if (f) atomicOr(bad, f);
+}
+
+// Checks the graph on the device before any kernel walks it: indptr starts at
+// 0, ends at nnz and never decreases, and every index lies in [0, n).
+int check_graph_device(lne_ctx *ctx, const lne_graph *g, cudaStream_t st) {
     int64_t ends[2] = {0, 0};
+    int bad = 0;
+    int *bad_dev = nullptr;
+    LNE_TRY(ctx->ws.get("graph.check", 1, &bad_dev));
+    LNE_CUDA_TRY(cudaMemsetAsync(bad_dev, 0, sizeof(int), st));
+    {
+        const int64_t work = std::max<int64_t>(std::max<int64_t>(g->n, g->nnz), 1);
+        const unsigned blocks = (unsigned)std::min<int64_t>(lne::ceil_div(work, (int64_t)256), lne::num_sms() * 8);
+        csr_structure_kernel<<<blocks, 256, 0, st>>>(g->indptr, g->n, g->indices, g->nnz, bad_dev);
+        LNE_LAUNCH_CHECK();
+    }
     LNE_CUDA_TRY(cudaMemcpyAsync(&ends[0], g->indptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     LNE_CUDA_TRY(cudaMemcpyAsync(&ends[1], g->indptr + g->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LNE_CUDA_TRY(cudaMemcpyAsync(&bad, bad_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
     LNE_CUDA_TRY(cudaStreamSynchronize(st));
     if (ends[0] != 0 || ends[1] != g->nnz)
         return lne::fail(LNE_ERR_INVALID, "graph indptr must start at 0 and end at nnz");
+    if (bad & 1) return lne::fail(LNE_ERR_INVALID, "graph indptr decreases");
+    if (bad & 2) return lne::fail(LNE_ERR_INVALID, "a graph index is outside [0, n)");
     return 0;
 }
 
@@ -453,7 +485,7 @@ int lne_sample_pairs(lne_ctx *ctx, const lne_graph *g, const lne_params *p, int6
     if (rc == 0 && (!count_out || (capacity > 0 && (!u1_dev || !v1_dev))))
         rc = lne::fail(LNE_ERR_INVALID, "NULL output");
     cudaStream_t st = as_stream(stream);
-    if (rc == 0) rc = check_graph_device(g, st);
+    if (rc == 0) rc = check_graph_device(ctx, g, st);
     lne::GraphView gv = view(g);
     if (rc == 0) rc = lne::prepare_weighted(ctx->ws, &gv, st);
     lne::SamplerSpec sp;
@@ -474,7 +506,7 @@ int lne_sparsifier_counts(lne_ctx *ctx, const lne_graph *g, const lne_params *p,
     if (rc == 0) rc = check_params(p, true);
     if (rc == 0 && !out) rc = lne::fail(LNE_ERR_INVALID, "NULL output");
     cudaStream_t st = as_stream(stream);
-    if (rc == 0) rc = check_graph_device(g, st);
+    if (rc == 0) rc = check_graph_device(ctx, g, st);
     lne::GraphView gv = view(g);
     if (rc == 0) rc = lne::prepare_weighted(ctx->ws, &gv, st);
     lne::SamplerSpec sp;
@@ -503,7 +535,7 @@ int lne_sparsifier_csr(lne_ctx *ctx, const lne_graph *g, const lne_params *p, ln
     if (rc == 0) rc = check_params(p, true);
     if (rc == 0 && !out) rc = lne::fail(LNE_ERR_INVALID, "NULL output");
     cudaStream_t st = as_stream(stream);
-    if (rc == 0) rc = check_graph_device(g, st);
+    if (rc == 0) rc = check_graph_device(ctx, g, st);
     lne::GraphView gv = view(g);
     if (rc == 0) rc = lne::prepare_weighted(ctx->ws, &gv, st);
     lne::SamplerSpec sp;
@@ -679,7 +711,7 @@ int lne_embed(lne_ctx *ctx, const lne_graph *g, const lne_params *p, float *X_de
     if (rc == 0 && !X_dev) rc = lne::fail(LNE_ERR_INVALID, "NULL embedding buffer");
     if (rc == 0 && (p->k < 0 || p->q < 0 || p->d < 1)) rc = lne::fail(LNE_ERR_INVALID, "need d >= 1, q >= 0, k >= 0");
     cudaStream_t st = as_stream(stream);
-    if (rc == 0) rc = check_graph_device(g, st);
+    if (rc == 0) rc = check_graph_device(ctx, g, st);
     lne::GraphView gv = view(g);
     if (rc == 0) rc = lne::prepare_weighted(ctx->ws, &gv, st);
     lne::SamplerSpec sp;
@@ -716,7 +748,7 @@ int lne_tune_batch(lne_ctx *ctx, const lne_graph *g, const lne_params *cands, in
     if (rc == 0 && (!labels_dev || L < 1 || !train_dev || n_train < 1 || !test_dev || n_test < 1 || iters < 0))
         rc = lne::fail(LNE_ERR_INVALID, "bad evaluation split or labels");
     cudaStream_t st = as_stream(stream);
-    if (rc == 0) rc = check_graph_device(g, st);
+    if (rc == 0) rc = check_graph_device(ctx, g, st);
     lne::GraphView gv = view(g);
     if (rc == 0) rc = lne::prepare_weighted(ctx->ws, &gv, st);
     if (rc == 0 && !ctx->prop_graph) ctx->prop_graph = lne::new_prop_cache();
@@ -745,7 +777,7 @@ int lne_tune_tasks(lne_ctx *ctx, const lne_task *tasks, int32_t ntasks, const ln
         if (rc == 0 && (!k.labels_dev || k.L < 1 || !k.train_dev || k.n_train < 1 || !k.test_dev || k.n_test < 1))
             rc = lne::fail(LNE_ERR_INVALID, "bad evaluation split or labels");
         for (int j = 0; rc == 0 && j < ncand; ++j) rc = check_params(&cands[(size_t)t * ncand + j], true);
-        if (rc == 0) rc = check_graph_device(&k.graph, st);
+        if (rc == 0) rc = check_graph_device(ctx, &k.graph, st);
         if (rc == 0) {
             tt[t].g = view(&k.graph);
             tt[t].labels = k.labels_dev;

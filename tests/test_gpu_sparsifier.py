@@ -141,8 +141,24 @@ def test_bad_arguments_are_rejected(ctx):
     # indptr not ending at nnz
     broken = lne.DeviceGraph(g.indptr, g.indices)
     broken.nnz = g.n_arcs - 1
+    ok = make_params(10, np.ones(10), 10.0 * g.n_arcs)
     with pytest.raises(lne.LneError):
-        ctx.sparsifier_counts(broken, make_params(10, np.ones(10), 10.0 * g.n_arcs))
+        ctx.sparsifier_counts(broken, ok)
+    # an index outside [0, n) and an indptr that decreases between valid end
+    # points: the library's device check of the CSR refuses both before any
+    # kernel walks the graph, and the context stays usable
+    for v in (g.n, -3):
+        idx = g.indices.copy()
+        idx[5] = v
+        with pytest.raises(lne.LneError, match="outside"):
+            ctx.sparsifier_counts(lne.DeviceGraph(g.indptr, idx), ok)
+    ip = g.indptr.copy()
+    k = g.n // 2
+    assert ip[k - 1] >= 1
+    ip[k] = ip[k - 1] - 1
+    with pytest.raises(lne.LneError, match="decreases"):
+        ctx.sparsifier_counts(lne.DeviceGraph(ip, g.indices), ok)
+    assert int(ctx.sparsifier_counts(dg, ok)["count"].to(torch.int64).sum()) > 0
 
 
 def test_bench_workload_sampled(ctx):
