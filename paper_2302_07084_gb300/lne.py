@@ -177,6 +177,32 @@ class Params:
         return p, arr
 
 
+def _check_tensor(name, t, device, dtype=None, shape=None, min_rows=None, cols=None, min_numel=None):
+    """Checks a tensor whose raw pointer goes to the library: on `device`,
+    contiguous, of the given dtype (or one of a tuple of them), and at least as
+    large as what the library reads or writes through it. A mismatch raises
+    ValueError before anything is launched."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name} must be a tensor, got {type(t).__name__}")
+    if t.device != device:
+        raise ValueError(f"{name} is on {t.device}; the library needs it on {device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None:
+        ok = dtype if isinstance(dtype, tuple) else (dtype,)
+        if t.dtype not in ok:
+            raise ValueError(f"{name} must be {' or '.join(str(x) for x in ok)}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(int(x) for x in shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if min_rows is not None and (t.dim() < 1 or t.shape[0] < min_rows):
+        raise ValueError(f"{name} needs at least {min_rows} rows, got shape {tuple(t.shape)}")
+    if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+        raise ValueError(f"{name} must be 2-D with {cols} columns, got shape {tuple(t.shape)}")
+    if min_numel is not None and t.numel() < min_numel:
+        raise ValueError(f"{name} needs at least {min_numel} elements, got {t.numel()}")
+    return t
+
+
 class DeviceGraph:
     """A CSR graph resident on the GPU (int64 indptr, int32 indices, optional
     positive integer arc weights held as their uint32 bits)."""
@@ -206,7 +232,13 @@ class DeviceGraph:
         g.weights = None
         return g
 
-    def _c(self):
+    def _c(self, device):
+        """The C struct; the arrays are checked against n and nnz first (the
+        library reads indptr[0..n] and indices / weights [0..nnz))."""
+        _check_tensor("graph indptr", self.indptr, device, torch.int64, min_numel=self.n + 1)
+        _check_tensor("graph indices", self.indices, device, torch.int32, min_numel=self.nnz)
+        if self.weights is not None:
+            _check_tensor("graph weights", self.weights, device, torch.int32, min_numel=self.nnz)
         w = self.weights.data_ptr() if self.weights is not None and self.nnz else None
         return _Graph(self.n, self.nnz, self.indptr.data_ptr(), self.indices.data_ptr() if self.nnz else None, w)
 
@@ -266,7 +298,8 @@ def _stream():
 def _ptr(t: Optional[torch.Tensor]):
     if t is None:
         return None
-    assert t.is_cuda and t.is_contiguous()
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError(f"the library needs a contiguous CUDA tensor, got one on {t.device}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -338,7 +371,7 @@ class Context:
         u1 = torch.empty(capacity, dtype=torch.int32, device=self.dev)
         v1 = torch.empty(capacity, dtype=torch.int32, device=self.dev)
         cnt = ctypes.c_int64()
-        gc = g._c()
+        gc = g._c(self.dev)
         pc, keep = p._c()
         self._check(self.lib.lne_sample_pairs(self.h, ctypes.byref(gc), ctypes.byref(pc), arc_begin, arc_end,
                                               _ptr(u1), _ptr(v1), capacity, ctypes.byref(cnt), _stream()))
@@ -346,7 +379,7 @@ class Context:
 
     def sparsifier_counts(self, g: DeviceGraph, p: Params):
         out = _Counts()
-        gc = g._c()
+        gc = g._c(self.dev)
         pc, keep = p._c()
         self._check(self.lib.lne_sparsifier_counts(self.h, ctypes.byref(gc), ctypes.byref(pc), ctypes.byref(out),
                                                    _stream()))
@@ -367,7 +400,7 @@ class Context:
         """The trunc_log sparsifier as a CSR dict. copy=False returns views of
         the context's buffers, valid until the next call on this context."""
         out = _Csr()
-        gc = g._c()
+        gc = g._c(self.dev)
         pc, keep = p._c()
         self._check(self.lib.lne_sparsifier_csr(self.h, ctypes.byref(gc), ctypes.byref(pc), ctypes.byref(out),
                                                 _stream()))
@@ -393,8 +426,8 @@ class Context:
 
     def sparse_sign_spmm(self, csr: dict, c: int, zeta: int, seed: int) -> torch.Tensor:
         """Y = M Omega for the sparse sign Omega (never formed)."""
-        Y = torch.empty((int(csr["n"]), c), dtype=torch.float32, device=self.dev)
         m = self._csr(csr)
+        Y = torch.empty((int(csr["n"]), c), dtype=torch.float32, device=self.dev)
         self._check(self.lib.lne_sparse_sign_spmm(self.h, ctypes.byref(m), c, zeta, int(seed) & 0xFFFFFFFFFFFFFFFF,
                                                   _ptr(Y), c, _stream()))
         return Y
@@ -408,32 +441,42 @@ class Context:
 
     def very_sparse_spmm(self, csr: dict, c: int, s: float, seed: int) -> torch.Tensor:
         """Y = M Omega for the very sparse Omega (never formed)."""
-        Y = torch.empty((int(csr["n"]), c), dtype=torch.float32, device=self.dev)
         m = self._csr(csr)
+        Y = torch.empty((int(csr["n"]), c), dtype=torch.float32, device=self.dev)
         self._check(self.lib.lne_very_sparse_spmm(self.h, ctypes.byref(m), c, float(s),
                                                   int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(Y), c, _stream()))
         return Y
 
-    @staticmethod
-    def _csr(csr: dict) -> _Csr:
-        return _Csr(int(csr["n"]), int(csr["nnz"]), csr["indptr"].data_ptr(),
-                    csr["indices"].data_ptr() if csr["nnz"] else None,
-                    csr["data"].data_ptr() if csr["nnz"] else None)
+    def _csr(self, csr: dict) -> _Csr:
+        n, nnz = int(csr["n"]), int(csr["nnz"])
+        _check_tensor("CSR indptr", csr["indptr"], self.dev, torch.int64, min_numel=n + 1)
+        if nnz:
+            _check_tensor("CSR indices", csr["indices"], self.dev, torch.int32, min_numel=nnz)
+            _check_tensor("CSR data", csr["data"], self.dev, torch.float32, min_numel=nnz)
+        return _Csr(n, nnz, csr["indptr"].data_ptr(), csr["indices"].data_ptr() if nnz else None,
+                    csr["data"].data_ptr() if nnz else None)
 
     def spmm(self, csr: dict, X: torch.Tensor) -> torch.Tensor:
         """Y = M X; X float32 or bfloat16 (FP32 accumulation either way)."""
         X = X.contiguous()
+        if X.dim() != 2:
+            raise ValueError(f"X must be 2-D, got shape {tuple(X.shape)}")
         n, c = X.shape
         prec = PREC_BF16_MIXED if X.dtype == torch.bfloat16 else PREC_FP32
         if prec == PREC_FP32:
             X = X.float()
-        Y = torch.empty((int(csr["n"]), c), dtype=torch.float32, device=self.dev)
         m = self._csr(csr)
+        # the product gathers X rows by column index (< csr n)
+        _check_tensor("X", X, self.dev, min_rows=int(csr["n"]))
+        Y = torch.empty((int(csr["n"]), c), dtype=torch.float32, device=self.dev)
         self._check(self.lib.lne_spmm(self.h, ctypes.byref(m), _ptr(X), c, c, _ptr(Y), c, prec, _stream()))
         return Y
 
     def cholqr2(self, Y: torch.Tensor):
         """Returns (Q, R): Q overwrites a copy of Y; R is FP64 upper triangular."""
+        _check_tensor("Y", Y.contiguous(), self.dev, torch.float32)
+        if Y.dim() != 2:
+            raise ValueError(f"Y must be 2-D, got shape {tuple(Y.shape)}")
         Q = Y.contiguous().clone()
         n, c = Q.shape
         R = torch.zeros((c, c), dtype=torch.float64, device=self.dev)
@@ -443,6 +486,9 @@ class Context:
     def svd_small(self, R: torch.Tensor):
         """(U, sigma) of a small FP64 matrix R."""
         R = R.to(torch.float64).contiguous()
+        if R.dim() != 2 or R.shape[0] != R.shape[1]:
+            raise ValueError(f"R must be square, got shape {tuple(R.shape)}")
+        _check_tensor("R", R, self.dev)
         c = R.shape[0]
         U = torch.empty((c, c), dtype=torch.float64, device=self.dev)
         sig = torch.empty(c, dtype=torch.float64, device=self.dev)
@@ -451,10 +497,10 @@ class Context:
 
     def rsvd(self, csr: dict, p: Params):
         n = int(csr["n"])
+        m = self._csr(csr)
         U = torch.empty((n, p.d), dtype=torch.float32, device=self.dev)
         X0 = torch.empty((n, p.d), dtype=torch.float32, device=self.dev)
         sig = torch.empty(p.d, dtype=torch.float64, device=self.dev)
-        m = self._csr(csr)
         pc, keep = p._c()
         self._check(self.lib.lne_rsvd(self.h, ctypes.byref(m), ctypes.byref(pc), _ptr(U), _ptr(sig), _ptr(X0),
                                       _stream()))
@@ -462,10 +508,11 @@ class Context:
 
     def propagate(self, g: DeviceGraph, p: Params, X0: torch.Tensor, want_intermediates: bool = False):
         X0 = X0.contiguous()
+        gc = g._c(self.dev)
+        _check_tensor("X0", X0, self.dev, torch.float32, shape=(g.n, p.d))
         X = torch.empty_like(X0)
         F = torch.empty_like(X0) if want_intermediates else None
         P = torch.empty_like(X0) if want_intermediates else None
-        gc = g._c()
         pc, keep = p._c()
         self._check(self.lib.lne_propagate(self.h, ctypes.byref(gc), ctypes.byref(pc), _ptr(X0), _ptr(X), _ptr(F),
                                            _ptr(P), _stream()))
@@ -478,7 +525,13 @@ class Context:
         lab = labels.contiguous().to(torch.uint8)
         tr = train_idx.contiguous().to(torch.int32)
         te = test_idx.contiguous().to(torch.int32)
+        if X.dim() != 2 or lab.dim() != 2:
+            raise ValueError("X and labels must be 2-D")
         n, d = X.shape
+        _check_tensor("X", X, self.dev)
+        _check_tensor("labels", lab, self.dev, min_rows=n)
+        _check_tensor("train_idx", tr, self.dev)
+        _check_tensor("test_idx", te, self.dev)
         ma, mi = ctypes.c_double(), ctypes.c_double()
         self._check(self.lib.lne_macro_f1(self.h, _ptr(X), n, d, d, _ptr(lab), lab.shape[1], _ptr(tr), tr.numel(),
                                           _ptr(te), te.numel(), float(C), int(iters), ctypes.byref(ma),
@@ -495,10 +548,15 @@ class Context:
         lab = labels.contiguous().to(torch.uint8)
         tr = train_idx.contiguous().to(torch.int32)
         te = test_idx.contiguous().to(torch.int32)
+        if lab.dim() != 2:
+            raise ValueError("labels must be 2-D")
+        gc = g._c(self.dev)
+        _check_tensor("labels", lab, self.dev, min_rows=g.n)
+        _check_tensor("train_idx", tr, self.dev)
+        _check_tensor("test_idx", te, self.dev)
         ma = (ctypes.c_double * nc)()
         mi = (ctypes.c_double * nc)()
         X = torch.empty((nc, g.n, cands[0].d), dtype=torch.float32, device=self.dev) if want_embeddings else None
-        gc = g._c()
         self._check(self.lib.lne_tune_batch(self.h, ctypes.byref(gc), ctypes.cast(arr, ctypes.c_void_p), nc,
                                             _ptr(lab), lab.shape[1], _ptr(tr), tr.numel(), _ptr(te), te.numel(),
                                             float(C), int(iters), ma, mi, _ptr(X) if X is not None else None,
@@ -520,8 +578,13 @@ class Context:
             lab = lab.contiguous().to(torch.uint8)
             tr = tr.contiguous().to(torch.int32)
             te = te.contiguous().to(torch.int32)
+            if lab.dim() != 2:
+                raise ValueError(f"task {t}: labels must be 2-D")
+            _check_tensor(f"task {t} labels", lab, self.dev, min_rows=g.n)
+            _check_tensor(f"task {t} train_idx", tr, self.dev)
+            _check_tensor(f"task {t} test_idx", te, self.dev)
             keep += [lab, tr, te]
-            tarr[t] = _Task(g._c(), lab.data_ptr(), lab.shape[1], tr.data_ptr(), tr.numel(), te.data_ptr(),
+            tarr[t] = _Task(g._c(self.dev), lab.data_ptr(), lab.shape[1], tr.data_ptr(), tr.numel(), te.data_ptr(),
                             te.numel())
         built = [p._c() for row in cands for p in row]
         parr = (_Params * (nt * nc))(*[b[0] for b in built])
@@ -539,6 +602,7 @@ class Context:
 
     def surrogate_fit_scaling(self, X: torch.Tensor):
         X = X.contiguous().float()
+        _check_tensor("X", X, self.dev, cols=SURROGATE_INPUTS)
         self._check(self.lib.lne_surrogate_fit_scaling(self.h, _ptr(X), X.shape[0], _stream()))
 
     def surrogate_set_params(self, theta, mean, std):
@@ -559,6 +623,8 @@ class Context:
                         seed: int = 0) -> float:
         X = X.contiguous().float()
         y = y.contiguous().float()
+        _check_tensor("X", X, self.dev, cols=SURROGATE_INPUTS)
+        _check_tensor("y", y, self.dev, min_numel=X.shape[0])
         loss = ctypes.c_double()
         self._check(self.lib.lne_surrogate_train(self.h, _ptr(X), _ptr(y), X.shape[0], int(epochs), int(batch),
                                                  float(lr), int(seed) & 0xFFFFFFFFFFFFFFFF, ctypes.byref(loss),
@@ -567,6 +633,7 @@ class Context:
 
     def surrogate_predict(self, X: torch.Tensor) -> torch.Tensor:
         X = X.contiguous().float()
+        _check_tensor("X", X, self.dev, cols=SURROGATE_INPUTS)
         out = torch.empty(X.shape[0], dtype=torch.float32, device=self.dev)
         self._check(self.lib.lne_surrogate_predict(self.h, _ptr(X), X.shape[0], _ptr(out), _stream()))
         return out
@@ -574,6 +641,8 @@ class Context:
     def surrogate_grad(self, X: torch.Tensor, y: torch.Tensor):
         X = X.contiguous().float()
         y = y.contiguous().float()
+        _check_tensor("X", X, self.dev, cols=SURROGATE_INPUTS)
+        _check_tensor("y", y, self.dev, min_numel=X.shape[0])
         g = torch.empty(SURROGATE_PARAMS, dtype=torch.float32, device=self.dev)
         loss = ctypes.c_double()
         self._check(self.lib.lne_surrogate_grad(self.h, _ptr(X), _ptr(y), X.shape[0], _ptr(g), ctypes.byref(loss),
@@ -581,8 +650,10 @@ class Context:
         return g, float(loss.value)
 
     def embed(self, g: DeviceGraph, p: Params, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        gc = g._c(self.dev)
+        if out is not None:
+            _check_tensor("out", out, self.dev, torch.float32, shape=(g.n, p.d))
         X = out if out is not None else torch.empty((g.n, p.d), dtype=torch.float32, device=self.dev)
-        gc = g._c()
         pc, keep = p._c()
         self._check(self.lib.lne_embed(self.h, ctypes.byref(gc), ctypes.byref(pc), _ptr(X), _stream()))
         return X
