@@ -178,8 +178,9 @@ const char *lne_last_error(const lne_ctx *ctx);
 int64_t lne_workspace_bytes(const lne_ctx *ctx);
 /* Release all workspace (the next call re-allocates). */
 int lne_trim(lne_ctx *ctx);
-/* Set a context option (LNE_OPT_*); both aggregation methods give identical
- * (exact) counts, they differ in memory use and speed. */
+/* Set a context option (LNE_OPT_*); the three aggregation methods give
+ * identical (exact) counts, they differ in memory use and speed. An unknown
+ * option or a value outside its range fails with LNE_ERR_INVALID. */
 int lne_set_option(lne_ctx *ctx, int option, int64_t value);
 
 /*
