@@ -293,7 +293,9 @@ int lne_cholqr2(lne_ctx *ctx, float *Y_dev, int64_t n, int32_t c, int64_t ld, do
  * factor of the last sketch, so that Y = Q R gives Y's SVD as Q U_R) -- the
  * eig step of eigSVD (Algorithm 2). U_dev [c][c] row-major FP64 (column j = j-th
  * left singular vector), sigma_dev [c] FP64 descending. FP64-accurate: FP32
- * one-sided Jacobi start, then Ogita-Aishima refinement of the SVD of R in FP64.
+ * one-sided Jacobi start, then Ogita-Aishima refinement of the SVD of R in FP64,
+ * then an exact FP64 two-sided Jacobi on the pairs of close singular values
+ * the refinement leaves coupled.
  */
 int lne_svd_small(lne_ctx *ctx, const double *R_dev, int32_t c, double *U_dev, double *sigma_dev,
                   void *stream);
