@@ -94,7 +94,7 @@ def walk_ops_per_sample(params):
 
 def kernel_model(name, g, params, counts):
     """(bound, algorithmic amount per launch, unit, per-unit description) of a
-    kernel, or None. The byte models are the survey's algorithmic ones:
+    kernel, or None. The byte models count the algorithmic (compulsory) bytes:
 
     walk_count / walk_emit (sampling into the pair table): HBM -- 8 B per
         sample (4 B key write + 4 B key read of the aggregation; the walk's
@@ -751,7 +751,7 @@ def run_large(args):
     csr = ctx.sparsifier_csr(g, p32, copy=False)
     out["config"]["nnz_M"] = csr["nnz"]
     # roofline of the products with M (q + 1 per embedding): the compulsory
-    # bytes of the survey's model (8 B per nonzero, the BF16 operand row once,
+    # bytes (8 B per nonzero, the BF16 operand row once,
     # the FP32 result row), and the row gathers (2 c B per nonzero) separately
     if "spmm" in out["stage_ms"]:
         hbm, _, src = read_peaks()

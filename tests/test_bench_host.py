@@ -22,7 +22,7 @@ def test_walk_ops_per_sample_closed_forms():
     assert bench.walk_ops_per_sample({"s": [1, 1, 1, 1]}) == pytest.approx(want)
 
 
-def test_kernel_models_are_the_survey_byte_counts():
+def test_kernel_models_are_the_algorithmic_byte_counts():
     g = synth.sbm(300, 3, 0.05, 0.01, seed=1)
     params = dict(d=32, oversample=16, precision=0)
     counts = dict(total_samples=1000.0, nnz_M=5000)
