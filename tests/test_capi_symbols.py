@@ -76,3 +76,34 @@ def test_binding_constants_match_header():
         assert getattr(lne, short) == value, short
     for code, name in lne.ERRORS.items():
         assert h[name] == code, name
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """Every C ABI struct as a C99 compiler lays it out from include/lne.h
+    (size and each field's offset) equals the binding's ctypes mirror."""
+    import shutil
+    import subprocess
+    from paper_2302_07084_gb300 import lne
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    exe = tmp_path / "abi_layout"
+    subprocess.run([cc, "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "cpp", "abi_layout.c"), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = dict((ln.rsplit(" ", 1)[0], int(ln.rsplit(" ", 1)[1])) for ln in out if ln.strip())
+    mirrors = {"lne_graph": lne._Graph, "lne_params": lne._Params, "lne_csr": lne._Csr, "lne_counts": lne._Counts,
+               "lne_task": lne._Task, "lne_trace_entry": lne._TraceEntry}
+    # the binding's field names where they differ from the header's
+    renames = {("lne_task", "labels_dev"): "labels", ("lne_task", "train_dev"): "train",
+               ("lne_task", "test_dev"): "test"}
+    checked = 0
+    for cname, py in mirrors.items():
+        assert c_layout[f"{cname} sizeof"] == ctypes.sizeof(py), cname
+        c_fields = [k.split(".", 1)[1] for k in c_layout if k.startswith(cname + ".")]
+        assert len(c_fields) == len(py._fields_), cname
+        for f in c_fields:
+            pf = renames.get((cname, f), f)
+            assert c_layout[f"{cname}.{f}"] == getattr(py, pf).offset, (cname, f)
+            checked += 1
+    assert checked == sum(len(py._fields_) for py in mirrors.values())
